@@ -1,0 +1,187 @@
+/*
+ * glasma.h -- C ABI of the GB300 colored-particle-in-cell (CPIC) library:
+ * boost-invariant SU(3) Glasma fields coupled to Wong test particles
+ * (Avramescu, Baran, Greco, Ipp, Mueller, Ruggieri, arXiv:2303.05599).
+ *
+ * One context holds one event: an N x N periodic transverse lattice with the
+ * Glasma fields and an ensemble of test particles of up to GL_MAX_SPECIES
+ * species.  All device memory lives in ONE workspace that the CALLER
+ * allocates (cudaMalloc, or a PyTorch tensor) and owns; the library never
+ * allocates device memory.  The context itself is a small host object owned
+ * by the library (gl_create / gl_destroy).
+ *
+ * Every call is enqueued on the CUDA stream given to gl_create and returns
+ * without waiting, except gl_upload, gl_download and observables, which wait
+ * for the stream.  Calls on one context must not overlap from several host
+ * threads.  Errors are returned as gl_status; gl_error_string gives the last
+ * message of a context.  No call aborts the process.
+ *
+ * Units.  The configuration is given in physical units (fm, GeV).  Inside,
+ * everything is in lattice units with a = L/N: t = tau/a, dt = dtau/a,
+ * momenta p a, masses m a.  The fields are stored as
+ *   phi = g A_eta, pi = g a^2 P^eta, e_i = g a P^i   (Sec. 2.1),
+ * Hermitian traceless, given by their 8 components X^a = 2 tr(X T^a) with
+ * T^a = lambda^a/2.  The site fields are E^ = g a^2 E, B^ = g a^2 B (Sec. 3.1).
+ *
+ * Canonical host layouts used by gl_upload / gl_download (always double):
+ *   GL_BUF_LINKS      [2][N*N][18]  U_x, U_y at step n; site s = y*N + x;
+ *                                   3x3 complex row-major, (re, im) pairs
+ *   GL_BUF_PHI        [N*N][8]      phi(n)
+ *   GL_BUF_E          [2][N*N][8]   e_x, e_y at n - 1/2
+ *   GL_BUF_PI         [N*N][8]      pi at n - 1/2
+ *   GL_BUF_SITE       [6][N*N][8]   E_x, E_y, E_eta, B_x, B_y, B_eta at the
+ *                                   last pushed time t_{n-1} (download only)
+ *   GL_BUF_PARTICLES  [np][16]      x, y, eta, p^x, p^y, P_eta, Q^1..Q^8,
+ *                                   p_T^2 at formation, species index;
+ *                                   x, y in [0, N); P_eta = tau^2 p^eta
+ *                                   (static species: accumulated p_L)
+ */
+#ifndef GLASMA_H
+#define GLASMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GL_ABI_VERSION 1
+#define GL_MAX_SPECIES 8
+
+typedef enum {
+    GL_OK = 0,
+    GL_ERR_ARG = 1,      /* invalid argument or configuration */
+    GL_ERR_CUDA = 2,     /* a CUDA runtime call or kernel launch failed */
+    GL_ERR_STATE = 3,    /* call out of order (e.g. push without field step) */
+    GL_ERR_TIMEOUT = 4,  /* a bounded device wait gave up */
+    GL_ERR_NUMERIC = 5,  /* non-finite values or failed link matching at init */
+    GL_ERR_SIZE = 6      /* workspace or host buffer of the wrong size */
+} gl_status;
+
+typedef enum { GL_FP64 = 0, GL_FP32_2ROW = 1 } gl_precision;
+
+typedef enum {
+    GL_BUF_LINKS = 0,
+    GL_BUF_PHI = 1,
+    GL_BUF_E = 2,
+    GL_BUF_PI = 3,
+    GL_BUF_SITE = 4,
+    GL_BUF_PARTICLES = 5
+} gl_buffer;
+
+/* One MV event (Sec. 2, parameters of Sec. 7.1). */
+typedef struct {
+    int32_t N;              /* lattice sites per transverse direction, >= 4 */
+    int32_t Ns;             /* colour sheets per nucleus (eq. for the regularised correlator) */
+    int32_t precision;      /* gl_precision */
+    int32_t reunit_every;   /* FP32: re-unitarise links in FP64 every k steps (0: never) */
+    double L_fm;            /* transverse box length */
+    double g2mu_GeV;        /* MV parameter g^2 mu */
+    double mIR_GeV;         /* infrared regulator of the Poisson kernel */
+    double LambdaUV_GeV;    /* ultraviolet cutoff of the Poisson kernel (<= 0: none) */
+    double dtau_over_a;     /* leapfrog time step in units of a */
+    uint64_t seed;          /* Philox key of this event's random numbers */
+} gl_config;
+
+/* One species of test particles (Sec. 3.1 and 7.1). */
+typedef struct {
+    double mass_GeV;        /* INFINITY: infinitely massive static quark (Sec. 5.1) */
+    double tau_form_fm;     /* formation time; pushed from the first t_n >= tau_form */
+    int64_t count;
+    int32_t rep;            /* 0: fundamental charge (q2 = 4, q3 = 10/3); 1: adjoint (24, 0) */
+    int32_t mom_mode;       /* 0: |p_T| = p0, uniform azimuth; 1: |p_T| ~ U[p0, p1], uniform
+                               azimuth; 2: p^x = p0, p^y = 0 */
+    double p0_GeV, p1_GeV;
+} gl_species;
+
+/* Ensemble and field observables (Sec. 3.1 eq. for momentum broadening). */
+typedef struct {
+    int64_t step;                       /* field step n of the context */
+    double tau_fm;                      /* tau of the particle state */
+    int32_t n_species;
+    int32_t pad;
+    int64_t n_active[GL_MAX_SPECIES];   /* particles pushed at the last step */
+    double sum_px2[GL_MAX_SPECIES];     /* sums over active particles, GeV^2 */
+    double sum_py2[GL_MAX_SPECIES];
+    double sum_pL2[GL_MAX_SPECIES];     /* p_L = lab p^z (static: accumulated) */
+    double sum_dpT2[GL_MAX_SPECIES];    /* sum of p_T^2 - p_T^2(tau_form) */
+    double casimir2_dev[GL_MAX_SPECIES];/* max |q2 - q2(R)| over particles */
+    double casimir3_dev[GL_MAX_SPECIES];/* max |q3 - q3(R)| */
+    double gauss_max;                   /* max over sites of |G(x)|, lattice units */
+    double gauss_rms;
+    double unitarity_max;               /* max over links of ||U U^+ - 1||_F */
+    double mean_trE_T2;                 /* lattice means of tr(E_x^2 + E_y^2), tr E_eta^2, */
+    double mean_trE_L2;                 /* tr(B_x^2 + B_y^2), tr B_eta^2 at the last pushed */
+    double mean_trB_T2;                 /* time, lattice units (E^ = g a^2 E) */
+    double mean_trB_L2;
+} gl_obs;
+
+typedef struct gl_ctx gl_ctx;
+
+/* Bytes of device workspace a context with this configuration needs.
+ * Returns 0 for an invalid configuration. */
+size_t gl_workspace_bytes(const gl_config* cfg, const gl_species* species, int32_t n_species);
+
+/* Create a context on the current CUDA device.  d_workspace: caller-owned
+ * device memory of at least gl_workspace_bytes() bytes, 256-byte aligned,
+ * kept alive until gl_destroy.  stream: a cudaStream_t (NULL = default). */
+gl_status gl_create(const gl_config* cfg, const gl_species* species, int32_t n_species, void* d_workspace,
+                    size_t workspace_bytes, void* stream, gl_ctx** out);
+
+/* Release the host context (the workspace stays the caller's). */
+gl_status gl_destroy(gl_ctx* ctx);
+
+/* Message for the last error of ctx (or of gl_create when ctx is NULL). */
+const char* gl_error_string(const gl_ctx* ctx);
+
+/* MV initial condition at tau = 0 (Sec. 2.1): Gaussian colour charges on Ns
+ * sheets per nucleus, Poisson solve by FFT, path-ordered Wilson lines, the
+ * pure-gauge links of both nuclei, the Glasma links from the lattice matching
+ * condition and E_eta(0).  Sets the step to 0.  GL_ERR_NUMERIC if the link
+ * matching did not converge somewhere. */
+gl_status glasma_init(gl_ctx* ctx);
+
+/* Sample all particles (Sec. 3.1 and 4.2): uniform transverse positions,
+ * eta = 0, momenta per species mode, classical charges Q = U Q0 U^+ with U
+ * Haar-distributed. */
+gl_status wong_init(gl_ctx* ctx);
+
+/* Copy a host buffer in the canonical layout into the context (waits).
+ * count = number of doubles; GL_ERR_SIZE if it does not match. */
+gl_status gl_upload(gl_ctx* ctx, gl_buffer which, const double* host, size_t count);
+
+/* Copy a context buffer out in the canonical layout (waits). */
+gl_status gl_download(gl_ctx* ctx, gl_buffer which, double* host, size_t count);
+
+/* Set the field step index n (t_n = n dt) of the uploaded state; the
+ * particles are taken to be at the same time. */
+gl_status gl_set_step(gl_ctx* ctx, int64_t step);
+
+/* Advance the fields n_steps leapfrog steps (Sec. 2.1 equations of motion).
+ * Particles that are then more than one step behind can no longer be pushed
+ * (wong_push returns GL_ERR_STATE). */
+gl_status glasma_step(gl_ctx* ctx, int32_t n_steps);
+
+/* Interpolate E and B to the lattice sites at the particles' time t_n
+ * (Sec. 3.1 formulas; GL_BUF_SITE).  Needs exactly one glasma_step since the
+ * particles' time (the momenta at n - 1/2 and n + 1/2 are both used).
+ * wong_push calls it itself when it has not been called for this step. */
+gl_status wong_site_fields(gl_ctx* ctx);
+
+/* Push the particles from t_n to t_{n+1} (Sec. 3.1 and 3.2: site E/B
+ * interpolation, Euler step of Wong's equations, NGP colour rotation with the
+ * crossed links and the rapidity Wilson line).  Needs exactly one preceding
+ * glasma_step since the particles' time. */
+gl_status wong_push(gl_ctx* ctx);
+
+/* n_steps coupled steps: glasma_step(1) + wong_push each. */
+gl_status gl_step_coupled(gl_ctx* ctx, int32_t n_steps);
+
+/* Ensemble sums and field checks at the current time (waits). */
+gl_status observables(gl_ctx* ctx, gl_obs* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -77,6 +77,7 @@ void or_wilson_lines(int N, int Ns, double g2mu_a, double m_a, double Lambda_a,
     for (int64_t s = 0; s < V; s++) m_store(m_id(), vdag + s * 18);
     const double sigma = g2mu_a / sqrt((double)Ns);
     for (int sheet = 0; sheet < Ns; sheet++) {
+#pragma omp parallel for schedule(static)
         for (int64_t s = 0; s < V; s++) {
             double z[8];
             for (int j = 0; j < 2; j++) {
@@ -87,6 +88,7 @@ void or_wilson_lines(int N, int Ns, double g2mu_a, double m_a, double Lambda_a,
             }
             for (int a = 0; a < 8; a++) rho[a * V + s] = sigma * z[a];
         }
+#pragma omp parallel for schedule(static)
         for (int a = 0; a < 8; a++) {
             double complex* f = rho + a * V;
             fft2(f, N, -1);
@@ -95,6 +97,7 @@ void or_wilson_lines(int N, int Ns, double g2mu_a, double m_a, double Lambda_a,
             for (int64_t s = 0; s < V; s++) f[s] /= (double)V;
         }
         /* V^+ <- V^+ exp(-i alpha_n): sheet 1 leftmost */
+#pragma omp parallel for schedule(static)
         for (int64_t s = 0; s < V; s++) {
             double al[8];
             for (int a = 0; a < 8; a++) al[a] = -creal(rho[a * V + s]);

@@ -1,0 +1,202 @@
+"""ctypes binding of ``libglasma_gb300.so`` (declared in include/glasma.h).
+
+Argument marshalling only: every numerical step runs in the library's CUDA
+kernels.  PyTorch supplies the device workspace and the CUDA stream.  Loading
+fails loudly when the library is missing; there is no other code path.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libglasma_gb300.so")
+
+GL_MAX_SPECIES = 8
+GL_OK, GL_ERR_ARG, GL_ERR_CUDA, GL_ERR_STATE, GL_ERR_TIMEOUT, GL_ERR_NUMERIC, GL_ERR_SIZE = range(7)
+GL_FP64, GL_FP32_2ROW = 0, 1
+GL_BUF_LINKS, GL_BUF_PHI, GL_BUF_E, GL_BUF_PI, GL_BUF_SITE, GL_BUF_PARTICLES = range(6)
+
+STATUS_NAMES = {0: "GL_OK", 1: "GL_ERR_ARG", 2: "GL_ERR_CUDA", 3: "GL_ERR_STATE", 4: "GL_ERR_TIMEOUT",
+                5: "GL_ERR_NUMERIC", 6: "GL_ERR_SIZE"}
+
+
+class gl_config(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("Ns", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reunit_every", ctypes.c_int32), ("L_fm", ctypes.c_double), ("g2mu_GeV", ctypes.c_double),
+                ("mIR_GeV", ctypes.c_double), ("LambdaUV_GeV", ctypes.c_double),
+                ("dtau_over_a", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class gl_species(ctypes.Structure):
+    _fields_ = [("mass_GeV", ctypes.c_double), ("tau_form_fm", ctypes.c_double), ("count", ctypes.c_int64),
+                ("rep", ctypes.c_int32), ("mom_mode", ctypes.c_int32), ("p0_GeV", ctypes.c_double),
+                ("p1_GeV", ctypes.c_double)]
+
+
+_D8 = ctypes.c_double * GL_MAX_SPECIES
+
+
+class gl_obs(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("tau_fm", ctypes.c_double), ("n_species", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("n_active", ctypes.c_int64 * GL_MAX_SPECIES),
+                ("sum_px2", _D8), ("sum_py2", _D8), ("sum_pL2", _D8), ("sum_dpT2", _D8),
+                ("casimir2_dev", _D8), ("casimir3_dev", _D8), ("gauss_max", ctypes.c_double),
+                ("gauss_rms", ctypes.c_double), ("unitarity_max", ctypes.c_double),
+                ("mean_trE_T2", ctypes.c_double), ("mean_trE_L2", ctypes.c_double),
+                ("mean_trB_T2", ctypes.c_double), ("mean_trB_L2", ctypes.c_double)]
+
+
+# every symbol include/glasma.h declares, with its signature
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "gl_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(gl_config), ctypes.POINTER(gl_species), ctypes.c_int32]),
+    "gl_create": (ctypes.c_int, [ctypes.POINTER(gl_config), ctypes.POINTER(gl_species), ctypes.c_int32, _P,
+                                 ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    "gl_destroy": (ctypes.c_int, [_P]),
+    "gl_error_string": (ctypes.c_char_p, [_P]),
+    "glasma_init": (ctypes.c_int, [_P]),
+    "wong_init": (ctypes.c_int, [_P]),
+    "gl_upload": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
+    "gl_download": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
+    "gl_set_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "glasma_step": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "wong_site_fields": (ctypes.c_int, [_P]),
+    "wong_push": (ctypes.c_int, [_P]),
+    "gl_step_coupled": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "observables": (ctypes.c_int, [_P, ctypes.POINTER(gl_obs)]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libglasma_gb300.so is not built; run __graft_entry__.build() "
+                               "(python paper_2303_05599_gb300/build.py)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class GlasmaError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__("%s: %s (%s)" % (where, STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _check(status, ctx, where):
+    if status != GL_OK:
+        msg = lib().gl_error_string(ctx)
+        raise GlasmaError(status, where, msg.decode() if msg else "")
+
+
+def make_config(w):
+    """gl_config from a workloads.Workload."""
+    return gl_config(N=w.N, Ns=w.Ns, precision=w.precision, reunit_every=w.reunit_every, L_fm=w.L_fm,
+                     g2mu_GeV=w.g2mu_GeV, mIR_GeV=w.mIR_GeV, LambdaUV_GeV=w.LambdaUV_GeV,
+                     dtau_over_a=w.dtau_over_a, seed=w.seed)
+
+
+def make_species(w):
+    arr = (gl_species * max(1, len(w.species)))()
+    for k, s in enumerate(w.species):
+        arr[k] = gl_species(mass_GeV=s.mass_GeV, tau_form_fm=s.tau_form_fm, count=s.count, rep=s.rep,
+                            mom_mode=s.mom_mode, p0_GeV=s.p0_GeV, p1_GeV=s.p1_GeV)
+    return arr
+
+
+def gl_workspace_bytes(w):
+    cfg = make_config(w)
+    sp = make_species(w)
+    return int(lib().gl_workspace_bytes(ctypes.byref(cfg), sp, len(w.species)))
+
+
+class Event:
+    """One MV event with its particle ensemble on the current CUDA device.
+
+    The workspace is a torch uint8 tensor on the device; all calls are
+    enqueued on the given torch stream (default: the current stream)."""
+
+    def __init__(self, workload, stream=None, device=None):
+        import torch
+        self.w = workload
+        self.cfg = make_config(workload)
+        self.sp = make_species(workload)
+        nbytes = int(lib().gl_workspace_bytes(ctypes.byref(self.cfg), self.sp, len(workload.species)))
+        if nbytes == 0:
+            raise GlasmaError(GL_ERR_ARG, "gl_workspace_bytes", "invalid workload")
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.ctx = ctypes.c_void_p()
+        st = lib().gl_create(ctypes.byref(self.cfg), self.sp, len(workload.species), ctypes.c_void_p(aligned),
+                             nbytes, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.ctx))
+        _check(st, None, "gl_create")
+        self.N = workload.N
+        self.np = workload.n_particles
+
+    def close(self):
+        if self.ctx:
+            lib().gl_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- the C ABI, one call each
+    def glasma_init(self):
+        _check(lib().glasma_init(self.ctx), self.ctx, "glasma_init")
+
+    def wong_init(self):
+        _check(lib().wong_init(self.ctx), self.ctx, "wong_init")
+
+    def glasma_step(self, n=1):
+        _check(lib().glasma_step(self.ctx, n), self.ctx, "glasma_step")
+
+    def wong_site_fields(self):
+        _check(lib().wong_site_fields(self.ctx), self.ctx, "wong_site_fields")
+
+    def wong_push(self):
+        _check(lib().wong_push(self.ctx), self.ctx, "wong_push")
+
+    def step(self, n=1):
+        _check(lib().gl_step_coupled(self.ctx, n), self.ctx, "gl_step_coupled")
+
+    def set_step(self, n):
+        _check(lib().gl_set_step(self.ctx, n), self.ctx, "gl_set_step")
+
+    def observables(self):
+        o = gl_obs()
+        _check(lib().observables(self.ctx, ctypes.byref(o)), self.ctx, "observables")
+        return o
+
+    def _shape(self, which):
+        V = self.N * self.N
+        return {GL_BUF_LINKS: (2, V, 18), GL_BUF_PHI: (V, 8), GL_BUF_E: (2, V, 8), GL_BUF_PI: (V, 8),
+                GL_BUF_SITE: (6, V, 8), GL_BUF_PARTICLES: (self.np, 16)}[which]
+
+    def upload(self, which, arr):
+        a = np.ascontiguousarray(arr, dtype=np.float64)
+        if a.shape != self._shape(which) and a.size == int(np.prod(self._shape(which))):
+            a = a.reshape(self._shape(which))
+        _check(lib().gl_upload(self.ctx, which, a.ctypes.data_as(ctypes.c_void_p), a.size), self.ctx, "gl_upload")
+
+    def download(self, which):
+        a = np.empty(self._shape(which), dtype=np.float64)
+        _check(lib().gl_download(self.ctx, which, a.ctypes.data_as(ctypes.c_void_p), a.size), self.ctx,
+               "gl_download")
+        return a

@@ -1,0 +1,392 @@
+// C ABI of the library (declared in include/glasma.h): context, workspace
+// carving, call ordering and status codes.  Every numerical step runs in the
+// kernels of field.cu, particles.cu, init.cu and obs.cu.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "internal.h"
+
+namespace gl {
+size_t init_scratch_bytes(int64_t Vn);
+void launch_parts_convert(int prec, void* parts, int64_t np, double* stg, int to_device, cudaStream_t st);
+}  // namespace gl
+
+using namespace gl;
+
+static const double HBARC = 0.1973269804;  // GeV fm
+static const int MAX_BLOCKS = 1024;
+
+struct gl_ctx {
+    gl_config cfg;
+    int ns;
+    gl_species sp[GL_MAX_SPECIES];
+    int N;
+    int prec;
+    int64_t Vn, np;
+    int64_t off[GL_MAX_SPECIES + 1];
+    double a_fm, aG, dt, g2mu_a, m_a, Lambda_a;
+    double t_form[GL_MAX_SPECIES];
+    double p0[GL_MAX_SPECIES], p1[GL_MAX_SPECIES];
+    int rep[GL_MAX_SPECIES], mode[GL_MAX_SPECIES];
+    SpeciesParams spp;
+    double q0[2][8];
+    double q2ref[GL_MAX_SPECIES], q3ref[GL_MAX_SPECIES];
+    cudaStream_t stream;
+    char* ws;
+    size_t ws_bytes;
+    void* field[2];
+    void* site;
+    void* parts;
+    void* scratch;
+    size_t scratch_bytes;
+    double* partials;
+    double* obs_dev;
+    int* d_bad;
+    int cur;
+    int64_t step, pstep;
+    int64_t site_step;  // particle step whose site fields are in `site` (-1: none)
+    int reunit_count;
+    char err[256];
+};
+
+static char g_create_err[256] = "";
+
+static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static gl_status fail(gl_ctx* c, gl_status s, const char* msg) {
+    char* dst = c ? c->err : g_create_err;
+    snprintf(dst, 256, "%s", msg);
+    return s;
+}
+
+static gl_status check_cuda(gl_ctx* c, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        char m[256];
+        snprintf(m, sizeof m, "%s: %s", where, cudaGetErrorString(e));
+        return fail(c, GL_ERR_CUDA, m);
+    }
+    return GL_OK;
+}
+
+static const char* validate(const gl_config* cfg, const gl_species* sp, int32_t ns) {
+    if (!cfg) return "null config";
+    if (cfg->N < 4 || cfg->N > 32768) return "N must be in [4, 32768]";
+    if (cfg->Ns < 1) return "Ns must be >= 1";
+    if (cfg->precision != GL_FP64 && cfg->precision != GL_FP32_2ROW) return "unknown precision";
+    if (!(cfg->L_fm > 0) || !(cfg->dtau_over_a > 0)) return "L_fm and dtau_over_a must be positive";
+    if (ns < 0 || ns > GL_MAX_SPECIES) return "n_species must be in [0, 8]";
+    if (ns > 0 && !sp) return "null species";
+    int64_t np = 0;
+    for (int k = 0; k < ns; k++) {
+        if (sp[k].count < 0) return "negative particle count";
+        if (sp[k].rep != 0 && sp[k].rep != 1) return "rep must be 0 or 1";
+        if (sp[k].mom_mode < 0 || sp[k].mom_mode > 2) return "mom_mode must be 0, 1 or 2";
+        if (!(sp[k].mass_GeV >= 0)) return "mass must be >= 0 or INFINITY";
+        np += sp[k].count;
+    }
+    if (np >= ((int64_t)1 << 31)) return "at most 2^31 - 1 particles";
+    return nullptr;
+}
+
+struct Carve {
+    size_t field, site, parts, scratch, partials, obs, bad, total;
+};
+
+static Carve carve(const gl_config* cfg, int64_t np) {
+    const int64_t Vn = (int64_t)cfg->N * cfg->N;
+    const int prec = cfg->precision;
+    Carve c;
+    size_t o = 0;
+    c.field = o; o += 2 * a256(field_bytes(prec, Vn));
+    c.site = o; o += a256(site_bytes(prec, Vn));
+    c.parts = o; o += a256(particle_bytes(prec, np));
+    size_t sc = init_scratch_bytes(Vn);
+    size_t stg = (size_t)Vn * 6 * 8 * sizeof(double);
+    if (stg > sc) sc = stg;
+    if ((size_t)np * 16 * sizeof(double) > sc) sc = (size_t)np * 16 * sizeof(double);
+    c.scratch = o; o += a256(sc);
+    c.partials = o; o += a256((size_t)MAX_BLOCKS * (GL_MAX_SPECIES * PO_N + FO_N) * sizeof(double));
+    c.obs = o; o += a256((GL_MAX_SPECIES * PO_N + FO_N) * sizeof(double));
+    c.bad = o; o += 256;
+    c.total = o;
+    return c;
+}
+
+// Q0 of the fundamental classical charge: Q^8 = s is the root near -1.06 of
+// s^3 - 12 s - 20/sqrt(3) = 0 (q2 = 4, q3 = 10/3 with only Q^5, Q^8 nonzero),
+// taken from the trigonometric form of the depressed-cubic roots; Q^5 = -sqrt(4 - s^2).
+static void q0_vectors(double q0[2][8]) {
+    memset(q0, 0, sizeof(double) * 16);
+    const double p = -12.0, q = -20.0 / sqrt(3.0);
+    const double r = 2.0 * sqrt(-p / 3.0);
+    const double th = acos((3.0 * q / (2.0 * p)) * sqrt(-3.0 / p)) / 3.0;
+    const double s = r * cos(th - 2.0 * M_PI / 3.0);
+    q0[0][7] = s;
+    q0[0][4] = -sqrt(4.0 - s * s);
+    q0[1][0] = sqrt(24.0);
+}
+
+extern "C" {
+
+size_t gl_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t ns) {
+    if (validate(cfg, sp, ns)) return 0;
+    int64_t np = 0;
+    for (int k = 0; k < ns; k++) np += sp[k].count;
+    return carve(cfg, np).total;
+}
+
+gl_status gl_create(const gl_config* cfg, const gl_species* sp, int32_t ns, void* d_workspace, size_t bytes,
+                    void* stream, gl_ctx** out) {
+    if (!out) return fail(nullptr, GL_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    if (const char* m = validate(cfg, sp, ns)) return fail(nullptr, GL_ERR_ARG, m);
+    if (!d_workspace || ((uintptr_t)d_workspace & 255)) return fail(nullptr, GL_ERR_ARG, "workspace must be 256-byte aligned");
+    gl_ctx* c = new (std::nothrow) gl_ctx;
+    if (!c) return fail(nullptr, GL_ERR_ARG, "host allocation failed");
+    memset(c, 0, sizeof *c);
+    c->cfg = *cfg;
+    c->ns = ns;
+    c->N = cfg->N;
+    c->prec = cfg->precision;
+    c->Vn = (int64_t)cfg->N * cfg->N;
+    c->np = 0;
+    c->off[0] = 0;
+    for (int k = 0; k < ns; k++) {
+        c->sp[k] = sp[k];
+        c->np += sp[k].count;
+        c->off[k + 1] = c->np;
+    }
+    Carve cv = carve(cfg, c->np);
+    if (bytes < cv.total) {
+        delete c;
+        return fail(nullptr, GL_ERR_SIZE, "workspace smaller than gl_workspace_bytes()");
+    }
+    c->ws = (char*)d_workspace;
+    c->ws_bytes = bytes;
+    c->field[0] = c->ws + cv.field;
+    c->field[1] = c->ws + cv.field + a256(field_bytes(c->prec, c->Vn));
+    c->site = c->ws + cv.site;
+    c->parts = c->ws + cv.parts;
+    c->scratch = c->ws + cv.scratch;
+    c->scratch_bytes = cv.partials - cv.scratch;
+    c->partials = (double*)(c->ws + cv.partials);
+    c->obs_dev = (double*)(c->ws + cv.obs);
+    c->d_bad = (int*)(c->ws + cv.bad);
+    c->stream = (cudaStream_t)stream;
+    // lattice units (same expressions as the Python workload definitions)
+    c->a_fm = cfg->L_fm / cfg->N;
+    c->aG = cfg->L_fm / cfg->N / HBARC;
+    c->dt = cfg->dtau_over_a;
+    c->g2mu_a = cfg->g2mu_GeV * (cfg->L_fm / cfg->N / HBARC);
+    c->m_a = cfg->mIR_GeV * (cfg->L_fm / cfg->N / HBARC);
+    c->Lambda_a = cfg->LambdaUV_GeV > 0 ? cfg->LambdaUV_GeV * (cfg->L_fm / cfg->N / HBARC) : 0.0;
+    q0_vectors(c->q0);
+    c->spp.n_species = ns;
+    for (int k = 0; k < GL_MAX_SPECIES; k++) {
+        const bool on = k < ns;
+        const bool st = on && isinf(sp[k].mass_GeV);
+        c->spp.is_static[k] = st;
+        c->spp.mass[k] = on ? (st ? INFINITY : sp[k].mass_GeV * c->aG) : 0.0;
+        c->t_form[k] = on ? sp[k].tau_form_fm * cfg->N / cfg->L_fm : 0.0;
+        c->p0[k] = on ? sp[k].p0_GeV * c->aG : 0.0;
+        c->p1[k] = on ? sp[k].p1_GeV * c->aG : 0.0;
+        c->rep[k] = on ? sp[k].rep : 0;
+        c->mode[k] = on ? sp[k].mom_mode : 0;
+        c->q2ref[k] = c->rep[k] == 1 ? 24.0 : 4.0;
+        c->q3ref[k] = c->rep[k] == 1 ? 0.0 : 10.0 / 3.0;
+    }
+    c->cur = 0;
+    c->step = c->pstep = 0;
+    c->site_step = -1;
+    *out = c;
+    return GL_OK;
+}
+
+gl_status gl_destroy(gl_ctx* c) {
+    if (!c) return GL_ERR_ARG;
+    delete c;
+    return GL_OK;
+}
+
+const char* gl_error_string(const gl_ctx* c) { return c ? c->err : g_create_err; }
+
+static uint32_t active_mask(const gl_ctx* c, int64_t n) {
+    uint32_t m = 0;
+    const double t = n * c->dt;
+    for (int k = 0; k < c->ns; k++)
+        if (t >= c->t_form[k]) m |= 1u << k;
+    return m;
+}
+
+gl_status glasma_init(gl_ctx* c) {
+    if (!c) return GL_ERR_ARG;
+    launch_mv_init(c->prec, c->field[c->cur], c->scratch, c->N, c->cfg.Ns, c->g2mu_a, c->m_a, c->Lambda_a,
+                   c->cfg.seed, c->d_bad, c->stream);
+    if (gl_status s = check_cuda(c, "glasma_init")) return s;
+    int bad = 0;
+    cudaMemcpyAsync(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, "glasma_init sync");
+    c->step = c->pstep = 0;
+    c->site_step = -1;
+    c->reunit_count = 0;
+    if (bad) {
+        char m[128];
+        snprintf(m, sizeof m, "link matching did not converge on %d links", bad);
+        return fail(c, GL_ERR_NUMERIC, m);
+    }
+    return GL_OK;
+}
+
+gl_status wong_init(gl_ctx* c) {
+    if (!c) return GL_ERR_ARG;
+    launch_sample(c->prec, c->parts, c->np, c->N, c->cfg.seed, c->off, c->ns, c->rep, c->mode, c->p0, c->p1, c->q0,
+                  c->stream);
+    c->pstep = c->step;
+    return check_cuda(c, "wong_init");
+}
+
+static size_t expected_count(const gl_ctx* c, gl_buffer which) {
+    switch (which) {
+        case GL_BUF_LINKS: return (size_t)2 * c->Vn * 18;
+        case GL_BUF_PHI: return (size_t)c->Vn * 8;
+        case GL_BUF_E: return (size_t)2 * c->Vn * 8;
+        case GL_BUF_PI: return (size_t)c->Vn * 8;
+        case GL_BUF_SITE: return (size_t)6 * c->Vn * 8;
+        case GL_BUF_PARTICLES: return (size_t)c->np * 16;
+    }
+    return 0;
+}
+
+static gl_status transfer(gl_ctx* c, gl_buffer which, double* host, size_t count, int to_device) {
+    if (!c || (!host && count)) return GL_ERR_ARG;
+    if ((int)which < 0 || (int)which > GL_BUF_PARTICLES) return fail(c, GL_ERR_ARG, "unknown buffer");
+    if (count != expected_count(c, which)) return fail(c, GL_ERR_SIZE, "host buffer size does not match");
+    if (to_device && which == GL_BUF_SITE) return fail(c, GL_ERR_ARG, "site fields are download-only");
+    if (count == 0) return GL_OK;
+    double* stg = (double*)c->scratch;
+    if (to_device) cudaMemcpyAsync(stg, host, count * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (which == GL_BUF_PARTICLES) launch_parts_convert(c->prec, c->parts, c->np, stg, to_device, c->stream);
+    else launch_convert(c->prec, which, to_device, which == GL_BUF_SITE ? c->site : c->field[c->cur], stg, c->N, c->np,
+                        c->stream);
+    if (!to_device) cudaMemcpyAsync(host, stg, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (gl_status s = check_cuda(c, to_device ? "gl_upload" : "gl_download")) return s;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, "transfer sync");
+    return GL_OK;
+}
+
+gl_status gl_upload(gl_ctx* c, gl_buffer which, const double* host, size_t count) {
+    return transfer(c, which, (double*)host, count, 1);
+}
+
+gl_status gl_download(gl_ctx* c, gl_buffer which, double* host, size_t count) {
+    return transfer(c, which, host, count, 0);
+}
+
+gl_status gl_set_step(gl_ctx* c, int64_t step) {
+    if (!c || step < 0) return GL_ERR_ARG;
+    c->step = c->pstep = step;
+    c->site_step = -1;
+    return GL_OK;
+}
+
+static void one_field_step(gl_ctx* c) {
+    int reunit = 0;
+    if (c->prec == GL_FP32_2ROW && c->cfg.reunit_every > 0) {
+        if (++c->reunit_count >= c->cfg.reunit_every) { reunit = 1; c->reunit_count = 0; }
+    }
+    launch_field_step(c->prec, c->field[c->cur], c->field[1 - c->cur], c->N, c->step * c->dt, c->dt, reunit, c->stream);
+    c->cur = 1 - c->cur;
+    c->step++;
+}
+
+gl_status glasma_step(gl_ctx* c, int32_t n) {
+    if (!c || n < 0) return GL_ERR_ARG;
+    for (int k = 0; k < n; k++) one_field_step(c);
+    return check_cuda(c, "glasma_step");
+}
+
+static gl_status site_once(gl_ctx* c) {
+    if (c->pstep != c->step - 1) return fail(c, GL_ERR_STATE, "needs exactly one field step since the particles' time");
+    launch_site_fields(c->prec, c->field[1 - c->cur], c->field[c->cur], c->site, c->N, c->pstep * c->dt, c->stream);
+    c->site_step = c->pstep;
+    return GL_OK;
+}
+
+gl_status wong_site_fields(gl_ctx* c) {
+    if (!c) return GL_ERR_ARG;
+    if (gl_status s = site_once(c)) return s;
+    return check_cuda(c, "wong_site_fields");
+}
+
+static gl_status push_once(gl_ctx* c) {
+    if (c->pstep != c->step - 1) return fail(c, GL_ERR_STATE, "wong_push needs exactly one field step since the particles' time");
+    const double t = c->pstep * c->dt;
+    if (c->site_step != c->pstep)
+        if (gl_status s = site_once(c)) return s;
+    if (c->np) launch_push(c->prec, c->site, c->field[c->cur], c->parts, c->np, c->N, t, c->dt, active_mask(c, c->pstep),
+                           c->spp, c->stream);
+    c->pstep++;
+    return GL_OK;
+}
+
+gl_status wong_push(gl_ctx* c) {
+    if (!c) return GL_ERR_ARG;
+    if (gl_status s = push_once(c)) return s;
+    return check_cuda(c, "wong_push");
+}
+
+gl_status gl_step_coupled(gl_ctx* c, int32_t n) {
+    if (!c || n < 0) return GL_ERR_ARG;
+    for (int k = 0; k < n; k++) {
+        if (c->pstep != c->step) return fail(c, GL_ERR_STATE, "particles are not at the fields' time");
+        one_field_step(c);
+        if (gl_status s = push_once(c)) return s;
+    }
+    return check_cuda(c, "gl_step_coupled");
+}
+
+gl_status observables(gl_ctx* c, gl_obs* o) {
+    if (!c || !o) return GL_ERR_ARG;
+    memset(o, 0, sizeof *o);
+    const int64_t pushed = c->pstep > 0 ? c->pstep - 1 : -1;
+    const uint32_t mask = pushed >= 0 ? active_mask(c, pushed) : 0u;
+    double host[GL_MAX_SPECIES * PO_N + FO_N];
+    if (c->np) launch_particle_obs(c->prec, c->parts, c->np, c->pstep * c->dt, mask, c->spp, c->q2ref, c->q3ref,
+                                   c->partials, MAX_BLOCKS, c->obs_dev, c->stream);
+    else cudaMemsetAsync(c->obs_dev, 0, GL_MAX_SPECIES * PO_N * sizeof(double), c->stream);
+    launch_field_obs(c->prec, c->field[c->cur], c->site, c->N, c->partials + (size_t)MAX_BLOCKS * GL_MAX_SPECIES * PO_N,
+                     MAX_BLOCKS, c->obs_dev + GL_MAX_SPECIES * PO_N, c->stream);
+    cudaMemcpyAsync(host, c->obs_dev, sizeof host, cudaMemcpyDeviceToHost, c->stream);
+    if (gl_status s = check_cuda(c, "observables")) return s;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, "observables sync");
+    const double u2 = 1.0 / (c->aG * c->aG);  // lattice momentum^2 -> GeV^2
+    o->step = c->step;
+    o->tau_fm = c->pstep * c->dt * c->a_fm;
+    o->n_species = c->ns;
+    for (int k = 0; k < c->ns; k++) {
+        const double* h = host + k * PO_N;
+        o->n_active[k] = (int64_t)llround(h[PO_COUNT]);
+        o->sum_px2[k] = h[PO_PX2] * u2;
+        o->sum_py2[k] = h[PO_PY2] * u2;
+        o->sum_pL2[k] = h[PO_PL2] * u2;
+        o->sum_dpT2[k] = h[PO_DPT2] * u2;
+        o->casimir2_dev[k] = h[PO_Q2];
+        o->casimir3_dev[k] = h[PO_Q3];
+    }
+    const double* f = host + GL_MAX_SPECIES * PO_N;
+    o->gauss_max = f[FO_GMAX];
+    o->gauss_rms = sqrt(f[FO_GSUM] / (double)c->Vn);
+    o->unitarity_max = f[FO_UMAX];
+    o->mean_trE_T2 = f[FO_ET2] / (double)c->Vn;
+    o->mean_trE_L2 = f[FO_EL2] / (double)c->Vn;
+    o->mean_trB_T2 = f[FO_BT2] / (double)c->Vn;
+    o->mean_trB_L2 = f[FO_BL2] / (double)c->Vn;
+    return GL_OK;
+}
+
+}  // extern "C"

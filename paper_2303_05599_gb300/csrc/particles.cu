@@ -1,0 +1,590 @@
+// Test particles (Sec. 3 of arXiv:2303.05599): site interpolation of E and B,
+// Euler integration of Wong's equations in Milne coordinates, CPIC colour
+// rotation, and the sampling of positions, momenta and Haar-random charges.
+//
+// Particle layout (structure of arrays, np entries per plane):
+//   FP64: double2 xy, pxy, (eta, P_eta), q[4]    (7 planes, 112 B per particle)
+//   FP32: float4 (x, y, p^x, p^y), float2 (eta, P_eta), float4 q[2]  (56 B)
+//   both: int32 species, double p_T^2 at formation, int32 original index
+// P_eta = tau^2 p^eta is evolved instead of p^eta so that the step is regular
+// at tau = 0; for an infinitely massive species its slot accumulates p_L.
+#include "internal.h"
+#include "layout.cuh"
+#include "philox.cuh"
+
+namespace gl {
+
+template <typename R>
+struct PState {
+    R x, y, eta, px, py, Pe;
+    A8<R> q;
+};
+
+template <typename R>
+struct Parts;
+
+template <>
+struct Parts<double> {
+    double2 *xy, *pxy, *eP, *q;
+    int32_t* sp;
+    double* pt0;
+    int32_t* id;
+    int64_t np;
+    __device__ PState<double> load(int64_t i) const {
+        PState<double> s;
+        double2 a = xy[i], b = pxy[i], c = eP[i];
+        s.x = a.x; s.y = a.y; s.px = b.x; s.py = b.y; s.eta = c.x; s.Pe = c.y;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            double2 v = q[(size_t)k * np + i];
+            s.q.v[2 * k] = v.x;
+            s.q.v[2 * k + 1] = v.y;
+        }
+        return s;
+    }
+    __device__ void store(int64_t i, const PState<double>& s) const {
+        xy[i] = make_double2(s.x, s.y);
+        pxy[i] = make_double2(s.px, s.py);
+        eP[i] = make_double2(s.eta, s.Pe);
+#pragma unroll
+        for (int k = 0; k < 4; k++) q[(size_t)k * np + i] = make_double2(s.q.v[2 * k], s.q.v[2 * k + 1]);
+    }
+    __device__ void store_momenta(int64_t i, const PState<double>& s) const {
+        pxy[i] = make_double2(s.px, s.py);
+        eP[i] = make_double2(s.eta, s.Pe);
+    }
+};
+
+template <>
+struct Parts<float> {
+    float4* xyp;
+    float2* eP;
+    float4* q;
+    int32_t* sp;
+    double* pt0;
+    int32_t* id;
+    int64_t np;
+    __device__ PState<float> load(int64_t i) const {
+        PState<float> s;
+        float4 a = xyp[i];
+        float2 c = eP[i];
+        float4 q0 = q[i], q1 = q[np + i];
+        s.x = a.x; s.y = a.y; s.px = a.z; s.py = a.w; s.eta = c.x; s.Pe = c.y;
+        s.q.v[0] = q0.x; s.q.v[1] = q0.y; s.q.v[2] = q0.z; s.q.v[3] = q0.w;
+        s.q.v[4] = q1.x; s.q.v[5] = q1.y; s.q.v[6] = q1.z; s.q.v[7] = q1.w;
+        return s;
+    }
+    __device__ void store(int64_t i, const PState<float>& s) const {
+        xyp[i] = make_float4(s.x, s.y, s.px, s.py);
+        eP[i] = make_float2(s.eta, s.Pe);
+        q[i] = make_float4(s.q.v[0], s.q.v[1], s.q.v[2], s.q.v[3]);
+        q[np + i] = make_float4(s.q.v[4], s.q.v[5], s.q.v[6], s.q.v[7]);
+    }
+    __device__ void store_momenta(int64_t i, const PState<float>& s) const {
+        xyp[i] = make_float4(s.x, s.y, s.px, s.py);
+        eP[i] = make_float2(s.eta, s.Pe);
+    }
+};
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <typename R>
+static Parts<R> carve_parts(void* base, int64_t np);
+
+template <>
+Parts<double> carve_parts<double>(void* base, int64_t np) {
+    Parts<double> p;
+    char* c = (char*)base;
+    p.np = np;
+    p.xy = (double2*)c; c += align256(16 * np);
+    p.pxy = (double2*)c; c += align256(16 * np);
+    p.eP = (double2*)c; c += align256(16 * np);
+    p.q = (double2*)c; c += align256(64 * np);
+    p.sp = (int32_t*)c; c += align256(4 * np);
+    p.pt0 = (double*)c; c += align256(8 * np);
+    p.id = (int32_t*)c;
+    return p;
+}
+
+template <>
+Parts<float> carve_parts<float>(void* base, int64_t np) {
+    Parts<float> p;
+    char* c = (char*)base;
+    p.np = np;
+    p.xyp = (float4*)c; c += align256(16 * np);
+    p.eP = (float2*)c; c += align256(8 * np);
+    p.q = (float4*)c; c += align256(32 * np);
+    p.sp = (int32_t*)c; c += align256(4 * np);
+    p.pt0 = (double*)c; c += align256(8 * np);
+    p.id = (int32_t*)c;
+    return p;
+}
+
+size_t particle_bytes(int prec, int64_t np) {
+    if (prec == 0) return align256(16 * np) * 3 + align256(64 * np) + align256(4 * np) * 2 + align256(8 * np);
+    return align256(16 * np) + align256(8 * np) + align256(32 * np) + align256(4 * np) * 2 + align256(8 * np);
+}
+
+size_t site_bytes(int prec, int64_t Vn) { return (size_t)6 * 8 * Vn * (prec == 0 ? 8 : 4); }
+
+size_t field_bytes(int prec, int64_t Vn) {
+    return prec == 0 ? fields_vectors<double>(Vn) * 16 : fields_vectors<float>(Vn) * 16;
+}
+
+// ------------------------------------------------------------ site fields
+// Sec. 3.1 interpolation at t_n:
+//   E_i   = (1/4t) { e_i(x) + U_i(x-i)^+ e_i(x-i) U_i(x-i) }, e summed over n +- 1/2
+//   E_eta = (pi(n+1/2) + pi(n-1/2)) / 2
+//   B_x   = -(1/t) D_y phi,  B_y = +(1/t) D_x phi   (central covariant differences;
+//           the components follow B_i = eps_ij F_eta_j / tau and Wong's equations)
+//   B_eta = (i/4) [U_xy + U_y,-x + U_-x,-y + U_-y,x]_ah   (clover of the four plaquettes)
+template <typename R>
+__global__ void __launch_bounds__(128) site_fields_kernel(Fields<R> bn, Fields<R> bn1,
+                                                          typename Prec<R>::V* site, int N, R inv_t) {
+    constexpr int AP = Prec<R>::AP;
+    const int64_t Vn = (int64_t)N * N;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < Vn; s += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(s % N), y = (int)(s / N);
+        const int xp = x + 1 == N ? 0 : x + 1, xm = x == 0 ? N - 1 : x - 1;
+        const int yp = y + 1 == N ? 0 : y + 1, ym = y == 0 ? N - 1 : y - 1;
+        const int64_t s_xp = (int64_t)y * N + xp, s_xm = (int64_t)y * N + xm;
+        const int64_t s_yp = (int64_t)yp * N + x, s_ym = (int64_t)ym * N + x;
+        const M3<R> Ux = load_link(bn.U, 0, s, Vn), Uy = load_link(bn.U, 1, s, Vn);
+        const M3<R> Ux_xm = load_link(bn.U, 0, s_xm, Vn), Uy_ym = load_link(bn.U, 1, s_ym, Vn);
+        // electric
+        for (int d = 0; d < 2; d++) {
+            const int64_t sb = d == 0 ? s_xm : s_ym;
+            const typename Prec<R>::V* eo = bn.e + (size_t)d * AP * Vn;
+            const typename Prec<R>::V* en = bn1.e + (size_t)d * AP * Vn;
+            A8<R> h = load_alg(eo, s, Vn), hn = load_alg(en, s, Vn);
+            A8<R> b = load_alg(eo, sb, Vn), bnn = load_alg(en, sb, Vn);
+#pragma unroll
+            for (int a = 0; a < 8; a++) { h.v[a] += hn.v[a]; b.v[a] += bnn.v[a]; }
+            const A8<R> bt = adj_dag(d == 0 ? Ux_xm : Uy_ym, b);
+            A8<R> E;
+#pragma unroll
+            for (int a = 0; a < 8; a++) E.v[a] = R(0.25) * inv_t * (h.v[a] + bt.v[a]);
+            store_alg(site + (size_t)d * AP * Vn, s, Vn, E);
+        }
+        {
+            A8<R> p = load_alg(bn.pi, s, Vn), pn = load_alg(bn1.pi, s, Vn);
+#pragma unroll
+            for (int a = 0; a < 8; a++) p.v[a] = R(0.5) * (p.v[a] + pn.v[a]);
+            store_alg(site + (size_t)2 * AP * Vn, s, Vn, p);
+        }
+        // magnetic, longitudinal components from the scalar
+        {
+            const A8<R> fx = adj(Ux, load_alg(bn.phi, s_xp, Vn));
+            const A8<R> bx = adj_dag(Ux_xm, load_alg(bn.phi, s_xm, Vn));
+            const A8<R> fy = adj(Uy, load_alg(bn.phi, s_yp, Vn));
+            const A8<R> by = adj_dag(Uy_ym, load_alg(bn.phi, s_ym, Vn));
+            A8<R> Bx, By;
+#pragma unroll
+            for (int a = 0; a < 8; a++) {
+                Bx.v[a] = -R(0.5) * inv_t * (fy.v[a] - by.v[a]);
+                By.v[a] = R(0.5) * inv_t * (fx.v[a] - bx.v[a]);
+            }
+            store_alg(site + (size_t)3 * AP * Vn, s, Vn, Bx);
+            store_alg(site + (size_t)4 * AP * Vn, s, Vn, By);
+        }
+        // B_eta from the clover
+        {
+            const int64_t s_xm_yp = (int64_t)yp * N + xm, s_xm_ym = (int64_t)ym * N + xm;
+            const int64_t s_xp_ym = (int64_t)ym * N + xp;
+            // U_xy(x) = Ux(x) Uy(x+x) Ux(x+y)^+ Uy(x)^+
+            M3<R> c = mul_nd(mul_nd(mul(Ux, load_link(bn.U, 1, s_xp, Vn)), load_link(bn.U, 0, s_yp, Vn)), Uy);
+            // U_y,-x(x) = Uy(x) Ux(x-x+y)^+ Uy(x-x)^+ Ux(x-x)
+            const M3<R> Uy_xm = load_link(bn.U, 1, s_xm, Vn);
+            c = add(c, mul(mul_nd(mul_nd(Uy, load_link(bn.U, 0, s_xm_yp, Vn)), Uy_xm), Ux_xm));
+            // U_-x,-y(x) = Ux(x-x)^+ Uy(x-x-y)^+ Ux(x-x-y) Uy(x-y)
+            c = add(c, mul(mul(mul_dn(Ux_xm, dag(load_link(bn.U, 1, s_xm_ym, Vn))), load_link(bn.U, 0, s_xm_ym, Vn)),
+                           Uy_ym));
+            // U_-y,x(x) = Uy(x-y)^+ Ux(x-y) Uy(x+x-y) Ux(x)^+
+            c = add(c, mul_nd(mul(mul_dn(Uy_ym, load_link(bn.U, 0, s_ym, Vn)), load_link(bn.U, 1, s_xp_ym, Vn)), Ux));
+            A8<R> Be = iah_to_alg(c);
+#pragma unroll
+            for (int a = 0; a < 8; a++) Be.v[a] *= R(0.25);
+            store_alg(site + (size_t)5 * AP * Vn, s, Vn, Be);
+        }
+    }
+}
+
+template <typename R>
+static void site_fields_t(const void* bn, const void* bn1, void* site, int N, double t, cudaStream_t st) {
+    const int64_t Vn = (int64_t)N * N;
+    const int threads = 128;
+    int64_t blocks = (Vn + threads - 1) / threads;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    site_fields_kernel<R><<<(unsigned)blocks, threads, 0, st>>>(
+        carve_fields<R>((void*)bn, Vn), carve_fields<R>((void*)bn1, Vn), (typename Prec<R>::V*)site, N,
+        (R)(t > 0 ? 1.0 / t : 0.0));
+}
+
+void launch_site_fields(int prec, const void* bn, const void* bn1, void* site, int N, double t, cudaStream_t st) {
+    if (prec == 0) site_fields_t<double>(bn, bn1, site, N, t, st);
+    else site_fields_t<float>(bn, bn1, site, N, t, st);
+}
+
+// ------------------------------------------------------------ push
+template <typename R>
+struct SpeciesArgs {
+    R mass[GL_MAX_SPECIES];
+    int is_static[GL_MAX_SPECIES];
+};
+
+template <typename R>
+__device__ __forceinline__ R floor_r(R v);
+template <>
+__device__ __forceinline__ double floor_r<double>(double v) { return floor(v); }
+template <>
+__device__ __forceinline__ float floor_r<float>(float v) { return floorf(v); }
+
+template <typename R>
+__device__ __forceinline__ R fmod_r(R a, R b);
+template <>
+__device__ __forceinline__ double fmod_r<double>(double a, double b) { return fmod(a, b); }
+template <>
+__device__ __forceinline__ float fmod_r<float>(float a, float b) { return fmodf(a, b); }
+
+template <typename R>
+__global__ void __launch_bounds__(128) push_kernel(const typename Prec<R>::V* __restrict__ site, Fields<R> bn1,
+                                                   Parts<R> P, int N, R t, R dt, R dt_over_t, uint32_t active,
+                                                   SpeciesArgs<R> sa) {
+    constexpr int AP = Prec<R>::AP;
+    const int64_t Vn = (int64_t)N * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.np; i += (int64_t)gridDim.x * blockDim.x) {
+        const int s = P.sp[i];
+        if (!((active >> s) & 1u)) continue;
+        PState<R> p = P.load(i);
+        const int ixu = (int)floor_r<R>(p.x + R(0.5)), iyu = (int)floor_r<R>(p.y + R(0.5));
+        // wrap keeps every index inside the lattice even for a non-finite position
+        // (float-to-int conversion maps NaN to 0 and saturates out-of-range values)
+        const int ix = wrapi(ixu, N), iy = wrapi(iyu, N);
+        const int64_t cell = (int64_t)iy * N + ix;
+        const R qEx = a_dot(p.q, load_alg(site, cell, Vn));
+        const R qEy = a_dot(p.q, load_alg(site + (size_t)1 * AP * Vn, cell, Vn));
+        const R qEe = a_dot(p.q, load_alg(site + (size_t)2 * AP * Vn, cell, Vn));
+        if (sa.is_static[s]) {
+            // infinitely massive: no motion and no colour rotation (temporal gauge)
+            p.px += dt * qEx;
+            p.py += dt * qEy;
+            p.Pe += dt * qEe;
+            P.store_momenta(i, p);
+            continue;
+        }
+        const R qBx = a_dot(p.q, load_alg(site + (size_t)3 * AP * Vn, cell, Vn));
+        const R qBy = a_dot(p.q, load_alg(site + (size_t)4 * AP * Vn, cell, Vn));
+        const R qBe = a_dot(p.q, load_alg(site + (size_t)5 * AP * Vn, cell, Vn));
+        const R m = sa.mass[s];
+        const R w = t > R(0) ? p.Pe / t : R(0);  // tau p^eta
+        const R ptau = sqrt(p.px * p.px + p.py * p.py + w * w + m * m);
+        const R inv_pt = ptau > R(0) ? R(1) / ptau : R(0);
+        const R vx = p.px * inv_pt, vy = p.py * inv_pt, vw = w * inv_pt;
+        // Wong's equations in Milne coordinates (Sec. 3.1), forward Euler
+        const R dpx = qEx + qBe * vy - qBy * vw;
+        const R dpy = qEy - qBe * vx + qBx * vw;
+        const R dPe = t * (qEe - qBx * vy + qBy * vx);
+        const R deta = dt_over_t * vw;
+        R xn = p.x + dt * vx, yn = p.y + dt * vy;
+        p.eta += deta;
+        p.px += dt * dpx;
+        p.py += dt * dpy;
+        p.Pe += dt * dPe;
+        const int jxu = (int)floor_r<R>(xn + R(0.5)), jyu = (int)floor_r<R>(yn + R(0.5));
+        xn = fmod_r<R>(xn, (R)N);
+        if (xn < R(0)) xn += (R)N;
+        yn = fmod_r<R>(yn, (R)N);
+        if (yn < R(0)) yn += (R)N;
+        p.x = xn;
+        p.y = yn;
+        // CPIC: rotate with the crossed links at t_{n+1}, x first, then y
+        const int dxc = jxu - ixu, dyc = jyu - iyu;
+        const int jx = wrapi(jxu, N), jy = wrapi(jyu, N);
+        if (dxc == 1) p.q = adj_dag(load_link(bn1.U, 0, cell, Vn), p.q);
+        else if (dxc == -1) p.q = adj(load_link(bn1.U, 0, (int64_t)iy * N + jx, Vn), p.q);
+        if (dyc == 1) p.q = adj_dag(load_link(bn1.U, 1, (int64_t)iy * N + jx, Vn), p.q);
+        else if (dyc == -1) p.q = adj(load_link(bn1.U, 1, (int64_t)jy * N + jx, Vn), p.q);
+        // rapidity Wilson line at the new cell: Q <- e^{-i deta phi} Q e^{+i deta phi}
+        if (deta != R(0)) {
+            const A8<R> ph = load_alg(bn1.phi, (int64_t)jy * N + jx, Vn);
+            p.q = adj(exp_i_alg<R, (sizeof(R) == 8 ? 20 : 10)>(ph, -deta), p.q);
+        }
+        P.store(i, p);
+    }
+}
+
+template <typename R>
+static void push_t(const void* site, const void* bn1, void* parts, int64_t np, int N, double t, double dt,
+                   uint32_t active, const SpeciesParams& sp, cudaStream_t st) {
+    const int64_t Vn = (int64_t)N * N;
+    SpeciesArgs<R> sa;
+    for (int k = 0; k < GL_MAX_SPECIES; k++) {
+        sa.mass[k] = (R)(k < sp.n_species && !sp.is_static[k] ? sp.mass[k] : 0.0);
+        sa.is_static[k] = k < sp.n_species ? sp.is_static[k] : 0;
+    }
+    const int threads = 128;
+    int64_t blocks = (np + threads - 1) / threads;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks < 1) return;
+    push_kernel<R><<<(unsigned)blocks, threads, 0, st>>>((const typename Prec<R>::V*)site,
+                                                         carve_fields<R>((void*)bn1, Vn), carve_parts<R>(parts, np), N,
+                                                         (R)t, (R)dt, (R)(t > 0 ? dt / t : 0.0), active, sa);
+}
+
+void launch_push(int prec, const void* site, const void* bn1, void* parts, int64_t np, int N, double t, double dt,
+                 uint32_t active_mask, const SpeciesParams& sp, cudaStream_t st) {
+    if (prec == 0) push_t<double>(site, bn1, parts, np, N, t, dt, active_mask, sp, st);
+    else push_t<float>(site, bn1, parts, np, N, t, dt, active_mask, sp, st);
+}
+
+// ------------------------------------------------------------ sampling
+struct SampleArgs {
+    int64_t off[GL_MAX_SPECIES + 1];
+    int rep[GL_MAX_SPECIES], mode[GL_MAX_SPECIES];
+    double p0[GL_MAX_SPECIES], p1[GL_MAX_SPECIES];
+    double q0[2][8];
+    int n_species;
+};
+
+// Haar-random U(3) from the QR decomposition of a complex Ginibre matrix
+// (Gram-Schmidt on the columns, R's diagonal positive), then Q = U Q0 U^+.
+__device__ A8<double> haar_charge(const double* g, const double* q0) {
+    double zr[3][3], zi[3][3];
+    const double is2 = 0.70710678118654752440;
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) { zr[r][c] = g[2 * (3 * r + c)] * is2; zi[r][c] = g[2 * (3 * r + c) + 1] * is2; }
+    M3<double> u;
+    for (int c = 0; c < 3; c++) {
+        double vr[3], vi[3];
+        for (int r = 0; r < 3; r++) { vr[r] = zr[r][c]; vi[r] = zi[r][c]; }
+        for (int pass = 0; pass < 2; pass++)
+            for (int k = 0; k < c; k++) {
+                double dr = 0, di = 0;  // sum conj(u_rk) v_r
+                for (int r = 0; r < 3; r++) {
+                    dr += u.re[r][k] * vr[r] + u.im[r][k] * vi[r];
+                    di += u.re[r][k] * vi[r] - u.im[r][k] * vr[r];
+                }
+                for (int r = 0; r < 3; r++) {
+                    vr[r] -= dr * u.re[r][k] - di * u.im[r][k];
+                    vi[r] -= dr * u.im[r][k] + di * u.re[r][k];
+                }
+            }
+        double n = 0;
+        for (int r = 0; r < 3; r++) n += vr[r] * vr[r] + vi[r] * vi[r];
+        n = 1.0 / sqrt(n);
+        for (int r = 0; r < 3; r++) { u.re[r][c] = vr[r] * n; u.im[r][c] = vi[r] * n; }
+    }
+    A8<double> Q0;
+    for (int a = 0; a < 8; a++) Q0.v[a] = q0[a];
+    return adj(u, Q0);
+}
+
+template <typename R>
+__global__ void sample_kernel(Parts<R> P, int N, uint32_t k0, uint32_t k1, SampleArgs sa) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.np; i += (int64_t)gridDim.x * blockDim.x) {
+        int s = 0;
+        while (s + 1 < sa.n_species && i >= sa.off[s + 1]) s++;
+        const uint32_t idx = (uint32_t)(i - sa.off[s]);
+        U4 w = philox4x32_10(U4{idx, (uint32_t)s, 2u, 0u}, k0, k1);
+        const double x = N * u01(w.x), y = N * u01(w.y);
+        const double psi = 2.0 * 3.14159265358979323846 * u01(w.z);
+        const double pt = sa.mode[s] == 1 ? sa.p0[s] + (sa.p1[s] - sa.p0[s]) * u01(w.w) : sa.p0[s];
+        double px = pt * cos(psi), py = pt * sin(psi);
+        if (sa.mode[s] == 2) { px = sa.p0[s]; py = 0.0; }
+        double g[20];
+        for (int j = 0; j < 5; j++) {
+            U4 v = philox4x32_10(U4{idx, (uint32_t)s, 3u, (uint32_t)j}, k0, k1);
+            box_muller(u01(v.x), u01(v.y), g[4 * j], g[4 * j + 1]);
+            box_muller(u01(v.z), u01(v.w), g[4 * j + 2], g[4 * j + 3]);
+        }
+        const A8<double> q = haar_charge(g, sa.q0[sa.rep[s]]);
+        PState<R> p;
+        p.x = (R)x; p.y = (R)y; p.eta = R(0); p.px = (R)px; p.py = (R)py; p.Pe = R(0);
+        for (int a = 0; a < 8; a++) p.q.v[a] = (R)q.v[a];
+        P.store(i, p);
+        P.sp[i] = s;
+        P.pt0[i] = (double)p.px * (double)p.px + (double)p.py * (double)p.py;
+        P.id[i] = (int32_t)i;
+    }
+}
+
+template <typename R>
+static void sample_t(void* parts, int64_t np, int N, uint64_t seed, const SampleArgs& sa, cudaStream_t st) {
+    const int threads = 128;
+    int64_t blocks = (np + threads - 1) / threads;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) return;
+    sample_kernel<R><<<(unsigned)blocks, threads, 0, st>>>(carve_parts<R>(parts, np), N, (uint32_t)seed,
+                                                           (uint32_t)(seed >> 32), sa);
+}
+
+void launch_sample(int prec, void* parts, int64_t np, int N, uint64_t seed, const int64_t* offsets, int n_species,
+                   const int* rep, const int* mom_mode, const double* p0, const double* p1,
+                   const double q0[2][8], cudaStream_t st) {
+    SampleArgs sa;
+    sa.n_species = n_species;
+    for (int k = 0; k <= GL_MAX_SPECIES; k++) sa.off[k] = k <= n_species ? offsets[k] : np;
+    for (int k = 0; k < GL_MAX_SPECIES; k++) {
+        sa.rep[k] = k < n_species ? rep[k] : 0;
+        sa.mode[k] = k < n_species ? mom_mode[k] : 0;
+        sa.p0[k] = k < n_species ? p0[k] : 0;
+        sa.p1[k] = k < n_species ? p1[k] : 0;
+    }
+    for (int r = 0; r < 2; r++)
+        for (int a = 0; a < 8; a++) sa.q0[r][a] = q0[r][a];
+    if (prec == 0) sample_t<double>(parts, np, N, seed, sa, st);
+    else sample_t<float>(parts, np, N, seed, sa, st);
+}
+
+// ------------------------------------------------------------ canonical conversion of particles
+template <typename R>
+__global__ void parts_convert_kernel(Parts<R> P, double* stg, int to_device) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.np; i += (int64_t)gridDim.x * blockDim.x) {
+        double* r = stg + i * 16;
+        if (to_device) {
+            PState<R> p;
+            p.x = (R)r[0]; p.y = (R)r[1]; p.eta = (R)r[2]; p.px = (R)r[3]; p.py = (R)r[4]; p.Pe = (R)r[5];
+            for (int a = 0; a < 8; a++) p.q.v[a] = (R)r[6 + a];
+            P.store(i, p);
+            P.pt0[i] = r[14];
+            P.sp[i] = (int32_t)r[15];
+            P.id[i] = (int32_t)i;
+        } else {
+            PState<R> p = P.load(i);
+            r[0] = p.x; r[1] = p.y; r[2] = p.eta; r[3] = p.px; r[4] = p.py; r[5] = p.Pe;
+            for (int a = 0; a < 8; a++) r[6 + a] = p.q.v[a];
+            r[14] = P.pt0[i];
+            r[15] = (double)P.sp[i];
+        }
+    }
+}
+
+void launch_parts_convert(int prec, void* parts, int64_t np, double* stg, int to_device, cudaStream_t st) {
+    const int threads = 128;
+    int64_t blocks = (np + threads - 1) / threads;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) return;
+    if (prec == 0) parts_convert_kernel<double><<<(unsigned)blocks, threads, 0, st>>>(carve_parts<double>(parts, np), stg, to_device);
+    else parts_convert_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(carve_parts<float>(parts, np), stg, to_device);
+}
+
+// ------------------------------------------------------------ particle observables
+// per block: [species][PO_N] partial sums (count, px^2, py^2, pL^2, pT^2 - pT0^2 as
+// sums; Casimir deviations as maxima) in FP64.  Lanes reduce by warp shuffles,
+// warps keep their own slots, and blocks and warps are combined in a fixed
+// order, so the result does not depend on scheduling.
+struct ObsArgs {
+    SpeciesParams sp;
+    double q2ref[GL_MAX_SPECIES], q3ref[GL_MAX_SPECIES];
+};
+
+__device__ __forceinline__ bool po_is_max(int k) { return k == PO_Q2 || k == PO_Q3; }
+
+template <typename R>
+__global__ void __launch_bounds__(256) particle_obs_kernel(Parts<R> P, double t, uint32_t active, ObsArgs oa,
+                                                           double* partials) {
+    __shared__ double wacc[8][GL_MAX_SPECIES * PO_N];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = lane; k < GL_MAX_SPECIES * PO_N; k += 32) wacc[warp][k] = 0.0;
+    __syncwarp();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < P.np; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        int s = -1;
+        double v[PO_N] = {0, 0, 0, 0, 0, 0, 0};
+        if (i < P.np) {
+            s = P.sp[i];
+            if (!((active >> s) & 1u)) s = -1;
+        }
+        if (s >= 0) {
+            const PState<R> p = P.load(i);
+            const double px = p.px, py = p.py, Pe = p.Pe, eta = p.eta;
+            double pl;
+            if (oa.sp.is_static[s]) {
+                pl = Pe;
+            } else {
+                const double m = oa.sp.mass[s];
+                const double w = t > 0 ? Pe / t : 0.0;
+                const double ptau = sqrt(px * px + py * py + w * w + m * m);
+                pl = ptau * sinh(eta) + w * cosh(eta);
+            }
+            A8<double> q;
+            for (int a = 0; a < 8; a++) q.v[a] = p.q.v[a];
+            const double q2 = a_dot(q, q);
+            const M3<double> Q = alg_to_mat(q);
+            const M3<double> Q2 = mul(Q, Q);
+            double tr3 = 0;  // Re tr(Q^3); q3 = 4 tr(Q^3) (App. A)
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) tr3 += Q2.re[a][b] * Q.re[b][a] - Q2.im[a][b] * Q.im[b][a];
+            v[PO_COUNT] = 1.0;
+            v[PO_PX2] = px * px;
+            v[PO_PY2] = py * py;
+            v[PO_PL2] = pl * pl;
+            v[PO_DPT2] = px * px + py * py - P.pt0[i];
+            v[PO_Q2] = fabs(q2 - oa.q2ref[s]);
+            v[PO_Q3] = fabs(4.0 * tr3 - oa.q3ref[s]);
+        }
+        for (int sp_ = 0; sp_ < oa.sp.n_species; sp_++) {
+            const bool mine = s == sp_;
+            if (!__any_sync(0xffffffffu, mine)) continue;
+            double r[PO_N];
+#pragma unroll
+            for (int k = 0; k < PO_N; k++) r[k] = mine ? v[k] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int k = 0; k < PO_N; k++) {
+                    const double oth = __shfl_down_sync(0xffffffffu, r[k], o);
+                    r[k] = po_is_max(k) ? fmax(r[k], oth) : r[k] + oth;
+                }
+            if (lane == 0)
+                for (int k = 0; k < PO_N; k++) {
+                    double* a = &wacc[warp][sp_ * PO_N + k];
+                    *a = po_is_max(k) ? fmax(*a, r[k]) : *a + r[k];
+                }
+        }
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    for (int k = threadIdx.x; k < GL_MAX_SPECIES * PO_N; k += blockDim.x) {
+        double a = 0.0;
+        for (int w = 0; w < nw; w++) a = po_is_max(k % PO_N) ? fmax(a, wacc[w][k]) : a + wacc[w][k];
+        partials[(size_t)blockIdx.x * GL_MAX_SPECIES * PO_N + k] = a;
+    }
+}
+
+__global__ void particle_obs_finalize(const double* partials, int nblocks, double* out) {
+    const int width = GL_MAX_SPECIES * PO_N;
+    for (int k = threadIdx.x; k < width; k += blockDim.x) {
+        double a = 0.0;
+        for (int b = 0; b < nblocks; b++) {
+            const double v = partials[(size_t)b * width + k];
+            a = po_is_max(k % PO_N) ? fmax(a, v) : a + v;
+        }
+        out[k] = a;
+    }
+}
+
+void launch_particle_obs(int prec, const void* parts, int64_t np, double t, uint32_t active_mask,
+                         const SpeciesParams& sp, const double q2ref[GL_MAX_SPECIES],
+                         const double q3ref[GL_MAX_SPECIES], double* partials, int max_blocks, double* out,
+                         cudaStream_t st) {
+    ObsArgs oa;
+    oa.sp = sp;
+    for (int k = 0; k < GL_MAX_SPECIES; k++) { oa.q2ref[k] = q2ref[k]; oa.q3ref[k] = q3ref[k]; }
+    const int threads = 256;
+    int64_t blocks = (np + threads - 1) / threads;
+    if (blocks > max_blocks) blocks = max_blocks;
+    if (blocks < 1) blocks = 1;
+    if (prec == 0)
+        particle_obs_kernel<double><<<(unsigned)blocks, threads, 0, st>>>(carve_parts<double>((void*)parts, np), t,
+                                                                          active_mask, oa, partials);
+    else
+        particle_obs_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(carve_parts<float>((void*)parts, np), t,
+                                                                         active_mask, oa, partials);
+    particle_obs_finalize<<<1, 64, 0, st>>>(partials, (int)blocks, out);
+}
+
+}  // namespace gl

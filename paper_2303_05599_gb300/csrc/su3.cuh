@@ -1,0 +1,313 @@
+// SU(3) algebra on the device, templated on the real type (double for the
+// plain FP64 path, float for the FP32 path).
+//
+// Matrices are held as separate real and imaginary 3x3 arrays so that every
+// element lives in a register after unrolling.  The Lie algebra is spanned by
+// T^a = lambda^a / 2 (Gell-Mann); an element is stored as its 8 real
+// components X^a = 2 tr(X T^a) (App. B of arXiv:2303.05599).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace gl {
+
+template <typename R>
+struct M3 {
+    R re[3][3];
+    R im[3][3];
+};
+
+template <typename R>
+struct A8 {
+    R v[8];
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ R inv_sqrt3() { return R(0.57735026918962576451); }
+
+template <typename R>
+__device__ __forceinline__ M3<R> m_zero() {
+    M3<R> m;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) { m.re[i][j] = R(0); m.im[i][j] = R(0); }
+    return m;
+}
+
+template <typename R>
+__device__ __forceinline__ M3<R> m_id() {
+    M3<R> m = m_zero<R>();
+    m.re[0][0] = m.re[1][1] = m.re[2][2] = R(1);
+    return m;
+}
+
+// c = a b
+template <typename R>
+__device__ __forceinline__ M3<R> mul(const M3<R>& a, const M3<R>& b) {
+    M3<R> c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            R sr = R(0), si = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                sr = fma(a.re[i][k], b.re[k][j], sr);
+                sr = fma(-a.im[i][k], b.im[k][j], sr);
+                si = fma(a.re[i][k], b.im[k][j], si);
+                si = fma(a.im[i][k], b.re[k][j], si);
+            }
+            c.re[i][j] = sr;
+            c.im[i][j] = si;
+        }
+    return c;
+}
+
+// c = a b^+
+template <typename R>
+__device__ __forceinline__ M3<R> mul_nd(const M3<R>& a, const M3<R>& b) {
+    M3<R> c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            R sr = R(0), si = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                // a_ik conj(b_jk)
+                sr = fma(a.re[i][k], b.re[j][k], sr);
+                sr = fma(a.im[i][k], b.im[j][k], sr);
+                si = fma(a.im[i][k], b.re[j][k], si);
+                si = fma(-a.re[i][k], b.im[j][k], si);
+            }
+            c.re[i][j] = sr;
+            c.im[i][j] = si;
+        }
+    return c;
+}
+
+// c = a^+ b
+template <typename R>
+__device__ __forceinline__ M3<R> mul_dn(const M3<R>& a, const M3<R>& b) {
+    M3<R> c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            R sr = R(0), si = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                // conj(a_ki) b_kj
+                sr = fma(a.re[k][i], b.re[k][j], sr);
+                sr = fma(a.im[k][i], b.im[k][j], sr);
+                si = fma(a.re[k][i], b.im[k][j], si);
+                si = fma(-a.im[k][i], b.re[k][j], si);
+            }
+            c.re[i][j] = sr;
+            c.im[i][j] = si;
+        }
+    return c;
+}
+
+template <typename R>
+__device__ __forceinline__ M3<R> dag(const M3<R>& a) {
+    M3<R> c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) { c.re[i][j] = a.re[j][i]; c.im[i][j] = -a.im[j][i]; }
+    return c;
+}
+
+template <typename R>
+__device__ __forceinline__ M3<R> add(const M3<R>& a, const M3<R>& b) {
+    M3<R> c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) { c.re[i][j] = a.re[i][j] + b.re[i][j]; c.im[i][j] = a.im[i][j] + b.im[i][j]; }
+    return c;
+}
+
+template <typename R>
+__device__ __forceinline__ M3<R> sub(const M3<R>& a, const M3<R>& b) {
+    M3<R> c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) { c.re[i][j] = a.re[i][j] - b.re[i][j]; c.im[i][j] = a.im[i][j] - b.im[i][j]; }
+    return c;
+}
+
+// Hermitian matrix X = sum_a x^a T^a
+template <typename R>
+__device__ __forceinline__ M3<R> alg_to_mat(const A8<R>& x) {
+    const R h = R(0.5), s3 = inv_sqrt3<R>();
+    M3<R> m;
+    m.re[0][0] = h * (x.v[2] + x.v[7] * s3); m.im[0][0] = R(0);
+    m.re[1][1] = h * (-x.v[2] + x.v[7] * s3); m.im[1][1] = R(0);
+    m.re[2][2] = -x.v[7] * s3; m.im[2][2] = R(0);
+    m.re[0][1] = h * x.v[0]; m.im[0][1] = -h * x.v[1];
+    m.re[1][0] = h * x.v[0]; m.im[1][0] = h * x.v[1];
+    m.re[0][2] = h * x.v[3]; m.im[0][2] = -h * x.v[4];
+    m.re[2][0] = h * x.v[3]; m.im[2][0] = h * x.v[4];
+    m.re[1][2] = h * x.v[5]; m.im[1][2] = -h * x.v[6];
+    m.re[2][1] = h * x.v[5]; m.im[2][1] = h * x.v[6];
+    return m;
+}
+
+// components x^a = 2 Re tr(X T^a) of the traceless part of a Hermitian X
+template <typename R>
+__device__ __forceinline__ A8<R> herm_to_alg(const M3<R>& X) {
+    A8<R> x;
+    x.v[0] = X.re[0][1] + X.re[1][0];
+    x.v[1] = X.im[1][0] - X.im[0][1];
+    x.v[2] = X.re[0][0] - X.re[1][1];
+    x.v[3] = X.re[0][2] + X.re[2][0];
+    x.v[4] = X.im[2][0] - X.im[0][2];
+    x.v[5] = X.re[1][2] + X.re[2][1];
+    x.v[6] = X.im[2][1] - X.im[1][2];
+    x.v[7] = (X.re[0][0] + X.re[1][1] - R(2) * X.re[2][2]) * inv_sqrt3<R>();
+    return x;
+}
+
+// components of the Hermitian traceless matrix i [M]_ah, with
+// [M]_ah = (M - M^+)/2 - tr(M - M^+)/6  (anti-Hermitian traceless part)
+template <typename R>
+__device__ __forceinline__ A8<R> iah_to_alg(const M3<R>& M) {
+    A8<R> x;
+    x.v[0] = -(M.im[0][1] + M.im[1][0]);
+    x.v[1] = M.re[1][0] - M.re[0][1];
+    x.v[2] = M.im[1][1] - M.im[0][0];
+    x.v[3] = -(M.im[0][2] + M.im[2][0]);
+    x.v[4] = M.re[2][0] - M.re[0][2];
+    x.v[5] = -(M.im[1][2] + M.im[2][1]);
+    x.v[6] = M.re[2][1] - M.re[1][2];
+    x.v[7] = (R(2) * M.im[2][2] - M.im[0][0] - M.im[1][1]) * inv_sqrt3<R>();
+    return x;
+}
+
+template <typename R>
+__device__ __forceinline__ void cmul(R ar, R ai, R br, R bi, R& cr, R& ci) {
+    cr = ar * br - ai * bi;
+    ci = ar * bi + ai * br;
+}
+
+template <typename R>
+__device__ __forceinline__ A8<R> a_zero() {
+    A8<R> x;
+#pragma unroll
+    for (int a = 0; a < 8; a++) x.v[a] = R(0);
+    return x;
+}
+
+template <typename R>
+__device__ __forceinline__ R a_dot(const A8<R>& p, const A8<R>& q) {
+    R s = R(0);
+#pragma unroll
+    for (int a = 0; a < 8; a++) s = fma(p.v[a], q.v[a], s);
+    return s;
+}
+
+// U X U^+ for Hermitian X, as algebra components
+template <typename R>
+__device__ __forceinline__ A8<R> adj(const M3<R>& U, const A8<R>& x) {
+    return herm_to_alg(mul_nd(mul(U, alg_to_mat(x)), U));
+}
+
+// U^+ X U for Hermitian X, as algebra components
+template <typename R>
+__device__ __forceinline__ A8<R> adj_dag(const M3<R>& U, const A8<R>& x) {
+    return herm_to_alg(mul(mul_dn(U, alg_to_mat(x)), U));
+}
+
+// exp(i s X) for Hermitian traceless X = x^a T^a.  Cayley-Hamilton gives
+// X^3 = c1 X + c0 with c1 = tr(X^2)/2 and c0 = det X, so every power of iX
+// is a combination of 1, X, X^2; the exponential series is summed on those
+// three scalar coefficients (scaling and squaring when |sX| > 1).
+template <typename R, int TERMS>
+__device__ __forceinline__ M3<R> exp_i_alg(const A8<R>& x, R s) {
+    M3<R> X = alg_to_mat(x);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) { X.re[i][j] *= s; X.im[i][j] *= s; }
+    M3<R> X2 = mul(X, X);
+    R c1 = R(0.5) * (X2.re[0][0] + X2.re[1][1] + X2.re[2][2]);
+    int nsq = 0;
+    R scl = R(1);
+    // Frobenius norm^2 of X is 2 c1; keep the scaled norm below 1
+    R nrm2 = R(2) * c1;
+    while (nrm2 > R(1) && nsq < 30) { nrm2 *= R(0.25); scl *= R(0.5); nsq++; }
+    if (nsq) {
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                X.re[i][j] *= scl; X.im[i][j] *= scl;
+                X2.re[i][j] *= scl * scl; X2.im[i][j] *= scl * scl;
+            }
+        c1 *= scl * scl;
+    }
+    // det X (real for Hermitian X): cofactor expansion along the first row
+    R m1r, m1i, m2r, m2i, m3r, m3i, pr, pi_, qr, qi;
+    cmul(X.re[1][1], X.im[1][1], X.re[2][2], X.im[2][2], pr, pi_);
+    cmul(X.re[1][2], X.im[1][2], X.re[2][1], X.im[2][1], qr, qi);
+    m1r = pr - qr; m1i = pi_ - qi;
+    cmul(X.re[1][0], X.im[1][0], X.re[2][2], X.im[2][2], pr, pi_);
+    cmul(X.re[1][2], X.im[1][2], X.re[2][0], X.im[2][0], qr, qi);
+    m2r = pr - qr; m2i = pi_ - qi;
+    cmul(X.re[1][0], X.im[1][0], X.re[2][1], X.im[2][1], pr, pi_);
+    cmul(X.re[1][1], X.im[1][1], X.re[2][0], X.im[2][0], qr, qi);
+    m3r = pr - qr; m3i = pi_ - qi;
+    R c0 = (X.re[0][0] * m1r - X.im[0][0] * m1i)
+         - (X.re[0][1] * m2r - X.im[0][1] * m2i)
+         + (X.re[0][2] * m3r - X.im[0][2] * m3i);
+    // coefficients of 1, X, X^2 in (iX)^k / k!, summed
+    R ar = R(1), ai = R(0), br = R(0), bi = R(0), cr = R(0), ci = R(0);
+    R f0r = R(1), f0i = R(0), f1r = R(0), f1i = R(0), f2r = R(0), f2i = R(0);
+#pragma unroll
+    for (int k = 1; k <= TERMS; k++) {
+        const R inv = R(1) / R(k);
+        // a' = i c0 c / k ; b' = i (a + c1 c) / k ; c' = i b / k
+        R nar = -c0 * ci * inv, nai = c0 * cr * inv;
+        R tr_ = ar + c1 * cr, ti = ai + c1 * ci;
+        R nbr = -ti * inv, nbi = tr_ * inv;
+        R ncr = -bi * inv, nci = br * inv;
+        ar = nar; ai = nai; br = nbr; bi = nbi; cr = ncr; ci = nci;
+        f0r += ar; f0i += ai; f1r += br; f1i += bi; f2r += cr; f2i += ci;
+    }
+    M3<R> U;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const R d = (i == j) ? R(1) : R(0);
+            // (f0 + f1 X + f2 X2)_ij, complex coefficients
+            U.re[i][j] = f0r * d + f1r * X.re[i][j] - f1i * X.im[i][j] + f2r * X2.re[i][j] - f2i * X2.im[i][j];
+            U.im[i][j] = f0i * d + f1r * X.im[i][j] + f1i * X.re[i][j] + f2r * X2.im[i][j] + f2i * X2.re[i][j];
+        }
+    for (int k = 0; k < nsq; k++) U = mul(U, U);
+    return U;
+}
+
+// third row of an SU(3) matrix from the first two: u_2 = conj(u_0 x u_1)
+template <typename R>
+__device__ __forceinline__ void rebuild_row2(M3<R>& u) {
+#define GL_CX(ar, ai, br, bi, cr, ci, dr, di) ((ar) * (br) - (ai) * (bi) - ((cr) * (dr) - (ci) * (di)))
+#define GL_CY(ar, ai, br, bi, cr, ci, dr, di) ((ar) * (bi) + (ai) * (br) - ((cr) * (di) + (ci) * (dr)))
+    // u20 = conj(u01 u12 - u02 u11)
+    u.re[2][0] = GL_CX(u.re[0][1], u.im[0][1], u.re[1][2], u.im[1][2], u.re[0][2], u.im[0][2], u.re[1][1], u.im[1][1]);
+    u.im[2][0] = -GL_CY(u.re[0][1], u.im[0][1], u.re[1][2], u.im[1][2], u.re[0][2], u.im[0][2], u.re[1][1], u.im[1][1]);
+    // u21 = conj(u02 u10 - u00 u12)
+    u.re[2][1] = GL_CX(u.re[0][2], u.im[0][2], u.re[1][0], u.im[1][0], u.re[0][0], u.im[0][0], u.re[1][2], u.im[1][2]);
+    u.im[2][1] = -GL_CY(u.re[0][2], u.im[0][2], u.re[1][0], u.im[1][0], u.re[0][0], u.im[0][0], u.re[1][2], u.im[1][2]);
+    // u22 = conj(u00 u11 - u01 u10)
+    u.re[2][2] = GL_CX(u.re[0][0], u.im[0][0], u.re[1][1], u.im[1][1], u.re[0][1], u.im[0][1], u.re[1][0], u.im[1][0]);
+    u.im[2][2] = -GL_CY(u.re[0][0], u.im[0][0], u.re[1][1], u.im[1][1], u.re[0][1], u.im[0][1], u.re[1][0], u.im[1][0]);
+#undef GL_CX
+#undef GL_CY
+}
+
+}  // namespace gl

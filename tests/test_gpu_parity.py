@@ -1,0 +1,310 @@
+"""GPU parity of the CUDA path against the FP64 oracle, called through the
+C ABI.  FP64: 1e-10 relative on fields, site fields, single trajectories and
+observables (1e-3 on late-time ensemble averages of the full small run); FP32
+two-row path: error bounds checked and printed.  Full-size cases compare one
+step from a downloaded GPU state with the oracle's step from the same state."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2303_05599_gb300 import _binding as B
+from paper_2303_05599_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FP64_TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu_ready():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2303_05599_gb300 import build
+    build.build()
+    B.lib()
+
+
+def wl(N, prec=W.FP64, species=(), seed=3, Ns=6, L=None):
+    return W.Workload("test", N=N, L_fm=L if L else 0.09375 * N, precision=prec, seed=seed, Ns=Ns,
+                      species=list(species))
+
+
+def rel(a, b):
+    scale = max(1e-300, np.abs(b).max())
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / scale
+
+
+def oracle_init(w):
+    st, bad = O.mv_init(w.N, w.Ns, w.g2mu_a, w.m_a, w.Lambda_a, w.seed)
+    assert bad == 0
+    return st
+
+
+def upload_state(ev, st):
+    ev.upload(B.GL_BUF_LINKS, st.U)
+    ev.upload(B.GL_BUF_PHI, st.phi)
+    ev.upload(B.GL_BUF_E, st.e)
+    ev.upload(B.GL_BUF_PI, st.pi)
+
+
+def download_state(ev):
+    return O.FieldState(ev.N, ev.download(B.GL_BUF_LINKS), ev.download(B.GL_BUF_PHI), ev.download(B.GL_BUF_E),
+                        ev.download(B.GL_BUF_PI))
+
+
+def oracle_particles(w):
+    parts = []
+    for k, s in enumerate(w.species):
+        m, tf, p0, p1 = w.lattice_species()[k]
+        parts.append(O.sample_species(w.N, w.seed, k, s.rep, s.mom_mode, p0, p1, s.count))
+    return np.concatenate(parts) if parts else np.zeros((0, 16))
+
+
+def oracle_run(w, st, part):
+    ls = w.lattice_species()
+    return O.Run(st, part, [s[0] for s in ls], [s[1] for s in ls], [s.rep for s in w.species], w.dt)
+
+
+MIXED = [W.Species(W.M_CHARM, 0.06, 120, W.REP_F, W.MOM_FIXED_PT, 0.5),
+         W.Species(math.inf, 0.0, 60, W.REP_F, W.MOM_FIXED_PT, 0.0),
+         W.Species(0.0, 0.0, 60, W.REP_A, W.MOM_ALONG_X, 10.0),
+         W.Species(W.M_BEAUTY, 0.02, 60, W.REP_A, W.MOM_UNIFORM_PT, 0.0, 5.0)]
+
+
+# ------------------------------------------------------------------ init
+@pytest.mark.parametrize("N", [8, 37])
+def test_mv_init_parity(N):
+    w = wl(N)
+    ev = B.Event(w)
+    ev.glasma_init()
+    st = oracle_init(w)
+    g = download_state(ev)
+    assert rel(g.U, st.U) < FP64_TOL
+    assert rel(g.pi, st.pi) < FP64_TOL
+    assert np.abs(g.phi).max() == 0 and np.abs(g.e).max() == 0
+
+
+@pytest.mark.parametrize("N", [16, 37])
+def test_sampling_parity(N):
+    w = wl(N, species=MIXED)
+    ev = B.Event(w)
+    ev.wong_init()
+    got = ev.download(B.GL_BUF_PARTICLES)
+    want = oracle_particles(w)
+    assert np.array_equal(got[:, 15], want[:, 15])
+    assert np.abs(got[:, :2] - want[:, :2]).max() < 1e-12
+    assert rel(got[:, 3:5], want[:, 3:5]) < 1e-13
+    assert rel(got[:, 6:14], want[:, 6:14]) < 1e-12
+    assert rel(got[:, 14], want[:, 14]) < 1e-13
+
+
+# ------------------------------------------------------------------ fields
+@pytest.mark.parametrize("N", [4, 16, 37])
+def test_field_steps_fp64_parity(N):
+    w = wl(N)
+    st = oracle_init(w)
+    ev = B.Event(w)
+    upload_state(ev, st)
+    k = 12
+    ev.glasma_step(k)
+    for n in range(k):
+        st = O.field_step(st, n * w.dt, w.dt)
+    g = download_state(ev)
+    for a, b in [(g.U, st.U), (g.phi, st.phi), (g.e, st.e), (g.pi, st.pi)]:
+        assert rel(a, b) < FP64_TOL
+    o = ev.observables()
+    assert o.gauss_max < 1e-12 and o.unitarity_max < 1e-12
+
+
+def test_field_steps_fp32_error_bounds():
+    w = wl(32, prec=W.FP32_2ROW)
+    st = oracle_init(w)
+    ev = B.Event(w)
+    upload_state(ev, st)
+    k = 24
+    ev.glasma_step(k)
+    for n in range(k):
+        st = O.field_step(st, n * w.dt, w.dt)
+    g = download_state(ev)
+    errs = {name: rel(a, b) for name, a, b in [("U", g.U, st.U), ("phi", g.phi, st.phi), ("e", g.e, st.e),
+                                               ("pi", g.pi, st.pi)]}
+    print("FP32 two-row field error vs FP64 oracle after %d steps:" % k, errs)
+    assert max(errs.values()) < 2e-5
+    o = ev.observables()
+    print("FP32 gauss_max %.3e unitarity_max %.3e" % (o.gauss_max, o.unitarity_max))
+    assert o.unitarity_max < 1e-5
+
+
+# ------------------------------------------------------------------ coupled
+def _coupled(N, prec, steps, species=MIXED, seed=3):
+    w = wl(N, prec=prec, species=species, seed=seed)
+    st = oracle_init(w)
+    part = oracle_particles(w)
+    ev = B.Event(w)
+    upload_state(ev, st)
+    ev.upload(B.GL_BUF_PARTICLES, part)
+    run = oracle_run(w, st, part)
+    for _ in range(steps):
+        run.step()
+    ev.step(steps)
+    return w, ev, run
+
+
+@pytest.mark.parametrize("N", [16, 37])
+def test_coupled_fp64_parity(N):
+    w, ev, run = _coupled(N, W.FP64, 30)
+    got = ev.download(B.GL_BUF_PARTICLES)
+    assert rel(got[:, :2], run.part[:, :2]) < FP64_TOL
+    for sl in (slice(2, 3), slice(3, 5), slice(5, 6), slice(6, 14)):
+        assert rel(got[:, sl], run.part[:, sl]) < FP64_TOL
+    site = ev.download(B.GL_BUF_SITE)
+    assert rel(site, run.site) < FP64_TOL
+    g = download_state(ev)
+    assert rel(g.U, run.st.U) < FP64_TOL and rel(g.e, run.st.e) < FP64_TOL
+    # observables through the ABI against the oracle's sums (lattice units -> GeV^2)
+    o = ev.observables()
+    want = run.observables()
+    a2 = w.a_GeVinv ** 2
+    for k in range(len(w.species)):
+        assert o.n_active[k] == int(want[k, 0])
+        for got_v, want_v in [(o.sum_px2[k], want[k, 1]), (o.sum_py2[k], want[k, 2]),
+                              (o.sum_pL2[k], want[k, 3]), (o.sum_dpT2[k], want[k, 4])]:
+            assert abs(got_v * a2 - want_v) <= FP64_TOL * max(1.0, abs(want_v))
+        assert o.casimir2_dev[k] < 1e-12 and o.casimir3_dev[k] < 1e-12
+    assert o.gauss_max < 1e-12
+
+
+def test_coupled_fp32_error_bounds():
+    w, ev, run = _coupled(32, W.FP32_2ROW, 40)
+    got = ev.download(B.GL_BUF_PARTICLES)
+    errs = {"x": np.abs(got[:, :2] - run.part[:, :2]).max(), "p": rel(got[:, 3:5], run.part[:, 3:5]),
+            "P_eta": rel(got[:, 5], run.part[:, 5]), "Q": rel(got[:, 6:14], run.part[:, 6:14])}
+    print("FP32 particle error vs FP64 oracle after 40 steps:", errs)
+    assert errs["x"] < 1e-3 and errs["p"] < 1e-3 and errs["Q"] < 1e-3
+    o = ev.observables()
+    print("FP32 Casimir drift q2 %s q3 %s" % (list(o.casimir2_dev)[:4], list(o.casimir3_dev)[:4]))
+    assert max(o.casimir2_dev[:4]) < 1e-4
+
+
+def test_small_workload_full_run_fp64():
+    """32x32, L = 3 fm, 1000 charm quarks, 86 steps to tau = 1 fm/c, entirely
+    from the GPU's own initial state and sampler, against the oracle."""
+    w = W.config_small()
+    ev = B.Event(w)
+    ev.glasma_init()
+    ev.wong_init()
+    st = oracle_init(w)
+    part = oracle_particles(w)
+    run = oracle_run(w, st, part)
+    short = 20
+    ev.step(short)
+    for _ in range(short):
+        run.step()
+    got = ev.download(B.GL_BUF_PARTICLES)
+    assert rel(got[:, :6], run.part[:, :6]) < FP64_TOL      # single trajectories, short horizon
+    ev.step(w.n_steps - short)
+    for _ in range(w.n_steps - short):
+        run.step()
+    g = download_state(ev)
+    field_err = max(rel(g.U, run.st.U), rel(g.e, run.st.e), rel(g.phi, run.st.phi), rel(g.pi, run.st.pi))
+    print("full small run: field rel error %.3e" % field_err)
+    assert field_err < FP64_TOL
+    o = ev.observables()
+    want = run.observables()
+    a2 = w.a_GeVinv ** 2
+    pT2 = (o.sum_px2[0] + o.sum_py2[0]) * a2 / o.n_active[0]
+    pL2 = o.sum_pL2[0] * a2 / o.n_active[0]
+    wpT2 = (want[0, 1] + want[0, 2]) / want[0, 0]
+    wpL2 = want[0, 3] / want[0, 0]
+    print("<pT^2> %.6e vs %.6e, <pL^2> %.6e vs %.6e (lattice units)" % (pT2, wpT2, pL2, wpL2))
+    assert abs(pT2 - wpT2) < 1e-3 * wpT2 and abs(pL2 - wpL2) < 1e-3 * wpL2
+
+
+# ------------------------------------------------------------------ full size, sampled
+@pytest.mark.parametrize("prec,tol", [(W.FP64, FP64_TOL), (W.FP32_2ROW, 3e-6)])
+def test_full_size_one_step_parity(prec, tol):
+    """256x256 with 1e5 charm + 1e5 static quarks (the benchmark workload):
+    GPU init and sampler, a few coupled steps, then one more coupled step on
+    the GPU against the oracle's step from the downloaded state."""
+    w = W.config_n256(precision=prec)
+    ev = B.Event(w)
+    ev.glasma_init()
+    ev.wong_init()
+    ev.step(10)
+    st = download_state(ev)
+    part = ev.download(B.GL_BUF_PARTICLES)
+    run = oracle_run(w, st, part.copy())
+    run.n = 10
+    run.step()
+    ev.step(1)
+    g = download_state(ev)
+    errs = [rel(g.U, run.st.U), rel(g.e, run.st.e), rel(g.phi, run.st.phi), rel(g.pi, run.st.pi)]
+    site = ev.download(B.GL_BUF_SITE)
+    errs.append(rel(site, run.site))
+    got = ev.download(B.GL_BUF_PARTICLES)
+    perr = [rel(got[:, sl], run.part[:, sl]) for sl in (slice(0, 2), slice(3, 5), slice(5, 6), slice(6, 14))]
+    print("full size one-step errors (fields, site, particles):", errs, perr)
+    assert max(errs) < tol
+    # FP32 positions: compare where both sides pick the same cell
+    assert max(perr) < tol * (10 if prec == W.FP32_2ROW else 1)
+    o = ev.observables()
+    assert o.gauss_max < (1e-11 if prec == W.FP64 else 1e-3)
+
+
+# ------------------------------------------------------------------ edge cases
+def test_zero_particles_and_inactive_species():
+    late = W.Species(W.M_CHARM, 1e6, 10, W.REP_F, W.MOM_FIXED_PT, 1.0)
+    w = wl(8, species=[late])
+    ev = B.Event(w)
+    ev.glasma_init()
+    ev.wong_init()
+    before = ev.download(B.GL_BUF_PARTICLES)
+    ev.step(5)
+    assert np.array_equal(ev.download(B.GL_BUF_PARTICLES), before)
+    assert ev.observables().n_active[0] == 0
+    w0 = wl(8)
+    e0 = B.Event(w0)
+    e0.glasma_init()
+    e0.step(3)
+    assert e0.observables().gauss_max < 1e-12
+
+
+def test_cell_edge_ties_and_degenerate_momenta():
+    # positions exactly on x = k + 1/2 (NGP rounds up), a massless particle at
+    # rest (p^tau = 0: no motion), and static quarks
+    sp = [W.Species(0.0, 0.0, 4, W.REP_F, W.MOM_FIXED_PT, 0.0), W.Species(2.0, 0.0, 4, W.REP_F, W.MOM_FIXED_PT, 1.0)]
+    w = wl(8, species=sp)
+    st = oracle_init(w)
+    part = oracle_particles(w)
+    part[:, 0] = [0.5, 3.5, 7.5, 2.0, 0.5, 6.5, 7.49999999, 1.5]
+    part[:, 1] = [1.5, 0.5, 7.5, 4.5, 6.5, 3.0, 7.5, 2.5]
+    ev = B.Event(w)
+    upload_state(ev, st)
+    ev.upload(B.GL_BUF_PARTICLES, part)
+    run = oracle_run(w, st, part.copy())
+    for _ in range(16):
+        run.step()
+    ev.step(16)
+    got = ev.download(B.GL_BUF_PARTICLES)
+    assert rel(got[:, :14], run.part[:, :14]) < FP64_TOL
+    assert np.all(np.isfinite(got))
+
+
+def test_call_order_errors():
+    w = wl(8, species=[W.Species(W.M_CHARM, 0.0, 4)])
+    ev = B.Event(w)
+    ev.glasma_init()
+    ev.wong_init()
+    with pytest.raises(B.GlasmaError) as e:
+        ev.wong_push()
+    assert e.value.status == B.GL_ERR_STATE
+    ev.glasma_step(2)
+    with pytest.raises(B.GlasmaError) as e:
+        ev.wong_push()
+    assert e.value.status == B.GL_ERR_STATE
+    with pytest.raises(B.GlasmaError) as e:
+        ev.upload(B.GL_BUF_LINKS, np.zeros(10))
+    assert e.value.status == B.GL_ERR_SIZE
