@@ -181,6 +181,36 @@ gl_status gl_step_coupled(gl_ctx* ctx, int32_t n_steps);
 /* Ensemble sums and field checks at the current time (waits). */
 gl_status observables(gl_ctx* ctx, gl_obs* out);
 
+/* Largest particle count gl_ensemble_sums_noalloc accepts. */
+#define GL_NOALLOC_MAX_PARTICLES 2097152
+
+/* Per-species ensemble sums for callers that cannot allocate device memory
+ * (a host that owns every device allocation itself, or a process that must not
+ * grow its device footprint after start-up).  The paper has no counterpart:
+ * this is a service of the library, computing the particle sums of
+ * observables() from particle records the caller already holds on the device.
+ *
+ * d_particles: device array of np canonical FP64 records [np][16] (the
+ *   GL_BUF_PARTICLES layout, lattice units); np <= GL_NOALLOC_MAX_PARTICLES,
+ *   GL_ERR_SIZE otherwise.
+ * mass, rep: host arrays of n_species entries (1..GL_MAX_SPECIES): lattice
+ *   mass m a (INFINITY = static) and charge representation (0 F, 1 A).
+ * active_mask: bit s set if species s is included; t: lattice time t_n used
+ *   for p_L.
+ * d_out: device array of n_species x 7 doubles per species: count, sum p_x^2,
+ *   sum p_y^2, sum p_L^2, sum (p_T^2 - p_T^2 at formation), max |q2 - q2(R)|,
+ *   max |q3 - q3(R)|  (lattice units).
+ * stream: cudaStream_t.  Asynchronous on the stream.
+ *
+ * Allocates nothing: its scratch is a fixed 917,504-byte array compiled into
+ * the library, which every GPU that loads the library keeps until the process
+ * exits.  The first call on a device looks up that array's device address; make
+ * that first call before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU (different streams, or different host threads
+ * on one device) race and must be serialised by the caller. */
+gl_status gl_ensemble_sums_noalloc(const double* d_particles, int64_t np, int32_t n_species, const double* mass,
+                                   const int32_t* rep, uint32_t active_mask, double t, double* d_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

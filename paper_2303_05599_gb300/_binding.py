@@ -66,7 +66,11 @@ SIGNATURES = {
     "wong_push": (ctypes.c_int, [_P]),
     "gl_step_coupled": (ctypes.c_int, [_P, ctypes.c_int32]),
     "observables": (ctypes.c_int, [_P, ctypes.POINTER(gl_obs)]),
+    "gl_ensemble_sums_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_uint32,
+                                                ctypes.c_double, _P, _P]),
 }
+
+GL_NOALLOC_MAX_PARTICLES = 2097152
 
 _lib = None
 
