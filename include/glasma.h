@@ -21,7 +21,7 @@
  * momenta p a, masses m a.  The fields are stored as
  *   phi = g A_eta, pi = g a^2 P^eta, e_i = g a P^i   (Sec. 2.1),
  * Hermitian traceless, given by their 8 components X^a = 2 tr(X T^a) with
- * T^a = lambda^a/2.  The site fields are E^ = g a^2 E, B^ = g a^2 B (Sec. 3.1).
+ * T^a = lambda^a/2.  The site fields are E^ = g a^2 E, B^ = g a^2 B (Sec. 3.2).
  *
  * Canonical host layouts used by gl_upload / gl_download (always double):
  *   GL_BUF_LINKS      [2][N*N][18]  U_x, U_y at step n; site s = y*N + x;
@@ -84,7 +84,7 @@ typedef struct {
     uint64_t seed;          /* Philox key of this event's random numbers */
 } gl_config;
 
-/* One species of test particles (Sec. 3.1 and 7.1). */
+/* One species of test particles (Sec. 3.2 and 7.1). */
 typedef struct {
     double mass_GeV;        /* INFINITY: infinitely massive static quark (Sec. 5.1) */
     double tau_form_fm;     /* formation time; pushed from the first t_n >= tau_form */
@@ -142,7 +142,7 @@ const char* gl_error_string(const gl_ctx* ctx);
  * matching did not converge somewhere. */
 gl_status glasma_init(gl_ctx* ctx);
 
-/* Sample all particles (Sec. 3.1 and 4.2): uniform transverse positions,
+/* Sample all particles (Sec. 3.2 and 4.2): uniform transverse positions,
  * eta = 0, momenta per species mode, classical charges Q = U Q0 U^+ with U
  * Haar-distributed. */
 gl_status wong_init(gl_ctx* ctx);
@@ -164,7 +164,7 @@ gl_status gl_set_step(gl_ctx* ctx, int64_t step);
 gl_status glasma_step(gl_ctx* ctx, int32_t n_steps);
 
 /* Interpolate E and B to the lattice sites at the particles' time t_n
- * (Sec. 3.1 formulas; GL_BUF_SITE).  Needs exactly one glasma_step since the
+ * (Sec. 3.2 formulas; GL_BUF_SITE).  Needs exactly one glasma_step since the
  * particles' time (the momenta at n - 1/2 and n + 1/2 are both used).
  * wong_push calls it itself when it has not been called for this step. */
 gl_status wong_site_fields(gl_ctx* ctx);

@@ -64,7 +64,7 @@ void or_field_step(int N, double t, double dt,
  * + i[phi(x), pi(x)], as 8 components -> g[N*N][8]. */
 void or_gauss(int N, const double* U, const double* phi, const double* e, const double* pi,
               double* g);
-/* Site E and B at t_n (Sec. 3.1 interpolation formulas), out [6][N*N][8]. */
+/* Site E and B at t_n (Sec. 3.2 interpolation formulas), out [6][N*N][8]. */
 void or_site_fields(int N, double t, const double* U, const double* phi,
                     const double* e_old, const double* e_new,
                     const double* pi_old, const double* pi_new, double* out);

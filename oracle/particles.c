@@ -2,7 +2,7 @@
  * Test particles for the FP64 oracle (test infrastructure; see oracle.h):
  * classical SU(3) charges sampled over the Haar measure (Sec. 4.2, App. C),
  * Wong's equations in Milne coordinates integrated with Euler's method
- * (Sec. 3.1, App. A), and CPIC colour rotation with nearest-grid-point links
+ * (Sec. 3.1 and 3.2, App. A), and CPIC colour rotation with nearest-grid-point links
  * (Sec. 3.2, eq. for the short Wilson line U(tau_{n-1}, tau_n)).
  */
 #include <complex.h>

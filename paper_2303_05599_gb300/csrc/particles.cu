@@ -132,7 +132,7 @@ size_t field_bytes(int prec, int64_t Vn) {
 }
 
 // ------------------------------------------------------------ site fields
-// Sec. 3.1 interpolation at t_n:
+// Sec. 3.2 interpolation at t_n:
 //   E_i   = (1/4t) { e_i(x) + U_i(x-i)^+ e_i(x-i) U_i(x-i) }, e summed over n +- 1/2
 //   E_eta = (pi(n+1/2) + pi(n-1/2)) / 2
 //   B_x   = -(1/t) D_y phi,  B_y = +(1/t) D_x phi   (central covariant differences;
