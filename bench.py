@@ -1,7 +1,7 @@
 """Benchmark of the coupled CPIC time step (Glasma leapfrog + Wong push).
 
-A step is one pass of the whole hot path over one event: the field leapfrog
-kernel, the site E/B interpolation kernel and the particle push kernel
+A step is one pass of the whole hot path over one event: the fused kernel
+(leapfrog step and site E/B interpolation) and the particle push kernel
 (gl_step_coupled).  The default workload is the 256x256 event (L = 10 fm,
 g^2 mu = 2 GeV, m = 0.2 GeV, Ns = 50, dtau = a/8) with 1e5 charm quarks
 (p_T = 0.5 GeV) and 1e5 static quarks, FP32 two-row links.
@@ -53,22 +53,20 @@ def workload(args, rank=0):
 
 
 def field_bytes_per_site(prec):
-    # each field read once and written once per step: U (2 links), phi, e (2), pi
-    return (36 + 8 + 24) * 2 * 8 if prec == 0 else (24 + 8 + 24) * 2 * 4
-
-
-def site_bytes_per_site(prec):
-    # reads U(n), phi(n), e(n-1/2), e(n+1/2), pi(n-1/2), pi(n+1/2); writes 6 site fields
+    """Fused leapfrog + site-field kernel: every field of step n read once, the
+    fields of step n+1 written once (U: 2 links, phi, e: 2, pi) and the six site
+    fields E, B written once."""
     r = 8 if prec == 0 else 4
     links = 36 if prec == 0 else 24
-    return (links + 8 + 32 + 16) * r + 48 * r
+    return (links + 8 + 16 + 8) * 2 * r + 48 * r
 
 
-def push_bytes_per_particle(prec):
-    # state read + written (x, y, eta, p^x, p^y, P_eta, Q: 14 reals) + species id
-    # + the gathered site fields (48 reals); the scalar for the rapidity line
+def push_bytes(prec, n_active, V):
+    """Push kernel: each active particle's state read and written once (x, y,
+    eta, p^x, p^y, P_eta, Q: 14 reals) plus its species index; the site fields
+    (48 reals per site) and the scalar at t_{n+1} (8 reals per site) read once."""
     r = 8 if prec == 0 else 4
-    return 14 * 2 * r + 4 + 48 * r + 8 * r
+    return n_active * (14 * 2 * r + 4) + V * (48 + 8) * r
 
 
 class ClockSampler:
@@ -175,11 +173,10 @@ def run_ours(args):
         ev.wong_init()
         for _ in range(args.warmup):
             ev.glasma_step(1)
-            ev.wong_site_fields()
             ev.wong_push()
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
         K = args.steps
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -191,12 +188,10 @@ def run_ours(args):
             flush.zero_()  # L2 flush between timed steps, outside the step's events
             e = evs[k]
             e[0].record(stream)
-            ev.glasma_step(1)
+            ev.glasma_step(1)      # fused leapfrog + site E, B kernel
             e[1].record(stream)
-            ev.wong_site_fields()
+            ev.wong_push()         # push kernel
             e[2].record(stream)
-            ev.wong_push()
-            e[3].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         if world > 1:
@@ -204,9 +199,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         ck = clocks.stop()
         t_field = sum(e[0].elapsed_time(e[1]) for e in evs) / 1e3
-        t_site = sum(e[1].elapsed_time(e[2]) for e in evs) / 1e3
-        t_push = sum(e[2].elapsed_time(e[3]) for e in evs) / 1e3
-        t_step = t_field + t_site + t_push
+        t_push = sum(e[1].elapsed_time(e[2]) for e in evs) / 1e3
+        t_step = t_field + t_push
         obs = ev.observables()
         n_active = sum(obs.n_active[k] for k in range(len(w.species)))
 
@@ -237,8 +231,7 @@ def run_ours(args):
         peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
         kern = {
             "field_step": (field_bytes_per_site(w.precision) * V, t_field / K),
-            "site_fields": (site_bytes_per_site(w.precision) * V, t_site / K),
-            "wong_push": (push_bytes_per_particle(w.precision) * n_active, t_push / K),
+            "wong_push": (push_bytes(w.precision, n_active, V), t_push / K),
         }
         dom = max(kern, key=lambda k: kern[k][1])
         roof = {}
@@ -265,15 +258,14 @@ def run_ours(args):
                        "events_per_gpu": 1, "parallelism": "events sharded over ranks",
                        "l2": "flushed (512 MiB write) between timed steps, flush outside the step's events"},
             "particle_steps_per_s": n_active_all * K / t_step,
-            "kernel_ms_per_step": {"field_step": t_field / K * 1e3, "site_fields": t_site / K * 1e3,
-                                   "wong_push": t_push / K * 1e3},
+            "kernel_ms_per_step": {"field_step": t_field / K * 1e3, "wong_push": t_push / K * 1e3},
             "roofline": dict(roof[dom], kernel=dom),
             "roofline_kernels": roof,
             "e2e": {"value": world * V * K / e2e_t, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 8 * (8 * 7 + 7),
                     "includes": "gl_step_coupled + observables() read back to the host every step, wall clock; "
                                 "the step's inputs are the device-resident state"},
-            "gpu_launches": 3 * K,
+            "gpu_launches": 2 * K,
             "clocks": ck,
             "wall_s_timed_loop": wall,
         }

@@ -82,6 +82,9 @@ typedef struct {
     double LambdaUV_GeV;    /* ultraviolet cutoff of the Poisson kernel (<= 0: none) */
     double dtau_over_a;     /* leapfrog time step in units of a */
     uint64_t seed;          /* Philox key of this event's random numbers */
+    int32_t sort_every;     /* reorder particles by cell every k pushes (0: never); only the
+                               memory order changes, downloads keep the caller's order */
+    int32_t reserved;       /* must be 0 */
 } gl_config;
 
 /* One species of test particles (Sec. 3.2 and 7.1). */

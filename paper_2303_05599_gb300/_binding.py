@@ -26,7 +26,8 @@ class gl_config(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("Ns", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("reunit_every", ctypes.c_int32), ("L_fm", ctypes.c_double), ("g2mu_GeV", ctypes.c_double),
                 ("mIR_GeV", ctypes.c_double), ("LambdaUV_GeV", ctypes.c_double),
-                ("dtau_over_a", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("dtau_over_a", ctypes.c_double), ("seed", ctypes.c_uint64), ("sort_every", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class gl_species(ctypes.Structure):
@@ -107,7 +108,7 @@ def make_config(w):
     """gl_config from a workloads.Workload."""
     return gl_config(N=w.N, Ns=w.Ns, precision=w.precision, reunit_every=w.reunit_every, L_fm=w.L_fm,
                      g2mu_GeV=w.g2mu_GeV, mIR_GeV=w.mIR_GeV, LambdaUV_GeV=w.LambdaUV_GeV,
-                     dtau_over_a=w.dtau_over_a, seed=w.seed)
+                     dtau_over_a=w.dtau_over_a, seed=w.seed, sort_every=w.sort_every, reserved=0)
 
 
 def make_species(w):

@@ -41,6 +41,9 @@ struct gl_ctx {
     void* field[2];
     void* site;
     void* parts;
+    void* parts_alt;    // second particle buffer for the cell sort
+    void* sort_scratch;
+    int sort_ok;
     void* scratch;
     size_t scratch_bytes;
     double* partials;
@@ -94,7 +97,7 @@ static const char* validate(const gl_config* cfg, const gl_species* sp, int32_t 
 }
 
 struct Carve {
-    size_t field, site, parts, scratch, partials, obs, bad, total;
+    size_t field, site, parts, parts_alt, sort, scratch, partials, obs, bad, total;
 };
 
 static Carve carve(const gl_config* cfg, int64_t np) {
@@ -105,6 +108,9 @@ static Carve carve(const gl_config* cfg, int64_t np) {
     c.field = o; o += 2 * a256(field_bytes(prec, Vn));
     c.site = o; o += a256(site_bytes(prec, Vn));
     c.parts = o; o += a256(particle_bytes(prec, np));
+    const bool sorting = cfg->sort_every > 0 && np > 0 && sort_supported(Vn);
+    c.parts_alt = o; o += sorting ? a256(particle_bytes(prec, np)) : 0;
+    c.sort = o; o += sorting ? a256(sort_scratch_bytes(Vn, np)) : 0;
     size_t sc = init_scratch_bytes(Vn);
     size_t stg = (size_t)Vn * 6 * 8 * sizeof(double);
     if (stg > sc) sc = stg;
@@ -172,6 +178,9 @@ gl_status gl_create(const gl_config* cfg, const gl_species* sp, int32_t ns, void
     c->field[1] = c->ws + cv.field + a256(field_bytes(c->prec, c->Vn));
     c->site = c->ws + cv.site;
     c->parts = c->ws + cv.parts;
+    c->sort_ok = cfg->sort_every > 0 && c->np > 0 && sort_supported(c->Vn);
+    c->parts_alt = c->sort_ok ? c->ws + cv.parts_alt : nullptr;
+    c->sort_scratch = c->sort_ok ? c->ws + cv.sort : nullptr;
     c->scratch = c->ws + cv.scratch;
     c->scratch_bytes = cv.partials - cv.scratch;
     c->partials = (double*)(c->ws + cv.partials);
@@ -294,19 +303,24 @@ gl_status gl_set_step(gl_ctx* c, int64_t step) {
     return GL_OK;
 }
 
-static void one_field_step(gl_ctx* c) {
+// One leapfrog step.  When the particles are at the fields' time the same
+// kernel also interpolates E, B at that time for the push that follows.
+static void one_field_step(gl_ctx* c, bool site) {
     int reunit = 0;
     if (c->prec == GL_FP32_2ROW && c->cfg.reunit_every > 0) {
         if (++c->reunit_count >= c->cfg.reunit_every) { reunit = 1; c->reunit_count = 0; }
     }
-    launch_field_step(c->prec, c->field[c->cur], c->field[1 - c->cur], c->N, c->step * c->dt, c->dt, reunit, c->stream);
+    site = site && c->pstep == c->step;
+    launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], site ? c->site : nullptr, c->N,
+                      c->step * c->dt, c->dt, reunit, c->stream);
+    if (site) c->site_step = c->pstep;
     c->cur = 1 - c->cur;
     c->step++;
 }
 
 gl_status glasma_step(gl_ctx* c, int32_t n) {
     if (!c || n < 0) return GL_ERR_ARG;
-    for (int k = 0; k < n; k++) one_field_step(c);
+    for (int k = 0; k < n; k++) one_field_step(c, k == n - 1 && c->np > 0);
     return check_cuda(c, "glasma_step");
 }
 
@@ -319,6 +333,7 @@ static gl_status site_once(gl_ctx* c) {
 
 gl_status wong_site_fields(gl_ctx* c) {
     if (!c) return GL_ERR_ARG;
+    if (c->site_step == c->pstep && c->pstep == c->step - 1) return GL_OK;  // written by the field step
     if (gl_status s = site_once(c)) return s;
     return check_cuda(c, "wong_site_fields");
 }
@@ -331,6 +346,12 @@ static gl_status push_once(gl_ctx* c) {
     if (c->np) launch_push(c->prec, c->site, c->field[c->cur], c->parts, c->np, c->N, t, c->dt, active_mask(c, c->pstep),
                            c->spp, c->stream);
     c->pstep++;
+    if (c->sort_ok && c->pstep % c->cfg.sort_every == 0) {
+        launch_sort(c->prec, c->parts, c->parts_alt, c->np, c->N, c->sort_scratch, c->stream);
+        void* tmp = c->parts;
+        c->parts = c->parts_alt;
+        c->parts_alt = tmp;
+    }
     return GL_OK;
 }
 
@@ -344,7 +365,7 @@ gl_status gl_step_coupled(gl_ctx* c, int32_t n) {
     if (!c || n < 0) return GL_ERR_ARG;
     for (int k = 0; k < n; k++) {
         if (c->pstep != c->step) return fail(c, GL_ERR_STATE, "particles are not at the fields' time");
-        one_field_step(c);
+        one_field_step(c, true);
         if (gl_status s = push_once(c)) return s;
     }
     return check_cuda(c, "gl_step_coupled");

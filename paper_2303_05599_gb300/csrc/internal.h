@@ -14,8 +14,10 @@ struct SpeciesParams {
     int n_species;
 };
 
-// field step n -> n+1 on buffers in/out (FP64 or FP32 two-row layout)
-void launch_field_step(int prec, void* in, void* out, int N, double t, double dt, int reunit, cudaStream_t st);
+// field step n -> n+1 on buffers in/out (FP64 or FP32 two-row layout); when
+// site is not null the same kernel also writes the site E, B at t_n
+void launch_fused_step(int prec, void* in, void* out, void* site, int N, double t, double dt, int reunit,
+                       cudaStream_t st);
 // site E, B at t_n from buffer n (U, phi, e(n-1/2), pi(n-1/2)) and buffer n+1 (e, pi at n+1/2)
 void launch_site_fields(int prec, const void* bn, const void* bn1, void* site, int N, double t, cudaStream_t st);
 // Euler + CPIC push of all particles active at t_n (bit s of active_mask)
@@ -40,6 +42,11 @@ void launch_particle_obs(int prec, const void* parts, int64_t np, double t, uint
                          cudaStream_t st);
 void launch_field_obs(int prec, const void* b, const void* site, int N, double* partials, int max_blocks,
                       double* out, cudaStream_t st);
+
+// counting sort of the particles by cell from src into dst (same layout)
+void launch_sort(int prec, void* src, void* dst, int64_t np, int N, void* scratch, cudaStream_t st);
+size_t sort_scratch_bytes(int64_t Vn, int64_t np);
+bool sort_supported(int64_t Vn);
 
 size_t particle_bytes(int prec, int64_t np);
 size_t site_bytes(int prec, int64_t Vn);

@@ -1,0 +1,376 @@
+// Fused Glasma leapfrog step and site E/B interpolation (Sec. 2.1 and 3.2 of
+// arXiv:2303.05599) on shared-memory tiles.
+//
+// One CTA owns a TX x TY tile of sites.  Per step it computes, from U(n),
+// phi(n), e(n-1/2), pi(n-1/2):
+//   the momenta e(n+1/2), pi(n+1/2), the links U(n+1) and the scalar phi(n+1),
+//   and (SITE) the site fields E, B at t_n that the particle push gathers.
+// Every cell plaquette is formed once per tile and shared.  With
+//   A(c)  = components of i[P(c)]_ah,  P(c) = Ux(c) Uy(c+x) Ux(c+y)^+ Uy(c)^+,
+//   Dn(s) = Uy(s-y)^+ A(s-y) Uy(s-y),   Lf(s) = Ux(s-x)^+ A(s-x) Ux(s-x),
+// the plaquette forces and the clover are
+//   F_x = t (A - Dn),  F_y = t (Lf - A),
+//   B_eta = (A + Lf + Dn + Uy(s-y)^+ Lf(s-y) Uy(s-y)) / 4.
+// E_i(s) needs e_i(n+1/2) at s - i, so the tile also advances the momenta of
+// one halo column (x0 - 1) and one halo row (y0 - 1).
+//
+// Shared-memory regions, in tile coordinates (origin at the tile corner):
+//   links, phi: x in [-2, TX], y in [-2, TY]      (LW x LH)
+//   plaquettes: x in [-2, TX-1], y in [-2, TY-1]  (AW x AH)
+//   momenta:    x in [-1, TX-1], y in [-1, TY-1]  (EW x EH)
+#include "internal.h"
+#include "layout.cuh"
+
+namespace gl {
+
+template <typename R>
+struct ExpN;
+template <>
+struct ExpN<double> { static constexpr int n = 20; };
+template <>
+struct ExpN<float> { static constexpr int n = 12; };
+
+// components of V^+ X V for Hermitian X (only the upper triangle of the
+// Hermitian result is formed)
+template <typename R>
+__device__ __forceinline__ A8<R> conj_dn(const M3<R>& V, const A8<R>& x) {
+    const M3<R> X = alg_to_mat(x);
+    // Y = X V, X with real diagonal
+    M3<R> Y;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            R sr = X.re[i][i] * V.re[i][j], si = X.re[i][i] * V.im[i][j];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (k == i) continue;
+                sr = fma(X.re[i][k], V.re[k][j], sr);
+                sr = fma(-X.im[i][k], V.im[k][j], sr);
+                si = fma(X.re[i][k], V.im[k][j], si);
+                si = fma(X.im[i][k], V.re[k][j], si);
+            }
+            Y.re[i][j] = sr;
+            Y.im[i][j] = si;
+        }
+    // Z = V^+ Y, upper triangle; Z_ij = sum_k conj(V_ki) Y_kj
+    R zr[3][3], zi[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = i; j < 3; j++) {
+            R sr = R(0), si = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                sr = fma(V.re[k][i], Y.re[k][j], sr);
+                sr = fma(V.im[k][i], Y.im[k][j], sr);
+                if (i != j) {
+                    si = fma(V.re[k][i], Y.im[k][j], si);
+                    si = fma(-V.im[k][i], Y.re[k][j], si);
+                }
+            }
+            zr[i][j] = sr;
+            zi[i][j] = si;
+        }
+    A8<R> o;
+    o.v[0] = R(2) * zr[0][1];
+    o.v[1] = -R(2) * zi[0][1];
+    o.v[2] = zr[0][0] - zr[1][1];
+    o.v[3] = R(2) * zr[0][2];
+    o.v[4] = -R(2) * zi[0][2];
+    o.v[5] = R(2) * zr[1][2];
+    o.v[6] = -R(2) * zi[1][2];
+    o.v[7] = (zr[0][0] + zr[1][1] - R(2) * zr[2][2]) * inv_sqrt3<R>();
+    return o;
+}
+
+// components of V X V^+ for Hermitian X
+template <typename R>
+__device__ __forceinline__ A8<R> conj_up(const M3<R>& V, const A8<R>& x) {
+    return conj_dn(dag(V), x);
+}
+
+template <typename R, int TX, int TY>
+struct Tile {
+    static constexpr int LW = TX + 3, LH = TY + 3, LN = LW * LH;
+    static constexpr int AW = TX + 2, AH = TY + 2, AN = AW * AH;
+    static constexpr int EW = TX + 1, EH = TY + 1, EN = EW * EH;
+    static constexpr int NT = TX * TY;
+    // shared-memory words (R): links 2 x 18 x LN, phi 8 x LN, A 8 x AN,
+    // e_old 16 x EN, e_new 16 x EN, Lf 8 x EN
+    static constexpr size_t words = (size_t)36 * LN + 8 * LN + 8 * AN + 40 * EN;
+    static constexpr size_t bytes = words * sizeof(R);
+};
+
+template <typename R>
+__device__ __forceinline__ M3<R> s_link(const R* sU, int d, int li, int LN) {
+    const R* b = sU + (size_t)d * 18 * LN + li;
+    M3<R> m;
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        m.re[k / 3][k % 3] = b[(2 * k) * LN];
+        m.im[k / 3][k % 3] = b[(2 * k + 1) * LN];
+    }
+    return m;
+}
+
+template <typename R>
+__device__ __forceinline__ A8<R> s_alg(const R* s, int i, int n) {
+    A8<R> x;
+#pragma unroll
+    for (int a = 0; a < 8; a++) x.v[a] = s[a * n + i];
+    return x;
+}
+
+template <typename R>
+__device__ __forceinline__ void s_alg_put(R* s, int i, int n, const A8<R>& x) {
+#pragma unroll
+    for (int a = 0; a < 8; a++) s[a * n + i] = x.v[a];
+}
+
+__device__ __forceinline__ void reunit(M3<float>& u) {
+    double r0r[3], r0i[3], r1r[3], r1i[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        r0r[j] = u.re[0][j]; r0i[j] = u.im[0][j];
+        r1r[j] = u.re[1][j]; r1i[j] = u.im[1][j];
+    }
+    double n0 = 0;
+#pragma unroll
+    for (int j = 0; j < 3; j++) n0 += r0r[j] * r0r[j] + r0i[j] * r0i[j];
+    n0 = 1.0 / sqrt(n0);
+#pragma unroll
+    for (int j = 0; j < 3; j++) { r0r[j] *= n0; r0i[j] *= n0; }
+    double cr = 0, ci = 0;
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        cr += r0r[j] * r1r[j] + r0i[j] * r1i[j];
+        ci += r0r[j] * r1i[j] - r0i[j] * r1r[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        r1r[j] -= cr * r0r[j] - ci * r0i[j];
+        r1i[j] -= cr * r0i[j] + ci * r0r[j];
+    }
+    double n1 = 0;
+#pragma unroll
+    for (int j = 0; j < 3; j++) n1 += r1r[j] * r1r[j] + r1i[j] * r1i[j];
+    n1 = 1.0 / sqrt(n1);
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        u.re[0][j] = (float)r0r[j]; u.im[0][j] = (float)r0i[j];
+        u.re[1][j] = (float)(r1r[j] * n1); u.im[1][j] = (float)(r1i[j] * n1);
+    }
+}
+__device__ __forceinline__ void reunit(M3<double>&) {}
+
+struct StepArgs {
+    int N;
+    int tiles_x;
+    double t, dt, inv_t, dt_over_th, dt_th;
+    int reunit;
+};
+
+template <typename R, int TX, int TY, bool SITE>
+__global__ void __launch_bounds__(TX * TY) fused_step_kernel(Fields<R> in, Fields<R> out,
+                                                             typename Prec<R>::V* site, StepArgs a) {
+    using T = Tile<R, TX, TY>;
+    using Vec = typename Prec<R>::V;
+    constexpr int AP = Prec<R>::AP;
+    constexpr int LW = T::LW, LN = T::LN, AW = T::AW, AN = T::AN, EW = T::EW, EN = T::EN, NT = T::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* sU = (R*)smem_raw;          // [2][18][LN]
+    R* sPhi = sU + 36 * LN;        // [8][LN]
+    R* sA = sPhi + 8 * LN;         // [8][AN]
+    R* sEo = sA + 8 * AN;          // [2][8][EN]
+    R* sEn = sEo + 16 * EN;        // [2][8][EN]
+    R* sLf = sEn + 16 * EN;        // [8][EN]
+
+    const int N = a.N;
+    const int64_t Vn = (int64_t)N * N;
+    const int x0 = (blockIdx.x % a.tiles_x) * TX, y0 = (blockIdx.x / a.tiles_x) * TY;
+    const int tid = threadIdx.x;
+    const R t = (R)a.t, dt = (R)a.dt, inv_t = (R)a.inv_t;
+
+    // ---- phase 1: links, scalar and old momenta into shared memory
+    for (int i = tid; i < LN; i += NT) {
+        const int lx = i % LW - 2, ly = i / LW - 2;
+        const int gx = wrapi(x0 + lx, N), gy = wrapi(y0 + ly, N);
+        const int64_t g = (int64_t)gy * N + gx;
+#pragma unroll
+        for (int d = 0; d < 2; d++) {
+            const M3<R> u = load_link(in.U, d, g, Vn);
+            R* b = sU + (size_t)d * 18 * LN + i;
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+                b[(2 * k) * LN] = u.re[k / 3][k % 3];
+                b[(2 * k + 1) * LN] = u.im[k / 3][k % 3];
+            }
+        }
+        s_alg_put(sPhi, i, LN, load_alg(in.phi, g, Vn));
+    }
+    for (int i = tid; i < EN; i += NT) {
+        const int ex = i % EW - 1, ey = i / EW - 1;
+        const int64_t g = (int64_t)wrapi(y0 + ey, N) * N + wrapi(x0 + ex, N);
+        s_alg_put(sEo, i, EN, load_alg(in.e, g, Vn));
+        s_alg_put(sEo + 8 * EN, i, EN, load_alg(in.e + (size_t)AP * Vn, g, Vn));
+    }
+    __syncthreads();
+
+    // ---- phase 2: plaquettes of the tile cells and their halo
+    for (int i = tid; i < AN; i += NT) {
+        const int ax = i % AW - 2, ay = i / AW - 2;
+        const int l = (ay + 2) * LW + (ax + 2);
+        const M3<R> C = mul(s_link(sU, 0, l, LN), s_link(sU, 1, l + 1, LN));
+        const M3<R> P = mul_nd(mul_nd(C, s_link(sU, 0, l + LW, LN)), s_link(sU, 1, l, LN));
+        s_alg_put(sA, i, AN, iah_to_alg(P));
+    }
+    __syncthreads();
+
+    // ---- phase 3: momenta at n+1/2 on the tile and the halo column/row.
+    // Index 0..NT-1 are the tile sites in thread order (kept in registers for
+    // phase 4); the halo follows.
+    A8<R> my_ex, my_ey, my_tx, my_ty, my_b;
+    for (int k = tid; k < EN; k += NT) {
+        int ex, ey;
+        if (k < NT) { ex = k % TX; ey = k / TX; }
+        else {
+            const int h = k - NT;
+            if (h < TY + 1) { ex = -1; ey = h - 1; }
+            else { ex = h - (TY + 1); ey = -1; }
+        }
+        const int e = (ey + 1) * EW + (ex + 1);
+        const int l = (ey + 2) * LW + (ex + 2);
+        const int ai = (ey + 2) * AW + (ex + 2);
+        const A8<R> A0 = s_alg(sA, ai, AN);
+        const A8<R> Dn = conj_dn(s_link(sU, 1, l - LW, LN), s_alg(sA, ai - AW, AN));
+        const A8<R> Lf = conj_dn(s_link(sU, 0, l - 1, LN), s_alg(sA, ai - 1, AN));
+        const A8<R> ph = s_alg(sPhi, l, LN);
+        const A8<R> tx = conj_up(s_link(sU, 0, l, LN), s_alg(sPhi, l + 1, LN));
+        const A8<R> ty = conj_up(s_link(sU, 1, l, LN), s_alg(sPhi, l + LW, LN));
+        const A8<R> cx = icomm(tx, ph), cy = icomm(ty, ph);
+        A8<R> ex_n = s_alg(sEo, e, EN), ey_n = s_alg(sEo + 8 * EN, e, EN);
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            ex_n.v[c] += dt * (t * (A0.v[c] - Dn.v[c]) + inv_t * cx.v[c]);
+            ey_n.v[c] += dt * (t * (Lf.v[c] - A0.v[c]) + inv_t * cy.v[c]);
+        }
+        s_alg_put(sEn, e, EN, ex_n);
+        s_alg_put(sEn + 8 * EN, e, EN, ey_n);
+        s_alg_put(sLf, e, EN, Lf);
+        if (k < NT) {
+            my_ex = ex_n; my_ey = ey_n; my_tx = tx; my_ty = ty;
+#pragma unroll
+            for (int c = 0; c < 8; c++) my_b.v[c] = A0.v[c] + Lf.v[c] + Dn.v[c];
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 4: the tile sites
+    const int ix = tid % TX, iy = tid / TX;
+    const int gx = x0 + ix, gy = y0 + iy;
+    if (gx >= N || gy >= N) return;
+    const int64_t g = (int64_t)gy * N + gx;
+    const int e = (iy + 1) * EW + (ix + 1);
+    const int l = (iy + 2) * LW + (ix + 2);
+    const A8<R> ph = s_alg(sPhi, l, LN);
+    const M3<R> Ux_m = s_link(sU, 0, l - 1, LN);
+    const M3<R> Uy_m = s_link(sU, 1, l - LW, LN);
+    const A8<R> bx = conj_dn(Ux_m, s_alg(sPhi, l - 1, LN));
+    const A8<R> by = conj_dn(Uy_m, s_alg(sPhi, l - LW, LN));
+    const A8<R> p_old = load_alg(in.pi, g, Vn);
+    A8<R> p_new, ph_new;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        const R lap = my_tx.v[c] + my_ty.v[c] + bx.v[c] + by.v[c] - R(4) * ph.v[c];
+        p_new.v[c] = p_old.v[c] + dt * inv_t * lap;
+        ph_new.v[c] = ph.v[c] + (R)a.dt_th * p_new.v[c];
+    }
+    if (SITE) {
+        // E_i = (1/4t){e_i(s) + U_i(s-i)^+ e_i(s-i) U_i(s-i)}, e summed over n -+ 1/2
+        A8<R> sx, sy;
+        const A8<R> eox = s_alg(sEo, e, EN), eoy = s_alg(sEo + 8 * EN, e, EN);
+        {
+            A8<R> bsum = s_alg(sEn, e - 1, EN);
+            const A8<R> bo = s_alg(sEo, e - 1, EN);
+#pragma unroll
+            for (int c = 0; c < 8; c++) bsum.v[c] += bo.v[c];
+            sx = conj_dn(Ux_m, bsum);
+        }
+        {
+            A8<R> bsum = s_alg(sEn + 8 * EN, e - EW, EN);
+            const A8<R> bo = s_alg(sEo + 8 * EN, e - EW, EN);
+#pragma unroll
+            for (int c = 0; c < 8; c++) bsum.v[c] += bo.v[c];
+            sy = conj_dn(Uy_m, bsum);
+        }
+        const A8<R> cr = conj_dn(Uy_m, s_alg(sLf, e - EW, EN));
+        A8<R> Ex, Ey, Ee, Bx, By, Be;
+        const R q = R(0.25) * inv_t, hf = R(0.5) * inv_t;
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            Ex.v[c] = q * (my_ex.v[c] + eox.v[c] + sx.v[c]);
+            Ey.v[c] = q * (my_ey.v[c] + eoy.v[c] + sy.v[c]);
+            Ee.v[c] = R(0.5) * (p_old.v[c] + p_new.v[c]);
+            Bx.v[c] = -hf * (my_ty.v[c] - by.v[c]);
+            By.v[c] = hf * (my_tx.v[c] - bx.v[c]);
+            Be.v[c] = R(0.25) * (my_b.v[c] + cr.v[c]);
+        }
+        store_alg(site, g, Vn, Ex);
+        store_alg(site + (size_t)1 * AP * Vn, g, Vn, Ey);
+        store_alg(site + (size_t)2 * AP * Vn, g, Vn, Ee);
+        store_alg(site + (size_t)3 * AP * Vn, g, Vn, Bx);
+        store_alg(site + (size_t)4 * AP * Vn, g, Vn, By);
+        store_alg(site + (size_t)5 * AP * Vn, g, Vn, Be);
+    }
+    store_alg(out.e, g, Vn, my_ex);
+    store_alg(out.e + (size_t)AP * Vn, g, Vn, my_ey);
+    store_alg(out.pi, g, Vn, p_new);
+    store_alg(out.phi, g, Vn, ph_new);
+    M3<R> nx = mul(exp_i_alg<R, ExpN<R>::n>(my_ex, (R)a.dt_over_th), s_link(sU, 0, l, LN));
+    M3<R> ny = mul(exp_i_alg<R, ExpN<R>::n>(my_ey, (R)a.dt_over_th), s_link(sU, 1, l, LN));
+    if (a.reunit) { reunit(nx); reunit(ny); }
+    store_link(out.U, 0, g, Vn, nx);
+    store_link(out.U, 1, g, Vn, ny);
+}
+
+template <typename R, int TX, int TY, bool SITE>
+static void launch_t(void* in, void* out, void* site, int N, double t, double dt, int reunit, cudaStream_t st) {
+    using T = Tile<R, TX, TY>;
+    // the dynamic shared-memory limit is a per-device function attribute
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        cudaFuncSetAttribute(fused_step_kernel<R, TX, TY, SITE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)T::bytes);
+        attr[dev] = true;
+    }
+    const int64_t Vn = (int64_t)N * N;
+    StepArgs a;
+    a.N = N;
+    a.tiles_x = (N + TX - 1) / TX;
+    const int tiles_y = (N + TY - 1) / TY;
+    const double th = t + 0.5 * dt;
+    a.t = t;
+    a.dt = dt;
+    a.inv_t = t > 0 ? 1.0 / t : 0.0;
+    a.dt_over_th = dt / th;
+    a.dt_th = dt * th;
+    a.reunit = reunit;
+    fused_step_kernel<R, TX, TY, SITE><<<a.tiles_x * tiles_y, TX * TY, T::bytes, st>>>(
+        carve_fields<R>(in, Vn), carve_fields<R>(out, Vn), (typename Prec<R>::V*)site, a);
+}
+
+void launch_fused_step(int prec, void* in, void* out, void* site, int N, double t, double dt, int reunit,
+                       cudaStream_t st) {
+    if (prec == 0) {
+        if (site) launch_t<double, 16, 8, true>(in, out, site, N, t, dt, 0, st);
+        else launch_t<double, 16, 8, false>(in, out, site, N, t, dt, 0, st);
+    } else {
+        if (site) launch_t<float, 16, 8, true>(in, out, site, N, t, dt, reunit, st);
+        else launch_t<float, 16, 8, false>(in, out, site, N, t, dt, reunit, st);
+    }
+}
+
+}  // namespace gl

@@ -51,6 +51,7 @@ class Workload:
     tau_max_fm: float = 1.0
     precision: int = FP64
     reunit_every: int = 8
+    sort_every: int = 16
     seed: int = 0
     species: List[Species] = field(default_factory=list)
     report_every_fm: float = 0.0
