@@ -224,6 +224,15 @@ gl_status gl_destroy(gl_ctx* c) {
 
 const char* gl_error_string(const gl_ctx* c) { return c ? c->err : g_create_err; }
 
+// reorder the particles by cell (memory order only)
+static void sort_particles(gl_ctx* c) {
+    if (!c->sort_ok) return;
+    launch_sort(c->prec, c->parts, c->parts_alt, c->np, c->N, c->sort_scratch, c->stream);
+    void* tmp = c->parts;
+    c->parts = c->parts_alt;
+    c->parts_alt = tmp;
+}
+
 static uint32_t active_mask(const gl_ctx* c, int64_t n) {
     uint32_t m = 0;
     const double t = n * c->dt;
@@ -255,6 +264,7 @@ gl_status wong_init(gl_ctx* c) {
     if (!c) return GL_ERR_ARG;
     launch_sample(c->prec, c->parts, c->np, c->N, c->cfg.seed, c->off, c->ns, c->rep, c->mode, c->p0, c->p1, c->q0,
                   c->stream);
+    sort_particles(c);
     c->pstep = c->step;
     return check_cuda(c, "wong_init");
 }
@@ -279,7 +289,10 @@ static gl_status transfer(gl_ctx* c, gl_buffer which, double* host, size_t count
     if (count == 0) return GL_OK;
     double* stg = (double*)c->scratch;
     if (to_device) cudaMemcpyAsync(stg, host, count * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-    if (which == GL_BUF_PARTICLES) launch_parts_convert(c->prec, c->parts, c->np, stg, to_device, c->stream);
+    if (which == GL_BUF_PARTICLES) {
+        launch_parts_convert(c->prec, c->parts, c->np, stg, to_device, c->stream);
+        if (to_device) sort_particles(c);
+    }
     else launch_convert(c->prec, which, to_device, which == GL_BUF_SITE ? c->site : c->field[c->cur], stg, c->N, c->np,
                         c->stream);
     if (!to_device) cudaMemcpyAsync(host, stg, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
@@ -346,12 +359,7 @@ static gl_status push_once(gl_ctx* c) {
     if (c->np) launch_push(c->prec, c->site, c->field[c->cur], c->parts, c->np, c->N, t, c->dt, active_mask(c, c->pstep),
                            c->spp, c->stream);
     c->pstep++;
-    if (c->sort_ok && c->pstep % c->cfg.sort_every == 0) {
-        launch_sort(c->prec, c->parts, c->parts_alt, c->np, c->N, c->sort_scratch, c->stream);
-        void* tmp = c->parts;
-        c->parts = c->parts_alt;
-        c->parts_alt = tmp;
-    }
+    if (c->sort_ok && c->pstep % c->cfg.sort_every == 0) sort_particles(c);
     return GL_OK;
 }
 

@@ -1,8 +1,8 @@
 // Fused Glasma leapfrog step and site E/B interpolation (Sec. 2.1 and 3.2 of
 // arXiv:2303.05599) on shared-memory tiles.
 //
-// One CTA owns a TX x TY tile of sites.  Per step it computes, from U(n),
-// phi(n), e(n-1/2), pi(n-1/2):
+// One CTA owns a TX x TY tile of sites (TX = 32: one warp per tile row).  Per
+// step it computes, from U(n), phi(n), e(n-1/2), pi(n-1/2):
 //   the momenta e(n+1/2), pi(n+1/2), the links U(n+1) and the scalar phi(n+1),
 //   and (SITE) the site fields E, B at t_n that the particle push gathers.
 // Every cell plaquette is formed once per tile and shared.  With
@@ -14,10 +14,13 @@
 // E_i(s) needs e_i(n+1/2) at s - i, so the tile also advances the momenta of
 // one halo column (x0 - 1) and one halo row (y0 - 1).
 //
-// Shared-memory regions, in tile coordinates (origin at the tile corner):
-//   links, phi: x in [-2, TX], y in [-2, TY]      (LW x LH)
-//   plaquettes: x in [-2, TX-1], y in [-2, TY-1]  (AW x AH)
-//   momenta:    x in [-1, TX-1], y in [-1, TY-1]  (EW x EH)
+// The tile's inputs are copied to shared memory with cp.async in the storage
+// layout of global memory (16-byte vectors; FP32 links as two rows, the third
+// rebuilt when a link is read).  Regions, in tile coordinates:
+//   links, phi:      x in [-2, TX],   y in [-2, TY]    (LW x LH)
+//   plaquettes A:    x in [-2, TX-1], y in [-2, TY-1]  (AW x AH)
+//   momenta, Lf:     x in [-1, TX-1], y in [-1, TY-1]  (EW x EH)
+//   pi(n-1/2):       the tile
 #include "internal.h"
 #include "layout.cuh"
 
@@ -35,8 +38,7 @@ struct ExpN<float> { static constexpr int n = 12; };
 template <typename R>
 __device__ __forceinline__ A8<R> conj_dn(const M3<R>& V, const A8<R>& x) {
     const M3<R> X = alg_to_mat(x);
-    // Y = X V, X with real diagonal
-    M3<R> Y;
+    M3<R> Y;  // X V, with X's diagonal real
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -53,8 +55,7 @@ __device__ __forceinline__ A8<R> conj_dn(const M3<R>& V, const A8<R>& x) {
             Y.re[i][j] = sr;
             Y.im[i][j] = si;
         }
-    // Z = V^+ Y, upper triangle; Z_ij = sum_k conj(V_ki) Y_kj
-    R zr[3][3], zi[3][3];
+    R zr[3][3], zi[3][3];  // V^+ Y, upper triangle
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -92,42 +93,76 @@ __device__ __forceinline__ A8<R> conj_up(const M3<R>& V, const A8<R>& x) {
 
 template <typename R, int TX, int TY>
 struct Tile {
+    using V = typename Prec<R>::V;
+    static constexpr int LP = Prec<R>::LP, AP = Prec<R>::AP;
     static constexpr int LW = TX + 3, LH = TY + 3, LN = LW * LH;
     static constexpr int AW = TX + 2, AH = TY + 2, AN = AW * AH;
     static constexpr int EW = TX + 1, EH = TY + 1, EN = EW * EH;
     static constexpr int NT = TX * TY;
-    // shared-memory words (R): links 2 x 18 x LN, phi 8 x LN, A 8 x AN,
-    // e_old 16 x EN, e_new 16 x EN, Lf 8 x EN
-    static constexpr size_t words = (size_t)36 * LN + 8 * LN + 8 * AN + 40 * EN;
-    static constexpr size_t bytes = words * sizeof(R);
+    // vectors: links 2 LP LN, phi AP LN, A AP AN, e sums 2 AP EN, Lf AP EN, pi AP NT
+    static constexpr size_t vecs = (size_t)2 * LP * LN + (size_t)AP * LN + (size_t)AP * AN + (size_t)3 * AP * EN +
+                                   (size_t)AP * NT;
+    static constexpr size_t bytes = vecs * sizeof(V);
 };
 
-template <typename R>
-__device__ __forceinline__ M3<R> s_link(const R* sU, int d, int li, int LN) {
-    const R* b = sU + (size_t)d * 18 * LN + li;
-    M3<R> m;
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// link (d) of shared-memory site li, planes of LN vectors
+__device__ __forceinline__ M3<double> s_link(const double2* sU, int d, int li, int LN) {
+    const double2* b = sU + (size_t)d * 9 * LN + li;
+    M3<double> m;
 #pragma unroll
     for (int k = 0; k < 9; k++) {
-        m.re[k / 3][k % 3] = b[(2 * k) * LN];
-        m.im[k / 3][k % 3] = b[(2 * k + 1) * LN];
+        const double2 v = b[k * LN];
+        m.re[k / 3][k % 3] = v.x;
+        m.im[k / 3][k % 3] = v.y;
     }
     return m;
 }
+__device__ __forceinline__ M3<float> s_link(const float4* sU, int d, int li, int LN) {
+    const float4* b = sU + (size_t)d * 3 * LN + li;
+    const float4 a = b[0], c = b[LN], e = b[2 * LN];
+    M3<float> m;
+    m.re[0][0] = a.x; m.im[0][0] = a.y; m.re[0][1] = a.z; m.im[0][1] = a.w;
+    m.re[0][2] = c.x; m.im[0][2] = c.y; m.re[1][0] = c.z; m.im[1][0] = c.w;
+    m.re[1][1] = e.x; m.im[1][1] = e.y; m.re[1][2] = e.z; m.im[1][2] = e.w;
+    rebuild_row2(m);
+    return m;
+}
 
-template <typename R>
-__device__ __forceinline__ A8<R> s_alg(const R* s, int i, int n) {
-    A8<R> x;
+__device__ __forceinline__ A8<double> s_alg(const double2* s, int i, int n) {
+    A8<double> x;
 #pragma unroll
-    for (int a = 0; a < 8; a++) x.v[a] = s[a * n + i];
+    for (int k = 0; k < 4; k++) {
+        const double2 v = s[k * n + i];
+        x.v[2 * k] = v.x;
+        x.v[2 * k + 1] = v.y;
+    }
     return x;
 }
-
-template <typename R>
-__device__ __forceinline__ void s_alg_put(R* s, int i, int n, const A8<R>& x) {
+__device__ __forceinline__ A8<float> s_alg(const float4* s, int i, int n) {
+    const float4 a = s[i], b = s[n + i];
+    A8<float> x;
+    x.v[0] = a.x; x.v[1] = a.y; x.v[2] = a.z; x.v[3] = a.w;
+    x.v[4] = b.x; x.v[5] = b.y; x.v[6] = b.z; x.v[7] = b.w;
+    return x;
+}
+__device__ __forceinline__ void s_alg_put(double2* s, int i, int n, const A8<double>& x) {
 #pragma unroll
-    for (int a = 0; a < 8; a++) s[a * n + i] = x.v[a];
+    for (int k = 0; k < 4; k++) s[k * n + i] = make_double2(x.v[2 * k], x.v[2 * k + 1]);
+}
+__device__ __forceinline__ void s_alg_put(float4* s, int i, int n, const A8<float>& x) {
+    s[i] = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
+    s[n + i] = make_float4(x.v[4], x.v[5], x.v[6], x.v[7]);
 }
 
+// FP64 Gram-Schmidt of rows 0 and 1 (FP32 links are stored as two rows)
 __device__ __forceinline__ void reunit(M3<float>& u) {
     double r0r[3], r0i[3], r1r[3], r1i[3];
 #pragma unroll
@@ -176,15 +211,15 @@ __global__ void __launch_bounds__(TX * TY) fused_step_kernel(Fields<R> in, Field
                                                              typename Prec<R>::V* site, StepArgs a) {
     using T = Tile<R, TX, TY>;
     using Vec = typename Prec<R>::V;
-    constexpr int AP = Prec<R>::AP;
+    constexpr int LP = T::LP, AP = T::AP;
     constexpr int LW = T::LW, LN = T::LN, AW = T::AW, AN = T::AN, EW = T::EW, EN = T::EN, NT = T::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* sU = (R*)smem_raw;          // [2][18][LN]
-    R* sPhi = sU + 36 * LN;        // [8][LN]
-    R* sA = sPhi + 8 * LN;         // [8][AN]
-    R* sEo = sA + 8 * AN;          // [2][8][EN]
-    R* sEn = sEo + 16 * EN;        // [2][8][EN]
-    R* sLf = sEn + 16 * EN;        // [8][EN]
+    Vec* sU = (Vec*)smem_raw;          // [2][LP][LN]
+    Vec* sPhi = sU + 2 * LP * LN;      // [AP][LN]
+    Vec* sA = sPhi + AP * LN;          // [AP][AN]
+    Vec* sEs = sA + AP * AN;           // [2][AP][EN]: e(n-1/2), then e(n-1/2) + e(n+1/2)
+    Vec* sLf = sEs + 2 * AP * EN;      // [AP][EN]
+    Vec* sPi = sLf + AP * EN;          // [AP][NT]
 
     const int N = a.N;
     const int64_t Vn = (int64_t)N * N;
@@ -192,35 +227,33 @@ __global__ void __launch_bounds__(TX * TY) fused_step_kernel(Fields<R> in, Field
     const int tid = threadIdx.x;
     const R t = (R)a.t, dt = (R)a.dt, inv_t = (R)a.inv_t;
 
-    // ---- phase 1: links, scalar and old momenta into shared memory
+    // ---- phase 1: asynchronous copies of the tile's inputs
     for (int i = tid; i < LN; i += NT) {
-        const int lx = i % LW - 2, ly = i / LW - 2;
-        const int gx = wrapi(x0 + lx, N), gy = wrapi(y0 + ly, N);
+        const int gx = wrapi(x0 + i % LW - 2, N), gy = wrapi(y0 + i / LW - 2, N);
         const int64_t g = (int64_t)gy * N + gx;
 #pragma unroll
-        for (int d = 0; d < 2; d++) {
-            const M3<R> u = load_link(in.U, d, g, Vn);
-            R* b = sU + (size_t)d * 18 * LN + i;
+        for (int k = 0; k < 2 * LP; k++) cp_async16(sU + (size_t)k * LN + i, in.U + (size_t)k * Vn + g);
 #pragma unroll
-            for (int k = 0; k < 9; k++) {
-                b[(2 * k) * LN] = u.re[k / 3][k % 3];
-                b[(2 * k + 1) * LN] = u.im[k / 3][k % 3];
-            }
-        }
-        s_alg_put(sPhi, i, LN, load_alg(in.phi, g, Vn));
+        for (int k = 0; k < AP; k++) cp_async16(sPhi + (size_t)k * LN + i, in.phi + (size_t)k * Vn + g);
     }
     for (int i = tid; i < EN; i += NT) {
-        const int ex = i % EW - 1, ey = i / EW - 1;
-        const int64_t g = (int64_t)wrapi(y0 + ey, N) * N + wrapi(x0 + ex, N);
-        s_alg_put(sEo, i, EN, load_alg(in.e, g, Vn));
-        s_alg_put(sEo + 8 * EN, i, EN, load_alg(in.e + (size_t)AP * Vn, g, Vn));
+        const int gx = wrapi(x0 + i % EW - 1, N), gy = wrapi(y0 + i / EW - 1, N);
+        const int64_t g = (int64_t)gy * N + gx;
+#pragma unroll
+        for (int k = 0; k < 2 * AP; k++) cp_async16(sEs + (size_t)k * EN + i, in.e + (size_t)k * Vn + g);
     }
+    {
+        const int gx = x0 + tid % TX, gy = y0 + tid / TX;
+        const int64_t g = (int64_t)wrapi(gy, N) * N + wrapi(gx, N);
+#pragma unroll
+        for (int k = 0; k < AP; k++) cp_async16(sPi + (size_t)k * NT + tid, in.pi + (size_t)k * Vn + g);
+    }
+    cp_async_wait_all();
     __syncthreads();
 
     // ---- phase 2: plaquettes of the tile cells and their halo
     for (int i = tid; i < AN; i += NT) {
-        const int ax = i % AW - 2, ay = i / AW - 2;
-        const int l = (ay + 2) * LW + (ax + 2);
+        const int l = (i / AW) * LW + (i % AW);  // cell (ax, ay) = (i % AW - 2, i / AW - 2)
         const M3<R> C = mul(s_link(sU, 0, l, LN), s_link(sU, 1, l + 1, LN));
         const M3<R> P = mul_nd(mul_nd(C, s_link(sU, 0, l + LW, LN)), s_link(sU, 1, l, LN));
         s_alg_put(sA, i, AN, iah_to_alg(P));
@@ -228,8 +261,8 @@ __global__ void __launch_bounds__(TX * TY) fused_step_kernel(Fields<R> in, Field
     __syncthreads();
 
     // ---- phase 3: momenta at n+1/2 on the tile and the halo column/row.
-    // Index 0..NT-1 are the tile sites in thread order (kept in registers for
-    // phase 4); the halo follows.
+    // Indices 0..NT-1 are the tile sites in thread order (kept in registers
+    // for phase 4); the halo follows.
     A8<R> my_ex, my_ey, my_tx, my_ty, my_b;
     for (int k = tid; k < EN; k += NT) {
         int ex, ey;
@@ -249,14 +282,18 @@ __global__ void __launch_bounds__(TX * TY) fused_step_kernel(Fields<R> in, Field
         const A8<R> tx = conj_up(s_link(sU, 0, l, LN), s_alg(sPhi, l + 1, LN));
         const A8<R> ty = conj_up(s_link(sU, 1, l, LN), s_alg(sPhi, l + LW, LN));
         const A8<R> cx = icomm(tx, ph), cy = icomm(ty, ph);
-        A8<R> ex_n = s_alg(sEo, e, EN), ey_n = s_alg(sEo + 8 * EN, e, EN);
+        const A8<R> eox = s_alg(sEs, e, EN), eoy = s_alg(sEs + AP * EN, e, EN);
+        A8<R> ex_n, ey_n, sx, sy;
 #pragma unroll
         for (int c = 0; c < 8; c++) {
-            ex_n.v[c] += dt * (t * (A0.v[c] - Dn.v[c]) + inv_t * cx.v[c]);
-            ey_n.v[c] += dt * (t * (Lf.v[c] - A0.v[c]) + inv_t * cy.v[c]);
+            ex_n.v[c] = eox.v[c] + dt * (t * (A0.v[c] - Dn.v[c]) + inv_t * cx.v[c]);
+            ey_n.v[c] = eoy.v[c] + dt * (t * (Lf.v[c] - A0.v[c]) + inv_t * cy.v[c]);
+            sx.v[c] = eox.v[c] + ex_n.v[c];
+            sy.v[c] = eoy.v[c] + ey_n.v[c];
         }
-        s_alg_put(sEn, e, EN, ex_n);
-        s_alg_put(sEn + 8 * EN, e, EN, ey_n);
+        // only this thread reads site e of sEs before the barrier
+        s_alg_put(sEs, e, EN, sx);
+        s_alg_put(sEs + AP * EN, e, EN, sy);
         s_alg_put(sLf, e, EN, Lf);
         if (k < NT) {
             my_ex = ex_n; my_ey = ey_n; my_tx = tx; my_ty = ty;
@@ -278,7 +315,7 @@ __global__ void __launch_bounds__(TX * TY) fused_step_kernel(Fields<R> in, Field
     const M3<R> Uy_m = s_link(sU, 1, l - LW, LN);
     const A8<R> bx = conj_dn(Ux_m, s_alg(sPhi, l - 1, LN));
     const A8<R> by = conj_dn(Uy_m, s_alg(sPhi, l - LW, LN));
-    const A8<R> p_old = load_alg(in.pi, g, Vn);
+    const A8<R> p_old = s_alg(sPi, tid, NT);
     A8<R> p_new, ph_new;
 #pragma unroll
     for (int c = 0; c < 8; c++) {
@@ -288,29 +325,16 @@ __global__ void __launch_bounds__(TX * TY) fused_step_kernel(Fields<R> in, Field
     }
     if (SITE) {
         // E_i = (1/4t){e_i(s) + U_i(s-i)^+ e_i(s-i) U_i(s-i)}, e summed over n -+ 1/2
-        A8<R> sx, sy;
-        const A8<R> eox = s_alg(sEo, e, EN), eoy = s_alg(sEo + 8 * EN, e, EN);
-        {
-            A8<R> bsum = s_alg(sEn, e - 1, EN);
-            const A8<R> bo = s_alg(sEo, e - 1, EN);
-#pragma unroll
-            for (int c = 0; c < 8; c++) bsum.v[c] += bo.v[c];
-            sx = conj_dn(Ux_m, bsum);
-        }
-        {
-            A8<R> bsum = s_alg(sEn + 8 * EN, e - EW, EN);
-            const A8<R> bo = s_alg(sEo + 8 * EN, e - EW, EN);
-#pragma unroll
-            for (int c = 0; c < 8; c++) bsum.v[c] += bo.v[c];
-            sy = conj_dn(Uy_m, bsum);
-        }
+        const A8<R> sx = conj_dn(Ux_m, s_alg(sEs, e - 1, EN));
+        const A8<R> sy = conj_dn(Uy_m, s_alg(sEs + AP * EN, e - EW, EN));
+        const A8<R> hx = s_alg(sEs, e, EN), hy = s_alg(sEs + AP * EN, e, EN);
         const A8<R> cr = conj_dn(Uy_m, s_alg(sLf, e - EW, EN));
         A8<R> Ex, Ey, Ee, Bx, By, Be;
         const R q = R(0.25) * inv_t, hf = R(0.5) * inv_t;
 #pragma unroll
         for (int c = 0; c < 8; c++) {
-            Ex.v[c] = q * (my_ex.v[c] + eox.v[c] + sx.v[c]);
-            Ey.v[c] = q * (my_ey.v[c] + eoy.v[c] + sy.v[c]);
+            Ex.v[c] = q * (hx.v[c] + sx.v[c]);
+            Ey.v[c] = q * (hy.v[c] + sy.v[c]);
             Ee.v[c] = R(0.5) * (p_old.v[c] + p_new.v[c]);
             Bx.v[c] = -hf * (my_ty.v[c] - by.v[c]);
             By.v[c] = hf * (my_tx.v[c] - bx.v[c]);
@@ -365,11 +389,11 @@ static void launch_t(void* in, void* out, void* site, int N, double t, double dt
 void launch_fused_step(int prec, void* in, void* out, void* site, int N, double t, double dt, int reunit,
                        cudaStream_t st) {
     if (prec == 0) {
-        if (site) launch_t<double, 16, 8, true>(in, out, site, N, t, dt, 0, st);
-        else launch_t<double, 16, 8, false>(in, out, site, N, t, dt, 0, st);
+        if (site) launch_t<double, 32, 4, true>(in, out, site, N, t, dt, 0, st);
+        else launch_t<double, 32, 4, false>(in, out, site, N, t, dt, 0, st);
     } else {
-        if (site) launch_t<float, 16, 8, true>(in, out, site, N, t, dt, reunit, st);
-        else launch_t<float, 16, 8, false>(in, out, site, N, t, dt, reunit, st);
+        if (site) launch_t<float, 32, 8, true>(in, out, site, N, t, dt, reunit, st);
+        else launch_t<float, 32, 8, false>(in, out, site, N, t, dt, reunit, st);
     }
 }
 
