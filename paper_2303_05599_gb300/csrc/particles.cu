@@ -142,7 +142,7 @@ template <>
 __device__ __forceinline__ float fmod_r<float>(float a, float b) { return fmodf(a, b); }
 
 template <typename R>
-__global__ void __launch_bounds__(128) push_kernel(const typename Prec<R>::V* __restrict__ site, Fields<R> bn1,
+__global__ void __launch_bounds__(128, 8) push_kernel(const typename Prec<R>::V* __restrict__ site, Fields<R> bn1,
                                                    Parts<R> P, int N, R t, R dt, R dt_over_t, uint32_t active,
                                                    SpeciesArgs<R> sa) {
     constexpr int AP = Prec<R>::AP;
@@ -195,14 +195,14 @@ __global__ void __launch_bounds__(128) push_kernel(const typename Prec<R>::V* __
         // CPIC: rotate with the crossed links at t_{n+1}, x first, then y
         const int dxc = jxu - ixu, dyc = jyu - iyu;
         const int jx = wrapi(jxu, N), jy = wrapi(jyu, N);
-        if (dxc == 1) p.q = adj_dag(load_link(bn1.U, 0, cell, Vn), p.q);
-        else if (dxc == -1) p.q = adj(load_link(bn1.U, 0, (int64_t)iy * N + jx, Vn), p.q);
-        if (dyc == 1) p.q = adj_dag(load_link(bn1.U, 1, (int64_t)iy * N + jx, Vn), p.q);
-        else if (dyc == -1) p.q = adj(load_link(bn1.U, 1, (int64_t)jy * N + jx, Vn), p.q);
+        if (dxc == 1) p.q = conj_dn(load_link(bn1.U, 0, cell, Vn), p.q);
+        else if (dxc == -1) p.q = conj_up(load_link(bn1.U, 0, (int64_t)iy * N + jx, Vn), p.q);
+        if (dyc == 1) p.q = conj_dn(load_link(bn1.U, 1, (int64_t)iy * N + jx, Vn), p.q);
+        else if (dyc == -1) p.q = conj_up(load_link(bn1.U, 1, (int64_t)jy * N + jx, Vn), p.q);
         // rapidity Wilson line at the new cell: Q <- e^{-i deta phi} Q e^{+i deta phi}
         if (deta != R(0)) {
             const A8<R> ph = load_alg(bn1.phi, (int64_t)jy * N + jx, Vn);
-            p.q = adj(exp_i_alg<R, (sizeof(R) == 8 ? 20 : 10)>(ph, -deta), p.q);
+            p.q = conj_up(exp_i_alg<R, (sizeof(R) == 8 ? 20 : 6)>(ph, -deta), p.q);
         }
         P.store(i, p);
     }

@@ -33,64 +33,6 @@ struct ExpN<double> { static constexpr int n = 20; };
 template <>
 struct ExpN<float> { static constexpr int n = 12; };
 
-// components of V^+ X V for Hermitian X (only the upper triangle of the
-// Hermitian result is formed)
-template <typename R>
-__device__ __forceinline__ A8<R> conj_dn(const M3<R>& V, const A8<R>& x) {
-    const M3<R> X = alg_to_mat(x);
-    M3<R> Y;  // X V, with X's diagonal real
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            R sr = X.re[i][i] * V.re[i][j], si = X.re[i][i] * V.im[i][j];
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                if (k == i) continue;
-                sr = fma(X.re[i][k], V.re[k][j], sr);
-                sr = fma(-X.im[i][k], V.im[k][j], sr);
-                si = fma(X.re[i][k], V.im[k][j], si);
-                si = fma(X.im[i][k], V.re[k][j], si);
-            }
-            Y.re[i][j] = sr;
-            Y.im[i][j] = si;
-        }
-    R zr[3][3], zi[3][3];  // V^+ Y, upper triangle
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = i; j < 3; j++) {
-            R sr = R(0), si = R(0);
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                sr = fma(V.re[k][i], Y.re[k][j], sr);
-                sr = fma(V.im[k][i], Y.im[k][j], sr);
-                if (i != j) {
-                    si = fma(V.re[k][i], Y.im[k][j], si);
-                    si = fma(-V.im[k][i], Y.re[k][j], si);
-                }
-            }
-            zr[i][j] = sr;
-            zi[i][j] = si;
-        }
-    A8<R> o;
-    o.v[0] = R(2) * zr[0][1];
-    o.v[1] = -R(2) * zi[0][1];
-    o.v[2] = zr[0][0] - zr[1][1];
-    o.v[3] = R(2) * zr[0][2];
-    o.v[4] = -R(2) * zi[0][2];
-    o.v[5] = R(2) * zr[1][2];
-    o.v[6] = -R(2) * zi[1][2];
-    o.v[7] = (zr[0][0] + zr[1][1] - R(2) * zr[2][2]) * inv_sqrt3<R>();
-    return o;
-}
-
-// components of V X V^+ for Hermitian X
-template <typename R>
-__device__ __forceinline__ A8<R> conj_up(const M3<R>& V, const A8<R>& x) {
-    return conj_dn(dag(V), x);
-}
-
 template <typename R, int TX, int TY>
 struct Tile {
     using V = typename Prec<R>::V;

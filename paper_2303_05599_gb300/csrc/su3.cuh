@@ -222,6 +222,64 @@ __device__ __forceinline__ A8<R> adj_dag(const M3<R>& U, const A8<R>& x) {
     return herm_to_alg(mul(mul_dn(U, alg_to_mat(x)), U));
 }
 
+// components of V^+ X V for Hermitian X (only the upper triangle of the
+// Hermitian result is formed)
+template <typename R>
+__device__ __forceinline__ A8<R> conj_dn(const M3<R>& V, const A8<R>& x) {
+    const M3<R> X = alg_to_mat(x);
+    M3<R> Y;  // X V, with X's diagonal real
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            R sr = X.re[i][i] * V.re[i][j], si = X.re[i][i] * V.im[i][j];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (k == i) continue;
+                sr = fma(X.re[i][k], V.re[k][j], sr);
+                sr = fma(-X.im[i][k], V.im[k][j], sr);
+                si = fma(X.re[i][k], V.im[k][j], si);
+                si = fma(X.im[i][k], V.re[k][j], si);
+            }
+            Y.re[i][j] = sr;
+            Y.im[i][j] = si;
+        }
+    R zr[3][3], zi[3][3];  // V^+ Y, upper triangle
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = i; j < 3; j++) {
+            R sr = R(0), si = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                sr = fma(V.re[k][i], Y.re[k][j], sr);
+                sr = fma(V.im[k][i], Y.im[k][j], sr);
+                if (i != j) {
+                    si = fma(V.re[k][i], Y.im[k][j], si);
+                    si = fma(-V.im[k][i], Y.re[k][j], si);
+                }
+            }
+            zr[i][j] = sr;
+            zi[i][j] = si;
+        }
+    A8<R> o;
+    o.v[0] = R(2) * zr[0][1];
+    o.v[1] = -R(2) * zi[0][1];
+    o.v[2] = zr[0][0] - zr[1][1];
+    o.v[3] = R(2) * zr[0][2];
+    o.v[4] = -R(2) * zi[0][2];
+    o.v[5] = R(2) * zr[1][2];
+    o.v[6] = -R(2) * zi[1][2];
+    o.v[7] = (zr[0][0] + zr[1][1] - R(2) * zr[2][2]) * inv_sqrt3<R>();
+    return o;
+}
+
+// components of V X V^+ for Hermitian X
+template <typename R>
+__device__ __forceinline__ A8<R> conj_up(const M3<R>& V, const A8<R>& x) {
+    return conj_dn(dag(V), x);
+}
+
 // exp(i s X) for Hermitian traceless X = x^a T^a.  Cayley-Hamilton gives
 // X^3 = c1 X + c0 with c1 = tr(X^2)/2 and c0 = det X, so every power of iX
 // is a combination of 1, X, X^2; the exponential series is summed on those
@@ -237,9 +295,11 @@ __device__ __forceinline__ M3<R> exp_i_alg(const A8<R>& x, R s) {
     R c1 = R(0.5) * (X2.re[0][0] + X2.re[1][1] + X2.re[2][2]);
     int nsq = 0;
     R scl = R(1);
-    // Frobenius norm^2 of X is 2 c1; keep the scaled norm below 1
+    // Frobenius norm^2 of X is 2 c1; scale until the truncated series is
+    // accurate: |X| <= 1 with 12 or more terms, |X| <= 0.2 with fewer
+    const R lim = TERMS >= 12 ? R(1) : R(0.04);
     R nrm2 = R(2) * c1;
-    while (nrm2 > R(1) && nsq < 30) { nrm2 *= R(0.25); scl *= R(0.5); nsq++; }
+    while (nrm2 > lim && nsq < 30) { nrm2 *= R(0.25); scl *= R(0.5); nsq++; }
     if (nsq) {
 #pragma unroll
         for (int i = 0; i < 3; i++)
