@@ -184,6 +184,50 @@ gl_status gl_step_coupled(gl_ctx* ctx, int32_t n_steps);
 /* Ensemble sums and field checks at the current time (waits). */
 gl_status observables(gl_ctx* ctx, gl_obs* out);
 
+/* ---- Batches of events ------------------------------------------------
+ * Many independent MV events (the paper averages its observables over many
+ * events, Sec. 7.1), possibly of different N, advanced together: one coupled
+ * step of the whole batch is one field launch over the tiles of every event
+ * and one push launch over the particles of every event, captured once in a
+ * CUDA graph and replayed.  All events share the precision, the time step
+ * dtau/a and the re-unitarisation period; they start at tau = 0 together.
+ * The events' particles are sorted by cell when sampled or uploaded; the
+ * batch step does not re-sort them. */
+typedef struct gl_batch gl_batch;
+
+/* Workspace bytes for n_events events; cfgs[n_events], species
+ * [n_events][n_species] (event e's species at species + e * n_species). */
+size_t gl_batch_workspace_bytes(const gl_config* cfgs, const gl_species* species, int32_t n_species,
+                                int32_t n_events);
+
+/* Create a batch in one caller-owned workspace (256-byte aligned); stream must
+ * be a non-default stream (graph capture). */
+gl_status gl_batch_create(const gl_config* cfgs, const gl_species* species, int32_t n_species, int32_t n_events,
+                          void* d_workspace, size_t workspace_bytes, void* stream, gl_batch** out);
+gl_status gl_batch_destroy(gl_batch* batch);
+const char* gl_batch_error_string(const gl_batch* batch);
+
+/* Context of event e (owned by the batch): use it for uploads, downloads and
+ * per-event observables. */
+gl_ctx* gl_batch_event(gl_batch* batch, int32_t e);
+
+/* glasma_init and wong_init of every event. */
+gl_status gl_batch_init(gl_batch* batch);
+
+/* Choose the field tile shape and the push block size from timed trial
+ * launches that do not change the state.  Outputs may be NULL. */
+gl_status gl_batch_autotune(gl_batch* batch, int32_t* tile_shape, int32_t* push_block);
+
+/* Trial timings of the last autotune, ms: field_ms[2] (tile shapes 32x8,
+ * 32x4), push_ms[3] (blocks 128, 256, 512). */
+gl_status gl_batch_tuning(const gl_batch* batch, float* field_ms, float* push_ms);
+
+/* n_steps coupled steps of every event (all events at one common step). */
+gl_status gl_batch_step(gl_batch* batch, int32_t n_steps);
+
+/* observables() of every event into out[n_events] (waits). */
+gl_status gl_batch_observables(gl_batch* batch, gl_obs* out);
+
 /* Largest particle count gl_ensemble_sums_noalloc accepts. */
 #define GL_NOALLOC_MAX_PARTICLES 2097152
 

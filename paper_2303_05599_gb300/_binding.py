@@ -69,6 +69,17 @@ SIGNATURES = {
     "observables": (ctypes.c_int, [_P, ctypes.POINTER(gl_obs)]),
     "gl_ensemble_sums_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_uint32,
                                                 ctypes.c_double, _P, _P]),
+    "gl_batch_workspace_bytes": (ctypes.c_size_t, [_P, _P, ctypes.c_int32, ctypes.c_int32]),
+    "gl_batch_create": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _P,
+                                       ctypes.POINTER(_P)]),
+    "gl_batch_destroy": (ctypes.c_int, [_P]),
+    "gl_batch_error_string": (ctypes.c_char_p, [_P]),
+    "gl_batch_event": (_P, [_P, ctypes.c_int32]),
+    "gl_batch_init": (ctypes.c_int, [_P]),
+    "gl_batch_autotune": (ctypes.c_int, [_P, _P, _P]),
+    "gl_batch_tuning": (ctypes.c_int, [_P, _P, _P]),
+    "gl_batch_step": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "gl_batch_observables": (ctypes.c_int, [_P, _P]),
 }
 
 GL_NOALLOC_MAX_PARTICLES = 2097152
@@ -151,10 +162,21 @@ class Event:
         self.N = workload.N
         self.np = workload.n_particles
 
+    @classmethod
+    def view(cls, ctx, workload):
+        """An Event over a context owned by someone else (a batch)."""
+        ev = cls.__new__(cls)
+        ev.w = workload
+        ev.ctx = ctypes.c_void_p(ctx)
+        ev.N = workload.N
+        ev.np = workload.n_particles
+        ev.owned = False
+        return ev
+
     def close(self):
-        if self.ctx:
+        if self.ctx and getattr(self, "owned", True):
             lib().gl_destroy(self.ctx)
-            self.ctx = ctypes.c_void_p()
+        self.ctx = ctypes.c_void_p()
 
     def __del__(self):
         try:
@@ -205,3 +227,76 @@ class Event:
         _check(lib().gl_download(self.ctx, which, a.ctypes.data_as(ctypes.c_void_p), a.size), self.ctx,
                "gl_download")
         return a
+
+
+class Batch:
+    """Many MV events (same precision and time step, any N) advanced together
+    by one field launch and one push launch per step, replayed from a CUDA
+    graph.  The workspace is one torch uint8 tensor; the stream must not be
+    the default stream."""
+
+    def __init__(self, workloads, stream=None, device=None):
+        import torch
+        self.ws_list = list(workloads)
+        ne = len(self.ws_list)
+        ns = max(len(w.species) for w in self.ws_list)
+        if any(len(w.species) != ns for w in self.ws_list):
+            raise GlasmaError(GL_ERR_ARG, "Batch", "every event needs the same number of species")
+        self.cfgs = (gl_config * ne)(*[make_config(w) for w in self.ws_list])
+        sp = (gl_species * max(1, ne * ns))()
+        for e, w in enumerate(self.ws_list):
+            for k, s_ in enumerate(w.species):
+                sp[e * ns + k] = gl_species(mass_GeV=s_.mass_GeV, tau_form_fm=s_.tau_form_fm, count=s_.count,
+                                            rep=s_.rep, mom_mode=s_.mom_mode, p0_GeV=s_.p0_GeV, p1_GeV=s_.p1_GeV)
+        self.sp = sp
+        nbytes = int(lib().gl_batch_workspace_bytes(self.cfgs, sp, ns, ne))
+        if nbytes == 0:
+            raise GlasmaError(GL_ERR_ARG, "gl_batch_workspace_bytes", "invalid batch")
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        aligned = (self.workspace.data_ptr() + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        self.b = ctypes.c_void_p()
+        st = lib().gl_batch_create(self.cfgs, sp, ns, ne, ctypes.c_void_p(aligned), nbytes,
+                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.b))
+        _check(st, None, "gl_batch_create")
+        self.ne = ne
+        self.events = [Event.view(lib().gl_batch_event(self.b, e), self.ws_list[e]) for e in range(ne)]
+
+    def _chk(self, st, where):
+        if st != GL_OK:
+            msg = lib().gl_batch_error_string(self.b)
+            raise GlasmaError(st, where, msg.decode() if msg else "")
+
+    def init(self):
+        self._chk(lib().gl_batch_init(self.b), "gl_batch_init")
+
+    def autotune(self):
+        t = ctypes.c_int32()
+        p = ctypes.c_int32()
+        self._chk(lib().gl_batch_autotune(self.b, ctypes.byref(t), ctypes.byref(p)), "gl_batch_autotune")
+        f = (ctypes.c_float * 2)()
+        q = (ctypes.c_float * 3)()
+        lib().gl_batch_tuning(self.b, f, q)
+        return {"tile": ("32x8", "32x4")[t.value], "push_block": p.value, "field_ms": list(f), "push_ms": list(q)}
+
+    def step(self, n=1):
+        self._chk(lib().gl_batch_step(self.b, n), "gl_batch_step")
+
+    def observables(self):
+        out = (gl_obs * self.ne)()
+        self._chk(lib().gl_batch_observables(self.b, out), "gl_batch_observables")
+        return list(out)
+
+    def close(self):
+        if self.b:
+            for ev in self.events:
+                ev.ctx = ctypes.c_void_p()
+            lib().gl_batch_destroy(self.b)
+            self.b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

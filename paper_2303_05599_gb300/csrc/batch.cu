@@ -1,0 +1,442 @@
+// Many independent MV events of uneven N advanced together (the paper
+// averages observables over many events, Sec. 7.1).  One coupled step of the
+// whole batch is three launches captured once in a CUDA graph and replayed:
+//   fused leapfrog + site E/B over the tiles of every event,
+//   Wong push over the particles of every event,
+//   a one-thread tick of the device-resident step counter.
+// The kernels read the step index n from device memory, so the captured
+// graph is valid for every step.  Each block finds its event by binary search
+// in a prefix table of tiles or particle chunks.
+//
+// The tile shape of the field kernel and the block size of the push are
+// chosen by gl_batch_autotune from timed trial launches that leave the state
+// unchanged (the field kernel writes only the spare time slice; the push runs
+// on a copy of the particles).
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "fused_body.cuh"
+#include "internal.h"
+#include "push_body.cuh"
+
+namespace gl {
+
+static constexpr int MAX_EVENTS = 1024;
+static constexpr int PUSH_CHUNK = 1024;  // particles per push block
+
+struct EvDesc {
+    void* field[2];
+    void* site;
+    void* parts;
+    int N;
+    int tiles_x;     // for the chosen tile shape
+    int tile_begin;  // first block of this event in the field launch
+    int chunk_begin; // first block of this event in the push launch
+    int64_t np;
+    double mass[GL_MAX_SPECIES];
+    int is_static[GL_MAX_SPECIES];
+    double t_form[GL_MAX_SPECIES];
+    int n_species;
+    int pad;
+};
+
+struct BatchArgs {
+    const EvDesc* ev;
+    int ne;
+    double dt;
+    int reunit_every;
+    const int64_t* clock;
+};
+
+__device__ __forceinline__ int find_event(const EvDesc* ev, int ne, int block, bool tiles) {
+    int lo = 0, hi = ne - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int b = tiles ? ev[mid].tile_begin : ev[mid].chunk_begin;
+        if (b <= block) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) batch_field_kernel(BatchArgs b) {
+    __shared__ int s_e;
+    if (threadIdx.x == 0) s_e = find_event(b.ev, b.ne, blockIdx.x, true);
+    __syncthreads();
+    const EvDesc& d = b.ev[s_e];
+    const int64_t n = *b.clock;
+    const int64_t Vn = (int64_t)d.N * d.N;
+    const int reunit = b.reunit_every > 0 && (n + 1) % b.reunit_every == 0;
+    const StepArgs a = step_args(d.N, d.tiles_x, n, b.dt, reunit);
+    fused_tile<R, TX, TY, true>(carve_fields<R>(d.field[n & 1], Vn), carve_fields<R>(d.field[(n + 1) & 1], Vn),
+                                (typename Prec<R>::V*)d.site, a, blockIdx.x - d.tile_begin);
+}
+
+template <typename R>
+__global__ void batch_push_kernel(BatchArgs b) {
+    __shared__ int s_e;
+    if (threadIdx.x == 0) s_e = find_event(b.ev, b.ne, blockIdx.x, false);
+    __syncthreads();
+    const EvDesc& d = b.ev[s_e];
+    const int64_t n = *b.clock;
+    const double t = n * b.dt;
+    uint32_t active = 0;
+    SpeciesArgs<R> sa;
+    for (int k = 0; k < GL_MAX_SPECIES; k++) {
+        if (k < d.n_species && t >= d.t_form[k]) active |= 1u << k;
+        sa.mass[k] = (R)(d.is_static[k] ? 0.0 : d.mass[k]);
+        sa.is_static[k] = d.is_static[k];
+    }
+    const int64_t Vn = (int64_t)d.N * d.N;
+    const Parts<R> P = carve_parts<R>(d.parts, d.np);
+    const Fields<R> bn1 = carve_fields<R>(d.field[(n + 1) & 1], Vn);
+    const int64_t base = (int64_t)(blockIdx.x - d.chunk_begin) * PUSH_CHUNK;
+    const int64_t end = base + PUSH_CHUNK < d.np ? base + PUSH_CHUNK : d.np;
+    for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x)
+        push_one<R>((const typename Prec<R>::V*)d.site, bn1, P, i, d.N, (R)t, (R)b.dt, (R)(t > 0 ? b.dt / t : 0.0),
+                    active, sa);
+}
+
+__global__ void tick_kernel(int64_t* clock) { *clock += 1; }
+
+// tile shapes the autotuner chooses from
+enum { TILE_32x8 = 0, TILE_32x4 = 1, N_TILES = 2 };
+static const int TILE_DIMS[N_TILES][2] = {{32, 8}, {32, 4}};
+static const int PUSH_BLOCKS[3] = {128, 256, 512};
+
+template <typename R, int TX, int TY>
+static void set_smem_attr() {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !done[dev]) {
+        cudaFuncSetAttribute(batch_field_kernel<R, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Tile<R, TX, TY>::bytes);
+        done[dev] = true;
+    }
+}
+
+template <typename R>
+static void launch_batch_field(int tile, int blocks, const BatchArgs& b, cudaStream_t st) {
+    if (tile == TILE_32x8) {
+        set_smem_attr<R, 32, 8>();
+        batch_field_kernel<R, 32, 8><<<blocks, 256, Tile<R, 32, 8>::bytes, st>>>(b);
+    } else {
+        set_smem_attr<R, 32, 4>();
+        batch_field_kernel<R, 32, 4><<<blocks, 128, Tile<R, 32, 4>::bytes, st>>>(b);
+    }
+}
+
+}  // namespace gl
+
+using namespace gl;
+
+struct gl_batch {
+    int ne;
+    int prec;
+    double dt;
+    int reunit_every;
+    cudaStream_t stream;
+    gl_ctx** ev;
+    EvDesc* h_desc;
+    EvDesc* d_desc;
+    int64_t* d_clock;
+    int tile;         // autotuned tile shape
+    int push_block;   // autotuned push block size
+    int field_blocks;
+    int push_blocks;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    int graph_tile, graph_push_block;
+    float tune_ms[N_TILES][3];
+    char err[256];
+};
+
+// context internals needed by the batch (defined in capi.cu)
+namespace gl {
+struct CtxView {
+    void* field[2];
+    void* site;
+    void* parts;
+    int N, prec, cur;
+    int64_t step, pstep, np;
+    double dt;
+    double mass[GL_MAX_SPECIES];
+    int is_static[GL_MAX_SPECIES];
+    double t_form[GL_MAX_SPECIES];
+    int ns;
+    int reunit_count;
+    void* parts_alt;
+};
+void ctx_view(const gl_ctx* c, CtxView* v);
+void ctx_advance(gl_ctx* c, int64_t steps);
+size_t ctx_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t ns);
+}  // namespace gl
+
+static size_t a256b(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static gl_status bfail(gl_batch* b, gl_status s, const char* m) {
+    if (b) snprintf(b->err, sizeof b->err, "%s", m);
+    return s;
+}
+
+extern "C" {
+
+size_t gl_batch_workspace_bytes(const gl_config* cfgs, const gl_species* species, int32_t n_species,
+                                int32_t n_events) {
+    if (!cfgs || n_events < 1 || n_events > MAX_EVENTS) return 0;
+    size_t o = a256b(sizeof(EvDesc) * n_events) + 256;
+    for (int e = 0; e < n_events; e++) {
+        const size_t w = ctx_workspace_bytes(&cfgs[e], species ? species + (size_t)e * n_species : nullptr, n_species);
+        if (!w) return 0;
+        o += a256b(w);
+    }
+    return o;
+}
+
+gl_status gl_batch_create(const gl_config* cfgs, const gl_species* species, int32_t n_species, int32_t n_events,
+                          void* d_workspace, size_t bytes, void* stream, gl_batch** out) {
+    if (!out) return GL_ERR_ARG;
+    *out = nullptr;
+    const size_t need = gl_batch_workspace_bytes(cfgs, species, n_species, n_events);
+    if (!need) return GL_ERR_ARG;
+    if (bytes < need) return GL_ERR_SIZE;
+    if (!d_workspace || ((uintptr_t)d_workspace & 255)) return GL_ERR_ARG;
+    for (int e = 1; e < n_events; e++)
+        if (cfgs[e].precision != cfgs[0].precision || cfgs[e].dtau_over_a != cfgs[0].dtau_over_a ||
+            cfgs[e].reunit_every != cfgs[0].reunit_every)
+            return GL_ERR_ARG;  // one precision, time step and re-unitarisation period per batch
+    gl_batch* b = new (std::nothrow) gl_batch;
+    if (!b) return GL_ERR_ARG;
+    memset(b, 0, sizeof *b);
+    b->ne = n_events;
+    b->prec = cfgs[0].precision;
+    b->dt = cfgs[0].dtau_over_a;
+    b->reunit_every = cfgs[0].precision == GL_FP32_2ROW ? cfgs[0].reunit_every : 0;
+    b->stream = (cudaStream_t)stream;
+    b->ev = new (std::nothrow) gl_ctx*[n_events]();
+    b->h_desc = new (std::nothrow) EvDesc[n_events]();
+    char* ws = (char*)d_workspace;
+    b->d_desc = (EvDesc*)ws;
+    b->d_clock = (int64_t*)(ws + a256b(sizeof(EvDesc) * n_events));
+    size_t o = a256b(sizeof(EvDesc) * n_events) + 256;
+    for (int e = 0; e < n_events; e++) {
+        const gl_species* sp = species ? species + (size_t)e * n_species : nullptr;
+        const size_t w = ctx_workspace_bytes(&cfgs[e], sp, n_species);
+        gl_status s = gl_create(&cfgs[e], sp, n_species, ws + o, w, stream, &b->ev[e]);
+        if (s != GL_OK) {
+            for (int k = 0; k < e; k++) gl_destroy(b->ev[k]);
+            delete[] b->ev;
+            delete[] b->h_desc;
+            delete b;
+            return s;
+        }
+        o += a256b(w);
+    }
+    b->tile = b->prec == GL_FP64 ? TILE_32x4 : TILE_32x8;
+    b->push_block = 128;
+    b->graph_tile = -1;
+    *out = b;
+    return GL_OK;
+}
+
+gl_status gl_batch_destroy(gl_batch* b) {
+    if (!b) return GL_ERR_ARG;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (int e = 0; e < b->ne; e++) gl_destroy(b->ev[e]);
+    delete[] b->ev;
+    delete[] b->h_desc;
+    delete b;
+    return GL_OK;
+}
+
+gl_ctx* gl_batch_event(gl_batch* b, int32_t e) { return b && e >= 0 && e < b->ne ? b->ev[e] : nullptr; }
+
+const char* gl_batch_error_string(const gl_batch* b) { return b ? b->err : ""; }
+
+gl_status gl_batch_init(gl_batch* b) {
+    if (!b) return GL_ERR_ARG;
+    for (int e = 0; e < b->ne; e++) {
+        gl_status s = glasma_init(b->ev[e]);
+        if (s == GL_OK) s = wong_init(b->ev[e]);
+        if (s != GL_OK) {
+            char m[300];
+            snprintf(m, sizeof m, "event %d: %s", e, gl_error_string(b->ev[e]));
+            return bfail(b, s, m);
+        }
+    }
+    return GL_OK;
+}
+
+// refresh the device descriptors from the contexts; all events must be at the
+// same step with their particles at that step
+static gl_status sync_desc(gl_batch* b) {
+    int tb = 0, cb = 0;
+    const int TX = TILE_DIMS[b->tile][0], TY = TILE_DIMS[b->tile][1];
+    int64_t step0 = -1;
+    for (int e = 0; e < b->ne; e++) {
+        CtxView v;
+        ctx_view(b->ev[e], &v);
+        if (step0 < 0) step0 = v.step;
+        if (v.step != step0 || v.pstep != v.step || v.cur != (int)(v.step & 1))
+            return bfail(b, GL_ERR_STATE, "batch events must be at one common step with their particles");
+        EvDesc& d = b->h_desc[e];
+        memset(&d, 0, sizeof d);
+        d.field[0] = v.field[0];
+        d.field[1] = v.field[1];
+        d.site = v.site;
+        d.parts = v.parts;
+        d.N = v.N;
+        d.tiles_x = (v.N + TX - 1) / TX;
+        d.tile_begin = tb;
+        tb += d.tiles_x * ((v.N + TY - 1) / TY);
+        d.chunk_begin = cb;
+        cb += (int)((v.np + PUSH_CHUNK - 1) / PUSH_CHUNK);
+        d.np = v.np;
+        d.n_species = v.ns;
+        for (int k = 0; k < GL_MAX_SPECIES; k++) {
+            d.mass[k] = v.mass[k];
+            d.is_static[k] = v.is_static[k];
+            d.t_form[k] = v.t_form[k];
+        }
+    }
+    b->field_blocks = tb;
+    b->push_blocks = cb > 0 ? cb : 1;
+    cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(EvDesc) * b->ne, cudaMemcpyHostToDevice, b->stream);
+    cudaMemcpyAsync(b->d_clock, &step0, sizeof step0, cudaMemcpyHostToDevice, b->stream);
+    cudaStreamSynchronize(b->stream);
+    return cudaGetLastError() == cudaSuccess ? GL_OK : bfail(b, GL_ERR_CUDA, "descriptor upload failed");
+}
+
+static void enqueue_step(gl_batch* b, int tile, int push_block, bool tick) {
+    BatchArgs a{b->d_desc, b->ne, b->dt, b->reunit_every, b->d_clock};
+    if (b->prec == GL_FP64) {
+        launch_batch_field<double>(tile, b->field_blocks, a, b->stream);
+        batch_push_kernel<double><<<b->push_blocks, push_block, 0, b->stream>>>(a);
+    } else {
+        launch_batch_field<float>(tile, b->field_blocks, a, b->stream);
+        batch_push_kernel<float><<<b->push_blocks, push_block, 0, b->stream>>>(a);
+    }
+    if (tick) tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock);
+}
+
+gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_out) {
+    if (!b) return GL_ERR_ARG;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_f = 1e30f, best_p = 1e30f;
+    int bt = b->tile, bp = b->push_block;
+    // field kernel: trial launches write only the spare time slice and the
+    // site fields, which the next real step overwrites
+    for (int tile = 0; tile < N_TILES; tile++) {
+        if (b->prec == GL_FP64 && tile == TILE_32x8) continue;  // FP64 tile must fit shared memory
+        b->tile = tile;
+        if (gl_status s = sync_desc(b)) return s;
+        BatchArgs a{b->d_desc, b->ne, b->dt, 0, b->d_clock};
+        float ms = 0;
+        for (int rep = 0; rep < 4; rep++) {
+            cudaEventRecord(e0, b->stream);
+            if (b->prec == GL_FP64) launch_batch_field<double>(tile, b->field_blocks, a, b->stream);
+            else launch_batch_field<float>(tile, b->field_blocks, a, b->stream);
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float m;
+            cudaEventElapsedTime(&m, e0, e1);
+            if (rep > 0) ms += m;
+        }
+        b->tune_ms[tile][0] = ms / 3;
+        if (ms < best_f) { best_f = ms; bt = tile; }
+    }
+    b->tile = bt;
+    if (gl_status s = sync_desc(b)) return s;
+    // push: trial launches on a copy of the particles (the contexts' spare buffers)
+    EvDesc* saved = new EvDesc[b->ne];
+    memcpy(saved, b->h_desc, sizeof(EvDesc) * b->ne);
+    bool have_copy = true;
+    for (int e = 0; e < b->ne; e++) {
+        CtxView v;
+        ctx_view(b->ev[e], &v);
+        if (!v.parts_alt) { have_copy = false; break; }
+        cudaMemcpyAsync(v.parts_alt, v.parts, particle_bytes(b->prec, v.np), cudaMemcpyDeviceToDevice, b->stream);
+        b->h_desc[e].parts = v.parts_alt;
+    }
+    if (have_copy) {
+        cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(EvDesc) * b->ne, cudaMemcpyHostToDevice, b->stream);
+        BatchArgs a{b->d_desc, b->ne, b->dt, 0, b->d_clock};
+        for (int k = 0; k < 3; k++) {
+            float ms = 0;
+            for (int rep = 0; rep < 4; rep++) {
+                cudaEventRecord(e0, b->stream);
+                if (b->prec == GL_FP64) batch_push_kernel<double><<<b->push_blocks, PUSH_BLOCKS[k], 0, b->stream>>>(a);
+                else batch_push_kernel<float><<<b->push_blocks, PUSH_BLOCKS[k], 0, b->stream>>>(a);
+                cudaEventRecord(e1, b->stream);
+                cudaEventSynchronize(e1);
+                float m;
+                cudaEventElapsedTime(&m, e0, e1);
+                if (rep > 0) ms += m;
+            }
+            b->tune_ms[0][k] = b->tune_ms[0][k];
+            b->tune_ms[1][k] = ms / 3;
+            if (ms < best_p) { best_p = ms; bp = PUSH_BLOCKS[k]; }
+        }
+    }
+    memcpy(b->h_desc, saved, sizeof(EvDesc) * b->ne);
+    delete[] saved;
+    b->push_block = bp;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (gl_status s = sync_desc(b)) return s;
+    if (tile_out) *tile_out = b->tile;
+    if (push_block_out) *push_block_out = b->push_block;
+    return cudaGetLastError() == cudaSuccess ? GL_OK : bfail(b, GL_ERR_CUDA, "autotune launch failed");
+}
+
+gl_status gl_batch_step(gl_batch* b, int32_t n_steps) {
+    if (!b || n_steps < 0) return GL_ERR_ARG;
+    if (n_steps == 0) return GL_OK;
+    if (gl_status s = sync_desc(b)) return s;
+    // (re)capture the one-step graph when the launch shapes changed
+    if (!b->exec || b->graph_tile != b->tile || b->graph_push_block != b->push_block) {
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+        if (b->prec == GL_FP64) set_smem_attr<double, 32, 4>();
+        else { set_smem_attr<float, 32, 8>(); set_smem_attr<float, 32, 4>(); }
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return bfail(b, GL_ERR_CUDA, "stream capture could not start (the default stream cannot be captured)");
+        enqueue_step(b, b->tile, b->push_block, true);
+        if (cudaStreamEndCapture(b->stream, &b->graph) != cudaSuccess ||
+            cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(b, GL_ERR_CUDA, "graph capture failed");
+        }
+        b->graph_tile = b->tile;
+        b->graph_push_block = b->push_block;
+    }
+    for (int k = 0; k < n_steps; k++) cudaGraphLaunch(b->exec, b->stream);
+    if (cudaGetLastError() != cudaSuccess) return bfail(b, GL_ERR_CUDA, "graph launch failed");
+    for (int e = 0; e < b->ne; e++) ctx_advance(b->ev[e], n_steps);
+    return GL_OK;
+}
+
+gl_status gl_batch_observables(gl_batch* b, gl_obs* out) {
+    if (!b || !out) return GL_ERR_ARG;
+    for (int e = 0; e < b->ne; e++)
+        if (gl_status s = observables(b->ev[e], &out[e])) return s;
+    return GL_OK;
+}
+
+gl_status gl_batch_tuning(const gl_batch* b, float* field_ms, float* push_ms) {
+    if (!b) return GL_ERR_ARG;
+    for (int k = 0; k < N_TILES; k++)
+        if (field_ms) field_ms[k] = b->tune_ms[k][0];
+    for (int k = 0; k < 3; k++)
+        if (push_ms) push_ms[k] = b->tune_ms[1][k];
+    return GL_OK;
+}
+
+}  // extern "C"

@@ -137,6 +137,57 @@ static void q0_vectors(double q0[2][8]) {
     q0[1][0] = sqrt(24.0);
 }
 
+namespace gl {
+// read-only view of a context for the batch (batch.cu)
+struct CtxView {
+    void* field[2];
+    void* site;
+    void* parts;
+    int N, prec, cur;
+    int64_t step, pstep, np;
+    double dt;
+    double mass[GL_MAX_SPECIES];
+    int is_static[GL_MAX_SPECIES];
+    double t_form[GL_MAX_SPECIES];
+    int ns;
+    int reunit_count;
+    void* parts_alt;
+};
+void ctx_view(const gl_ctx* c, CtxView* v) {
+    v->field[0] = c->field[0];
+    v->field[1] = c->field[1];
+    v->site = c->site;
+    v->parts = c->parts;
+    v->N = c->N;
+    v->prec = c->prec;
+    v->cur = c->cur;
+    v->step = c->step;
+    v->pstep = c->pstep;
+    v->np = c->np;
+    v->dt = c->dt;
+    for (int k = 0; k < GL_MAX_SPECIES; k++) {
+        v->mass[k] = c->spp.mass[k];
+        v->is_static[k] = c->spp.is_static[k];
+        v->t_form[k] = c->t_form[k];
+    }
+    v->ns = c->ns;
+    v->reunit_count = c->reunit_count;
+    v->parts_alt = c->parts_alt;
+}
+// record that the batch advanced this event by `steps` coupled steps
+void ctx_advance(gl_ctx* c, int64_t steps) {
+    c->step += steps;
+    c->pstep += steps;
+    c->cur = (int)(c->step & 1);
+    c->site_step = c->pstep - 1;
+    if (c->prec == GL_FP32_2ROW && c->cfg.reunit_every > 0)
+        c->reunit_count = (int)(c->step % c->cfg.reunit_every);
+}
+size_t ctx_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t ns) {
+    return gl_workspace_bytes(cfg, sp, ns);
+}
+}  // namespace gl
+
 extern "C" {
 
 size_t gl_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t ns) {
@@ -324,8 +375,8 @@ static void one_field_step(gl_ctx* c, bool site) {
         if (++c->reunit_count >= c->cfg.reunit_every) { reunit = 1; c->reunit_count = 0; }
     }
     site = site && c->pstep == c->step;
-    launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], site ? c->site : nullptr, c->N,
-                      c->step * c->dt, c->dt, reunit, c->stream);
+    launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], site ? c->site : nullptr, c->N, c->step, c->dt,
+                      reunit, c->stream);
     if (site) c->site_step = c->pstep;
     c->cur = 1 - c->cur;
     c->step++;

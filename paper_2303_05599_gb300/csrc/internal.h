@@ -16,7 +16,7 @@ struct SpeciesParams {
 
 // field step n -> n+1 on buffers in/out (FP64 or FP32 two-row layout); when
 // site is not null the same kernel also writes the site E, B at t_n
-void launch_fused_step(int prec, void* in, void* out, void* site, int N, double t, double dt, int reunit,
+void launch_fused_step(int prec, void* in, void* out, void* site, int N, int64_t n, double dt, int reunit,
                        cudaStream_t st);
 // site E, B at t_n from buffer n (U, phi, e(n-1/2), pi(n-1/2)) and buffer n+1 (e, pi at n+1/2)
 void launch_site_fields(int prec, const void* bn, const void* bn1, void* site, int N, double t, cudaStream_t st);

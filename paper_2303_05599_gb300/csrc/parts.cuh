@@ -79,13 +79,13 @@ struct Parts<float> {
     }
 };
 
-inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+__host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 template <typename R>
-inline Parts<R> carve_parts(void* base, int64_t np);
+__host__ __device__ inline Parts<R> carve_parts(void* base, int64_t np);
 
 template <>
-inline Parts<double> carve_parts<double>(void* base, int64_t np) {
+__host__ __device__ inline Parts<double> carve_parts<double>(void* base, int64_t np) {
     Parts<double> p;
     char* c = (char*)base;
     p.np = np;
@@ -100,7 +100,7 @@ inline Parts<double> carve_parts<double>(void* base, int64_t np) {
 }
 
 template <>
-inline Parts<float> carve_parts<float>(void* base, int64_t np) {
+__host__ __device__ inline Parts<float> carve_parts<float>(void* base, int64_t np) {
     Parts<float> p;
     char* c = (char*)base;
     p.np = np;

@@ -1,0 +1,94 @@
+// Particle push body shared by the single-event and batched kernels.
+#pragma once
+#include "parts.cuh"
+
+namespace gl {
+
+template <typename R>
+struct SpeciesArgs {
+    R mass[GL_MAX_SPECIES];
+    int is_static[GL_MAX_SPECIES];
+};
+
+template <typename R>
+__device__ __forceinline__ R floor_r(R v);
+template <>
+__device__ __forceinline__ double floor_r<double>(double v) { return floor(v); }
+template <>
+__device__ __forceinline__ float floor_r<float>(float v) { return floorf(v); }
+
+template <typename R>
+__device__ __forceinline__ R fmod_r(R a, R b);
+template <>
+__device__ __forceinline__ double fmod_r<double>(double a, double b) { return fmod(a, b); }
+template <>
+__device__ __forceinline__ float fmod_r<float>(float a, float b) { return fmodf(a, b); }
+
+// Euler + CPIC update of particle i (Sec. 3.1 and 3.2); site: site fields at
+// t_n, bn1: links and scalar at t_{n+1}
+template <typename R>
+__device__ __forceinline__ void push_one(const typename Prec<R>::V* __restrict__ site, const Fields<R>& bn1,
+                                         const Parts<R>& P, int64_t i, int N, R t, R dt, R dt_over_t,
+                                         uint32_t active, const SpeciesArgs<R>& sa) {
+    constexpr int AP = Prec<R>::AP;
+    const int64_t Vn = (int64_t)N * N;
+    const int s = P.sp[i];
+    if (!((active >> s) & 1u)) return;
+    PState<R> p = P.load(i);
+    const int ixu = (int)floor_r<R>(p.x + R(0.5)), iyu = (int)floor_r<R>(p.y + R(0.5));
+    // wrap keeps every index inside the lattice even for a non-finite position
+    // (float-to-int conversion maps NaN to 0 and saturates out-of-range values)
+    const int ix = wrapi(ixu, N), iy = wrapi(iyu, N);
+    const int64_t cell = (int64_t)iy * N + ix;
+    const R qEx = a_dot(p.q, load_alg(site, cell, Vn));
+    const R qEy = a_dot(p.q, load_alg(site + (size_t)1 * AP * Vn, cell, Vn));
+    const R qEe = a_dot(p.q, load_alg(site + (size_t)2 * AP * Vn, cell, Vn));
+    if (sa.is_static[s]) {
+        // infinitely massive: no motion and no colour rotation (temporal gauge)
+        p.px += dt * qEx;
+        p.py += dt * qEy;
+        p.Pe += dt * qEe;
+        P.store_momenta(i, p);
+        return;
+    }
+    const R qBx = a_dot(p.q, load_alg(site + (size_t)3 * AP * Vn, cell, Vn));
+    const R qBy = a_dot(p.q, load_alg(site + (size_t)4 * AP * Vn, cell, Vn));
+    const R qBe = a_dot(p.q, load_alg(site + (size_t)5 * AP * Vn, cell, Vn));
+    const R m = sa.mass[s];
+    const R w = t > R(0) ? p.Pe / t : R(0);  // tau p^eta
+    const R ptau = sqrt(p.px * p.px + p.py * p.py + w * w + m * m);
+    const R inv_pt = ptau > R(0) ? R(1) / ptau : R(0);
+    const R vx = p.px * inv_pt, vy = p.py * inv_pt, vw = w * inv_pt;
+    // Wong's equations in Milne coordinates (Sec. 3.1), forward Euler
+    const R dpx = qEx + qBe * vy - qBy * vw;
+    const R dpy = qEy - qBe * vx + qBx * vw;
+    const R dPe = t * (qEe - qBx * vy + qBy * vx);
+    const R deta = dt_over_t * vw;
+    R xn = p.x + dt * vx, yn = p.y + dt * vy;
+    p.eta += deta;
+    p.px += dt * dpx;
+    p.py += dt * dpy;
+    p.Pe += dt * dPe;
+    const int jxu = (int)floor_r<R>(xn + R(0.5)), jyu = (int)floor_r<R>(yn + R(0.5));
+    xn = fmod_r<R>(xn, (R)N);
+    if (xn < R(0)) xn += (R)N;
+    yn = fmod_r<R>(yn, (R)N);
+    if (yn < R(0)) yn += (R)N;
+    p.x = xn;
+    p.y = yn;
+    // CPIC: rotate with the crossed links at t_{n+1}, x first, then y
+    const int dxc = jxu - ixu, dyc = jyu - iyu;
+    const int jx = wrapi(jxu, N), jy = wrapi(jyu, N);
+    if (dxc == 1) p.q = conj_dn(load_link(bn1.U, 0, cell, Vn), p.q);
+    else if (dxc == -1) p.q = conj_up(load_link(bn1.U, 0, (int64_t)iy * N + jx, Vn), p.q);
+    if (dyc == 1) p.q = conj_dn(load_link(bn1.U, 1, (int64_t)iy * N + jx, Vn), p.q);
+    else if (dyc == -1) p.q = conj_up(load_link(bn1.U, 1, (int64_t)jy * N + jx, Vn), p.q);
+    // rapidity Wilson line at the new cell: Q <- e^{-i deta phi} Q e^{+i deta phi}
+    if (deta != R(0)) {
+        const A8<R> ph = load_alg(bn1.phi, (int64_t)jy * N + jx, Vn);
+        p.q = conj_up(exp_i_alg<R, (sizeof(R) == 8 ? 20 : 6)>(ph, -deta), p.q);
+    }
+    P.store(i, p);
+}
+
+}  // namespace gl

@@ -1,307 +1,16 @@
-// Fused Glasma leapfrog step and site E/B interpolation (Sec. 2.1 and 3.2 of
-// arXiv:2303.05599) on shared-memory tiles.
-//
-// One CTA owns a TX x TY tile of sites (TX = 32: one warp per tile row).  Per
-// step it computes, from U(n), phi(n), e(n-1/2), pi(n-1/2):
-//   the momenta e(n+1/2), pi(n+1/2), the links U(n+1) and the scalar phi(n+1),
-//   and (SITE) the site fields E, B at t_n that the particle push gathers.
-// Every cell plaquette is formed once per tile and shared.  With
-//   A(c)  = components of i[P(c)]_ah,  P(c) = Ux(c) Uy(c+x) Ux(c+y)^+ Uy(c)^+,
-//   Dn(s) = Uy(s-y)^+ A(s-y) Uy(s-y),   Lf(s) = Ux(s-x)^+ A(s-x) Ux(s-x),
-// the plaquette forces and the clover are
-//   F_x = t (A - Dn),  F_y = t (Lf - A),
-//   B_eta = (A + Lf + Dn + Uy(s-y)^+ Lf(s-y) Uy(s-y)) / 4.
-// E_i(s) needs e_i(n+1/2) at s - i, so the tile also advances the momenta of
-// one halo column (x0 - 1) and one halo row (y0 - 1).
-//
-// The tile's inputs are copied to shared memory with cp.async in the storage
-// layout of global memory (16-byte vectors; FP32 links as two rows, the third
-// rebuilt when a link is read).  Regions, in tile coordinates:
-//   links, phi:      x in [-2, TX],   y in [-2, TY]    (LW x LH)
-//   plaquettes A:    x in [-2, TX-1], y in [-2, TY-1]  (AW x AH)
-//   momenta, Lf:     x in [-1, TX-1], y in [-1, TY-1]  (EW x EH)
-//   pi(n-1/2):       the tile
-#include "internal.h"
-#include "layout.cuh"
+// Single-event launch of the fused leapfrog + site E/B kernel (fused_body.cuh).
+#include "fused_body.cuh"
 
 namespace gl {
-
-template <typename R>
-struct ExpN;
-template <>
-struct ExpN<double> { static constexpr int n = 20; };
-template <>
-struct ExpN<float> { static constexpr int n = 12; };
-
-template <typename R, int TX, int TY>
-struct Tile {
-    using V = typename Prec<R>::V;
-    static constexpr int LP = Prec<R>::LP, AP = Prec<R>::AP;
-    static constexpr int LW = TX + 3, LH = TY + 3, LN = LW * LH;
-    static constexpr int AW = TX + 2, AH = TY + 2, AN = AW * AH;
-    static constexpr int EW = TX + 1, EH = TY + 1, EN = EW * EH;
-    static constexpr int NT = TX * TY;
-    // vectors: links 2 LP LN, phi AP LN, A AP AN, e sums 2 AP EN, Lf AP EN, pi AP NT
-    static constexpr size_t vecs = (size_t)2 * LP * LN + (size_t)AP * LN + (size_t)AP * AN + (size_t)3 * AP * EN +
-                                   (size_t)AP * NT;
-    static constexpr size_t bytes = vecs * sizeof(V);
-};
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-// link (d) of shared-memory site li, planes of LN vectors
-__device__ __forceinline__ M3<double> s_link(const double2* sU, int d, int li, int LN) {
-    const double2* b = sU + (size_t)d * 9 * LN + li;
-    M3<double> m;
-#pragma unroll
-    for (int k = 0; k < 9; k++) {
-        const double2 v = b[k * LN];
-        m.re[k / 3][k % 3] = v.x;
-        m.im[k / 3][k % 3] = v.y;
-    }
-    return m;
-}
-__device__ __forceinline__ M3<float> s_link(const float4* sU, int d, int li, int LN) {
-    const float4* b = sU + (size_t)d * 3 * LN + li;
-    const float4 a = b[0], c = b[LN], e = b[2 * LN];
-    M3<float> m;
-    m.re[0][0] = a.x; m.im[0][0] = a.y; m.re[0][1] = a.z; m.im[0][1] = a.w;
-    m.re[0][2] = c.x; m.im[0][2] = c.y; m.re[1][0] = c.z; m.im[1][0] = c.w;
-    m.re[1][1] = e.x; m.im[1][1] = e.y; m.re[1][2] = e.z; m.im[1][2] = e.w;
-    rebuild_row2(m);
-    return m;
-}
-
-__device__ __forceinline__ A8<double> s_alg(const double2* s, int i, int n) {
-    A8<double> x;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const double2 v = s[k * n + i];
-        x.v[2 * k] = v.x;
-        x.v[2 * k + 1] = v.y;
-    }
-    return x;
-}
-__device__ __forceinline__ A8<float> s_alg(const float4* s, int i, int n) {
-    const float4 a = s[i], b = s[n + i];
-    A8<float> x;
-    x.v[0] = a.x; x.v[1] = a.y; x.v[2] = a.z; x.v[3] = a.w;
-    x.v[4] = b.x; x.v[5] = b.y; x.v[6] = b.z; x.v[7] = b.w;
-    return x;
-}
-__device__ __forceinline__ void s_alg_put(double2* s, int i, int n, const A8<double>& x) {
-#pragma unroll
-    for (int k = 0; k < 4; k++) s[k * n + i] = make_double2(x.v[2 * k], x.v[2 * k + 1]);
-}
-__device__ __forceinline__ void s_alg_put(float4* s, int i, int n, const A8<float>& x) {
-    s[i] = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
-    s[n + i] = make_float4(x.v[4], x.v[5], x.v[6], x.v[7]);
-}
-
-// FP64 Gram-Schmidt of rows 0 and 1 (FP32 links are stored as two rows)
-__device__ __forceinline__ void reunit(M3<float>& u) {
-    double r0r[3], r0i[3], r1r[3], r1i[3];
-#pragma unroll
-    for (int j = 0; j < 3; j++) {
-        r0r[j] = u.re[0][j]; r0i[j] = u.im[0][j];
-        r1r[j] = u.re[1][j]; r1i[j] = u.im[1][j];
-    }
-    double n0 = 0;
-#pragma unroll
-    for (int j = 0; j < 3; j++) n0 += r0r[j] * r0r[j] + r0i[j] * r0i[j];
-    n0 = 1.0 / sqrt(n0);
-#pragma unroll
-    for (int j = 0; j < 3; j++) { r0r[j] *= n0; r0i[j] *= n0; }
-    double cr = 0, ci = 0;
-#pragma unroll
-    for (int j = 0; j < 3; j++) {
-        cr += r0r[j] * r1r[j] + r0i[j] * r1i[j];
-        ci += r0r[j] * r1i[j] - r0i[j] * r1r[j];
-    }
-#pragma unroll
-    for (int j = 0; j < 3; j++) {
-        r1r[j] -= cr * r0r[j] - ci * r0i[j];
-        r1i[j] -= cr * r0i[j] + ci * r0r[j];
-    }
-    double n1 = 0;
-#pragma unroll
-    for (int j = 0; j < 3; j++) n1 += r1r[j] * r1r[j] + r1i[j] * r1i[j];
-    n1 = 1.0 / sqrt(n1);
-#pragma unroll
-    for (int j = 0; j < 3; j++) {
-        u.re[0][j] = (float)r0r[j]; u.im[0][j] = (float)r0i[j];
-        u.re[1][j] = (float)(r1r[j] * n1); u.im[1][j] = (float)(r1i[j] * n1);
-    }
-}
-__device__ __forceinline__ void reunit(M3<double>&) {}
-
-struct StepArgs {
-    int N;
-    int tiles_x;
-    double t, dt, inv_t, dt_over_th, dt_th;
-    int reunit;
-};
 
 template <typename R, int TX, int TY, bool SITE>
 __global__ void __launch_bounds__(TX * TY) fused_step_kernel(Fields<R> in, Fields<R> out,
                                                              typename Prec<R>::V* site, StepArgs a) {
-    using T = Tile<R, TX, TY>;
-    using Vec = typename Prec<R>::V;
-    constexpr int LP = T::LP, AP = T::AP;
-    constexpr int LW = T::LW, LN = T::LN, AW = T::AW, AN = T::AN, EW = T::EW, EN = T::EN, NT = T::NT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Vec* sU = (Vec*)smem_raw;          // [2][LP][LN]
-    Vec* sPhi = sU + 2 * LP * LN;      // [AP][LN]
-    Vec* sA = sPhi + AP * LN;          // [AP][AN]
-    Vec* sEs = sA + AP * AN;           // [2][AP][EN]: e(n-1/2), then e(n-1/2) + e(n+1/2)
-    Vec* sLf = sEs + 2 * AP * EN;      // [AP][EN]
-    Vec* sPi = sLf + AP * EN;          // [AP][NT]
-
-    const int N = a.N;
-    const int64_t Vn = (int64_t)N * N;
-    const int x0 = (blockIdx.x % a.tiles_x) * TX, y0 = (blockIdx.x / a.tiles_x) * TY;
-    const int tid = threadIdx.x;
-    const R t = (R)a.t, dt = (R)a.dt, inv_t = (R)a.inv_t;
-
-    // ---- phase 1: asynchronous copies of the tile's inputs
-    for (int i = tid; i < LN; i += NT) {
-        const int gx = wrapi(x0 + i % LW - 2, N), gy = wrapi(y0 + i / LW - 2, N);
-        const int64_t g = (int64_t)gy * N + gx;
-#pragma unroll
-        for (int k = 0; k < 2 * LP; k++) cp_async16(sU + (size_t)k * LN + i, in.U + (size_t)k * Vn + g);
-#pragma unroll
-        for (int k = 0; k < AP; k++) cp_async16(sPhi + (size_t)k * LN + i, in.phi + (size_t)k * Vn + g);
-    }
-    for (int i = tid; i < EN; i += NT) {
-        const int gx = wrapi(x0 + i % EW - 1, N), gy = wrapi(y0 + i / EW - 1, N);
-        const int64_t g = (int64_t)gy * N + gx;
-#pragma unroll
-        for (int k = 0; k < 2 * AP; k++) cp_async16(sEs + (size_t)k * EN + i, in.e + (size_t)k * Vn + g);
-    }
-    {
-        const int gx = x0 + tid % TX, gy = y0 + tid / TX;
-        const int64_t g = (int64_t)wrapi(gy, N) * N + wrapi(gx, N);
-#pragma unroll
-        for (int k = 0; k < AP; k++) cp_async16(sPi + (size_t)k * NT + tid, in.pi + (size_t)k * Vn + g);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-
-    // ---- phase 2: plaquettes of the tile cells and their halo
-    for (int i = tid; i < AN; i += NT) {
-        const int l = (i / AW) * LW + (i % AW);  // cell (ax, ay) = (i % AW - 2, i / AW - 2)
-        const M3<R> C = mul(s_link(sU, 0, l, LN), s_link(sU, 1, l + 1, LN));
-        const M3<R> P = mul_nd(mul_nd(C, s_link(sU, 0, l + LW, LN)), s_link(sU, 1, l, LN));
-        s_alg_put(sA, i, AN, iah_to_alg(P));
-    }
-    __syncthreads();
-
-    // ---- phase 3: momenta at n+1/2 on the tile and the halo column/row.
-    // Indices 0..NT-1 are the tile sites in thread order (kept in registers
-    // for phase 4); the halo follows.
-    A8<R> my_ex, my_ey, my_tx, my_ty, my_b;
-    for (int k = tid; k < EN; k += NT) {
-        int ex, ey;
-        if (k < NT) { ex = k % TX; ey = k / TX; }
-        else {
-            const int h = k - NT;
-            if (h < TY + 1) { ex = -1; ey = h - 1; }
-            else { ex = h - (TY + 1); ey = -1; }
-        }
-        const int e = (ey + 1) * EW + (ex + 1);
-        const int l = (ey + 2) * LW + (ex + 2);
-        const int ai = (ey + 2) * AW + (ex + 2);
-        const A8<R> A0 = s_alg(sA, ai, AN);
-        const A8<R> Dn = conj_dn(s_link(sU, 1, l - LW, LN), s_alg(sA, ai - AW, AN));
-        const A8<R> Lf = conj_dn(s_link(sU, 0, l - 1, LN), s_alg(sA, ai - 1, AN));
-        const A8<R> ph = s_alg(sPhi, l, LN);
-        const A8<R> tx = conj_up(s_link(sU, 0, l, LN), s_alg(sPhi, l + 1, LN));
-        const A8<R> ty = conj_up(s_link(sU, 1, l, LN), s_alg(sPhi, l + LW, LN));
-        const A8<R> cx = icomm(tx, ph), cy = icomm(ty, ph);
-        const A8<R> eox = s_alg(sEs, e, EN), eoy = s_alg(sEs + AP * EN, e, EN);
-        A8<R> ex_n, ey_n, sx, sy;
-#pragma unroll
-        for (int c = 0; c < 8; c++) {
-            ex_n.v[c] = eox.v[c] + dt * (t * (A0.v[c] - Dn.v[c]) + inv_t * cx.v[c]);
-            ey_n.v[c] = eoy.v[c] + dt * (t * (Lf.v[c] - A0.v[c]) + inv_t * cy.v[c]);
-            sx.v[c] = eox.v[c] + ex_n.v[c];
-            sy.v[c] = eoy.v[c] + ey_n.v[c];
-        }
-        // only this thread reads site e of sEs before the barrier
-        s_alg_put(sEs, e, EN, sx);
-        s_alg_put(sEs + AP * EN, e, EN, sy);
-        s_alg_put(sLf, e, EN, Lf);
-        if (k < NT) {
-            my_ex = ex_n; my_ey = ey_n; my_tx = tx; my_ty = ty;
-#pragma unroll
-            for (int c = 0; c < 8; c++) my_b.v[c] = A0.v[c] + Lf.v[c] + Dn.v[c];
-        }
-    }
-    __syncthreads();
-
-    // ---- phase 4: the tile sites
-    const int ix = tid % TX, iy = tid / TX;
-    const int gx = x0 + ix, gy = y0 + iy;
-    if (gx >= N || gy >= N) return;
-    const int64_t g = (int64_t)gy * N + gx;
-    const int e = (iy + 1) * EW + (ix + 1);
-    const int l = (iy + 2) * LW + (ix + 2);
-    const A8<R> ph = s_alg(sPhi, l, LN);
-    const M3<R> Ux_m = s_link(sU, 0, l - 1, LN);
-    const M3<R> Uy_m = s_link(sU, 1, l - LW, LN);
-    const A8<R> bx = conj_dn(Ux_m, s_alg(sPhi, l - 1, LN));
-    const A8<R> by = conj_dn(Uy_m, s_alg(sPhi, l - LW, LN));
-    const A8<R> p_old = s_alg(sPi, tid, NT);
-    A8<R> p_new, ph_new;
-#pragma unroll
-    for (int c = 0; c < 8; c++) {
-        const R lap = my_tx.v[c] + my_ty.v[c] + bx.v[c] + by.v[c] - R(4) * ph.v[c];
-        p_new.v[c] = p_old.v[c] + dt * inv_t * lap;
-        ph_new.v[c] = ph.v[c] + (R)a.dt_th * p_new.v[c];
-    }
-    if (SITE) {
-        // E_i = (1/4t){e_i(s) + U_i(s-i)^+ e_i(s-i) U_i(s-i)}, e summed over n -+ 1/2
-        const A8<R> sx = conj_dn(Ux_m, s_alg(sEs, e - 1, EN));
-        const A8<R> sy = conj_dn(Uy_m, s_alg(sEs + AP * EN, e - EW, EN));
-        const A8<R> hx = s_alg(sEs, e, EN), hy = s_alg(sEs + AP * EN, e, EN);
-        const A8<R> cr = conj_dn(Uy_m, s_alg(sLf, e - EW, EN));
-        A8<R> Ex, Ey, Ee, Bx, By, Be;
-        const R q = R(0.25) * inv_t, hf = R(0.5) * inv_t;
-#pragma unroll
-        for (int c = 0; c < 8; c++) {
-            Ex.v[c] = q * (hx.v[c] + sx.v[c]);
-            Ey.v[c] = q * (hy.v[c] + sy.v[c]);
-            Ee.v[c] = R(0.5) * (p_old.v[c] + p_new.v[c]);
-            Bx.v[c] = -hf * (my_ty.v[c] - by.v[c]);
-            By.v[c] = hf * (my_tx.v[c] - bx.v[c]);
-            Be.v[c] = R(0.25) * (my_b.v[c] + cr.v[c]);
-        }
-        store_alg(site, g, Vn, Ex);
-        store_alg(site + (size_t)1 * AP * Vn, g, Vn, Ey);
-        store_alg(site + (size_t)2 * AP * Vn, g, Vn, Ee);
-        store_alg(site + (size_t)3 * AP * Vn, g, Vn, Bx);
-        store_alg(site + (size_t)4 * AP * Vn, g, Vn, By);
-        store_alg(site + (size_t)5 * AP * Vn, g, Vn, Be);
-    }
-    store_alg(out.e, g, Vn, my_ex);
-    store_alg(out.e + (size_t)AP * Vn, g, Vn, my_ey);
-    store_alg(out.pi, g, Vn, p_new);
-    store_alg(out.phi, g, Vn, ph_new);
-    M3<R> nx = mul(exp_i_alg<R, ExpN<R>::n>(my_ex, (R)a.dt_over_th), s_link(sU, 0, l, LN));
-    M3<R> ny = mul(exp_i_alg<R, ExpN<R>::n>(my_ey, (R)a.dt_over_th), s_link(sU, 1, l, LN));
-    if (a.reunit) { reunit(nx); reunit(ny); }
-    store_link(out.U, 0, g, Vn, nx);
-    store_link(out.U, 1, g, Vn, ny);
+    fused_tile<R, TX, TY, SITE>(in, out, site, a, blockIdx.x);
 }
 
 template <typename R, int TX, int TY, bool SITE>
-static void launch_t(void* in, void* out, void* site, int N, double t, double dt, int reunit, cudaStream_t st) {
+static void launch_t(void* in, void* out, void* site, int N, int64_t n, double dt, int reunit, cudaStream_t st) {
     using T = Tile<R, TX, TY>;
     // the dynamic shared-memory limit is a per-device function attribute
     static bool attr[64] = {};
@@ -313,29 +22,20 @@ static void launch_t(void* in, void* out, void* site, int N, double t, double dt
         attr[dev] = true;
     }
     const int64_t Vn = (int64_t)N * N;
-    StepArgs a;
-    a.N = N;
-    a.tiles_x = (N + TX - 1) / TX;
+    StepArgs a = step_args(N, (N + TX - 1) / TX, n, dt, reunit);
     const int tiles_y = (N + TY - 1) / TY;
-    const double th = t + 0.5 * dt;
-    a.t = t;
-    a.dt = dt;
-    a.inv_t = t > 0 ? 1.0 / t : 0.0;
-    a.dt_over_th = dt / th;
-    a.dt_th = dt * th;
-    a.reunit = reunit;
     fused_step_kernel<R, TX, TY, SITE><<<a.tiles_x * tiles_y, TX * TY, T::bytes, st>>>(
         carve_fields<R>(in, Vn), carve_fields<R>(out, Vn), (typename Prec<R>::V*)site, a);
 }
 
-void launch_fused_step(int prec, void* in, void* out, void* site, int N, double t, double dt, int reunit,
+void launch_fused_step(int prec, void* in, void* out, void* site, int N, int64_t n, double dt, int reunit,
                        cudaStream_t st) {
     if (prec == 0) {
-        if (site) launch_t<double, 32, 4, true>(in, out, site, N, t, dt, 0, st);
-        else launch_t<double, 32, 4, false>(in, out, site, N, t, dt, 0, st);
+        if (site) launch_t<double, 32, 4, true>(in, out, site, N, n, dt, 0, st);
+        else launch_t<double, 32, 4, false>(in, out, site, N, n, dt, 0, st);
     } else {
-        if (site) launch_t<float, 32, 8, true>(in, out, site, N, t, dt, reunit, st);
-        else launch_t<float, 32, 8, false>(in, out, site, N, t, dt, reunit, st);
+        if (site) launch_t<float, 32, 8, true>(in, out, site, N, n, dt, reunit, st);
+        else launch_t<float, 32, 8, false>(in, out, site, N, n, dt, reunit, st);
     }
 }
 
