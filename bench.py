@@ -222,6 +222,7 @@ def run_ours(args):
         ev = B.Event(w, stream=stream)
         ev.glasma_init()
         ev.wong_init()
+        tune = ev.autotune()
         for _ in range(args.warmup):
             ev.glasma_step(1)
             ev.wong_push()
@@ -315,6 +316,7 @@ def run_ours(args):
                        "l2": "flushed between timed steps (512 MiB write, then 256 MiB read), outside the step's events"},
             "particle_steps_per_s": n_active_all * K / t_step,
             "kernel_ms_per_step": {"field_step": t_field / K * 1e3, "wong_push": t_push / K * 1e3},
+            "autotune": tune,
             "roofline": dict(roof[dom], kernel=dom),
             "roofline_kernels": roof,
             "e2e": {"value": world * V * K / e2e_t, "unit": "site-updates/s", "h2d_bytes_per_step": 0,

@@ -181,6 +181,16 @@ gl_status wong_push(gl_ctx* ctx);
 /* n_steps coupled steps: glasma_step(1) + wong_push each. */
 gl_status gl_step_coupled(gl_ctx* ctx, int32_t n_steps);
 
+/* Choose the tile shape of the field kernel (0: 32x8, 1: 32x4, 2: 32x2) and
+ * the push block size (64, 128, 256) for this context from timed trial
+ * launches (waits).  Needs the particles at the fields' time; the trials write
+ * only buffers that the next coupled step rewrites.  Outputs may be NULL. */
+gl_status gl_autotune(gl_ctx* ctx, int32_t* tile_shape, int32_t* push_block);
+
+/* Trial timings of the last gl_autotune, ms: field_ms[3] by tile shape,
+ * push_ms[3] by block size (0 where not tried). */
+gl_status gl_tuning(const gl_ctx* ctx, float* field_ms, float* push_ms);
+
 /* Ensemble sums and field checks at the current time (waits). */
 gl_status observables(gl_ctx* ctx, gl_obs* out);
 

@@ -67,6 +67,8 @@ SIGNATURES = {
     "wong_push": (ctypes.c_int, [_P]),
     "gl_step_coupled": (ctypes.c_int, [_P, ctypes.c_int32]),
     "observables": (ctypes.c_int, [_P, ctypes.POINTER(gl_obs)]),
+    "gl_autotune": (ctypes.c_int, [_P, _P, _P]),
+    "gl_tuning": (ctypes.c_int, [_P, _P, _P]),
     "gl_ensemble_sums_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_uint32,
                                                 ctypes.c_double, _P, _P]),
     "gl_batch_workspace_bytes": (ctypes.c_size_t, [_P, _P, ctypes.c_int32, ctypes.c_int32]),
@@ -210,6 +212,16 @@ class Event:
         o = gl_obs()
         _check(lib().observables(self.ctx, ctypes.byref(o)), self.ctx, "observables")
         return o
+
+    def autotune(self):
+        t = ctypes.c_int32()
+        p = ctypes.c_int32()
+        _check(lib().gl_autotune(self.ctx, ctypes.byref(t), ctypes.byref(p)), self.ctx, "gl_autotune")
+        f = (ctypes.c_float * 3)()
+        q = (ctypes.c_float * 3)()
+        lib().gl_tuning(self.ctx, f, q)
+        return {"tile": ("32x8", "32x4", "32x2")[t.value], "push_block": p.value,
+                "field_ms": list(f), "push_ms": list(q)}
 
     def _shape(self, which):
         V = self.N * self.N

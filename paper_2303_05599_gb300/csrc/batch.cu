@@ -12,6 +12,7 @@
 // chosen by gl_batch_autotune from timed trial launches that leave the state
 // unchanged (the field kernel writes only the spare time slice; the push runs
 // on a copy of the particles).
+#include <math.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -151,7 +152,8 @@ struct gl_batch {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     int graph_tile, graph_push_block;
-    float tune_ms[N_TILES][3];
+    float tune_field_ms[N_TILES];
+    float tune_push_ms[3];
     char err[256];
 };
 
@@ -349,7 +351,7 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
             cudaEventElapsedTime(&m, e0, e1);
             if (rep > 0) ms += m;
         }
-        b->tune_ms[tile][0] = ms / 3;
+        b->tune_field_ms[tile] = ms / 3;
         if (ms < best_f) { best_f = ms; bt = tile; }
     }
     b->tile = bt;
@@ -366,6 +368,17 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
         b->h_desc[e].parts = v.parts_alt;
     }
     if (have_copy) {
+        // time the push at a step where every species is formed, then restore the clock
+        int64_t trial = 0, now = 0;
+        for (int e = 0; e < b->ne; e++)
+            for (int k = 0; k < b->h_desc[e].n_species; k++) {
+                const int64_t n = (int64_t)ceil(b->h_desc[e].t_form[k] / b->dt);
+                if (n > trial) trial = n;
+            }
+        cudaMemcpyAsync(&now, b->d_clock, sizeof now, cudaMemcpyDeviceToHost, b->stream);
+        cudaStreamSynchronize(b->stream);
+        if (trial < now) trial = now;
+        cudaMemcpyAsync(b->d_clock, &trial, sizeof trial, cudaMemcpyHostToDevice, b->stream);
         cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(EvDesc) * b->ne, cudaMemcpyHostToDevice, b->stream);
         BatchArgs a{b->d_desc, b->ne, b->dt, 0, b->d_clock};
         for (int k = 0; k < 3; k++) {
@@ -380,10 +393,10 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
                 cudaEventElapsedTime(&m, e0, e1);
                 if (rep > 0) ms += m;
             }
-            b->tune_ms[0][k] = b->tune_ms[0][k];
-            b->tune_ms[1][k] = ms / 3;
+            b->tune_push_ms[k] = ms / 3;
             if (ms < best_p) { best_p = ms; bp = PUSH_BLOCKS[k]; }
         }
+        cudaMemcpyAsync(b->d_clock, &now, sizeof now, cudaMemcpyHostToDevice, b->stream);
     }
     memcpy(b->h_desc, saved, sizeof(EvDesc) * b->ne);
     delete[] saved;
@@ -433,9 +446,9 @@ gl_status gl_batch_observables(gl_batch* b, gl_obs* out) {
 gl_status gl_batch_tuning(const gl_batch* b, float* field_ms, float* push_ms) {
     if (!b) return GL_ERR_ARG;
     for (int k = 0; k < N_TILES; k++)
-        if (field_ms) field_ms[k] = b->tune_ms[k][0];
+        if (field_ms) field_ms[k] = b->tune_field_ms[k];
     for (int k = 0; k < 3; k++)
-        if (push_ms) push_ms[k] = b->tune_ms[1][k];
+        if (push_ms) push_ms[k] = b->tune_push_ms[k];
     return GL_OK;
 }
 

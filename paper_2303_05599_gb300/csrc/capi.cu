@@ -52,6 +52,9 @@ struct gl_ctx {
     int cur;
     int64_t step, pstep;
     int64_t site_step;  // particle step whose site fields are in `site` (-1: none)
+    int tile;           // fused-kernel tile shape (gl_autotune)
+    int push_block;     // push block size (gl_autotune)
+    float tune_field_ms[3], tune_push_ms[3];
     int reunit_count;
     char err[256];
 };
@@ -263,6 +266,8 @@ gl_status gl_create(const gl_config* cfg, const gl_species* sp, int32_t ns, void
     c->cur = 0;
     c->step = c->pstep = 0;
     c->site_step = -1;
+    c->tile = 0;
+    c->push_block = 128;
     *out = c;
     return GL_OK;
 }
@@ -376,7 +381,7 @@ static void one_field_step(gl_ctx* c, bool site) {
     }
     site = site && c->pstep == c->step;
     launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], site ? c->site : nullptr, c->N, c->step, c->dt,
-                      reunit, c->stream);
+                      reunit, c->tile, c->stream);
     if (site) c->site_step = c->pstep;
     c->cur = 1 - c->cur;
     c->step++;
@@ -408,7 +413,7 @@ static gl_status push_once(gl_ctx* c) {
     if (c->site_step != c->pstep)
         if (gl_status s = site_once(c)) return s;
     if (c->np) launch_push(c->prec, c->site, c->field[c->cur], c->parts, c->np, c->N, t, c->dt, active_mask(c, c->pstep),
-                           c->spp, c->stream);
+                           c->spp, c->stream, c->push_block);
     c->pstep++;
     if (c->sort_ok && c->pstep % c->cfg.sort_every == 0) sort_particles(c);
     return GL_OK;
@@ -428,6 +433,74 @@ gl_status gl_step_coupled(gl_ctx* c, int32_t n) {
         if (gl_status s = push_once(c)) return s;
     }
     return check_cuda(c, "gl_step_coupled");
+}
+
+gl_status gl_autotune(gl_ctx* c, int32_t* tile_out, int32_t* push_block_out) {
+    if (!c) return GL_ERR_ARG;
+    if (c->pstep != c->step) return fail(c, GL_ERR_STATE, "autotune needs the particles at the fields' time");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto timed = [&](auto&& fn) {
+        float acc = 0;
+        for (int rep = 0; rep < 4; rep++) {
+            cudaEventRecord(e0, c->stream);
+            fn();
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            float m = 0;
+            cudaEventElapsedTime(&m, e0, e1);
+            if (rep > 0) acc += m;
+        }
+        return acc / 3;
+    };
+    // field kernel: writes only the spare time slice and the site fields at
+    // the current time, both of which the next coupled step rewrites
+    const int tiles[3] = {0, 1, 2};
+    float best = 1e30f;
+    for (int k = 0; k < 3; k++) {
+        if (c->prec == GL_FP64 && k == 0) { c->tune_field_ms[k] = 0; continue; }
+        const float ms = timed([&] {
+            launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], c->np ? c->site : nullptr, c->N, c->step,
+                              c->dt, 0, tiles[k], c->stream);
+        });
+        c->tune_field_ms[k] = ms;
+        if (ms < best) { best = ms; c->tile = tiles[k]; }
+    }
+    // push: on a copy of the particles, at a step where every species is formed
+    if (c->np && c->parts_alt) {
+        int64_t trial = c->step;
+        for (int k = 0; k < c->ns; k++) {
+            const int64_t n = (int64_t)ceil(c->t_form[k] / c->dt);
+            if (n > trial) trial = n;
+        }
+        const int blocks[3] = {64, 128, 256};
+        best = 1e30f;
+        for (int k = 0; k < 3; k++) {
+            cudaMemcpyAsync(c->parts_alt, c->parts, particle_bytes(c->prec, c->np), cudaMemcpyDeviceToDevice, c->stream);
+            const float ms = timed([&] {
+                launch_push(c->prec, c->site, c->field[1 - c->cur], c->parts_alt, c->np, c->N, trial * c->dt, c->dt,
+                            active_mask(c, trial), c->spp, c->stream, blocks[k]);
+            });
+            c->tune_push_ms[k] = ms;
+            if (ms < best) { best = ms; c->push_block = blocks[k]; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->site_step = -1;
+    if (tile_out) *tile_out = c->tile;
+    if (push_block_out) *push_block_out = c->push_block;
+    return check_cuda(c, "gl_autotune");
+}
+
+gl_status gl_tuning(const gl_ctx* c, float* field_ms, float* push_ms) {
+    if (!c) return GL_ERR_ARG;
+    for (int k = 0; k < 3; k++) {
+        if (field_ms) field_ms[k] = c->tune_field_ms[k];
+        if (push_ms) push_ms[k] = c->tune_push_ms[k];
+    }
+    return GL_OK;
 }
 
 gl_status observables(gl_ctx* c, gl_obs* o) {

@@ -16,13 +16,14 @@ struct SpeciesParams {
 
 // field step n -> n+1 on buffers in/out (FP64 or FP32 two-row layout); when
 // site is not null the same kernel also writes the site E, B at t_n
-void launch_fused_step(int prec, void* in, void* out, void* site, int N, int64_t n, double dt, int reunit,
+// tile: 0 = 32x8, 1 = 32x4, 2 = 32x2 (FP64 uses 32x4 for 0 and 1)
+void launch_fused_step(int prec, void* in, void* out, void* site, int N, int64_t n, double dt, int reunit, int tile,
                        cudaStream_t st);
 // site E, B at t_n from buffer n (U, phi, e(n-1/2), pi(n-1/2)) and buffer n+1 (e, pi at n+1/2)
 void launch_site_fields(int prec, const void* bn, const void* bn1, void* site, int N, double t, cudaStream_t st);
 // Euler + CPIC push of all particles active at t_n (bit s of active_mask)
 void launch_push(int prec, const void* site, const void* bn1, void* parts, int64_t np, int N, double t, double dt,
-                 uint32_t active_mask, const SpeciesParams& sp, cudaStream_t st);
+                 uint32_t active_mask, const SpeciesParams& sp, cudaStream_t st, int block = 128);
 // particle sampling: positions, momenta, Haar charges
 void launch_sample(int prec, void* parts, int64_t np, int N, uint64_t seed, const int64_t* offsets, int n_species,
                    const int* rep, const int* mom_mode, const double* p0, const double* p1,

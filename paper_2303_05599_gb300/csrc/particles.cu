@@ -122,36 +122,42 @@ void launch_site_fields(int prec, const void* bn, const void* bn1, void* site, i
 }
 
 // ------------------------------------------------------------ push
-template <typename R>
-__global__ void __launch_bounds__(128, 8) push_kernel(const typename Prec<R>::V* __restrict__ site, Fields<R> bn1,
-                                                      Parts<R> P, int N, R t, R dt, R dt_over_t, uint32_t active,
-                                                      SpeciesArgs<R> sa) {
+template <typename R, int B>
+__global__ void __launch_bounds__(B, 1024 / B) push_kernel(const typename Prec<R>::V* __restrict__ site,
+                                                           Fields<R> bn1, Parts<R> P, int N, R t, R dt, R dt_over_t,
+                                                           uint32_t active, SpeciesArgs<R> sa) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.np; i += (int64_t)gridDim.x * blockDim.x)
         push_one<R>(site, bn1, P, i, N, t, dt, dt_over_t, active, sa);
 }
 
 template <typename R>
 static void push_t(const void* site, const void* bn1, void* parts, int64_t np, int N, double t, double dt,
-                   uint32_t active, const SpeciesParams& sp, cudaStream_t st) {
+                   uint32_t active, const SpeciesParams& sp, cudaStream_t st, int block) {
     const int64_t Vn = (int64_t)N * N;
     SpeciesArgs<R> sa;
     for (int k = 0; k < GL_MAX_SPECIES; k++) {
         sa.mass[k] = (R)(k < sp.n_species && !sp.is_static[k] ? sp.mass[k] : 0.0);
         sa.is_static[k] = k < sp.n_species ? sp.is_static[k] : 0;
     }
-    const int threads = 128;
+    const int threads = block == 64 || block == 256 ? block : 128;
     int64_t blocks = (np + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (blocks < 1) return;
-    push_kernel<R><<<(unsigned)blocks, threads, 0, st>>>((const typename Prec<R>::V*)site,
-                                                         carve_fields<R>((void*)bn1, Vn), carve_parts<R>(parts, np), N,
-                                                         (R)t, (R)dt, (R)(t > 0 ? dt / t : 0.0), active, sa);
+    const Fields<R> f = carve_fields<R>((void*)bn1, Vn);
+    const Parts<R> P = carve_parts<R>(parts, np);
+    const R tr = (R)t, dtr = (R)dt, dto = (R)(t > 0 ? dt / t : 0.0);
+    if (threads == 64)
+        push_kernel<R, 64><<<(unsigned)blocks, 64, 0, st>>>((const typename Prec<R>::V*)site, f, P, N, tr, dtr, dto, active, sa);
+    else if (threads == 256)
+        push_kernel<R, 256><<<(unsigned)blocks, 256, 0, st>>>((const typename Prec<R>::V*)site, f, P, N, tr, dtr, dto, active, sa);
+    else
+        push_kernel<R, 128><<<(unsigned)blocks, 128, 0, st>>>((const typename Prec<R>::V*)site, f, P, N, tr, dtr, dto, active, sa);
 }
 
 void launch_push(int prec, const void* site, const void* bn1, void* parts, int64_t np, int N, double t, double dt,
-                 uint32_t active_mask, const SpeciesParams& sp, cudaStream_t st) {
-    if (prec == 0) push_t<double>(site, bn1, parts, np, N, t, dt, active_mask, sp, st);
-    else push_t<float>(site, bn1, parts, np, N, t, dt, active_mask, sp, st);
+                 uint32_t active_mask, const SpeciesParams& sp, cudaStream_t st, int block) {
+    if (prec == 0) push_t<double>(site, bn1, parts, np, N, t, dt, active_mask, sp, st, block);
+    else push_t<float>(site, bn1, parts, np, N, t, dt, active_mask, sp, st, block);
 }
 
 // ------------------------------------------------------------ sampling

@@ -28,11 +28,23 @@ static void launch_t(void* in, void* out, void* site, int N, int64_t n, double d
         carve_fields<R>(in, Vn), carve_fields<R>(out, Vn), (typename Prec<R>::V*)site, a);
 }
 
-void launch_fused_step(int prec, void* in, void* out, void* site, int N, int64_t n, double dt, int reunit,
+void launch_fused_step(int prec, void* in, void* out, void* site, int N, int64_t n, double dt, int reunit, int tile,
                        cudaStream_t st) {
     if (prec == 0) {
-        if (site) launch_t<double, 32, 4, true>(in, out, site, N, n, dt, 0, st);
-        else launch_t<double, 32, 4, false>(in, out, site, N, n, dt, 0, st);
+        // FP64 tiles: 32x4 (139 KB of shared memory) or 32x2
+        if (tile == 2) {
+            if (site) launch_t<double, 32, 2, true>(in, out, site, N, n, dt, 0, st);
+            else launch_t<double, 32, 2, false>(in, out, site, N, n, dt, 0, st);
+        } else {
+            if (site) launch_t<double, 32, 4, true>(in, out, site, N, n, dt, 0, st);
+            else launch_t<double, 32, 4, false>(in, out, site, N, n, dt, 0, st);
+        }
+    } else if (tile == 1) {
+        if (site) launch_t<float, 32, 4, true>(in, out, site, N, n, dt, reunit, st);
+        else launch_t<float, 32, 4, false>(in, out, site, N, n, dt, reunit, st);
+    } else if (tile == 2) {
+        if (site) launch_t<float, 32, 2, true>(in, out, site, N, n, dt, reunit, st);
+        else launch_t<float, 32, 2, false>(in, out, site, N, n, dt, reunit, st);
     } else {
         if (site) launch_t<float, 32, 8, true>(in, out, site, N, n, dt, reunit, st);
         else launch_t<float, 32, 8, false>(in, out, site, N, n, dt, reunit, st);

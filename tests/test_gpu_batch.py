@@ -68,3 +68,23 @@ def test_batch_rejects_events_at_different_steps():
         with pytest.raises(B.GlasmaError) as e:
             batch.step(1)
         assert e.value.status == B.GL_ERR_STATE
+
+
+@pytest.mark.parametrize("prec", [W.FP64, W.FP32_2ROW])
+def test_autotuned_tile_shape_changes_nothing(prec):
+    """The fused kernel computes every site with the same operations whatever
+    the tile shape, so a context tuned to any shape evolves bitwise like one
+    with the default shape."""
+    w = events(prec)[1]
+    w.sort_every = 16
+    a = B.Event(w)
+    b = B.Event(w)
+    for ev in (a, b):
+        ev.glasma_init()
+        ev.wong_init()
+    tune = a.autotune()
+    print("single-event autotune:", tune)
+    a.step(19)
+    b.step(19)
+    for buf in (B.GL_BUF_LINKS, B.GL_BUF_E, B.GL_BUF_PI, B.GL_BUF_PHI, B.GL_BUF_PARTICLES):
+        assert np.array_equal(a.download(buf), b.download(buf))
