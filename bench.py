@@ -279,6 +279,9 @@ def run_ours(args):
         n_active_all = float(n_active)
     V = w.N * w.N
     value = world * V * K / t_step
+    # report-time ensemble average over every rank's event (outside the timed region)
+    from paper_2303_05599_gb300 import multi
+    ens = multi.ensemble_reduce([obs], len(w.species))
     line = None
     if rank == 0:
         import json as _json
@@ -315,6 +318,7 @@ def run_ours(args):
                        "events_per_gpu": 1, "parallelism": "events sharded over ranks",
                        "l2": "flushed between timed steps (512 MiB write, then 256 MiB read), outside the step's events"},
             "particle_steps_per_s": n_active_all * K / t_step,
+            "ensemble": {"tau_fm": obs.tau_fm, "per_species": ens},
             "kernel_ms_per_step": {"field_step": t_field / K * 1e3, "wong_push": t_push / K * 1e3},
             "autotune": tune,
             "roofline": dict(roof[dom], kernel=dom),

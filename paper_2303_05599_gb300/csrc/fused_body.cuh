@@ -32,7 +32,7 @@ struct ExpN;
 template <>
 struct ExpN<double> { static constexpr int n = 20; };
 template <>
-struct ExpN<float> { static constexpr int n = 12; };
+struct ExpN<float> { static constexpr int n = 8; };
 
 template <typename R, int TX, int TY>
 struct Tile {
@@ -200,8 +200,7 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
     for (int i = tid; i < AN; i += NT) {
         const int l = (i / AW) * LW + (i % AW);  // cell (ax, ay) = (i % AW - 2, i / AW - 2)
         const M3<R> C = mul(s_link(sU, 0, l, LN), s_link(sU, 1, l + 1, LN));
-        const M3<R> P = mul_nd(mul_nd(C, s_link(sU, 0, l + LW, LN)), s_link(sU, 1, l, LN));
-        s_alg_put(sA, i, AN, iah_to_alg(P));
+        s_alg_put(sA, i, AN, iah_of_mul_nd(mul_nd(C, s_link(sU, 0, l + LW, LN)), s_link(sU, 1, l, LN)));
     }
     __syncthreads();
 

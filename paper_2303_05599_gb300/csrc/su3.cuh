@@ -280,6 +280,69 @@ __device__ __forceinline__ A8<R> conj_up(const M3<R>& V, const A8<R>& x) {
     return conj_dn(dag(V), x);
 }
 
+// X^2 for Hermitian X: the upper triangle is formed, the lower one mirrored
+template <typename R>
+__device__ __forceinline__ M3<R> sq_herm(const M3<R>& X) {
+    M3<R> Z;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = i; j < 3; j++) {
+            R sr = R(0), si = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                sr = fma(X.re[i][k], X.re[k][j], sr);
+                sr = fma(-X.im[i][k], X.im[k][j], sr);
+                if (i != j) {
+                    si = fma(X.re[i][k], X.im[k][j], si);
+                    si = fma(X.im[i][k], X.re[k][j], si);
+                }
+            }
+            Z.re[i][j] = sr;
+            Z.im[i][j] = si;
+            Z.re[j][i] = sr;
+            Z.im[j][i] = -si;
+        }
+#pragma unroll
+    for (int i = 0; i < 3; i++) Z.im[i][i] = R(0);
+    return Z;
+}
+
+// components of i[A B^+]_ah without forming the whole product: only the
+// imaginary parts of the diagonal and both triangles are needed
+template <typename R>
+__device__ __forceinline__ A8<R> iah_of_mul_nd(const M3<R>& A, const M3<R>& B) {
+    R dr[3][3], di[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            R sr = R(0), si = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                // A_ik conj(B_jk)
+                if (i != j) {
+                    sr = fma(A.re[i][k], B.re[j][k], sr);
+                    sr = fma(A.im[i][k], B.im[j][k], sr);
+                }
+                si = fma(A.im[i][k], B.re[j][k], si);
+                si = fma(-A.re[i][k], B.im[j][k], si);
+            }
+            dr[i][j] = sr;
+            di[i][j] = si;
+        }
+    A8<R> x;
+    x.v[0] = -(di[0][1] + di[1][0]);
+    x.v[1] = dr[1][0] - dr[0][1];
+    x.v[2] = di[1][1] - di[0][0];
+    x.v[3] = -(di[0][2] + di[2][0]);
+    x.v[4] = dr[2][0] - dr[0][2];
+    x.v[5] = -(di[1][2] + di[2][1]);
+    x.v[6] = dr[2][1] - dr[1][2];
+    x.v[7] = (R(2) * di[2][2] - di[0][0] - di[1][1]) * inv_sqrt3<R>();
+    return x;
+}
+
 // exp(i s X) for Hermitian traceless X = x^a T^a.  Cayley-Hamilton gives
 // X^3 = c1 X + c0 with c1 = tr(X^2)/2 and c0 = det X, so every power of iX
 // is a combination of 1, X, X^2; the exponential series is summed on those
@@ -291,13 +354,14 @@ __device__ __forceinline__ M3<R> exp_i_alg(const A8<R>& x, R s) {
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) { X.re[i][j] *= s; X.im[i][j] *= s; }
-    M3<R> X2 = mul(X, X);
+    M3<R> X2 = sq_herm(X);
     R c1 = R(0.5) * (X2.re[0][0] + X2.re[1][1] + X2.re[2][2]);
     int nsq = 0;
     R scl = R(1);
     // Frobenius norm^2 of X is 2 c1; scale until the truncated series is
-    // accurate: |X| <= 1 with 12 or more terms, |X| <= 0.2 with fewer
-    const R lim = TERMS >= 12 ? R(1) : R(0.04);
+    // accurate: |X| <= 1 with 12 or more terms, |X| <= 0.5 with 8 to 11,
+    // |X| <= 0.2 with fewer (truncation error below 1e-8 in each case)
+    const R lim = TERMS >= 12 ? R(1) : (TERMS >= 8 ? R(0.25) : R(0.04));
     R nrm2 = R(2) * c1;
     while (nrm2 > lim && nsq < 30) { nrm2 *= R(0.25); scl *= R(0.5); nsq++; }
     if (nsq) {
