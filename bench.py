@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
+    ap.add_argument("--reunit-every", type=int, default=None)
     return ap.parse_args()
 
 
@@ -53,6 +54,8 @@ def workload(args, rank=0):
             w.seed = w.seed + 64 * rank
         return evs
     w = W.WORKLOADS[args.workload]()
+    if args.reunit_every is not None:
+        w.reunit_every = args.reunit_every
     if args.precision == "fp64":
         w.precision = W.FP64
     elif args.precision == "fp32":
@@ -255,6 +258,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
         ck = clocks.stop()
+        field_each = sorted(e[0].elapsed_time(e[1]) for e in evs)
         t_field = sum(e[0].elapsed_time(e[1]) for e in evs) / 1e3
         t_push = sum(e[1].elapsed_time(e[2]) for e in evs) / 1e3
         t_step = t_field + t_push
@@ -320,6 +324,7 @@ def run_ours(args):
             "particle_steps_per_s": n_active_all * K / t_step,
             "ensemble": {"tau_fm": obs.tau_fm, "per_species": ens},
             "kernel_ms_per_step": {"field_step": t_field / K * 1e3, "wong_push": t_push / K * 1e3},
+            "field_step_ms_min_median_max": [field_each[0], field_each[K // 2], field_each[-1]],
             "autotune": tune,
             "roofline": dict(roof[dom], kernel=dom),
             "roofline_kernels": roof,

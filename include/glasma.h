@@ -75,7 +75,8 @@ typedef struct {
     int32_t N;              /* lattice sites per transverse direction, >= 4 */
     int32_t Ns;             /* colour sheets per nucleus (eq. for the regularised correlator) */
     int32_t precision;      /* gl_precision */
-    int32_t reunit_every;   /* FP32: re-unitarise links in FP64 every k steps (0: never) */
+    int32_t reunit_every;   /* FP32: re-unitarise links in FP64 every k steps (0: never); on GB300 an
+                               FP64 re-unitarising step costs about 2.5 normal steps, 64 is a good period */
     double L_fm;            /* transverse box length */
     double g2mu_GeV;        /* MV parameter g^2 mu */
     double mIR_GeV;         /* infrared regulator of the Poisson kernel */
@@ -181,13 +182,13 @@ gl_status wong_push(gl_ctx* ctx);
 /* n_steps coupled steps: glasma_step(1) + wong_push each. */
 gl_status gl_step_coupled(gl_ctx* ctx, int32_t n_steps);
 
-/* Choose the tile shape of the field kernel (0: 32x8, 1: 32x4, 2: 32x2) and
+/* Choose the tile shape of the field kernel (0: 32x8, 1: 32x4, 2: 32x2, 3: 32x16) and
  * the push block size (64, 128, 256) for this context from timed trial
  * launches (waits).  Needs the particles at the fields' time; the trials write
  * only buffers that the next coupled step rewrites.  Outputs may be NULL. */
 gl_status gl_autotune(gl_ctx* ctx, int32_t* tile_shape, int32_t* push_block);
 
-/* Trial timings of the last gl_autotune, ms: field_ms[3] by tile shape,
+/* Trial timings of the last gl_autotune, ms: field_ms[4] by tile shape,
  * push_ms[3] by block size (0 where not tried). */
 gl_status gl_tuning(const gl_ctx* ctx, float* field_ms, float* push_ms);
 

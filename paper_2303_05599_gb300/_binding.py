@@ -217,10 +217,10 @@ class Event:
         t = ctypes.c_int32()
         p = ctypes.c_int32()
         _check(lib().gl_autotune(self.ctx, ctypes.byref(t), ctypes.byref(p)), self.ctx, "gl_autotune")
-        f = (ctypes.c_float * 3)()
+        f = (ctypes.c_float * 4)()
         q = (ctypes.c_float * 3)()
         lib().gl_tuning(self.ctx, f, q)
-        return {"tile": ("32x8", "32x4", "32x2")[t.value], "push_block": p.value,
+        return {"tile": ("32x8", "32x4", "32x2", "32x16")[t.value], "push_block": p.value,
                 "field_ms": list(f), "push_ms": list(q)}
 
     def _shape(self, which):

@@ -54,7 +54,7 @@ struct gl_ctx {
     int64_t site_step;  // particle step whose site fields are in `site` (-1: none)
     int tile;           // fused-kernel tile shape (gl_autotune)
     int push_block;     // push block size (gl_autotune)
-    float tune_field_ms[3], tune_push_ms[3];
+    float tune_field_ms[4], tune_push_ms[3];
     int reunit_count;
     char err[256];
 };
@@ -456,10 +456,10 @@ gl_status gl_autotune(gl_ctx* c, int32_t* tile_out, int32_t* push_block_out) {
     };
     // field kernel: writes only the spare time slice and the site fields at
     // the current time, both of which the next coupled step rewrites
-    const int tiles[3] = {0, 1, 2};
+    const int tiles[4] = {0, 1, 2, 3};
     float best = 1e30f;
-    for (int k = 0; k < 3; k++) {
-        if (c->prec == GL_FP64 && k == 0) { c->tune_field_ms[k] = 0; continue; }
+    for (int k = 0; k < 4; k++) {
+        if (c->prec == GL_FP64 && (k == 0 || k == 3)) { c->tune_field_ms[k] = 0; continue; }
         const float ms = timed([&] {
             launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], c->np ? c->site : nullptr, c->N, c->step,
                               c->dt, 0, tiles[k], c->stream);
@@ -496,10 +496,10 @@ gl_status gl_autotune(gl_ctx* c, int32_t* tile_out, int32_t* push_block_out) {
 
 gl_status gl_tuning(const gl_ctx* c, float* field_ms, float* push_ms) {
     if (!c) return GL_ERR_ARG;
-    for (int k = 0; k < 3; k++) {
+    for (int k = 0; k < 4; k++)
         if (field_ms) field_ms[k] = c->tune_field_ms[k];
+    for (int k = 0; k < 3; k++)
         if (push_ms) push_ms[k] = c->tune_push_ms[k];
-    }
     return GL_OK;
 }
 

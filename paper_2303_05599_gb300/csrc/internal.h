@@ -16,7 +16,7 @@ struct SpeciesParams {
 
 // field step n -> n+1 on buffers in/out (FP64 or FP32 two-row layout); when
 // site is not null the same kernel also writes the site E, B at t_n
-// tile: 0 = 32x8, 1 = 32x4, 2 = 32x2 (FP64 uses 32x4 for 0 and 1)
+// tile: 0 = 32x8, 1 = 32x4, 2 = 32x2, 3 = 32x16 (FP64: 32x4 for 0, 1 and 3)
 void launch_fused_step(int prec, void* in, void* out, void* site, int N, int64_t n, double dt, int reunit, int tile,
                        cudaStream_t st);
 // site E, B at t_n from buffer n (U, phi, e(n-1/2), pi(n-1/2)) and buffer n+1 (e, pi at n+1/2)

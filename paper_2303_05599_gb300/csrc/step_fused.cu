@@ -45,6 +45,9 @@ void launch_fused_step(int prec, void* in, void* out, void* site, int N, int64_t
     } else if (tile == 2) {
         if (site) launch_t<float, 32, 2, true>(in, out, site, N, n, dt, reunit, st);
         else launch_t<float, 32, 2, false>(in, out, site, N, n, dt, reunit, st);
+    } else if (tile == 3) {
+        if (site) launch_t<float, 32, 16, true>(in, out, site, N, n, dt, reunit, st);
+        else launch_t<float, 32, 16, false>(in, out, site, N, n, dt, reunit, st);
     } else {
         if (site) launch_t<float, 32, 8, true>(in, out, site, N, n, dt, reunit, st);
         else launch_t<float, 32, 8, false>(in, out, site, N, n, dt, reunit, st);

@@ -50,7 +50,7 @@ class Workload:
     dtau_over_a: float = 0.125
     tau_max_fm: float = 1.0
     precision: int = FP64
-    reunit_every: int = 8
+    reunit_every: int = 64
     sort_every: int = 16
     seed: int = 0
     species: List[Species] = field(default_factory=list)
