@@ -39,16 +39,21 @@ __global__ void __launch_bounds__(256) field_obs_kernel(Fields<R> f, const typen
         for (int d = 0; d < 2; d++) {
             const typename Prec<R>::V* e = f.e + (size_t)d * AP * Vn;
             const A8<double> eh = to_d(load_alg(e, s, Vn));
-            const A8<double> eb = adj_dag(to_d(load_link(f.U, d, sb[d], Vn)), to_d(load_alg(e, sb[d], Vn)));
+            const A8<double> eb = conj_dn(to_d(load_link(f.U, d, sb[d], Vn)), to_d(load_alg(e, sb[d], Vn)));
             for (int a = 0; a < 8; a++) G.v[a] += eh.v[a] - eb.v[a];
-            // unitarity of the link at (d, s)
+            // unitarity of the link at (d, s): ||U U^+ - 1||_F from the Gram
+            // matrix of the rows (Hermitian: upper triangle, off-diagonal twice)
             const M3<double> u = to_d(load_link(f.U, d, s, Vn));
-            const M3<double> uu = mul_nd(u, u);
             double n2 = 0;
             for (int i = 0; i < 3; i++)
-                for (int j = 0; j < 3; j++) {
-                    const double r = uu.re[i][j] - (i == j ? 1.0 : 0.0), im = uu.im[i][j];
-                    n2 += r * r + im * im;
+                for (int j = i; j < 3; j++) {
+                    double gr = 0, gi = 0;
+                    for (int k = 0; k < 3; k++) {
+                        gr += u.re[i][k] * u.re[j][k] + u.im[i][k] * u.im[j][k];
+                        gi += u.im[i][k] * u.re[j][k] - u.re[i][k] * u.im[j][k];
+                    }
+                    const double r = gr - (i == j ? 1.0 : 0.0);
+                    n2 += (i == j ? 1.0 : 2.0) * (r * r + gi * gi);
                 }
             v[FO_UMAX] = fmax(v[FO_UMAX], sqrt(n2));
         }
@@ -83,15 +88,23 @@ __global__ void __launch_bounds__(256) field_obs_kernel(Fields<R> f, const typen
     }
 }
 
-__global__ void field_obs_finalize(const double* partials, int nblocks, double* out) {
-    const int k = threadIdx.x;
-    if (k >= FO_N) return;
+// one block per output value: strided partial results, then a fixed-order tree
+__global__ void __launch_bounds__(256) field_obs_finalize(const double* partials, int nblocks, double* out) {
+    __shared__ double red[256];
+    const int k = blockIdx.x;
+    const bool mx = k == FO_GMAX || k == FO_UMAX;
     double a = 0.0;
-    for (int b = 0; b < nblocks; b++) {
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
         const double v = partials[(size_t)b * FO_N + k];
-        a = (k == FO_GMAX || k == FO_UMAX) ? fmax(a, v) : a + v;
+        a = mx ? fmax(a, v) : a + v;
     }
-    out[k] = a;
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = mx ? fmax(red[threadIdx.x], red[threadIdx.x + o]) : red[threadIdx.x] + red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = red[0];
 }
 
 void launch_field_obs(int prec, const void* b, const void* site, int N, double* partials, int max_blocks,
@@ -106,7 +119,7 @@ void launch_field_obs(int prec, const void* b, const void* site, int N, double* 
     else
         field_obs_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(carve_fields<float>((void*)b, Vn),
                                                                       (const float4*)site, N, partials);
-    field_obs_finalize<<<1, 32, 0, st>>>(partials, (int)blocks, out);
+    field_obs_finalize<<<FO_N, 256, 0, st>>>(partials, (int)blocks, out);
 }
 
 // ------------------------------------------------------------ canonical <-> device

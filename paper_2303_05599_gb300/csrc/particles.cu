@@ -338,18 +338,14 @@ __global__ void __launch_bounds__(256) particle_obs_kernel(Parts<R> P, double t,
             A8<double> q;
             for (int a = 0; a < 8; a++) q.v[a] = p.q.v[a];
             const double q2 = a_dot(q, q);
-            const M3<double> Q = alg_to_mat(q);
-            const M3<double> Q2 = mul(Q, Q);
-            double tr3 = 0;  // Re tr(Q^3); q3 = 4 tr(Q^3) (App. A)
-            for (int a = 0; a < 3; a++)
-                for (int b = 0; b < 3; b++) tr3 += Q2.re[a][b] * Q.re[b][a] - Q2.im[a][b] * Q.im[b][a];
+            const double q3 = casimir3(q);
             v[PO_COUNT] = 1.0;
             v[PO_PX2] = px * px;
             v[PO_PY2] = py * py;
             v[PO_PL2] = pl * pl;
             v[PO_DPT2] = px * px + py * py - P.pt0[i];
             v[PO_Q2] = fabs(q2 - oa.q2ref[s]);
-            v[PO_Q3] = fabs(4.0 * tr3 - oa.q3ref[s]);
+            v[PO_Q3] = fabs(q3 - oa.q3ref[s]);
         }
         for (int sp_ = 0; sp_ < oa.sp.n_species; sp_++) {
             const bool mine = s == sp_;
@@ -380,16 +376,24 @@ __global__ void __launch_bounds__(256) particle_obs_kernel(Parts<R> P, double t,
     }
 }
 
-__global__ void particle_obs_finalize(const double* partials, int nblocks, double* out) {
+// one block per output value: strided partial sums, then a fixed-order tree
+__global__ void __launch_bounds__(256) particle_obs_finalize(const double* partials, int nblocks, double* out) {
+    __shared__ double red[256];
     const int width = GL_MAX_SPECIES * PO_N;
-    for (int k = threadIdx.x; k < width; k += blockDim.x) {
-        double a = 0.0;
-        for (int b = 0; b < nblocks; b++) {
-            const double v = partials[(size_t)b * width + k];
-            a = po_is_max(k % PO_N) ? fmax(a, v) : a + v;
-        }
-        out[k] = a;
+    const int k = blockIdx.x;
+    const bool mx = po_is_max(k % PO_N);
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const double v = partials[(size_t)b * width + k];
+        a = mx ? fmax(a, v) : a + v;
     }
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = mx ? fmax(red[threadIdx.x], red[threadIdx.x + o]) : red[threadIdx.x] + red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = red[0];
 }
 
 void launch_particle_obs(int prec, const void* parts, int64_t np, double t, uint32_t active_mask,
@@ -409,7 +413,7 @@ void launch_particle_obs(int prec, const void* parts, int64_t np, double t, uint
     else
         particle_obs_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(carve_parts<float>((void*)parts, np), t,
                                                                          active_mask, oa, partials);
-    particle_obs_finalize<<<1, 64, 0, st>>>(partials, (int)blocks, out);
+    particle_obs_finalize<<<GL_MAX_SPECIES * PO_N, 256, 0, st>>>(partials, (int)blocks, out);
 }
 
 }  // namespace gl

@@ -343,6 +343,23 @@ __device__ __forceinline__ A8<R> iah_of_mul_nd(const M3<R>& A, const M3<R>& B) {
     return x;
 }
 
+// cubic Casimir q3 = d_abc Q^a Q^b Q^c from the 16 independent nonzero
+// symmetric structure constants of SU(3) (Table II), each weighted by the
+// number of distinct index orderings
+template <typename R>
+__device__ __forceinline__ R casimir3(const A8<R>& q) {
+    const R s3 = inv_sqrt3<R>();  // 1/sqrt(3)
+    const R* Q = q.v;             // Q[0] = Q^1 ... Q[7] = Q^8
+    const R h = R(0.5);
+    R r = R(3) * s3 * (Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2]) * Q[7]    // d118, d228, d338
+        + R(6) * h * (Q[0] * Q[3] * Q[5] + Q[0] * Q[4] * Q[6]             // d146, d157
+                      - Q[1] * Q[3] * Q[6] + Q[1] * Q[4] * Q[5])          // d247, d256
+        + R(3) * h * Q[2] * (Q[3] * Q[3] + Q[4] * Q[4] - Q[5] * Q[5] - Q[6] * Q[6])  // d344 d355 d366 d377
+        - R(3) * h * s3 * (Q[3] * Q[3] + Q[4] * Q[4] + Q[5] * Q[5] + Q[6] * Q[6]) * Q[7]  // d448..d778
+        - s3 * Q[7] * Q[7] * Q[7];                                           // d888
+    return r;
+}
+
 // exp(i s X) for Hermitian traceless X = x^a T^a.  Cayley-Hamilton gives
 // X^3 = c1 X + c0 with c1 = tr(X^2)/2 and c0 = det X, so every power of iX
 // is a combination of 1, X, X^2; the exponential series is summed on those
