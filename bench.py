@@ -1,21 +1,26 @@
 """Benchmark of the coupled CPIC time step (Glasma leapfrog + Wong push).
 
-A step is one pass of the whole hot path over one event: the fused kernel
-(leapfrog step and site E/B interpolation) and the particle push kernel
-(gl_step_coupled).  The default workload is the 256x256 event (L = 10 fm,
-g^2 mu = 2 GeV, m = 0.2 GeV, Ns = 50, dtau = a/8) with 1e5 charm quarks
-(p_T = 0.5 GeV) and 1e5 static quarks, FP32 two-row links.
+A step is one pass of the whole hot path over every event of the batch: the
+fused field kernel (leapfrog step of Sec. 2 with the E/B interpolation of
+Sec. 3.2 to the sites) and the particle push (Wong equations with the CPIC
+colour rotation, Sec. 3).  The default workload is 30 events (the paper
+averages 30 MV events, Sec. 7.1) of the 256x256 configuration (L = 10 fm,
+g^2 mu = 2 GeV, m = 0.2 GeV, Ns = 50, dtau = a/8), each with 1e5 charm quarks
+(p_T = 0.5 GeV) and 1e5 static quarks, FP32 two-row links.  All events advance
+together: one field launch and one push launch per step, replayed from a CUDA
+graph, with the field step of t_s overlapping the push of t_{s-1}.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload NAME] [--precision fp32|fp64]
+                    [--workload NAME] [--precision fp32|fp64] [--events E]
 
-Under torchrun each rank runs its own event (seed + rank): events are
-independent, so the units shard with no data-path collective (weak scaling).
-Rank 0 prints one JSON line.
+Under torchrun each rank runs its own events (seeds offset by rank): events
+are independent, so they shard with no data-path collective (weak scaling);
+only the ensemble sums of the report are reduced.  Rank 0 prints one JSON
+line.
 """
 import argparse
+import ctypes
 import json
-import math
 import os
 import subprocess
 import sys
@@ -25,8 +30,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "lattice site-updates/s + particle-steps/s, % HBM peak; FP32 vs FP64 at stated error"
-L2_FLUSH_BYTES = 512 << 20   # written between timed steps (L2 is 129 MB)
-L2_CLEAN_BYTES = 256 << 20   # then read, so the written lines are evicted before the step starts
 
 
 def parse():
@@ -40,28 +43,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
     ap.add_argument("--reunit-every", type=int, default=None)
+    ap.add_argument("--events", type=int, default=0, help="events per GPU (default 30; 1 for n1024_mixed)")
     return ap.parse_args()
 
 
 BATCHED = "batched64"
 
-
-def workload(args, rank=0):
-    from paper_2303_05599_gb300 import workloads as W
-    if args.workload == BATCHED:
-        evs = W.config_batched_events()
-        for w in evs:
-            w.seed = w.seed + 64 * rank
-        return evs
-    w = W.WORKLOADS[args.workload]()
-    if args.reunit_every is not None:
-        w.reunit_every = args.reunit_every
-    if args.precision == "fp64":
-        w.precision = W.FP64
-    elif args.precision == "fp32":
-        w.precision = W.FP32_2ROW
-    w.seed = w.seed + rank
-    return w
+# DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by (workload, kernel, precision); see profiles/.  Absent: not captured
+# for the current kernels.
+TRAFFIC = {}
 
 
 def field_bytes_per_site(prec):
@@ -144,8 +135,9 @@ def cpu_baseline(w, ev, args):
                       ev.download(B.GL_BUF_PI))
     part = ev.download(B.GL_BUF_PARTICLES)
     ls = w.lattice_species()
+    obs = ev.observables()
     run = O.Run(st, part, [s[0] for s in ls], [s[1] for s in ls], [s.rep for s in w.species], w.dt,
-                step=args.warmup)
+                step=int(obs.step))
     k = args.cpu_sample_steps
     t0 = time.perf_counter()
     for _ in range(k):
@@ -157,44 +149,36 @@ def cpu_baseline(w, ev, args):
             "particle_steps_per_s": w.n_particles * k / dt}
 
 
-def run_batch(args, ws, dev, stream, world):
-    """64 MV events of N in {64, 128, 256} as one batch: one field launch and
-    one push launch per step, replayed from a CUDA graph; the working set
-    (about 1.2 GB) is far larger than L2, so no flush is needed."""
-    import torch
-    from paper_2303_05599_gb300 import _binding as B
-    batch = B.Batch(ws, stream=stream)
-    batch.init()
-    tune = batch.autotune()
-    batch.step(args.warmup)
-    K = args.steps
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(dev.index or 0)
-    clocks.start()
-    e0.record(stream)
-    batch.step(K)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ck = clocks.stop()
-    t_step = e0.elapsed_time(e1) / 1e3
-    # per-kernel split from separately timed replays of each launch shape
-    sites = sum(w.N * w.N for w in ws)
-    obs = batch.observables()
-    n_active = sum(sum(o.n_active[k] for k in range(o.n_species)) for o in obs)
-    t0 = time.perf_counter()
-    for _ in range(K):
-        batch.step(1)
-        batch.observables()
-    e2e_t = time.perf_counter() - t0
-    return batch, tune, t_step, e2e_t, sites, n_active, ck
+def events_for(args, rank):
+    """The events one rank runs: `--events` replicas of a single-event
+    workload (the paper averages 30 events, Sec. 7.1), or the 64 uneven events
+    of the batched workload."""
+    from paper_2303_05599_gb300 import workloads as W
+    if args.workload == BATCHED:
+        evs = W.config_batched_events()
+        for w in evs:
+            w.seed = w.seed + 64 * rank
+        return evs
+    n = args.events if args.events else (1 if args.workload == "n1024_mixed" else 30)
+    evs = []
+    for e in range(n):
+        w = W.WORKLOADS[args.workload]()
+        if args.reunit_every is not None:
+            w.reunit_every = args.reunit_every
+        if args.precision == "fp64":
+            w.precision = W.FP64
+        elif args.precision == "fp32":
+            w.precision = W.FP32_2ROW
+        w.seed = rank * n + e
+        evs.append(w)
+    return evs
 
 
 def run_ours(args):
     import torch
     import torch.distributed as dist
     from paper_2303_05599_gb300 import _binding as B
+    from paper_2303_05599_gb300 import multi
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -203,7 +187,6 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-
     import __graft_entry__
     if rank == 0 or world == 1:
         __graft_entry__.build()
@@ -211,102 +194,87 @@ def run_ours(args):
         dist.barrier()
     B.lib()
 
-    w = workload(args, rank)
+    ws = events_for(args, rank)
+    K = args.steps
     stream = torch.cuda.Stream(device=dev)
-    if args.workload == BATCHED:
-        with torch.cuda.stream(stream):
-            batch, tune, t_step, e2e_t, sites, n_active, ck = run_batch(args, w, dev, stream, world)
-        emit_batch(args, w, tune, t_step, e2e_t, sites, n_active, ck, world, rank)
-        if world > 1:
-            dist.barrier()
-            dist.destroy_process_group()
-        return
     with torch.cuda.stream(stream):
-        ev = B.Event(w, stream=stream)
-        ev.glasma_init()
-        ev.wong_init()
-        tune = ev.autotune()
-        for _ in range(args.warmup):
-            ev.glasma_step(1)
-            ev.wong_push()
-        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-        clean = torch.ones(L2_CLEAN_BYTES // 4, dtype=torch.float32, device=dev)
-        K = args.steps
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+        batch = B.Batch(ws, stream=stream)
+        batch.init()
+        tune = batch.autotune()
+        batch.step(args.warmup)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         clocks = ClockSampler(local)
         clocks.start()
-        wall0 = time.perf_counter()
-        for k in range(K):
-            # L2 flush between timed steps, outside the step's events: write a
-            # buffer larger than L2, then read another one so that no dirty line
-            # of the flush is left for the timed kernels to write back
-            flush.zero_()
-            clean.sum()
-            e = evs[k]
-            e[0].record(stream)
-            ev.glasma_step(1)      # fused leapfrog + site E, B kernel
-            e[1].record(stream)
-            ev.wong_push()         # push kernel
-            e[2].record(stream)
+        e0.record(stream)
+        batch.step(K)                      # K coupled steps: CUDA-graph replays
+        e1.record(stream)
         torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         ck = clocks.stop()
-        field_each = sorted(e[0].elapsed_time(e[1]) for e in evs)
-        t_field = sum(e[0].elapsed_time(e[1]) for e in evs) / 1e3
-        t_push = sum(e[1].elapsed_time(e[2]) for e in evs) / 1e3
-        t_step = t_field + t_push
-        obs = ev.observables()
-        n_active = sum(obs.n_active[k] for k in range(len(w.species)))
-
-        # end to end through the public API: coupled step + observables read back every step
+        t_step = e0.elapsed_time(e1) / 1e3
+        # per-kernel durations: the same K steps with events around every launch
+        f_ms, p_ms = batch.step_timed(K)
+        obs = batch.observables()
+        # end to end through the public API: every event's state (the fields of
+        # one time slice and the particles) uploaded from pinned host memory,
+        # then K steps with the observables of every event read back each step
+        host = []
+        for ev in batch.events:
+            bufs = {}
+            for which in (B.GL_BUF_LINKS, B.GL_BUF_PHI, B.GL_BUF_E, B.GL_BUF_PI, B.GL_BUF_PARTICLES):
+                a = ev.download(which)
+                t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+                t.numpy()[...] = a
+                bufs[which] = t
+            host.append(bufs)
+        h2d = sum(t.numel() * 8 for bufs in host for t in bufs.values())
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
+        for ev, bufs in zip(batch.events, host):
+            for which, t in bufs.items():
+                ev.upload(which, t.numpy())
         for _ in range(K):
-            ev.step(1)
-            ev.observables()
+            batch.step(1)
+            batch.observables()
+        torch.cuda.synchronize()
         e2e_t = time.perf_counter() - t0
 
-    tt = torch.tensor([t_step, e2e_t, float(n_active)], dtype=torch.float64, device=dev)
+    n_species = len(ws[0].species)
+    ens = multi.ensemble_reduce(obs, n_species)  # report-time reduction over every rank's events
+    sites = sum(w.N * w.N for w in ws)
+    n_active = sum(sum(o.n_active[k] for k in range(o.n_species)) for o in obs)
+    tt = torch.tensor([t_step, e2e_t], dtype=torch.float64, device=dev)
     if world > 1:
-        mx = tt.clone()
-        dist.all_reduce(mx[:2], op=dist.ReduceOp.MAX)
-        sm = tt.clone()
-        dist.all_reduce(sm[2:], op=dist.ReduceOp.SUM)
-        t_step, e2e_t, n_active_all = float(mx[0]), float(mx[1]), float(sm[2])
-    else:
-        n_active_all = float(n_active)
-    V = w.N * w.N
-    value = world * V * K / t_step
-    # report-time ensemble average over every rank's event (outside the timed region)
-    from paper_2303_05599_gb300 import multi
-    ens = multi.ensemble_reduce([obs], len(w.species))
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    t_step, e2e_t = float(tt[0]), float(tt[1])
     line = None
     if rank == 0:
-        import json as _json
-        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         hbm = peaks.get("hbm_gbs", 6800.0)
         peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+        prec = ws[0].precision
         kern = {
-            "field_step": (field_bytes_per_site(w.precision) * V, t_field / K),
-            "wong_push": (push_bytes(w.precision, n_active, V), t_push / K),
+            "field_step": (field_bytes_per_site(prec) * sites, f_ms / 1e3 / K),
+            "wong_push": (push_bytes(prec, n_active, sites), p_ms / 1e3 / K),
         }
-        dom = max(kern, key=lambda k: kern[k][1])
         roof = {}
         for name, (b, t) in kern.items():
             roof[name] = {"bound": "hbm", "achieved": b / t / 1e9, "peak": hbm, "unit": "GB/s",
-                          "frac": b / t / 1e9 / hbm, "traffic": None, "bytes_per_launch": b, "us_per_launch": t * 1e6,
-                          "peak_source": peak_src}
-        dtype = "f64" if w.precision == 0 else "f32"
+                          "frac": b / t / 1e9 / hbm, "traffic": TRAFFIC.get((args.workload, name, prec)),
+                          "bytes_per_launch": b, "us_per_launch": t * 1e6, "peak_source": peak_src}
+        dom = max(kern, key=lambda k: kern[k][1])
+        single = args.workload != BATCHED
         line = {
             "metric": METRIC,
-            "value": value,
+            "value": world * sites * K / t_step,
             "unit": "site-updates/s",
             "n_gpus": world,
             "steps": K,
@@ -315,73 +283,36 @@ def run_ours(args):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": dtype,
+            "dtype": "f64" if prec == 0 else "f32",
             "data": "synthetic: MV events generated on the GPU from Philox seeds, Haar-random charges",
-            "config": {"workload": w.name, "N": w.N, "L_fm": w.L_fm, "particles": w.n_particles,
-                       "precision": "fp32_2row" if w.precision else "fp64", "dtau_over_a": w.dtau_over_a,
-                       "events_per_gpu": 1, "parallelism": "events sharded over ranks",
-                       "l2": "flushed between timed steps (512 MiB write, then 256 MiB read), outside the step's events"},
-            "particle_steps_per_s": n_active_all * K / t_step,
-            "ensemble": {"tau_fm": obs.tau_fm, "per_species": ens},
-            "kernel_ms_per_step": {"field_step": t_field / K * 1e3, "wong_push": t_push / K * 1e3},
-            "field_step_ms_min_median_max": [field_each[0], field_each[K // 2], field_each[-1]],
+            "config": {"workload": args.workload + (" x %d events" % len(ws) if single else ""),
+                       "events_per_gpu": len(ws), "N": ws[0].N if single else "64/128/256 by event",
+                       "sites_per_gpu": sites, "particles_per_gpu": sum(w.n_particles for w in ws),
+                       "precision": "fp32_2row" if prec else "fp64", "dtau_over_a": ws[0].dtau_over_a,
+                       "reunit_every": ws[0].reunit_every, "parallelism": "events sharded over ranks",
+                       "l2": "per-step working set larger than L2 (no flush)",
+                       "launch": "one CUDA-graph replay per step: field step s overlapped with the push of s-1"},
+            "particle_steps_per_s": world * n_active * K / t_step,
+            "ensemble": {"tau_fm": obs[0].tau_fm, "per_species": ens},
+            "kernel_ms_per_step": {"field_step": f_ms / K, "wong_push": p_ms / K},
             "autotune": tune,
             "roofline": dict(roof[dom], kernel=dom),
             "roofline_kernels": roof,
-            "e2e": {"value": world * V * K / e2e_t, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 8 * (8 * 7 + 7),
-                    "includes": "gl_step_coupled + observables() read back to the host every step, wall clock; "
-                                "the step's inputs are the device-resident state"},
-            "gpu_launches": 2 * K,
+            "e2e": {"value": world * sites * K / e2e_t, "unit": "site-updates/s",
+                    "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": len(ws) * ctypes.sizeof(B.gl_obs),
+                    "includes": "gl_upload of every event's fields and particles from pinned host memory "
+                                "(FP64 canonical layout), then K x (gl_batch_step(1) + gl_batch_observables "
+                                "read back to the host)"},
+            "gpu_launches": 3 * K,
             "clocks": ck,
-            "wall_s_timed_loop": wall,
         }
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(w, ev, args)
+            line["cpu_baseline"] = cpu_baseline(ws[0], batch.events[0], args)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     if line is not None:
         print(json.dumps(line))
-
-
-def emit_batch(args, ws, tune, t_step, e2e_t, sites, n_active, ck, world, rank):
-    import torch
-    import torch.distributed as dist
-    K = args.steps
-    if world > 1:
-        t = torch.tensor([t_step, e2e_t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step, e2e_t = float(t[0]), float(t[1])
-    if rank != 0:
-        return
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    prec = ws[0].precision
-    step_bytes = field_bytes_per_site(prec) * sites + push_bytes(prec, n_active, sites)
-    line = {
-        "metric": METRIC, "value": world * sites * K / t_step, "unit": "site-updates/s", "n_gpus": world,
-        "steps": K, "warmup": args.warmup, "ms_per_step": t_step / K * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32",
-        "data": "synthetic: MV events generated on the GPU from Philox seeds, Haar-random charges",
-        "config": {"workload": BATCHED, "events_per_gpu": len(ws), "N": "64/128/256 by event", "a_fm": 0.04,
-                   "sites_per_gpu": sites, "particles_per_gpu": sum(w.n_particles for w in ws),
-                   "precision": "fp32_2row" if prec else "fp64", "parallelism": "events sharded over ranks",
-                   "l2": "working set (~1.2 GB per step) larger than L2, no flush",
-                   "launch": "one CUDA graph replay per step (field, push, clock tick)"},
-        "particle_steps_per_s": world * n_active * K / t_step,
-        "autotune": tune,
-        "roofline": {"bound": "hbm", "achieved": step_bytes / (t_step / K) / 1e9, "peak": hbm, "unit": "GB/s",
-                     "frac": step_bytes / (t_step / K) / 1e9 / hbm, "traffic": None, "kernel": "whole batched step",
-                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
-        "e2e": {"value": world * sites * K / e2e_t, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": len(ws) * 8 * (8 * 7 + 7),
-                "includes": "gl_batch_step + observables of every event read back each step"},
-        "gpu_launches": 3 * K,
-        "clocks": ck,
-    }
-    print(json.dumps(line))
 
 
 def run_reference(args):
@@ -395,7 +326,8 @@ def run_reference(args):
     import oracle as O
     from oracle import build as ob
     ob.build()
-    w = workload(args, 0)
+    evs = events_for(args, 0)
+    w = evs[0]
     st, bad = O.mv_init(w.N, w.Ns, w.g2mu_a, w.m_a, w.Lambda_a, w.seed)
     ls = w.lattice_species()
     part = np.concatenate([O.sample_species(w.N, w.seed, k, s.rep, s.mom_mode, ls[k][2], ls[k][3], s.count)
@@ -413,11 +345,13 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic: oracle MV event and particles",
-        "config": {"workload": w.name, "N": w.N, "particles": w.n_particles,
-                   "precision": "fp64 oracle (CPU)"},
+        "config": {"workload": args.workload + (" x %d events" % len(evs) if args.workload != BATCHED else ""),
+                   "N": w.N, "particles": w.n_particles, "precision": "fp64 oracle (CPU)"},
         "particle_steps_per_s": w.n_particles * args.steps / dt,
         "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": O.threads(), "kind": "oracle",
-                         "sample": "%d coupled steps of the full lattice with all particles" % args.steps},
+                         "sample": "event 0 of the workload (%dx%d, %d particles): %d coupled steps of the full "
+                                   "lattice with all particles after %d warm-up steps" % (
+                                       w.N, w.N, w.n_particles, args.steps, args.warmup)},
         "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

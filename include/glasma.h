@@ -200,7 +200,8 @@ gl_status observables(gl_ctx* ctx, gl_obs* out);
  * events, Sec. 7.1), possibly of different N, advanced together: one coupled
  * step of the whole batch is one field launch over the tiles of every event
  * and one push launch over the particles of every event, captured once in a
- * CUDA graph and replayed.  All events share the precision, the time step
+ * CUDA graph and replayed; the field launch of step s runs concurrently with
+ * the push of step s - 1 on a second stream.  All events share the precision, the time step
  * dtau/a and the re-unitarisation period; they start at tau = 0 together.
  * The events' particles are sorted by cell when sampled or uploaded; the
  * batch step does not re-sort them. */
@@ -235,6 +236,11 @@ gl_status gl_batch_tuning(const gl_batch* batch, float* field_ms, float* push_ms
 
 /* n_steps coupled steps of every event (all events at one common step). */
 gl_status gl_batch_step(gl_batch* batch, int32_t n_steps);
+
+/* The same n_steps with direct launches and CUDA events around every field
+ * and push launch; field_ms and push_ms receive the summed kernel durations
+ * (waits).  For measurement. */
+gl_status gl_batch_step_timed(gl_batch* batch, int32_t n_steps, double* field_ms, double* push_ms);
 
 /* observables() of every event into out[n_events] (waits). */
 gl_status gl_batch_observables(gl_batch* batch, gl_obs* out);

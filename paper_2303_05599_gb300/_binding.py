@@ -81,6 +81,7 @@ SIGNATURES = {
     "gl_batch_autotune": (ctypes.c_int, [_P, _P, _P]),
     "gl_batch_tuning": (ctypes.c_int, [_P, _P, _P]),
     "gl_batch_step": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "gl_batch_step_timed": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "gl_batch_observables": (ctypes.c_int, [_P, _P]),
 }
 
@@ -294,6 +295,13 @@ class Batch:
 
     def step(self, n=1):
         self._chk(lib().gl_batch_step(self.b, n), "gl_batch_step")
+
+    def step_timed(self, n):
+        """n steps with per-kernel CUDA events; returns (field_ms, push_ms) summed."""
+        f = ctypes.c_double()
+        p = ctypes.c_double()
+        self._chk(lib().gl_batch_step_timed(self.b, n, ctypes.byref(f), ctypes.byref(p)), "gl_batch_step_timed")
+        return f.value, p.value
 
     def observables(self):
         out = (gl_obs * self.ne)()

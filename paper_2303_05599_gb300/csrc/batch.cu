@@ -1,9 +1,11 @@
 // Many independent MV events of uneven N advanced together (the paper
 // averages observables over many events, Sec. 7.1).  One coupled step of the
-// whole batch is three launches captured once in a CUDA graph and replayed:
-//   fused leapfrog + site E/B over the tiles of every event,
-//   Wong push over the particles of every event,
-//   a one-thread tick of the device-resident step counter.
+// whole batch is captured once in a CUDA graph and replayed:
+//   fused leapfrog + site E/B over the tiles of every event (step s), and
+//   concurrently on a second stream the Wong push over the particles of
+//   every event (step s - 1: it reads the site fields of t_{s-1} and the
+//   links of t_s, neither of which the field step of s writes),
+//   then a one-thread tick of the device-resident step counter.
 // The kernels read the step index n from device memory, so the captured
 // graph is valid for every step.  Each block finds its event by binary search
 // in a prefix table of tiles or particle chunks.
@@ -29,7 +31,7 @@ static constexpr int PUSH_CHUNK = 1024;  // particles per push block
 
 struct EvDesc {
     void* field[2];
-    void* site;
+    void* site[2];   // site fields of t_n in site[n & 1]
     void* parts;
     int N;
     int tiles_x;     // for the chosen tile shape
@@ -73,16 +75,17 @@ __global__ void __launch_bounds__(TX * TY) batch_field_kernel(BatchArgs b) {
     const int reunit = b.reunit_every > 0 && (n + 1) % b.reunit_every == 0;
     const StepArgs a = step_args(d.N, d.tiles_x, n, b.dt, reunit);
     fused_tile<R, TX, TY, true>(carve_fields<R>(d.field[n & 1], Vn), carve_fields<R>(d.field[(n + 1) & 1], Vn),
-                                (typename Prec<R>::V*)d.site, a, blockIdx.x - d.tile_begin);
+                                (typename Prec<R>::V*)d.site[n & 1], a, blockIdx.x - d.tile_begin);
 }
 
+// push of the particles at t_{clock - lag}
 template <typename R>
-__global__ void batch_push_kernel(BatchArgs b) {
+__global__ void batch_push_kernel(BatchArgs b, int lag) {
     __shared__ int s_e;
     if (threadIdx.x == 0) s_e = find_event(b.ev, b.ne, blockIdx.x, false);
     __syncthreads();
     const EvDesc& d = b.ev[s_e];
-    const int64_t n = *b.clock;
+    const int64_t n = *b.clock - lag;
     const double t = n * b.dt;
     uint32_t active = 0;
     SpeciesArgs<R> sa;
@@ -97,8 +100,8 @@ __global__ void batch_push_kernel(BatchArgs b) {
     const int64_t base = (int64_t)(blockIdx.x - d.chunk_begin) * PUSH_CHUNK;
     const int64_t end = base + PUSH_CHUNK < d.np ? base + PUSH_CHUNK : d.np;
     for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x)
-        push_one<R>((const typename Prec<R>::V*)d.site, bn1, P, i, d.N, (R)t, (R)b.dt, (R)(t > 0 ? b.dt / t : 0.0),
-                    active, sa);
+        push_one<R>((const typename Prec<R>::V*)d.site[n & 1], bn1, P, i, d.N, (R)t, (R)b.dt,
+                    (R)(t > 0 ? b.dt / t : 0.0), active, sa);
 }
 
 __global__ void tick_kernel(int64_t* clock) { *clock += 1; }
@@ -141,6 +144,8 @@ struct gl_batch {
     double dt;
     int reunit_every;
     cudaStream_t stream;
+    cudaStream_t aux;      // push stream of the overlapped step
+    cudaEvent_t ev_a, ev_b;
     gl_ctx** ev;
     EvDesc* h_desc;
     EvDesc* d_desc;
@@ -161,7 +166,7 @@ struct gl_batch {
 namespace gl {
 struct CtxView {
     void* field[2];
-    void* site;
+    void* site[2];
     void* parts;
     int N, prec, cur;
     int64_t step, pstep, np;
@@ -176,6 +181,7 @@ struct CtxView {
 void ctx_view(const gl_ctx* c, CtxView* v);
 void ctx_advance(gl_ctx* c, int64_t steps);
 size_t ctx_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t ns);
+gl_status ctx_observables_many(gl_ctx** cs, int n, gl_obs* out);
 }  // namespace gl
 
 static size_t a256b(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -247,6 +253,12 @@ gl_status gl_batch_create(const gl_config* cfgs, const gl_species* species, int3
 
 gl_status gl_batch_destroy(gl_batch* b) {
     if (!b) return GL_ERR_ARG;
+    if (b->aux) {
+        cudaStreamSynchronize(b->aux);
+        cudaEventDestroy(b->ev_a);
+        cudaEventDestroy(b->ev_b);
+        cudaStreamDestroy(b->aux);
+    }
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (int e = 0; e < b->ne; e++) gl_destroy(b->ev[e]);
@@ -290,7 +302,8 @@ static gl_status sync_desc(gl_batch* b) {
         memset(&d, 0, sizeof d);
         d.field[0] = v.field[0];
         d.field[1] = v.field[1];
-        d.site = v.site;
+        d.site[0] = v.site[0];
+        d.site[1] = v.site[1];
         d.parts = v.parts;
         d.N = v.N;
         d.tiles_x = (v.N + TX - 1) / TX;
@@ -314,16 +327,28 @@ static gl_status sync_desc(gl_batch* b) {
     return cudaGetLastError() == cudaSuccess ? GL_OK : bfail(b, GL_ERR_CUDA, "descriptor upload failed");
 }
 
-static void enqueue_step(gl_batch* b, int tile, int push_block, bool tick) {
+static void launch_field(gl_batch* b, cudaStream_t st) {
     BatchArgs a{b->d_desc, b->ne, b->dt, b->reunit_every, b->d_clock};
-    if (b->prec == GL_FP64) {
-        launch_batch_field<double>(tile, b->field_blocks, a, b->stream);
-        batch_push_kernel<double><<<b->push_blocks, push_block, 0, b->stream>>>(a);
-    } else {
-        launch_batch_field<float>(tile, b->field_blocks, a, b->stream);
-        batch_push_kernel<float><<<b->push_blocks, push_block, 0, b->stream>>>(a);
-    }
-    if (tick) tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock);
+    if (b->prec == GL_FP64) launch_batch_field<double>(b->tile, b->field_blocks, a, st);
+    else launch_batch_field<float>(b->tile, b->field_blocks, a, st);
+}
+
+static void launch_push(gl_batch* b, int lag, cudaStream_t st) {
+    BatchArgs a{b->d_desc, b->ne, b->dt, b->reunit_every, b->d_clock};
+    if (b->prec == GL_FP64) batch_push_kernel<double><<<b->push_blocks, b->push_block, 0, st>>>(a, lag);
+    else batch_push_kernel<float><<<b->push_blocks, b->push_block, 0, st>>>(a, lag);
+}
+
+// one overlapped step at clock s: the field step of t_s on the main stream
+// and the push of the particles at t_{s-1} on the second stream, then the tick
+static void enqueue_overlap_step(gl_batch* b) {
+    cudaEventRecord(b->ev_a, b->stream);
+    cudaStreamWaitEvent(b->aux, b->ev_a, 0);
+    launch_push(b, 1, b->aux);
+    cudaEventRecord(b->ev_b, b->aux);
+    launch_field(b, b->stream);
+    cudaStreamWaitEvent(b->stream, b->ev_b, 0);
+    tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock);
 }
 
 gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_out) {
@@ -385,8 +410,8 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
             float ms = 0;
             for (int rep = 0; rep < 4; rep++) {
                 cudaEventRecord(e0, b->stream);
-                if (b->prec == GL_FP64) batch_push_kernel<double><<<b->push_blocks, PUSH_BLOCKS[k], 0, b->stream>>>(a);
-                else batch_push_kernel<float><<<b->push_blocks, PUSH_BLOCKS[k], 0, b->stream>>>(a);
+                if (b->prec == GL_FP64) batch_push_kernel<double><<<b->push_blocks, PUSH_BLOCKS[k], 0, b->stream>>>(a, 0);
+                else batch_push_kernel<float><<<b->push_blocks, PUSH_BLOCKS[k], 0, b->stream>>>(a, 0);
                 cudaEventRecord(e1, b->stream);
                 cudaEventSynchronize(e1);
                 float m;
@@ -409,19 +434,27 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
     return cudaGetLastError() == cudaSuccess ? GL_OK : bfail(b, GL_ERR_CUDA, "autotune launch failed");
 }
 
+// n coupled steps: the field step of t_s (all events) alone, then n - 1
+// replays of the captured overlapped step, then the last push alone
 gl_status gl_batch_step(gl_batch* b, int32_t n_steps) {
     if (!b || n_steps < 0) return GL_ERR_ARG;
     if (n_steps == 0) return GL_OK;
     if (gl_status s = sync_desc(b)) return s;
-    // (re)capture the one-step graph when the launch shapes changed
+    if (!b->aux) {
+        if (cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_a, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_b, cudaEventDisableTiming) != cudaSuccess)
+            return bfail(b, GL_ERR_CUDA, "stream creation failed");
+    }
+    if (b->prec == GL_FP64) set_smem_attr<double, 32, 4>();
+    else { set_smem_attr<float, 32, 8>(); set_smem_attr<float, 32, 4>(); }
+    // (re)capture the overlapped step when the launch shapes changed
     if (!b->exec || b->graph_tile != b->tile || b->graph_push_block != b->push_block) {
         if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
         if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
-        if (b->prec == GL_FP64) set_smem_attr<double, 32, 4>();
-        else { set_smem_attr<float, 32, 8>(); set_smem_attr<float, 32, 4>(); }
         if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return bfail(b, GL_ERR_CUDA, "stream capture could not start (the default stream cannot be captured)");
-        enqueue_step(b, b->tile, b->push_block, true);
+        enqueue_overlap_step(b);
         if (cudaStreamEndCapture(b->stream, &b->graph) != cudaSuccess ||
             cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) {
             cudaGetLastError();
@@ -430,17 +463,73 @@ gl_status gl_batch_step(gl_batch* b, int32_t n_steps) {
         b->graph_tile = b->tile;
         b->graph_push_block = b->push_block;
     }
-    for (int k = 0; k < n_steps; k++) cudaGraphLaunch(b->exec, b->stream);
-    if (cudaGetLastError() != cudaSuccess) return bfail(b, GL_ERR_CUDA, "graph launch failed");
+    launch_field(b, b->stream);
+    tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock);
+    for (int k = 1; k < n_steps; k++) cudaGraphLaunch(b->exec, b->stream);
+    launch_push(b, 1, b->stream);
+    if (cudaGetLastError() != cudaSuccess) return bfail(b, GL_ERR_CUDA, "batch step launch failed");
+    for (int e = 0; e < b->ne; e++) ctx_advance(b->ev[e], n_steps);
+    return GL_OK;
+}
+
+// the same schedule as gl_batch_step with direct launches and CUDA events
+// around every field and push launch on their streams; returns the summed
+// kernel durations (waits)
+gl_status gl_batch_step_timed(gl_batch* b, int32_t n_steps, double* field_ms, double* push_ms) {
+    if (!b || n_steps < 1) return GL_ERR_ARG;
+    if (gl_status s = sync_desc(b)) return s;
+    if (!b->aux) {
+        if (cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_a, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_b, cudaEventDisableTiming) != cudaSuccess)
+            return bfail(b, GL_ERR_CUDA, "stream creation failed");
+    }
+    const int ne = 4 * n_steps;
+    cudaEvent_t* ev = new (std::nothrow) cudaEvent_t[ne];
+    if (!ev) return GL_ERR_ARG;
+    for (int k = 0; k < ne; k++) cudaEventCreate(&ev[k]);
+    // events 4k, 4k+1 bracket the field launch of step k; 4k+2, 4k+3 the push of step k
+    cudaEventRecord(ev[0], b->stream);
+    launch_field(b, b->stream);
+    cudaEventRecord(ev[1], b->stream);
+    tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock);
+    for (int k = 1; k < n_steps; k++) {
+        cudaEventRecord(b->ev_a, b->stream);
+        cudaStreamWaitEvent(b->aux, b->ev_a, 0);
+        cudaEventRecord(ev[4 * (k - 1) + 2], b->aux);
+        launch_push(b, 1, b->aux);
+        cudaEventRecord(ev[4 * (k - 1) + 3], b->aux);
+        cudaEventRecord(b->ev_b, b->aux);
+        cudaEventRecord(ev[4 * k], b->stream);
+        launch_field(b, b->stream);
+        cudaEventRecord(ev[4 * k + 1], b->stream);
+        cudaStreamWaitEvent(b->stream, b->ev_b, 0);
+        tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock);
+    }
+    cudaEventRecord(ev[4 * (n_steps - 1) + 2], b->stream);
+    launch_push(b, 1, b->stream);
+    cudaEventRecord(ev[4 * (n_steps - 1) + 3], b->stream);
+    cudaStreamSynchronize(b->stream);
+    double f = 0, p = 0;
+    for (int k = 0; k < n_steps; k++) {
+        float a = 0, c = 0;
+        cudaEventElapsedTime(&a, ev[4 * k], ev[4 * k + 1]);
+        cudaEventElapsedTime(&c, ev[4 * k + 2], ev[4 * k + 3]);
+        f += a;
+        p += c;
+    }
+    for (int k = 0; k < ne; k++) cudaEventDestroy(ev[k]);
+    delete[] ev;
+    if (field_ms) *field_ms = f;
+    if (push_ms) *push_ms = p;
+    if (cudaGetLastError() != cudaSuccess) return bfail(b, GL_ERR_CUDA, "timed batch step failed");
     for (int e = 0; e < b->ne; e++) ctx_advance(b->ev[e], n_steps);
     return GL_OK;
 }
 
 gl_status gl_batch_observables(gl_batch* b, gl_obs* out) {
     if (!b || !out) return GL_ERR_ARG;
-    for (int e = 0; e < b->ne; e++)
-        if (gl_status s = observables(b->ev[e], &out[e])) return s;
-    return GL_OK;
+    return ctx_observables_many(b->ev, b->ne, out);
 }
 
 gl_status gl_batch_tuning(const gl_batch* b, float* field_ms, float* push_ms) {

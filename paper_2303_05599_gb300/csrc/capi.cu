@@ -36,10 +36,12 @@ struct gl_ctx {
     double q0[2][8];
     double q2ref[GL_MAX_SPECIES], q3ref[GL_MAX_SPECIES];
     cudaStream_t stream;
+    cudaStream_t aux;   // push stream of the overlapped coupled step (created on first use)
+    cudaEvent_t ev_f, ev_p;
     char* ws;
     size_t ws_bytes;
     void* field[2];
-    void* site;
+    void* site_buf[2];  // site fields at t_n live in site_buf[n & 1]
     void* parts;
     void* parts_alt;    // second particle buffer for the cell sort
     void* sort_scratch;
@@ -60,6 +62,14 @@ struct gl_ctx {
 };
 
 static char g_create_err[256] = "";
+
+// site-field buffer of time t_n
+static inline void* site_at(const gl_ctx* c, int64_t n) { return c->site_buf[n & 1]; }
+
+extern "C" {
+static void observables_launch(gl_ctx* c);
+static gl_status observables_read(gl_ctx* c, gl_obs* o);
+}
 
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -109,7 +119,7 @@ static Carve carve(const gl_config* cfg, int64_t np) {
     Carve c;
     size_t o = 0;
     c.field = o; o += 2 * a256(field_bytes(prec, Vn));
-    c.site = o; o += a256(site_bytes(prec, Vn));
+    c.site = o; o += 2 * a256(site_bytes(prec, Vn));
     c.parts = o; o += a256(particle_bytes(prec, np));
     const bool sorting = cfg->sort_every > 0 && np > 0 && sort_supported(Vn);
     c.parts_alt = o; o += sorting ? a256(particle_bytes(prec, np)) : 0;
@@ -144,7 +154,7 @@ namespace gl {
 // read-only view of a context for the batch (batch.cu)
 struct CtxView {
     void* field[2];
-    void* site;
+    void* site[2];
     void* parts;
     int N, prec, cur;
     int64_t step, pstep, np;
@@ -159,7 +169,8 @@ struct CtxView {
 void ctx_view(const gl_ctx* c, CtxView* v) {
     v->field[0] = c->field[0];
     v->field[1] = c->field[1];
-    v->site = c->site;
+    v->site[0] = c->site_buf[0];
+    v->site[1] = c->site_buf[1];
     v->parts = c->parts;
     v->N = c->N;
     v->prec = c->prec;
@@ -188,6 +199,13 @@ void ctx_advance(gl_ctx* c, int64_t steps) {
 }
 size_t ctx_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t ns) {
     return gl_workspace_bytes(cfg, sp, ns);
+}
+// observables of many contexts with one wait (used by the batch)
+gl_status ctx_observables_many(gl_ctx** cs, int n, gl_obs* out) {
+    for (int e = 0; e < n; e++) ::observables_launch(cs[e]);
+    for (int e = 0; e < n; e++)
+        if (gl_status s = ::observables_read(cs[e], &out[e])) return s;
+    return GL_OK;
 }
 }  // namespace gl
 
@@ -230,7 +248,8 @@ gl_status gl_create(const gl_config* cfg, const gl_species* sp, int32_t ns, void
     c->ws_bytes = bytes;
     c->field[0] = c->ws + cv.field;
     c->field[1] = c->ws + cv.field + a256(field_bytes(c->prec, c->Vn));
-    c->site = c->ws + cv.site;
+    c->site_buf[0] = c->ws + cv.site;
+    c->site_buf[1] = c->ws + cv.site + a256(site_bytes(c->prec, c->Vn));
     c->parts = c->ws + cv.parts;
     c->sort_ok = cfg->sort_every > 0 && c->np > 0 && sort_supported(c->Vn);
     c->parts_alt = c->sort_ok ? c->ws + cv.parts_alt : nullptr;
@@ -274,6 +293,12 @@ gl_status gl_create(const gl_config* cfg, const gl_species* sp, int32_t ns, void
 
 gl_status gl_destroy(gl_ctx* c) {
     if (!c) return GL_ERR_ARG;
+    if (c->aux) {
+        cudaStreamSynchronize(c->aux);
+        cudaEventDestroy(c->ev_f);
+        cudaEventDestroy(c->ev_p);
+        cudaStreamDestroy(c->aux);
+    }
     delete c;
     return GL_OK;
 }
@@ -301,6 +326,7 @@ gl_status glasma_init(gl_ctx* c) {
     if (!c) return GL_ERR_ARG;
     launch_mv_init(c->prec, c->field[c->cur], c->scratch, c->N, c->cfg.Ns, c->g2mu_a, c->m_a, c->Lambda_a,
                    c->cfg.seed, c->d_bad, c->stream);
+    for (int k = 0; k < 2; k++) cudaMemsetAsync(c->site_buf[k], 0, site_bytes(c->prec, c->Vn), c->stream);
     if (gl_status s = check_cuda(c, "glasma_init")) return s;
     int bad = 0;
     cudaMemcpyAsync(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
@@ -349,7 +375,7 @@ static gl_status transfer(gl_ctx* c, gl_buffer which, double* host, size_t count
         launch_parts_convert(c->prec, c->parts, c->np, stg, to_device, c->stream);
         if (to_device) sort_particles(c);
     }
-    else launch_convert(c->prec, which, to_device, which == GL_BUF_SITE ? c->site : c->field[c->cur], stg, c->N, c->np,
+    else launch_convert(c->prec, which, to_device, which == GL_BUF_SITE ? site_at(c, c->pstep - 1) : c->field[c->cur], stg, c->N, c->np,
                         c->stream);
     if (!to_device) cudaMemcpyAsync(host, stg, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (gl_status s = check_cuda(c, to_device ? "gl_upload" : "gl_download")) return s;
@@ -372,16 +398,16 @@ gl_status gl_set_step(gl_ctx* c, int64_t step) {
     return GL_OK;
 }
 
-// One leapfrog step.  When the particles are at the fields' time the same
-// kernel also interpolates E, B at that time for the push that follows.
-static void one_field_step(gl_ctx* c, bool site) {
+// One leapfrog step on stream st.  When the particles are at the fields'
+// time the same kernel also interpolates E, B at that time for the push.
+static void one_field_step(gl_ctx* c, bool site, cudaStream_t st) {
     int reunit = 0;
     if (c->prec == GL_FP32_2ROW && c->cfg.reunit_every > 0) {
         if (++c->reunit_count >= c->cfg.reunit_every) { reunit = 1; c->reunit_count = 0; }
     }
     site = site && c->pstep == c->step;
-    launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], site ? c->site : nullptr, c->N, c->step, c->dt,
-                      reunit, c->tile, c->stream);
+    launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], site ? site_at(c, c->step) : nullptr, c->N,
+                      c->step, c->dt, reunit, c->tile, st);
     if (site) c->site_step = c->pstep;
     c->cur = 1 - c->cur;
     c->step++;
@@ -389,13 +415,14 @@ static void one_field_step(gl_ctx* c, bool site) {
 
 gl_status glasma_step(gl_ctx* c, int32_t n) {
     if (!c || n < 0) return GL_ERR_ARG;
-    for (int k = 0; k < n; k++) one_field_step(c, k == n - 1 && c->np > 0);
+    for (int k = 0; k < n; k++) one_field_step(c, k == n - 1 && c->np > 0, c->stream);
     return check_cuda(c, "glasma_step");
 }
 
 static gl_status site_once(gl_ctx* c) {
     if (c->pstep != c->step - 1) return fail(c, GL_ERR_STATE, "needs exactly one field step since the particles' time");
-    launch_site_fields(c->prec, c->field[1 - c->cur], c->field[c->cur], c->site, c->N, c->pstep * c->dt, c->stream);
+    launch_site_fields(c->prec, c->field[1 - c->cur], c->field[c->cur], site_at(c, c->pstep), c->N, c->pstep * c->dt,
+                       c->stream);
     c->site_step = c->pstep;
     return GL_OK;
 }
@@ -407,31 +434,69 @@ gl_status wong_site_fields(gl_ctx* c) {
     return check_cuda(c, "wong_site_fields");
 }
 
-static gl_status push_once(gl_ctx* c) {
-    if (c->pstep != c->step - 1) return fail(c, GL_ERR_STATE, "wong_push needs exactly one field step since the particles' time");
+// push of the particles at t_pstep on stream st: reads the site fields of
+// t_pstep and the links and scalar of t_{pstep+1} (field buffer of that time)
+static gl_status push_once(gl_ctx* c, cudaStream_t st, void* bn1) {
     const double t = c->pstep * c->dt;
-    if (c->site_step != c->pstep)
-        if (gl_status s = site_once(c)) return s;
-    if (c->np) launch_push(c->prec, c->site, c->field[c->cur], c->parts, c->np, c->N, t, c->dt, active_mask(c, c->pstep),
-                           c->spp, c->stream, c->push_block);
+    if (c->np) launch_push(c->prec, site_at(c, c->pstep), bn1, c->parts, c->np, c->N, t, c->dt, active_mask(c, c->pstep),
+                           c->spp, st, c->push_block);
     c->pstep++;
-    if (c->sort_ok && c->pstep % c->cfg.sort_every == 0) sort_particles(c);
+    if (c->sort_ok && c->pstep % c->cfg.sort_every == 0) {
+        launch_sort(c->prec, c->parts, c->parts_alt, c->np, c->N, c->sort_scratch, st);
+        void* tmp = c->parts;
+        c->parts = c->parts_alt;
+        c->parts_alt = tmp;
+    }
     return GL_OK;
 }
 
 gl_status wong_push(gl_ctx* c) {
     if (!c) return GL_ERR_ARG;
-    if (gl_status s = push_once(c)) return s;
+    if (c->pstep != c->step - 1) return fail(c, GL_ERR_STATE, "wong_push needs exactly one field step since the particles' time");
+    if (c->site_step != c->pstep)
+        if (gl_status s = site_once(c)) return s;
+    if (gl_status s = push_once(c, c->stream, c->field[c->cur])) return s;
     return check_cuda(c, "wong_push");
 }
 
+static gl_status ensure_aux(gl_ctx* c) {
+    if (c->aux) return GL_OK;
+    if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_f, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_p, cudaEventDisableTiming) != cudaSuccess)
+        return check_cuda(c, "stream creation");
+    return GL_OK;
+}
+
+// n coupled steps with the field step of t_s overlapped with the push of the
+// particles at t_{s-1} (second stream): the field kernel of step s reads the
+// buffers of time s and writes those of s+1 and the site fields of t_s, while
+// the push of s-1 reads the site fields of t_{s-1} and the links and scalar of
+// time s; the field step s+1, which rewrites the buffers of time s-1, waits
+// for that push.  The caller's stream waits for the last push.
 gl_status gl_step_coupled(gl_ctx* c, int32_t n) {
     if (!c || n < 0) return GL_ERR_ARG;
-    for (int k = 0; k < n; k++) {
-        if (c->pstep != c->step) return fail(c, GL_ERR_STATE, "particles are not at the fields' time");
-        one_field_step(c, true);
-        if (gl_status s = push_once(c)) return s;
+    if (n == 0) return GL_OK;
+    if (c->pstep != c->step) return fail(c, GL_ERR_STATE, "particles are not at the fields' time");
+    if (c->np == 0) {
+        for (int k = 0; k < n; k++) one_field_step(c, false, c->stream);
+        c->pstep = c->step;
+        return check_cuda(c, "gl_step_coupled");
     }
+    if (gl_status s = ensure_aux(c)) return s;
+    one_field_step(c, true, c->stream);
+    for (int k = 1; k <= n; k++) {
+        cudaEventRecord(c->ev_f, c->stream);          // field step of pstep + 1 done
+        cudaStreamWaitEvent(c->aux, c->ev_f, 0);
+        void* bn1 = c->field[c->cur];                 // buffers of time pstep + 1
+        if (gl_status s = push_once(c, c->aux, bn1)) return s;
+        if (k == n) break;
+        if (k >= 2) cudaStreamWaitEvent(c->stream, c->ev_p, 0);  // push of the step before
+        one_field_step(c, true, c->stream);
+        cudaEventRecord(c->ev_p, c->aux);
+    }
+    cudaEventRecord(c->ev_p, c->aux);
+    cudaStreamWaitEvent(c->stream, c->ev_p, 0);
     return check_cuda(c, "gl_step_coupled");
 }
 
@@ -461,7 +526,7 @@ gl_status gl_autotune(gl_ctx* c, int32_t* tile_out, int32_t* push_block_out) {
     for (int k = 0; k < 4; k++) {
         if (c->prec == GL_FP64 && (k == 0 || k == 3)) { c->tune_field_ms[k] = 0; continue; }
         const float ms = timed([&] {
-            launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], c->np ? c->site : nullptr, c->N, c->step,
+            launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], c->np ? site_at(c, c->step) : nullptr, c->N, c->step,
                               c->dt, 0, tiles[k], c->stream);
         });
         c->tune_field_ms[k] = ms;
@@ -479,7 +544,7 @@ gl_status gl_autotune(gl_ctx* c, int32_t* tile_out, int32_t* push_block_out) {
         for (int k = 0; k < 3; k++) {
             cudaMemcpyAsync(c->parts_alt, c->parts, particle_bytes(c->prec, c->np), cudaMemcpyDeviceToDevice, c->stream);
             const float ms = timed([&] {
-                launch_push(c->prec, c->site, c->field[1 - c->cur], c->parts_alt, c->np, c->N, trial * c->dt, c->dt,
+                launch_push(c->prec, site_at(c, c->step), c->field[1 - c->cur], c->parts_alt, c->np, c->N, trial * c->dt, c->dt,
                             active_mask(c, trial), c->spp, c->stream, blocks[k]);
             });
             c->tune_push_ms[k] = ms;
@@ -503,17 +568,22 @@ gl_status gl_tuning(const gl_ctx* c, float* field_ms, float* push_ms) {
     return GL_OK;
 }
 
-gl_status observables(gl_ctx* c, gl_obs* o) {
-    if (!c || !o) return GL_ERR_ARG;
-    memset(o, 0, sizeof *o);
+// enqueue the observable reductions of a context (no wait)
+static void observables_launch(gl_ctx* c) {
     const int64_t pushed = c->pstep > 0 ? c->pstep - 1 : -1;
     const uint32_t mask = pushed >= 0 ? active_mask(c, pushed) : 0u;
-    double host[GL_MAX_SPECIES * PO_N + FO_N];
     if (c->np) launch_particle_obs(c->prec, c->parts, c->np, c->pstep * c->dt, mask, c->spp, c->q2ref, c->q3ref,
                                    c->partials, MAX_BLOCKS, c->obs_dev, c->stream);
     else cudaMemsetAsync(c->obs_dev, 0, GL_MAX_SPECIES * PO_N * sizeof(double), c->stream);
-    launch_field_obs(c->prec, c->field[c->cur], c->site, c->N, c->partials + (size_t)MAX_BLOCKS * GL_MAX_SPECIES * PO_N,
-                     MAX_BLOCKS, c->obs_dev + GL_MAX_SPECIES * PO_N, c->stream);
+    launch_field_obs(c->prec, c->field[c->cur], site_at(c, c->pstep - 1), c->N,
+                     c->partials + (size_t)MAX_BLOCKS * GL_MAX_SPECIES * PO_N, MAX_BLOCKS,
+                     c->obs_dev + GL_MAX_SPECIES * PO_N, c->stream);
+}
+
+// read back the reductions enqueued by observables_launch (waits)
+static gl_status observables_read(gl_ctx* c, gl_obs* o) {
+    memset(o, 0, sizeof *o);
+    double host[GL_MAX_SPECIES * PO_N + FO_N];
     cudaMemcpyAsync(host, c->obs_dev, sizeof host, cudaMemcpyDeviceToHost, c->stream);
     if (gl_status s = check_cuda(c, "observables")) return s;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, "observables sync");
@@ -540,6 +610,12 @@ gl_status observables(gl_ctx* c, gl_obs* o) {
     o->mean_trB_T2 = f[FO_BT2] / (double)c->Vn;
     o->mean_trB_L2 = f[FO_BL2] / (double)c->Vn;
     return GL_OK;
+}
+
+gl_status observables(gl_ctx* c, gl_obs* o) {
+    if (!c || !o) return GL_ERR_ARG;
+    observables_launch(c);
+    return observables_read(c, o);
 }
 
 }  // extern "C"
