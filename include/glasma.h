@@ -104,7 +104,7 @@ typedef struct {
     int64_t step;                       /* field step n of the context */
     double tau_fm;                      /* tau of the particle state */
     int32_t n_species;
-    int32_t pad;
+    uint32_t what;                      /* GL_OBS_* parts computed; the others are NaN (counts 0) */
     int64_t n_active[GL_MAX_SPECIES];   /* particles pushed at the last step */
     double sum_px2[GL_MAX_SPECIES];     /* sums over active particles, GeV^2 */
     double sum_py2[GL_MAX_SPECIES];
@@ -192,8 +192,24 @@ gl_status gl_autotune(gl_ctx* ctx, int32_t* tile_shape, int32_t* push_block);
  * push_ms[3] by block size (0 where not tried). */
 gl_status gl_tuning(const gl_ctx* ctx, float* field_ms, float* push_ms);
 
-/* Ensemble sums and field checks at the current time (waits). */
+/* Ensemble sums and field checks at the current time (waits): the same as
+ * gl_observables_ex(ctx, GL_OBS_ALL, out). */
 gl_status observables(gl_ctx* ctx, gl_obs* out);
+
+/* Parts of gl_obs to compute.  GL_OBS_PARTICLES: the per-species sums and
+ * Casimir drifts (a pass over the particles; per-particle values in the
+ * context's precision, accumulated in FP64).  GL_OBS_FIELDS: Gauss residual,
+ * link unitarity and the site-field means (an FP64 pass over the lattice,
+ * which on GPUs with slow FP64 costs more than a coupled step: meant for
+ * report intervals). */
+#define GL_OBS_PARTICLES 1u
+#define GL_OBS_FIELDS 2u
+#define GL_OBS_ALL 3u
+
+/* observables() restricted to the parts in `what` (waits).  The values of the
+ * other parts are NaN and their counts 0; out->what records the parts
+ * computed.  GL_ERR_ARG for a null pointer or unknown bits in `what`. */
+gl_status gl_observables_ex(gl_ctx* ctx, uint32_t what, gl_obs* out);
 
 /* ---- Batches of events ------------------------------------------------
  * Many independent MV events (the paper averages its observables over many
@@ -244,6 +260,11 @@ gl_status gl_batch_step_timed(gl_batch* batch, int32_t n_steps, double* field_ms
 
 /* observables() of every event into out[n_events] (waits). */
 gl_status gl_batch_observables(gl_batch* batch, gl_obs* out);
+
+/* gl_observables_ex of every event into out[n_events] (waits).  The particle
+ * sums of all events are reduced by one launch pair; each event's values are
+ * bitwise those of gl_observables_ex on that event alone. */
+gl_status gl_batch_observables_ex(gl_batch* batch, uint32_t what, gl_obs* out);
 
 /* Largest particle count gl_ensemble_sums_noalloc accepts. */
 #define GL_NOALLOC_MAX_PARTICLES 2097152

@@ -41,7 +41,7 @@ _D8 = ctypes.c_double * GL_MAX_SPECIES
 
 class gl_obs(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("tau_fm", ctypes.c_double), ("n_species", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("n_active", ctypes.c_int64 * GL_MAX_SPECIES),
+                ("what", ctypes.c_uint32), ("n_active", ctypes.c_int64 * GL_MAX_SPECIES),
                 ("sum_px2", _D8), ("sum_py2", _D8), ("sum_pL2", _D8), ("sum_dpT2", _D8),
                 ("casimir2_dev", _D8), ("casimir3_dev", _D8), ("gauss_max", ctypes.c_double),
                 ("gauss_rms", ctypes.c_double), ("unitarity_max", ctypes.c_double),
@@ -67,6 +67,7 @@ SIGNATURES = {
     "wong_push": (ctypes.c_int, [_P]),
     "gl_step_coupled": (ctypes.c_int, [_P, ctypes.c_int32]),
     "observables": (ctypes.c_int, [_P, ctypes.POINTER(gl_obs)]),
+    "gl_observables_ex": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.POINTER(gl_obs)]),
     "gl_autotune": (ctypes.c_int, [_P, _P, _P]),
     "gl_tuning": (ctypes.c_int, [_P, _P, _P]),
     "gl_ensemble_sums_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_uint32,
@@ -83,9 +84,11 @@ SIGNATURES = {
     "gl_batch_step": (ctypes.c_int, [_P, ctypes.c_int32]),
     "gl_batch_step_timed": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "gl_batch_observables": (ctypes.c_int, [_P, _P]),
+    "gl_batch_observables_ex": (ctypes.c_int, [_P, ctypes.c_uint32, _P]),
 }
 
 GL_NOALLOC_MAX_PARTICLES = 2097152
+GL_OBS_PARTICLES, GL_OBS_FIELDS, GL_OBS_ALL = 1, 2, 3
 
 _lib = None
 
@@ -209,9 +212,14 @@ class Event:
     def set_step(self, n):
         _check(lib().gl_set_step(self.ctx, n), self.ctx, "gl_set_step")
 
-    def observables(self):
+    def observables(self, what=None):
+        """gl_obs of the current time; `what` (GL_OBS_* bits) selects the parts
+        computed, all by default."""
         o = gl_obs()
-        _check(lib().observables(self.ctx, ctypes.byref(o)), self.ctx, "observables")
+        if what is None:
+            _check(lib().observables(self.ctx, ctypes.byref(o)), self.ctx, "observables")
+        else:
+            _check(lib().gl_observables_ex(self.ctx, what, ctypes.byref(o)), self.ctx, "gl_observables_ex")
         return o
 
     def autotune(self):
@@ -303,9 +311,12 @@ class Batch:
         self._chk(lib().gl_batch_step_timed(self.b, n, ctypes.byref(f), ctypes.byref(p)), "gl_batch_step_timed")
         return f.value, p.value
 
-    def observables(self):
+    def observables(self, what=None):
         out = (gl_obs * self.ne)()
-        self._chk(lib().gl_batch_observables(self.b, out), "gl_batch_observables")
+        if what is None:
+            self._chk(lib().gl_batch_observables(self.b, out), "gl_batch_observables")
+        else:
+            self._chk(lib().gl_batch_observables_ex(self.b, what, out), "gl_batch_observables_ex")
         return list(out)
 
     def close(self):

@@ -10,6 +10,11 @@
 // graph is valid for every step.  Each block finds its event by binary search
 // in a prefix table of tiles or particle chunks.
 //
+// Every sort_every steps (per event) the run stops between a push and the next
+// field step and the particles of that event are reordered by cell, as in the
+// single-event schedule.  Observables of all events are reduced by one launch
+// pair over per-event chunks (obs_body.cuh).
+//
 // The tile shape of the field kernel and the block size of the push are
 // chosen by gl_batch_autotune from timed trial launches that leave the state
 // unchanged (the field kernel writes only the spare time slice; the push runs
@@ -22,6 +27,7 @@
 
 #include "fused_body.cuh"
 #include "internal.h"
+#include "obs_body.cuh"
 #include "push_body.cuh"
 
 namespace gl {
@@ -65,7 +71,7 @@ __device__ __forceinline__ int find_event(const EvDesc* ev, int ne, int block, b
 }
 
 template <typename R, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) batch_field_kernel(BatchArgs b) {
+__global__ void __launch_bounds__(TX * TY, (Tile<R, TX, TY>::min_blocks)) batch_field_kernel(BatchArgs b) {
     __shared__ int s_e;
     if (threadIdx.x == 0) s_e = find_event(b.ev, b.ne, blockIdx.x, true);
     __syncthreads();
@@ -106,9 +112,54 @@ __global__ void batch_push_kernel(BatchArgs b, int lag) {
 
 __global__ void tick_kernel(int64_t* clock) { *clock += 1; }
 
+// particle observables of every event: blocks [block_begin, block_begin +
+// nblocks) reduce the chunks of event e into its partial rows
+struct BObs {
+    const void* parts;
+    int64_t np;
+    double t;
+    uint32_t mask;
+    int block_begin;
+    int nblocks;
+    double* partials;
+    double* out;
+    ObsArgs oa;
+};
+
+__device__ __forceinline__ int find_obs_event(const BObs* ev, int ne, int block) {
+    int lo = 0, hi = ne - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ev[mid].block_begin <= block) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(OBS_THREADS) batch_obs_kernel(const BObs* ev, int ne) {
+    __shared__ int s_e;
+    if (threadIdx.x == 0) s_e = find_obs_event(ev, ne, blockIdx.x);
+    __syncthreads();
+    const BObs& d = ev[s_e];
+    const int b = blockIdx.x - d.block_begin;
+    const int64_t chunk = obs_chunk(d.np);
+    const int64_t c0 = (int64_t)b * chunk;
+    const int64_t c1 = c0 + chunk < d.np ? c0 + chunk : d.np;
+    particle_obs_block<R>(carve_parts<R>((void*)d.parts, d.np), d.t, d.mask, d.oa, c0, c1,
+                          d.partials + (size_t)b * GL_MAX_SPECIES * PO_N);
+}
+
+// one block per (event, value)
+__global__ void __launch_bounds__(256) batch_obs_finalize(const BObs* ev) {
+    constexpr int W = GL_MAX_SPECIES * PO_N;
+    const BObs& d = ev[blockIdx.x / W];
+    particle_obs_reduce(d.partials, d.nblocks, blockIdx.x % W, d.out);
+}
+
 // tile shapes the autotuner chooses from
-enum { TILE_32x8 = 0, TILE_32x4 = 1, N_TILES = 2 };
-static const int TILE_DIMS[N_TILES][2] = {{32, 8}, {32, 4}};
+enum { TILE_32x8 = 0, TILE_32x4 = 1, TILE_32x16 = 2, N_TILES = 3 };
+static const int TILE_DIMS[N_TILES][2] = {{32, 8}, {32, 4}, {32, 16}};
 static const int PUSH_BLOCKS[3] = {128, 256, 512};
 
 template <typename R, int TX, int TY>
@@ -125,9 +176,17 @@ static void set_smem_attr() {
 
 template <typename R>
 static void launch_batch_field(int tile, int blocks, const BatchArgs& b, cudaStream_t st) {
-    if (tile == TILE_32x8) {
+    if constexpr (sizeof(R) == 8) {
+        // FP64: the 32x4 tile only (shared memory)
+        (void)tile;
+        set_smem_attr<R, 32, 4>();
+        batch_field_kernel<R, 32, 4><<<blocks, 128, Tile<R, 32, 4>::bytes, st>>>(b);
+    } else if (tile == TILE_32x8) {
         set_smem_attr<R, 32, 8>();
         batch_field_kernel<R, 32, 8><<<blocks, 256, Tile<R, 32, 8>::bytes, st>>>(b);
+    } else if (tile == TILE_32x16) {
+        set_smem_attr<R, 32, 16>();
+        batch_field_kernel<R, 32, 16><<<blocks, 512, Tile<R, 32, 16>::bytes, st>>>(b);
     } else {
         set_smem_attr<R, 32, 4>();
         batch_field_kernel<R, 32, 4><<<blocks, 128, Tile<R, 32, 4>::bytes, st>>>(b);
@@ -150,6 +209,11 @@ struct gl_batch {
     EvDesc* h_desc;
     EvDesc* d_desc;
     int64_t* d_clock;
+    BObs* h_obs;
+    BObs* d_obs;
+    SortEv* h_sort;
+    SortEv* d_sort;
+    int* sort_every;  // per event (0: no sorting)
     int tile;         // autotuned tile shape
     int push_block;   // autotuned push block size
     int field_blocks;
@@ -161,28 +225,6 @@ struct gl_batch {
     float tune_push_ms[3];
     char err[256];
 };
-
-// context internals needed by the batch (defined in capi.cu)
-namespace gl {
-struct CtxView {
-    void* field[2];
-    void* site[2];
-    void* parts;
-    int N, prec, cur;
-    int64_t step, pstep, np;
-    double dt;
-    double mass[GL_MAX_SPECIES];
-    int is_static[GL_MAX_SPECIES];
-    double t_form[GL_MAX_SPECIES];
-    int ns;
-    int reunit_count;
-    void* parts_alt;
-};
-void ctx_view(const gl_ctx* c, CtxView* v);
-void ctx_advance(gl_ctx* c, int64_t steps);
-size_t ctx_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t ns);
-gl_status ctx_observables_many(gl_ctx** cs, int n, gl_obs* out);
-}  // namespace gl
 
 static size_t a256b(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -196,7 +238,8 @@ extern "C" {
 size_t gl_batch_workspace_bytes(const gl_config* cfgs, const gl_species* species, int32_t n_species,
                                 int32_t n_events) {
     if (!cfgs || n_events < 1 || n_events > MAX_EVENTS) return 0;
-    size_t o = a256b(sizeof(EvDesc) * n_events) + 256;
+    size_t o = a256b(sizeof(EvDesc) * n_events) + 256 + a256b(sizeof(BObs) * n_events) +
+               a256b(sizeof(SortEv) * n_events);
     for (int e = 0; e < n_events; e++) {
         const size_t w = ctx_workspace_bytes(&cfgs[e], species ? species + (size_t)e * n_species : nullptr, n_species);
         if (!w) return 0;
@@ -227,10 +270,28 @@ gl_status gl_batch_create(const gl_config* cfgs, const gl_species* species, int3
     b->stream = (cudaStream_t)stream;
     b->ev = new (std::nothrow) gl_ctx*[n_events]();
     b->h_desc = new (std::nothrow) EvDesc[n_events]();
+    b->h_obs = new (std::nothrow) BObs[n_events]();
+    b->h_sort = new (std::nothrow) SortEv[n_events]();
+    b->sort_every = new (std::nothrow) int[n_events]();
+    if (!b->ev || !b->h_desc || !b->h_obs || !b->h_sort || !b->sort_every) {
+        delete[] b->ev;
+        delete[] b->h_desc;
+        delete[] b->h_obs;
+        delete[] b->h_sort;
+        delete[] b->sort_every;
+        delete b;
+        return GL_ERR_ARG;
+    }
     char* ws = (char*)d_workspace;
+    size_t o = 0;
     b->d_desc = (EvDesc*)ws;
-    b->d_clock = (int64_t*)(ws + a256b(sizeof(EvDesc) * n_events));
-    size_t o = a256b(sizeof(EvDesc) * n_events) + 256;
+    o += a256b(sizeof(EvDesc) * n_events);
+    b->d_clock = (int64_t*)(ws + o);
+    o += 256;
+    b->d_obs = (BObs*)(ws + o);
+    o += a256b(sizeof(BObs) * n_events);
+    b->d_sort = (SortEv*)(ws + o);
+    o += a256b(sizeof(SortEv) * n_events);
     for (int e = 0; e < n_events; e++) {
         const gl_species* sp = species ? species + (size_t)e * n_species : nullptr;
         const size_t w = ctx_workspace_bytes(&cfgs[e], sp, n_species);
@@ -239,6 +300,9 @@ gl_status gl_batch_create(const gl_config* cfgs, const gl_species* species, int3
             for (int k = 0; k < e; k++) gl_destroy(b->ev[k]);
             delete[] b->ev;
             delete[] b->h_desc;
+            delete[] b->h_obs;
+            delete[] b->h_sort;
+            delete[] b->sort_every;
             delete b;
             return s;
         }
@@ -264,6 +328,9 @@ gl_status gl_batch_destroy(gl_batch* b) {
     for (int e = 0; e < b->ne; e++) gl_destroy(b->ev[e]);
     delete[] b->ev;
     delete[] b->h_desc;
+    delete[] b->h_obs;
+    delete[] b->h_sort;
+    delete[] b->sort_every;
     delete b;
     return GL_OK;
 }
@@ -313,6 +380,7 @@ static gl_status sync_desc(gl_batch* b) {
         cb += (int)((v.np + PUSH_CHUNK - 1) / PUSH_CHUNK);
         d.np = v.np;
         d.n_species = v.ns;
+        b->sort_every[e] = v.sort_every;
         for (int k = 0; k < GL_MAX_SPECIES; k++) {
             d.mass[k] = v.mass[k];
             d.is_static[k] = v.is_static[k];
@@ -361,7 +429,7 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
     // field kernel: trial launches write only the spare time slice and the
     // site fields, which the next real step overwrites
     for (int tile = 0; tile < N_TILES; tile++) {
-        if (b->prec == GL_FP64 && tile == TILE_32x8) continue;  // FP64 tile must fit shared memory
+        if (b->prec == GL_FP64 && tile != TILE_32x4) continue;  // FP64 tile must fit shared memory
         b->tile = tile;
         if (gl_status s = sync_desc(b)) return s;
         BatchArgs a{b->d_desc, b->ne, b->dt, 0, b->d_clock};
@@ -434,20 +502,68 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
     return cudaGetLastError() == cudaSuccess ? GL_OK : bfail(b, GL_ERR_CUDA, "autotune launch failed");
 }
 
-// n coupled steps: the field step of t_s (all events) alone, then n - 1
-// replays of the captured overlapped step, then the last push alone
+static gl_status ensure_aux(gl_batch* b) {
+    if (b->aux) return GL_OK;
+    if (cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_a, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_b, cudaEventDisableTiming) != cudaSuccess)
+        return bfail(b, GL_ERR_CUDA, "stream creation failed");
+    return GL_OK;
+}
+
+// steps from the common step `now` to the next sort of any event (at most n)
+static int32_t segment_length(const gl_batch* b, int64_t now, int32_t n) {
+    int32_t m = n;
+    for (int e = 0; e < b->ne; e++) {
+        const int se = b->sort_every[e];
+        if (se <= 0) continue;
+        const int64_t d = se - now % se;
+        if (d < m) m = (int32_t)d;
+    }
+    return m;
+}
+
+// after a segment that ended at step `now`: advance the contexts and sort the
+// particles of the events whose period divides `now` (between the push and
+// the next field step, as the single-event schedule does)
+static void end_segment(gl_batch* b, int32_t m, int64_t now) {
+    int n = 0, pb = 0, cb = 0;
+    for (int e = 0; e < b->ne; e++) {
+        ctx_advance(b->ev[e], m);
+        if (b->sort_every[e] > 0 && now % b->sort_every[e] == 0) {
+            CtxView v;
+            ctx_view(b->ev[e], &v);
+            if (v.np <= 0) continue;
+            SortEv& d = b->h_sort[n++];
+            d = sort_event(v.parts, v.parts_alt, v.np, v.N, v.sort_scratch);
+            d.pblk_begin = pb;
+            d.cblk_begin = cb;
+            pb += sort_particle_blocks(v.np);
+            cb += sort_cell_blocks(v.N);
+            ctx_swap_parts(b->ev[e]);
+        }
+    }
+    if (n == 0) return;
+    cudaMemcpyAsync(b->d_sort, b->h_sort, sizeof(SortEv) * n, cudaMemcpyHostToDevice, b->stream);
+    launch_sort_many(b->prec, b->d_sort, n, pb, cb, b->stream);
+}
+
+static int64_t common_step(const gl_batch* b) {
+    CtxView v;
+    ctx_view(b->ev[0], &v);
+    return v.step;
+}
+
+// n coupled steps.  Per segment between sorts: the field step of t_s (all
+// events) alone, then m - 1 replays of the captured overlapped step, then the
+// last push alone.
 gl_status gl_batch_step(gl_batch* b, int32_t n_steps) {
     if (!b || n_steps < 0) return GL_ERR_ARG;
     if (n_steps == 0) return GL_OK;
     if (gl_status s = sync_desc(b)) return s;
-    if (!b->aux) {
-        if (cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->ev_a, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->ev_b, cudaEventDisableTiming) != cudaSuccess)
-            return bfail(b, GL_ERR_CUDA, "stream creation failed");
-    }
+    if (gl_status s = ensure_aux(b)) return s;
     if (b->prec == GL_FP64) set_smem_attr<double, 32, 4>();
-    else { set_smem_attr<float, 32, 8>(); set_smem_attr<float, 32, 4>(); }
+    else { set_smem_attr<float, 32, 8>(); set_smem_attr<float, 32, 4>(); set_smem_attr<float, 32, 16>(); }
     // (re)capture the overlapped step when the launch shapes changed
     if (!b->exec || b->graph_tile != b->tile || b->graph_push_block != b->push_block) {
         if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
@@ -463,55 +579,56 @@ gl_status gl_batch_step(gl_batch* b, int32_t n_steps) {
         b->graph_tile = b->tile;
         b->graph_push_block = b->push_block;
     }
-    launch_field(b, b->stream);
-    tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock);
-    for (int k = 1; k < n_steps; k++) cudaGraphLaunch(b->exec, b->stream);
-    launch_push(b, 1, b->stream);
-    if (cudaGetLastError() != cudaSuccess) return bfail(b, GL_ERR_CUDA, "batch step launch failed");
-    for (int e = 0; e < b->ne; e++) ctx_advance(b->ev[e], n_steps);
+    int64_t now = common_step(b);
+    for (int32_t left = n_steps; left > 0;) {
+        const int32_t m = segment_length(b, now, left);
+        launch_field(b, b->stream);
+        tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock);
+        for (int k = 1; k < m; k++) cudaGraphLaunch(b->exec, b->stream);
+        launch_push(b, 1, b->stream);
+        if (cudaGetLastError() != cudaSuccess) return bfail(b, GL_ERR_CUDA, "batch step launch failed");
+        now += m;
+        left -= m;
+        end_segment(b, m, now);
+        if (left > 0)
+            if (gl_status s = sync_desc(b)) return s;
+    }
     return GL_OK;
 }
 
-// the same schedule as gl_batch_step with direct launches and CUDA events
-// around every field and push launch on their streams; returns the summed
-// kernel durations (waits)
+// The same steps with the field and push launches of each step run one after
+// the other on the batch stream (no overlap), each bracketed by CUDA events:
+// returns the summed durations of the field and push kernels (waits).  The
+// state evolves exactly as under gl_batch_step.
 gl_status gl_batch_step_timed(gl_batch* b, int32_t n_steps, double* field_ms, double* push_ms) {
     if (!b || n_steps < 1) return GL_ERR_ARG;
     if (gl_status s = sync_desc(b)) return s;
-    if (!b->aux) {
-        if (cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->ev_a, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->ev_b, cudaEventDisableTiming) != cudaSuccess)
-            return bfail(b, GL_ERR_CUDA, "stream creation failed");
-    }
     const int ne = 4 * n_steps;
     cudaEvent_t* ev = new (std::nothrow) cudaEvent_t[ne];
     if (!ev) return GL_ERR_ARG;
     for (int k = 0; k < ne; k++) cudaEventCreate(&ev[k]);
-    // events 4k, 4k+1 bracket the field launch of step k; 4k+2, 4k+3 the push of step k
-    cudaEventRecord(ev[0], b->stream);
-    launch_field(b, b->stream);
-    cudaEventRecord(ev[1], b->stream);
-    tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock);
-    for (int k = 1; k < n_steps; k++) {
-        cudaEventRecord(b->ev_a, b->stream);
-        cudaStreamWaitEvent(b->aux, b->ev_a, 0);
-        cudaEventRecord(ev[4 * (k - 1) + 2], b->aux);
-        launch_push(b, 1, b->aux);
-        cudaEventRecord(ev[4 * (k - 1) + 3], b->aux);
-        cudaEventRecord(b->ev_b, b->aux);
-        cudaEventRecord(ev[4 * k], b->stream);
-        launch_field(b, b->stream);
-        cudaEventRecord(ev[4 * k + 1], b->stream);
-        cudaStreamWaitEvent(b->stream, b->ev_b, 0);
-        tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock);
+    // events 4k, 4k+1 bracket the field launch of step k; 4k+2, 4k+3 its push
+    int64_t now = common_step(b);
+    gl_status st = GL_OK;
+    for (int32_t done = 0; done < n_steps && st == GL_OK;) {
+        const int32_t m = segment_length(b, now, n_steps - done);
+        for (int32_t k = done; k < done + m; k++) {
+            cudaEventRecord(ev[4 * k], b->stream);
+            launch_field(b, b->stream);
+            cudaEventRecord(ev[4 * k + 1], b->stream);
+            tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock);
+            cudaEventRecord(ev[4 * k + 2], b->stream);
+            launch_push(b, 1, b->stream);
+            cudaEventRecord(ev[4 * k + 3], b->stream);
+        }
+        now += m;
+        done += m;
+        end_segment(b, m, now);
+        if (done < n_steps) st = sync_desc(b);
     }
-    cudaEventRecord(ev[4 * (n_steps - 1) + 2], b->stream);
-    launch_push(b, 1, b->stream);
-    cudaEventRecord(ev[4 * (n_steps - 1) + 3], b->stream);
     cudaStreamSynchronize(b->stream);
     double f = 0, p = 0;
-    for (int k = 0; k < n_steps; k++) {
+    for (int k = 0; k < n_steps && st == GL_OK; k++) {
         float a = 0, c = 0;
         cudaEventElapsedTime(&a, ev[4 * k], ev[4 * k + 1]);
         cudaEventElapsedTime(&c, ev[4 * k + 2], ev[4 * k + 3]);
@@ -520,16 +637,46 @@ gl_status gl_batch_step_timed(gl_batch* b, int32_t n_steps, double* field_ms, do
     }
     for (int k = 0; k < ne; k++) cudaEventDestroy(ev[k]);
     delete[] ev;
+    if (st != GL_OK) return st;
     if (field_ms) *field_ms = f;
     if (push_ms) *push_ms = p;
     if (cudaGetLastError() != cudaSuccess) return bfail(b, GL_ERR_CUDA, "timed batch step failed");
-    for (int e = 0; e < b->ne; e++) ctx_advance(b->ev[e], n_steps);
     return GL_OK;
 }
 
-gl_status gl_batch_observables(gl_batch* b, gl_obs* out) {
-    if (!b || !out) return GL_ERR_ARG;
-    return ctx_observables_many(b->ev, b->ne, out);
+gl_status gl_batch_observables(gl_batch* b, gl_obs* out) { return gl_batch_observables_ex(b, GL_OBS_ALL, out); }
+
+gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
+    if (!b || !out || (what & ~GL_OBS_ALL)) return GL_ERR_ARG;
+    if (what & GL_OBS_PARTICLES) {
+        int blocks = 0;
+        for (int e = 0; e < b->ne; e++) {
+            ObsEvent o;
+            ctx_obs_event(b->ev[e], &o);
+            BObs& d = b->h_obs[e];
+            d.parts = o.parts;
+            d.np = o.np;
+            d.t = o.t;
+            d.mask = o.mask;
+            d.block_begin = blocks;
+            d.nblocks = obs_blocks(o.np);
+            d.partials = o.partials;
+            d.out = o.out;
+            d.oa.sp = o.sp;
+            for (int k = 0; k < GL_MAX_SPECIES; k++) { d.oa.q2ref[k] = o.q2ref[k]; d.oa.q3ref[k] = o.q3ref[k]; }
+            blocks += d.nblocks;
+            // an event without particles: zero sums, as the single-event path
+            if (d.nblocks == 0)
+                cudaMemsetAsync(o.out, 0, GL_MAX_SPECIES * PO_N * sizeof(double), b->stream);
+        }
+        cudaMemcpyAsync(b->d_obs, b->h_obs, sizeof(BObs) * b->ne, cudaMemcpyHostToDevice, b->stream);
+        if (blocks > 0) {
+            if (b->prec == GL_FP64) batch_obs_kernel<double><<<blocks, OBS_THREADS, 0, b->stream>>>(b->d_obs, b->ne);
+            else batch_obs_kernel<float><<<blocks, OBS_THREADS, 0, b->stream>>>(b->d_obs, b->ne);
+            batch_obs_finalize<<<b->ne * GL_MAX_SPECIES * PO_N, 256, 0, b->stream>>>(b->d_obs);
+        }
+    }
+    return ctx_observables_many(b->ev, b->ne, what & ~GL_OBS_PARTICLES, what, out);
 }
 
 gl_status gl_batch_tuning(const gl_batch* b, float* field_ms, float* push_ms) {

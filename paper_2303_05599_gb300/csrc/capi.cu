@@ -67,8 +67,9 @@ static char g_create_err[256] = "";
 static inline void* site_at(const gl_ctx* c, int64_t n) { return c->site_buf[n & 1]; }
 
 extern "C" {
-static void observables_launch(gl_ctx* c);
-static gl_status observables_read(gl_ctx* c, gl_obs* o);
+static uint32_t active_mask(const gl_ctx* c, int64_t n);
+static void observables_launch(gl_ctx* c, uint32_t what);
+static gl_status observables_read(gl_ctx* c, uint32_t what, gl_obs* o);
 }
 
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -152,20 +153,6 @@ static void q0_vectors(double q0[2][8]) {
 
 namespace gl {
 // read-only view of a context for the batch (batch.cu)
-struct CtxView {
-    void* field[2];
-    void* site[2];
-    void* parts;
-    int N, prec, cur;
-    int64_t step, pstep, np;
-    double dt;
-    double mass[GL_MAX_SPECIES];
-    int is_static[GL_MAX_SPECIES];
-    double t_form[GL_MAX_SPECIES];
-    int ns;
-    int reunit_count;
-    void* parts_alt;
-};
 void ctx_view(const gl_ctx* c, CtxView* v) {
     v->field[0] = c->field[0];
     v->field[1] = c->field[1];
@@ -187,6 +174,8 @@ void ctx_view(const gl_ctx* c, CtxView* v) {
     v->ns = c->ns;
     v->reunit_count = c->reunit_count;
     v->parts_alt = c->parts_alt;
+    v->sort_every = c->sort_ok ? c->cfg.sort_every : 0;
+    v->sort_scratch = c->sort_scratch;
 }
 // record that the batch advanced this event by `steps` coupled steps
 void ctx_advance(gl_ctx* c, int64_t steps) {
@@ -200,11 +189,24 @@ void ctx_advance(gl_ctx* c, int64_t steps) {
 size_t ctx_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t ns) {
     return gl_workspace_bytes(cfg, sp, ns);
 }
-// observables of many contexts with one wait (used by the batch)
-gl_status ctx_observables_many(gl_ctx** cs, int n, gl_obs* out) {
-    for (int e = 0; e < n; e++) ::observables_launch(cs[e]);
+// the particle-observables launch of a context, for the batched reduction
+void ctx_obs_event(const gl_ctx* c, ObsEvent* o) {
+    const int64_t pushed = c->pstep > 0 ? c->pstep - 1 : -1;
+    o->parts = c->parts;
+    o->np = c->np;
+    o->t = c->pstep * c->dt;
+    o->mask = pushed >= 0 ? active_mask(c, pushed) : 0u;
+    o->sp = c->spp;
+    for (int k = 0; k < GL_MAX_SPECIES; k++) { o->q2ref[k] = c->q2ref[k]; o->q3ref[k] = c->q3ref[k]; }
+    o->partials = c->partials;
+    o->out = c->obs_dev;
+}
+// observables of many contexts with one wait (used by the batch): `launch`
+// selects what is enqueued here, `what` what is read back
+gl_status ctx_observables_many(gl_ctx** cs, int n, uint32_t launch, uint32_t what, gl_obs* out) {
+    for (int e = 0; e < n; e++) ::observables_launch(cs[e], launch);
     for (int e = 0; e < n; e++)
-        if (gl_status s = ::observables_read(cs[e], &out[e])) return s;
+        if (gl_status s = ::observables_read(cs[e], what, &out[e])) return s;
     return GL_OK;
 }
 }  // namespace gl
@@ -313,6 +315,14 @@ static void sort_particles(gl_ctx* c) {
     c->parts = c->parts_alt;
     c->parts_alt = tmp;
 }
+}  // extern "C"
+void gl::ctx_sort(gl_ctx* c) { sort_particles(c); }
+void gl::ctx_swap_parts(gl_ctx* c) {
+    void* tmp = c->parts;
+    c->parts = c->parts_alt;
+    c->parts_alt = tmp;
+}
+extern "C" {
 
 static uint32_t active_mask(const gl_ctx* c, int64_t n) {
     uint32_t m = 0;
@@ -569,53 +579,59 @@ gl_status gl_tuning(const gl_ctx* c, float* field_ms, float* push_ms) {
 }
 
 // enqueue the observable reductions of a context (no wait)
-static void observables_launch(gl_ctx* c) {
-    const int64_t pushed = c->pstep > 0 ? c->pstep - 1 : -1;
-    const uint32_t mask = pushed >= 0 ? active_mask(c, pushed) : 0u;
-    if (c->np) launch_particle_obs(c->prec, c->parts, c->np, c->pstep * c->dt, mask, c->spp, c->q2ref, c->q3ref,
-                                   c->partials, MAX_BLOCKS, c->obs_dev, c->stream);
-    else cudaMemsetAsync(c->obs_dev, 0, GL_MAX_SPECIES * PO_N * sizeof(double), c->stream);
-    launch_field_obs(c->prec, c->field[c->cur], site_at(c, c->pstep - 1), c->N,
-                     c->partials + (size_t)MAX_BLOCKS * GL_MAX_SPECIES * PO_N, MAX_BLOCKS,
-                     c->obs_dev + GL_MAX_SPECIES * PO_N, c->stream);
+static void observables_launch(gl_ctx* c, uint32_t what) {
+    if (what & GL_OBS_PARTICLES) {
+        ObsEvent o;
+        ctx_obs_event(c, &o);
+        launch_particle_obs(c->prec, o.parts, o.np, o.t, o.mask, o.sp, o.q2ref, o.q3ref, o.partials, o.out, c->stream);
+    }
+    if (what & GL_OBS_FIELDS)
+        launch_field_obs(c->prec, c->field[c->cur], site_at(c, c->pstep - 1), c->N,
+                         c->partials + (size_t)MAX_BLOCKS * GL_MAX_SPECIES * PO_N, MAX_BLOCKS,
+                         c->obs_dev + GL_MAX_SPECIES * PO_N, c->stream);
 }
 
-// read back the reductions enqueued by observables_launch (waits)
-static gl_status observables_read(gl_ctx* c, gl_obs* o) {
+// read back the reductions enqueued by observables_launch (waits); the values
+// of the parts not in `what` are NaN (counts 0)
+static gl_status observables_read(gl_ctx* c, uint32_t what, gl_obs* o) {
     memset(o, 0, sizeof *o);
     double host[GL_MAX_SPECIES * PO_N + FO_N];
     cudaMemcpyAsync(host, c->obs_dev, sizeof host, cudaMemcpyDeviceToHost, c->stream);
     if (gl_status s = check_cuda(c, "observables")) return s;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, "observables sync");
     const double u2 = 1.0 / (c->aG * c->aG);  // lattice momentum^2 -> GeV^2
+    const bool P = (what & GL_OBS_PARTICLES) != 0, F = (what & GL_OBS_FIELDS) != 0;
     o->step = c->step;
     o->tau_fm = c->pstep * c->dt * c->a_fm;
     o->n_species = c->ns;
+    o->what = what & GL_OBS_ALL;
     for (int k = 0; k < c->ns; k++) {
         const double* h = host + k * PO_N;
-        o->n_active[k] = (int64_t)llround(h[PO_COUNT]);
-        o->sum_px2[k] = h[PO_PX2] * u2;
-        o->sum_py2[k] = h[PO_PY2] * u2;
-        o->sum_pL2[k] = h[PO_PL2] * u2;
-        o->sum_dpT2[k] = h[PO_DPT2] * u2;
-        o->casimir2_dev[k] = h[PO_Q2];
-        o->casimir3_dev[k] = h[PO_Q3];
+        o->n_active[k] = P ? (int64_t)llround(h[PO_COUNT]) : 0;
+        o->sum_px2[k] = P ? h[PO_PX2] * u2 : NAN;
+        o->sum_py2[k] = P ? h[PO_PY2] * u2 : NAN;
+        o->sum_pL2[k] = P ? h[PO_PL2] * u2 : NAN;
+        o->sum_dpT2[k] = P ? h[PO_DPT2] * u2 : NAN;
+        o->casimir2_dev[k] = P ? h[PO_Q2] : NAN;
+        o->casimir3_dev[k] = P ? h[PO_Q3] : NAN;
     }
     const double* f = host + GL_MAX_SPECIES * PO_N;
-    o->gauss_max = f[FO_GMAX];
-    o->gauss_rms = sqrt(f[FO_GSUM] / (double)c->Vn);
-    o->unitarity_max = f[FO_UMAX];
-    o->mean_trE_T2 = f[FO_ET2] / (double)c->Vn;
-    o->mean_trE_L2 = f[FO_EL2] / (double)c->Vn;
-    o->mean_trB_T2 = f[FO_BT2] / (double)c->Vn;
-    o->mean_trB_L2 = f[FO_BL2] / (double)c->Vn;
+    o->gauss_max = F ? f[FO_GMAX] : NAN;
+    o->gauss_rms = F ? sqrt(f[FO_GSUM] / (double)c->Vn) : NAN;
+    o->unitarity_max = F ? f[FO_UMAX] : NAN;
+    o->mean_trE_T2 = F ? f[FO_ET2] / (double)c->Vn : NAN;
+    o->mean_trE_L2 = F ? f[FO_EL2] / (double)c->Vn : NAN;
+    o->mean_trB_T2 = F ? f[FO_BT2] / (double)c->Vn : NAN;
+    o->mean_trB_L2 = F ? f[FO_BL2] / (double)c->Vn : NAN;
     return GL_OK;
 }
 
-gl_status observables(gl_ctx* c, gl_obs* o) {
-    if (!c || !o) return GL_ERR_ARG;
-    observables_launch(c);
-    return observables_read(c, o);
+gl_status observables(gl_ctx* c, gl_obs* o) { return gl_observables_ex(c, GL_OBS_ALL, o); }
+
+gl_status gl_observables_ex(gl_ctx* c, uint32_t what, gl_obs* o) {
+    if (!c || !o || (what & ~GL_OBS_ALL)) return GL_ERR_ARG;
+    observables_launch(c, what);
+    return observables_read(c, what, o);
 }
 
 }  // extern "C"

@@ -20,7 +20,7 @@
 //   links, phi:      x in [-2, TX],   y in [-2, TY]    (LW x LH)
 //   plaquettes A:    x in [-2, TX-1], y in [-2, TY-1]  (AW x AH)
 //   momenta, Lf:     x in [-1, TX-1], y in [-1, TY-1]  (EW x EH)
-//   pi(n-1/2):       the tile
+// pi(n-1/2) is read by each site's thread straight from global memory.
 #pragma once
 #include "internal.h"
 #include "layout.cuh"
@@ -42,10 +42,13 @@ struct Tile {
     static constexpr int AW = TX + 2, AH = TY + 2, AN = AW * AH;
     static constexpr int EW = TX + 1, EH = TY + 1, EN = EW * EH;
     static constexpr int NT = TX * TY;
-    // vectors: links 2 LP LN, phi AP LN, A AP AN, e sums 2 AP EN, Lf AP EN, pi AP NT
-    static constexpr size_t vecs = (size_t)2 * LP * LN + (size_t)AP * LN + (size_t)AP * AN + (size_t)3 * AP * EN +
-                                   (size_t)AP * NT;
+    // vectors: links 2 LP LN, phi AP LN, A AP AN, e sums 2 AP EN, Lf AP EN
+    static constexpr size_t vecs = (size_t)2 * LP * LN + (size_t)AP * LN + (size_t)AP * AN + (size_t)3 * AP * EN;
     static constexpr size_t bytes = vecs * sizeof(V);
+    // CTAs per SM the launch bounds ask for: FP32 kernels are capped at 128
+    // registers a thread so that 16 warps fit an SM (the shared memory of
+    // 32x4: 4 CTAs, 32x8: 2, 32x16: 1); FP64 tiles take one CTA
+    static constexpr int min_blocks = sizeof(R) == 8 ? 1 : (NT >= 512 ? 1 : 512 / NT);
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -164,7 +167,6 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
     Vec* sA = sPhi + AP * LN;          // [AP][AN]
     Vec* sEs = sA + AP * AN;           // [2][AP][EN]: e(n-1/2), then e(n-1/2) + e(n+1/2)
     Vec* sLf = sEs + 2 * AP * EN;      // [AP][EN]
-    Vec* sPi = sLf + AP * EN;          // [AP][NT]
 
     const int N = a.N;
     const int64_t Vn = (int64_t)N * N;
@@ -186,12 +188,6 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
         const int64_t g = (int64_t)gy * N + gx;
 #pragma unroll
         for (int k = 0; k < 2 * AP; k++) cp_async16(sEs + (size_t)k * EN + i, in.e + (size_t)k * Vn + g);
-    }
-    {
-        const int gx = x0 + tid % TX, gy = y0 + tid / TX;
-        const int64_t g = (int64_t)wrapi(gy, N) * N + wrapi(gx, N);
-#pragma unroll
-        for (int k = 0; k < AP; k++) cp_async16(sPi + (size_t)k * NT + tid, in.pi + (size_t)k * Vn + g);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -252,6 +248,7 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
     const int gx = x0 + ix, gy = y0 + iy;
     if (gx >= N || gy >= N) return;
     const int64_t g = (int64_t)gy * N + gx;
+    const A8<R> p_old = load_alg(in.pi, g, Vn);
     const int e = (iy + 1) * EW + (ix + 1);
     const int l = (iy + 2) * LW + (ix + 2);
     const A8<R> ph = s_alg(sPhi, l, LN);
@@ -259,7 +256,6 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
     const M3<R> Uy_m = s_link(sU, 1, l - LW, LN);
     const A8<R> bx = conj_dn(Ux_m, s_alg(sPhi, l - 1, LN));
     const A8<R> by = conj_dn(Uy_m, s_alg(sPhi, l - LW, LN));
-    const A8<R> p_old = s_alg(sPi, tid, NT);
     A8<R> p_new, ph_new;
 #pragma unroll
     for (int c = 0; c < 8; c++) {

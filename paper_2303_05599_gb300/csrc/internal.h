@@ -37,21 +37,82 @@ size_t init_scratch_bytes(int64_t Vn);
 void launch_convert(int prec, int which, int to_device, void* dev, double* staging, int N, int64_t np,
                     cudaStream_t st);
 // observables: per-species particle sums and field checks, FP64, fixed-order reductions
+// (partials: obs_blocks(np) <= 1024 rows of GL_MAX_SPECIES * PO_N; out: GL_MAX_SPECIES * PO_N)
 void launch_particle_obs(int prec, const void* parts, int64_t np, double t, uint32_t active_mask,
                          const SpeciesParams& sp, const double q2ref[GL_MAX_SPECIES],
-                         const double q3ref[GL_MAX_SPECIES], double* partials, int max_blocks, double* out,
-                         cudaStream_t st);
+                         const double q3ref[GL_MAX_SPECIES], double* partials, double* out, cudaStream_t st);
+// one context's particle-observables launch, for the batched reduction
+struct ObsEvent {
+    void* parts;
+    int64_t np;
+    double t;
+    uint32_t mask;
+    SpeciesParams sp;
+    double q2ref[GL_MAX_SPECIES], q3ref[GL_MAX_SPECIES];
+    double* partials;
+    double* out;
+};
 void launch_field_obs(int prec, const void* b, const void* site, int N, double* partials, int max_blocks,
                       double* out, cudaStream_t st);
 
 // counting sort of the particles by cell from src into dst (same layout)
 void launch_sort(int prec, void* src, void* dst, int64_t np, int N, void* scratch, cudaStream_t st);
+// one event of a batched sort; pblk_begin / cblk_begin: its first block in the
+// particle-indexed (sort_particle_blocks) and cell-indexed (sort_cell_blocks)
+// launches, set by the caller
+struct SortEv {
+    void* src;
+    void* dst;
+    int64_t np;
+    int N;
+    int pblk_begin, cblk_begin;
+    int* key;
+    int* rank;
+    int* perm;
+    int* cnt;
+    int* bsum;
+};
+SortEv sort_event(void* src, void* dst, int64_t np, int N, void* scratch);
+int sort_particle_blocks(int64_t np);
+int sort_cell_blocks(int N);
+// the sort of ne events (descriptors d_ev in device memory) in one launch per stage
+void launch_sort_many(int prec, const SortEv* d_ev, int ne, int pblocks, int cblocks, cudaStream_t st);
 size_t sort_scratch_bytes(int64_t Vn, int64_t np);
 bool sort_supported(int64_t Vn);
 
 size_t particle_bytes(int prec, int64_t np);
 size_t site_bytes(int prec, int64_t Vn);
 size_t field_bytes(int prec, int64_t Vn);
+
+// context internals the batch reads and drives (capi.cu)
+struct CtxView {
+    void* field[2];
+    void* site[2];
+    void* parts;
+    int N, prec, cur;
+    int64_t step, pstep, np;
+    double dt;
+    double mass[GL_MAX_SPECIES];
+    int is_static[GL_MAX_SPECIES];
+    double t_form[GL_MAX_SPECIES];
+    int ns;
+    int reunit_count;
+    void* parts_alt;
+    int sort_every;
+    void* sort_scratch;
+};
+void ctx_view(const gl_ctx* c, CtxView* v);
+// record that the batch advanced the event by `steps` coupled steps
+void ctx_advance(gl_ctx* c, int64_t steps);
+// reorder the event's particles by cell on its stream
+void ctx_sort(gl_ctx* c);
+// exchange the particle buffer and its spare (after a batched sort into the spare)
+void ctx_swap_parts(gl_ctx* c);
+void ctx_obs_event(const gl_ctx* c, ObsEvent* o);
+size_t ctx_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t ns);
+// observables of many contexts with one wait: `launch` selects what is
+// enqueued, `what` what is read back
+gl_status ctx_observables_many(gl_ctx** cs, int n, uint32_t launch, uint32_t what, gl_obs* out);
 
 // observable slots
 enum { PO_COUNT = 0, PO_PX2, PO_PY2, PO_PL2, PO_DPT2, PO_Q2, PO_Q3, PO_N };

@@ -1,0 +1,128 @@
+// Per-species particle observables (Sec. 3.1: momentum broadening <p_T^2>,
+// <p_L^2>, <p_T^2(tau) - p_T^2(tau_form)>; Casimir drifts of the colour
+// charges) as one block's partial sums over a fixed chunk of particles.
+//
+// The particles of an event are cut into chunks of obs_chunk(np) particles,
+// one block each, and every block writes GL_MAX_SPECIES x PO_N partial values
+// (sums, or maxima for the Casimir drifts).  A second pass reduces the partials
+// of an event in a fixed order.  The chunking depends only on the event's
+// particle count, so an event gives bitwise the same observables whether it is
+// reduced on its own or inside a batch.
+//
+// Per-particle quantities are evaluated in the state's precision; every
+// accumulation is FP64.
+#pragma once
+#include "internal.h"
+#include "parts.cuh"
+#include "su3.cuh"
+
+namespace gl {
+
+static constexpr int OBS_THREADS = 256;
+static constexpr int OBS_MAX_BLOCKS = 1024;
+
+// particles per observables block: at least 1024, at most OBS_MAX_BLOCKS blocks
+__host__ __device__ inline int64_t obs_chunk(int64_t np) {
+    int64_t c = (np + OBS_MAX_BLOCKS - 1) / OBS_MAX_BLOCKS;
+    c = (c + OBS_THREADS - 1) / OBS_THREADS * OBS_THREADS;
+    return c < 1024 ? 1024 : c;
+}
+__host__ __device__ inline int obs_blocks(int64_t np) {
+    return np > 0 ? (int)((np + obs_chunk(np) - 1) / obs_chunk(np)) : 0;
+}
+
+struct ObsArgs {
+    SpeciesParams sp;
+    double q2ref[GL_MAX_SPECIES], q3ref[GL_MAX_SPECIES];
+};
+
+__device__ __forceinline__ bool po_is_max(int k) { return k == PO_Q2 || k == PO_Q3; }
+
+// p_L = p^tau sinh(eta) + w cosh(eta) with w = P_eta / t (static quarks: the
+// accumulated P_eta slot), in the precision of the state
+template <typename R>
+__device__ __forceinline__ R particle_pl(const PState<R>& p, R t, R mass, bool is_static) {
+    if (is_static) return p.Pe;
+    const R w = t > R(0) ? p.Pe / t : R(0);
+    const R ptau = sqrt(p.px * p.px + p.py * p.py + w * w + mass * mass);
+    return ptau * sinh(p.eta) + w * cosh(p.eta);
+}
+
+// partial observables of particles [c0, c1) into out[GL_MAX_SPECIES * PO_N];
+// blockDim.x == OBS_THREADS
+template <typename R>
+__device__ __forceinline__ void particle_obs_block(const Parts<R>& P, double t, uint32_t active, const ObsArgs& oa,
+                                                   int64_t c0, int64_t c1, double* out) {
+    __shared__ double wacc[OBS_THREADS / 32][GL_MAX_SPECIES * PO_N];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = lane; k < GL_MAX_SPECIES * PO_N; k += 32) wacc[warp][k] = 0.0;
+    __syncwarp();
+    for (int64_t base = c0; base < c1; base += OBS_THREADS) {
+        const int64_t i = base + threadIdx.x;
+        int s = -1;
+        double v[PO_N] = {0, 0, 0, 0, 0, 0, 0};
+        if (i < c1) {
+            s = P.sp[i];
+            if (!((active >> s) & 1u)) s = -1;
+        }
+        if (s >= 0) {
+            const PState<R> p = P.load(i);
+            const R pl = particle_pl<R>(p, (R)t, (R)oa.sp.mass[s], oa.sp.is_static[s] != 0);
+            const double px = p.px, py = p.py;
+            v[PO_COUNT] = 1.0;
+            v[PO_PX2] = px * px;
+            v[PO_PY2] = py * py;
+            v[PO_PL2] = (double)pl * (double)pl;
+            v[PO_DPT2] = px * px + py * py - P.pt0[i];
+            v[PO_Q2] = fabs((double)a_dot(p.q, p.q) - oa.q2ref[s]);
+            v[PO_Q3] = fabs((double)casimir3(p.q) - oa.q3ref[s]);
+        }
+        for (int sp_ = 0; sp_ < oa.sp.n_species; sp_++) {
+            const bool mine = s == sp_;
+            if (!__any_sync(0xffffffffu, mine)) continue;
+            double r[PO_N];
+#pragma unroll
+            for (int k = 0; k < PO_N; k++) r[k] = mine ? v[k] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int k = 0; k < PO_N; k++) {
+                    const double oth = __shfl_down_sync(0xffffffffu, r[k], o);
+                    r[k] = po_is_max(k) ? fmax(r[k], oth) : r[k] + oth;
+                }
+            if (lane == 0)
+                for (int k = 0; k < PO_N; k++) {
+                    double* a = &wacc[warp][sp_ * PO_N + k];
+                    *a = po_is_max(k) ? fmax(*a, r[k]) : *a + r[k];
+                }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < GL_MAX_SPECIES * PO_N; k += OBS_THREADS) {
+        double a = 0.0;
+        for (int w = 0; w < OBS_THREADS / 32; w++) a = po_is_max(k % PO_N) ? fmax(a, wacc[w][k]) : a + wacc[w][k];
+        out[k] = a;
+    }
+}
+
+// value k of GL_MAX_SPECIES * PO_N from nblocks partial rows: strided partial
+// results, then a fixed-order tree; blockDim.x == 256
+__device__ __forceinline__ void particle_obs_reduce(const double* partials, int nblocks, int k, double* out) {
+    __shared__ double red[256];
+    const int width = GL_MAX_SPECIES * PO_N;
+    const bool mx = po_is_max(k % PO_N);
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const double v = partials[(size_t)b * width + k];
+        a = mx ? fmax(a, v) : a + v;
+    }
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = mx ? fmax(red[threadIdx.x], red[threadIdx.x + o]) : red[threadIdx.x] + red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = red[0];
+}
+
+}  // namespace gl

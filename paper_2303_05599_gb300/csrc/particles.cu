@@ -13,6 +13,7 @@
 #include "parts.cuh"
 #include "philox.cuh"
 #include "push_body.cuh"
+#include "obs_body.cuh"
 
 namespace gl {
 
@@ -296,124 +297,38 @@ void launch_parts_convert(int prec, void* parts, int64_t np, double* stg, int to
 }
 
 // ------------------------------------------------------------ particle observables
-// per block: [species][PO_N] partial sums (count, px^2, py^2, pL^2, pT^2 - pT0^2 as
-// sums; Casimir deviations as maxima) in FP64.  Lanes reduce by warp shuffles,
-// warps keep their own slots, and blocks and warps are combined in a fixed
-// order, so the result does not depend on scheduling.
-struct ObsArgs {
-    SpeciesParams sp;
-    double q2ref[GL_MAX_SPECIES], q3ref[GL_MAX_SPECIES];
-};
-
-__device__ __forceinline__ bool po_is_max(int k) { return k == PO_Q2 || k == PO_Q3; }
-
+// one block per chunk of obs_chunk(np) particles, then one block per value
 template <typename R>
-__global__ void __launch_bounds__(256) particle_obs_kernel(Parts<R> P, double t, uint32_t active, ObsArgs oa,
-                                                           double* partials) {
-    __shared__ double wacc[8][GL_MAX_SPECIES * PO_N];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int k = lane; k < GL_MAX_SPECIES * PO_N; k += 32) wacc[warp][k] = 0.0;
-    __syncwarp();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < P.np; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        int s = -1;
-        double v[PO_N] = {0, 0, 0, 0, 0, 0, 0};
-        if (i < P.np) {
-            s = P.sp[i];
-            if (!((active >> s) & 1u)) s = -1;
-        }
-        if (s >= 0) {
-            const PState<R> p = P.load(i);
-            const double px = p.px, py = p.py, Pe = p.Pe, eta = p.eta;
-            double pl;
-            if (oa.sp.is_static[s]) {
-                pl = Pe;
-            } else {
-                const double m = oa.sp.mass[s];
-                const double w = t > 0 ? Pe / t : 0.0;
-                const double ptau = sqrt(px * px + py * py + w * w + m * m);
-                pl = ptau * sinh(eta) + w * cosh(eta);
-            }
-            A8<double> q;
-            for (int a = 0; a < 8; a++) q.v[a] = p.q.v[a];
-            const double q2 = a_dot(q, q);
-            const double q3 = casimir3(q);
-            v[PO_COUNT] = 1.0;
-            v[PO_PX2] = px * px;
-            v[PO_PY2] = py * py;
-            v[PO_PL2] = pl * pl;
-            v[PO_DPT2] = px * px + py * py - P.pt0[i];
-            v[PO_Q2] = fabs(q2 - oa.q2ref[s]);
-            v[PO_Q3] = fabs(q3 - oa.q3ref[s]);
-        }
-        for (int sp_ = 0; sp_ < oa.sp.n_species; sp_++) {
-            const bool mine = s == sp_;
-            if (!__any_sync(0xffffffffu, mine)) continue;
-            double r[PO_N];
-#pragma unroll
-            for (int k = 0; k < PO_N; k++) r[k] = mine ? v[k] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int k = 0; k < PO_N; k++) {
-                    const double oth = __shfl_down_sync(0xffffffffu, r[k], o);
-                    r[k] = po_is_max(k) ? fmax(r[k], oth) : r[k] + oth;
-                }
-            if (lane == 0)
-                for (int k = 0; k < PO_N; k++) {
-                    double* a = &wacc[warp][sp_ * PO_N + k];
-                    *a = po_is_max(k) ? fmax(*a, r[k]) : *a + r[k];
-                }
-        }
-    }
-    __syncthreads();
-    const int nw = blockDim.x >> 5;
-    for (int k = threadIdx.x; k < GL_MAX_SPECIES * PO_N; k += blockDim.x) {
-        double a = 0.0;
-        for (int w = 0; w < nw; w++) a = po_is_max(k % PO_N) ? fmax(a, wacc[w][k]) : a + wacc[w][k];
-        partials[(size_t)blockIdx.x * GL_MAX_SPECIES * PO_N + k] = a;
-    }
+__global__ void __launch_bounds__(OBS_THREADS) particle_obs_kernel(Parts<R> P, double t, uint32_t active, ObsArgs oa,
+                                                                   double* partials) {
+    const int64_t chunk = obs_chunk(P.np);
+    const int64_t c0 = (int64_t)blockIdx.x * chunk;
+    const int64_t c1 = c0 + chunk < P.np ? c0 + chunk : P.np;
+    particle_obs_block<R>(P, t, active, oa, c0, c1, partials + (size_t)blockIdx.x * GL_MAX_SPECIES * PO_N);
 }
 
-// one block per output value: strided partial sums, then a fixed-order tree
 __global__ void __launch_bounds__(256) particle_obs_finalize(const double* partials, int nblocks, double* out) {
-    __shared__ double red[256];
-    const int width = GL_MAX_SPECIES * PO_N;
-    const int k = blockIdx.x;
-    const bool mx = po_is_max(k % PO_N);
-    double a = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        const double v = partials[(size_t)b * width + k];
-        a = mx ? fmax(a, v) : a + v;
-    }
-    red[threadIdx.x] = a;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] = mx ? fmax(red[threadIdx.x], red[threadIdx.x + o]) : red[threadIdx.x] + red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[k] = red[0];
+    particle_obs_reduce(partials, nblocks, blockIdx.x, out);
 }
 
 void launch_particle_obs(int prec, const void* parts, int64_t np, double t, uint32_t active_mask,
                          const SpeciesParams& sp, const double q2ref[GL_MAX_SPECIES],
-                         const double q3ref[GL_MAX_SPECIES], double* partials, int max_blocks, double* out,
-                         cudaStream_t st) {
+                         const double q3ref[GL_MAX_SPECIES], double* partials, double* out, cudaStream_t st) {
     ObsArgs oa;
     oa.sp = sp;
     for (int k = 0; k < GL_MAX_SPECIES; k++) { oa.q2ref[k] = q2ref[k]; oa.q3ref[k] = q3ref[k]; }
-    const int threads = 256;
-    int64_t blocks = (np + threads - 1) / threads;
-    if (blocks > max_blocks) blocks = max_blocks;
-    if (blocks < 1) blocks = 1;
+    const int blocks = obs_blocks(np);
+    if (blocks < 1) {
+        cudaMemsetAsync(out, 0, GL_MAX_SPECIES * PO_N * sizeof(double), st);
+        return;
+    }
     if (prec == 0)
-        particle_obs_kernel<double><<<(unsigned)blocks, threads, 0, st>>>(carve_parts<double>((void*)parts, np), t,
-                                                                          active_mask, oa, partials);
+        particle_obs_kernel<double><<<blocks, OBS_THREADS, 0, st>>>(carve_parts<double>((void*)parts, np), t,
+                                                                    active_mask, oa, partials);
     else
-        particle_obs_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(carve_parts<float>((void*)parts, np), t,
-                                                                         active_mask, oa, partials);
-    particle_obs_finalize<<<GL_MAX_SPECIES * PO_N, 256, 0, st>>>(partials, (int)blocks, out);
+        particle_obs_kernel<float><<<blocks, OBS_THREADS, 0, st>>>(carve_parts<float>((void*)parts, np), t,
+                                                                   active_mask, oa, partials);
+    particle_obs_finalize<<<GL_MAX_SPECIES * PO_N, 256, 0, st>>>(partials, blocks, out);
 }
 
 }  // namespace gl

@@ -10,6 +10,8 @@
 // The original index travels with each particle, so downloads can restore the
 // caller's order.  Only the physics-free ordering changes; every particle's
 // update is independent of it.
+#include <string.h>
+
 #include "internal.h"
 #include "parts.cuh"
 
@@ -25,26 +27,76 @@ size_t sort_scratch_bytes(int64_t Vn, int64_t np) {
 
 bool sort_supported(int64_t Vn) { return Vn <= (int64_t)SCAN_CHUNK * SCAN_MAX_BLOCKS; }
 
+// Every kernel runs over the particles or the cells of one or many events.
+// Particle-indexed launches give each event ceil(np / SORT_PB) blocks of
+// SORT_PB particles, cell-indexed launches ceil(Vn / SCAN_CHUNK) blocks of
+// SCAN_CHUNK cells (one scan chunk); a block finds its event by binary search
+// in the descriptors, or takes the single descriptor passed by value.
+static constexpr int SORT_T = 256, SORT_PB = 1024;
+
+__device__ __forceinline__ int sort_find(const SortEv* ev, int ne, int block, bool cells) {
+    int lo = 0, hi = ne - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((cells ? ev[mid].cblk_begin : ev[mid].pblk_begin) <= block) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// the block's event and its block index within the event
+struct SortBlock {
+    SortEv d;
+    int b;
+};
+__device__ __forceinline__ SortBlock sort_block(const SortEv* ev, int ne, const SortEv& one, bool cells) {
+    __shared__ int s_e;
+    SortBlock r;
+    if (ev) {
+        if (threadIdx.x == 0) s_e = sort_find(ev, ne, blockIdx.x, cells);
+        __syncthreads();
+        r.d = ev[s_e];
+    } else {
+        r.d = one;
+    }
+    r.b = blockIdx.x - (cells ? r.d.cblk_begin : r.d.pblk_begin);
+    return r;
+}
+
+__global__ void __launch_bounds__(SORT_T) zero_counts_kernel(const SortEv* ev, int ne, SortEv one) {
+    const SortBlock k = sort_block(ev, ne, one, true);
+    const int64_t Vn = (int64_t)k.d.N * k.d.N;
+    const int64_t c0 = (int64_t)k.b * SCAN_CHUNK;
+    for (int64_t c = c0 + threadIdx.x; c < c0 + SCAN_CHUNK && c < Vn; c += SORT_T) k.d.cnt[c] = 0;
+}
+
 template <typename R>
-__global__ void cell_count_kernel(Parts<R> P, int N, int* cnt, int* key, int* rank) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.np; i += (int64_t)gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(SORT_T) cell_count_kernel(const SortEv* ev, int ne, SortEv one) {
+    const SortBlock k = sort_block(ev, ne, one, false);
+    const Parts<R> P = carve_parts<R>(k.d.src, k.d.np);
+    const int N = k.d.N;
+    const int64_t i0 = (int64_t)k.b * SORT_PB;
+    for (int64_t i = i0 + threadIdx.x; i < i0 + SORT_PB && i < k.d.np; i += SORT_T) {
         const PState<R> p = P.load(i);
         const int ix = wrapi((int)floor(p.x + R(0.5)), N), iy = wrapi((int)floor(p.y + R(0.5)), N);
         const int c = iy * N + ix;
-        key[i] = c;
-        rank[i] = atomicAdd(&cnt[c], 1);
+        k.d.key[i] = c;
+        k.d.rank[i] = atomicAdd(&k.d.cnt[c], 1);
     }
 }
 
-// exclusive scan of cnt[0, n) in place, per chunk of SCAN_CHUNK; chunk totals to bsum
-__global__ void __launch_bounds__(SCAN_T) scan_chunks_kernel(int* cnt, int64_t n, int* bsum) {
+// exclusive scan of one chunk of SCAN_CHUNK counts in place; its total to bsum
+__global__ void __launch_bounds__(SCAN_T) scan_chunks_kernel(const SortEv* ev, int ne, SortEv one) {
+    const SortBlock k = sort_block(ev, ne, one, true);
     __shared__ int warp_tot[SCAN_T / 32];
-    const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_PER;
+    int* cnt = k.d.cnt;
+    const int64_t n = (int64_t)k.d.N * k.d.N;
+    const int64_t base = (int64_t)k.b * SCAN_CHUNK + threadIdx.x * SCAN_PER;
     int v[SCAN_PER], s = 0;
 #pragma unroll
-    for (int k = 0; k < SCAN_PER; k++) {
-        v[k] = base + k < n ? cnt[base + k] : 0;
-        s += v[k];
+    for (int q = 0; q < SCAN_PER; q++) {
+        v[q] = base + q < n ? cnt[base + q] : 0;
+        s += v[q];
     }
     // inclusive warp scan of the per-thread totals
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -60,21 +112,25 @@ __global__ void __launch_bounds__(SCAN_T) scan_chunks_kernel(int* cnt, int64_t n
     for (int w = 0; w < warp; w++) woff += warp_tot[w];
     int run = woff + inc - s;  // exclusive prefix of this thread
 #pragma unroll
-    for (int k = 0; k < SCAN_PER; k++) {
-        if (base + k < n) cnt[base + k] = run;
-        run += v[k];
+    for (int q = 0; q < SCAN_PER; q++) {
+        if (base + q < n) cnt[base + q] = run;
+        run += v[q];
     }
-    if (threadIdx.x == SCAN_T - 1) bsum[blockIdx.x] = run;
+    if (threadIdx.x == SCAN_T - 1) k.d.bsum[k.b] = run;
 }
 
-// exclusive scan of the chunk totals (one block), then off[n] = total
-__global__ void __launch_bounds__(1024) scan_top_kernel(int* bsum, int nb, int* off, int64_t n) {
+// one block per event: exclusive scan of the chunk totals, then off[Vn] = total
+__global__ void __launch_bounds__(1024) scan_top_kernel(const SortEv* ev, SortEv one) {
+    const SortEv d = ev ? ev[blockIdx.x] : one;
     __shared__ int part[1024];
+    const int64_t n = (int64_t)d.N * d.N;
+    const int nb = (int)((n + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    int* bsum = d.bsum;
     const int per = (nb + 1023) / 1024;
     const int b0 = threadIdx.x * per;
     int s = 0;
-    for (int k = 0; k < per; k++)
-        if (b0 + k < nb) s += bsum[b0 + k];
+    for (int q = 0; q < per; q++)
+        if (b0 + q < nb) s += bsum[b0 + q];
     part[threadIdx.x] = s;
     __syncthreads();
     for (int o = 1; o < 1024; o <<= 1) {
@@ -84,28 +140,38 @@ __global__ void __launch_bounds__(1024) scan_top_kernel(int* bsum, int nb, int* 
         __syncthreads();
     }
     int run = part[threadIdx.x] - s;
-    for (int k = 0; k < per; k++)
-        if (b0 + k < nb) {
-            const int v = bsum[b0 + k];
-            bsum[b0 + k] = run;
+    for (int q = 0; q < per; q++)
+        if (b0 + q < nb) {
+            const int v = bsum[b0 + q];
+            bsum[b0 + q] = run;
             run += v;
         }
-    if (threadIdx.x == 1023) off[n] = part[1023];
+    if (threadIdx.x == 1023) d.cnt[n] = part[1023];
 }
 
-__global__ void scan_add_kernel(int* cnt, int64_t n, const int* bsum) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        cnt[i] += bsum[i / SCAN_CHUNK];
+__global__ void __launch_bounds__(SORT_T) scan_add_kernel(const SortEv* ev, int ne, SortEv one) {
+    const SortBlock k = sort_block(ev, ne, one, true);
+    const int64_t Vn = (int64_t)k.d.N * k.d.N;
+    const int add = k.d.bsum[k.b];
+    const int64_t c0 = (int64_t)k.b * SCAN_CHUNK;
+    for (int64_t c = c0 + threadIdx.x; c < c0 + SCAN_CHUNK && c < Vn; c += SORT_T) k.d.cnt[c] += add;
 }
 
-__global__ void scatter_kernel(int64_t np, const int* key, const int* rank, const int* off, int* perm) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x)
-        perm[off[key[i]] + rank[i]] = (int)i;
+__global__ void __launch_bounds__(SORT_T) scatter_kernel(const SortEv* ev, int ne, SortEv one) {
+    const SortBlock k = sort_block(ev, ne, one, false);
+    const int64_t i0 = (int64_t)k.b * SORT_PB;
+    for (int64_t i = i0 + threadIdx.x; i < i0 + SORT_PB && i < k.d.np; i += SORT_T)
+        k.d.perm[k.d.cnt[k.d.key[i]] + k.d.rank[i]] = (int)i;
 }
 
 // insertion sort of each cell's (short) segment of perm
-__global__ void cell_order_kernel(int64_t Vn, const int* off, int* perm) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < Vn; c += (int64_t)gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(SORT_T) cell_order_kernel(const SortEv* ev, int ne, SortEv one) {
+    const SortBlock k = sort_block(ev, ne, one, true);
+    const int64_t Vn = (int64_t)k.d.N * k.d.N;
+    const int* off = k.d.cnt;
+    int* perm = k.d.perm;
+    const int64_t c0 = (int64_t)k.b * SCAN_CHUNK;
+    for (int64_t c = c0 + threadIdx.x; c < c0 + SCAN_CHUNK && c < Vn; c += SORT_T) {
         const int b = off[c], e = off[c + 1];
         for (int i = b + 1; i < e; i++) {
             const int v = perm[i];
@@ -120,9 +186,12 @@ __global__ void cell_order_kernel(int64_t Vn, const int* off, int* perm) {
 }
 
 template <typename R>
-__global__ void gather_kernel(Parts<R> src, Parts<R> dst, const int* perm) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < src.np; j += (int64_t)gridDim.x * blockDim.x) {
-        const int i = perm[j];
+__global__ void __launch_bounds__(SORT_T) gather_kernel(const SortEv* ev, int ne, SortEv one) {
+    const SortBlock k = sort_block(ev, ne, one, false);
+    const Parts<R> src = carve_parts<R>(k.d.src, k.d.np), dst = carve_parts<R>(k.d.dst, k.d.np);
+    const int64_t j0 = (int64_t)k.b * SORT_PB;
+    for (int64_t j = j0 + threadIdx.x; j < j0 + SORT_PB && j < k.d.np; j += SORT_T) {
+        const int i = k.d.perm[j];
         dst.store(j, src.load(i));
         dst.sp[j] = src.sp[i];
         dst.pt0[j] = src.pt0[i];
@@ -130,37 +199,54 @@ __global__ void gather_kernel(Parts<R> src, Parts<R> dst, const int* perm) {
     }
 }
 
-static unsigned grid(int64_t n, int t) {
-    int64_t b = (n + t - 1) / t;
-    if (b > 152 * 32) b = 152 * 32;
-    return (unsigned)(b < 1 ? 1 : b);
+SortEv sort_event(void* src, void* dst, int64_t np, int N, void* scratch) {
+    const int64_t Vn = (int64_t)N * N;
+    SortEv d;
+    memset(&d, 0, sizeof d);
+    char* c = (char*)scratch;
+    d.src = src;
+    d.dst = dst;
+    d.np = np;
+    d.N = N;
+    d.key = (int*)c; c += align256(4 * (size_t)np);
+    d.rank = (int*)c; c += align256(4 * (size_t)np);
+    d.perm = (int*)c; c += align256(4 * (size_t)np);
+    d.cnt = (int*)c; c += align256(4 * ((size_t)Vn + 1));
+    d.bsum = (int*)c;
+    return d;
 }
 
+int sort_particle_blocks(int64_t np) { return (int)((np + SORT_PB - 1) / SORT_PB); }
+int sort_cell_blocks(int N) { return (int)(((int64_t)N * N + SCAN_CHUNK - 1) / SCAN_CHUNK); }
+
+// the stages over `pblocks` particle blocks and `cblocks` cell blocks of
+// `ne` events (descriptors in device memory), or of the single event `one`
 template <typename R>
-static void sort_t(void* src, void* dst, int64_t np, int N, void* scratch, cudaStream_t st) {
-    const int64_t Vn = (int64_t)N * N;
-    char* c = (char*)scratch;
-    int* key = (int*)c; c += align256(4 * (size_t)np);
-    int* rank = (int*)c; c += align256(4 * (size_t)np);
-    int* perm = (int*)c; c += align256(4 * (size_t)np);
-    int* cnt = (int*)c; c += align256(4 * ((size_t)Vn + 1));
-    int* bsum = (int*)c;
-    const int nb = (int)((Vn + SCAN_CHUNK - 1) / SCAN_CHUNK);
-    Parts<R> ps = carve_parts<R>(src, np), pd = carve_parts<R>(dst, np);
-    cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)Vn, st);
-    cell_count_kernel<R><<<grid(np, 256), 256, 0, st>>>(ps, N, cnt, key, rank);
-    scan_chunks_kernel<<<nb, SCAN_T, 0, st>>>(cnt, Vn, bsum);
-    scan_top_kernel<<<1, 1024, 0, st>>>(bsum, nb, cnt, Vn);
-    scan_add_kernel<<<grid(Vn, 256), 256, 0, st>>>(cnt, Vn, bsum);
-    scatter_kernel<<<grid(np, 256), 256, 0, st>>>(np, key, rank, cnt, perm);
-    cell_order_kernel<<<grid(Vn, 128), 128, 0, st>>>(Vn, cnt, perm);
-    gather_kernel<R><<<grid(np, 128), 128, 0, st>>>(ps, pd, perm);
+static void sort_stages(const SortEv* ev, int ne, const SortEv& one, int pblocks, int cblocks, cudaStream_t st) {
+    zero_counts_kernel<<<cblocks, SORT_T, 0, st>>>(ev, ne, one);
+    cell_count_kernel<R><<<pblocks, SORT_T, 0, st>>>(ev, ne, one);
+    scan_chunks_kernel<<<cblocks, SCAN_T, 0, st>>>(ev, ne, one);
+    scan_top_kernel<<<ev ? ne : 1, 1024, 0, st>>>(ev, one);
+    scan_add_kernel<<<cblocks, SORT_T, 0, st>>>(ev, ne, one);
+    scatter_kernel<<<pblocks, SORT_T, 0, st>>>(ev, ne, one);
+    cell_order_kernel<<<cblocks, SORT_T, 0, st>>>(ev, ne, one);
+    gather_kernel<R><<<pblocks, SORT_T, 0, st>>>(ev, ne, one);
 }
 
 void launch_sort(int prec, void* src, void* dst, int64_t np, int N, void* scratch, cudaStream_t st) {
     if (np <= 0) return;
-    if (prec == 0) sort_t<double>(src, dst, np, N, scratch, st);
-    else sort_t<float>(src, dst, np, N, scratch, st);
+    const SortEv one = sort_event(src, dst, np, N, scratch);
+    const int pb = sort_particle_blocks(np), cb = sort_cell_blocks(N);
+    if (prec == 0) sort_stages<double>(nullptr, 1, one, pb, cb, st);
+    else sort_stages<float>(nullptr, 1, one, pb, cb, st);
+}
+
+void launch_sort_many(int prec, const SortEv* d_ev, int ne, int pblocks, int cblocks, cudaStream_t st) {
+    if (ne <= 0 || pblocks <= 0) return;
+    SortEv none;
+    memset(&none, 0, sizeof none);
+    if (prec == 0) sort_stages<double>(d_ev, ne, none, pblocks, cblocks, st);
+    else sort_stages<float>(d_ev, ne, none, pblocks, cblocks, st);
 }
 
 }  // namespace gl

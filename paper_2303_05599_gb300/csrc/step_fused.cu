@@ -4,7 +4,7 @@
 namespace gl {
 
 template <typename R, int TX, int TY, bool SITE>
-__global__ void __launch_bounds__(TX * TY) fused_step_kernel(Fields<R> in, Fields<R> out,
+__global__ void __launch_bounds__(TX * TY, (Tile<R, TX, TY>::min_blocks)) fused_step_kernel(Fields<R> in, Fields<R> out,
                                                              typename Prec<R>::V* site, StepArgs a) {
     fused_tile<R, TX, TY, SITE>(in, out, site, a, blockIdx.x);
 }

@@ -24,18 +24,36 @@ def gpu_ready():
     B.lib()
 
 
-def events(prec):
+def events(prec, sort_every=0):
     out = []
     for e, N in enumerate([16, 40, 24, 64]):
-        out.append(W.Workload("b%d" % e, N=N, L_fm=0.04 * N * 2, Ns=4, precision=prec, seed=11 + e, sort_every=0,
+        out.append(W.Workload("b%d" % e, N=N, L_fm=0.04 * N * 2, Ns=4, precision=prec, seed=11 + e,
+                              sort_every=sort_every,
                               species=[W.Species(W.M_CHARM, 0.06, 300 + 50 * e, W.REP_F, W.MOM_UNIFORM_PT, 0.0, 5.0),
                                        W.Species(math.inf, 0.0, 40, W.REP_A, W.MOM_FIXED_PT, 0.0)]))
     return out
 
 
-@pytest.mark.parametrize("prec", [W.FP64, W.FP32_2ROW])
-def test_batch_equals_single_events(prec):
-    ws = events(prec)
+OBS_ARRAYS = ("n_active", "sum_px2", "sum_py2", "sum_pL2", "sum_dpT2", "casimir2_dev", "casimir3_dev")
+OBS_SCALARS = ("gauss_max", "gauss_rms", "unitarity_max", "mean_trE_T2", "mean_trE_L2", "mean_trB_T2",
+               "mean_trB_L2")
+
+
+def same_obs(a, b, n_species):
+    for f in OBS_ARRAYS:
+        x, y = list(getattr(a, f))[:n_species], list(getattr(b, f))[:n_species]
+        assert np.array_equal(x, y, equal_nan=True), (f, x, y)
+    for f in OBS_SCALARS:
+        x, y = getattr(a, f), getattr(b, f)
+        assert x == y or (math.isnan(x) and math.isnan(y)), (f, x, y)
+
+
+@pytest.mark.parametrize("prec,sort_every", [(W.FP64, 0), (W.FP32_2ROW, 0), (W.FP32_2ROW, 4)])
+def test_batch_equals_single_events(prec, sort_every):
+    """Fields, particles and observables (the particle sums come from the
+    batched reduction) bitwise equal to each event run alone, with and
+    without the periodic cell sort."""
+    ws = events(prec, sort_every)
     batch = B.Batch(ws)
     with torch.cuda.stream(batch.stream):
         batch.init()
@@ -45,6 +63,7 @@ def test_batch_equals_single_events(prec):
         batch.step(7)
         batch.step(steps - 7)
         torch.cuda.synchronize()
+        obs = batch.observables()
         for e, w in enumerate(ws):
             single = B.Event(w, stream=batch.stream)
             single.glasma_init()
@@ -54,9 +73,36 @@ def test_batch_equals_single_events(prec):
             for buf in (B.GL_BUF_LINKS, B.GL_BUF_E, B.GL_BUF_PI, B.GL_BUF_PHI, B.GL_BUF_PARTICLES, B.GL_BUF_SITE):
                 a, b = be.download(buf), single.download(buf)
                 assert np.array_equal(a, b), (e, buf, np.abs(a - b).max())
-        obs = batch.observables()
+            same_obs(obs[e], single.observables(), 2)
         assert all(o.step == steps for o in obs)
         assert all(o.n_active[0] > 0 for o in obs)
+        assert all(o.what == B.GL_OBS_ALL for o in obs)
+
+
+def test_observables_parts():
+    """GL_OBS_PARTICLES and GL_OBS_FIELDS each give their part of the full
+    observables bitwise and NaN (counts 0) for the other."""
+    ws = events(W.FP32_2ROW)
+    batch = B.Batch(ws)
+    with torch.cuda.stream(batch.stream):
+        batch.init()
+        batch.step(9)
+        full = batch.observables()
+        part = batch.observables(B.GL_OBS_PARTICLES)
+        fld = batch.observables(B.GL_OBS_FIELDS)
+        single_part = [ev.observables(B.GL_OBS_PARTICLES) for ev in batch.events]
+    for e in range(len(ws)):
+        assert part[e].what == B.GL_OBS_PARTICLES and fld[e].what == B.GL_OBS_FIELDS
+        for f in OBS_ARRAYS:
+            assert np.array_equal(list(getattr(part[e], f))[:2], list(getattr(full[e], f))[:2])
+            assert np.array_equal(list(getattr(single_part[e], f))[:2], list(getattr(full[e], f))[:2])
+            if f == "n_active":
+                assert list(fld[e].n_active)[:2] == [0, 0]
+            else:
+                assert all(math.isnan(v) for v in list(getattr(fld[e], f))[:2])
+        for f in OBS_SCALARS:
+            assert getattr(fld[e], f) == getattr(full[e], f)
+            assert math.isnan(getattr(part[e], f))
 
 
 def test_batch_rejects_events_at_different_steps():
