@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
     ap.add_argument("--reunit-every", type=int, default=None)
     ap.add_argument("--events", type=int, default=0, help="events per GPU (default 30; 1 for n1024_mixed)")
+    ap.add_argument("--launch", default=None, help="fixed launch shapes TILE:PUSH_BLOCK (e.g. 32x8:128) "
+                                                   "instead of the autotuner")
     return ap.parse_args()
 
 
@@ -200,7 +202,12 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         batch = B.Batch(ws, stream=stream)
         batch.init()
-        tune = batch.autotune()
+        if args.launch:
+            tile, pb = args.launch.split(":")
+            batch.set_launch(tile, int(pb))
+            tune = {"tile": tile, "push_block": int(pb), "fixed": True}
+        else:
+            tune = batch.autotune()
         batch.step(args.warmup)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)

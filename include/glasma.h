@@ -242,12 +242,18 @@ gl_ctx* gl_batch_event(gl_batch* batch, int32_t e);
 /* glasma_init and wong_init of every event. */
 gl_status gl_batch_init(gl_batch* batch);
 
-/* Choose the field tile shape and the push block size from timed trial
- * launches that do not change the state.  Outputs may be NULL. */
+/* Choose the field tile shape (0: 32x8, 1: 32x4, 2: 32x16; FP64 batches use
+ * 32x4) and the push block size from timed trial launches that do not change
+ * the state.  Outputs may be NULL. */
 gl_status gl_batch_autotune(gl_batch* batch, int32_t* tile_shape, int32_t* push_block);
 
-/* Trial timings of the last autotune, ms: field_ms[2] (tile shapes 32x8,
- * 32x4), push_ms[3] (blocks 128, 256, 512). */
+/* Set the launch shapes directly (tile shape as above; push block 128, 256 or
+ * 512).  Results do not depend on them.  GL_ERR_ARG for other values or a
+ * tile other than 32x4 in an FP64 batch. */
+gl_status gl_batch_set_launch(gl_batch* batch, int32_t tile_shape, int32_t push_block);
+
+/* Trial timings of the last autotune, ms: field_ms[3] by tile shape (0 where
+ * not tried), push_ms[3] (blocks 128, 256, 512). */
 gl_status gl_batch_tuning(const gl_batch* batch, float* field_ms, float* push_ms);
 
 /* n_steps coupled steps of every event (all events at one common step). */

@@ -84,11 +84,13 @@ SIGNATURES = {
     "gl_batch_step": (ctypes.c_int, [_P, ctypes.c_int32]),
     "gl_batch_step_timed": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "gl_batch_observables": (ctypes.c_int, [_P, _P]),
+    "gl_batch_set_launch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "gl_batch_observables_ex": (ctypes.c_int, [_P, ctypes.c_uint32, _P]),
 }
 
 GL_NOALLOC_MAX_PARTICLES = 2097152
 GL_OBS_PARTICLES, GL_OBS_FIELDS, GL_OBS_ALL = 1, 2, 3
+BATCH_TILES = ("32x8", "32x4", "32x16")
 
 _lib = None
 
@@ -296,10 +298,14 @@ class Batch:
         t = ctypes.c_int32()
         p = ctypes.c_int32()
         self._chk(lib().gl_batch_autotune(self.b, ctypes.byref(t), ctypes.byref(p)), "gl_batch_autotune")
-        f = (ctypes.c_float * 2)()
+        f = (ctypes.c_float * 3)()
         q = (ctypes.c_float * 3)()
         lib().gl_batch_tuning(self.b, f, q)
-        return {"tile": ("32x8", "32x4")[t.value], "push_block": p.value, "field_ms": list(f), "push_ms": list(q)}
+        return {"tile": BATCH_TILES[t.value], "push_block": p.value, "field_ms": list(f), "push_ms": list(q)}
+
+    def set_launch(self, tile, push_block):
+        """Fix the launch shapes (tile name from BATCH_TILES, push block size)."""
+        self._chk(lib().gl_batch_set_launch(self.b, BATCH_TILES.index(tile), push_block), "gl_batch_set_launch")
 
     def step(self, n=1):
         self._chk(lib().gl_batch_step(self.b, n), "gl_batch_step")

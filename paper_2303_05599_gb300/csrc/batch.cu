@@ -72,42 +72,63 @@ __device__ __forceinline__ int find_event(const EvDesc* ev, int ne, int block, b
 
 template <typename R, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY, (Tile<R, TX, TY>::min_blocks)) batch_field_kernel(BatchArgs b) {
+    // the block's event and step scalars, once per block
     __shared__ int s_e;
-    if (threadIdx.x == 0) s_e = find_event(b.ev, b.ne, blockIdx.x, true);
+    __shared__ int64_t s_n;
+    __shared__ StepR<R> s_a;
+    if (threadIdx.x == 0) {
+        const int e = find_event(b.ev, b.ne, blockIdx.x, true);
+        const int64_t n = *b.clock;
+        const int reunit = b.reunit_every > 0 && (n + 1) % b.reunit_every == 0;
+        s_e = e;
+        s_n = n;
+        s_a = step_r<R>(step_args(b.ev[e].N, b.ev[e].tiles_x, n, b.dt, reunit));
+    }
     __syncthreads();
     const EvDesc& d = b.ev[s_e];
-    const int64_t n = *b.clock;
+    const int64_t n = s_n;
     const int64_t Vn = (int64_t)d.N * d.N;
-    const int reunit = b.reunit_every > 0 && (n + 1) % b.reunit_every == 0;
-    const StepArgs a = step_args(d.N, d.tiles_x, n, b.dt, reunit);
     fused_tile<R, TX, TY, true>(carve_fields<R>(d.field[n & 1], Vn), carve_fields<R>(d.field[(n + 1) & 1], Vn),
-                                (typename Prec<R>::V*)d.site[n & 1], a, blockIdx.x - d.tile_begin);
+                                (typename Prec<R>::V*)d.site[n & 1], s_a, blockIdx.x - d.tile_begin);
 }
 
 // push of the particles at t_{clock - lag}
 template <typename R>
 __global__ void batch_push_kernel(BatchArgs b, int lag) {
+    // the block's event, time scalars and species table, once per block
     __shared__ int s_e;
-    if (threadIdx.x == 0) s_e = find_event(b.ev, b.ne, blockIdx.x, false);
+    __shared__ int64_t s_n;
+    __shared__ uint32_t s_active;
+    __shared__ R s_t, s_dt, s_dto;
+    __shared__ SpeciesArgs<R> s_sa;
+    if (threadIdx.x == 0) {
+        const int e = find_event(b.ev, b.ne, blockIdx.x, false);
+        const EvDesc& d = b.ev[e];
+        const int64_t n = *b.clock - lag;
+        const double t = n * b.dt;
+        uint32_t active = 0;
+        for (int k = 0; k < GL_MAX_SPECIES; k++) {
+            if (k < d.n_species && t >= d.t_form[k]) active |= 1u << k;
+            s_sa.mass[k] = (R)(d.is_static[k] ? 0.0 : d.mass[k]);
+            s_sa.is_static[k] = d.is_static[k];
+        }
+        s_e = e;
+        s_n = n;
+        s_active = active;
+        s_t = (R)t;
+        s_dt = (R)b.dt;
+        s_dto = (R)(t > 0 ? b.dt / t : 0.0);
+    }
     __syncthreads();
     const EvDesc& d = b.ev[s_e];
-    const int64_t n = *b.clock - lag;
-    const double t = n * b.dt;
-    uint32_t active = 0;
-    SpeciesArgs<R> sa;
-    for (int k = 0; k < GL_MAX_SPECIES; k++) {
-        if (k < d.n_species && t >= d.t_form[k]) active |= 1u << k;
-        sa.mass[k] = (R)(d.is_static[k] ? 0.0 : d.mass[k]);
-        sa.is_static[k] = d.is_static[k];
-    }
+    const int64_t n = s_n;
     const int64_t Vn = (int64_t)d.N * d.N;
     const Parts<R> P = carve_parts<R>(d.parts, d.np);
     const Fields<R> bn1 = carve_fields<R>(d.field[(n + 1) & 1], Vn);
     const int64_t base = (int64_t)(blockIdx.x - d.chunk_begin) * PUSH_CHUNK;
     const int64_t end = base + PUSH_CHUNK < d.np ? base + PUSH_CHUNK : d.np;
     for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x)
-        push_one<R>((const typename Prec<R>::V*)d.site[n & 1], bn1, P, i, d.N, (R)t, (R)b.dt,
-                    (R)(t > 0 ? b.dt / t : 0.0), active, sa);
+        push_one<R>((const typename Prec<R>::V*)d.site[n & 1], bn1, P, i, d.N, s_t, s_dt, s_dto, s_active, s_sa);
 }
 
 __global__ void tick_kernel(int64_t* clock) { *clock += 1; }
@@ -677,6 +698,17 @@ gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
         }
     }
     return ctx_observables_many(b->ev, b->ne, what & ~GL_OBS_PARTICLES, what, out);
+}
+
+gl_status gl_batch_set_launch(gl_batch* b, int32_t tile, int32_t push_block) {
+    if (!b || tile < 0 || tile >= N_TILES) return GL_ERR_ARG;
+    if (b->prec == GL_FP64 && tile != TILE_32x4) return GL_ERR_ARG;
+    bool ok = false;
+    for (int k = 0; k < 3; k++) ok = ok || PUSH_BLOCKS[k] == push_block;
+    if (!ok) return GL_ERR_ARG;
+    b->tile = tile;
+    b->push_block = push_block;
+    return GL_OK;
 }
 
 gl_status gl_batch_tuning(const gl_batch* b, float* field_ms, float* push_ms) {

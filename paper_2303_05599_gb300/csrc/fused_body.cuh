@@ -152,11 +152,32 @@ struct StepArgs {
     int reunit;
 };
 
+// the step scalars in the kernel's precision (converted once per launch or
+// block: double arithmetic costs far more than single on GPUs with slow FP64)
+template <typename R>
+struct StepR {
+    int N, tiles_x, reunit;
+    R t, dt, inv_t, dt_over_th, dt_th;
+};
+template <typename R>
+__host__ __device__ inline StepR<R> step_r(const StepArgs& a) {
+    StepR<R> r;
+    r.N = a.N;
+    r.tiles_x = a.tiles_x;
+    r.reunit = a.reunit;
+    r.t = (R)a.t;
+    r.dt = (R)a.dt;
+    r.inv_t = (R)a.inv_t;
+    r.dt_over_th = (R)a.dt_over_th;
+    r.dt_th = (R)a.dt_th;
+    return r;
+}
+
 // one tile (index `tile` of a lattice with tiles_x tiles per row); the caller
 // provides the dynamic shared memory of Tile<R, TX, TY>::bytes
 template <typename R, int TX, int TY, bool SITE>
 __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>& out, typename Prec<R>::V* site,
-                                           const StepArgs& a, int tile) {
+                                           const StepR<R>& a, int tile) {
     using T = Tile<R, TX, TY>;
     using Vec = typename Prec<R>::V;
     constexpr int LP = T::LP, AP = T::AP;
@@ -172,7 +193,7 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
     const int64_t Vn = (int64_t)N * N;
     const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
     const int tid = threadIdx.x;
-    const R t = (R)a.t, dt = (R)a.dt, inv_t = (R)a.inv_t;
+    const R t = a.t, dt = a.dt, inv_t = a.inv_t;
 
     // ---- phase 1: asynchronous copies of the tile's inputs
     for (int i = tid; i < LN; i += NT) {
@@ -261,7 +282,7 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
     for (int c = 0; c < 8; c++) {
         const R lap = my_tx.v[c] + my_ty.v[c] + bx.v[c] + by.v[c] - R(4) * ph.v[c];
         p_new.v[c] = p_old.v[c] + dt * inv_t * lap;
-        ph_new.v[c] = ph.v[c] + (R)a.dt_th * p_new.v[c];
+        ph_new.v[c] = ph.v[c] + a.dt_th * p_new.v[c];
     }
     if (SITE) {
         // E_i = (1/4t){e_i(s) + U_i(s-i)^+ e_i(s-i) U_i(s-i)}, e summed over n -+ 1/2
@@ -291,8 +312,8 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
     store_alg(out.e + (size_t)AP * Vn, g, Vn, my_ey);
     store_alg(out.pi, g, Vn, p_new);
     store_alg(out.phi, g, Vn, ph_new);
-    M3<R> nx = mul(exp_i_alg<R, ExpN<R>::n>(my_ex, (R)a.dt_over_th), s_link(sU, 0, l, LN));
-    M3<R> ny = mul(exp_i_alg<R, ExpN<R>::n>(my_ey, (R)a.dt_over_th), s_link(sU, 1, l, LN));
+    M3<R> nx = mul(exp_i_alg<R, ExpN<R>::n>(my_ex, a.dt_over_th), s_link(sU, 0, l, LN));
+    M3<R> ny = mul(exp_i_alg<R, ExpN<R>::n>(my_ey, a.dt_over_th), s_link(sU, 1, l, LN));
     if (a.reunit) { reunit(nx); reunit(ny); }
     store_link(out.U, 0, g, Vn, nx);
     store_link(out.U, 1, g, Vn, ny);

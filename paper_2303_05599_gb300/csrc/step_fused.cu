@@ -5,7 +5,7 @@ namespace gl {
 
 template <typename R, int TX, int TY, bool SITE>
 __global__ void __launch_bounds__(TX * TY, (Tile<R, TX, TY>::min_blocks)) fused_step_kernel(Fields<R> in, Fields<R> out,
-                                                             typename Prec<R>::V* site, StepArgs a) {
+                                                             typename Prec<R>::V* site, StepR<R> a) {
     fused_tile<R, TX, TY, SITE>(in, out, site, a, blockIdx.x);
 }
 
@@ -25,7 +25,7 @@ static void launch_t(void* in, void* out, void* site, int N, int64_t n, double d
     StepArgs a = step_args(N, (N + TX - 1) / TX, n, dt, reunit);
     const int tiles_y = (N + TY - 1) / TY;
     fused_step_kernel<R, TX, TY, SITE><<<a.tiles_x * tiles_y, TX * TY, T::bytes, st>>>(
-        carve_fields<R>(in, Vn), carve_fields<R>(out, Vn), (typename Prec<R>::V*)site, a);
+        carve_fields<R>(in, Vn), carve_fields<R>(out, Vn), (typename Prec<R>::V*)site, step_r<R>(a));
 }
 
 void launch_fused_step(int prec, void* in, void* out, void* site, int N, int64_t n, double dt, int reunit, int tile,
