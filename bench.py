@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
     ap.add_argument("--reunit-every", type=int, default=None)
     ap.add_argument("--events", type=int, default=0, help="events per GPU (default 30; 1 for n1024_mixed)")
-    ap.add_argument("--launch", default=None, help="fixed launch shapes TILE:PUSH_BLOCK (e.g. 32x8:128) "
+    ap.add_argument("--launch", default=None, help="fixed launch shapes and schedule "
+                                                   "TILE:PUSH_BLOCK:PUSH_CHUNK:fused|streams[:PUSH_GRID] "
+                                                   "(e.g. 32x8:128:1024:streams:1) "
                                                    "instead of the autotuner")
     return ap.parse_args()
 
@@ -203,9 +205,10 @@ def run_ours(args):
         batch = B.Batch(ws, stream=stream)
         batch.init()
         if args.launch:
-            tile, pb = args.launch.split(":")
-            batch.set_launch(tile, int(pb))
-            tune = {"tile": tile, "push_block": int(pb), "fixed": True}
+            parts = args.launch.split(":")
+            tile, pb, pc, mode = parts[:4]
+            batch.set_launch(tile, int(pb), int(pc), mode == "fused", int(parts[4]) if len(parts) > 4 else 0)
+            tune = dict(batch.launch(), fixed=True)
         else:
             tune = batch.autotune()
         batch.step(args.warmup)
@@ -302,7 +305,8 @@ def run_ours(args):
                        "precision": "fp32_2row" if prec else "fp64", "dtau_over_a": ws[0].dtau_over_a,
                        "reunit_every": ws[0].reunit_every, "parallelism": "events sharded over ranks",
                        "l2": "per-step working set larger than L2 (no flush)",
-                       "launch": "one CUDA-graph replay per step: field step s overlapped with the push of s-1"},
+                       "launch": "one CUDA-graph replay per step: the field step of t_s and the push of t_{s-1}, "
+                                 "as one persistent fused launch or on two streams (autotuned)"},
             "particle_steps_per_s": world * n_active * K / t_step,
             "ensemble": {"tau_fm": obs[0].tau_fm, "per_species": ens},
             "kernel_ms_per_step": {"field_step": f_ms / K, "wong_push": p_ms / K},

@@ -242,19 +242,34 @@ gl_ctx* gl_batch_event(gl_batch* batch, int32_t e);
 /* glasma_init and wong_init of every event. */
 gl_status gl_batch_init(gl_batch* batch);
 
-/* Choose the field tile shape (0: 32x8, 1: 32x4, 2: 32x16; FP64 batches use
- * 32x4) and the push block size from timed trial launches that do not change
- * the state.  Outputs may be NULL. */
+/* Choose the launch shapes and the step schedule from timed trial launches
+ * that do not change the state (waits).  Chosen: the field tile shape (0:
+ * 32x8, 1: 32x4, 2: 32x16; FP64 batches use 32x4); the block size of the
+ * separate push kernel (128, 256, 512); and the steady-state step, either
+ *   - the field and push kernels on two streams, the push with one block per
+ *     chunk of particles or (push_grid 1, 2) that many resident 128-thread
+ *     blocks per SM launched ahead of the field tiles, or
+ *   - one persistent fused launch that interleaves field tiles and push
+ *     chunks of 512, 1024 or 2048 particles.
+ * Outputs may be NULL. */
 gl_status gl_batch_autotune(gl_batch* batch, int32_t* tile_shape, int32_t* push_block);
 
-/* Set the launch shapes directly (tile shape as above; push block 128, 256 or
- * 512).  Results do not depend on them.  GL_ERR_ARG for other values or a
- * tile other than 32x4 in an FP64 batch. */
-gl_status gl_batch_set_launch(gl_batch* batch, int32_t tile_shape, int32_t push_block);
+/* Set the launch shapes and schedule directly (values as above; fused 0 or 1;
+ * push_grid 0, 1 or 2, ignored when fused).  Results do not depend on them.
+ * GL_ERR_ARG for other values or a tile other than 32x4 in an FP64 batch. */
+gl_status gl_batch_set_launch(gl_batch* batch, int32_t tile_shape, int32_t push_block, int32_t push_chunk,
+                              int32_t fused, int32_t push_grid);
 
-/* Trial timings of the last autotune, ms: field_ms[3] by tile shape (0 where
- * not tried), push_ms[3] (blocks 128, 256, 512). */
-gl_status gl_batch_tuning(const gl_batch* batch, float* field_ms, float* push_ms);
+/* The launch shapes and schedule in use.  Outputs may be NULL. */
+gl_status gl_batch_get_launch(const gl_batch* batch, int32_t* tile_shape, int32_t* push_block,
+                              int32_t* push_chunk, int32_t* fused, int32_t* push_grid);
+
+/* Trial timings of the last autotune, ms (0 where not tried): field_ms[3] by
+ * tile shape; push_ms[3] by push block size; step_ms[8] for a whole step:
+ * [0] two streams, [1..3] fused with push chunks of 512, 1024, 2048, [4..7]
+ * two streams with push_grid 1 beside the 32x8 and 32x4 tiles, then push_grid
+ * 2 beside the same. */
+gl_status gl_batch_tuning(const gl_batch* batch, float* field_ms, float* push_ms, float* step_ms);
 
 /* n_steps coupled steps of every event (all events at one common step). */
 gl_status gl_batch_step(gl_batch* batch, int32_t n_steps);

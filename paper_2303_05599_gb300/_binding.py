@@ -80,11 +80,13 @@ SIGNATURES = {
     "gl_batch_event": (_P, [_P, ctypes.c_int32]),
     "gl_batch_init": (ctypes.c_int, [_P]),
     "gl_batch_autotune": (ctypes.c_int, [_P, _P, _P]),
-    "gl_batch_tuning": (ctypes.c_int, [_P, _P, _P]),
+    "gl_batch_tuning": (ctypes.c_int, [_P, _P, _P, _P]),
     "gl_batch_step": (ctypes.c_int, [_P, ctypes.c_int32]),
     "gl_batch_step_timed": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "gl_batch_observables": (ctypes.c_int, [_P, _P]),
-    "gl_batch_set_launch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "gl_batch_set_launch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32]),
+    "gl_batch_get_launch": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "gl_batch_observables_ex": (ctypes.c_int, [_P, ctypes.c_uint32, _P]),
 }
 
@@ -300,12 +302,25 @@ class Batch:
         self._chk(lib().gl_batch_autotune(self.b, ctypes.byref(t), ctypes.byref(p)), "gl_batch_autotune")
         f = (ctypes.c_float * 3)()
         q = (ctypes.c_float * 3)()
-        lib().gl_batch_tuning(self.b, f, q)
-        return {"tile": BATCH_TILES[t.value], "push_block": p.value, "field_ms": list(f), "push_ms": list(q)}
+        st = (ctypes.c_float * 8)()
+        lib().gl_batch_tuning(self.b, f, q, st)
+        out = self.launch()
+        out.update({"field_ms": list(f), "push_ms": list(q), "step_ms_two_streams": st[0],
+                    "step_ms_fused_by_chunk": list(st)[1:4],
+                    "step_ms_push_grid_by_tile": {"1": list(st)[4:6], "2": list(st)[6:8]}})
+        return out
 
-    def set_launch(self, tile, push_block):
-        """Fix the launch shapes (tile name from BATCH_TILES, push block size)."""
-        self._chk(lib().gl_batch_set_launch(self.b, BATCH_TILES.index(tile), push_block), "gl_batch_set_launch")
+    def launch(self):
+        """The launch shapes and schedule in use."""
+        v = [ctypes.c_int32() for _ in range(5)]
+        self._chk(lib().gl_batch_get_launch(self.b, *[ctypes.byref(x) for x in v]), "gl_batch_get_launch")
+        return {"tile": BATCH_TILES[v[0].value], "push_block": v[1].value, "push_chunk": v[2].value,
+                "fused": bool(v[3].value), "push_grid": v[4].value}
+
+    def set_launch(self, tile, push_block=128, push_chunk=1024, fused=False, push_grid=0):
+        """Fix the launch shapes and schedule (tile name from BATCH_TILES)."""
+        self._chk(lib().gl_batch_set_launch(self.b, BATCH_TILES.index(tile), push_block, push_chunk, int(fused),
+                                            push_grid), "gl_batch_set_launch")
 
     def step(self, n=1):
         self._chk(lib().gl_batch_step(self.b, n), "gl_batch_step")

@@ -33,7 +33,7 @@
 namespace gl {
 
 static constexpr int MAX_EVENTS = 1024;
-static constexpr int PUSH_CHUNK = 1024;  // particles per push block
+static constexpr int PUSH_CHUNK = 1024;  // default particles per push block
 
 struct EvDesc {
     void* field[2];
@@ -57,6 +57,7 @@ struct BatchArgs {
     double dt;
     int reunit_every;
     const int64_t* clock;
+    int push_chunk;  // particles per push block
 };
 
 __device__ __forceinline__ int find_event(const EvDesc* ev, int ne, int block, bool tiles) {
@@ -70,14 +71,15 @@ __device__ __forceinline__ int find_event(const EvDesc* ev, int ne, int block, b
     return lo;
 }
 
+// one field tile (block `blk` of the tile prefix table) of step n = clock
 template <typename R, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, (Tile<R, TX, TY>::min_blocks)) batch_field_kernel(BatchArgs b) {
+__device__ __forceinline__ void field_item(const BatchArgs& b, int blk) {
     // the block's event and step scalars, once per block
     __shared__ int s_e;
     __shared__ int64_t s_n;
     __shared__ StepR<R> s_a;
     if (threadIdx.x == 0) {
-        const int e = find_event(b.ev, b.ne, blockIdx.x, true);
+        const int e = find_event(b.ev, b.ne, blk, true);
         const int64_t n = *b.clock;
         const int reunit = b.reunit_every > 0 && (n + 1) % b.reunit_every == 0;
         s_e = e;
@@ -89,12 +91,13 @@ __global__ void __launch_bounds__(TX * TY, (Tile<R, TX, TY>::min_blocks)) batch_
     const int64_t n = s_n;
     const int64_t Vn = (int64_t)d.N * d.N;
     fused_tile<R, TX, TY, true>(carve_fields<R>(d.field[n & 1], Vn), carve_fields<R>(d.field[(n + 1) & 1], Vn),
-                                (typename Prec<R>::V*)d.site[n & 1], s_a, blockIdx.x - d.tile_begin);
+                                (typename Prec<R>::V*)d.site[n & 1], s_a, blk - d.tile_begin);
 }
 
-// push of the particles at t_{clock - lag}
+// one chunk of b.push_chunk particles (block `blk` of the chunk prefix table),
+// pushed from t_{clock - lag}
 template <typename R>
-__global__ void batch_push_kernel(BatchArgs b, int lag) {
+__device__ __forceinline__ void push_item(const BatchArgs& b, int lag, int blk) {
     // the block's event, time scalars and species table, once per block
     __shared__ int s_e;
     __shared__ int64_t s_n;
@@ -102,7 +105,7 @@ __global__ void batch_push_kernel(BatchArgs b, int lag) {
     __shared__ R s_t, s_dt, s_dto;
     __shared__ SpeciesArgs<R> s_sa;
     if (threadIdx.x == 0) {
-        const int e = find_event(b.ev, b.ne, blockIdx.x, false);
+        const int e = find_event(b.ev, b.ne, blk, false);
         const EvDesc& d = b.ev[e];
         const int64_t n = *b.clock - lag;
         const double t = n * b.dt;
@@ -125,10 +128,50 @@ __global__ void batch_push_kernel(BatchArgs b, int lag) {
     const int64_t Vn = (int64_t)d.N * d.N;
     const Parts<R> P = carve_parts<R>(d.parts, d.np);
     const Fields<R> bn1 = carve_fields<R>(d.field[(n + 1) & 1], Vn);
-    const int64_t base = (int64_t)(blockIdx.x - d.chunk_begin) * PUSH_CHUNK;
-    const int64_t end = base + PUSH_CHUNK < d.np ? base + PUSH_CHUNK : d.np;
+    const int64_t base = (int64_t)(blk - d.chunk_begin) * b.push_chunk;
+    const int64_t end = base + b.push_chunk < d.np ? base + b.push_chunk : d.np;
     for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x)
         push_one<R>((const typename Prec<R>::V*)d.site[n & 1], bn1, P, i, d.N, s_t, s_dt, s_dto, s_active, s_sa);
+}
+
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, (Tile<R, TX, TY>::min_blocks)) batch_field_kernel(BatchArgs b) {
+    field_item<R, TX, TY>(b, blockIdx.x);
+}
+
+template <typename R>
+__global__ void batch_push_kernel(BatchArgs b, int lag) {
+    push_item<R>(b, lag, blockIdx.x);
+}
+
+// the same push with a fixed number of resident blocks striding through the
+// chunks: launched before the field kernel on the second stream, it keeps a
+// share of every SM while the field tiles fill the rest
+template <typename R>
+__global__ void __launch_bounds__(128) batch_push_persist_kernel(BatchArgs b, int lag, int n_push) {
+    for (int blk = blockIdx.x; blk < n_push; blk += gridDim.x) {
+        push_item<R>(b, lag, blk);
+        __syncthreads();  // the block's shared event data is rewritten by the next chunk
+    }
+}
+
+// One persistent launch for a whole coupled step: the field tiles of t_s
+// (clock) and the push chunks of t_{s - lag}, interleaved evenly in one work
+// list that the resident blocks stride through.  The push reads the site
+// fields of t_{s-1} and the links and scalar of t_s, which no field tile of
+// this launch writes, so the two kinds of work are independent.  Field tiles
+// are bound by issue (SU(3) arithmetic), push chunks by memory latency;
+// sharing every SM between them keeps both busy.
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, (Tile<R, TX, TY>::min_blocks))
+    batch_fused_kernel(BatchArgs b, int lag, int n_field, int n_push) {
+    const int64_t total = (int64_t)n_field + n_push;
+    for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+        const int64_t f0 = w * n_field / total, f1 = (w + 1) * n_field / total;
+        if (f1 > f0) field_item<R, TX, TY>(b, (int)f0);
+        else push_item<R>(b, lag, (int)(w - f0));
+        __syncthreads();  // shared memory is reused by the next item
+    }
 }
 
 __global__ void tick_kernel(int64_t* clock) { *clock += 1; }
@@ -182,6 +225,8 @@ __global__ void __launch_bounds__(256) batch_obs_finalize(const BObs* ev) {
 enum { TILE_32x8 = 0, TILE_32x4 = 1, TILE_32x16 = 2, N_TILES = 3 };
 static const int TILE_DIMS[N_TILES][2] = {{32, 8}, {32, 4}, {32, 16}};
 static const int PUSH_BLOCKS[3] = {128, 256, 512};
+enum { N_CHUNKS = 3 };
+static const int PUSH_CHUNKS[N_CHUNKS] = {512, 1024, 2048};
 
 template <typename R, int TX, int TY>
 static void set_smem_attr() {
@@ -190,6 +235,8 @@ static void set_smem_attr() {
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !done[dev]) {
         cudaFuncSetAttribute(batch_field_kernel<R, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Tile<R, TX, TY>::bytes);
+        cudaFuncSetAttribute(batch_fused_kernel<R, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Tile<R, TX, TY>::bytes);
         done[dev] = true;
     }
@@ -211,6 +258,47 @@ static void launch_batch_field(int tile, int blocks, const BatchArgs& b, cudaStr
     } else {
         set_smem_attr<R, 32, 4>();
         batch_field_kernel<R, 32, 4><<<blocks, 128, Tile<R, 32, 4>::bytes, st>>>(b);
+    }
+}
+
+// resident blocks of the fused kernel on the whole GPU (occupancy x SMs)
+template <typename R, int TX, int TY>
+static int fused_grid() {
+    static int grid[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!grid[dev]) {
+        set_smem_attr<R, TX, TY>();
+        int per_sm = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_fused_kernel<R, TX, TY>, TX * TY,
+                                                      Tile<R, TX, TY>::bytes);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid[dev] = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    }
+    return grid[dev];
+}
+
+template <typename R, int TX, int TY>
+static void launch_fused_t(const BatchArgs& b, int lag, int n_field, int n_push, cudaStream_t st) {
+    int g = fused_grid<R, TX, TY>();
+    const int total = n_field + n_push;
+    if (g > total) g = total;
+    if (g < 1) return;
+    batch_fused_kernel<R, TX, TY><<<g, TX * TY, Tile<R, TX, TY>::bytes, st>>>(b, lag, n_field, n_push);
+}
+
+template <typename R>
+static void launch_batch_fused(int tile, const BatchArgs& b, int lag, int n_field, int n_push, cudaStream_t st) {
+    if constexpr (sizeof(R) == 8) {
+        (void)tile;
+        launch_fused_t<R, 32, 4>(b, lag, n_field, n_push, st);
+    } else if (tile == TILE_32x8) {
+        launch_fused_t<R, 32, 8>(b, lag, n_field, n_push, st);
+    } else if (tile == TILE_32x16) {
+        launch_fused_t<R, 32, 16>(b, lag, n_field, n_push, st);
+    } else {
+        launch_fused_t<R, 32, 4>(b, lag, n_field, n_push, st);
     }
 }
 
@@ -236,14 +324,20 @@ struct gl_batch {
     SortEv* d_sort;
     int* sort_every;  // per event (0: no sorting)
     int tile;         // autotuned tile shape
-    int push_block;   // autotuned push block size
+    int push_block;   // autotuned push block size (separate push kernel)
+    int push_chunk;   // particles per push block
+    int fused;        // 1: one persistent fused launch per step; 0: field and push on two streams
+    int push_grid;    // two streams: 0 = one push block per chunk, k > 0 = k resident 128-thread blocks per SM
     int field_blocks;
     int push_blocks;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
-    int graph_tile, graph_push_block;
+    int graph_tile, graph_push_block, graph_push_chunk, graph_fused, graph_push_grid;
     float tune_field_ms[N_TILES];
     float tune_push_ms[3];
+    // trial steps: two streams; fused by push chunk; two streams with 1 and 2
+    // resident push blocks per SM beside the 32x8 and the 32x4 tiles
+    float tune_step_ms[1 + N_CHUNKS + 4];
     char err[256];
 };
 
@@ -252,6 +346,39 @@ static size_t a256b(size_t b) { return (b + 255) & ~(size_t)255; }
 static gl_status bfail(gl_batch* b, gl_status s, const char* m) {
     if (b) snprintf(b->err, sizeof b->err, "%s", m);
     return s;
+}
+
+extern "C" {
+static gl_status sync_desc(gl_batch* b);
+}
+
+// descriptors for an autotune trial: the prefix tables of the current tile
+// shape and push chunk, the particles pointed at the contexts' spare buffers
+static gl_status trial_desc(gl_batch* b) {
+    if (gl_status s = sync_desc(b)) return s;
+    for (int e = 0; e < b->ne; e++) {
+        CtxView v;
+        ctx_view(b->ev[e], &v);
+        b->h_desc[e].parts = v.parts_alt;
+    }
+    cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(EvDesc) * b->ne, cudaMemcpyHostToDevice, b->stream);
+    return GL_OK;
+}
+
+// mean duration (ms) of reps - 1 timed repetitions of `launch` after one untimed
+template <typename F>
+static float time_trial(gl_batch* b, cudaEvent_t e0, cudaEvent_t e1, int reps, F launch) {
+    float total = 0;
+    for (int rep = 0; rep < reps; rep++) {
+        cudaEventRecord(e0, b->stream);
+        launch();
+        cudaEventRecord(e1, b->stream);
+        cudaEventSynchronize(e1);
+        float m = 0;
+        cudaEventElapsedTime(&m, e0, e1);
+        if (rep > 0) total += m;
+    }
+    return total / (reps - 1);
 }
 
 extern "C" {
@@ -331,6 +458,9 @@ gl_status gl_batch_create(const gl_config* cfgs, const gl_species* species, int3
     }
     b->tile = b->prec == GL_FP64 ? TILE_32x4 : TILE_32x8;
     b->push_block = 128;
+    b->push_chunk = PUSH_CHUNK;
+    b->fused = 0;
+    b->push_grid = 0;
     b->graph_tile = -1;
     *out = b;
     return GL_OK;
@@ -398,7 +528,7 @@ static gl_status sync_desc(gl_batch* b) {
         d.tile_begin = tb;
         tb += d.tiles_x * ((v.N + TY - 1) / TY);
         d.chunk_begin = cb;
-        cb += (int)((v.np + PUSH_CHUNK - 1) / PUSH_CHUNK);
+        cb += (int)((v.np + b->push_chunk - 1) / b->push_chunk);
         d.np = v.np;
         d.n_species = v.ns;
         b->sort_every[e] = v.sort_every;
@@ -409,80 +539,118 @@ static gl_status sync_desc(gl_batch* b) {
         }
     }
     b->field_blocks = tb;
-    b->push_blocks = cb > 0 ? cb : 1;
+    b->push_blocks = cb;
     cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(EvDesc) * b->ne, cudaMemcpyHostToDevice, b->stream);
     cudaMemcpyAsync(b->d_clock, &step0, sizeof step0, cudaMemcpyHostToDevice, b->stream);
     cudaStreamSynchronize(b->stream);
     return cudaGetLastError() == cudaSuccess ? GL_OK : bfail(b, GL_ERR_CUDA, "descriptor upload failed");
 }
 
+static BatchArgs batch_args(const gl_batch* b, int reunit_every) {
+    return BatchArgs{b->d_desc, b->ne, b->dt, reunit_every, b->d_clock, b->push_chunk};
+}
+
 static void launch_field(gl_batch* b, cudaStream_t st) {
-    BatchArgs a{b->d_desc, b->ne, b->dt, b->reunit_every, b->d_clock};
+    const BatchArgs a = batch_args(b, b->reunit_every);
     if (b->prec == GL_FP64) launch_batch_field<double>(b->tile, b->field_blocks, a, st);
     else launch_batch_field<float>(b->tile, b->field_blocks, a, st);
 }
 
-static void launch_push(gl_batch* b, int lag, cudaStream_t st) {
-    BatchArgs a{b->d_desc, b->ne, b->dt, b->reunit_every, b->d_clock};
-    if (b->prec == GL_FP64) batch_push_kernel<double><<<b->push_blocks, b->push_block, 0, st>>>(a, lag);
-    else batch_push_kernel<float><<<b->push_blocks, b->push_block, 0, st>>>(a, lag);
+static int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
 }
 
-// one overlapped step at clock s: the field step of t_s on the main stream
-// and the push of the particles at t_{s-1} on the second stream, then the tick
+// the separate push kernel: one block per chunk, or push_grid resident blocks per SM
+static void launch_push_shape(gl_batch* b, const BatchArgs& a, int lag, int push_block, int push_grid,
+                              cudaStream_t st) {
+    if (b->push_blocks < 1) return;
+    if (push_grid > 0) {
+        int g = push_grid * sm_count();
+        if (g > b->push_blocks) g = b->push_blocks;
+        if (b->prec == GL_FP64) batch_push_persist_kernel<double><<<g, 128, 0, st>>>(a, lag, b->push_blocks);
+        else batch_push_persist_kernel<float><<<g, 128, 0, st>>>(a, lag, b->push_blocks);
+    } else if (b->prec == GL_FP64) {
+        batch_push_kernel<double><<<b->push_blocks, push_block, 0, st>>>(a, lag);
+    } else {
+        batch_push_kernel<float><<<b->push_blocks, push_block, 0, st>>>(a, lag);
+    }
+}
+
+// a push with nothing beside it: one block per chunk
+static void launch_push(gl_batch* b, int lag, cudaStream_t st) {
+    launch_push_shape(b, batch_args(b, b->reunit_every), lag, b->push_block, 0, st);
+}
+
+static void launch_fused(gl_batch* b, int lag, cudaStream_t st) {
+    const BatchArgs a = batch_args(b, b->reunit_every);
+    if (b->prec == GL_FP64) launch_batch_fused<double>(b->tile, a, lag, b->field_blocks, b->push_blocks, st);
+    else launch_batch_fused<float>(b->tile, a, lag, b->field_blocks, b->push_blocks, st);
+}
+
+// one steady-state step at clock s, the field step of t_s and the push of the
+// particles at t_{s-1}, then the tick: either one fused persistent launch, or
+// the two kernels on the main and the second stream
 static void enqueue_overlap_step(gl_batch* b) {
+    if (b->fused) {
+        launch_fused(b, 1, b->stream);
+        tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock);
+        return;
+    }
     cudaEventRecord(b->ev_a, b->stream);
     cudaStreamWaitEvent(b->aux, b->ev_a, 0);
-    launch_push(b, 1, b->aux);
+    launch_push_shape(b, batch_args(b, b->reunit_every), 1, b->push_block, b->push_grid, b->aux);
     cudaEventRecord(b->ev_b, b->aux);
     launch_field(b, b->stream);
     cudaStreamWaitEvent(b->stream, b->ev_b, 0);
     tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock);
 }
 
+static gl_status ensure_aux(gl_batch* b);
+
 gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_out) {
     if (!b) return GL_ERR_ARG;
+    if (gl_status s = ensure_aux(b)) return s;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best_f = 1e30f, best_p = 1e30f;
-    int bt = b->tile, bp = b->push_block;
+    for (int k = 0; k < N_TILES; k++) b->tune_field_ms[k] = 0;
+    for (int k = 0; k < 3; k++) b->tune_push_ms[k] = 0;
+    for (int k = 0; k < 1 + N_CHUNKS + 4; k++) b->tune_step_ms[k] = 0;
     // field kernel: trial launches write only the spare time slice and the
     // site fields, which the next real step overwrites
+    float best_f = 1e30f;
+    int bt = b->tile;
     for (int tile = 0; tile < N_TILES; tile++) {
         if (b->prec == GL_FP64 && tile != TILE_32x4) continue;  // FP64 tile must fit shared memory
         b->tile = tile;
         if (gl_status s = sync_desc(b)) return s;
-        BatchArgs a{b->d_desc, b->ne, b->dt, 0, b->d_clock};
-        float ms = 0;
-        for (int rep = 0; rep < 4; rep++) {
-            cudaEventRecord(e0, b->stream);
+        const BatchArgs a = batch_args(b, 0);
+        const float ms = time_trial(b, e0, e1, 4, [&] {
             if (b->prec == GL_FP64) launch_batch_field<double>(tile, b->field_blocks, a, b->stream);
             else launch_batch_field<float>(tile, b->field_blocks, a, b->stream);
-            cudaEventRecord(e1, b->stream);
-            cudaEventSynchronize(e1);
-            float m;
-            cudaEventElapsedTime(&m, e0, e1);
-            if (rep > 0) ms += m;
-        }
-        b->tune_field_ms[tile] = ms / 3;
+        });
+        b->tune_field_ms[tile] = ms;
         if (ms < best_f) { best_f = ms; bt = tile; }
     }
     b->tile = bt;
     if (gl_status s = sync_desc(b)) return s;
-    // push: trial launches on a copy of the particles (the contexts' spare buffers)
+    // push and whole-step trials on a copy of the particles (the contexts'
+    // spare buffers), at a time where every species is formed
     EvDesc* saved = new EvDesc[b->ne];
     memcpy(saved, b->h_desc, sizeof(EvDesc) * b->ne);
-    bool have_copy = true;
-    for (int e = 0; e < b->ne; e++) {
+    bool have_copy = b->push_blocks > 0;
+    for (int e = 0; e < b->ne && have_copy; e++) {
         CtxView v;
         ctx_view(b->ev[e], &v);
         if (!v.parts_alt) { have_copy = false; break; }
         cudaMemcpyAsync(v.parts_alt, v.parts, particle_bytes(b->prec, v.np), cudaMemcpyDeviceToDevice, b->stream);
         b->h_desc[e].parts = v.parts_alt;
     }
+    int bp = b->push_block, bc = b->push_chunk, bf = b->fused;
     if (have_copy) {
-        // time the push at a step where every species is formed, then restore the clock
         int64_t trial = 0, now = 0;
         for (int e = 0; e < b->ne; e++)
             for (int k = 0; k < b->h_desc[e].n_species; k++) {
@@ -492,32 +660,73 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
         cudaMemcpyAsync(&now, b->d_clock, sizeof now, cudaMemcpyDeviceToHost, b->stream);
         cudaStreamSynchronize(b->stream);
         if (trial < now) trial = now;
-        cudaMemcpyAsync(b->d_clock, &trial, sizeof trial, cudaMemcpyHostToDevice, b->stream);
+        // the push of t_trial runs with the clock at `now` and lag now - trial,
+        // so that the field part of a trial step still writes the spare slice
+        const int lag = (int)(now - trial);
         cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(EvDesc) * b->ne, cudaMemcpyHostToDevice, b->stream);
-        BatchArgs a{b->d_desc, b->ne, b->dt, 0, b->d_clock};
+        const BatchArgs a = batch_args(b, 0);
+        float best_p = 1e30f;
         for (int k = 0; k < 3; k++) {
-            float ms = 0;
-            for (int rep = 0; rep < 4; rep++) {
-                cudaEventRecord(e0, b->stream);
-                if (b->prec == GL_FP64) batch_push_kernel<double><<<b->push_blocks, PUSH_BLOCKS[k], 0, b->stream>>>(a, 0);
-                else batch_push_kernel<float><<<b->push_blocks, PUSH_BLOCKS[k], 0, b->stream>>>(a, 0);
-                cudaEventRecord(e1, b->stream);
-                cudaEventSynchronize(e1);
-                float m;
-                cudaEventElapsedTime(&m, e0, e1);
-                if (rep > 0) ms += m;
-            }
-            b->tune_push_ms[k] = ms / 3;
+            const float ms = time_trial(b, e0, e1, 4, [&] {
+                if (b->prec == GL_FP64) batch_push_kernel<double><<<b->push_blocks, PUSH_BLOCKS[k], 0, b->stream>>>(a, lag);
+                else batch_push_kernel<float><<<b->push_blocks, PUSH_BLOCKS[k], 0, b->stream>>>(a, lag);
+            });
+            b->tune_push_ms[k] = ms;
             if (ms < best_p) { best_p = ms; bp = PUSH_BLOCKS[k]; }
         }
-        cudaMemcpyAsync(b->d_clock, &now, sizeof now, cudaMemcpyHostToDevice, b->stream);
+        // whole steps: field and push on two streams (the push one block per
+        // chunk, or 1 or 2 resident blocks per SM launched first, beside each
+        // field tile shape), or one fused launch by push chunk
+        b->push_block = bp;
+        float best_s = 1e30f;
+        int bt2 = b->tile, bg = 0;
+        bf = 0;
+        bc = b->push_chunk;
+        const int tile0 = b->tile;
+        for (int g = 0; g <= 2; g++)
+            for (int tile = 0; tile < N_TILES; tile++) {
+                if (b->prec == GL_FP64 && tile != TILE_32x4) continue;
+                if (g == 0 && tile != tile0) continue;
+                if (tile == TILE_32x16) continue;
+                b->tile = tile;
+                if (gl_status s = trial_desc(b)) return s;
+                const float ms = time_trial(b, e0, e1, 4, [&] {
+                    cudaEventRecord(b->ev_a, b->stream);
+                    cudaStreamWaitEvent(b->aux, b->ev_a, 0);
+                    launch_push_shape(b, a, lag, bp, g, b->aux);
+                    cudaEventRecord(b->ev_b, b->aux);
+                    if (b->prec == GL_FP64) launch_batch_field<double>(tile, b->field_blocks, a, b->stream);
+                    else launch_batch_field<float>(tile, b->field_blocks, a, b->stream);
+                    cudaStreamWaitEvent(b->stream, b->ev_b, 0);
+                });
+                b->tune_step_ms[g == 0 ? 0 : 1 + N_CHUNKS + 2 * (g - 1) + (tile == TILE_32x4)] = ms;
+                if (ms < best_s) { best_s = ms; bt2 = tile; bg = g; }
+            }
+        b->tile = tile0;
+        for (int k = 0; k < N_CHUNKS; k++) {
+            b->push_chunk = PUSH_CHUNKS[k];
+            if (gl_status s = trial_desc(b)) return s;
+            const BatchArgs ak = batch_args(b, 0);
+            const float ms = time_trial(b, e0, e1, 4, [&] {
+                if (b->prec == GL_FP64) launch_batch_fused<double>(b->tile, ak, lag, b->field_blocks, b->push_blocks, b->stream);
+                else launch_batch_fused<float>(b->tile, ak, lag, b->field_blocks, b->push_blocks, b->stream);
+            });
+            b->tune_step_ms[1 + k] = ms;
+            if (ms < best_s) { best_s = ms; bf = 1; bc = PUSH_CHUNKS[k]; bg = 0; bt2 = tile0; }
+        }
+        if (!bf) bc = PUSH_CHUNK;
+        b->push_chunk = bc;
+        b->tile = bt2;
+        b->push_grid = bg;
     }
     memcpy(b->h_desc, saved, sizeof(EvDesc) * b->ne);
     delete[] saved;
     b->push_block = bp;
+    b->push_chunk = bc;
+    b->fused = bf;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (gl_status s = sync_desc(b)) return s;
+    if (gl_status s = sync_desc(b)) return s;  // real particles, clock and chunk tables
     if (tile_out) *tile_out = b->tile;
     if (push_block_out) *push_block_out = b->push_block;
     return cudaGetLastError() == cudaSuccess ? GL_OK : bfail(b, GL_ERR_CUDA, "autotune launch failed");
@@ -586,7 +795,8 @@ gl_status gl_batch_step(gl_batch* b, int32_t n_steps) {
     if (b->prec == GL_FP64) set_smem_attr<double, 32, 4>();
     else { set_smem_attr<float, 32, 8>(); set_smem_attr<float, 32, 4>(); set_smem_attr<float, 32, 16>(); }
     // (re)capture the overlapped step when the launch shapes changed
-    if (!b->exec || b->graph_tile != b->tile || b->graph_push_block != b->push_block) {
+    if (!b->exec || b->graph_tile != b->tile || b->graph_push_block != b->push_block ||
+        b->graph_push_chunk != b->push_chunk || b->graph_fused != b->fused || b->graph_push_grid != b->push_grid) {
         if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
         if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
         if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
@@ -599,6 +809,9 @@ gl_status gl_batch_step(gl_batch* b, int32_t n_steps) {
         }
         b->graph_tile = b->tile;
         b->graph_push_block = b->push_block;
+        b->graph_push_chunk = b->push_chunk;
+        b->graph_fused = b->fused;
+        b->graph_push_grid = b->push_grid;
     }
     int64_t now = common_step(b);
     for (int32_t left = n_steps; left > 0;) {
@@ -700,23 +913,42 @@ gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
     return ctx_observables_many(b->ev, b->ne, what & ~GL_OBS_PARTICLES, what, out);
 }
 
-gl_status gl_batch_set_launch(gl_batch* b, int32_t tile, int32_t push_block) {
-    if (!b || tile < 0 || tile >= N_TILES) return GL_ERR_ARG;
+gl_status gl_batch_set_launch(gl_batch* b, int32_t tile, int32_t push_block, int32_t push_chunk, int32_t fused,
+                              int32_t push_grid) {
+    if (!b || tile < 0 || tile >= N_TILES || (fused != 0 && fused != 1) || push_grid < 0 || push_grid > 2)
+        return GL_ERR_ARG;
     if (b->prec == GL_FP64 && tile != TILE_32x4) return GL_ERR_ARG;
-    bool ok = false;
-    for (int k = 0; k < 3; k++) ok = ok || PUSH_BLOCKS[k] == push_block;
-    if (!ok) return GL_ERR_ARG;
+    bool ok_b = false, ok_c = false;
+    for (int k = 0; k < 3; k++) ok_b = ok_b || PUSH_BLOCKS[k] == push_block;
+    for (int k = 0; k < N_CHUNKS; k++) ok_c = ok_c || PUSH_CHUNKS[k] == push_chunk;
+    if (!ok_b || !ok_c) return GL_ERR_ARG;
     b->tile = tile;
     b->push_block = push_block;
+    b->push_chunk = push_chunk;
+    b->fused = fused;
+    b->push_grid = fused ? 0 : push_grid;
     return GL_OK;
 }
 
-gl_status gl_batch_tuning(const gl_batch* b, float* field_ms, float* push_ms) {
+gl_status gl_batch_get_launch(const gl_batch* b, int32_t* tile, int32_t* push_block, int32_t* push_chunk,
+                              int32_t* fused, int32_t* push_grid) {
+    if (!b) return GL_ERR_ARG;
+    if (tile) *tile = b->tile;
+    if (push_block) *push_block = b->push_block;
+    if (push_chunk) *push_chunk = b->push_chunk;
+    if (fused) *fused = b->fused;
+    if (push_grid) *push_grid = b->push_grid;
+    return GL_OK;
+}
+
+gl_status gl_batch_tuning(const gl_batch* b, float* field_ms, float* push_ms, float* step_ms) {
     if (!b) return GL_ERR_ARG;
     for (int k = 0; k < N_TILES; k++)
         if (field_ms) field_ms[k] = b->tune_field_ms[k];
     for (int k = 0; k < 3; k++)
         if (push_ms) push_ms[k] = b->tune_push_ms[k];
+    for (int k = 0; k < 1 + N_CHUNKS + 4; k++)
+        if (step_ms) step_ms[k] = b->tune_step_ms[k];
     return GL_OK;
 }
 

@@ -267,56 +267,59 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
     // ---- phase 4: the tile sites
     const int ix = tid % TX, iy = tid / TX;
     const int gx = x0 + ix, gy = y0 + iy;
-    if (gx >= N || gy >= N) return;
-    const int64_t g = (int64_t)gy * N + gx;
-    const A8<R> p_old = load_alg(in.pi, g, Vn);
-    const int e = (iy + 1) * EW + (ix + 1);
-    const int l = (iy + 2) * LW + (ix + 2);
-    const A8<R> ph = s_alg(sPhi, l, LN);
-    const M3<R> Ux_m = s_link(sU, 0, l - 1, LN);
-    const M3<R> Uy_m = s_link(sU, 1, l - LW, LN);
-    const A8<R> bx = conj_dn(Ux_m, s_alg(sPhi, l - 1, LN));
-    const A8<R> by = conj_dn(Uy_m, s_alg(sPhi, l - LW, LN));
-    A8<R> p_new, ph_new;
-#pragma unroll
-    for (int c = 0; c < 8; c++) {
-        const R lap = my_tx.v[c] + my_ty.v[c] + bx.v[c] + by.v[c] - R(4) * ph.v[c];
-        p_new.v[c] = p_old.v[c] + dt * inv_t * lap;
-        ph_new.v[c] = ph.v[c] + a.dt_th * p_new.v[c];
-    }
-    if (SITE) {
-        // E_i = (1/4t){e_i(s) + U_i(s-i)^+ e_i(s-i) U_i(s-i)}, e summed over n -+ 1/2
-        const A8<R> sx = conj_dn(Ux_m, s_alg(sEs, e - 1, EN));
-        const A8<R> sy = conj_dn(Uy_m, s_alg(sEs + AP * EN, e - EW, EN));
-        const A8<R> hx = s_alg(sEs, e, EN), hy = s_alg(sEs + AP * EN, e, EN);
-        const A8<R> cr = conj_dn(Uy_m, s_alg(sLf, e - EW, EN));
-        A8<R> Ex, Ey, Ee, Bx, By, Be;
-        const R q = R(0.25) * inv_t, hf = R(0.5) * inv_t;
+    // sites of a ragged tile beyond the lattice do nothing (no early return:
+    // persistent callers reach further barriers)
+    if (gx < N && gy < N) {
+        const int64_t g = (int64_t)gy * N + gx;
+        const A8<R> p_old = load_alg(in.pi, g, Vn);
+        const int e = (iy + 1) * EW + (ix + 1);
+        const int l = (iy + 2) * LW + (ix + 2);
+        const A8<R> ph = s_alg(sPhi, l, LN);
+        const M3<R> Ux_m = s_link(sU, 0, l - 1, LN);
+        const M3<R> Uy_m = s_link(sU, 1, l - LW, LN);
+        const A8<R> bx = conj_dn(Ux_m, s_alg(sPhi, l - 1, LN));
+        const A8<R> by = conj_dn(Uy_m, s_alg(sPhi, l - LW, LN));
+        A8<R> p_new, ph_new;
 #pragma unroll
         for (int c = 0; c < 8; c++) {
-            Ex.v[c] = q * (hx.v[c] + sx.v[c]);
-            Ey.v[c] = q * (hy.v[c] + sy.v[c]);
-            Ee.v[c] = R(0.5) * (p_old.v[c] + p_new.v[c]);
-            Bx.v[c] = -hf * (my_ty.v[c] - by.v[c]);
-            By.v[c] = hf * (my_tx.v[c] - bx.v[c]);
-            Be.v[c] = R(0.25) * (my_b.v[c] + cr.v[c]);
+            const R lap = my_tx.v[c] + my_ty.v[c] + bx.v[c] + by.v[c] - R(4) * ph.v[c];
+            p_new.v[c] = p_old.v[c] + dt * inv_t * lap;
+            ph_new.v[c] = ph.v[c] + a.dt_th * p_new.v[c];
         }
-        store_alg(site, g, Vn, Ex);
-        store_alg(site + (size_t)1 * AP * Vn, g, Vn, Ey);
-        store_alg(site + (size_t)2 * AP * Vn, g, Vn, Ee);
-        store_alg(site + (size_t)3 * AP * Vn, g, Vn, Bx);
-        store_alg(site + (size_t)4 * AP * Vn, g, Vn, By);
-        store_alg(site + (size_t)5 * AP * Vn, g, Vn, Be);
+        if (SITE) {
+            // E_i = (1/4t){e_i(s) + U_i(s-i)^+ e_i(s-i) U_i(s-i)}, e summed over n -+ 1/2
+            const A8<R> sx = conj_dn(Ux_m, s_alg(sEs, e - 1, EN));
+            const A8<R> sy = conj_dn(Uy_m, s_alg(sEs + AP * EN, e - EW, EN));
+            const A8<R> hx = s_alg(sEs, e, EN), hy = s_alg(sEs + AP * EN, e, EN);
+            const A8<R> cr = conj_dn(Uy_m, s_alg(sLf, e - EW, EN));
+            A8<R> Ex, Ey, Ee, Bx, By, Be;
+            const R q = R(0.25) * inv_t, hf = R(0.5) * inv_t;
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                Ex.v[c] = q * (hx.v[c] + sx.v[c]);
+                Ey.v[c] = q * (hy.v[c] + sy.v[c]);
+                Ee.v[c] = R(0.5) * (p_old.v[c] + p_new.v[c]);
+                Bx.v[c] = -hf * (my_ty.v[c] - by.v[c]);
+                By.v[c] = hf * (my_tx.v[c] - bx.v[c]);
+                Be.v[c] = R(0.25) * (my_b.v[c] + cr.v[c]);
+            }
+            store_alg(site, g, Vn, Ex);
+            store_alg(site + (size_t)1 * AP * Vn, g, Vn, Ey);
+            store_alg(site + (size_t)2 * AP * Vn, g, Vn, Ee);
+            store_alg(site + (size_t)3 * AP * Vn, g, Vn, Bx);
+            store_alg(site + (size_t)4 * AP * Vn, g, Vn, By);
+            store_alg(site + (size_t)5 * AP * Vn, g, Vn, Be);
+        }
+        store_alg(out.e, g, Vn, my_ex);
+        store_alg(out.e + (size_t)AP * Vn, g, Vn, my_ey);
+        store_alg(out.pi, g, Vn, p_new);
+        store_alg(out.phi, g, Vn, ph_new);
+        M3<R> nx = mul(exp_i_alg<R, ExpN<R>::n>(my_ex, a.dt_over_th), s_link(sU, 0, l, LN));
+        M3<R> ny = mul(exp_i_alg<R, ExpN<R>::n>(my_ey, a.dt_over_th), s_link(sU, 1, l, LN));
+        if (a.reunit) { reunit(nx); reunit(ny); }
+        store_link(out.U, 0, g, Vn, nx);
+        store_link(out.U, 1, g, Vn, ny);
     }
-    store_alg(out.e, g, Vn, my_ex);
-    store_alg(out.e + (size_t)AP * Vn, g, Vn, my_ey);
-    store_alg(out.pi, g, Vn, p_new);
-    store_alg(out.phi, g, Vn, ph_new);
-    M3<R> nx = mul(exp_i_alg<R, ExpN<R>::n>(my_ex, a.dt_over_th), s_link(sU, 0, l, LN));
-    M3<R> ny = mul(exp_i_alg<R, ExpN<R>::n>(my_ey, a.dt_over_th), s_link(sU, 1, l, LN));
-    if (a.reunit) { reunit(nx); reunit(ny); }
-    store_link(out.U, 0, g, Vn, nx);
-    store_link(out.U, 1, g, Vn, ny);
 }
 
 

@@ -134,3 +134,49 @@ def test_autotuned_tile_shape_changes_nothing(prec):
     b.step(19)
     for buf in (B.GL_BUF_LINKS, B.GL_BUF_E, B.GL_BUF_PI, B.GL_BUF_PHI, B.GL_BUF_PARTICLES):
         assert np.array_equal(a.download(buf), b.download(buf))
+
+
+@pytest.mark.parametrize("prec", [W.FP64, W.FP32_2ROW])
+def test_schedules_agree(prec):
+    """One persistent fused launch per step (any push chunk) and the two-stream
+    schedules (push one block per chunk, or resident push blocks) evolve the
+    batch bitwise alike, across sort segments."""
+    ws = events(prec, sort_every=5)
+    tile = "32x4" if prec == W.FP64 else "32x8"
+    shapes = [dict(tile=tile, push_block=128, push_chunk=1024, fused=False, push_grid=0),
+              dict(tile=tile, push_block=256, push_chunk=512, fused=True, push_grid=0),
+              dict(tile=tile, push_block=128, push_chunk=2048, fused=True, push_grid=0),
+              dict(tile=tile, push_block=128, push_chunk=1024, fused=False, push_grid=1),
+              dict(tile=tile, push_block=128, push_chunk=512, fused=False, push_grid=2)]
+    if prec != W.FP64:
+        shapes.append(dict(tile="32x16", push_block=512, push_chunk=1024, fused=True, push_grid=0))
+    results = []
+    for sh in shapes:
+        batch = B.Batch(ws)
+        with torch.cuda.stream(batch.stream):
+            batch.init()
+            batch.set_launch(**sh)
+            assert batch.launch() == sh
+            batch.step(3)
+            batch.step(10)
+            torch.cuda.synchronize()
+            results.append([[ev.download(buf) for buf in (B.GL_BUF_LINKS, B.GL_BUF_E, B.GL_BUF_PI, B.GL_BUF_PHI,
+                                                          B.GL_BUF_PARTICLES, B.GL_BUF_SITE)]
+                            for ev in batch.events])
+        batch.close()
+    for r in results[1:]:
+        for e in range(len(ws)):
+            for a, b in zip(results[0][e], r[e]):
+                assert np.array_equal(a, b)
+
+
+def test_set_launch_rejects_bad_shapes():
+    ws = events(W.FP64)[:1]
+    batch = B.Batch(ws)
+    with pytest.raises(B.GlasmaError):
+        batch.set_launch("32x8")          # FP64 batches use 32x4
+    with pytest.raises(B.GlasmaError):
+        batch.set_launch("32x4", push_block=100)
+    with pytest.raises(B.GlasmaError):
+        batch.set_launch("32x4", push_chunk=1000)
+    batch.close()
