@@ -21,6 +21,7 @@ line.
 import argparse
 import ctypes
 import json
+import math
 import os
 import subprocess
 import sys
@@ -129,9 +130,36 @@ class ClockSampler:
         return out
 
 
+def _rel(a, b):
+    import numpy as np
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(1e-300, np.abs(b).max()))
+
+
+def _ensemble(part, mass, t, static):
+    """<p_T^2>, <p_L^2> per species (lattice units) from canonical particle
+    records: p_L = p^tau sinh(eta) + w cosh(eta), w = P_eta / t (static: P_eta)."""
+    import numpy as np
+    out = {}
+    for k in range(len(mass)):
+        m = part[:, 15] == k
+        if not m.any():
+            continue
+        px, py, eta, Pe = part[m, 3], part[m, 4], part[m, 2], part[m, 5]
+        if static[k]:
+            pl = Pe
+        else:
+            w = Pe / t if t > 0 else 0 * Pe
+            pl = np.sqrt(px * px + py * py + w * w + mass[k] ** 2) * np.sinh(eta) + w * np.cosh(eta)
+        out[k] = (float(np.mean(px * px + py * py)), float(np.mean(pl * pl)))
+    return out
+
+
 def cpu_baseline(w, ev, args):
     """The oracle as it stands on the host cores: a few coupled steps of the
-    full lattice and all particles, from the GPU state after warm-up."""
+    full lattice and all particles, from the GPU state after the run.  The
+    same steps are then taken by the GPU on that event alone, and the GPU's
+    error against the FP64 oracle is reported for every observable."""
+    import math
     import numpy as np
     import oracle as O
     from paper_2303_05599_gb300 import _binding as B
@@ -140,17 +168,44 @@ def cpu_baseline(w, ev, args):
     part = ev.download(B.GL_BUF_PARTICLES)
     ls = w.lattice_species()
     obs = ev.observables()
-    run = O.Run(st, part, [s[0] for s in ls], [s[1] for s in ls], [s.rep for s in w.species], w.dt,
-                step=int(obs.step))
+    step0 = int(obs.step)
+    run = O.Run(st, part, [s[0] for s in ls], [s[1] for s in ls], [s.rep for s in w.species], w.dt, step=step0)
     k = args.cpu_sample_steps
     t0 = time.perf_counter()
     for _ in range(k):
         run.step()
     dt = time.perf_counter() - t0
+    # the same k steps on the GPU (this event alone), then the errors
+    ev.step(k)
+    gp = ev.download(B.GL_BUF_PARTICLES)
+    mass = [s[0] for s in ls]
+    static = [math.isinf(s.mass_GeV) for s in w.species]
+    t_end = run.n * w.dt
+    ens_g, ens_o = _ensemble(gp, mass, t_end, static), _ensemble(run.part, mass, t_end, static)
+    dpos = np.abs(gp[:, :2] - run.part[:, :2])
+    dpos = np.minimum(dpos, w.N - dpos)  # periodic
+    err = {
+        "steps": k, "from_step": step0,
+        "links": _rel(ev.download(B.GL_BUF_LINKS), run.st.U),
+        "e": _rel(ev.download(B.GL_BUF_E), run.st.e),
+        "phi": _rel(ev.download(B.GL_BUF_PHI), run.st.phi),
+        "pi": _rel(ev.download(B.GL_BUF_PI), run.st.pi),
+        "site_fields": _rel(ev.download(B.GL_BUF_SITE), run.site),
+        "positions_max_abs_lattice_units": float(dpos.max()),
+        "momenta": _rel(gp[:, 3:6], run.part[:, 3:6]),
+        "momenta_per_particle_p50_p99": [float(v) for v in np.percentile(
+            np.abs(gp[:, 3:6] - run.part[:, 3:6]).max(axis=1) / max(1e-300, np.abs(run.part[:, 3:6]).max()), [50, 99])],
+        "charges": _rel(gp[:, 6:14], run.part[:, 6:14]),
+        "cell_flips": "the max values come from the few particles whose FP32 position rounds to the other side "
+                      "of a cell edge (different NGP cell); the percentiles show the rest",
+        "ensemble_pT2": {str(s): abs(ens_g[s][0] / ens_o[s][0] - 1) for s in ens_o if ens_o[s][0] > 0},
+        "ensemble_pL2": {str(s): abs(ens_g[s][1] / ens_o[s][1] - 1) for s in ens_o if ens_o[s][1] > 0},
+    }
     return {"value": w.N * w.N * k / dt, "unit": "site-updates/s", "cores": O.threads(), "kind": "oracle",
-            "sample": "%d coupled steps of the full %dx%d lattice with all %d particles, FP64, from the GPU "
-                      "state after warm-up (%.1f s)" % (k, w.N, w.N, w.n_particles, dt),
-            "particle_steps_per_s": w.n_particles * k / dt}
+            "sample": "%d coupled steps of the full %dx%d lattice with all %d particles of one event, FP64, from "
+                      "the GPU state at step %d (%.1f s)" % (k, w.N, w.N, w.n_particles, step0, dt),
+            "particle_steps_per_s": w.n_particles * k / dt,
+            "error_vs_oracle": err}
 
 
 def events_for(args, rank):
@@ -211,7 +266,11 @@ def run_ours(args):
             tune = dict(batch.launch(), fixed=True)
         else:
             tune = batch.autotune()
-        batch.step(args.warmup)
+        # untimed: W warm-up steps, at least up to the first step at which every
+        # species is formed (the steady state of the run)
+        n_form = max(int(math.ceil(sp.tau_form_fm / (w.dtau_over_a * w.a_fm) - 1e-9)) for w in ws for sp in w.species)
+        pre = max(args.warmup, n_form + 1)
+        batch.step(pre)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -305,6 +364,7 @@ def run_ours(args):
                        "precision": "fp32_2row" if prec else "fp64", "dtau_over_a": ws[0].dtau_over_a,
                        "reunit_every": ws[0].reunit_every, "parallelism": "events sharded over ranks",
                        "l2": "per-step working set larger than L2 (no flush)",
+                       "timed_from_step": pre,
                        "launch": "one CUDA-graph replay per step: the field step of t_s and the push of t_{s-1}, "
                                  "as one persistent fused launch or on two streams (autotuned)"},
             "particle_steps_per_s": world * n_active * K / t_step,

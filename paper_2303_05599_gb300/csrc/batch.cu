@@ -139,9 +139,18 @@ __global__ void __launch_bounds__(TX * TY, (Tile<R, TX, TY>::min_blocks)) batch_
     field_item<R, TX, TY>(b, blockIdx.x);
 }
 
-template <typename R>
-__global__ void batch_push_kernel(BatchArgs b, int lag) {
+// at most 64 FP32 registers (B threads, 1024 / B blocks per SM): enough
+// warps per SM to keep the particle and site-field loads in flight
+template <typename R, int B>
+__global__ void __launch_bounds__(B, (sizeof(R) == 4 ? 1024 : 512) / B) batch_push_kernel(BatchArgs b, int lag) {
     push_item<R>(b, lag, blockIdx.x);
+}
+
+template <typename R>
+static void launch_batch_push(int block, int blocks, const BatchArgs& a, int lag, cudaStream_t st) {
+    if (block == 512) batch_push_kernel<R, 512><<<blocks, 512, 0, st>>>(a, lag);
+    else if (block == 256) batch_push_kernel<R, 256><<<blocks, 256, 0, st>>>(a, lag);
+    else batch_push_kernel<R, 128><<<blocks, 128, 0, st>>>(a, lag);
 }
 
 // the same push with a fixed number of resident blocks striding through the
@@ -344,7 +353,10 @@ struct gl_batch {
 static size_t a256b(size_t b) { return (b + 255) & ~(size_t)255; }
 
 static gl_status bfail(gl_batch* b, gl_status s, const char* m) {
-    if (b) snprintf(b->err, sizeof b->err, "%s", m);
+    if (b) {
+        strncpy(b->err, m, sizeof b->err - 1);
+        b->err[sizeof b->err - 1] = 0;
+    }
     return s;
 }
 
@@ -573,9 +585,9 @@ static void launch_push_shape(gl_batch* b, const BatchArgs& a, int lag, int push
         if (b->prec == GL_FP64) batch_push_persist_kernel<double><<<g, 128, 0, st>>>(a, lag, b->push_blocks);
         else batch_push_persist_kernel<float><<<g, 128, 0, st>>>(a, lag, b->push_blocks);
     } else if (b->prec == GL_FP64) {
-        batch_push_kernel<double><<<b->push_blocks, push_block, 0, st>>>(a, lag);
+        launch_batch_push<double>(push_block, b->push_blocks, a, lag, st);
     } else {
-        batch_push_kernel<float><<<b->push_blocks, push_block, 0, st>>>(a, lag);
+        launch_batch_push<float>(push_block, b->push_blocks, a, lag, st);
     }
 }
 
@@ -668,8 +680,8 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
         float best_p = 1e30f;
         for (int k = 0; k < 3; k++) {
             const float ms = time_trial(b, e0, e1, 4, [&] {
-                if (b->prec == GL_FP64) batch_push_kernel<double><<<b->push_blocks, PUSH_BLOCKS[k], 0, b->stream>>>(a, lag);
-                else batch_push_kernel<float><<<b->push_blocks, PUSH_BLOCKS[k], 0, b->stream>>>(a, lag);
+                if (b->prec == GL_FP64) launch_batch_push<double>(PUSH_BLOCKS[k], b->push_blocks, a, lag, b->stream);
+                else launch_batch_push<float>(PUSH_BLOCKS[k], b->push_blocks, a, lag, b->stream);
             });
             b->tune_push_ms[k] = ms;
             if (ms < best_p) { best_p = ms; bp = PUSH_BLOCKS[k]; }

@@ -11,16 +11,21 @@
 // the plaquette forces and the clover are
 //   F_x = t (A - Dn),  F_y = t (Lf - A),
 //   B_eta = (A + Lf + Dn + Uy(s-y)^+ Lf(s-y) Uy(s-y)) / 4.
-// E_i(s) needs e_i(n+1/2) at s - i, so the tile also advances the momenta of
-// one halo column (x0 - 1) and one halo row (y0 - 1).
+// E_x(s) needs e_x(n+1/2) at s - x and E_y(s) needs e_y(n+1/2) at s - y, so
+// the tile also advances e_x on one halo column (x0 - 1) and e_y (with Lf) on
+// one halo row (y0 - 1); nothing else of the halo is needed.
 //
 // The tile's inputs are copied to shared memory with cp.async in the storage
 // layout of global memory (16-byte vectors; FP32 links as two rows, the third
 // rebuilt when a link is read).  Regions, in tile coordinates:
-//   links, phi:      x in [-2, TX],   y in [-2, TY]    (LW x LH)
-//   plaquettes A:    x in [-2, TX-1], y in [-2, TY-1]  (AW x AH)
-//   momenta, Lf:     x in [-1, TX-1], y in [-1, TY-1]  (EW x EH)
+//   links, phi:                   x in [-1, TX],   y in [-1, TY]    (LW x LH)
+//   plaquettes A, momenta, Lf:    x in [-1, TX-1], y in [-1, TY-1]  (EW x EH)
 // pi(n-1/2) is read by each site's thread straight from global memory.
+//
+// Every site does each computation at the same point of the code (own and
+// halo momenta share one loop body), so the results do not depend on the tile
+// shape.  The links arrive in their own group of copies, so the plaquettes
+// start while phi and e(n-1/2) are still in flight.
 #pragma once
 #include "internal.h"
 #include "layout.cuh"
@@ -38,12 +43,13 @@ template <typename R, int TX, int TY>
 struct Tile {
     using V = typename Prec<R>::V;
     static constexpr int LP = Prec<R>::LP, AP = Prec<R>::AP;
-    static constexpr int LW = TX + 3, LH = TY + 3, LN = LW * LH;
-    static constexpr int AW = TX + 2, AH = TY + 2, AN = AW * AH;
+    static constexpr int LW = TX + 2, LH = TY + 2, LN = LW * LH;
     static constexpr int EW = TX + 1, EH = TY + 1, EN = EW * EH;
     static constexpr int NT = TX * TY;
-    // vectors: links 2 LP LN, phi AP LN, A AP AN, e sums 2 AP EN, Lf AP EN
-    static constexpr size_t vecs = (size_t)2 * LP * LN + (size_t)AP * LN + (size_t)AP * AN + (size_t)3 * AP * EN;
+    static constexpr int NH = TX + TY;  // halo momenta: left column (e_x), bottom row (e_y, Lf)
+    static_assert(NH <= NT, "halo momenta are one per thread");
+    // vectors: links 2 LP LN, phi AP LN, A AP EN, e sums 2 AP EN, Lf AP EN
+    static constexpr size_t vecs = (size_t)2 * LP * LN + (size_t)AP * LN + (size_t)4 * AP * EN;
     static constexpr size_t bytes = vecs * sizeof(V);
     // CTAs per SM the launch bounds ask for: FP32 kernels are capped at 128
     // registers a thread so that 16 warps fit an SM (the shared memory of
@@ -58,6 +64,9 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // link (d) of shared-memory site li, planes of LN vectors
 __device__ __forceinline__ M3<double> s_link(const double2* sU, int d, int li, int LN) {
@@ -181,12 +190,12 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
     using T = Tile<R, TX, TY>;
     using Vec = typename Prec<R>::V;
     constexpr int LP = T::LP, AP = T::AP;
-    constexpr int LW = T::LW, LN = T::LN, AW = T::AW, AN = T::AN, EW = T::EW, EN = T::EN, NT = T::NT;
+    constexpr int LW = T::LW, LN = T::LN, EW = T::EW, EN = T::EN, NT = T::NT, NH = T::NH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Vec* sU = (Vec*)smem_raw;          // [2][LP][LN]
     Vec* sPhi = sU + 2 * LP * LN;      // [AP][LN]
-    Vec* sA = sPhi + AP * LN;          // [AP][AN]
-    Vec* sEs = sA + AP * AN;           // [2][AP][EN]: e(n-1/2), then e(n-1/2) + e(n+1/2)
+    Vec* sA = sPhi + AP * LN;          // [AP][EN]
+    Vec* sEs = sA + AP * EN;           // [2][AP][EN]: e(n-1/2), then e(n-1/2) + e(n+1/2)
     Vec* sLf = sEs + 2 * AP * EN;      // [AP][EN]
 
     const int N = a.N;
@@ -194,13 +203,22 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
     const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
     const int tid = threadIdx.x;
     const R t = a.t, dt = a.dt, inv_t = a.inv_t;
+    // this thread's site in tile coordinates and its shared-memory indices
+    const int ix = tid % TX, iy = tid / TX;
+    const int ls = (iy + 1) * LW + (ix + 1), es = (iy + 1) * EW + (ix + 1);
 
-    // ---- phase 1: asynchronous copies of the tile's inputs
+    // ---- phase 1: asynchronous copies of the tile's inputs, in two groups:
+    // the links (all phase 2 needs), then phi and e(n-1/2)
     for (int i = tid; i < LN; i += NT) {
-        const int gx = wrapi(x0 + i % LW - 2, N), gy = wrapi(y0 + i / LW - 2, N);
+        const int gx = wrapi(x0 + i % LW - 1, N), gy = wrapi(y0 + i / LW - 1, N);
         const int64_t g = (int64_t)gy * N + gx;
 #pragma unroll
         for (int k = 0; k < 2 * LP; k++) cp_async16(sU + (size_t)k * LN + i, in.U + (size_t)k * Vn + g);
+    }
+    cp_async_commit();
+    for (int i = tid; i < LN; i += NT) {
+        const int gx = wrapi(x0 + i % LW - 1, N), gy = wrapi(y0 + i / LW - 1, N);
+        const int64_t g = (int64_t)gy * N + gx;
 #pragma unroll
         for (int k = 0; k < AP; k++) cp_async16(sPhi + (size_t)k * LN + i, in.phi + (size_t)k * Vn + g);
     }
@@ -210,75 +228,99 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
 #pragma unroll
         for (int k = 0; k < 2 * AP; k++) cp_async16(sEs + (size_t)k * EN + i, in.e + (size_t)k * Vn + g);
     }
-    cp_async_wait_all();
+    cp_async_commit();
+    cp_async_wait_group<1>();
     __syncthreads();
 
-    // ---- phase 2: plaquettes of the tile cells and their halo
-    for (int i = tid; i < AN; i += NT) {
-        const int l = (i / AW) * LW + (i % AW);  // cell (ax, ay) = (i % AW - 2, i / AW - 2)
+    // ---- phase 2: plaquettes of the cells x in [-1, TX-1], y in [-1, TY-1]
+    for (int i = tid; i < EN; i += NT) {
+        const int l = (i / EW) * LW + (i % EW);  // cell (i % EW - 1, i / EW - 1)
         const M3<R> C = mul(s_link(sU, 0, l, LN), s_link(sU, 1, l + 1, LN));
-        s_alg_put(sA, i, AN, iah_of_mul_nd(mul_nd(C, s_link(sU, 0, l + LW, LN)), s_link(sU, 1, l, LN)));
+        s_alg_put(sA, i, EN, iah_of_mul_nd(mul_nd(C, s_link(sU, 0, l + LW, LN)), s_link(sU, 1, l, LN)));
     }
+    cp_async_wait_group<0>();
     __syncthreads();
 
-    // ---- phase 3: momenta at n+1/2 on the tile and the halo column/row.
-    // Indices 0..NT-1 are the tile sites in thread order (kept in registers
-    // for phase 4); the halo follows.
+    // ---- phase 3: momenta at n+1/2 of the tile site (kept in registers for
+    // phase 4) and of the halo.  Item 0 is the thread's own site (both components); item 1, for the first
+    // NH threads, a halo site: left column (-1, h) needs e_x only, bottom row
+    // (h, -1) e_y and Lf only.  One loop body (not unrolled) computes both, so
+    // a momentum is computed by the same code whether the site is a tile's
+    // own or another tile's halo.
     A8<R> my_ex, my_ey, my_tx, my_ty, my_b;
-    for (int k = tid; k < EN; k += NT) {
-        int ex, ey;
-        if (k < NT) { ex = k % TX; ey = k / TX; }
-        else {
-            const int h = k - NT;
-            if (h < TY + 1) { ex = -1; ey = h - 1; }
-            else { ex = h - (TY + 1); ey = -1; }
+    const int gx = x0 + ix, gy = y0 + iy;
+    const bool valid = gx < N && gy < N;
+    const int64_t g = (int64_t)gy * N + gx;
+    const int n_items = tid < NH ? 2 : 1;
+#pragma unroll 1
+    for (int it = 0; it < n_items; it++) {
+        int e = es, l = ls;
+        bool wx = true, wy = true;
+        if (it == 1) {
+            if (tid < TY) {
+                e = (tid + 1) * EW;
+                l = (tid + 1) * LW;
+                wy = false;
+            } else {
+                e = tid - TY + 1;
+                l = tid - TY + 1;
+                wx = false;
+            }
         }
-        const int e = (ey + 1) * EW + (ex + 1);
-        const int l = (ey + 2) * LW + (ex + 2);
-        const int ai = (ey + 2) * AW + (ex + 2);
-        const A8<R> A0 = s_alg(sA, ai, AN);
-        const A8<R> Dn = conj_dn(s_link(sU, 1, l - LW, LN), s_alg(sA, ai - AW, AN));
-        const A8<R> Lf = conj_dn(s_link(sU, 0, l - 1, LN), s_alg(sA, ai - 1, AN));
+        const A8<R> A0 = s_alg(sA, e, EN);
         const A8<R> ph = s_alg(sPhi, l, LN);
-        const A8<R> tx = conj_up(s_link(sU, 0, l, LN), s_alg(sPhi, l + 1, LN));
-        const A8<R> ty = conj_up(s_link(sU, 1, l, LN), s_alg(sPhi, l + LW, LN));
-        const A8<R> cx = icomm(tx, ph), cy = icomm(ty, ph);
-        const A8<R> eox = s_alg(sEs, e, EN), eoy = s_alg(sEs + AP * EN, e, EN);
-        A8<R> ex_n, ey_n, sx, sy;
+        if (wx) {
+            const A8<R> Dn = conj_dn(s_link(sU, 1, l - LW, LN), s_alg(sA, e - EW, EN));
+            const A8<R> tx = conj_up(s_link(sU, 0, l, LN), s_alg(sPhi, l + 1, LN));
+            const A8<R> cx = icomm(tx, ph);
+            const A8<R> eox = s_alg(sEs, e, EN);
+            A8<R> ex_n, sx;
 #pragma unroll
-        for (int c = 0; c < 8; c++) {
-            ex_n.v[c] = eox.v[c] + dt * (t * (A0.v[c] - Dn.v[c]) + inv_t * cx.v[c]);
-            ey_n.v[c] = eoy.v[c] + dt * (t * (Lf.v[c] - A0.v[c]) + inv_t * cy.v[c]);
-            sx.v[c] = eox.v[c] + ex_n.v[c];
-            sy.v[c] = eoy.v[c] + ey_n.v[c];
+            for (int c = 0; c < 8; c++) {
+                ex_n.v[c] = eox.v[c] + dt * (t * (A0.v[c] - Dn.v[c]) + inv_t * cx.v[c]);
+                sx.v[c] = eox.v[c] + ex_n.v[c];
+            }
+            // only this thread reads site e of sEs before the barrier
+            s_alg_put(sEs, e, EN, sx);
+            if (it == 0) {
+                my_ex = ex_n;
+                my_tx = tx;
+                my_b = Dn;
+            }
         }
-        // only this thread reads site e of sEs before the barrier
-        s_alg_put(sEs, e, EN, sx);
-        s_alg_put(sEs + AP * EN, e, EN, sy);
-        s_alg_put(sLf, e, EN, Lf);
-        if (k < NT) {
-            my_ex = ex_n; my_ey = ey_n; my_tx = tx; my_ty = ty;
+        if (wy) {
+            const A8<R> Lf = conj_dn(s_link(sU, 0, l - 1, LN), s_alg(sA, e - 1, EN));
+            const A8<R> ty = conj_up(s_link(sU, 1, l, LN), s_alg(sPhi, l + LW, LN));
+            const A8<R> cy = icomm(ty, ph);
+            const A8<R> eoy = s_alg(sEs + AP * EN, e, EN);
+            A8<R> ey_n, sy;
 #pragma unroll
-            for (int c = 0; c < 8; c++) my_b.v[c] = A0.v[c] + Lf.v[c] + Dn.v[c];
+            for (int c = 0; c < 8; c++) {
+                ey_n.v[c] = eoy.v[c] + dt * (t * (Lf.v[c] - A0.v[c]) + inv_t * cy.v[c]);
+                sy.v[c] = eoy.v[c] + ey_n.v[c];
+            }
+            s_alg_put(sEs + AP * EN, e, EN, sy);
+            s_alg_put(sLf, e, EN, Lf);
+            if (it == 0) {
+                my_ey = ey_n;
+                my_ty = ty;
+#pragma unroll
+                for (int c = 0; c < 8; c++) my_b.v[c] = A0.v[c] + Lf.v[c] + my_b.v[c];
+            }
         }
     }
     __syncthreads();
 
     // ---- phase 4: the tile sites
-    const int ix = tid % TX, iy = tid / TX;
-    const int gx = x0 + ix, gy = y0 + iy;
     // sites of a ragged tile beyond the lattice do nothing (no early return:
     // persistent callers reach further barriers)
-    if (gx < N && gy < N) {
-        const int64_t g = (int64_t)gy * N + gx;
+    if (valid) {
         const A8<R> p_old = load_alg(in.pi, g, Vn);
-        const int e = (iy + 1) * EW + (ix + 1);
-        const int l = (iy + 2) * LW + (ix + 2);
-        const A8<R> ph = s_alg(sPhi, l, LN);
-        const M3<R> Ux_m = s_link(sU, 0, l - 1, LN);
-        const M3<R> Uy_m = s_link(sU, 1, l - LW, LN);
-        const A8<R> bx = conj_dn(Ux_m, s_alg(sPhi, l - 1, LN));
-        const A8<R> by = conj_dn(Uy_m, s_alg(sPhi, l - LW, LN));
+        const A8<R> ph = s_alg(sPhi, ls, LN);
+        const M3<R> Ux_m = s_link(sU, 0, ls - 1, LN);
+        const M3<R> Uy_m = s_link(sU, 1, ls - LW, LN);
+        const A8<R> bx = conj_dn(Ux_m, s_alg(sPhi, ls - 1, LN));
+        const A8<R> by = conj_dn(Uy_m, s_alg(sPhi, ls - LW, LN));
         A8<R> p_new, ph_new;
 #pragma unroll
         for (int c = 0; c < 8; c++) {
@@ -288,10 +330,10 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
         }
         if (SITE) {
             // E_i = (1/4t){e_i(s) + U_i(s-i)^+ e_i(s-i) U_i(s-i)}, e summed over n -+ 1/2
-            const A8<R> sx = conj_dn(Ux_m, s_alg(sEs, e - 1, EN));
-            const A8<R> sy = conj_dn(Uy_m, s_alg(sEs + AP * EN, e - EW, EN));
-            const A8<R> hx = s_alg(sEs, e, EN), hy = s_alg(sEs + AP * EN, e, EN);
-            const A8<R> cr = conj_dn(Uy_m, s_alg(sLf, e - EW, EN));
+            const A8<R> sx = conj_dn(Ux_m, s_alg(sEs, es - 1, EN));
+            const A8<R> sy = conj_dn(Uy_m, s_alg(sEs + AP * EN, es - EW, EN));
+            const A8<R> hx = s_alg(sEs, es, EN), hy = s_alg(sEs + AP * EN, es, EN);
+            const A8<R> cr = conj_dn(Uy_m, s_alg(sLf, es - EW, EN));
             A8<R> Ex, Ey, Ee, Bx, By, Be;
             const R q = R(0.25) * inv_t, hf = R(0.5) * inv_t;
 #pragma unroll
@@ -314,14 +356,14 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
         store_alg(out.e + (size_t)AP * Vn, g, Vn, my_ey);
         store_alg(out.pi, g, Vn, p_new);
         store_alg(out.phi, g, Vn, ph_new);
-        M3<R> nx = mul(exp_i_alg<R, ExpN<R>::n>(my_ex, a.dt_over_th), s_link(sU, 0, l, LN));
-        M3<R> ny = mul(exp_i_alg<R, ExpN<R>::n>(my_ey, a.dt_over_th), s_link(sU, 1, l, LN));
-        if (a.reunit) { reunit(nx); reunit(ny); }
+        M3<R> nx = mul(exp_i_alg<R, ExpN<R>::n>(my_ex, a.dt_over_th), s_link(sU, 0, ls, LN));
+        if (a.reunit) reunit(nx);
         store_link(out.U, 0, g, Vn, nx);
+        M3<R> ny = mul(exp_i_alg<R, ExpN<R>::n>(my_ey, a.dt_over_th), s_link(sU, 1, ls, LN));
+        if (a.reunit) reunit(ny);
         store_link(out.U, 1, g, Vn, ny);
     }
 }
-
 
 // step scalars of t_n = n dt, computed the same way on the host and the device
 __host__ __device__ inline StepArgs step_args(int N, int tiles_x, int64_t n, double dt, int reunit) {
