@@ -55,9 +55,13 @@ def parse():
 BATCHED = "batched64"
 
 # DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
-# keyed by (workload, kernel, precision); see profiles/.  Absent: not captured
-# for the current kernels.
-TRAFFIC = {}
+# keyed by (workload, events per GPU, kernel, precision), captured on the full
+# workload for the current kernels (profiles/launches_default_30x256.md).
+# Absent: not captured for the current kernels.
+TRAFFIC = {
+    ("n256_charm_static", 30, "field_step", 1): 440824832 + 759966720,
+    ("n256_charm_static", 30, "wong_push", 1): 929808640 + 250289152,
+}
 
 
 def field_bytes_per_site(prec):
@@ -341,7 +345,7 @@ def run_ours(args):
         roof = {}
         for name, (b, t) in kern.items():
             roof[name] = {"bound": "hbm", "achieved": b / t / 1e9, "peak": hbm, "unit": "GB/s",
-                          "frac": b / t / 1e9 / hbm, "traffic": TRAFFIC.get((args.workload, name, prec)),
+                          "frac": b / t / 1e9 / hbm, "traffic": TRAFFIC.get((args.workload, len(ws), name, prec)),
                           "bytes_per_launch": b, "us_per_launch": t * 1e6, "peak_source": peak_src}
         dom = max(kern, key=lambda k: kern[k][1])
         single = args.workload != BATCHED
