@@ -45,12 +45,17 @@ def lib():
             "or_haar_from_normals": (None, [P, P]),
             "or_sample_species": (None, [i, u64, i, i, i, d, d, i64, P]),
             "or_push": (None, [i, d, d, P, P, P, i64, P, P, P]),
+            "or_push_kinds": (None, [i, d, d, P, P, P, i64, P, P, P, P]),
             "or_pL": (d, [P, d, d]),
+            "or_pL_kind": (d, [P, d, d, i]),
+            "or_jets_init": (None, [i, u64, i64, P]),
+            "or_jets_step": (None, [i, d, d, P, P, i64, P]),
+            "or_jets_obs": (None, [i64, P, P]),
             "or_wilson_lines": (None, [i, i, d, d, d, u64, i, P]),
             "or_mv_init": (i, [i, i, d, d, d, u64, P, P]),
             "or_solve_link": (i, [P, P, P]),
             "or_fft": (None, [P, i, i]),
-            "or_particle_obs": (None, [i64, P, d, P, P, P, i, P]),
+            "or_particle_obs": (None, [i64, P, d, P, P, P, P, i, P]),
             "or_threads": (i, []),
         }
         for name, (res, args) in sig.items():
@@ -193,25 +198,63 @@ def sample_species(N, seed, species, rep, mom_mode, p0, p1, n):
     return out
 
 
-def push(N, t, dt, site, U1, phi1, part, mass, active):
+KIND_WONG, KIND_STATIC, KIND_EIKONAL = 0, 1, 2
+JET_LEN = 44
+
+
+def kinds_of(mass, mom_mode=None):
+    """Species kinds: static for INFINITY mass, eikonal for momentum mode 3."""
+    out = []
+    for k, m in enumerate(mass):
+        if np.isinf(m):
+            out.append(KIND_STATIC)
+        elif mom_mode is not None and mom_mode[k] == 3:
+            out.append(KIND_EIKONAL)
+        else:
+            out.append(KIND_WONG)
+    return np.asarray(out, dtype=np.int32)
+
+
+def push(N, t, dt, site, U1, phi1, part, mass, active, kind=None):
     """Euler + CPIC step of ``part`` (modified in place)."""
     m = _f64(mass)
     act = np.ascontiguousarray(active, dtype=np.int32)
-    lib().or_push(N, t, dt, _p(_f64(site)), _p(_f64(U1)), _p(_f64(phi1)), part.shape[0],
-                  _p(part), _p(m), _p(act))
+    kd = kinds_of(mass) if kind is None else np.ascontiguousarray(kind, dtype=np.int32)
+    lib().or_push_kinds(N, t, dt, _p(_f64(site)), _p(_f64(U1)), _p(_f64(phi1)), part.shape[0],
+                        _p(part), _p(m), _p(kd), _p(act))
 
 
-def p_long(rec, t, mass):
+def p_long(rec, t, mass, kind=None):
     rec = _f64(rec)
-    return lib().or_pL(_p(rec), t, mass)
+    if kind is None:
+        return lib().or_pL(_p(rec), t, mass)
+    return lib().or_pL_kind(_p(rec), t, mass, int(kind))
 
 
-def particle_obs(part, t, mass, active, rep):
+def particle_obs(part, t, mass, active, rep, kind=None):
     ns = len(mass)
     out = np.zeros((ns, 8))
-    lib().or_particle_obs(part.shape[0], _p(part), t, _p(_f64(mass)),
+    kd = kinds_of(mass) if kind is None else np.ascontiguousarray(kind, dtype=np.int32)
+    lib().or_particle_obs(part.shape[0], _p(part), t, _p(_f64(mass)), _p(kd),
                           _p(np.ascontiguousarray(active, dtype=np.int32)),
                           _p(np.ascontiguousarray(rep, dtype=np.int32)), ns, _p(out))
+    return out
+
+
+def jets_init(N, seed, n):
+    """Jet-correlator probes [n][44]: x0, y0, W (18), X_x, X_y, X_z (8 each)."""
+    out = np.zeros((n, JET_LEN))
+    lib().or_jets_init(N, seed, n, _p(out))
+    return out
+
+
+def jets_step(N, t, dt, site, U1, jets):
+    lib().or_jets_step(N, t, dt, _p(_f64(site)), _p(_f64(U1)), jets.shape[0], _p(jets))
+
+
+def jets_obs(jets):
+    out = np.zeros(3)
+    lib().or_jets_obs(jets.shape[0], _p(jets), _p(out))
     return out
 
 
@@ -250,17 +293,19 @@ def threads():
 class Run:
     """Coupled field + particle evolution in the oracle (the method's time
     step: leapfrog n -> n+1, site fields at t_n, Euler/CPIC push of the
-    particles active at t_n)."""
+    particles active at t_n, and the jet-correlator probes if any)."""
 
-    def __init__(self, state, particles, mass, t_form, rep, dt, step=0):
+    def __init__(self, state, particles, mass, t_form, rep, dt, step=0, kind=None, jets=None):
         self.st = state
         self.part = particles
         self.mass = np.asarray(mass, dtype=np.float64)
         self.t_form = np.asarray(t_form, dtype=np.float64)
         self.rep = np.asarray(rep, dtype=np.int32)
+        self.kind = kinds_of(self.mass) if kind is None else np.asarray(kind, dtype=np.int32)
         self.dt = dt
         self.n = step
         self.site = None
+        self.jets = jets
 
     def t(self):
         return self.n * self.dt
@@ -273,7 +318,9 @@ class Run:
         new = field_step(self.st, t, self.dt)
         self.site = site_fields(self.st, new, t)
         if self.part is not None and len(self.part):
-            push(self.st.N, t, self.dt, self.site, new.U, new.phi, self.part, self.mass, self.active())
+            push(self.st.N, t, self.dt, self.site, new.U, new.phi, self.part, self.mass, self.active(), self.kind)
+        if self.jets is not None and len(self.jets):
+            jets_step(self.st.N, t, self.dt, self.site, new.U, self.jets)
         self.st = new
         self.n += 1
 
@@ -281,4 +328,4 @@ class Run:
         """Particle sums after the last push (time t_n of the new step) with
         the species activity of the step that was pushed."""
         act = (((self.n - 1) * self.dt) >= self.t_form).astype(np.int32)
-        return particle_obs(self.part, self.t(), self.mass, act, self.rep)
+        return particle_obs(self.part, self.t(), self.mass, act, self.rep, self.kind)

@@ -82,20 +82,48 @@ void or_casimirs(const double* q8, double* q2, double* q3);
 void or_haar_from_normals(const double* g18, double* out18);
 /* Sample n particles of one species (positions, momenta, Haar charges).
  * mom_mode: 0 fixed |pT| = p0 with uniform azimuth; 1 |pT| ~ U[p0, p1] with
- * uniform azimuth; 2 p^x = p0, p^y = 0.  Momenta in lattice units. */
+ * uniform azimuth; 2 p^x = p0, p^y = 0; 3 zero (eikonal partons record only
+ * their kicks).  Momenta in lattice units. */
 void or_sample_species(int N, uint64_t seed, int species, int rep, int mom_mode,
                        double p0, double p1, int64_t n, double* out16);
+/* Species kinds: Wong particles of finite mass, infinitely massive static
+ * quarks (Sec. 5.1), eikonal light-like partons along +x (Sec. 5.2). */
+enum { OR_KIND_WONG = 0, OR_KIND_STATIC = 1, OR_KIND_EIKONAL = 2 };
+#define OR_MAX_SPECIES 8
 /* One Euler + CPIC step of all particles from t_n to t_n + dt.
  * site: site fields at t_n; U1, phi1: links and scalar at t_{n+1}.
- * mass[s] per species (INFINITY = static), active[s] nonzero if species s is
- * active at t_n.  Particle records are updated in place. */
+ * mass[s], kind[s] per species, active[s] nonzero if species s is active at
+ * t_n.  Particle records are updated in place.  Eikonal partons move by dt
+ * along +x, keep y and eta, add the kicks dt Q.(E_x, E_y - B_z, E_z + B_y) to
+ * p^x, p^y and the P_eta slot, and rotate Q with the crossed x link. */
+void or_push_kinds(int N, double t, double dt, const double* site, const double* U1,
+                   const double* phi1, int64_t n, double* part, const double* mass,
+                   const int* kind, const int* active);
+/* or_push_kinds with the kinds from the masses (INFINITY = static, else Wong). */
 void or_push(int N, double t, double dt, const double* site, const double* U1,
              const double* phi1, int64_t n, double* part, const double* mass,
              const int* active);
 /* Longitudinal momentum p_L = p^z of one particle at time t (lab frame,
- * p^z = p^tau sinh(eta) + tau p^eta cosh(eta)); static species return the
- * accumulated value. */
+ * p^z = p^tau sinh(eta) + tau p^eta cosh(eta)); static and eikonal species
+ * return the accumulated value. */
+double or_pL_kind(const double* rec16, double t, double mass, int kind);
+/* or_pL_kind with the kind from the mass (INFINITY = static). */
 double or_pL(const double* rec16, double t, double mass);
+
+/* Light-like jet correlator (Sec. 5.2): probe records of OR_JET_LEN doubles,
+ * x0, y0, W (3x3 complex, row-major re/im), X_x, X_y, X_z (8 each).  A probe
+ * starts at (x0, y0) at tau = 0, moves along +x at the speed of light,
+ * multiplies W by each x link it crosses (links at t_{n+1}) and accumulates
+ * X_i += dt W f_i W^+ with f = (E_x, E_y - B_z, E_z + B_y) at its cell at
+ * t_n.  A parton of charge Q0 on that path receives the kicks Q0 . X_i; the
+ * charge-averaged broadening is <dp_i^2> = (q2 / 8) <X_i . X_i>. */
+#define OR_JET_LEN 44
+/* Probes at uniform positions from Philox counters (j, 0, 4, 0). */
+void or_jets_init(int N, uint64_t seed, int64_t n, double* jets);
+/* One step of every probe from t_n = t (site fields at t_n, links U1 at t_{n+1}). */
+void or_jets_step(int N, double t, double dt, const double* site, const double* U1, int64_t n, double* jets);
+/* out3[i] = mean over probes of X_i . X_i. */
+void or_jets_obs(int64_t n, const double* jets, double* out3);
 
 /* ---- MV initial conditions (init.c) ------------------------------------ */
 /* Wilson lines V^+ of one nucleus (nucleus 0 = A, 1 = B) from Ns sheets of
@@ -119,7 +147,7 @@ void or_fft(double* data, int n, int sign);
  * out[s*8 + k]: k=0 count, 1 sum px^2, 2 sum py^2, 3 sum pL^2,
  * 4 sum (pT^2 - pT0^2), 5 max |q2 - q2_0|, 6 max |q3 - q3_0|, 7 unused. */
 void or_particle_obs(int64_t n, const double* part, double t, const double* mass,
-                     const int* active, const int* rep, int n_species, double* out);
+                     const int* kind, const int* active, const int* rep, int n_species, double* out);
 
 /* OpenMP threads used by the site and particle loops. */
 int or_threads(void);

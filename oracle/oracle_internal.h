@@ -30,7 +30,7 @@ double u01(uint32_t r);
 /* two standard normals from two uniforms (Box-Muller) */
 void box_muller(double u1, double u2, double* z0, double* z1);
 /* Philox counter purposes */
-enum { PURPOSE_MV = 1, PURPOSE_KIN = 2, PURPOSE_HAAR = 3 };
+enum { PURPOSE_MV = 1, PURPOSE_KIN = 2, PURPOSE_HAAR = 3, PURPOSE_JET = 4 };
 
 static inline int wrap(int i, int n) { i %= n; return i < 0 ? i + n : i; }
 static inline int64_t site_index(int N, int x, int y) { return (int64_t)wrap(y, N) * N + wrap(x, N); }

@@ -83,6 +83,7 @@ void or_sample_species(int N, uint64_t seed, int species, int rep, int mom_mode,
         double pt = mom_mode == 1 ? p0 + (p1 - p0) * u01(w[3]) : p0;
         double px = pt * cos(psi), py = pt * sin(psi);
         if (mom_mode == 2) { px = p0; py = 0.0; }
+        if (mom_mode == 3) { px = 0.0; py = 0.0; }  /* eikonal: only the kicks are recorded */
         /* 18 normals from 5 Philox blocks (Box-Muller on pairs of uniforms) */
         double g[20];
         for (int j = 0; j < 5; j++) {
@@ -117,9 +118,9 @@ static void rotate(double* q, mat3 W) {
     mat_to_alg(m_mul(m_mul(W, Q), m_dag(W)), q);
 }
 
-void or_push(int N, double t, double dt, const double* site, const double* U1,
-             const double* phi1, int64_t n, double* part, const double* mass,
-             const int* active) {
+void or_push_kinds(int N, double t, double dt, const double* site, const double* U1,
+                   const double* phi1, int64_t n, double* part, const double* mass,
+                   const int* kind, const int* active) {
     const int64_t V = (int64_t)N * N;
 #pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < n; p++) {
@@ -139,12 +140,30 @@ void or_push(int N, double t, double dt, const double* site, const double* U1,
         double* q = r + 6;
         double qEx = qdot(q, Ex), qEy = qdot(q, Ey), qEe = qdot(q, Ee);
         double qBx = qdot(q, Bx), qBy = qdot(q, By), qBe = qdot(q, Be);
-        if (isinf(m)) {
+        if (kind[s] == OR_KIND_STATIC) {
             /* infinitely massive: no motion, no colour rotation (temporal
              * gauge), momentum kicks from the electric field only */
             r[3] += dt * qEx;
             r[4] += dt * qEy;
             r[5] += dt * qEe;
+            continue;
+        }
+        if (kind[s] == OR_KIND_EIKONAL) {
+            /* light-like parton along +x at eta = 0 (Sec. 5.2): the path is
+             * x = x0 + t, the kicks of the Lorentz force (E_x, E_y - B_z,
+             * E_z + B_y) accumulate in p^x, p^y and the P_eta slot (lab p_z),
+             * and Q is carried along by the crossed x links */
+            r[3] += dt * qEx;
+            r[4] += dt * (qEy - qBe);
+            r[5] += dt * (qEe + qBy);
+            double xn = r[0] + dt;
+            int jxu = (int)floor(xn + 0.5);
+            xn = fmod(xn, (double)N); if (xn < 0) xn += N;
+            r[0] = xn;
+            if (jxu != ixu) {
+                mat3 u = m_load(U1 + (0 * V + site_index(N, ixu, iyu)) * 18);
+                rotate(q, m_dag(u));
+            }
             continue;
         }
         double px = r[3], py = r[4], Pe = r[5];
@@ -192,6 +211,25 @@ void or_push(int N, double t, double dt, const double* site, const double* U1,
     }
 }
 
+void or_push(int N, double t, double dt, const double* site, const double* U1,
+             const double* phi1, int64_t n, double* part, const double* mass,
+             const int* active) {
+    int kind[OR_MAX_SPECIES];
+    for (int s = 0; s < OR_MAX_SPECIES; s++) kind[s] = OR_KIND_WONG;
+    for (int64_t p = 0; p < n; p++) {
+        int s = (int)part[p * 16 + 15];
+        if (s >= 0 && s < OR_MAX_SPECIES && isinf(mass[s])) kind[s] = OR_KIND_STATIC;
+    }
+    or_push_kinds(N, t, dt, site, U1, phi1, n, part, mass, kind, active);
+}
+
+double or_pL_kind(const double* r, double t, double m, int kind) {
+    if (kind != OR_KIND_WONG) return r[5];
+    double w = t > 0 ? r[5] / t : 0.0;
+    double ptau = sqrt(r[3] * r[3] + r[4] * r[4] + w * w + m * m);
+    return ptau * sinh(r[2]) + w * cosh(r[2]);
+}
+
 double or_pL(const double* r, double t, double m) {
     if (isinf(m)) return r[5];
     double w = t > 0 ? r[5] / t : 0.0;
@@ -200,7 +238,7 @@ double or_pL(const double* r, double t, double m) {
 }
 
 void or_particle_obs(int64_t n, const double* part, double t, const double* mass,
-                     const int* active, const int* rep, int n_species, double* out) {
+                     const int* kind, const int* active, const int* rep, int n_species, double* out) {
     memset(out, 0, (size_t)n_species * 8 * sizeof(double));
     double q2r[2], q3r[2];
     for (int k = 0; k < 2; k++) {
@@ -213,7 +251,7 @@ void or_particle_obs(int64_t n, const double* part, double t, const double* mass
         int s = (int)r[15];
         if (!active[s]) continue;
         double* o = out + s * 8;
-        double pl = or_pL(r, t, mass[s]);
+        double pl = or_pL_kind(r, t, mass[s], kind[s]);
         double q2, q3;
         or_casimirs(r + 6, &q2, &q3);
         o[0] += 1;
@@ -225,4 +263,69 @@ void or_particle_obs(int64_t n, const double* part, double t, const double* mass
         if (d2 > o[5]) o[5] = d2;
         if (d3 > o[6]) o[6] = d3;
     }
+}
+
+/* ---- light-like jet correlator (Sec. 5.2, light-like jets) ------------- */
+/* A probe starts at (x0, y0) at tau = 0 and moves along +x at the speed of
+ * light (x = x0 + t in lattice units).  It carries the Wilson line W of the x
+ * links it has crossed (W <- W U_x on each crossing, links at t_{n+1}) and
+ * the integrals X_i = sum_n dt W f_i W^+ of the Lorentz-force components
+ * f = (E_x, E_y - B_z, E_z + B_y) at its cell, so that a parton of charge Q0
+ * would have received the kicks Q0 . X_i.  Record: x0, y0, W (18), X (3 x 8). */
+void or_jets_init(int N, uint64_t seed, int64_t n, double* jets) {
+    uint32_t key[2];
+    key_of(seed, key);
+    for (int64_t j = 0; j < n; j++) {
+        double* r = jets + j * OR_JET_LEN;
+        memset(r, 0, OR_JET_LEN * sizeof(double));
+        uint32_t ctr[4] = {(uint32_t)j, 0u, PURPOSE_JET, 0u}, w[4];
+        or_philox4x32_10(ctr, key, w);
+        r[0] = N * u01(w[0]);
+        r[1] = N * u01(w[1]);
+        for (int i = 0; i < 3; i++) r[2 + 2 * (3 * i + i)] = 1.0;  /* W = 1 */
+    }
+}
+
+void or_jets_step(int N, double t, double dt, const double* site, const double* U1, int64_t n, double* jets) {
+    const int64_t V = (int64_t)N * N;
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n; j++) {
+        double* r = jets + j * OR_JET_LEN;
+        const double x = r[0] + t;
+        const int ixu = (int)floor(x + 0.5), iyu = (int)floor(r[1] + 0.5);
+        const int64_t cell = site_index(N, ixu, iyu);
+        const double* Ex = site + (0 * V + cell) * 8;
+        const double* Ey = site + (1 * V + cell) * 8;
+        const double* Ee = site + (2 * V + cell) * 8;
+        const double* By = site + (4 * V + cell) * 8;
+        const double* Be = site + (5 * V + cell) * 8;
+        double f[3][8];
+        for (int a = 0; a < 8; a++) {
+            f[0][a] = Ex[a];
+            f[1][a] = Ey[a] - Be[a];
+            f[2][a] = Ee[a] + By[a];
+        }
+        mat3 W = m_load(r + 2);
+        for (int i = 0; i < 3; i++) {
+            double g[8];
+            mat_to_alg(m_mul(m_mul(W, alg_to_mat(f[i])), m_dag(W)), g);
+            for (int a = 0; a < 8; a++) r[20 + 8 * i + a] += dt * g[a];
+        }
+        if ((int)floor(x + dt + 0.5) != ixu) {
+            W = m_mul(W, m_load(U1 + (0 * V + cell) * 18));
+            m_store(W, r + 2);
+        }
+    }
+}
+
+void or_jets_obs(int64_t n, const double* jets, double* out3) {
+    out3[0] = out3[1] = out3[2] = 0.0;
+    for (int64_t j = 0; j < n; j++)
+        for (int i = 0; i < 3; i++)
+            for (int a = 0; a < 8; a++) {
+                const double v = jets[j * OR_JET_LEN + 20 + 8 * i + a];
+                out3[i] += v * v;
+            }
+    if (n > 0)
+        for (int i = 0; i < 3; i++) out3[i] /= (double)n;
 }

@@ -185,6 +185,70 @@ def test_light_like_limit_equals_jet_correlator():
     assert g2 < 0.75 * g1 and g1 < 0.2 * np.abs(pred[:, 2]).max()
 
 
+def _probes_at(x0, y0):
+    jets = np.zeros((len(x0), O.JET_LEN))
+    jets[:, 0], jets[:, 1] = x0, y0
+    for i in range(3):
+        jets[:, 2 + 2 * (3 * i + i)] = 1.0
+    return jets
+
+
+def test_oracle_jet_correlator_equals_direct_sum():
+    """The oracle's jet correlator (Sec. 5.2) against the transported-force
+    sum written out here with numpy on the oracle's own site fields and links
+    (W <- W U_x on each crossing, X_i += dt W f_i W^+)."""
+    N, n, dt, T = 16, 30, 0.125, 7.5
+    st = mv_state(N)
+    rng = np.random.default_rng(5)
+    x0, y0 = rng.uniform(0, N, n), rng.uniform(0, N, n)
+    jets = _probes_at(x0, y0)
+    r = O.Run(st, None, [0.0], [0.0], [0], dt, jets=jets)
+    W = np.broadcast_to(np.eye(3, dtype=complex), (n, 3, 3)).copy()
+    X = np.zeros((n, 3, 3, 3), dtype=complex)
+    iy = np.floor(y0 + 0.5).astype(int) % N
+    for k in range(int(round(T / dt))):
+        ix = np.floor(x0 + k * dt + 0.5).astype(int)
+        r.step()
+        cell = iy * N + ix % N
+        Ex, Ey, Ee, Bx, By, Be = [H.alg2mat(r.site[j][cell]) for j in range(6)]
+        for i, f in enumerate((Ex, Ey - Be, Ee + By)):
+            X[:, i] += dt * W @ f @ W.conj().transpose(0, 2, 1)
+        cross = np.floor(x0 + (k + 1) * dt + 0.5).astype(int) != ix
+        W[cross] = W[cross] @ H.links(r.st.U)[0][cell][cross]
+    want = np.stack([H.mat2alg(X[:, i]) for i in range(3)], 1)
+    got = jets[:, 20:44].reshape(n, 3, 8)
+    assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+    Wgot = jets[:, 2:20].view(np.complex128).reshape(n, 3, 3)
+    assert np.abs(Wgot - W).max() < 1e-12
+    assert np.allclose(O.jets_obs(jets), (want ** 2).sum(axis=2).mean(axis=0), rtol=1e-12)
+
+
+def test_eikonal_partons_receive_the_correlator_kicks():
+    """Eikonal partons (fixed light-like path along +x, no momentum feedback)
+    rotate their charge instead of transporting the force: their kicks equal
+    Q0 . X_i of probes on the same paths to rounding, whatever the charge."""
+    N, n, dt, T = 16, 40, 0.125, 6.0
+    st = mv_state(N)
+    part = O.sample_species(N, 9, 0, 0, 3, 0.0, 0.0, n)
+    assert np.all(part[:, 3:6] == 0.0) and np.all(part[:, 14] == 0.0)
+    x0, y0, Q0 = part[:, 0].copy(), part[:, 1].copy(), part[:, 6:14].copy()
+    jets = _probes_at(x0, y0)
+    r = O.Run(st, part, [0.0], [0.0], [0], dt, kind=[O.KIND_EIKONAL], jets=jets)
+    steps = int(round(T / dt))
+    for _ in range(steps):
+        r.step()
+    X = jets[:, 20:44].reshape(n, 3, 8)
+    kick = np.einsum("na,nia->ni", Q0, X)
+    assert np.abs(part[:, 3:6] - kick).max() < 1e-12 * np.abs(kick).max()
+    assert np.allclose(part[:, 0], (x0 + steps * dt) % N, atol=1e-12)
+    assert np.array_equal(part[:, 1], y0) and np.all(part[:, 2] == 0.0)
+    # the charge moved on the colour sphere: Casimirs unchanged
+    q2 = (part[:, 6:14] ** 2).sum(axis=1)
+    assert np.abs(q2 - 4.0).max() < 1e-12
+    # p_L of an eikonal parton is the accumulated lab p_z
+    assert O.p_long(part[0], r.t(), 0.0, O.KIND_EIKONAL) == part[0, 5]
+
+
 # ------------------------------------------------------------------ closed forms
 def _hyperbolic_gap(dt):
     # uniform Abelian E_eta on a trivial background = uniform lab E_z; a
