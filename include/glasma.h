@@ -34,7 +34,11 @@
  *   GL_BUF_PARTICLES  [np][16]      x, y, eta, p^x, p^y, P_eta, Q^1..Q^8,
  *                                   p_T^2 at formation, species index;
  *                                   x, y in [0, N); P_eta = tau^2 p^eta
- *                                   (static species: accumulated p_L)
+ *                                   (static and eikonal species: accumulated
+ *                                   lab p_z)
+ *   GL_BUF_JETS       [n_jets][44]  light-like jet-correlator probes: x0, y0,
+ *                                   W (3x3 complex, row-major re/im), X_x, X_y,
+ *                                   X_z (8 components each), see gl_config
  */
 #ifndef GLASMA_H
 #define GLASMA_H
@@ -67,7 +71,8 @@ typedef enum {
     GL_BUF_E = 2,
     GL_BUF_PI = 3,
     GL_BUF_SITE = 4,
-    GL_BUF_PARTICLES = 5
+    GL_BUF_PARTICLES = 5,
+    GL_BUF_JETS = 6
 } gl_buffer;
 
 /* One MV event (Sec. 2, parameters of Sec. 7.1). */
@@ -85,7 +90,12 @@ typedef struct {
     uint64_t seed;          /* Philox key of this event's random numbers */
     int32_t sort_every;     /* reorder particles by cell every k pushes (0: never); only the
                                memory order changes, downloads keep the caller's order */
-    int32_t reserved;       /* must be 0 */
+    int32_t n_jets;         /* light-like jet-correlator probes (Sec. 5.2, light-like jets), >= 0:
+                               each starts at a uniform (x0, y0) at tau = 0 (Philox counters
+                               (j, 0, 4, 0)) and moves along +x at the speed of light, carrying
+                               the Wilson line W of the x links it crosses (links at t_{n+1})
+                               and X_i = sum dt W f_i W^+, f = (E_x, E_y - B_eta, E_eta + B_y)
+                               at its cell at t_n; advanced by every push; single events only */
 } gl_config;
 
 /* One species of test particles (Sec. 3.2 and 7.1). */
@@ -95,7 +105,12 @@ typedef struct {
     int64_t count;
     int32_t rep;            /* 0: fundamental charge (q2 = 4, q3 = 10/3); 1: adjoint (24, 0) */
     int32_t mom_mode;       /* 0: |p_T| = p0, uniform azimuth; 1: |p_T| ~ U[p0, p1], uniform
-                               azimuth; 2: p^x = p0, p^y = 0 */
+                               azimuth; 2: p^x = p0, p^y = 0; 3: eikonal light-like parton
+                               along +x (Sec. 5.2): the path x = x0 + t is fixed, y and eta
+                               stay, the momenta start at 0 and accumulate the kicks
+                               dt Q.(E_x, E_y - B_eta, E_eta + B_y) (p^x, p^y, lab p_z in the
+                               P_eta slot), and Q is rotated by the crossed x links; the mass
+                               is not used */
     double p0_GeV, p1_GeV;
 } gl_species;
 
@@ -206,6 +221,14 @@ gl_status observables(gl_ctx* ctx, gl_obs* out);
 #define GL_OBS_FIELDS 2u
 #define GL_OBS_ALL 3u
 
+/* Jet-correlator result (waits): out[i] = mean over the probes of X_i . X_i
+ * = sum_a (X_i^a)^2 for i = x, y, z, in GeV^2.  A parton of charge Q0 on a
+ * probe's path receives the kicks Q0 . X_i, so the charge-averaged momentum
+ * broadening of a light-like parton in representation R is
+ * <delta p_i^2> = (q2(R) / 8) out[i] (q2 = 4 fundamental, 24 adjoint).
+ * GL_ERR_STATE if the context has no probes. */
+gl_status gl_jets_observables(gl_ctx* ctx, double* out3);
+
 /* observables() restricted to the parts in `what` (waits).  The values of the
  * other parts are NaN and their counts 0; out->what records the parts
  * computed.  GL_ERR_ARG for a null pointer or unknown bits in `what`. */
@@ -217,10 +240,12 @@ gl_status gl_observables_ex(gl_ctx* ctx, uint32_t what, gl_obs* out);
  * step of the whole batch is one field launch over the tiles of every event
  * and one push launch over the particles of every event, captured once in a
  * CUDA graph and replayed; the field launch of step s runs concurrently with
- * the push of step s - 1 on a second stream.  All events share the precision, the time step
- * dtau/a and the re-unitarisation period; they start at tau = 0 together.
- * The events' particles are sorted by cell when sampled or uploaded; the
- * batch step does not re-sort them. */
+ * the push of step s - 1 (the schedule is chosen by gl_batch_autotune).  All
+ * events share the precision, the time step dtau/a and the re-unitarisation
+ * period; they start at tau = 0 together.  Each event's particles are sorted
+ * by cell when sampled or uploaded and every sort_every steps (all events in
+ * one launch per sort stage).  Jet-correlator probes (n_jets > 0) are not
+ * supported in batches (GL_ERR_ARG). */
 typedef struct gl_batch gl_batch;
 
 /* Workspace bytes for n_events events; cfgs[n_events], species

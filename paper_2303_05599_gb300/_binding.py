@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(HERE, "libglasma_gb300.so")
 GL_MAX_SPECIES = 8
 GL_OK, GL_ERR_ARG, GL_ERR_CUDA, GL_ERR_STATE, GL_ERR_TIMEOUT, GL_ERR_NUMERIC, GL_ERR_SIZE = range(7)
 GL_FP64, GL_FP32_2ROW = 0, 1
-GL_BUF_LINKS, GL_BUF_PHI, GL_BUF_E, GL_BUF_PI, GL_BUF_SITE, GL_BUF_PARTICLES = range(6)
+GL_BUF_LINKS, GL_BUF_PHI, GL_BUF_E, GL_BUF_PI, GL_BUF_SITE, GL_BUF_PARTICLES, GL_BUF_JETS = range(7)
+JET_LEN = 44
 
 STATUS_NAMES = {0: "GL_OK", 1: "GL_ERR_ARG", 2: "GL_ERR_CUDA", 3: "GL_ERR_STATE", 4: "GL_ERR_TIMEOUT",
                 5: "GL_ERR_NUMERIC", 6: "GL_ERR_SIZE"}
@@ -27,7 +28,7 @@ class gl_config(ctypes.Structure):
                 ("reunit_every", ctypes.c_int32), ("L_fm", ctypes.c_double), ("g2mu_GeV", ctypes.c_double),
                 ("mIR_GeV", ctypes.c_double), ("LambdaUV_GeV", ctypes.c_double),
                 ("dtau_over_a", ctypes.c_double), ("seed", ctypes.c_uint64), ("sort_every", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("n_jets", ctypes.c_int32)]
 
 
 class gl_species(ctypes.Structure):
@@ -70,6 +71,7 @@ SIGNATURES = {
     "gl_observables_ex": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.POINTER(gl_obs)]),
     "gl_autotune": (ctypes.c_int, [_P, _P, _P]),
     "gl_tuning": (ctypes.c_int, [_P, _P, _P]),
+    "gl_jets_observables": (ctypes.c_int, [_P, _P]),
     "gl_ensemble_sums_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_uint32,
                                                 ctypes.c_double, _P, _P]),
     "gl_batch_workspace_bytes": (ctypes.c_size_t, [_P, _P, ctypes.c_int32, ctypes.c_int32]),
@@ -129,7 +131,7 @@ def make_config(w):
     """gl_config from a workloads.Workload."""
     return gl_config(N=w.N, Ns=w.Ns, precision=w.precision, reunit_every=w.reunit_every, L_fm=w.L_fm,
                      g2mu_GeV=w.g2mu_GeV, mIR_GeV=w.mIR_GeV, LambdaUV_GeV=w.LambdaUV_GeV,
-                     dtau_over_a=w.dtau_over_a, seed=w.seed, sort_every=w.sort_every, reserved=0)
+                     dtau_over_a=w.dtau_over_a, seed=w.seed, sort_every=w.sort_every, n_jets=w.n_jets)
 
 
 def make_species(w):
@@ -171,6 +173,7 @@ class Event:
         _check(st, None, "gl_create")
         self.N = workload.N
         self.np = workload.n_particles
+        self.n_jets = workload.n_jets
 
     @classmethod
     def view(cls, ctx, workload):
@@ -180,6 +183,7 @@ class Event:
         ev.ctx = ctypes.c_void_p(ctx)
         ev.N = workload.N
         ev.np = workload.n_particles
+        ev.n_jets = workload.n_jets
         ev.owned = False
         return ev
 
@@ -239,7 +243,14 @@ class Event:
     def _shape(self, which):
         V = self.N * self.N
         return {GL_BUF_LINKS: (2, V, 18), GL_BUF_PHI: (V, 8), GL_BUF_E: (2, V, 8), GL_BUF_PI: (V, 8),
-                GL_BUF_SITE: (6, V, 8), GL_BUF_PARTICLES: (self.np, 16)}[which]
+                GL_BUF_SITE: (6, V, 8), GL_BUF_PARTICLES: (self.np, 16),
+                GL_BUF_JETS: (self.n_jets, JET_LEN)}[which]
+
+    def jets_observables(self):
+        """Mean over the jet-correlator probes of X_i . X_i (i = x, y, z), GeV^2."""
+        out = (ctypes.c_double * 3)()
+        _check(lib().gl_jets_observables(self.ctx, out), self.ctx, "gl_jets_observables")
+        return list(out)
 
     def upload(self, which, arr):
         a = np.ascontiguousarray(arr, dtype=np.float64)

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libglasma_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-UNITS = ["step_fused.cu", "particles.cu", "init.cu", "obs.cu", "capi.cu", "noalloc.cu", "sort.cu", "batch.cu"]
+UNITS = ["step_fused.cu", "particles.cu", "init.cu", "obs.cu", "capi.cu", "noalloc.cu", "sort.cu", "batch.cu", "jets.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]

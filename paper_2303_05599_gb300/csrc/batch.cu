@@ -45,7 +45,7 @@ struct EvDesc {
     int chunk_begin; // first block of this event in the push launch
     int64_t np;
     double mass[GL_MAX_SPECIES];
-    int is_static[GL_MAX_SPECIES];
+    int motion[GL_MAX_SPECIES];
     double t_form[GL_MAX_SPECIES];
     int n_species;
     int pad;
@@ -112,8 +112,8 @@ __device__ __forceinline__ void push_item(const BatchArgs& b, int lag, int blk) 
         uint32_t active = 0;
         for (int k = 0; k < GL_MAX_SPECIES; k++) {
             if (k < d.n_species && t >= d.t_form[k]) active |= 1u << k;
-            s_sa.mass[k] = (R)(d.is_static[k] ? 0.0 : d.mass[k]);
-            s_sa.is_static[k] = d.is_static[k];
+            s_sa.mass[k] = (R)(d.motion[k] == MOTION_WONG ? d.mass[k] : 0.0);
+            s_sa.motion[k] = d.motion[k];
         }
         s_e = e;
         s_n = n;
@@ -416,6 +416,8 @@ gl_status gl_batch_create(const gl_config* cfgs, const gl_species* species, int3
     if (!need) return GL_ERR_ARG;
     if (bytes < need) return GL_ERR_SIZE;
     if (!d_workspace || ((uintptr_t)d_workspace & 255)) return GL_ERR_ARG;
+    for (int e = 0; e < n_events; e++)
+        if (cfgs[e].n_jets != 0) return GL_ERR_ARG;  // jet probes: single events only
     for (int e = 1; e < n_events; e++)
         if (cfgs[e].precision != cfgs[0].precision || cfgs[e].dtau_over_a != cfgs[0].dtau_over_a ||
             cfgs[e].reunit_every != cfgs[0].reunit_every)
@@ -546,7 +548,7 @@ static gl_status sync_desc(gl_batch* b) {
         b->sort_every[e] = v.sort_every;
         for (int k = 0; k < GL_MAX_SPECIES; k++) {
             d.mass[k] = v.mass[k];
-            d.is_static[k] = v.is_static[k];
+            d.motion[k] = v.motion[k];
             d.t_form[k] = v.t_form[k];
         }
     }

@@ -46,6 +46,9 @@ struct gl_ctx {
     void* parts_alt;    // second particle buffer for the cell sort
     void* sort_scratch;
     int sort_ok;
+    int64_t n_jets;       // light-like jet-correlator probes (0: none)
+    void* jets;
+    double* jet_partials; // 1024 x 3 block partials, then the 3 results
     void* scratch;
     size_t scratch_bytes;
     double* partials;
@@ -102,16 +105,17 @@ static const char* validate(const gl_config* cfg, const gl_species* sp, int32_t 
     for (int k = 0; k < ns; k++) {
         if (sp[k].count < 0) return "negative particle count";
         if (sp[k].rep != 0 && sp[k].rep != 1) return "rep must be 0 or 1";
-        if (sp[k].mom_mode < 0 || sp[k].mom_mode > 2) return "mom_mode must be 0, 1 or 2";
+        if (sp[k].mom_mode < 0 || sp[k].mom_mode > 3) return "mom_mode must be 0, 1, 2 or 3";
         if (!(sp[k].mass_GeV >= 0)) return "mass must be >= 0 or INFINITY";
         np += sp[k].count;
     }
     if (np >= ((int64_t)1 << 31)) return "at most 2^31 - 1 particles";
+    if (cfg->n_jets < 0 || cfg->n_jets > (1 << 24)) return "n_jets must be in [0, 2^24]";
     return nullptr;
 }
 
 struct Carve {
-    size_t field, site, parts, parts_alt, sort, scratch, partials, obs, bad, total;
+    size_t field, site, parts, parts_alt, sort, jets, jet_partials, scratch, partials, obs, bad, total;
 };
 
 static Carve carve(const gl_config* cfg, int64_t np) {
@@ -125,10 +129,14 @@ static Carve carve(const gl_config* cfg, int64_t np) {
     const bool sorting = cfg->sort_every > 0 && np > 0 && sort_supported(Vn);
     c.parts_alt = o; o += sorting ? a256(particle_bytes(prec, np)) : 0;
     c.sort = o; o += sorting ? a256(sort_scratch_bytes(Vn, np)) : 0;
+    const size_t nj = cfg->n_jets > 0 ? (size_t)cfg->n_jets : 0;
+    c.jets = o; o += nj ? a256(nj * JET_LEN * (prec == 0 ? 8 : 4)) : 0;
+    c.jet_partials = o; o += nj ? a256((1024 * 3 + 3) * sizeof(double)) : 0;
     size_t sc = init_scratch_bytes(Vn);
     size_t stg = (size_t)Vn * 6 * 8 * sizeof(double);
     if (stg > sc) sc = stg;
     if ((size_t)np * 16 * sizeof(double) > sc) sc = (size_t)np * 16 * sizeof(double);
+    if (nj * JET_LEN * sizeof(double) > sc) sc = nj * JET_LEN * sizeof(double);
     c.scratch = o; o += a256(sc);
     c.partials = o; o += a256((size_t)MAX_BLOCKS * (GL_MAX_SPECIES * PO_N + FO_N) * sizeof(double));
     c.obs = o; o += a256((GL_MAX_SPECIES * PO_N + FO_N) * sizeof(double));
@@ -168,7 +176,7 @@ void ctx_view(const gl_ctx* c, CtxView* v) {
     v->dt = c->dt;
     for (int k = 0; k < GL_MAX_SPECIES; k++) {
         v->mass[k] = c->spp.mass[k];
-        v->is_static[k] = c->spp.is_static[k];
+        v->motion[k] = c->spp.motion[k];
         v->t_form[k] = c->t_form[k];
     }
     v->ns = c->ns;
@@ -256,6 +264,9 @@ gl_status gl_create(const gl_config* cfg, const gl_species* sp, int32_t ns, void
     c->sort_ok = cfg->sort_every > 0 && c->np > 0 && sort_supported(c->Vn);
     c->parts_alt = c->sort_ok ? c->ws + cv.parts_alt : nullptr;
     c->sort_scratch = c->sort_ok ? c->ws + cv.sort : nullptr;
+    c->n_jets = cfg->n_jets;
+    c->jets = c->n_jets ? c->ws + cv.jets : nullptr;
+    c->jet_partials = c->n_jets ? (double*)(c->ws + cv.jet_partials) : nullptr;
     c->scratch = c->ws + cv.scratch;
     c->scratch_bytes = cv.partials - cv.scratch;
     c->partials = (double*)(c->ws + cv.partials);
@@ -274,7 +285,7 @@ gl_status gl_create(const gl_config* cfg, const gl_species* sp, int32_t ns, void
     for (int k = 0; k < GL_MAX_SPECIES; k++) {
         const bool on = k < ns;
         const bool st = on && isinf(sp[k].mass_GeV);
-        c->spp.is_static[k] = st;
+        c->spp.motion[k] = st ? MOTION_STATIC : (on && sp[k].mom_mode == 3 ? MOTION_EIKONAL : MOTION_WONG);
         c->spp.mass[k] = on ? (st ? INFINITY : sp[k].mass_GeV * c->aG) : 0.0;
         c->t_form[k] = on ? sp[k].tau_form_fm * cfg->N / cfg->L_fm : 0.0;
         c->p0[k] = on ? sp[k].p0_GeV * c->aG : 0.0;
@@ -357,6 +368,7 @@ gl_status wong_init(gl_ctx* c) {
     launch_sample(c->prec, c->parts, c->np, c->N, c->cfg.seed, c->off, c->ns, c->rep, c->mode, c->p0, c->p1, c->q0,
                   c->stream);
     sort_particles(c);
+    if (c->n_jets) launch_jets_init(c->prec, c->jets, c->n_jets, c->N, c->cfg.seed, c->stream);
     c->pstep = c->step;
     return check_cuda(c, "wong_init");
 }
@@ -369,13 +381,14 @@ static size_t expected_count(const gl_ctx* c, gl_buffer which) {
         case GL_BUF_PI: return (size_t)c->Vn * 8;
         case GL_BUF_SITE: return (size_t)6 * c->Vn * 8;
         case GL_BUF_PARTICLES: return (size_t)c->np * 16;
+        case GL_BUF_JETS: return (size_t)c->n_jets * JET_LEN;
     }
     return 0;
 }
 
 static gl_status transfer(gl_ctx* c, gl_buffer which, double* host, size_t count, int to_device) {
     if (!c || (!host && count)) return GL_ERR_ARG;
-    if ((int)which < 0 || (int)which > GL_BUF_PARTICLES) return fail(c, GL_ERR_ARG, "unknown buffer");
+    if ((int)which < 0 || (int)which > GL_BUF_JETS) return fail(c, GL_ERR_ARG, "unknown buffer");
     if (count != expected_count(c, which)) return fail(c, GL_ERR_SIZE, "host buffer size does not match");
     if (to_device && which == GL_BUF_SITE) return fail(c, GL_ERR_ARG, "site fields are download-only");
     if (count == 0) return GL_OK;
@@ -384,8 +397,9 @@ static gl_status transfer(gl_ctx* c, gl_buffer which, double* host, size_t count
     if (which == GL_BUF_PARTICLES) {
         launch_parts_convert(c->prec, c->parts, c->np, stg, to_device, c->stream);
         if (to_device) sort_particles(c);
-    }
-    else launch_convert(c->prec, which, to_device, which == GL_BUF_SITE ? site_at(c, c->pstep - 1) : c->field[c->cur], stg, c->N, c->np,
+    } else if (which == GL_BUF_JETS) {
+        launch_jets_convert(c->prec, c->jets, c->n_jets, stg, to_device, c->stream);
+    } else launch_convert(c->prec, which, to_device, which == GL_BUF_SITE ? site_at(c, c->pstep - 1) : c->field[c->cur], stg, c->N, c->np,
                         c->stream);
     if (!to_device) cudaMemcpyAsync(host, stg, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (gl_status s = check_cuda(c, to_device ? "gl_upload" : "gl_download")) return s;
@@ -450,6 +464,7 @@ static gl_status push_once(gl_ctx* c, cudaStream_t st, void* bn1) {
     const double t = c->pstep * c->dt;
     if (c->np) launch_push(c->prec, site_at(c, c->pstep), bn1, c->parts, c->np, c->N, t, c->dt, active_mask(c, c->pstep),
                            c->spp, st, c->push_block);
+    if (c->n_jets) launch_jets_step(c->prec, site_at(c, c->pstep), bn1, c->jets, c->n_jets, c->N, t, c->dt, st);
     c->pstep++;
     if (c->sort_ok && c->pstep % c->cfg.sort_every == 0) {
         launch_sort(c->prec, c->parts, c->parts_alt, c->np, c->N, c->sort_scratch, st);
@@ -627,6 +642,20 @@ static gl_status observables_read(gl_ctx* c, uint32_t what, gl_obs* o) {
 }
 
 gl_status observables(gl_ctx* c, gl_obs* o) { return gl_observables_ex(c, GL_OBS_ALL, o); }
+
+gl_status gl_jets_observables(gl_ctx* c, double* out3) {
+    if (!c || !out3) return GL_ERR_ARG;
+    if (!c->n_jets) return fail(c, GL_ERR_STATE, "the context has no jet-correlator probes");
+    double* dout = c->jet_partials + 1024 * 3;
+    launch_jets_obs(c->prec, c->jets, c->n_jets, c->jet_partials, dout, c->stream);
+    double h[3];
+    cudaMemcpyAsync(h, dout, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    if (gl_status s = check_cuda(c, "gl_jets_observables")) return s;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, "gl_jets_observables sync");
+    const double u2 = 1.0 / (c->aG * c->aG);  // lattice momentum^2 -> GeV^2
+    for (int i = 0; i < 3; i++) out3[i] = h[i] * u2;
+    return GL_OK;
+}
 
 gl_status gl_observables_ex(gl_ctx* c, uint32_t what, gl_obs* o) {
     if (!c || !o || (what & ~GL_OBS_ALL)) return GL_ERR_ARG;

@@ -8,9 +8,13 @@
 
 namespace gl {
 
+// how a species moves: Wong particles of finite mass, infinitely massive
+// static quarks (Sec. 5.1), eikonal light-like partons along +x (Sec. 5.2)
+enum { MOTION_WONG = 0, MOTION_STATIC = 1, MOTION_EIKONAL = 2 };
+
 struct SpeciesParams {
     double mass[GL_MAX_SPECIES];   // lattice units; INFINITY = static
-    int is_static[GL_MAX_SPECIES];
+    int motion[GL_MAX_SPECIES];
     int n_species;
 };
 
@@ -55,6 +59,18 @@ struct ObsEvent {
 void launch_field_obs(int prec, const void* b, const void* site, int N, double* partials, int max_blocks,
                       double* out, cudaStream_t st);
 
+// light-like jet-correlator probes (Sec. 5.2), [n][JET_LEN] in the state's
+// precision: x0, y0, W (18), X_x, X_y, X_z (8 each)
+static constexpr int JET_LEN = 44;
+void launch_jets_init(int prec, void* jets, int64_t n, int N, uint64_t seed, cudaStream_t st);
+// one step of every probe from t_n = t: site fields at t_n, links at t_{n+1} (bn1)
+void launch_jets_step(int prec, const void* site, const void* bn1, void* jets, int64_t n, int N, double t,
+                      double dt, cudaStream_t st);
+// out[3] = mean over probes of X_i . X_i (FP64, fixed order); partials: 1024 x 3 doubles
+void launch_jets_obs(int prec, const void* jets, int64_t n, double* partials, double* out, cudaStream_t st);
+// canonical FP64 <-> device probes
+void launch_jets_convert(int prec, void* jets, int64_t n, double* stg, int to_device, cudaStream_t st);
+
 // counting sort of the particles by cell from src into dst (same layout)
 void launch_sort(int prec, void* src, void* dst, int64_t np, int N, void* scratch, cudaStream_t st);
 // one event of a batched sort; pblk_begin / cblk_begin: its first block in the
@@ -93,7 +109,7 @@ struct CtxView {
     int64_t step, pstep, np;
     double dt;
     double mass[GL_MAX_SPECIES];
-    int is_static[GL_MAX_SPECIES];
+    int motion[GL_MAX_SPECIES];
     double t_form[GL_MAX_SPECIES];
     int ns;
     int reunit_count;

@@ -38,11 +38,11 @@ struct ObsArgs {
 
 __device__ __forceinline__ bool po_is_max(int k) { return k == PO_Q2 || k == PO_Q3; }
 
-// p_L = p^tau sinh(eta) + w cosh(eta) with w = P_eta / t (static quarks: the
-// accumulated P_eta slot), in the precision of the state
+// p_L = p^tau sinh(eta) + w cosh(eta) with w = P_eta / t (static quarks and
+// eikonal partons: the accumulated P_eta slot), in the precision of the state
 template <typename R>
-__device__ __forceinline__ R particle_pl(const PState<R>& p, R t, R mass, bool is_static) {
-    if (is_static) return p.Pe;
+__device__ __forceinline__ R particle_pl(const PState<R>& p, R t, R mass, bool accumulated) {
+    if (accumulated) return p.Pe;
     const R w = t > R(0) ? p.Pe / t : R(0);
     const R ptau = sqrt(p.px * p.px + p.py * p.py + w * w + mass * mass);
     return ptau * sinh(p.eta) + w * cosh(p.eta);
@@ -67,7 +67,7 @@ __device__ __forceinline__ void particle_obs_block(const Parts<R>& P, double t, 
         }
         if (s >= 0) {
             const PState<R> p = P.load(i);
-            const R pl = particle_pl<R>(p, (R)t, (R)oa.sp.mass[s], oa.sp.is_static[s] != 0);
+            const R pl = particle_pl<R>(p, (R)t, (R)oa.sp.mass[s], oa.sp.motion[s] != MOTION_WONG);
             const double px = p.px, py = p.py;
             v[PO_COUNT] = 1.0;
             v[PO_PX2] = px * px;

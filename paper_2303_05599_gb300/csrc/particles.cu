@@ -137,8 +137,8 @@ static void push_t(const void* site, const void* bn1, void* parts, int64_t np, i
     const int64_t Vn = (int64_t)N * N;
     SpeciesArgs<R> sa;
     for (int k = 0; k < GL_MAX_SPECIES; k++) {
-        sa.mass[k] = (R)(k < sp.n_species && !sp.is_static[k] ? sp.mass[k] : 0.0);
-        sa.is_static[k] = k < sp.n_species ? sp.is_static[k] : 0;
+        sa.mass[k] = (R)(k < sp.n_species && sp.motion[k] == MOTION_WONG ? sp.mass[k] : 0.0);
+        sa.motion[k] = k < sp.n_species ? sp.motion[k] : MOTION_WONG;
     }
     const int threads = block == 64 || block == 256 ? block : 128;
     int64_t blocks = (np + threads - 1) / threads;
@@ -217,6 +217,7 @@ __global__ void sample_kernel(Parts<R> P, int N, uint32_t k0, uint32_t k1, Sampl
         const double pt = sa.mode[s] == 1 ? sa.p0[s] + (sa.p1[s] - sa.p0[s]) * u01(w.w) : sa.p0[s];
         double px = pt * cos(psi), py = pt * sin(psi);
         if (sa.mode[s] == 2) { px = sa.p0[s]; py = 0.0; }
+        if (sa.mode[s] == 3) { px = 0.0; py = 0.0; }  // eikonal: only the kicks are recorded
         double g[20];
         for (int j = 0; j < 5; j++) {
             U4 v = philox4x32_10(U4{idx, (uint32_t)s, 3u, (uint32_t)j}, k0, k1);

@@ -7,7 +7,7 @@ namespace gl {
 template <typename R>
 struct SpeciesArgs {
     R mass[GL_MAX_SPECIES];
-    int is_static[GL_MAX_SPECIES];
+    int motion[GL_MAX_SPECIES];  // MOTION_*
 };
 
 template <typename R>
@@ -43,12 +43,31 @@ __device__ __forceinline__ void push_one(const typename Prec<R>::V* __restrict__
     const R qEx = a_dot(p.q, load_alg(site, cell, Vn));
     const R qEy = a_dot(p.q, load_alg(site + (size_t)1 * AP * Vn, cell, Vn));
     const R qEe = a_dot(p.q, load_alg(site + (size_t)2 * AP * Vn, cell, Vn));
-    if (sa.is_static[s]) {
+    if (sa.motion[s] == MOTION_STATIC) {
         // infinitely massive: no motion and no colour rotation (temporal gauge)
         p.px += dt * qEx;
         p.py += dt * qEy;
         p.Pe += dt * qEe;
         P.store_momenta(i, p);
+        return;
+    }
+    if (sa.motion[s] == MOTION_EIKONAL) {
+        // light-like parton along +x at eta = 0 (Sec. 5.2): fixed path
+        // x = x0 + t; the kicks of the Lorentz force (E_x, E_y - B_z, E_z + B_y)
+        // accumulate in p^x, p^y and the P_eta slot (lab p_z); Q is carried
+        // along by the crossed x link
+        const R qBy = a_dot(p.q, load_alg(site + (size_t)4 * AP * Vn, cell, Vn));
+        const R qBe = a_dot(p.q, load_alg(site + (size_t)5 * AP * Vn, cell, Vn));
+        p.px += dt * qEx;
+        p.py += dt * (qEy - qBe);
+        p.Pe += dt * (qEe + qBy);
+        R xn = p.x + dt;
+        const int jxu = (int)floor_r<R>(xn + R(0.5));
+        xn = fmod_r<R>(xn, (R)N);
+        if (xn < R(0)) xn += (R)N;
+        p.x = xn;
+        if (jxu != ixu) p.q = conj_dn(load_link(bn1.U, 0, cell, Vn), p.q);
+        P.store(i, p);
         return;
     }
     const R qBx = a_dot(p.q, load_alg(site + (size_t)3 * AP * Vn, cell, Vn));

@@ -19,6 +19,7 @@ M_BEAUTY = 4.18  # GeV (Sec. 7.1)
 MOM_FIXED_PT = 0     # |p_T| = p0, uniform azimuth
 MOM_UNIFORM_PT = 1   # |p_T| ~ U[p0, p1], uniform azimuth
 MOM_ALONG_X = 2      # p^x = p0, p^y = 0
+MOM_EIKONAL_X = 3    # eikonal light-like parton along +x: fixed path, momenta record the kicks
 
 REP_F = 0  # fundamental classical charge, q2 = 4, q3 = 10/3
 REP_A = 1  # adjoint classical charge, q2 = 24, q3 = 0
@@ -52,6 +53,7 @@ class Workload:
     precision: int = FP64
     reunit_every: int = 64
     sort_every: int = 16
+    n_jets: int = 0              # light-like jet-correlator probes (single events)
     seed: int = 0
     species: List[Species] = field(default_factory=list)
     report_every_fm: float = 0.0

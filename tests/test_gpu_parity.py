@@ -63,9 +63,11 @@ def oracle_particles(w):
     return np.concatenate(parts) if parts else np.zeros((0, 16))
 
 
-def oracle_run(w, st, part):
+def oracle_run(w, st, part, jets=None):
     ls = w.lattice_species()
-    return O.Run(st, part, [s[0] for s in ls], [s[1] for s in ls], [s.rep for s in w.species], w.dt)
+    kind = O.kinds_of([s[0] for s in ls], [s.mom_mode for s in w.species])
+    return O.Run(st, part, [s[0] for s in ls], [s[1] for s in ls], [s.rep for s in w.species], w.dt, kind=kind,
+                 jets=jets)
 
 
 MIXED = [W.Species(W.M_CHARM, 0.06, 120, W.REP_F, W.MOM_FIXED_PT, 0.5),
@@ -328,3 +330,85 @@ def test_call_order_errors():
     with pytest.raises(B.GlasmaError) as e:
         ev.upload(B.GL_BUF_LINKS, np.zeros(10))
     assert e.value.status == B.GL_ERR_SIZE
+
+
+# ------------------------------------------------------------------ light-like jets
+JET_SPECIES = [W.Species(0.0, 0.0, 64, W.REP_F, W.MOM_EIKONAL_X, 0.0),
+               W.Species(W.M_CHARM, 0.0, 32, W.REP_A, W.MOM_FIXED_PT, 0.5)]
+
+
+@pytest.mark.parametrize("prec,tol", [(W.FP64, FP64_TOL), (W.FP32_2ROW, 2e-4)])
+def test_jets_and_eikonal_parity(prec, tol):
+    """Light-like jet-correlator probes and eikonal partons (Sec. 5.2) against
+    the oracle: probe Wilson lines and force integrals, the partons' kicks and
+    charges, and the charge-averaged broadening through the C ABI."""
+    w = wl(24, prec=prec, species=JET_SPECIES, seed=5)
+    w.n_jets = 50
+    st = oracle_init(w)
+    part = oracle_particles(w)
+    jets = O.jets_init(w.N, w.seed, w.n_jets)
+    ev = B.Event(w)
+    upload_state(ev, st)
+    ev.upload(B.GL_BUF_PARTICLES, part)
+    ev.upload(B.GL_BUF_JETS, jets)
+    run = oracle_run(w, st, part, jets=jets.copy())
+    steps = 40
+    for _ in range(steps):
+        run.step()
+    ev.step(steps)
+    gj = ev.download(B.GL_BUF_JETS)
+    assert rel(gj[:, :2], run.jets[:, :2]) < tol
+    assert rel(gj[:, 2:20], run.jets[:, 2:20]) < tol       # Wilson lines
+    assert rel(gj[:, 20:44], run.jets[:, 20:44]) < tol     # force integrals
+    gp = ev.download(B.GL_BUF_PARTICLES)
+    eik = gp[:, 15] == 0
+    for sl in (slice(0, 3), slice(3, 6), slice(6, 14)):
+        assert rel(gp[eik, sl], run.part[eik, sl]) < tol
+    a2 = w.a_GeVinv ** 2
+    got = np.array(ev.jets_observables()) * a2
+    want = O.jets_obs(run.jets)
+    assert np.abs(got - want).max() <= tol * np.abs(want).max()
+    o = ev.observables()
+    want_o = run.observables()
+    assert abs(o.sum_pL2[0] * a2 - want_o[0, 3]) <= tol * abs(want_o[0, 3])
+
+
+def test_eikonal_kicks_equal_probe_integrals_on_gpu():
+    """Eikonal partons and probes started on the same paths: the partons'
+    kicks are Q0 . X_i of the probes (charge rotated vs force transported), and
+    the GPU's own probe initialisation equals the oracle's Philox positions."""
+    w = wl(24, prec=W.FP64, species=JET_SPECIES[:1], seed=8)
+    w.n_jets = 64
+    ev = B.Event(w)
+    ev.glasma_init()
+    ev.wong_init()
+    gj0 = ev.download(B.GL_BUF_JETS)
+    assert np.array_equal(gj0[:, :2], O.jets_init(w.N, w.seed, w.n_jets)[:, :2])
+    part = ev.download(B.GL_BUF_PARTICLES)
+    probes = np.zeros((len(part), B.JET_LEN))
+    probes[:, :2] = part[:, :2]
+    for i in range(3):
+        probes[:, 2 + 2 * (3 * i + i)] = 1.0
+    w2 = wl(24, prec=W.FP64, species=JET_SPECIES[:1], seed=8)
+    w2.n_jets = len(part)
+    ev2 = B.Event(w2)
+    for which in (B.GL_BUF_LINKS, B.GL_BUF_PHI, B.GL_BUF_E, B.GL_BUF_PI, B.GL_BUF_PARTICLES):
+        ev2.upload(which, ev.download(which))
+    ev2.upload(B.GL_BUF_JETS, probes)
+    ev2.step(30)
+    gp = ev2.download(B.GL_BUF_PARTICLES)
+    X = ev2.download(B.GL_BUF_JETS)[:, 20:44].reshape(-1, 3, 8)
+    kick = np.einsum("na,nia->ni", part[:, 6:14], X)
+    assert np.abs(gp[:, 3:6] - kick).max() < 1e-12 * np.abs(kick).max()
+
+
+def test_jets_need_a_single_event():
+    w = wl(16, prec=W.FP32_2ROW, species=JET_SPECIES[:1])
+    w.n_jets = 4
+    with pytest.raises(B.GlasmaError):
+        B.Batch([w])
+    w.n_jets = 0
+    ev = B.Event(w)
+    with pytest.raises(B.GlasmaError) as e:
+        ev.jets_observables()
+    assert e.value.status == B.GL_ERR_STATE
