@@ -39,6 +39,12 @@
  *   GL_BUF_JETS       [n_jets][44]  light-like jet-correlator probes: x0, y0,
  *                                   W (3x3 complex, row-major re/im), X_x, X_y,
  *                                   X_z (8 components each), see gl_config
+ *   GL_BUF_ENERGY     [N*N]         energy density of the Glasma fields at the
+ *                                   last pushed time t_{n-1} (Figs. 6 and 9
+ *                                   background): tr(E_x^2 + E_y^2 + E_eta^2 +
+ *                                   B_x^2 + B_y^2 + B_eta^2) of the site fields,
+ *                                   lattice units; the physical value is this
+ *                                   / (g^2 a^4) (download only)
  */
 #ifndef GLASMA_H
 #define GLASMA_H
@@ -72,7 +78,8 @@ typedef enum {
     GL_BUF_PI = 3,
     GL_BUF_SITE = 4,
     GL_BUF_PARTICLES = 5,
-    GL_BUF_JETS = 6
+    GL_BUF_JETS = 6,
+    GL_BUF_ENERGY = 7
 } gl_buffer;
 
 /* One MV event (Sec. 2, parameters of Sec. 7.1). */

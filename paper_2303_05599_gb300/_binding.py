@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libglasma_gb300.so")
 GL_MAX_SPECIES = 8
 GL_OK, GL_ERR_ARG, GL_ERR_CUDA, GL_ERR_STATE, GL_ERR_TIMEOUT, GL_ERR_NUMERIC, GL_ERR_SIZE = range(7)
 GL_FP64, GL_FP32_2ROW = 0, 1
-GL_BUF_LINKS, GL_BUF_PHI, GL_BUF_E, GL_BUF_PI, GL_BUF_SITE, GL_BUF_PARTICLES, GL_BUF_JETS = range(7)
+GL_BUF_LINKS, GL_BUF_PHI, GL_BUF_E, GL_BUF_PI, GL_BUF_SITE, GL_BUF_PARTICLES, GL_BUF_JETS, GL_BUF_ENERGY = range(8)
 JET_LEN = 44
 
 STATUS_NAMES = {0: "GL_OK", 1: "GL_ERR_ARG", 2: "GL_ERR_CUDA", 3: "GL_ERR_STATE", 4: "GL_ERR_TIMEOUT",
@@ -244,7 +244,7 @@ class Event:
         V = self.N * self.N
         return {GL_BUF_LINKS: (2, V, 18), GL_BUF_PHI: (V, 8), GL_BUF_E: (2, V, 8), GL_BUF_PI: (V, 8),
                 GL_BUF_SITE: (6, V, 8), GL_BUF_PARTICLES: (self.np, 16),
-                GL_BUF_JETS: (self.n_jets, JET_LEN)}[which]
+                GL_BUF_JETS: (self.n_jets, JET_LEN), GL_BUF_ENERGY: (V,)}[which]
 
     def jets_observables(self):
         """Mean over the jet-correlator probes of X_i . X_i (i = x, y, z), GeV^2."""

@@ -382,15 +382,17 @@ static size_t expected_count(const gl_ctx* c, gl_buffer which) {
         case GL_BUF_SITE: return (size_t)6 * c->Vn * 8;
         case GL_BUF_PARTICLES: return (size_t)c->np * 16;
         case GL_BUF_JETS: return (size_t)c->n_jets * JET_LEN;
+        case GL_BUF_ENERGY: return (size_t)c->Vn;
     }
     return 0;
 }
 
 static gl_status transfer(gl_ctx* c, gl_buffer which, double* host, size_t count, int to_device) {
     if (!c || (!host && count)) return GL_ERR_ARG;
-    if ((int)which < 0 || (int)which > GL_BUF_JETS) return fail(c, GL_ERR_ARG, "unknown buffer");
+    if ((int)which < 0 || (int)which > GL_BUF_ENERGY) return fail(c, GL_ERR_ARG, "unknown buffer");
     if (count != expected_count(c, which)) return fail(c, GL_ERR_SIZE, "host buffer size does not match");
-    if (to_device && which == GL_BUF_SITE) return fail(c, GL_ERR_ARG, "site fields are download-only");
+    if (to_device && (which == GL_BUF_SITE || which == GL_BUF_ENERGY))
+        return fail(c, GL_ERR_ARG, "site fields and energy density are download-only");
     if (count == 0) return GL_OK;
     double* stg = (double*)c->scratch;
     if (to_device) cudaMemcpyAsync(stg, host, count * sizeof(double), cudaMemcpyHostToDevice, c->stream);
@@ -399,6 +401,8 @@ static gl_status transfer(gl_ctx* c, gl_buffer which, double* host, size_t count
         if (to_device) sort_particles(c);
     } else if (which == GL_BUF_JETS) {
         launch_jets_convert(c->prec, c->jets, c->n_jets, stg, to_device, c->stream);
+    } else if (which == GL_BUF_ENERGY) {
+        launch_energy(c->prec, site_at(c, c->pstep - 1), c->N, stg, c->stream);
     } else launch_convert(c->prec, which, to_device, which == GL_BUF_SITE ? site_at(c, c->pstep - 1) : c->field[c->cur], stg, c->N, c->np,
                         c->stream);
     if (!to_device) cudaMemcpyAsync(host, stg, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream);

@@ -58,6 +58,8 @@ struct ObsEvent {
 };
 void launch_field_obs(int prec, const void* b, const void* site, int N, double* partials, int max_blocks,
                       double* out, cudaStream_t st);
+// energy density per site, tr of the squared site fields (FP64 out[N*N])
+void launch_energy(int prec, const void* site, int N, double* out, cudaStream_t st);
 
 // light-like jet-correlator probes (Sec. 5.2), [n][JET_LEN] in the state's
 // precision: x0, y0, W (18), X_x, X_y, X_z (8 each)

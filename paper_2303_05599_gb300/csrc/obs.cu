@@ -174,6 +174,29 @@ __global__ void convert_kernel(int which, int to_dev, Fields<R> f, typename Prec
     }
 }
 
+// energy density per site: sum over the six site fields of tr X^2 = X^a X^a / 2
+template <typename R>
+__global__ void energy_kernel(const typename Prec<R>::V* __restrict__ site, int N, double* out) {
+    constexpr int AP = Prec<R>::AP;
+    const int64_t Vn = (int64_t)N * N;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < Vn; s += (int64_t)gridDim.x * blockDim.x) {
+        double e = 0.0;
+        for (int k = 0; k < 6; k++) {
+            const A8<double> X = to_d(load_alg(site + (size_t)k * AP * Vn, s, Vn));
+            e += 0.5 * a_dot(X, X);
+        }
+        out[s] = e;
+    }
+}
+
+void launch_energy(int prec, const void* site, int N, double* out, cudaStream_t st) {
+    const int64_t Vn = (int64_t)N * N;
+    int64_t blocks = (Vn + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (prec == 0) energy_kernel<double><<<(unsigned)blocks, 256, 0, st>>>((const double2*)site, N, out);
+    else energy_kernel<float><<<(unsigned)blocks, 256, 0, st>>>((const float4*)site, N, out);
+}
+
 void launch_convert(int prec, int which, int to_device, void* dev, double* staging, int N, int64_t np,
                     cudaStream_t st) {
     (void)np;

@@ -412,3 +412,18 @@ def test_jets_need_a_single_event():
     with pytest.raises(B.GlasmaError) as e:
         ev.jets_observables()
     assert e.value.status == B.GL_ERR_STATE
+
+
+def test_energy_density_download():
+    """GL_BUF_ENERGY: tr of the squared site fields per site at the last pushed
+    time, against the oracle's site fields, and its lattice mean against the
+    FP64 field means of the observables."""
+    w, ev, run = _coupled(16, W.FP64, 12)
+    e = ev.download(B.GL_BUF_ENERGY)
+    want = 0.5 * (run.site ** 2).sum(axis=(0, 2))
+    assert rel(e, want) < FP64_TOL
+    o = ev.observables()
+    mean = o.mean_trE_T2 + o.mean_trE_L2 + o.mean_trB_T2 + o.mean_trB_L2
+    assert abs(e.mean() - mean) <= 1e-12 * abs(mean)
+    with pytest.raises(B.GlasmaError):
+        ev.upload(B.GL_BUF_ENERGY, e)
