@@ -221,10 +221,11 @@ def events_for(args, rank):
         for w in evs:
             w.seed = w.seed + 64 * rank
         return evs
-    n = args.events if args.events else (1 if args.workload == "n1024_mixed" else 30)
+    n = args.events if args.events else (1 if W.WORKLOADS[args.workload]().N >= 1024 else 30)
     evs = []
     for e in range(n):
         w = W.WORKLOADS[args.workload]()
+        w.n_jets = 0  # jet-correlator probes run on the single-event API only
         if args.reunit_every is not None:
             w.reunit_every = args.reunit_every
         if args.precision == "fp64":
@@ -383,7 +384,8 @@ def run_ours(args):
                                      "sums of every event read back to the host); one full report with the FP64 "
                                      "field checks at the end",
                          "gauss_max_final": max(o.gauss_max for o in final)}, **e2e_parts),
-            "gpu_launches": 3 * K,
+            "gpu_launches": 3 * K + 8 * sum(1 for s_ in range(pre + 1, pre + K + 1)
+                                            if ws[0].sort_every > 0 and s_ % ws[0].sort_every == 0),
             "clocks": ck,
         }
         if world == 1 and not args.no_cpu_baseline:

@@ -144,9 +144,21 @@ def config_n1024(precision=FP32_2ROW):
                              Species(0.0, 0.0, c[2], REP_F, MOM_FIXED_PT, 10.0)])
 
 
+def config_jets_dt16(precision=FP32_2ROW):
+    """The paper's jet setup (Sec. 7.1): 1024x1024, L = 10 fm, dtau = a/16, to
+    tau = 1 fm/c; quark jets with m = 1 GeV and p^x = 10 GeV (Sec. 7.3), eikonal
+    light-like partons along +x (the limit they approach) and jet-correlator
+    probes on the same kind of paths (single event)."""
+    return Workload("jets_n1024_dt16", N=1024, L_fm=10.0, precision=precision, seed=0, dtau_over_a=1.0 / 16,
+                    n_jets=100_000,
+                    species=[Species(1.0, 0.0, 100_000, REP_F, MOM_ALONG_X, 10.0),
+                             Species(0.0, 0.0, 100_000, REP_F, MOM_EIKONAL_X, 0.0)])
+
+
 WORKLOADS = {
     "small_N32_fp64": config_small,
     "n256_charm_static": config_n256,
     "n512_beauty_jets": config_n512,
     "n1024_mixed": config_n1024,
+    "jets_n1024_dt16": config_jets_dt16,
 }

@@ -427,3 +427,31 @@ def test_energy_density_download():
     assert abs(e.mean() - mean) <= 1e-12 * abs(mean)
     with pytest.raises(B.GlasmaError):
         ev.upload(B.GL_BUF_ENERGY, e)
+
+
+def test_half_time_step_jets_parity():
+    """dtau = a/16, the paper's time step for jets (Sec. 7.1): quark jets
+    (m = 1 GeV, p^x = 10 GeV), eikonal partons and correlator probes through
+    the coupled step, FP64 against the oracle."""
+    species = [W.Species(1.0, 0.0, 40, W.REP_F, W.MOM_ALONG_X, 10.0),
+               W.Species(0.0, 0.0, 40, W.REP_A, W.MOM_EIKONAL_X, 0.0)]
+    w = wl(20, prec=W.FP64, species=species, seed=12)
+    w.dtau_over_a = 1.0 / 16
+    w.n_jets = 30
+    st = oracle_init(w)
+    part = oracle_particles(w)
+    jets = O.jets_init(w.N, w.seed, w.n_jets)
+    ev = B.Event(w)
+    upload_state(ev, st)
+    ev.upload(B.GL_BUF_PARTICLES, part)
+    ev.upload(B.GL_BUF_JETS, jets)
+    run = oracle_run(w, st, part, jets=jets.copy())
+    for _ in range(48):
+        run.step()
+    ev.step(48)
+    gp = ev.download(B.GL_BUF_PARTICLES)
+    for sl in (slice(0, 2), slice(3, 6), slice(6, 14)):
+        assert rel(gp[:, sl], run.part[:, sl]) < FP64_TOL
+    assert rel(ev.download(B.GL_BUF_JETS), run.jets) < FP64_TOL
+    g = download_state(ev)
+    assert rel(g.U, run.st.U) < FP64_TOL and rel(g.e, run.st.e) < FP64_TOL
