@@ -58,9 +58,7 @@ BATCHED = "batched64"
 # keyed by (workload, events per GPU, kernel, precision), captured on the full
 # workload for the current kernels (profiles/launches_default_30x256.md).
 # Absent: not captured for the current kernels.
-TRAFFIC = {
-    ("n256_charm_static", 30, "field_step", 1): 440824832 + 759966720,
-}
+TRAFFIC = {}
 
 
 def field_bytes_per_site(prec):

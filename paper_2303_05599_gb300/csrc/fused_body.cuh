@@ -50,7 +50,10 @@ struct Tile {
     static_assert(NH <= NT, "halo momenta are one per thread");
     // vectors: links 2 LP LN, phi AP LN, A AP EN, e sums 2 AP EN, Lf AP EN
     static constexpr size_t vecs = (size_t)2 * LP * LN + (size_t)AP * LN + (size_t)4 * AP * EN;
-    static constexpr size_t bytes = vecs * sizeof(V);
+    // FP32 two-row links: the third rows, rebuilt once per staged link,
+    // [2][3][LN] float2 after the vectors
+    static constexpr size_t row2_bytes = sizeof(R) == 4 ? (size_t)2 * 3 * LN * 8 : 0;
+    static constexpr size_t bytes = vecs * sizeof(V) + row2_bytes;
     // CTAs per SM the launch bounds ask for: FP32 kernels are capped at 128
     // registers a thread so that 16 warps fit an SM (the shared memory of
     // 32x4: 4 CTAs, 32x8: 2, 32x16: 1); FP64 tiles take one CTA
@@ -90,6 +93,36 @@ __device__ __forceinline__ M3<float> s_link(const float4* sU, int d, int li, int
     rebuild_row2(m);
     return m;
 }
+
+// links of the tile in shared memory; FP32 links come with their third rows
+// stored beside them (rebuilt once when staged)
+template <typename R>
+struct SLinks;
+template <>
+struct SLinks<double> {
+    const double2* u;
+    int LN;
+    __device__ __forceinline__ M3<double> operator()(int d, int li) const { return s_link(u, d, li, LN); }
+};
+template <>
+struct SLinks<float> {
+    const float4* u;
+    const float2* r2;
+    int LN;
+    __device__ __forceinline__ M3<float> operator()(int d, int li) const {
+        const float4* b = u + (size_t)d * 3 * LN + li;
+        const float4 a = b[0], c = b[LN], e = b[2 * LN];
+        const float2* t = r2 + (size_t)d * 3 * LN + li;
+        const float2 f0 = t[0], f1 = t[LN], f2 = t[2 * LN];
+        M3<float> m;
+        m.re[0][0] = a.x; m.im[0][0] = a.y; m.re[0][1] = a.z; m.im[0][1] = a.w;
+        m.re[0][2] = c.x; m.im[0][2] = c.y; m.re[1][0] = c.z; m.im[1][0] = c.w;
+        m.re[1][1] = e.x; m.im[1][1] = e.y; m.re[1][2] = e.z; m.im[1][2] = e.w;
+        m.re[2][0] = f0.x; m.im[2][0] = f0.y; m.re[2][1] = f1.x; m.im[2][1] = f1.y;
+        m.re[2][2] = f2.x; m.im[2][2] = f2.y;
+        return m;
+    }
+};
 
 __device__ __forceinline__ A8<double> s_alg(const double2* s, int i, int n) {
     A8<double> x;
@@ -197,6 +230,10 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
     Vec* sA = sPhi + AP * LN;          // [AP][EN]
     Vec* sEs = sA + AP * EN;           // [2][AP][EN]: e(n-1/2), then e(n-1/2) + e(n+1/2)
     Vec* sLf = sEs + 2 * AP * EN;      // [AP][EN]
+    float2* sU2 = (float2*)(smem_raw + T::vecs * sizeof(Vec));  // FP32: [2][3][LN] third rows
+    SLinks<R> lk;
+    if constexpr (sizeof(R) == 4) lk = SLinks<R>{(const float4*)sU, sU2, LN};
+    else lk = SLinks<R>{(const double2*)sU, LN};
 
     const int N = a.N;
     const int64_t Vn = (int64_t)N * N;
@@ -230,13 +267,25 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
     }
     cp_async_commit();
     cp_async_wait_group<1>();
+    if constexpr (sizeof(R) == 4) {
+        // third rows of the links this thread copied (its own copies are
+        // complete after the wait), once per staged link
+        for (int i = tid; i < LN; i += NT)
+#pragma unroll
+            for (int d = 0; d < 2; d++) {
+                const M3<float> m = s_link((const float4*)sU, d, i, LN);
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    sU2[(size_t)(d * 3 + k) * LN + i] = make_float2(m.re[2][k], m.im[2][k]);
+            }
+    }
     __syncthreads();
 
     // ---- phase 2: plaquettes of the cells x in [-1, TX-1], y in [-1, TY-1]
     for (int i = tid; i < EN; i += NT) {
         const int l = (i / EW) * LW + (i % EW);  // cell (i % EW - 1, i / EW - 1)
-        const M3<R> C = mul(s_link(sU, 0, l, LN), s_link(sU, 1, l + 1, LN));
-        s_alg_put(sA, i, EN, iah_of_mul_nd(mul_nd(C, s_link(sU, 0, l + LW, LN)), s_link(sU, 1, l, LN)));
+        const M3<R> C = mul(lk(0, l), lk(1, l + 1));
+        s_alg_put(sA, i, EN, iah_of_mul_nd(mul_nd(C, lk(0, l + LW)), lk(1, l)));
     }
     cp_async_wait_group<0>();
     __syncthreads();
@@ -270,8 +319,8 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
         const A8<R> A0 = s_alg(sA, e, EN);
         const A8<R> ph = s_alg(sPhi, l, LN);
         if (wx) {
-            const A8<R> Dn = conj_dn(s_link(sU, 1, l - LW, LN), s_alg(sA, e - EW, EN));
-            const A8<R> tx = conj_up(s_link(sU, 0, l, LN), s_alg(sPhi, l + 1, LN));
+            const A8<R> Dn = conj_dn(lk(1, l - LW), s_alg(sA, e - EW, EN));
+            const A8<R> tx = conj_up(lk(0, l), s_alg(sPhi, l + 1, LN));
             const A8<R> cx = icomm(tx, ph);
             const A8<R> eox = s_alg(sEs, e, EN);
             A8<R> ex_n, sx;
@@ -289,8 +338,8 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
             }
         }
         if (wy) {
-            const A8<R> Lf = conj_dn(s_link(sU, 0, l - 1, LN), s_alg(sA, e - 1, EN));
-            const A8<R> ty = conj_up(s_link(sU, 1, l, LN), s_alg(sPhi, l + LW, LN));
+            const A8<R> Lf = conj_dn(lk(0, l - 1), s_alg(sA, e - 1, EN));
+            const A8<R> ty = conj_up(lk(1, l), s_alg(sPhi, l + LW, LN));
             const A8<R> cy = icomm(ty, ph);
             const A8<R> eoy = s_alg(sEs + AP * EN, e, EN);
             A8<R> ey_n, sy;
@@ -317,8 +366,8 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
     if (valid) {
         const A8<R> p_old = load_alg(in.pi, g, Vn);
         const A8<R> ph = s_alg(sPhi, ls, LN);
-        const M3<R> Ux_m = s_link(sU, 0, ls - 1, LN);
-        const M3<R> Uy_m = s_link(sU, 1, ls - LW, LN);
+        const M3<R> Ux_m = lk(0, ls - 1);
+        const M3<R> Uy_m = lk(1, ls - LW);
         const A8<R> bx = conj_dn(Ux_m, s_alg(sPhi, ls - 1, LN));
         const A8<R> by = conj_dn(Uy_m, s_alg(sPhi, ls - LW, LN));
         A8<R> p_new, ph_new;
@@ -356,10 +405,10 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
         store_alg(out.e + (size_t)AP * Vn, g, Vn, my_ey);
         store_alg(out.pi, g, Vn, p_new);
         store_alg(out.phi, g, Vn, ph_new);
-        M3<R> nx = mul(exp_i_alg<R, ExpN<R>::n>(my_ex, a.dt_over_th), s_link(sU, 0, ls, LN));
+        M3<R> nx = mul(exp_i_alg<R, ExpN<R>::n>(my_ex, a.dt_over_th), lk(0, ls));
         if (a.reunit) reunit(nx);
         store_link(out.U, 0, g, Vn, nx);
-        M3<R> ny = mul(exp_i_alg<R, ExpN<R>::n>(my_ey, a.dt_over_th), s_link(sU, 1, ls, LN));
+        M3<R> ny = mul(exp_i_alg<R, ExpN<R>::n>(my_ey, a.dt_over_th), lk(1, ls));
         if (a.reunit) reunit(ny);
         store_link(out.U, 1, g, Vn, ny);
     }
