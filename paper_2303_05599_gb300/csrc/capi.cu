@@ -423,6 +423,9 @@ gl_status gl_set_step(gl_ctx* c, int64_t step) {
     if (!c || step < 0) return GL_ERR_ARG;
     c->step = c->pstep = step;
     c->site_step = -1;
+    // the re-unitarisation period counts from step 0, so a resumed run
+    // re-unitarises at the same steps as an uninterrupted one
+    if (c->prec == GL_FP32_2ROW && c->cfg.reunit_every > 0) c->reunit_count = (int)(step % c->cfg.reunit_every);
     return GL_OK;
 }
 

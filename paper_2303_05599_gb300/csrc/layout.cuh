@@ -147,6 +147,10 @@ __device__ __forceinline__ A8<R> icomm(const A8<R>& A, const A8<R>& B) {
     return o;
 }
 
+// maximum that propagates NaN (fmax drops it), so that a non-finite value
+// anywhere shows in the reported maxima
+__device__ __forceinline__ double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
+
 __device__ __forceinline__ int wrapi(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;

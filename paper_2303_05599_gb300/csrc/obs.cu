@@ -55,10 +55,10 @@ __global__ void __launch_bounds__(256) field_obs_kernel(Fields<R> f, const typen
                     const double r = gr - (i == j ? 1.0 : 0.0);
                     n2 += (i == j ? 1.0 : 2.0) * (r * r + gi * gi);
                 }
-            v[FO_UMAX] = fmax(v[FO_UMAX], sqrt(n2));
+            v[FO_UMAX] = nanmax(v[FO_UMAX], sqrt(n2));
         }
         const double g2 = a_dot(G, G);
-        v[FO_GMAX] = fmax(v[FO_GMAX], sqrt(g2));
+        v[FO_GMAX] = nanmax(v[FO_GMAX], sqrt(g2));
         v[FO_GSUM] += g2;
         // tr X^2 = X^a X^a / 2
         double tr[6];
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) field_obs_kernel(Fields<R> f, const typen
     for (int o = 16; o > 0; o >>= 1)
         for (int k = 0; k < FO_N; k++) {
             const double oth = __shfl_down_sync(0xffffffffu, v[k], o);
-            v[k] = (k == FO_GMAX || k == FO_UMAX) ? fmax(v[k], oth) : v[k] + oth;
+            v[k] = (k == FO_GMAX || k == FO_UMAX) ? nanmax(v[k], oth) : v[k] + oth;
         }
     if (lane == 0)
         for (int k = 0; k < FO_N; k++) wacc[warp][k] = v[k];
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) field_obs_kernel(Fields<R> f, const typen
         const int k = threadIdx.x;
         double a = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++)
-            a = (k == FO_GMAX || k == FO_UMAX) ? fmax(a, wacc[w][k]) : a + wacc[w][k];
+            a = (k == FO_GMAX || k == FO_UMAX) ? nanmax(a, wacc[w][k]) : a + wacc[w][k];
         partials[(size_t)blockIdx.x * FO_N + k] = a;
     }
 }
@@ -96,12 +96,12 @@ __global__ void __launch_bounds__(256) field_obs_finalize(const double* partials
     double a = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
         const double v = partials[(size_t)b * FO_N + k];
-        a = mx ? fmax(a, v) : a + v;
+        a = mx ? nanmax(a, v) : a + v;
     }
     red[threadIdx.x] = a;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] = mx ? fmax(red[threadIdx.x], red[threadIdx.x + o]) : red[threadIdx.x] + red[threadIdx.x + o];
+        if (threadIdx.x < o) red[threadIdx.x] = mx ? nanmax(red[threadIdx.x], red[threadIdx.x + o]) : red[threadIdx.x] + red[threadIdx.x + o];
         __syncthreads();
     }
     if (threadIdx.x == 0) out[k] = red[0];

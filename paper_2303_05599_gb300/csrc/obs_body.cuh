@@ -13,6 +13,7 @@
 // accumulation is FP64.
 #pragma once
 #include "internal.h"
+#include "layout.cuh"
 #include "parts.cuh"
 #include "su3.cuh"
 
@@ -88,19 +89,19 @@ __device__ __forceinline__ void particle_obs_block(const Parts<R>& P, double t, 
 #pragma unroll
                 for (int k = 0; k < PO_N; k++) {
                     const double oth = __shfl_down_sync(0xffffffffu, r[k], o);
-                    r[k] = po_is_max(k) ? fmax(r[k], oth) : r[k] + oth;
+                    r[k] = po_is_max(k) ? nanmax(r[k], oth) : r[k] + oth;
                 }
             if (lane == 0)
                 for (int k = 0; k < PO_N; k++) {
                     double* a = &wacc[warp][sp_ * PO_N + k];
-                    *a = po_is_max(k) ? fmax(*a, r[k]) : *a + r[k];
+                    *a = po_is_max(k) ? nanmax(*a, r[k]) : *a + r[k];
                 }
         }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < GL_MAX_SPECIES * PO_N; k += OBS_THREADS) {
         double a = 0.0;
-        for (int w = 0; w < OBS_THREADS / 32; w++) a = po_is_max(k % PO_N) ? fmax(a, wacc[w][k]) : a + wacc[w][k];
+        for (int w = 0; w < OBS_THREADS / 32; w++) a = po_is_max(k % PO_N) ? nanmax(a, wacc[w][k]) : a + wacc[w][k];
         out[k] = a;
     }
 }
@@ -114,12 +115,12 @@ __device__ __forceinline__ void particle_obs_reduce(const double* partials, int 
     double a = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
         const double v = partials[(size_t)b * width + k];
-        a = mx ? fmax(a, v) : a + v;
+        a = mx ? nanmax(a, v) : a + v;
     }
     red[threadIdx.x] = a;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] = mx ? fmax(red[threadIdx.x], red[threadIdx.x + o]) : red[threadIdx.x] + red[threadIdx.x + o];
+        if (threadIdx.x < o) red[threadIdx.x] = mx ? nanmax(red[threadIdx.x], red[threadIdx.x + o]) : red[threadIdx.x] + red[threadIdx.x + o];
         __syncthreads();
     }
     if (threadIdx.x == 0) out[k] = red[0];
