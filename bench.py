@@ -58,7 +58,10 @@ BATCHED = "batched64"
 # keyed by (workload, events per GPU, kernel, precision), captured on the full
 # workload for the current kernels (profiles/launches_default_30x256.md).
 # Absent: not captured for the current kernels.
-TRAFFIC = {}
+TRAFFIC = {
+    ("n256_charm_static", 30, "field_step", 1): 440567808 + 766247168,
+    ("n256_charm_static", 30, "wong_push", 1): 931843072 + 251340800,
+}
 
 
 def field_bytes_per_site(prec):
