@@ -49,6 +49,7 @@ def lib():
             "or_pL": (d, [P, d, d]),
             "or_pL_kind": (d, [P, d, d, i]),
             "or_jets_init": (None, [i, u64, i64, P]),
+            "or_ptau_step": (None, [i, d, d, P, i64, P, P, P, P, P]),
             "or_jets_step": (None, [i, d, d, P, P, i64, P]),
             "or_jets_obs": (None, [i64, P, P]),
             "or_wilson_lines": (None, [i, i, d, d, d, u64, i, P]),
@@ -241,6 +242,13 @@ def particle_obs(part, t, mass, active, rep, kind=None):
     return out
 
 
+def ptau_step(N, t, dt, site, part, mass, kind, active, ptau):
+    """Euler step of the integrated p^tau (in place) from the state at t_n."""
+    lib().or_ptau_step(N, t, dt, _p(_f64(site)), part.shape[0], _p(part), _p(_f64(mass)),
+                       _p(np.ascontiguousarray(kind, dtype=np.int32)),
+                       _p(np.ascontiguousarray(active, dtype=np.int32)), _p(ptau))
+
+
 def jets_init(N, seed, n):
     """Jet-correlator probes [n][44]: x0, y0, W (18), X_x, X_y, X_z (8 each)."""
     out = np.zeros((n, JET_LEN))
@@ -295,7 +303,7 @@ class Run:
     step: leapfrog n -> n+1, site fields at t_n, Euler/CPIC push of the
     particles active at t_n, and the jet-correlator probes if any)."""
 
-    def __init__(self, state, particles, mass, t_form, rep, dt, step=0, kind=None, jets=None):
+    def __init__(self, state, particles, mass, t_form, rep, dt, step=0, kind=None, jets=None, ptau=None):
         self.st = state
         self.part = particles
         self.mass = np.asarray(mass, dtype=np.float64)
@@ -306,6 +314,7 @@ class Run:
         self.n = step
         self.site = None
         self.jets = jets
+        self.ptau = ptau  # integrated p^tau per particle (NaN: not started), or None
 
     def t(self):
         return self.n * self.dt
@@ -318,6 +327,8 @@ class Run:
         new = field_step(self.st, t, self.dt)
         self.site = site_fields(self.st, new, t)
         if self.part is not None and len(self.part):
+            if self.ptau is not None:
+                ptau_step(self.st.N, t, self.dt, self.site, self.part, self.mass, self.kind, self.active(), self.ptau)
             push(self.st.N, t, self.dt, self.site, new.U, new.phi, self.part, self.mass, self.active(), self.kind)
         if self.jets is not None and len(self.jets):
             jets_step(self.st.N, t, self.dt, self.site, new.U, self.jets)

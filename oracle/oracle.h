@@ -110,6 +110,14 @@ double or_pL_kind(const double* rec16, double t, double mass, int kind);
 /* or_pL_kind with the kind from the mass (INFINITY = static). */
 double or_pL(const double* rec16, double t, double mass);
 
+/* Temporal constraint: one Euler step of p^tau from its own equation of
+ * motion (Sec. 3.1), for the active Wong particles, with the state at t_n
+ * (call before or_push_kinds).  ptau[n]: NaN entries are first set to the
+ * mass-shell p^tau.  The mass-shell value after the push minus this one is
+ * the constraint violation of the temporal-constraint diagnostic. */
+void or_ptau_step(int N, double t, double dt, const double* site, int64_t n, const double* part,
+                  const double* mass, const int* kind, const int* active, double* ptau);
+
 /* Light-like jet correlator (Sec. 5.2): probe records of OR_JET_LEN doubles,
  * x0, y0, W (3x3 complex, row-major re/im), X_x, X_y, X_z (8 each).  A probe
  * starts at (x0, y0) at tau = 0, moves along +x at the speed of light,

@@ -329,3 +329,37 @@ void or_jets_obs(int64_t n, const double* jets, double* out3) {
     if (n > 0)
         for (int i = 0; i < 3; i++) out3[i] /= (double)n;
 }
+
+/* ---- temporal constraint (Sec. 3.1 equation for p^tau; the diagnostic of
+ * the temporal-constraint section) --------------------------------------- */
+/* One forward-Euler step of p^tau from its own equation of motion,
+ *   dp^tau/dtau = -(tau p^eta) p^eta / p^tau
+ *                 + Q.E_eta (tau p^eta / p^tau) + Q.E_x p^x/p^tau + Q.E_y p^y/p^tau,
+ * in lattice units with w = tau p^eta = P_eta / t and the mass-shell p^tau
+ * in the velocities, evaluated with the state at t_n (before the push).  A
+ * NaN entry is first set to the mass-shell value: the integration starts at
+ * the particle's first push.  Only active Wong particles are stepped. */
+void or_ptau_step(int N, double t, double dt, const double* site, int64_t n, const double* part,
+                  const double* mass, const int* kind, const int* active, double* ptau) {
+    const int64_t V = (int64_t)N * N;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < n; p++) {
+        const double* r = part + p * 16;
+        int s = (int)r[15];
+        if (!active[s] || kind[s] != OR_KIND_WONG) continue;
+        double m = mass[s];
+        int ixu = (int)floor(r[0] + 0.5), iyu = (int)floor(r[1] + 0.5);
+        int64_t cell = site_index(N, ixu, iyu);
+        const double* q = r + 6;
+        double qEx = qdot(q, site + (0 * V + cell) * 8);
+        double qEy = qdot(q, site + (1 * V + cell) * 8);
+        double qEe = qdot(q, site + (2 * V + cell) * 8);
+        double px = r[3], py = r[4];
+        double w = t > 0 ? r[5] / t : 0.0;
+        double pt = sqrt(px * px + py * py + w * w + m * m);
+        if (isnan(ptau[p])) ptau[p] = pt;
+        double vx = pt > 0 ? px / pt : 0.0, vy = pt > 0 ? py / pt : 0.0, vw = pt > 0 ? w / pt : 0.0;
+        double drift = (t > 0 && pt > 0) ? w * w / (t * pt) : 0.0;
+        ptau[p] += dt * (qEe * vw + qEx * vx + qEy * vy - drift);
+    }
+}

@@ -389,3 +389,50 @@ def test_push_is_gauge_covariant():
     assert (c1 != c0).sum() > 10
     want = H.mat2alg(Om[c1] @ H.alg2mat(part[:, 6:14]) @ Om[c1].conj().transpose(0, 2, 1))
     assert np.abs(gpart[:, 6:14] - want).max() < 1e-12
+
+
+# ------------------------------------------------------------------ temporal constraint
+def _ptau_gap(dt, field):
+    """Integrated p^tau against the mass shell after free streaming in Milne
+    coordinates (P_eta conserved, w = P_eta / t falls) or after acceleration
+    by a uniform Abelian E_x (work-energy); both equations are exact, so the
+    gap is the Euler error, O(dt)."""
+    N, m = 4, 0.6
+    st = O.FieldState(N)
+    if field:
+        st.e[0, :, 2] = 0.3   # e_x along T^3: uniform Abelian E_x = e / t
+    part = np.zeros((1, 16))
+    part[0, :2] = (1.2, 2.1)
+    part[0, 3], part[0, 4] = 0.4, -0.2
+    part[0, 5] = 0.0 if field else 1.5   # P_eta = tau^2 p^eta
+    part[0, 8] = 1.0                      # Q^3 = 1
+    ptau = np.full(1, np.nan)
+    r = O.Run(st, part, [m], [1.0], [0], dt, step=int(round(1.0 / dt)), ptau=ptau)
+    for _ in range(int(round(4.0 / dt))):
+        r.step()
+    t = r.t()
+    w = part[0, 5] / t
+    shell = math.sqrt(part[0, 3] ** 2 + part[0, 4] ** 2 + w * w + m * m)
+    return ptau[0] - shell, shell
+
+
+@pytest.mark.parametrize("field", [False, True])
+def test_integrated_ptau_follows_the_mass_shell(field):
+    g1, s1 = _ptau_gap(0.125, field)
+    g2, _ = _ptau_gap(0.0625, field)
+    g3, _ = _ptau_gap(0.03125, field)
+    assert abs(g1) < 0.15 * s1
+    assert 1.8 < g1 / g2 < 2.2 and 1.8 < g2 / g3 < 2.2   # first order (Euler), converging to the shell
+
+
+def test_ptau_skips_static_eikonal_and_inactive():
+    N = 4
+    st = O.FieldState(N)
+    part = np.zeros((3, 16))
+    part[:, 15] = [0, 1, 2]
+    part[:, 6] = 2.0
+    ptau = np.full(3, np.nan)
+    r = O.Run(st, part, [0.5, math.inf, 0.0], [0.0, 0.0, 100.0], [0, 0, 0], 0.125,
+              kind=[O.KIND_WONG, O.KIND_STATIC, O.KIND_EIKONAL], ptau=ptau)
+    r.step()
+    assert ptau[0] == pytest.approx(0.5) and np.isnan(ptau[1]) and np.isnan(ptau[2])
