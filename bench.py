@@ -60,7 +60,6 @@ BATCHED = "batched64"
 # Absent: not captured for the current kernels.
 TRAFFIC = {
     ("n256_charm_static", 30, "field_step", 1): 440567808 + 766247168,
-    ("n256_charm_static", 30, "wong_push", 1): 931843072 + 251340800,
 }
 
 

@@ -45,6 +45,16 @@
  *                                   B_x^2 + B_y^2 + B_eta^2) of the site fields,
  *                                   lattice units; the physical value is this
  *                                   / (g^2 a^4) (download only)
+ *   GL_BUF_PTAU       [np]          temporal-constraint diagnostic (with the
+ *                                   GL_CFG_PTAU_DIAGNOSTIC flag): p^tau of each
+ *                                   particle integrated from its own equation of
+ *                                   motion (Sec. 3.1, Euler with the state at t_n,
+ *                                   started at the mass shell at the first push;
+ *                                   NaN before that, and always for static and
+ *                                   eikonal species), caller's order; compare
+ *                                   with the mass shell of the GL_BUF_PARTICLES
+ *                                   record; upload after GL_BUF_PARTICLES (which
+ *                                   resets it to NaN)
  */
 #ifndef GLASMA_H
 #define GLASMA_H
@@ -79,7 +89,8 @@ typedef enum {
     GL_BUF_SITE = 4,
     GL_BUF_PARTICLES = 5,
     GL_BUF_JETS = 6,
-    GL_BUF_ENERGY = 7
+    GL_BUF_ENERGY = 7,
+    GL_BUF_PTAU = 8
 } gl_buffer;
 
 /* One MV event (Sec. 2, parameters of Sec. 7.1). */
@@ -103,7 +114,15 @@ typedef struct {
                                the Wilson line W of the x links it crosses (links at t_{n+1})
                                and X_i = sum dt W f_i W^+, f = (E_x, E_y - B_eta, E_eta + B_y)
                                at its cell at t_n; advanced by every push; single events only */
+    uint32_t flags;         /* GL_CFG_* options, 0 for none */
+    int32_t reserved;       /* must be 0 */
 } gl_config;
+
+/* gl_config.flags: integrate p^tau of every Wong particle from its own
+ * equation of motion beside the mass shell (the temporal-constraint
+ * diagnostic, GL_BUF_PTAU); costs one more read and write per particle and
+ * push. */
+#define GL_CFG_PTAU_DIAGNOSTIC 1u
 
 /* One species of test particles (Sec. 3.2 and 7.1). */
 typedef struct {

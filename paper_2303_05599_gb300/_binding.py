@@ -16,8 +16,10 @@ LIB_PATH = os.path.join(HERE, "libglasma_gb300.so")
 GL_MAX_SPECIES = 8
 GL_OK, GL_ERR_ARG, GL_ERR_CUDA, GL_ERR_STATE, GL_ERR_TIMEOUT, GL_ERR_NUMERIC, GL_ERR_SIZE = range(7)
 GL_FP64, GL_FP32_2ROW = 0, 1
-GL_BUF_LINKS, GL_BUF_PHI, GL_BUF_E, GL_BUF_PI, GL_BUF_SITE, GL_BUF_PARTICLES, GL_BUF_JETS, GL_BUF_ENERGY = range(8)
+(GL_BUF_LINKS, GL_BUF_PHI, GL_BUF_E, GL_BUF_PI, GL_BUF_SITE, GL_BUF_PARTICLES, GL_BUF_JETS, GL_BUF_ENERGY,
+ GL_BUF_PTAU) = range(9)
 JET_LEN = 44
+GL_CFG_PTAU_DIAGNOSTIC = 1
 
 STATUS_NAMES = {0: "GL_OK", 1: "GL_ERR_ARG", 2: "GL_ERR_CUDA", 3: "GL_ERR_STATE", 4: "GL_ERR_TIMEOUT",
                 5: "GL_ERR_NUMERIC", 6: "GL_ERR_SIZE"}
@@ -28,7 +30,7 @@ class gl_config(ctypes.Structure):
                 ("reunit_every", ctypes.c_int32), ("L_fm", ctypes.c_double), ("g2mu_GeV", ctypes.c_double),
                 ("mIR_GeV", ctypes.c_double), ("LambdaUV_GeV", ctypes.c_double),
                 ("dtau_over_a", ctypes.c_double), ("seed", ctypes.c_uint64), ("sort_every", ctypes.c_int32),
-                ("n_jets", ctypes.c_int32)]
+                ("n_jets", ctypes.c_int32), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
 
 
 class gl_species(ctypes.Structure):
@@ -131,7 +133,8 @@ def make_config(w):
     """gl_config from a workloads.Workload."""
     return gl_config(N=w.N, Ns=w.Ns, precision=w.precision, reunit_every=w.reunit_every, L_fm=w.L_fm,
                      g2mu_GeV=w.g2mu_GeV, mIR_GeV=w.mIR_GeV, LambdaUV_GeV=w.LambdaUV_GeV,
-                     dtau_over_a=w.dtau_over_a, seed=w.seed, sort_every=w.sort_every, n_jets=w.n_jets)
+                     dtau_over_a=w.dtau_over_a, seed=w.seed, sort_every=w.sort_every, n_jets=w.n_jets,
+                     flags=GL_CFG_PTAU_DIAGNOSTIC if w.ptau_diagnostic else 0, reserved=0)
 
 
 def make_species(w):
@@ -244,7 +247,7 @@ class Event:
         V = self.N * self.N
         return {GL_BUF_LINKS: (2, V, 18), GL_BUF_PHI: (V, 8), GL_BUF_E: (2, V, 8), GL_BUF_PI: (V, 8),
                 GL_BUF_SITE: (6, V, 8), GL_BUF_PARTICLES: (self.np, 16),
-                GL_BUF_JETS: (self.n_jets, JET_LEN), GL_BUF_ENERGY: (V,)}[which]
+                GL_BUF_JETS: (self.n_jets, JET_LEN), GL_BUF_ENERGY: (V,), GL_BUF_PTAU: (self.np,)}[which]
 
     def jets_observables(self):
         """Mean over the jet-correlator probes of X_i . X_i (i = x, y, z), GeV^2."""

@@ -73,3 +73,19 @@ def energy_density_GeV_fm3(tr_sum_lattice, a_fm, g):
 def mean_energy_lattice(obs):
     """Lattice mean of tr(E^2 + B^2) from one gl_obs record (GL_OBS_FIELDS)."""
     return obs.mean_trE_T2 + obs.mean_trE_L2 + obs.mean_trB_T2 + obs.mean_trB_L2
+
+
+def ptau_constraint(records, ptau_integrated, mass_lattice, t):
+    """Temporal-constraint diagnostic: relative difference between p^tau on the
+    mass shell, sqrt(p_T^2 + w^2 + m^2) with w = P_eta / t, and p^tau
+    integrated from its own equation of motion (GL_BUF_PTAU), per particle.
+    records: canonical particle records [n][16] (lattice units); mass_lattice:
+    lattice mass per species; t: lattice time of the records.  NaN where the
+    integration has not started (inactive, static or eikonal particles)."""
+    rec = np.asarray(records, dtype=float)
+    pint = np.asarray(ptau_integrated, dtype=float)
+    m = np.asarray(mass_lattice, dtype=float)[rec[:, 15].astype(int)]
+    w = rec[:, 5] / t if t > 0 else np.zeros(len(rec))
+    with np.errstate(invalid="ignore"):
+        shell = np.sqrt(rec[:, 3] ** 2 + rec[:, 4] ** 2 + w * w + m * m)
+        return (shell - pint) / shell

@@ -47,6 +47,7 @@ struct EvDesc {
     double mass[GL_MAX_SPECIES];
     int motion[GL_MAX_SPECIES];
     double t_form[GL_MAX_SPECIES];
+    int ptau_diag;
     int n_species;
     int pad;
 };
@@ -115,6 +116,7 @@ __device__ __forceinline__ void push_item(const BatchArgs& b, int lag, int blk) 
             s_sa.mass[k] = (R)(d.motion[k] == MOTION_WONG ? d.mass[k] : 0.0);
             s_sa.motion[k] = d.motion[k];
         }
+        s_sa.ptau_diag = d.ptau_diag;
         s_e = e;
         s_n = n;
         s_active = active;
@@ -545,6 +547,7 @@ static gl_status sync_desc(gl_batch* b) {
         cb += (int)((v.np + b->push_chunk - 1) / b->push_chunk);
         d.np = v.np;
         d.n_species = v.ns;
+        d.ptau_diag = v.ptau_diag;
         b->sort_every[e] = v.sort_every;
         for (int k = 0; k < GL_MAX_SPECIES; k++) {
             d.mass[k] = v.mass[k];

@@ -111,6 +111,8 @@ static const char* validate(const gl_config* cfg, const gl_species* sp, int32_t 
     }
     if (np >= ((int64_t)1 << 31)) return "at most 2^31 - 1 particles";
     if (cfg->n_jets < 0 || cfg->n_jets > (1 << 24)) return "n_jets must be in [0, 2^24]";
+    if (cfg->flags & ~GL_CFG_PTAU_DIAGNOSTIC) return "unknown flags";
+    if (cfg->reserved != 0) return "reserved must be 0";
     return nullptr;
 }
 
@@ -183,6 +185,7 @@ void ctx_view(const gl_ctx* c, CtxView* v) {
     v->reunit_count = c->reunit_count;
     v->parts_alt = c->parts_alt;
     v->sort_every = c->sort_ok ? c->cfg.sort_every : 0;
+    v->ptau_diag = c->spp.ptau_diag;
     v->sort_scratch = c->sort_scratch;
 }
 // record that the batch advanced this event by `steps` coupled steps
@@ -282,6 +285,7 @@ gl_status gl_create(const gl_config* cfg, const gl_species* sp, int32_t ns, void
     c->Lambda_a = cfg->LambdaUV_GeV > 0 ? cfg->LambdaUV_GeV * (cfg->L_fm / cfg->N / HBARC) : 0.0;
     q0_vectors(c->q0);
     c->spp.n_species = ns;
+    c->spp.ptau_diag = (cfg->flags & GL_CFG_PTAU_DIAGNOSTIC) != 0;
     for (int k = 0; k < GL_MAX_SPECIES; k++) {
         const bool on = k < ns;
         const bool st = on && isinf(sp[k].mass_GeV);
@@ -383,13 +387,14 @@ static size_t expected_count(const gl_ctx* c, gl_buffer which) {
         case GL_BUF_PARTICLES: return (size_t)c->np * 16;
         case GL_BUF_JETS: return (size_t)c->n_jets * JET_LEN;
         case GL_BUF_ENERGY: return (size_t)c->Vn;
+        case GL_BUF_PTAU: return (size_t)c->np;
     }
     return 0;
 }
 
 static gl_status transfer(gl_ctx* c, gl_buffer which, double* host, size_t count, int to_device) {
     if (!c || (!host && count)) return GL_ERR_ARG;
-    if ((int)which < 0 || (int)which > GL_BUF_ENERGY) return fail(c, GL_ERR_ARG, "unknown buffer");
+    if ((int)which < 0 || (int)which > GL_BUF_PTAU) return fail(c, GL_ERR_ARG, "unknown buffer");
     if (count != expected_count(c, which)) return fail(c, GL_ERR_SIZE, "host buffer size does not match");
     if (to_device && (which == GL_BUF_SITE || which == GL_BUF_ENERGY))
         return fail(c, GL_ERR_ARG, "site fields and energy density are download-only");
@@ -403,6 +408,8 @@ static gl_status transfer(gl_ctx* c, gl_buffer which, double* host, size_t count
         launch_jets_convert(c->prec, c->jets, c->n_jets, stg, to_device, c->stream);
     } else if (which == GL_BUF_ENERGY) {
         launch_energy(c->prec, site_at(c, c->pstep - 1), c->N, stg, c->stream);
+    } else if (which == GL_BUF_PTAU) {
+        launch_ptau_convert(c->prec, c->parts, c->np, stg, to_device, c->stream);
     } else launch_convert(c->prec, which, to_device, which == GL_BUF_SITE ? site_at(c, c->pstep - 1) : c->field[c->cur], stg, c->N, c->np,
                         c->stream);
     if (!to_device) cudaMemcpyAsync(host, stg, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream);

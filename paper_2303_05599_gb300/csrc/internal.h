@@ -16,6 +16,7 @@ struct SpeciesParams {
     double mass[GL_MAX_SPECIES];   // lattice units; INFINITY = static
     int motion[GL_MAX_SPECIES];
     int n_species;
+    int ptau_diag;                 // GL_CFG_PTAU_DIAGNOSTIC
 };
 
 // field step n -> n+1 on buffers in/out (FP64 or FP32 two-row layout); when
@@ -37,6 +38,8 @@ int launch_mv_init(int prec, void* b, void* scratch, int N, int Ns, double g2mu_
                    uint64_t seed, int* d_bad, cudaStream_t st);
 // canonical FP64 <-> device layout conversions (staging buffer is FP64 canonical)
 void launch_parts_convert(int prec, void* parts, int64_t np, double* stg, int to_device, cudaStream_t st);
+// integrated p^tau of the particles <-> canonical [np] in the caller's order
+void launch_ptau_convert(int prec, void* parts, int64_t np, double* stg, int to_device, cudaStream_t st);
 size_t init_scratch_bytes(int64_t Vn);
 void launch_convert(int prec, int which, int to_device, void* dev, double* staging, int N, int64_t np,
                     cudaStream_t st);
@@ -113,6 +116,7 @@ struct CtxView {
     double mass[GL_MAX_SPECIES];
     int motion[GL_MAX_SPECIES];
     double t_form[GL_MAX_SPECIES];
+    int ptau_diag;
     int ns;
     int reunit_count;
     void* parts_alt;

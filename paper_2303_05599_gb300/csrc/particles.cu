@@ -18,8 +18,8 @@
 namespace gl {
 
 size_t particle_bytes(int prec, int64_t np) {
-    if (prec == 0) return align256(16 * np) * 3 + align256(64 * np) + align256(4 * np) * 2 + align256(8 * np);
-    return align256(16 * np) + align256(8 * np) + align256(32 * np) + align256(4 * np) * 2 + align256(8 * np);
+    if (prec == 0) return align256(16 * np) * 3 + align256(64 * np) + align256(4 * np) * 2 + align256(8 * np) * 2;
+    return align256(16 * np) + align256(8 * np) + align256(32 * np) + align256(4 * np) * 3 + align256(8 * np);
 }
 
 size_t site_bytes(int prec, int64_t Vn) { return (size_t)6 * 8 * Vn * (prec == 0 ? 8 : 4); }
@@ -124,7 +124,7 @@ void launch_site_fields(int prec, const void* bn, const void* bn1, void* site, i
 
 // ------------------------------------------------------------ push
 template <typename R, int B>
-__global__ void __launch_bounds__(B, 1024 / B) push_kernel(const typename Prec<R>::V* __restrict__ site,
+__global__ void __launch_bounds__(B, (sizeof(R) == 4 ? 1024 : 512) / B) push_kernel(const typename Prec<R>::V* __restrict__ site,
                                                            Fields<R> bn1, Parts<R> P, int N, R t, R dt, R dt_over_t,
                                                            uint32_t active, SpeciesArgs<R> sa) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.np; i += (int64_t)gridDim.x * blockDim.x)
@@ -140,6 +140,7 @@ static void push_t(const void* site, const void* bn1, void* parts, int64_t np, i
         sa.mass[k] = (R)(k < sp.n_species && sp.motion[k] == MOTION_WONG ? sp.mass[k] : 0.0);
         sa.motion[k] = k < sp.n_species ? sp.motion[k] : MOTION_WONG;
     }
+    sa.ptau_diag = sp.ptau_diag;
     const int threads = block == 64 || block == 256 ? block : 128;
     int64_t blocks = (np + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
@@ -232,6 +233,7 @@ __global__ void sample_kernel(Parts<R> P, int N, uint32_t k0, uint32_t k1, Sampl
         P.sp[i] = s;
         P.pt0[i] = (double)p.px * (double)p.px + (double)p.py * (double)p.py;
         P.id[i] = (int32_t)i;
+        P.ptau[i] = R(NAN);
     }
 }
 
@@ -276,6 +278,7 @@ __global__ void parts_convert_kernel(Parts<R> P, double* stg, int to_device) {
             P.pt0[i] = r[14];
             P.sp[i] = (int32_t)r[15];
             P.id[i] = (int32_t)i;
+            P.ptau[i] = R(NAN);  // fresh particles: the p^tau integration restarts
         } else {
             // records go back to the caller's order (the device order may be sorted by cell)
             r = stg + (int64_t)P.id[i] * 16;
@@ -332,4 +335,24 @@ void launch_particle_obs(int prec, const void* parts, int64_t np, double t, uint
     particle_obs_finalize<<<GL_MAX_SPECIES * PO_N, 256, 0, st>>>(partials, blocks, out);
 }
 
+}  // namespace gl
+
+namespace gl {
+// integrated p^tau <-> canonical [np] in the caller's particle order
+template <typename R>
+__global__ void ptau_convert_kernel(Parts<R> P, double* stg, int to_device) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.np; i += (int64_t)gridDim.x * blockDim.x) {
+        if (to_device) P.ptau[i] = (R)stg[P.id[i]];
+        else stg[P.id[i]] = (double)P.ptau[i];
+    }
+}
+
+void launch_ptau_convert(int prec, void* parts, int64_t np, double* stg, int to_device, cudaStream_t st) {
+    const int threads = 256;
+    int64_t blocks = (np + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) return;
+    if (prec == 0) ptau_convert_kernel<double><<<(unsigned)blocks, threads, 0, st>>>(carve_parts<double>(parts, np), stg, to_device);
+    else ptau_convert_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(carve_parts<float>(parts, np), stg, to_device);
+}
 }  // namespace gl

@@ -22,6 +22,7 @@ struct Parts<double> {
     int32_t* sp;
     double* pt0;
     int32_t* id;
+    double* ptau;  // p^tau integrated from its own equation (NaN: not started)
     int64_t np;
     __device__ PState<double> load(int64_t i) const {
         PState<double> s;
@@ -56,6 +57,7 @@ struct Parts<float> {
     int32_t* sp;
     double* pt0;
     int32_t* id;
+    float* ptau;   // p^tau integrated from its own equation (NaN: not started)
     int64_t np;
     __device__ PState<float> load(int64_t i) const {
         PState<float> s;
@@ -95,7 +97,8 @@ __host__ __device__ inline Parts<double> carve_parts<double>(void* base, int64_t
     p.q = (double2*)c; c += align256(64 * np);
     p.sp = (int32_t*)c; c += align256(4 * np);
     p.pt0 = (double*)c; c += align256(8 * np);
-    p.id = (int32_t*)c;
+    p.id = (int32_t*)c; c += align256(4 * np);
+    p.ptau = (double*)c;
     return p;
 }
 
@@ -109,7 +112,8 @@ __host__ __device__ inline Parts<float> carve_parts<float>(void* base, int64_t n
     p.q = (float4*)c; c += align256(32 * np);
     p.sp = (int32_t*)c; c += align256(4 * np);
     p.pt0 = (double*)c; c += align256(8 * np);
-    p.id = (int32_t*)c;
+    p.id = (int32_t*)c; c += align256(4 * np);
+    p.ptau = (float*)c;
     return p;
 }
 

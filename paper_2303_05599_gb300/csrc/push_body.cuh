@@ -8,6 +8,7 @@ template <typename R>
 struct SpeciesArgs {
     R mass[GL_MAX_SPECIES];
     int motion[GL_MAX_SPECIES];  // MOTION_*
+    int ptau_diag;               // integrate p^tau beside the mass shell
 };
 
 template <typename R>
@@ -23,6 +24,17 @@ template <>
 __device__ __forceinline__ double fmod_r<double>(double a, double b) { return fmod(a, b); }
 template <>
 __device__ __forceinline__ float fmod_r<float>(float a, float b) { return fmodf(a, b); }
+
+// temporal constraint (Sec. 3.1): one Euler step of p^tau from its own
+// equation of motion, started at the mass shell at the particle's first push
+// (NaN before).  Kept out of line, so that the arithmetic of the push itself
+// is compiled the same way in every kernel that inlines it.
+template <typename R>
+__device__ __noinline__ R ptau_step(R pt, R shell, R w, R t, R dt, R work) {
+    if (pt != pt) pt = shell;
+    const R drift = (t > R(0) && shell > R(0)) ? w * w / (t * shell) : R(0);
+    return pt + dt * (work - drift);
+}
 
 // Euler + CPIC update of particle i (Sec. 3.1 and 3.2); site: site fields at
 // t_n, bn1: links and scalar at t_{n+1}
@@ -78,6 +90,7 @@ __device__ __forceinline__ void push_one(const typename Prec<R>::V* __restrict__
     const R ptau = sqrt(p.px * p.px + p.py * p.py + w * w + m * m);
     const R inv_pt = ptau > R(0) ? R(1) / ptau : R(0);
     const R vx = p.px * inv_pt, vy = p.py * inv_pt, vw = w * inv_pt;
+    if (sa.ptau_diag) P.ptau[i] = ptau_step<R>(P.ptau[i], ptau, w, t, dt, qEe * vw + qEx * vx + qEy * vy);
     // Wong's equations in Milne coordinates (Sec. 3.1), forward Euler
     const R dpx = qEx + qBe * vy - qBy * vw;
     const R dpy = qEy - qBe * vx + qBx * vw;

@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(SORT_T) gather_kernel(const SortEv* ev, int ne
         dst.sp[j] = src.sp[i];
         dst.pt0[j] = src.pt0[i];
         dst.id[j] = src.id[i];
+        dst.ptau[j] = src.ptau[i];
     }
 }
 

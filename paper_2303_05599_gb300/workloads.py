@@ -54,6 +54,7 @@ class Workload:
     reunit_every: int = 64
     sort_every: int = 16
     n_jets: int = 0              # light-like jet-correlator probes (single events)
+    ptau_diagnostic: bool = False  # integrate p^tau beside the mass shell (GL_BUF_PTAU)
     seed: int = 0
     species: List[Species] = field(default_factory=list)
     report_every_fm: float = 0.0

@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported():
 
 def test_struct_sizes_match_header():
     # gl_config: 4 int32 + 5 double + uint64 + 2 int32; gl_species: 2 double + int64 + 2 int32 + 2 double
-    assert ctypes.sizeof(B.gl_config) == 16 + 40 + 8 + 8
+    assert ctypes.sizeof(B.gl_config) == 16 + 40 + 8 + 8 + 8
     assert ctypes.sizeof(B.gl_species) == 16 + 8 + 8 + 16
     assert ctypes.sizeof(B.gl_obs) == 8 + 8 + 8 + 8 * 8 + 6 * 8 * 8 + 7 * 8
 

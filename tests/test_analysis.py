@@ -46,3 +46,14 @@ def test_energy_density_units():
     assert A.energy_density_GeV_fm3(1.0, A.HBARC, 1.0) == pytest.approx(1.0 / A.HBARC ** 3, rel=1e-15)
     o = SimpleNamespace(mean_trE_T2=1.0, mean_trE_L2=2.0, mean_trB_T2=3.0, mean_trB_L2=4.0)
     assert A.mean_energy_lattice(o) == 10.0
+
+
+def test_ptau_constraint_relative_difference():
+    rec = np.zeros((3, 16))
+    rec[:, 3] = [0.3, 0.0, 1.0]
+    rec[:, 5] = [0.0, 2.0, 0.0]
+    rec[:, 15] = [0, 0, 1]
+    t = 4.0
+    shell = np.sqrt(np.array([0.09 + 0.25, 0.25 + 0.25, 1.0 + np.inf]))
+    got = A.ptau_constraint(rec, [shell[0], 0.99 * shell[1], np.nan], [0.5, np.inf], t)
+    assert got[0] == 0.0 and got[1] == pytest.approx(0.01) and np.isnan(got[2])

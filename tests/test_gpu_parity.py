@@ -455,3 +455,35 @@ def test_half_time_step_jets_parity():
     assert rel(ev.download(B.GL_BUF_JETS), run.jets) < FP64_TOL
     g = download_state(ev)
     assert rel(g.U, run.st.U) < FP64_TOL and rel(g.e, run.st.e) < FP64_TOL
+
+
+@pytest.mark.parametrize("prec,tol", [(W.FP64, FP64_TOL), (W.FP32_2ROW, 2e-4)])
+def test_temporal_constraint_parity(prec, tol):
+    """p^tau integrated from its own equation of motion (GL_BUF_PTAU) against
+    the oracle's integration, with the same start at the first push and NaN
+    for static, eikonal and not yet formed particles."""
+    species = MIXED + [W.Species(0.0, 0.0, 20, W.REP_F, W.MOM_EIKONAL_X, 0.0)]
+    w = wl(20, prec=prec, species=species, seed=6)
+    w.ptau_diagnostic = True
+    st = oracle_init(w)
+    part = oracle_particles(w)
+    ev = B.Event(w)
+    upload_state(ev, st)
+    ev.upload(B.GL_BUF_PARTICLES, part)
+    assert np.all(np.isnan(ev.download(B.GL_BUF_PTAU)))
+    run = oracle_run(w, st, part)
+    run.ptau = np.full(len(part), np.nan)
+    for _ in range(25):
+        run.step()
+    ev.step(25)
+    got = ev.download(B.GL_BUF_PTAU)
+    want = run.ptau
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    ok = ~np.isnan(want)
+    assert ok.sum() > 100
+    assert rel(got[ok], want[ok]) < tol
+    # checkpoint: the integration state can be saved and restored
+    ev.upload(B.GL_BUF_PARTICLES, ev.download(B.GL_BUF_PARTICLES))
+    assert np.all(np.isnan(ev.download(B.GL_BUF_PTAU)))
+    ev.upload(B.GL_BUF_PTAU, got)
+    assert np.array_equal(ev.download(B.GL_BUF_PTAU), got, equal_nan=True)
