@@ -296,7 +296,8 @@ gl_status gl_batch_init(gl_batch* batch);
 /* Choose the launch shapes and the step schedule from timed trial launches
  * that do not change the state (waits).  Chosen: the field tile shape (0:
  * 32x8, 1: 32x4, 2: 32x16; FP64 batches use 32x4); the block size of the
- * separate push kernel (128, 256, 512); and the steady-state step, either
+ * separate push kernel (128, 256, 512, by the time of the whole overlapped
+ * step, not of the push alone); and the steady-state step, either
  *   - the field and push kernels on two streams, the push with one block per
  *     chunk of particles or (push_grid 1, 2) that many resident 128-thread
  *     blocks per SM launched ahead of the field tiles, or
@@ -317,7 +318,7 @@ gl_status gl_batch_get_launch(const gl_batch* batch, int32_t* tile_shape, int32_
 
 /* Trial timings of the last autotune, ms (0 where not tried): field_ms[3] by
  * tile shape; push_ms[3] by push block size; step_ms[8] for a whole step:
- * [0] two streams, [1..3] fused with push chunks of 512, 1024, 2048, [4..7]
+ * [0] two streams (the fastest push block size), [1..3] fused with push chunks of 512, 1024, 2048, [4..7]
  * two streams with push_grid 1 beside the 32x8 and 32x4 tiles, then push_grid
  * 2 beside the same. */
 gl_status gl_batch_tuning(const gl_batch* batch, float* field_ms, float* push_ms, float* step_ms);
@@ -334,7 +335,8 @@ gl_status gl_batch_step_timed(gl_batch* batch, int32_t n_steps, double* field_ms
 gl_status gl_batch_observables(gl_batch* batch, gl_obs* out);
 
 /* gl_observables_ex of every event into out[n_events] (waits).  The particle
- * sums of all events are reduced by one launch pair; each event's values are
+ * sums of all events are reduced by one launch pair and the results of all
+ * events come back in one device-to-host copy; each event's values are
  * bitwise those of gl_observables_ex on that event alone. */
 gl_status gl_batch_observables_ex(gl_batch* batch, uint32_t what, gl_obs* out);
 

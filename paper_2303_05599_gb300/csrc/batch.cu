@@ -232,6 +232,14 @@ __global__ void __launch_bounds__(256) batch_obs_finalize(const BObs* ev) {
     particle_obs_reduce(d.partials, d.nblocks, blockIdx.x % W, d.out);
 }
 
+// every event's obs row into one array [n_events][OBS_W], so the host reads
+// all of them with one copy; one block per event
+static constexpr int OBS_W = GL_MAX_SPECIES * PO_N + FO_N;
+__global__ void __launch_bounds__(64) gather_obs_kernel(const BObs* ev, double* all) {
+    const double* src = ev[blockIdx.x].out;
+    for (int k = threadIdx.x; k < OBS_W; k += blockDim.x) all[(size_t)blockIdx.x * OBS_W + k] = src[k];
+}
+
 // tile shapes the autotuner chooses from
 enum { TILE_32x8 = 0, TILE_32x4 = 1, TILE_32x16 = 2, N_TILES = 3 };
 static const int TILE_DIMS[N_TILES][2] = {{32, 8}, {32, 4}, {32, 16}};
@@ -327,10 +335,14 @@ struct gl_batch {
     cudaEvent_t ev_a, ev_b;
     gl_ctx** ev;
     EvDesc* h_desc;
+    EvDesc* h_prev;        // descriptors last uploaded (valid if desc_valid)
+    int desc_valid;
+    int64_t clock_host;    // value of the device step counter after the enqueued work
     EvDesc* d_desc;
     int64_t* d_clock;
     BObs* h_obs;
     BObs* d_obs;
+    double* d_obs_all;  // [ne][OBS_W], gathered obs rows
     SortEv* h_sort;
     SortEv* d_sort;
     int* sort_every;  // per event (0: no sorting)
@@ -369,6 +381,7 @@ static gl_status sync_desc(gl_batch* b);
 // descriptors for an autotune trial: the prefix tables of the current tile
 // shape and push chunk, the particles pointed at the contexts' spare buffers
 static gl_status trial_desc(gl_batch* b) {
+    b->desc_valid = 0;
     if (gl_status s = sync_desc(b)) return s;
     for (int e = 0; e < b->ne; e++) {
         CtxView v;
@@ -376,6 +389,7 @@ static gl_status trial_desc(gl_batch* b) {
         b->h_desc[e].parts = v.parts_alt;
     }
     cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(EvDesc) * b->ne, cudaMemcpyHostToDevice, b->stream);
+    b->desc_valid = 0;  // the device now holds the trial descriptors
     return GL_OK;
 }
 
@@ -401,7 +415,7 @@ size_t gl_batch_workspace_bytes(const gl_config* cfgs, const gl_species* species
                                 int32_t n_events) {
     if (!cfgs || n_events < 1 || n_events > MAX_EVENTS) return 0;
     size_t o = a256b(sizeof(EvDesc) * n_events) + 256 + a256b(sizeof(BObs) * n_events) +
-               a256b(sizeof(SortEv) * n_events);
+               a256b(sizeof(double) * OBS_W * n_events) + a256b(sizeof(SortEv) * n_events);
     for (int e = 0; e < n_events; e++) {
         const size_t w = ctx_workspace_bytes(&cfgs[e], species ? species + (size_t)e * n_species : nullptr, n_species);
         if (!w) return 0;
@@ -434,12 +448,14 @@ gl_status gl_batch_create(const gl_config* cfgs, const gl_species* species, int3
     b->stream = (cudaStream_t)stream;
     b->ev = new (std::nothrow) gl_ctx*[n_events]();
     b->h_desc = new (std::nothrow) EvDesc[n_events]();
+    b->h_prev = new (std::nothrow) EvDesc[n_events]();
     b->h_obs = new (std::nothrow) BObs[n_events]();
     b->h_sort = new (std::nothrow) SortEv[n_events]();
     b->sort_every = new (std::nothrow) int[n_events]();
-    if (!b->ev || !b->h_desc || !b->h_obs || !b->h_sort || !b->sort_every) {
+    if (!b->ev || !b->h_desc || !b->h_prev || !b->h_obs || !b->h_sort || !b->sort_every) {
         delete[] b->ev;
         delete[] b->h_desc;
+        delete[] b->h_prev;
         delete[] b->h_obs;
         delete[] b->h_sort;
         delete[] b->sort_every;
@@ -454,6 +470,8 @@ gl_status gl_batch_create(const gl_config* cfgs, const gl_species* species, int3
     o += 256;
     b->d_obs = (BObs*)(ws + o);
     o += a256b(sizeof(BObs) * n_events);
+    b->d_obs_all = (double*)(ws + o);
+    o += a256b(sizeof(double) * OBS_W * n_events);
     b->d_sort = (SortEv*)(ws + o);
     o += a256b(sizeof(SortEv) * n_events);
     for (int e = 0; e < n_events; e++) {
@@ -464,6 +482,7 @@ gl_status gl_batch_create(const gl_config* cfgs, const gl_species* species, int3
             for (int k = 0; k < e; k++) gl_destroy(b->ev[k]);
             delete[] b->ev;
             delete[] b->h_desc;
+            delete[] b->h_prev;
             delete[] b->h_obs;
             delete[] b->h_sort;
             delete[] b->sort_every;
@@ -495,6 +514,7 @@ gl_status gl_batch_destroy(gl_batch* b) {
     for (int e = 0; e < b->ne; e++) gl_destroy(b->ev[e]);
     delete[] b->ev;
     delete[] b->h_desc;
+    delete[] b->h_prev;
     delete[] b->h_obs;
     delete[] b->h_sort;
     delete[] b->sort_every;
@@ -508,6 +528,7 @@ const char* gl_batch_error_string(const gl_batch* b) { return b ? b->err : ""; }
 
 gl_status gl_batch_init(gl_batch* b) {
     if (!b) return GL_ERR_ARG;
+    b->desc_valid = 0;
     for (int e = 0; e < b->ne; e++) {
         gl_status s = glasma_init(b->ev[e]);
         if (s == GL_OK) s = wong_init(b->ev[e]);
@@ -557,10 +578,18 @@ static gl_status sync_desc(gl_batch* b) {
     }
     b->field_blocks = tb;
     b->push_blocks = cb;
+    // nothing changed since the last upload (the usual case between steps):
+    // no copy and no wait
+    if (b->desc_valid && b->clock_host == step0 && memcmp(b->h_prev, b->h_desc, sizeof(EvDesc) * b->ne) == 0)
+        return GL_OK;
     cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(EvDesc) * b->ne, cudaMemcpyHostToDevice, b->stream);
     cudaMemcpyAsync(b->d_clock, &step0, sizeof step0, cudaMemcpyHostToDevice, b->stream);
     cudaStreamSynchronize(b->stream);
-    return cudaGetLastError() == cudaSuccess ? GL_OK : bfail(b, GL_ERR_CUDA, "descriptor upload failed");
+    if (cudaGetLastError() != cudaSuccess) return bfail(b, GL_ERR_CUDA, "descriptor upload failed");
+    memcpy(b->h_prev, b->h_desc, sizeof(EvDesc) * b->ne);
+    b->clock_host = step0;
+    b->desc_valid = 1;
+    return GL_OK;
 }
 
 static BatchArgs batch_args(const gl_batch* b, int reunit_every) {
@@ -629,6 +658,7 @@ static gl_status ensure_aux(gl_batch* b);
 
 gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_out) {
     if (!b) return GL_ERR_ARG;
+    b->desc_valid = 0;  // the trials rewrite the device descriptors and clock
     if (gl_status s = ensure_aux(b)) return s;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -682,19 +712,19 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
         const int lag = (int)(now - trial);
         cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(EvDesc) * b->ne, cudaMemcpyHostToDevice, b->stream);
         const BatchArgs a = batch_args(b, 0);
-        float best_p = 1e30f;
         for (int k = 0; k < 3; k++) {
             const float ms = time_trial(b, e0, e1, 4, [&] {
                 if (b->prec == GL_FP64) launch_batch_push<double>(PUSH_BLOCKS[k], b->push_blocks, a, lag, b->stream);
                 else launch_batch_push<float>(PUSH_BLOCKS[k], b->push_blocks, a, lag, b->stream);
             });
             b->tune_push_ms[k] = ms;
-            if (ms < best_p) { best_p = ms; bp = PUSH_BLOCKS[k]; }
         }
         // whole steps: field and push on two streams (the push one block per
-        // chunk, or 1 or 2 resident blocks per SM launched first, beside each
-        // field tile shape), or one fused launch by push chunk
-        b->push_block = bp;
+        // chunk at each block size, or 1 or 2 resident blocks per SM launched
+        // first, beside each field tile shape), or one fused launch by push
+        // chunk.  The push block size is chosen here, by the time of the whole
+        // overlapped step, not by the push timed alone: beside the field
+        // kernel a smaller block often fills the SMs better.
         float best_s = 1e30f;
         int bt2 = b->tile, bg = 0;
         bf = 0;
@@ -707,17 +737,22 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
                 if (tile == TILE_32x16) continue;
                 b->tile = tile;
                 if (gl_status s = trial_desc(b)) return s;
-                const float ms = time_trial(b, e0, e1, 4, [&] {
-                    cudaEventRecord(b->ev_a, b->stream);
-                    cudaStreamWaitEvent(b->aux, b->ev_a, 0);
-                    launch_push_shape(b, a, lag, bp, g, b->aux);
-                    cudaEventRecord(b->ev_b, b->aux);
-                    if (b->prec == GL_FP64) launch_batch_field<double>(tile, b->field_blocks, a, b->stream);
-                    else launch_batch_field<float>(tile, b->field_blocks, a, b->stream);
-                    cudaStreamWaitEvent(b->stream, b->ev_b, 0);
-                });
-                b->tune_step_ms[g == 0 ? 0 : 1 + N_CHUNKS + 2 * (g - 1) + (tile == TILE_32x4)] = ms;
-                if (ms < best_s) { best_s = ms; bt2 = tile; bg = g; }
+                float best_g = 1e30f;
+                for (int kb = 0; kb < (g == 0 ? 3 : 1); kb++) {
+                    const int blk = g == 0 ? PUSH_BLOCKS[kb] : 128;
+                    const float ms = time_trial(b, e0, e1, 4, [&] {
+                        cudaEventRecord(b->ev_a, b->stream);
+                        cudaStreamWaitEvent(b->aux, b->ev_a, 0);
+                        launch_push_shape(b, a, lag, blk, g, b->aux);
+                        cudaEventRecord(b->ev_b, b->aux);
+                        if (b->prec == GL_FP64) launch_batch_field<double>(tile, b->field_blocks, a, b->stream);
+                        else launch_batch_field<float>(tile, b->field_blocks, a, b->stream);
+                        cudaStreamWaitEvent(b->stream, b->ev_b, 0);
+                    });
+                    if (ms < best_g) best_g = ms;
+                    if (ms < best_s) { best_s = ms; bt2 = tile; bg = g; if (g == 0) bp = blk; }
+                }
+                b->tune_step_ms[g == 0 ? 0 : 1 + N_CHUNKS + 2 * (g - 1) + (tile == TILE_32x4)] = best_g;
             }
         b->tile = tile0;
         for (int k = 0; k < N_CHUNKS; k++) {
@@ -738,6 +773,7 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
     }
     memcpy(b->h_desc, saved, sizeof(EvDesc) * b->ne);
     delete[] saved;
+    b->desc_valid = 0;
     b->push_block = bp;
     b->push_chunk = bc;
     b->fused = bf;
@@ -840,6 +876,7 @@ gl_status gl_batch_step(gl_batch* b, int32_t n_steps) {
         if (cudaGetLastError() != cudaSuccess) return bfail(b, GL_ERR_CUDA, "batch step launch failed");
         now += m;
         left -= m;
+        b->clock_host += m;
         end_segment(b, m, now);
         if (left > 0)
             if (gl_status s = sync_desc(b)) return s;
@@ -874,6 +911,7 @@ gl_status gl_batch_step_timed(gl_batch* b, int32_t n_steps, double* field_ms, do
         }
         now += m;
         done += m;
+        b->clock_host += m;
         end_segment(b, m, now);
         if (done < n_steps) st = sync_desc(b);
     }
@@ -899,8 +937,15 @@ gl_status gl_batch_observables(gl_batch* b, gl_obs* out) { return gl_batch_obser
 
 gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
     if (!b || !out || (what & ~GL_OBS_ALL)) return GL_ERR_ARG;
+    // obs rows of all events: out pointers (also for the gather when only the
+    // field checks are asked for)
+    int blocks = 0;
+    for (int e = 0; e < b->ne; e++) {
+        ObsEvent o;
+        ctx_obs_event(b->ev[e], &o);
+        b->h_obs[e].out = o.out;
+    }
     if (what & GL_OBS_PARTICLES) {
-        int blocks = 0;
         for (int e = 0; e < b->ne; e++) {
             ObsEvent o;
             ctx_obs_event(b->ev[e], &o);
@@ -920,14 +965,33 @@ gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
             if (d.nblocks == 0)
                 cudaMemsetAsync(o.out, 0, GL_MAX_SPECIES * PO_N * sizeof(double), b->stream);
         }
-        cudaMemcpyAsync(b->d_obs, b->h_obs, sizeof(BObs) * b->ne, cudaMemcpyHostToDevice, b->stream);
-        if (blocks > 0) {
-            if (b->prec == GL_FP64) batch_obs_kernel<double><<<blocks, OBS_THREADS, 0, b->stream>>>(b->d_obs, b->ne);
-            else batch_obs_kernel<float><<<blocks, OBS_THREADS, 0, b->stream>>>(b->d_obs, b->ne);
-            batch_obs_finalize<<<b->ne * GL_MAX_SPECIES * PO_N, 256, 0, b->stream>>>(b->d_obs);
-        }
     }
-    return ctx_observables_many(b->ev, b->ne, what & ~GL_OBS_PARTICLES, what, out);
+    cudaMemcpyAsync(b->d_obs, b->h_obs, sizeof(BObs) * b->ne, cudaMemcpyHostToDevice, b->stream);
+    if (blocks > 0) {
+        int ns = 0;
+        for (int e = 0; e < b->ne; e++) ns = b->h_obs[e].oa.sp.n_species > ns ? b->h_obs[e].oa.sp.n_species : ns;
+        const size_t smem = obs_smem_bytes(ns);
+        if (b->prec == GL_FP64) {
+            obs_smem_attr(batch_obs_kernel<double>);
+            batch_obs_kernel<double><<<blocks, OBS_THREADS, smem, b->stream>>>(b->d_obs, b->ne);
+        } else {
+            obs_smem_attr(batch_obs_kernel<float>);
+            batch_obs_kernel<float><<<blocks, OBS_THREADS, smem, b->stream>>>(b->d_obs, b->ne);
+        }
+        batch_obs_finalize<<<b->ne * GL_MAX_SPECIES * PO_N, 256, 0, b->stream>>>(b->d_obs);
+    }
+    // the field checks per event (the contexts share the batch stream)
+    if (what & GL_OBS_FIELDS)
+        for (int e = 0; e < b->ne; e++) ctx_obs_launch(b->ev[e], GL_OBS_FIELDS);
+    gather_obs_kernel<<<b->ne, 64, 0, b->stream>>>(b->d_obs, b->d_obs_all);
+    double* host = new (std::nothrow) double[(size_t)OBS_W * b->ne];
+    if (!host) return bfail(b, GL_ERR_ARG, "host allocation failed");
+    cudaMemcpyAsync(host, b->d_obs_all, sizeof(double) * OBS_W * b->ne, cudaMemcpyDeviceToHost, b->stream);
+    const bool ok = cudaStreamSynchronize(b->stream) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+    if (ok)
+        for (int e = 0; e < b->ne; e++) ctx_obs_fill(b->ev[e], what, host + (size_t)OBS_W * e, &out[e]);
+    delete[] host;
+    return ok ? GL_OK : bfail(b, GL_ERR_CUDA, "batch observables failed");
 }
 
 gl_status gl_batch_set_launch(gl_batch* b, int32_t tile, int32_t push_block, int32_t push_chunk, int32_t fused,

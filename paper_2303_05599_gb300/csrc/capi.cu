@@ -73,6 +73,7 @@ extern "C" {
 static uint32_t active_mask(const gl_ctx* c, int64_t n);
 static void observables_launch(gl_ctx* c, uint32_t what);
 static gl_status observables_read(gl_ctx* c, uint32_t what, gl_obs* o);
+static void observables_fill(const gl_ctx* c, uint32_t what, const double* host, gl_obs* o);
 }
 
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -212,13 +213,9 @@ void ctx_obs_event(const gl_ctx* c, ObsEvent* o) {
     o->partials = c->partials;
     o->out = c->obs_dev;
 }
-// observables of many contexts with one wait (used by the batch): `launch`
-// selects what is enqueued here, `what` what is read back
-gl_status ctx_observables_many(gl_ctx** cs, int n, uint32_t launch, uint32_t what, gl_obs* out) {
-    for (int e = 0; e < n; e++) ::observables_launch(cs[e], launch);
-    for (int e = 0; e < n; e++)
-        if (gl_status s = ::observables_read(cs[e], what, &out[e])) return s;
-    return GL_OK;
+void ctx_obs_launch(gl_ctx* c, uint32_t what) { ::observables_launch(c, what); }
+void ctx_obs_fill(const gl_ctx* c, uint32_t what, const double* host, gl_obs* o) {
+    ::observables_fill(c, what, host, o);
 }
 }  // namespace gl
 
@@ -623,11 +620,17 @@ static void observables_launch(gl_ctx* c, uint32_t what) {
 // read back the reductions enqueued by observables_launch (waits); the values
 // of the parts not in `what` are NaN (counts 0)
 static gl_status observables_read(gl_ctx* c, uint32_t what, gl_obs* o) {
-    memset(o, 0, sizeof *o);
     double host[GL_MAX_SPECIES * PO_N + FO_N];
     cudaMemcpyAsync(host, c->obs_dev, sizeof host, cudaMemcpyDeviceToHost, c->stream);
     if (gl_status s = check_cuda(c, "observables")) return s;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, "observables sync");
+    observables_fill(c, what, host, o);
+    return GL_OK;
+}
+
+// a gl_obs record from the raw reductions host[GL_MAX_SPECIES * PO_N + FO_N]
+static void observables_fill(const gl_ctx* c, uint32_t what, const double* host, gl_obs* o) {
+    memset(o, 0, sizeof *o);
     const double u2 = 1.0 / (c->aG * c->aG);  // lattice momentum^2 -> GeV^2
     const bool P = (what & GL_OBS_PARTICLES) != 0, F = (what & GL_OBS_FIELDS) != 0;
     o->step = c->step;
@@ -652,7 +655,6 @@ static gl_status observables_read(gl_ctx* c, uint32_t what, gl_obs* o) {
     o->mean_trE_L2 = F ? f[FO_EL2] / (double)c->Vn : NAN;
     o->mean_trB_T2 = F ? f[FO_BT2] / (double)c->Vn : NAN;
     o->mean_trB_L2 = F ? f[FO_BL2] / (double)c->Vn : NAN;
-    return GL_OK;
 }
 
 gl_status observables(gl_ctx* c, gl_obs* o) { return gl_observables_ex(c, GL_OBS_ALL, o); }

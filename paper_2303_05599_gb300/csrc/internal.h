@@ -132,9 +132,11 @@ void ctx_sort(gl_ctx* c);
 void ctx_swap_parts(gl_ctx* c);
 void ctx_obs_event(const gl_ctx* c, ObsEvent* o);
 size_t ctx_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t ns);
-// observables of many contexts with one wait: `launch` selects what is
-// enqueued, `what` what is read back
-gl_status ctx_observables_many(gl_ctx** cs, int n, uint32_t launch, uint32_t what, gl_obs* out);
+// enqueue a context's observable reductions into its obs row (ObsEvent::out,
+// GL_MAX_SPECIES * PO_N particle values then FO_N field values), no wait
+void ctx_obs_launch(gl_ctx* c, uint32_t what);
+// a gl_obs record from a host copy of that row
+void ctx_obs_fill(const gl_ctx* c, uint32_t what, const double* row, gl_obs* o);
 
 // observable slots
 enum { PO_COUNT = 0, PO_PX2, PO_PY2, PO_PL2, PO_DPT2, PO_Q2, PO_Q3, PO_N };

@@ -10,7 +10,11 @@
 // reduced on its own or inside a batch.
 //
 // Per-particle quantities are evaluated in the state's precision; every
-// accumulation is FP64.
+// accumulation is FP64.  Within a block each thread accumulates its own
+// particles (c0 + tid, c0 + tid + OBS_THREADS, ...) into its own column of
+// shared memory, then one fixed-order tree combines the columns: one FP64
+// add per particle and value, instead of a warp-wide shuffle tree per group
+// of 32 particles (FP64 issue is the scarce resource of this reduction).
 #pragma once
 #include "internal.h"
 #include "layout.cuh"
@@ -49,61 +53,57 @@ __device__ __forceinline__ R particle_pl(const PState<R>& p, R t, R mass, bool a
     return ptau * sinh(p.eta) + w * cosh(p.eta);
 }
 
+// dynamic shared memory of particle_obs_block for ns species:
+// [ns * PO_N][OBS_THREADS] doubles
+__host__ __device__ inline size_t obs_smem_bytes(int ns) {
+    return (size_t)ns * PO_N * OBS_THREADS * sizeof(double);
+}
+
 // partial observables of particles [c0, c1) into out[GL_MAX_SPECIES * PO_N];
-// blockDim.x == OBS_THREADS
+// blockDim.x == OBS_THREADS, obs_smem_bytes(oa.sp.n_species) of dynamic
+// shared memory at least
 template <typename R>
 __device__ __forceinline__ void particle_obs_block(const Parts<R>& P, double t, uint32_t active, const ObsArgs& oa,
                                                    int64_t c0, int64_t c1, double* out) {
-    __shared__ double wacc[OBS_THREADS / 32][GL_MAX_SPECIES * PO_N];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int k = lane; k < GL_MAX_SPECIES * PO_N; k += 32) wacc[warp][k] = 0.0;
-    __syncwarp();
-    for (int64_t base = c0; base < c1; base += OBS_THREADS) {
-        const int64_t i = base + threadIdx.x;
-        int s = -1;
-        double v[PO_N] = {0, 0, 0, 0, 0, 0, 0};
-        if (i < c1) {
-            s = P.sp[i];
-            if (!((active >> s) & 1u)) s = -1;
-        }
-        if (s >= 0) {
-            const PState<R> p = P.load(i);
-            const R pl = particle_pl<R>(p, (R)t, (R)oa.sp.mass[s], oa.sp.motion[s] != MOTION_WONG);
-            const double px = p.px, py = p.py;
-            v[PO_COUNT] = 1.0;
-            v[PO_PX2] = px * px;
-            v[PO_PY2] = py * py;
-            v[PO_PL2] = (double)pl * (double)pl;
-            v[PO_DPT2] = px * px + py * py - P.pt0[i];
-            v[PO_Q2] = fabs((double)a_dot(p.q, p.q) - oa.q2ref[s]);
-            v[PO_Q3] = fabs((double)casimir3(p.q) - oa.q3ref[s]);
-        }
-        for (int sp_ = 0; sp_ < oa.sp.n_species; sp_++) {
-            const bool mine = s == sp_;
-            if (!__any_sync(0xffffffffu, mine)) continue;
-            double r[PO_N];
+    extern __shared__ double obs_acc[];
+    const int ns = oa.sp.n_species, rows = ns * PO_N, tid = threadIdx.x;
+    for (int r = 0; r < rows; r++) obs_acc[r * OBS_THREADS + tid] = 0.0;
+    for (int64_t i = c0 + tid; i < c1; i += OBS_THREADS) {
+        const int s = P.sp[i];
+        if ((unsigned)s >= (unsigned)ns || !((active >> s) & 1u)) continue;
+        const PState<R> p = P.load(i);
+        const R pl = particle_pl<R>(p, (R)t, (R)oa.sp.mass[s], oa.sp.motion[s] != MOTION_WONG);
+        const double px = p.px, py = p.py;
+        double v[PO_N];
+        v[PO_COUNT] = 1.0;
+        v[PO_PX2] = px * px;
+        v[PO_PY2] = py * py;
+        v[PO_PL2] = (double)pl * (double)pl;
+        v[PO_DPT2] = px * px + py * py - P.pt0[i];
+        v[PO_Q2] = fabs((double)a_dot(p.q, p.q) - oa.q2ref[s]);
+        v[PO_Q3] = fabs((double)casimir3(p.q) - oa.q3ref[s]);
+        double* a = obs_acc + (size_t)s * PO_N * OBS_THREADS + tid;
 #pragma unroll
-            for (int k = 0; k < PO_N; k++) r[k] = mine ? v[k] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int k = 0; k < PO_N; k++) {
-                    const double oth = __shfl_down_sync(0xffffffffu, r[k], o);
-                    r[k] = po_is_max(k) ? nanmax(r[k], oth) : r[k] + oth;
-                }
-            if (lane == 0)
-                for (int k = 0; k < PO_N; k++) {
-                    double* a = &wacc[warp][sp_ * PO_N + k];
-                    *a = po_is_max(k) ? nanmax(*a, r[k]) : *a + r[k];
-                }
+        for (int k = 0; k < PO_N; k++)
+            a[k * OBS_THREADS] = po_is_max(k) ? nanmax(a[k * OBS_THREADS], v[k]) : a[k * OBS_THREADS] + v[k];
+    }
+    // level o folds column c + o into column c (c < o) of every row
+    for (int o = OBS_THREADS / 2; o > 0; o >>= 1) {
+        __syncthreads();
+        for (int w = tid; w < rows * o; w += OBS_THREADS) {
+            const int r = w / o, c = w - r * o;
+            double* a = obs_acc + r * OBS_THREADS;
+            a[c] = po_is_max(r % PO_N) ? nanmax(a[c], a[c + o]) : a[c] + a[c + o];
         }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < GL_MAX_SPECIES * PO_N; k += OBS_THREADS) {
-        double a = 0.0;
-        for (int w = 0; w < OBS_THREADS / 32; w++) a = po_is_max(k % PO_N) ? nanmax(a, wacc[w][k]) : a + wacc[w][k];
-        out[k] = a;
-    }
+    for (int k = tid; k < GL_MAX_SPECIES * PO_N; k += OBS_THREADS) out[k] = k < rows ? obs_acc[k * OBS_THREADS] : 0.0;
+}
+
+// allow the largest dynamic shared memory of particle_obs_block on kernel f
+template <typename K>
+inline void obs_smem_attr(K f) {
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obs_smem_bytes(GL_MAX_SPECIES));
 }
 
 // value k of GL_MAX_SPECIES * PO_N from nblocks partial rows: strided partial

@@ -326,12 +326,16 @@ void launch_particle_obs(int prec, const void* parts, int64_t np, double t, uint
         cudaMemsetAsync(out, 0, GL_MAX_SPECIES * PO_N * sizeof(double), st);
         return;
     }
-    if (prec == 0)
-        particle_obs_kernel<double><<<blocks, OBS_THREADS, 0, st>>>(carve_parts<double>((void*)parts, np), t,
-                                                                    active_mask, oa, partials);
-    else
-        particle_obs_kernel<float><<<blocks, OBS_THREADS, 0, st>>>(carve_parts<float>((void*)parts, np), t,
-                                                                   active_mask, oa, partials);
+    const size_t smem = obs_smem_bytes(sp.n_species);
+    if (prec == 0) {
+        obs_smem_attr(particle_obs_kernel<double>);
+        particle_obs_kernel<double><<<blocks, OBS_THREADS, smem, st>>>(carve_parts<double>((void*)parts, np), t,
+                                                                       active_mask, oa, partials);
+    } else {
+        obs_smem_attr(particle_obs_kernel<float>);
+        particle_obs_kernel<float><<<blocks, OBS_THREADS, smem, st>>>(carve_parts<float>((void*)parts, np), t,
+                                                                      active_mask, oa, partials);
+    }
     particle_obs_finalize<<<GL_MAX_SPECIES * PO_N, 256, 0, st>>>(partials, blocks, out);
 }
 
