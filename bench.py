@@ -59,7 +59,8 @@ BATCHED = "batched64"
 # workload for the current kernels (profiles/launches_default_30x256.md).
 # Absent: not captured for the current kernels.
 TRAFFIC = {
-    ("n256_charm_static", 30, "field_step", 1): 440567808 + 766247168,
+    ("n256_charm_static", 30, "field_step", 1): 440534784 + 765778944,
+    ("n256_charm_static", 30, "wong_push", 1): 930865408 + 250609408,
 }
 
 
