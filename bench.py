@@ -60,7 +60,6 @@ BATCHED = "batched64"
 # Absent: not captured for the current kernels.
 TRAFFIC = {
     ("n256_charm_static", 30, "field_step", 1): 440534784 + 765778944,
-    ("n256_charm_static", 30, "wong_push", 1): 930865408 + 250609408,
 }
 
 

@@ -106,8 +106,9 @@ typedef struct {
     double LambdaUV_GeV;    /* ultraviolet cutoff of the Poisson kernel (<= 0: none) */
     double dtau_over_a;     /* leapfrog time step in units of a */
     uint64_t seed;          /* Philox key of this event's random numbers */
-    int32_t sort_every;     /* reorder particles by cell every k pushes (0: never); only the
-                               memory order changes, downloads keep the caller's order */
+    int32_t sort_every;     /* reorder particles by lattice row, motion class (Wong, static,
+                               eikonal) and cell every k pushes (0: never); only the memory
+                               order changes, downloads keep the caller's order */
     int32_t n_jets;         /* light-like jet-correlator probes (Sec. 5.2, light-like jets), >= 0:
                                each starts at a uniform (x0, y0) at tau = 0 (Philox counters
                                (j, 0, 4, 0)) and moves along +x at the speed of light, carrying
@@ -269,7 +270,7 @@ gl_status gl_observables_ex(gl_ctx* ctx, uint32_t what, gl_obs* out);
  * the push of step s - 1 (the schedule is chosen by gl_batch_autotune).  All
  * events share the precision, the time step dtau/a and the re-unitarisation
  * period; they start at tau = 0 together.  Each event's particles are sorted
- * by cell when sampled or uploaded and every sort_every steps (all events in
+ * by row, motion class and cell when sampled or uploaded and every sort_every steps (all events in
  * one launch per sort stage).  Jet-correlator probes (n_jets > 0) are not
  * supported in batches (GL_ERR_ARG). */
 typedef struct gl_batch gl_batch;

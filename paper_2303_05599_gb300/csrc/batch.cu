@@ -11,7 +11,7 @@
 // in a prefix table of tiles or particle chunks.
 //
 // Every sort_every steps (per event) the run stops between a push and the next
-// field step and the particles of that event are reordered by cell, as in the
+// field step and the particles of that event are reordered (by row, motion class and cell), as in the
 // single-event schedule.  Observables of all events are reduced by one launch
 // pair over per-event chunks (obs_body.cuh).
 //
@@ -818,11 +818,11 @@ static void end_segment(gl_batch* b, int32_t m, int64_t now) {
             ctx_view(b->ev[e], &v);
             if (v.np <= 0) continue;
             SortEv& d = b->h_sort[n++];
-            d = sort_event(v.parts, v.parts_alt, v.np, v.N, v.sort_scratch);
+            d = sort_event(v.parts, v.parts_alt, v.np, v.N, v.ns, v.motion, v.sort_scratch);
             d.pblk_begin = pb;
             d.cblk_begin = cb;
             pb += sort_particle_blocks(v.np);
-            cb += sort_cell_blocks(v.N);
+            cb += sort_cell_blocks(d);
             ctx_swap_parts(b->ev[e]);
         }
     }

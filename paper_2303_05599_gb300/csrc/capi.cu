@@ -121,7 +121,7 @@ struct Carve {
     size_t field, site, parts, parts_alt, sort, jets, jet_partials, scratch, partials, obs, bad, total;
 };
 
-static Carve carve(const gl_config* cfg, int64_t np) {
+static Carve carve(const gl_config* cfg, int64_t np, int ns) {
     const int64_t Vn = (int64_t)cfg->N * cfg->N;
     const int prec = cfg->precision;
     Carve c;
@@ -129,9 +129,9 @@ static Carve carve(const gl_config* cfg, int64_t np) {
     c.field = o; o += 2 * a256(field_bytes(prec, Vn));
     c.site = o; o += 2 * a256(site_bytes(prec, Vn));
     c.parts = o; o += a256(particle_bytes(prec, np));
-    const bool sorting = cfg->sort_every > 0 && np > 0 && sort_supported(Vn);
+    const bool sorting = cfg->sort_every > 0 && np > 0 && sort_supported(Vn, ns);
     c.parts_alt = o; o += sorting ? a256(particle_bytes(prec, np)) : 0;
-    c.sort = o; o += sorting ? a256(sort_scratch_bytes(Vn, np)) : 0;
+    c.sort = o; o += sorting ? a256(sort_scratch_bytes(Vn, np, ns)) : 0;
     const size_t nj = cfg->n_jets > 0 ? (size_t)cfg->n_jets : 0;
     c.jets = o; o += nj ? a256(nj * JET_LEN * (prec == 0 ? 8 : 4)) : 0;
     c.jet_partials = o; o += nj ? a256((1024 * 3 + 3) * sizeof(double)) : 0;
@@ -225,7 +225,7 @@ size_t gl_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t ns
     if (validate(cfg, sp, ns)) return 0;
     int64_t np = 0;
     for (int k = 0; k < ns; k++) np += sp[k].count;
-    return carve(cfg, np).total;
+    return carve(cfg, np, ns).total;
 }
 
 gl_status gl_create(const gl_config* cfg, const gl_species* sp, int32_t ns, void* d_workspace, size_t bytes,
@@ -249,7 +249,7 @@ gl_status gl_create(const gl_config* cfg, const gl_species* sp, int32_t ns, void
         c->np += sp[k].count;
         c->off[k + 1] = c->np;
     }
-    Carve cv = carve(cfg, c->np);
+    Carve cv = carve(cfg, c->np, ns);
     if (bytes < cv.total) {
         delete c;
         return fail(nullptr, GL_ERR_SIZE, "workspace smaller than gl_workspace_bytes()");
@@ -261,7 +261,7 @@ gl_status gl_create(const gl_config* cfg, const gl_species* sp, int32_t ns, void
     c->site_buf[0] = c->ws + cv.site;
     c->site_buf[1] = c->ws + cv.site + a256(site_bytes(c->prec, c->Vn));
     c->parts = c->ws + cv.parts;
-    c->sort_ok = cfg->sort_every > 0 && c->np > 0 && sort_supported(c->Vn);
+    c->sort_ok = cfg->sort_every > 0 && c->np > 0 && sort_supported(c->Vn, ns);
     c->parts_alt = c->sort_ok ? c->ws + cv.parts_alt : nullptr;
     c->sort_scratch = c->sort_ok ? c->ws + cv.sort : nullptr;
     c->n_jets = cfg->n_jets;
@@ -319,10 +319,10 @@ gl_status gl_destroy(gl_ctx* c) {
 
 const char* gl_error_string(const gl_ctx* c) { return c ? c->err : g_create_err; }
 
-// reorder the particles by cell (memory order only)
+// reorder the particles by row, motion class and cell (memory order only)
 static void sort_particles(gl_ctx* c) {
     if (!c->sort_ok) return;
-    launch_sort(c->prec, c->parts, c->parts_alt, c->np, c->N, c->sort_scratch, c->stream);
+    launch_sort(c->prec, c->parts, c->parts_alt, c->np, c->N, c->ns, c->spp.motion, c->sort_scratch, c->stream);
     void* tmp = c->parts;
     c->parts = c->parts_alt;
     c->parts_alt = tmp;
@@ -478,7 +478,7 @@ static gl_status push_once(gl_ctx* c, cudaStream_t st, void* bn1) {
     if (c->n_jets) launch_jets_step(c->prec, site_at(c, c->pstep), bn1, c->jets, c->n_jets, c->N, t, c->dt, st);
     c->pstep++;
     if (c->sort_ok && c->pstep % c->cfg.sort_every == 0) {
-        launch_sort(c->prec, c->parts, c->parts_alt, c->np, c->N, c->sort_scratch, st);
+        launch_sort(c->prec, c->parts, c->parts_alt, c->np, c->N, c->ns, c->spp.motion, c->sort_scratch, st);
         void* tmp = c->parts;
         c->parts = c->parts_alt;
         c->parts_alt = tmp;

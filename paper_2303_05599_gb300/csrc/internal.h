@@ -76,8 +76,9 @@ void launch_jets_obs(int prec, const void* jets, int64_t n, double* partials, do
 // canonical FP64 <-> device probes
 void launch_jets_convert(int prec, void* jets, int64_t n, double* stg, int to_device, cudaStream_t st);
 
-// counting sort of the particles by cell from src into dst (same layout)
-void launch_sort(int prec, void* src, void* dst, int64_t np, int N, void* scratch, cudaStream_t st);
+// counting sort of the particles by row, motion class and cell from src into dst (same layout)
+void launch_sort(int prec, void* src, void* dst, int64_t np, int N, int ns, const int* motion, void* scratch,
+                 cudaStream_t st);
 // one event of a batched sort; pblk_begin / cblk_begin: its first block in the
 // particle-indexed (sort_particle_blocks) and cell-indexed (sort_cell_blocks)
 // launches, set by the caller
@@ -86,6 +87,8 @@ struct SortEv {
     void* dst;
     int64_t np;
     int N;
+    int ng;                      // motion classes present: keys (row, class, cell), ng N^2 of them
+    int8_t grp[GL_MAX_SPECIES];  // class of each species
     int pblk_begin, cblk_begin;
     int* key;
     int* rank;
@@ -93,13 +96,13 @@ struct SortEv {
     int* cnt;
     int* bsum;
 };
-SortEv sort_event(void* src, void* dst, int64_t np, int N, void* scratch);
+SortEv sort_event(void* src, void* dst, int64_t np, int N, int ns, const int* motion, void* scratch);
 int sort_particle_blocks(int64_t np);
-int sort_cell_blocks(int N);
+int sort_cell_blocks(const SortEv& d);
 // the sort of ne events (descriptors d_ev in device memory) in one launch per stage
 void launch_sort_many(int prec, const SortEv* d_ev, int ne, int pblocks, int cblocks, cudaStream_t st);
-size_t sort_scratch_bytes(int64_t Vn, int64_t np);
-bool sort_supported(int64_t Vn);
+size_t sort_scratch_bytes(int64_t Vn, int64_t np, int ns);
+bool sort_supported(int64_t Vn, int ns);
 
 size_t particle_bytes(int prec, int64_t np);
 size_t site_bytes(int prec, int64_t Vn);
@@ -126,7 +129,7 @@ struct CtxView {
 void ctx_view(const gl_ctx* c, CtxView* v);
 // record that the batch advanced the event by `steps` coupled steps
 void ctx_advance(gl_ctx* c, int64_t steps);
-// reorder the event's particles by cell on its stream
+// reorder the event's particles (row, motion class, cell) on its stream
 void ctx_sort(gl_ctx* c);
 // exchange the particle buffer and its spare (after a batched sort into the spare)
 void ctx_swap_parts(gl_ctx* c);

@@ -280,7 +280,7 @@ __global__ void parts_convert_kernel(Parts<R> P, double* stg, int to_device) {
             P.id[i] = (int32_t)i;
             P.ptau[i] = R(NAN);  // fresh particles: the p^tau integration restarts
         } else {
-            // records go back to the caller's order (the device order may be sorted by cell)
+            // records go back to the caller's order (the device order may be sorted)
             r = stg + (int64_t)P.id[i] * 16;
             PState<R> p = P.load(i);
             r[0] = p.x; r[1] = p.y; r[2] = p.eta; r[3] = p.px; r[4] = p.py; r[5] = p.Pe;

@@ -1,10 +1,17 @@
-// Counting sort of the particles by nearest-grid-point cell, so that the push
-// reads the site fields of neighbouring particles from the same cache lines.
+// Counting sort of the particles by lattice row, then by motion class (Wong,
+// static, eikonal), then by nearest-grid-point cell: the push reads the site
+// fields of neighbouring particles from the same cache lines (a row's fields
+// stay in cache while its classes are pushed one after the other), and the 32
+// particles of a warp are (but at the edges of a row's class ranges) of one
+// class, so they take one branch of the push instead of running every branch
+// present with the other lanes idle.  Species of one class stay mixed by cell.
 //
-//   count:    key[i] = cell of particle i, rank[i] = atomic slot within its cell
-//   scan:     off[c] = number of particles in cells < c (two-level block scan)
+//   count:    key[i] = (y ng + g) N + x for particle i of class g (of ng
+//             classes present) in cell (x, y), rank[i] = atomic slot within
+//             its key
+//   scan:     off[k] = number of particles with keys < k (two-level block scan)
 //   scatter:  perm[off[key[i]] + rank[i]] = i
-//   order:    each cell's entries of perm sorted ascending, so the result does
+//   order:    each key's entries of perm sorted ascending, so the result does
 //             not depend on the order the atomics were served in
 //   gather:   new[j] = old[perm[j]] for every particle plane
 // The original index travels with each particle, so downloads can restore the
@@ -18,19 +25,24 @@
 namespace gl {
 
 static constexpr int SCAN_T = 256, SCAN_PER = 4, SCAN_CHUNK = SCAN_T * SCAN_PER;  // 1024 cells per block
-static constexpr int SCAN_MAX_BLOCKS = 4096;                                       // cells <= 4 Mi
+static constexpr int SCAN_MAX_BLOCKS = 32768;                                      // keys <= 32 Mi
 
-size_t sort_scratch_bytes(int64_t Vn, int64_t np) {
-    // key, rank, perm (np each), counts/offsets (Vn + 1), block sums
-    return align256(4 * (size_t)np) * 3 + align256(4 * ((size_t)Vn + 1)) + align256(4 * (size_t)SCAN_MAX_BLOCKS);
+// keys of an event: one per (class, cell)
+__host__ __device__ inline int64_t sort_keys(int64_t Vn, int ng) { return (int64_t)(ng > 0 ? ng : 1) * Vn; }
+
+// ns (species) bounds the classes present
+size_t sort_scratch_bytes(int64_t Vn, int64_t np, int ns) {
+    // key, rank, perm (np each), counts/offsets (keys + 1), block sums
+    return align256(4 * (size_t)np) * 3 + align256(4 * ((size_t)sort_keys(Vn, ns) + 1)) +
+           align256(4 * (size_t)SCAN_MAX_BLOCKS);
 }
 
-bool sort_supported(int64_t Vn) { return Vn <= (int64_t)SCAN_CHUNK * SCAN_MAX_BLOCKS; }
+bool sort_supported(int64_t Vn, int ns) { return sort_keys(Vn, ns) <= (int64_t)SCAN_CHUNK * SCAN_MAX_BLOCKS; }
 
-// Every kernel runs over the particles or the cells of one or many events.
+// Every kernel runs over the particles or the keys of one or many events.
 // Particle-indexed launches give each event ceil(np / SORT_PB) blocks of
-// SORT_PB particles, cell-indexed launches ceil(Vn / SCAN_CHUNK) blocks of
-// SCAN_CHUNK cells (one scan chunk); a block finds its event by binary search
+// SORT_PB particles, key-indexed launches ceil(ng Vn / SCAN_CHUNK) blocks of
+// SCAN_CHUNK keys (one scan chunk); a block finds its event by binary search
 // in the descriptors, or takes the single descriptor passed by value.
 static constexpr int SORT_T = 256, SORT_PB = 1024;
 
@@ -65,7 +77,7 @@ __device__ __forceinline__ SortBlock sort_block(const SortEv* ev, int ne, const 
 
 __global__ void __launch_bounds__(SORT_T) zero_counts_kernel(const SortEv* ev, int ne, SortEv one) {
     const SortBlock k = sort_block(ev, ne, one, true);
-    const int64_t Vn = (int64_t)k.d.N * k.d.N;
+    const int64_t Vn = sort_keys((int64_t)k.d.N * k.d.N, k.d.ng);
     const int64_t c0 = (int64_t)k.b * SCAN_CHUNK;
     for (int64_t c = c0 + threadIdx.x; c < c0 + SCAN_CHUNK && c < Vn; c += SORT_T) k.d.cnt[c] = 0;
 }
@@ -79,7 +91,9 @@ __global__ void __launch_bounds__(SORT_T) cell_count_kernel(const SortEv* ev, in
     for (int64_t i = i0 + threadIdx.x; i < i0 + SORT_PB && i < k.d.np; i += SORT_T) {
         const PState<R> p = P.load(i);
         const int ix = wrapi((int)floor(p.x + R(0.5)), N), iy = wrapi((int)floor(p.y + R(0.5)), N);
-        const int c = iy * N + ix;
+        const int sp = P.sp[i];
+        const int g = (unsigned)sp < (unsigned)GL_MAX_SPECIES ? k.d.grp[sp] : 0;
+        const int c = (iy * k.d.ng + g) * N + ix;
         k.d.key[i] = c;
         k.d.rank[i] = atomicAdd(&k.d.cnt[c], 1);
     }
@@ -90,7 +104,7 @@ __global__ void __launch_bounds__(SCAN_T) scan_chunks_kernel(const SortEv* ev, i
     const SortBlock k = sort_block(ev, ne, one, true);
     __shared__ int warp_tot[SCAN_T / 32];
     int* cnt = k.d.cnt;
-    const int64_t n = (int64_t)k.d.N * k.d.N;
+    const int64_t n = sort_keys((int64_t)k.d.N * k.d.N, k.d.ng);
     const int64_t base = (int64_t)k.b * SCAN_CHUNK + threadIdx.x * SCAN_PER;
     int v[SCAN_PER], s = 0;
 #pragma unroll
@@ -123,7 +137,7 @@ __global__ void __launch_bounds__(SCAN_T) scan_chunks_kernel(const SortEv* ev, i
 __global__ void __launch_bounds__(1024) scan_top_kernel(const SortEv* ev, SortEv one) {
     const SortEv d = ev ? ev[blockIdx.x] : one;
     __shared__ int part[1024];
-    const int64_t n = (int64_t)d.N * d.N;
+    const int64_t n = sort_keys((int64_t)d.N * d.N, d.ng);
     const int nb = (int)((n + SCAN_CHUNK - 1) / SCAN_CHUNK);
     int* bsum = d.bsum;
     const int per = (nb + 1023) / 1024;
@@ -151,7 +165,7 @@ __global__ void __launch_bounds__(1024) scan_top_kernel(const SortEv* ev, SortEv
 
 __global__ void __launch_bounds__(SORT_T) scan_add_kernel(const SortEv* ev, int ne, SortEv one) {
     const SortBlock k = sort_block(ev, ne, one, true);
-    const int64_t Vn = (int64_t)k.d.N * k.d.N;
+    const int64_t Vn = sort_keys((int64_t)k.d.N * k.d.N, k.d.ng);
     const int add = k.d.bsum[k.b];
     const int64_t c0 = (int64_t)k.b * SCAN_CHUNK;
     for (int64_t c = c0 + threadIdx.x; c < c0 + SCAN_CHUNK && c < Vn; c += SORT_T) k.d.cnt[c] += add;
@@ -164,10 +178,10 @@ __global__ void __launch_bounds__(SORT_T) scatter_kernel(const SortEv* ev, int n
         k.d.perm[k.d.cnt[k.d.key[i]] + k.d.rank[i]] = (int)i;
 }
 
-// insertion sort of each cell's (short) segment of perm
+// insertion sort of each key's (short) segment of perm
 __global__ void __launch_bounds__(SORT_T) cell_order_kernel(const SortEv* ev, int ne, SortEv one) {
     const SortBlock k = sort_block(ev, ne, one, true);
-    const int64_t Vn = (int64_t)k.d.N * k.d.N;
+    const int64_t Vn = sort_keys((int64_t)k.d.N * k.d.N, k.d.ng);
     const int* off = k.d.cnt;
     int* perm = k.d.perm;
     const int64_t c0 = (int64_t)k.b * SCAN_CHUNK;
@@ -200,10 +214,19 @@ __global__ void __launch_bounds__(SORT_T) gather_kernel(const SortEv* ev, int ne
     }
 }
 
-SortEv sort_event(void* src, void* dst, int64_t np, int N, void* scratch) {
-    const int64_t Vn = (int64_t)N * N;
+SortEv sort_event(void* src, void* dst, int64_t np, int N, int ns, const int* motion, void* scratch) {
     SortEv d;
     memset(&d, 0, sizeof d);
+    // classes numbered in order of first appearance among the species
+    int code[GL_MAX_SPECIES], ng = 0;
+    for (int s = 0; s < ns && s < GL_MAX_SPECIES; s++) {
+        int g = 0;
+        while (g < ng && code[g] != motion[s]) g++;
+        if (g == ng) code[ng++] = motion[s];
+        d.grp[s] = (int8_t)g;
+    }
+    d.ng = ng > 0 ? ng : 1;
+    const int64_t keys = sort_keys((int64_t)N * N, d.ng);
     char* c = (char*)scratch;
     d.src = src;
     d.dst = dst;
@@ -212,13 +235,15 @@ SortEv sort_event(void* src, void* dst, int64_t np, int N, void* scratch) {
     d.key = (int*)c; c += align256(4 * (size_t)np);
     d.rank = (int*)c; c += align256(4 * (size_t)np);
     d.perm = (int*)c; c += align256(4 * (size_t)np);
-    d.cnt = (int*)c; c += align256(4 * ((size_t)Vn + 1));
+    d.cnt = (int*)c; c += align256(4 * ((size_t)keys + 1));
     d.bsum = (int*)c;
     return d;
 }
 
 int sort_particle_blocks(int64_t np) { return (int)((np + SORT_PB - 1) / SORT_PB); }
-int sort_cell_blocks(int N) { return (int)(((int64_t)N * N + SCAN_CHUNK - 1) / SCAN_CHUNK); }
+int sort_cell_blocks(const SortEv& d) {
+    return (int)((sort_keys((int64_t)d.N * d.N, d.ng) + SCAN_CHUNK - 1) / SCAN_CHUNK);
+}
 
 // the stages over `pblocks` particle blocks and `cblocks` cell blocks of
 // `ne` events (descriptors in device memory), or of the single event `one`
@@ -234,10 +259,11 @@ static void sort_stages(const SortEv* ev, int ne, const SortEv& one, int pblocks
     gather_kernel<R><<<pblocks, SORT_T, 0, st>>>(ev, ne, one);
 }
 
-void launch_sort(int prec, void* src, void* dst, int64_t np, int N, void* scratch, cudaStream_t st) {
+void launch_sort(int prec, void* src, void* dst, int64_t np, int N, int ns, const int* motion, void* scratch,
+                 cudaStream_t st) {
     if (np <= 0) return;
-    const SortEv one = sort_event(src, dst, np, N, scratch);
-    const int pb = sort_particle_blocks(np), cb = sort_cell_blocks(N);
+    const SortEv one = sort_event(src, dst, np, N, ns, motion, scratch);
+    const int pb = sort_particle_blocks(np), cb = sort_cell_blocks(one);
     if (prec == 0) sort_stages<double>(nullptr, 1, one, pb, cb, st);
     else sort_stages<float>(nullptr, 1, one, pb, cb, st);
 }
