@@ -59,7 +59,6 @@ BATCHED = "batched64"
 # workload for the current kernels (profiles/launches_default_30x256.md).
 # Absent: not captured for the current kernels.
 TRAFFIC = {
-    ("n256_charm_static", 30, "field_step", 1): 440534784 + 765778944,
 }
 
 

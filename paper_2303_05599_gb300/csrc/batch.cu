@@ -7,8 +7,8 @@
 //   links of t_s, neither of which the field step of s writes),
 //   then a one-thread tick of the device-resident step counter.
 // The kernels read the step index n from device memory, so the captured
-// graph is valid for every step.  Each block finds its event by binary search
-// in a prefix table of tiles or particle chunks.
+// graph is valid for every step.  Each block finds its event in a prefix
+// table of tiles or particle chunks (one warp, one round of loads).
 //
 // Every sort_every steps (per event) the run stops between a push and the next
 // field step and the particles of that event are reordered (by row, motion class and cell), as in the
@@ -61,15 +61,22 @@ struct BatchArgs {
     int push_chunk;  // particles per push block
 };
 
-__device__ __forceinline__ int find_event(const EvDesc* ev, int ne, int block, bool tiles) {
-    int lo = 0, hi = ne - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        const int b = tiles ? ev[mid].tile_begin : ev[mid].chunk_begin;
-        if (b <= block) lo = mid;
-        else hi = mid - 1;
+// the last event whose first block is <= block (the prefix tables are
+// non-decreasing, event 0 starts at 0), found by a whole warp: each lane
+// reads one event's entry and a ballot counts those at or before the block,
+// 32 events per round, so a block starts after one round of loads instead of
+// a chain of dependent ones
+__device__ __forceinline__ int find_event_warp(const EvDesc* ev, int ne, int block, bool tiles) {
+    const int lane = threadIdx.x & 31;
+    int cnt = 0;
+    for (int g = 0; g < ne; g += 32) {
+        const int k = g + lane;
+        const bool le = k < ne && (tiles ? ev[k].tile_begin : ev[k].chunk_begin) <= block;
+        const unsigned m = __ballot_sync(0xffffffffu, le);
+        cnt += __popc(m);
+        if (m != 0xffffffffu) break;
     }
-    return lo;
+    return cnt > 0 ? cnt - 1 : 0;
 }
 
 // one field tile (block `blk` of the tile prefix table) of step n = clock
@@ -79,13 +86,15 @@ __device__ __forceinline__ void field_item(const BatchArgs& b, int blk) {
     __shared__ int s_e;
     __shared__ int64_t s_n;
     __shared__ StepR<R> s_a;
-    if (threadIdx.x == 0) {
-        const int e = find_event(b.ev, b.ne, blk, true);
+    if (threadIdx.x < 32) {
         const int64_t n = *b.clock;
-        const int reunit = b.reunit_every > 0 && (n + 1) % b.reunit_every == 0;
-        s_e = e;
-        s_n = n;
-        s_a = step_r<R>(step_args(b.ev[e].N, b.ev[e].tiles_x, n, b.dt, reunit));
+        const int e = find_event_warp(b.ev, b.ne, blk, true);
+        if (threadIdx.x == 0) {
+            const int reunit = b.reunit_every > 0 && (n + 1) % b.reunit_every == 0;
+            s_e = e;
+            s_n = n;
+            s_a = step_r<R>(step_args(b.ev[e].N, b.ev[e].tiles_x, n, b.dt, reunit));
+        }
     }
     __syncthreads();
     const EvDesc& d = b.ev[s_e];
@@ -105,24 +114,30 @@ __device__ __forceinline__ void push_item(const BatchArgs& b, int lag, int blk) 
     __shared__ uint32_t s_active;
     __shared__ R s_t, s_dt, s_dto;
     __shared__ SpeciesArgs<R> s_sa;
-    if (threadIdx.x == 0) {
-        const int e = find_event(b.ev, b.ne, blk, false);
-        const EvDesc& d = b.ev[e];
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
         const int64_t n = *b.clock - lag;
+        const int e = find_event_warp(b.ev, b.ne, blk, false);
+        const EvDesc& d = b.ev[e];
         const double t = n * b.dt;
-        uint32_t active = 0;
-        for (int k = 0; k < GL_MAX_SPECIES; k++) {
-            if (k < d.n_species && t >= d.t_form[k]) active |= 1u << k;
-            s_sa.mass[k] = (R)(d.motion[k] == MOTION_WONG ? d.mass[k] : 0.0);
-            s_sa.motion[k] = d.motion[k];
+        // species k on lane k
+        bool act = false;
+        if (lane < GL_MAX_SPECIES) {
+            const int mo = d.motion[lane];
+            act = lane < d.n_species && t >= d.t_form[lane];
+            s_sa.mass[lane] = (R)(mo == MOTION_WONG ? d.mass[lane] : 0.0);
+            s_sa.motion[lane] = mo;
         }
-        s_sa.ptau_diag = d.ptau_diag;
-        s_e = e;
-        s_n = n;
-        s_active = active;
-        s_t = (R)t;
-        s_dt = (R)b.dt;
-        s_dto = (R)(t > 0 ? b.dt / t : 0.0);
+        const uint32_t active = __ballot_sync(0xffffffffu, act);
+        if (lane == 0) {
+            s_sa.ptau_diag = d.ptau_diag;
+            s_e = e;
+            s_n = n;
+            s_active = active;
+            s_t = (R)t;
+            s_dt = (R)b.dt;
+            s_dto = (R)(t > 0 ? b.dt / t : 0.0);
+        }
     }
     __syncthreads();
     const EvDesc& d = b.ev[s_e];
