@@ -296,19 +296,21 @@ gl_status gl_batch_init(gl_batch* batch);
 
 /* Choose the launch shapes and the step schedule from timed trial launches
  * that do not change the state (waits).  Chosen: the field tile shape (0:
- * 32x8, 1: 32x4, 2: 32x16; FP64 batches use 32x4); the block size of the
- * separate push kernel (128, 256, 512, by the time of the whole overlapped
- * step, not of the push alone); and the steady-state step, either
+ * 32x8, 1: 32x4, 2: 32x16; FP64 batches use 32x4); the block size (128,
+ * 256, 512) and chunk (particles per block: 128, 256, 512, 1024) of the
+ * separate push kernel, by the time of the whole overlapped step, not of the
+ * push alone; and the steady-state step, either
  *   - the field and push kernels on two streams, the push with one block per
  *     chunk of particles or (push_grid 1, 2) that many resident 128-thread
- *     blocks per SM launched ahead of the field tiles, or
+ *     blocks per SM launched ahead of the field tiles (chunks of 1024), or
  *   - one persistent fused launch that interleaves field tiles and push
  *     chunks of 512, 1024 or 2048 particles.
  * Outputs may be NULL. */
 gl_status gl_batch_autotune(gl_batch* batch, int32_t* tile_shape, int32_t* push_block);
 
-/* Set the launch shapes and schedule directly (values as above; fused 0 or 1;
- * push_grid 0, 1 or 2, ignored when fused).  Results do not depend on them.
+/* Set the launch shapes and schedule directly (values as above: push_chunk
+ * 128, 256, 512, 1024 or 2048; fused 0 or 1; push_grid 0, 1 or 2, ignored
+ * when fused).  Results do not depend on them.
  * GL_ERR_ARG for other values or a tile other than 32x4 in an FP64 batch. */
 gl_status gl_batch_set_launch(gl_batch* batch, int32_t tile_shape, int32_t push_block, int32_t push_chunk,
                               int32_t fused, int32_t push_grid);
@@ -319,7 +321,7 @@ gl_status gl_batch_get_launch(const gl_batch* batch, int32_t* tile_shape, int32_
 
 /* Trial timings of the last autotune, ms (0 where not tried): field_ms[3] by
  * tile shape; push_ms[3] by push block size; step_ms[8] for a whole step:
- * [0] two streams (the fastest push block size), [1..3] fused with push chunks of 512, 1024, 2048, [4..7]
+ * [0] two streams (the fastest push block and chunk sizes), [1..3] fused with push chunks of 512, 1024, 2048, [4..7]
  * two streams with push_grid 1 beside the 32x8 and 32x4 tiles, then push_grid
  * 2 beside the same. */
 gl_status gl_batch_tuning(const gl_batch* batch, float* field_ms, float* push_ms, float* step_ms);

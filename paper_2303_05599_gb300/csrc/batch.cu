@@ -260,7 +260,9 @@ enum { TILE_32x8 = 0, TILE_32x4 = 1, TILE_32x16 = 2, N_TILES = 3 };
 static const int TILE_DIMS[N_TILES][2] = {{32, 8}, {32, 4}, {32, 16}};
 static const int PUSH_BLOCKS[3] = {128, 256, 512};
 enum { N_CHUNKS = 3 };
-static const int PUSH_CHUNKS[N_CHUNKS] = {512, 1024, 2048};
+static const int PUSH_CHUNKS[N_CHUNKS] = {512, 1024, 2048};  // fused launch
+enum { N_SEP_CHUNKS = 4 };
+static const int SEP_CHUNKS[N_SEP_CHUNKS] = {128, 256, 512, 1024};  // separate push kernel
 
 template <typename R, int TX, int TY>
 static void set_smem_attr() {
@@ -735,11 +737,12 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
             b->tune_push_ms[k] = ms;
         }
         // whole steps: field and push on two streams (the push one block per
-        // chunk at each block size, or 1 or 2 resident blocks per SM launched
-        // first, beside each field tile shape), or one fused launch by push
-        // chunk.  The push block size is chosen here, by the time of the whole
-        // overlapped step, not by the push timed alone: beside the field
-        // kernel a smaller block often fills the SMs better.
+        // chunk at each chunk and block size, or 1 or 2 resident blocks per SM
+        // launched first, beside each field tile shape), or one fused launch
+        // by push chunk.  The push block and chunk sizes are chosen here, by
+        // the time of the whole overlapped step, not by the push timed alone:
+        // beside the field kernel a smaller block often fills the SMs better,
+        // and short chunks shorten the tail of blocks of unequal length.
         float best_s = 1e30f;
         int bt2 = b->tile, bg = 0;
         bf = 0;
@@ -751,21 +754,32 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
                 if (g == 0 && tile != tile0) continue;
                 if (tile == TILE_32x16) continue;
                 b->tile = tile;
-                if (gl_status s = trial_desc(b)) return s;
                 float best_g = 1e30f;
-                for (int kb = 0; kb < (g == 0 ? 3 : 1); kb++) {
-                    const int blk = g == 0 ? PUSH_BLOCKS[kb] : 128;
-                    const float ms = time_trial(b, e0, e1, 4, [&] {
-                        cudaEventRecord(b->ev_a, b->stream);
-                        cudaStreamWaitEvent(b->aux, b->ev_a, 0);
-                        launch_push_shape(b, a, lag, blk, g, b->aux);
-                        cudaEventRecord(b->ev_b, b->aux);
-                        if (b->prec == GL_FP64) launch_batch_field<double>(tile, b->field_blocks, a, b->stream);
-                        else launch_batch_field<float>(tile, b->field_blocks, a, b->stream);
-                        cudaStreamWaitEvent(b->stream, b->ev_b, 0);
-                    });
-                    if (ms < best_g) best_g = ms;
-                    if (ms < best_s) { best_s = ms; bt2 = tile; bg = g; if (g == 0) bp = blk; }
+                for (int kc = 0; kc < (g == 0 ? N_SEP_CHUNKS : 1); kc++) {
+                    b->push_chunk = g == 0 ? SEP_CHUNKS[kc] : PUSH_CHUNK;
+                    if (gl_status s = trial_desc(b)) return s;
+                    const BatchArgs ag = batch_args(b, 0);
+                    for (int kb = 0; kb < (g == 0 ? 3 : 1); kb++) {
+                        const int blk = g == 0 ? PUSH_BLOCKS[kb] : 128;
+                        if (blk > b->push_chunk) continue;  // threads without particles
+                        const float ms = time_trial(b, e0, e1, 4, [&] {
+                            cudaEventRecord(b->ev_a, b->stream);
+                            cudaStreamWaitEvent(b->aux, b->ev_a, 0);
+                            launch_push_shape(b, ag, lag, blk, g, b->aux);
+                            cudaEventRecord(b->ev_b, b->aux);
+                            if (b->prec == GL_FP64) launch_batch_field<double>(tile, b->field_blocks, ag, b->stream);
+                            else launch_batch_field<float>(tile, b->field_blocks, ag, b->stream);
+                            cudaStreamWaitEvent(b->stream, b->ev_b, 0);
+                        });
+                        if (ms < best_g) best_g = ms;
+                        if (ms < best_s) {
+                            best_s = ms;
+                            bt2 = tile;
+                            bg = g;
+                            bc = b->push_chunk;
+                            if (g == 0) bp = blk;
+                        }
+                    }
                 }
                 b->tune_step_ms[g == 0 ? 0 : 1 + N_CHUNKS + 2 * (g - 1) + (tile == TILE_32x4)] = best_g;
             }
@@ -781,7 +795,6 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
             b->tune_step_ms[1 + k] = ms;
             if (ms < best_s) { best_s = ms; bf = 1; bc = PUSH_CHUNKS[k]; bg = 0; bt2 = tile0; }
         }
-        if (!bf) bc = PUSH_CHUNK;
         b->push_chunk = bc;
         b->tile = bt2;
         b->push_grid = bg;
@@ -1017,6 +1030,7 @@ gl_status gl_batch_set_launch(gl_batch* b, int32_t tile, int32_t push_block, int
     bool ok_b = false, ok_c = false;
     for (int k = 0; k < 3; k++) ok_b = ok_b || PUSH_BLOCKS[k] == push_block;
     for (int k = 0; k < N_CHUNKS; k++) ok_c = ok_c || PUSH_CHUNKS[k] == push_chunk;
+    for (int k = 0; k < N_SEP_CHUNKS; k++) ok_c = ok_c || SEP_CHUNKS[k] == push_chunk;
     if (!ok_b || !ok_c) return GL_ERR_ARG;
     b->tile = tile;
     b->push_block = push_block;

@@ -171,7 +171,9 @@ def test_schedules_agree(prec):
               dict(tile=tile, push_block=256, push_chunk=512, fused=True, push_grid=0),
               dict(tile=tile, push_block=128, push_chunk=2048, fused=True, push_grid=0),
               dict(tile=tile, push_block=128, push_chunk=1024, fused=False, push_grid=1),
-              dict(tile=tile, push_block=128, push_chunk=512, fused=False, push_grid=2)]
+              dict(tile=tile, push_block=128, push_chunk=512, fused=False, push_grid=2),
+              dict(tile=tile, push_block=128, push_chunk=128, fused=False, push_grid=0),
+              dict(tile=tile, push_block=256, push_chunk=256, fused=False, push_grid=0)]
     if prec != W.FP64:
         shapes.append(dict(tile="32x16", push_block=512, push_chunk=1024, fused=True, push_grid=0))
     results = []
