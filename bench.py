@@ -62,6 +62,19 @@ TRAFFIC = {
 }
 
 
+def sort_launches(ws):
+    """Kernels of one batched particle sort: keys, then per 8-bit digit pass a
+    histogram, three scan kernels and a scatter, then the gather.  The passes
+    cover the largest key, (number of motion classes) x N^2 - 1, of any event."""
+    top = 1
+    for w in ws:
+        classes = {"static" if math.isinf(s.mass_GeV) else ("eikonal" if s.mom_mode == 3 else "wong")
+                   for s in w.species}
+        top = max(top, len(classes) * w.N * w.N - 1)
+    passes = (max(1, top.bit_length()) + 7) // 8
+    return 2 + 5 * passes
+
+
 def field_bytes_per_site(prec):
     """Fused leapfrog + site-field kernel: every field of step n read once, the
     fields of step n+1 written once (U: 2 links, phi, e: 2, pi) and the six site
@@ -383,8 +396,8 @@ def run_ours(args):
                                      "sums of every event read back to the host); one full report with the FP64 "
                                      "field checks at the end",
                          "gauss_max_final": max(o.gauss_max for o in final)}, **e2e_parts),
-            "gpu_launches": 3 * K + 8 * sum(1 for s_ in range(pre + 1, pre + K + 1)
-                                            if ws[0].sort_every > 0 and s_ % ws[0].sort_every == 0),
+            "gpu_launches": 3 * K + sort_launches(ws) * sum(1 for s_ in range(pre + 1, pre + K + 1)
+                                                          if ws[0].sort_every > 0 and s_ % ws[0].sort_every == 0),
             "clocks": ck,
         }
         if world == 1 and not args.no_cpu_baseline:

@@ -838,7 +838,7 @@ static int32_t segment_length(const gl_batch* b, int64_t now, int32_t n) {
 // particles of the events whose period divides `now` (between the push and
 // the next field step, as the single-event schedule does)
 static void end_segment(gl_batch* b, int32_t m, int64_t now) {
-    int n = 0, pb = 0, cb = 0;
+    int n = 0, pb = 0, cb = 0, passes = 1;
     for (int e = 0; e < b->ne; e++) {
         ctx_advance(b->ev[e], m);
         if (b->sort_every[e] > 0 && now % b->sort_every[e] == 0) {
@@ -851,12 +851,13 @@ static void end_segment(gl_batch* b, int32_t m, int64_t now) {
             d.cblk_begin = cb;
             pb += sort_particle_blocks(v.np);
             cb += sort_cell_blocks(d);
+            if (sort_passes(d) > passes) passes = sort_passes(d);
             ctx_swap_parts(b->ev[e]);
         }
     }
     if (n == 0) return;
     cudaMemcpyAsync(b->d_sort, b->h_sort, sizeof(SortEv) * n, cudaMemcpyHostToDevice, b->stream);
-    launch_sort_many(b->prec, b->d_sort, n, pb, cb, b->stream);
+    launch_sort_many(b->prec, b->d_sort, n, pb, cb, passes, b->stream);
 }
 
 static int64_t common_step(const gl_batch* b) {

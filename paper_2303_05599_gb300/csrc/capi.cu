@@ -129,7 +129,7 @@ static Carve carve(const gl_config* cfg, int64_t np, int ns) {
     c.field = o; o += 2 * a256(field_bytes(prec, Vn));
     c.site = o; o += 2 * a256(site_bytes(prec, Vn));
     c.parts = o; o += a256(particle_bytes(prec, np));
-    const bool sorting = cfg->sort_every > 0 && np > 0 && sort_supported(Vn, ns);
+    const bool sorting = cfg->sort_every > 0 && np > 0 && sort_supported(Vn, ns, np);
     c.parts_alt = o; o += sorting ? a256(particle_bytes(prec, np)) : 0;
     c.sort = o; o += sorting ? a256(sort_scratch_bytes(Vn, np, ns)) : 0;
     const size_t nj = cfg->n_jets > 0 ? (size_t)cfg->n_jets : 0;
@@ -261,7 +261,7 @@ gl_status gl_create(const gl_config* cfg, const gl_species* sp, int32_t ns, void
     c->site_buf[0] = c->ws + cv.site;
     c->site_buf[1] = c->ws + cv.site + a256(site_bytes(c->prec, c->Vn));
     c->parts = c->ws + cv.parts;
-    c->sort_ok = cfg->sort_every > 0 && c->np > 0 && sort_supported(c->Vn, ns);
+    c->sort_ok = cfg->sort_every > 0 && c->np > 0 && sort_supported(c->Vn, ns, c->np);
     c->parts_alt = c->sort_ok ? c->ws + cv.parts_alt : nullptr;
     c->sort_scratch = c->sort_ok ? c->ws + cv.sort : nullptr;
     c->n_jets = cfg->n_jets;

@@ -80,7 +80,7 @@ void launch_jets_convert(int prec, void* jets, int64_t n, double* stg, int to_de
 void launch_sort(int prec, void* src, void* dst, int64_t np, int N, int ns, const int* motion, void* scratch,
                  cudaStream_t st);
 // one event of a batched sort; pblk_begin / cblk_begin: its first block in the
-// particle-indexed (sort_particle_blocks) and cell-indexed (sort_cell_blocks)
+// particle-indexed (sort_particle_blocks) and scan-indexed (sort_cell_blocks)
 // launches, set by the caller
 struct SortEv {
     void* src;
@@ -89,20 +89,23 @@ struct SortEv {
     int N;
     int ng;                      // motion classes present: keys (row, class, cell), ng N^2 of them
     int8_t grp[GL_MAX_SPECIES];  // class of each species
-    int pblk_begin, cblk_begin;
-    int* key;
-    int* rank;
-    int* perm;
-    int* cnt;
+    int nblk;                    // particle blocks of the sort
+    int pblk_begin, cblk_begin;  // first particle block and first scan block in a batched launch
+    uint32_t* key[2];            // radix pass ping-pong: keys and original indices
+    uint32_t* val[2];
+    int* hist;                   // [digit][block] counts, scanned in place
     int* bsum;
 };
 SortEv sort_event(void* src, void* dst, int64_t np, int N, int ns, const int* motion, void* scratch);
 int sort_particle_blocks(int64_t np);
 int sort_cell_blocks(const SortEv& d);
-// the sort of ne events (descriptors d_ev in device memory) in one launch per stage
-void launch_sort_many(int prec, const SortEv* d_ev, int ne, int pblocks, int cblocks, cudaStream_t st);
+// digit passes that cover the keys of one event
+int sort_passes(const SortEv& d);
+// the sort of ne events (descriptors d_ev in device memory) in one launch per
+// stage, `passes` digit passes (the largest any of them needs)
+void launch_sort_many(int prec, const SortEv* d_ev, int ne, int pblocks, int cblocks, int passes, cudaStream_t st);
 size_t sort_scratch_bytes(int64_t Vn, int64_t np, int ns);
-bool sort_supported(int64_t Vn, int ns);
+bool sort_supported(int64_t Vn, int ns, int64_t np);
 
 size_t particle_bytes(int prec, int64_t np);
 size_t site_bytes(int prec, int64_t Vn);

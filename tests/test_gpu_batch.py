@@ -160,6 +160,32 @@ def test_particle_order_changes_nothing():
             np.testing.assert_allclose(list(getattr(o, f))[:2], list(getattr(o0, f))[:2], rtol=1e-12)
 
 
+def test_sort_of_particles_all_in_one_cell():
+    """A legal but degenerate ensemble, 120k particles of two motion classes
+    uploaded into one cell: the radix sort takes linear work whatever the
+    keys, and the ensemble evolves bitwise as it does without any sort."""
+    import time
+    runs = []
+    for se in (0, 2):
+        w = W.Workload("one_cell", N=32, L_fm=1.28, Ns=4, precision=W.FP32_2ROW, seed=5, sort_every=se,
+                       species=[W.Species(W.M_CHARM, 0.0, 100_000, W.REP_F, W.MOM_UNIFORM_PT, 0.0, 5.0),
+                                W.Species(math.inf, 0.0, 20_000, W.REP_A, W.MOM_FIXED_PT, 0.0)])
+        ev = B.Event(w)
+        ev.glasma_init()
+        ev.wong_init()
+        rec = ev.download(B.GL_BUF_PARTICLES)
+        rec[:, 0] = 7.2
+        rec[:, 1] = 19.9
+        t0 = time.perf_counter()
+        ev.upload(B.GL_BUF_PARTICLES, rec)
+        ev.step(9)
+        got = ev.download(B.GL_BUF_PARTICLES)
+        dt = time.perf_counter() - t0
+        runs.append(got)
+        assert dt < 30.0, "sorting one crowded cell took %.1f s" % dt
+    assert np.array_equal(runs[0], runs[1])
+
+
 @pytest.mark.parametrize("prec", [W.FP64, W.FP32_2ROW])
 def test_schedules_agree(prec):
     """One persistent fused launch per step (any push chunk) and the two-stream
