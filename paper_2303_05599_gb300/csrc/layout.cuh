@@ -151,7 +151,11 @@ __device__ __forceinline__ A8<R> icomm(const A8<R>& A, const A8<R>& B) {
 // anywhere shows in the reported maxima
 __device__ __forceinline__ double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
 
+// i mod n in [0, n) for n > 0; indices within one period of the lattice
+// (tile halos, particle cells) take a compare and an add instead of a
+// division by the runtime n
 __device__ __forceinline__ int wrapi(int i, int n) {
+    if (i >= -n && i < 2 * n) return i < 0 ? i + n : (i >= n ? i - n : i);
     i %= n;
     return i < 0 ? i + n : i;
 }

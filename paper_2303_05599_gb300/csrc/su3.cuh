@@ -222,11 +222,31 @@ __device__ __forceinline__ A8<R> adj_dag(const M3<R>& U, const A8<R>& x) {
     return herm_to_alg(mul(mul_dn(U, alg_to_mat(x)), U));
 }
 
+// 2 X for X = sum_a x^a T^a: the off-diagonal entries are the components
+// themselves (no factor 1/2)
+template <typename R>
+__device__ __forceinline__ M3<R> alg_to_mat2(const A8<R>& x) {
+    const R s3 = inv_sqrt3<R>();
+    M3<R> m;
+    m.re[0][0] = x.v[2] + x.v[7] * s3; m.im[0][0] = R(0);
+    m.re[1][1] = -x.v[2] + x.v[7] * s3; m.im[1][1] = R(0);
+    m.re[2][2] = R(-2) * (x.v[7] * s3); m.im[2][2] = R(0);
+    m.re[0][1] = x.v[0]; m.im[0][1] = -x.v[1];
+    m.re[1][0] = x.v[0]; m.im[1][0] = x.v[1];
+    m.re[0][2] = x.v[3]; m.im[0][2] = -x.v[4];
+    m.re[2][0] = x.v[3]; m.im[2][0] = x.v[4];
+    m.re[1][2] = x.v[5]; m.im[1][2] = -x.v[6];
+    m.re[2][1] = x.v[5]; m.im[2][1] = x.v[6];
+    return m;
+}
+
 // components of V^+ X V for Hermitian X (only the upper triangle of the
-// Hermitian result is formed)
+// Hermitian result is formed).  The product is taken of 2 X, so that the
+// off-diagonal components need no factor 2 and the diagonal ones a factor
+// 1/2; scaling by powers of 2 is exact, so the result is bitwise that of X.
 template <typename R>
 __device__ __forceinline__ A8<R> conj_dn(const M3<R>& V, const A8<R>& x) {
-    const M3<R> X = alg_to_mat(x);
+    const M3<R> X = alg_to_mat2(x);
     M3<R> Y;  // X V, with X's diagonal real
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -263,14 +283,14 @@ __device__ __forceinline__ A8<R> conj_dn(const M3<R>& V, const A8<R>& x) {
             zi[i][j] = si;
         }
     A8<R> o;
-    o.v[0] = R(2) * zr[0][1];
-    o.v[1] = -R(2) * zi[0][1];
-    o.v[2] = zr[0][0] - zr[1][1];
-    o.v[3] = R(2) * zr[0][2];
-    o.v[4] = -R(2) * zi[0][2];
-    o.v[5] = R(2) * zr[1][2];
-    o.v[6] = -R(2) * zi[1][2];
-    o.v[7] = (zr[0][0] + zr[1][1] - R(2) * zr[2][2]) * inv_sqrt3<R>();
+    o.v[0] = zr[0][1];
+    o.v[1] = -zi[0][1];
+    o.v[2] = R(0.5) * (zr[0][0] - zr[1][1]);
+    o.v[3] = zr[0][2];
+    o.v[4] = -zi[0][2];
+    o.v[5] = zr[1][2];
+    o.v[6] = -zi[1][2];
+    o.v[7] = (zr[0][0] + zr[1][1] - R(2) * zr[2][2]) * (R(0.5) * inv_sqrt3<R>());
     return o;
 }
 
@@ -366,11 +386,21 @@ __device__ __forceinline__ R casimir3(const A8<R>& q) {
 // three scalar coefficients (scaling and squaring when |sX| > 1).
 template <typename R, int TERMS>
 __device__ __forceinline__ M3<R> exp_i_alg(const A8<R>& x, R s) {
-    M3<R> X = alg_to_mat(x);
+    // s X: 2 X from the components, times s / 2 (exact: a power of 2), one
+    // product per distinct entry
+    M3<R> X = alg_to_mat2(x);
+    const R hs = R(0.5) * s;
 #pragma unroll
-    for (int i = 0; i < 3; i++)
+    for (int i = 0; i < 3; i++) {
+        X.re[i][i] *= hs;
 #pragma unroll
-        for (int j = 0; j < 3; j++) { X.re[i][j] *= s; X.im[i][j] *= s; }
+        for (int j = i + 1; j < 3; j++) {
+            X.re[i][j] *= hs;
+            X.im[i][j] *= hs;
+            X.re[j][i] = X.re[i][j];
+            X.im[j][i] = -X.im[i][j];
+        }
+    }
     M3<R> X2 = sq_herm(X);
     R c1 = R(0.5) * (X2.re[0][0] + X2.re[1][1] + X2.re[2][2]);
     int nsq = 0;
