@@ -12,9 +12,10 @@
 // Per-particle quantities are evaluated in the state's precision; every
 // accumulation is FP64.  Within a block each thread accumulates its own
 // particles (c0 + tid, c0 + tid + OBS_THREADS, ...) into its own column of
-// shared memory, then one fixed-order tree combines the columns: one FP64
-// add per particle and value, instead of a warp-wide shuffle tree per group
-// of 32 particles (FP64 issue is the scarce resource of this reduction).
+// shared memory, then one fixed-order tree combines the columns.  FP64 issue
+// is the scarce resource of this reduction, so a particle costs four FP64
+// fused adds (p_x^2, p_y^2, p_L^2, p_T^2(tau_form)) and its conversions: the
+// count is an integer and the Casimir deviations are taken at the extremes.
 #pragma once
 #include "internal.h"
 #include "layout.cuh"
@@ -26,11 +27,13 @@ namespace gl {
 static constexpr int OBS_THREADS = 256;
 static constexpr int OBS_MAX_BLOCKS = 1024;
 
-// particles per observables block: at least 1024, at most OBS_MAX_BLOCKS blocks
+// particles per observables block: at least 4096 (16 a thread, so that the
+// block's final tree is a small share of its FP64 work), at most
+// OBS_MAX_BLOCKS blocks
 __host__ __device__ inline int64_t obs_chunk(int64_t np) {
     int64_t c = (np + OBS_MAX_BLOCKS - 1) / OBS_MAX_BLOCKS;
     c = (c + OBS_THREADS - 1) / OBS_THREADS * OBS_THREADS;
-    return c < 1024 ? 1024 : c;
+    return c < 4096 ? 4096 : c;
 }
 __host__ __device__ inline int obs_blocks(int64_t np) {
     return np > 0 ? (int)((np + obs_chunk(np) - 1) / obs_chunk(np)) : 0;
@@ -59,33 +62,100 @@ __host__ __device__ inline size_t obs_smem_bytes(int ns) {
     return (size_t)ns * PO_N * OBS_THREADS * sizeof(double);
 }
 
+// Casimir deviations |q - ref| of one thread's particles.  FP32 state: the
+// thread keeps the smallest and largest q (exact in any precision: no
+// rounding) in the 8-byte slot of its column and takes |q - ref| in FP64 at
+// the two extremes only, where the largest deviation lies; bitwise the
+// maximum of the per-particle FP64 deviations.  FP64 state: the deviation per
+// particle.  A NaN q propagates.
+__device__ __forceinline__ float nanmin_f(float a, float b) { return (a < b || a != a) ? a : b; }
+__device__ __forceinline__ float nanmax_f(float a, float b) { return (a > b || a != a) ? a : b; }
+
+template <typename R>
+struct CasimirSlot;
+template <>
+struct CasimirSlot<float> {
+    static __device__ __forceinline__ void init(double* slot) {
+        *(float2*)slot = make_float2(INFINITY, -INFINITY);
+    }
+    static __device__ __forceinline__ void add(double* slot, float q, double) {
+        float2 e = *(float2*)slot;
+        e.x = nanmin_f(e.x, q);
+        e.y = nanmax_f(e.y, q);
+        *(float2*)slot = e;
+    }
+    static __device__ __forceinline__ double finish(const double* slot, double ref, long long n) {
+        if (n == 0) return 0.0;
+        const float2 e = *(const float2*)slot;
+        return nanmax(fabs((double)e.x - ref), fabs((double)e.y - ref));
+    }
+};
+template <>
+struct CasimirSlot<double> {
+    static __device__ __forceinline__ void init(double* slot) { *slot = 0.0; }
+    static __device__ __forceinline__ void add(double* slot, double q, double ref) {
+        *slot = nanmax(*slot, fabs(q - ref));
+    }
+    static __device__ __forceinline__ double finish(const double* slot, double, long long) { return *slot; }
+};
+
 // partial observables of particles [c0, c1) into out[GL_MAX_SPECIES * PO_N];
 // blockDim.x == OBS_THREADS, obs_smem_bytes(oa.sp.n_species) of dynamic
-// shared memory at least
+// shared memory at least.  Per thread and species, in its column: the count
+// (an integer in the PO_COUNT slot until the end), sums of p_x^2, p_y^2, p_L^2
+// (the products of the state's values, exact in FP64) and of p_T^2(tau_form)
+// in the PO_DPT2 slot (<dp_T^2> = sum p_x^2 + sum p_y^2 - sum p_T^2(tau_form)),
+// and the Casimir slots; then one fixed-order tree over the columns.
 template <typename R>
 __device__ __forceinline__ void particle_obs_block(const Parts<R>& P, double t, uint32_t active, const ObsArgs& oa,
                                                    int64_t c0, int64_t c1, double* out) {
     extern __shared__ double obs_acc[];
     const int ns = oa.sp.n_species, rows = ns * PO_N, tid = threadIdx.x;
-    for (int r = 0; r < rows; r++) obs_acc[r * OBS_THREADS + tid] = 0.0;
-    for (int64_t i = c0 + tid; i < c1; i += OBS_THREADS) {
-        const int s = P.sp[i];
-        if ((unsigned)s >= (unsigned)ns || !((active >> s) & 1u)) continue;
-        const PState<R> p = P.load(i);
-        const R pl = particle_pl<R>(p, (R)t, (R)oa.sp.mass[s], oa.sp.motion[s] != MOTION_WONG);
-        const double px = p.px, py = p.py;
-        double v[PO_N];
-        v[PO_COUNT] = 1.0;
-        v[PO_PX2] = px * px;
-        v[PO_PY2] = py * py;
-        v[PO_PL2] = (double)pl * (double)pl;
-        v[PO_DPT2] = px * px + py * py - P.pt0[i];
-        v[PO_Q2] = fabs((double)a_dot(p.q, p.q) - oa.q2ref[s]);
-        v[PO_Q3] = fabs((double)casimir3(p.q) - oa.q3ref[s]);
+    for (int s = 0; s < ns; s++) {
         double* a = obs_acc + (size_t)s * PO_N * OBS_THREADS + tid;
-#pragma unroll
-        for (int k = 0; k < PO_N; k++)
-            a[k * OBS_THREADS] = po_is_max(k) ? nanmax(a[k * OBS_THREADS], v[k]) : a[k * OBS_THREADS] + v[k];
+        *(long long*)(a + PO_COUNT * OBS_THREADS) = 0;
+        a[PO_PX2 * OBS_THREADS] = 0.0;
+        a[PO_PY2 * OBS_THREADS] = 0.0;
+        a[PO_PL2 * OBS_THREADS] = 0.0;
+        a[PO_DPT2 * OBS_THREADS] = 0.0;
+        CasimirSlot<R>::init(a + PO_Q2 * OBS_THREADS);
+        CasimirSlot<R>::init(a + PO_Q3 * OBS_THREADS);
+    }
+    // two particles per iteration, both loaded before either is accumulated
+    // (in order: the first, then the second), so their loads overlap
+    auto accumulate = [&](int64_t i, int s, const PState<R>& p, double pt0) {
+        const R pl = particle_pl<R>(p, (R)t, (R)oa.sp.mass[s], oa.sp.motion[s] != MOTION_WONG);
+        const double px = p.px, py = p.py, dpl = pl;
+        double* a = obs_acc + (size_t)s * PO_N * OBS_THREADS + tid;
+        *(long long*)(a + PO_COUNT * OBS_THREADS) += 1;
+        a[PO_PX2 * OBS_THREADS] = fma(px, px, a[PO_PX2 * OBS_THREADS]);
+        a[PO_PY2 * OBS_THREADS] = fma(py, py, a[PO_PY2 * OBS_THREADS]);
+        a[PO_PL2 * OBS_THREADS] = fma(dpl, dpl, a[PO_PL2 * OBS_THREADS]);
+        a[PO_DPT2 * OBS_THREADS] += pt0;
+        CasimirSlot<R>::add(a + PO_Q2 * OBS_THREADS, a_dot(p.q, p.q), oa.q2ref[s]);
+        CasimirSlot<R>::add(a + PO_Q3 * OBS_THREADS, casimir3(p.q), oa.q3ref[s]);
+    };
+    for (int64_t i = c0 + tid; i < c1; i += 2 * OBS_THREADS) {
+        const int64_t j = i + OBS_THREADS;
+        const int si = P.sp[i];
+        const int sj = j < c1 ? P.sp[j] : -1;
+        const bool oki = (unsigned)si < (unsigned)ns && ((active >> si) & 1u);
+        const bool okj = (unsigned)sj < (unsigned)ns && ((active >> sj) & 1u);
+        PState<R> pi_, pj;
+        double ti = 0.0, tj = 0.0;
+        if (oki) { pi_ = P.load(i); ti = P.pt0[i]; }
+        if (okj) { pj = P.load(j); tj = P.pt0[j]; }
+        if (oki) accumulate(i, si, pi_, ti);
+        if (okj) accumulate(j, sj, pj, tj);
+    }
+    // the thread's partial values in place, in its own column
+    for (int s = 0; s < ns; s++) {
+        double* a = obs_acc + (size_t)s * PO_N * OBS_THREADS + tid;
+        const long long n = *(long long*)(a + PO_COUNT * OBS_THREADS);
+        a[PO_COUNT * OBS_THREADS] = (double)n;
+        a[PO_DPT2 * OBS_THREADS] = a[PO_PX2 * OBS_THREADS] + a[PO_PY2 * OBS_THREADS] - a[PO_DPT2 * OBS_THREADS];
+        a[PO_Q2 * OBS_THREADS] = CasimirSlot<R>::finish(a + PO_Q2 * OBS_THREADS, oa.q2ref[s], n);
+        a[PO_Q3 * OBS_THREADS] = CasimirSlot<R>::finish(a + PO_Q3 * OBS_THREADS, oa.q3ref[s], n);
     }
     // level o folds column c + o into column c (c < o) of every row
     for (int o = OBS_THREADS / 2; o > 0; o >>= 1) {
