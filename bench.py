@@ -324,9 +324,8 @@ def run_ours(args):
         h2d = sum(t.numel() * 8 for bufs in host for t in bufs.values())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for ev, bufs in zip(batch.events, host):
-            for which, t in bufs.items():
-                ev.upload(which, t.numpy())
+        for which in (B.GL_BUF_LINKS, B.GL_BUF_PHI, B.GL_BUF_E, B.GL_BUF_PI, B.GL_BUF_PARTICLES):
+            batch.upload(which, [bufs[which].numpy() for bufs in host])
         t1 = time.perf_counter()
         for _ in range(K):
             batch.step(1)
@@ -393,7 +392,7 @@ def run_ours(args):
             "roofline_kernels": roof,
             "e2e": dict({"value": world * sites * K / e2e_t, "unit": "site-updates/s",
                          "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": len(ws) * ctypes.sizeof(B.gl_obs),
-                         "includes": "gl_upload of every event's fields and particles from pinned host memory "
+                         "includes": "gl_batch_upload of every event's fields and particles from pinned host memory "
                                      "(FP64 canonical layout); K x (gl_batch_step(1) + the per-species particle "
                                      "sums of every event read back to the host); one full report with the FP64 "
                                      "field checks at the end",

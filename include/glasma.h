@@ -201,7 +201,8 @@ gl_status gl_upload(gl_ctx* ctx, gl_buffer which, const double* host, size_t cou
 gl_status gl_download(gl_ctx* ctx, gl_buffer which, double* host, size_t count);
 
 /* Set the field step index n (t_n = n dt) of the uploaded state; the
- * particles are taken to be at the same time. */
+ * particles are taken to be at the same time.  The uploaded fields stay the
+ * current ones, so uploads may come before or after this call. */
 gl_status gl_set_step(gl_ctx* ctx, int64_t step);
 
 /* Advance the fields n_steps leapfrog steps (Sec. 2.1 equations of motion).
@@ -333,6 +334,14 @@ gl_status gl_batch_step(gl_batch* batch, int32_t n_steps);
  * and push launch; field_ms and push_ms receive the summed kernel durations
  * (waits).  For measurement. */
 gl_status gl_batch_step_timed(gl_batch* batch, int32_t n_steps, double* field_ms, double* push_ms);
+
+/* gl_upload of buffer `which` of every event: host[e] holds count[e] doubles
+ * in the canonical layout for event e.  The copies and conversions of all
+ * events are enqueued on the batch stream and waited for once, at the end, so
+ * a restore of many events pays one wait per buffer instead of one per event
+ * (waits).  Errors as gl_upload, reported for the first failing event; the
+ * events before it are uploaded. */
+gl_status gl_batch_upload(gl_batch* batch, gl_buffer which, const double* const* host, const size_t* count);
 
 /* observables() of every event into out[n_events] (waits). */
 gl_status gl_batch_observables(gl_batch* batch, gl_obs* out);

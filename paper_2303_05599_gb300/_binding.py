@@ -88,6 +88,7 @@ SIGNATURES = {
     "gl_batch_step": (ctypes.c_int, [_P, ctypes.c_int32]),
     "gl_batch_step_timed": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "gl_batch_observables": (ctypes.c_int, [_P, _P]),
+    "gl_batch_upload": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "gl_batch_set_launch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_int32]),
     "gl_batch_get_launch": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -345,6 +346,22 @@ class Batch:
         p = ctypes.c_double()
         self._chk(lib().gl_batch_step_timed(self.b, n, ctypes.byref(f), ctypes.byref(p)), "gl_batch_step_timed")
         return f.value, p.value
+
+    def upload(self, which, arrays):
+        """Buffer `which` of every event from arrays[e] (canonical layout),
+        with one wait for all events (gl_batch_upload)."""
+        keep = []
+        for ev, arr in zip(self.events, arrays):
+            a = np.ascontiguousarray(arr, dtype=np.float64)
+            if a.size != int(np.prod(ev._shape(which))):
+                raise ValueError("array for buffer %d has %d doubles, the event needs %d"
+                                 % (which, a.size, int(np.prod(ev._shape(which)))))
+            keep.append(a)
+        if len(keep) != self.ne:
+            raise ValueError("one array per event")
+        ptrs = (ctypes.c_void_p * self.ne)(*[a.ctypes.data for a in keep])
+        counts = (ctypes.c_size_t * self.ne)(*[a.size for a in keep])
+        self._chk(lib().gl_batch_upload(self.b, which, ptrs, counts), "gl_batch_upload")
 
     def observables(self, what=None):
         out = (gl_obs * self.ne)()

@@ -962,6 +962,33 @@ gl_status gl_batch_step_timed(gl_batch* b, int32_t n_steps, double* field_ms, do
     return GL_OK;
 }
 
+static gl_status ensure_aux(gl_batch* b);
+
+// events alternate between the batch stream and the second one (each event has
+// its own staging and sort buffers), so that one event's host copy overlaps
+// another's conversion and sort
+gl_status gl_batch_upload(gl_batch* b, gl_buffer which, const double* const* host, const size_t* count) {
+    if (!b || !host || !count) return GL_ERR_ARG;
+    if (gl_status s = ensure_aux(b)) return s;
+    cudaEventRecord(b->ev_a, b->stream);
+    cudaStreamWaitEvent(b->aux, b->ev_a, 0);
+    gl_status st = GL_OK;
+    int bad = -1;
+    for (int e = 0; e < b->ne && st == GL_OK; e++) {
+        st = ctx_upload_enqueue(b->ev[e], which, host[e], count[e], (e & 1) ? b->aux : b->stream);
+        if (st != GL_OK) bad = e;
+    }
+    cudaEventRecord(b->ev_b, b->aux);
+    cudaStreamWaitEvent(b->stream, b->ev_b, 0);
+    const bool ok = cudaStreamSynchronize(b->stream) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+    if (bad >= 0) {
+        char m[300];
+        snprintf(m, sizeof m, "event %d: %s", bad, gl_error_string(b->ev[bad]));
+        return bfail(b, st, m);
+    }
+    return ok ? GL_OK : bfail(b, GL_ERR_CUDA, "batch upload failed");
+}
+
 gl_status gl_batch_observables(gl_batch* b, gl_obs* out) { return gl_batch_observables_ex(b, GL_OBS_ALL, out); }
 
 gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {

@@ -73,6 +73,7 @@ extern "C" {
 static uint32_t active_mask(const gl_ctx* c, int64_t n);
 static void observables_launch(gl_ctx* c, uint32_t what);
 static gl_status observables_read(gl_ctx* c, uint32_t what, gl_obs* o);
+static gl_status transfer_enqueue(gl_ctx* c, gl_buffer which, double* host, size_t count, int to_device);
 static void observables_fill(const gl_ctx* c, uint32_t what, const double* host, gl_obs* o);
 }
 
@@ -214,6 +215,13 @@ void ctx_obs_event(const gl_ctx* c, ObsEvent* o) {
     o->out = c->obs_dev;
 }
 void ctx_obs_launch(gl_ctx* c, uint32_t what) { ::observables_launch(c, what); }
+gl_status ctx_upload_enqueue(gl_ctx* c, gl_buffer which, const double* host, size_t count, cudaStream_t st) {
+    const cudaStream_t own = c->stream;
+    c->stream = st;  // the copy, the conversion and a particle sort go to st
+    const gl_status s = ::transfer_enqueue(c, which, (double*)host, count, 1);
+    c->stream = own;
+    return s;
+}
 void ctx_obs_fill(const gl_ctx* c, uint32_t what, const double* host, gl_obs* o) {
     ::observables_fill(c, what, host, o);
 }
@@ -389,7 +397,9 @@ static size_t expected_count(const gl_ctx* c, gl_buffer which) {
     return 0;
 }
 
-static gl_status transfer(gl_ctx* c, gl_buffer which, double* host, size_t count, int to_device) {
+// the copies and conversions of one transfer, enqueued on the context's
+// stream (the caller waits)
+static gl_status transfer_enqueue(gl_ctx* c, gl_buffer which, double* host, size_t count, int to_device) {
     if (!c || (!host && count)) return GL_ERR_ARG;
     if ((int)which < 0 || (int)which > GL_BUF_PTAU) return fail(c, GL_ERR_ARG, "unknown buffer");
     if (count != expected_count(c, which)) return fail(c, GL_ERR_SIZE, "host buffer size does not match");
@@ -410,7 +420,11 @@ static gl_status transfer(gl_ctx* c, gl_buffer which, double* host, size_t count
     } else launch_convert(c->prec, which, to_device, which == GL_BUF_SITE ? site_at(c, c->pstep - 1) : c->field[c->cur], stg, c->N, c->np,
                         c->stream);
     if (!to_device) cudaMemcpyAsync(host, stg, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-    if (gl_status s = check_cuda(c, to_device ? "gl_upload" : "gl_download")) return s;
+    return check_cuda(c, to_device ? "gl_upload" : "gl_download");
+}
+
+static gl_status transfer(gl_ctx* c, gl_buffer which, double* host, size_t count, int to_device) {
+    if (gl_status s = transfer_enqueue(c, which, host, count, to_device)) return s;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, "transfer sync");
     return GL_OK;
 }
@@ -425,6 +439,14 @@ gl_status gl_download(gl_ctx* c, gl_buffer which, double* host, size_t count) {
 
 gl_status gl_set_step(gl_ctx* c, int64_t step) {
     if (!c || step < 0) return GL_ERR_ARG;
+    // the current fields stay current; their buffer takes the index of the
+    // new step's parity, as after any sequence of field steps
+    if ((int)(step & 1) != c->cur) {
+        void* f = c->field[0];
+        c->field[0] = c->field[1];
+        c->field[1] = f;
+        c->cur = (int)(step & 1);
+    }
     c->step = c->pstep = step;
     c->site_step = -1;
     // the re-unitarisation period counts from step 0, so a resumed run

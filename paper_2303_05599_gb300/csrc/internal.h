@@ -143,6 +143,8 @@ size_t ctx_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t n
 void ctx_obs_launch(gl_ctx* c, uint32_t what);
 // a gl_obs record from a host copy of that row
 void ctx_obs_fill(const gl_ctx* c, uint32_t what, const double* row, gl_obs* o);
+// gl_upload without its wait: copies, conversions and a particle sort enqueued on st
+gl_status ctx_upload_enqueue(gl_ctx* c, gl_buffer which, const double* host, size_t count, cudaStream_t st);
 
 // observable slots
 enum { PO_COUNT = 0, PO_PX2, PO_PY2, PO_PL2, PO_DPT2, PO_Q2, PO_Q3, PO_N };

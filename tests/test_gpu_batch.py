@@ -3,6 +3,7 @@ field launch and one push launch per step (CUDA-graph replays) give bitwise
 the same fields and particles as each event stepped on its own, for any tile
 shape the autotuner picks; ragged lattices (N not a multiple of the tile)
 included."""
+import ctypes
 import math
 
 import numpy as np
@@ -103,6 +104,37 @@ def test_observables_parts():
         for f in OBS_SCALARS:
             assert getattr(fld[e], f) == getattr(full[e], f)
             assert math.isnan(getattr(part[e], f))
+
+
+RESTORE_BUFS = (B.GL_BUF_LINKS, B.GL_BUF_PHI, B.GL_BUF_E, B.GL_BUF_PI, B.GL_BUF_PARTICLES)
+
+
+def test_batch_upload_restores_a_run():
+    """A batch restored with gl_batch_upload (one wait per buffer for all
+    events) from the downloads of another batch at step 7 evolves bitwise
+    like the uninterrupted one; a wrong size is rejected with GL_ERR_SIZE."""
+    ws = events(W.FP32_2ROW, sort_every=4)
+    a = B.Batch(ws)
+    b = B.Batch(ws)
+    with torch.cuda.stream(a.stream):
+        a.init()
+        a.step(7)
+        saved = {which: [ev.download(which) for ev in a.events] for which in RESTORE_BUFS}
+        a.step(6)
+    with torch.cuda.stream(b.stream):
+        b.init()
+        for which in RESTORE_BUFS:
+            b.upload(which, saved[which])
+        for ev in b.events:
+            ev.set_step(7)
+        b.step(6)
+        bad = [np.zeros(3)] * len(ws)
+        ptrs = (ctypes.c_void_p * len(ws))(*[x.ctypes.data for x in bad])
+        counts = (ctypes.c_size_t * len(ws))(*[x.size for x in bad])
+        assert B.lib().gl_batch_upload(b.b, B.GL_BUF_PHI, ptrs, counts) == B.GL_ERR_SIZE
+    for ea, eb in zip(a.events, b.events):
+        for which in RESTORE_BUFS:
+            assert np.array_equal(ea.download(which), eb.download(which))
 
 
 def test_batch_rejects_events_at_different_steps():
