@@ -64,6 +64,17 @@ TRAFFIC = {
 }
 
 
+# FP64 path: bound by the FP64 pipe (ncu: 90 % of its cycles active), so its
+# roofline is arithmetic.  Peak: 152 SMs x 2 FP64 FMA per clock x 2 flops x
+# 2.07 GHz = 1.26 TFLOP/s (NVIDIA's nominal 1.25).  Flops counted with ncu
+# (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on; 2 per DFMA) on
+# 8 events of the default workload: per site of the field step, and per
+# active particle of its half Wong, half static mix.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_FLOP_PER_SITE = 5938
+FP64_FLOP_PER_PARTICLE = 616
+
+
 def sort_launches(ws):
     """Kernels of one batched particle sort: keys, then per 8-bit digit pass a
     histogram, three scan kernels and a scatter, then the gather.  The passes
@@ -360,6 +371,13 @@ def run_ours(args):
             roof[name] = {"bound": "hbm", "achieved": b / t / 1e9, "peak": hbm, "unit": "GB/s",
                           "frac": b / t / 1e9 / hbm, "traffic": TRAFFIC.get((args.workload, len(ws), name, prec)),
                           "bytes_per_launch": b, "us_per_launch": t * 1e6, "peak_source": peak_src}
+        if prec == 0:
+            flops = {"field_step": FP64_FLOP_PER_SITE * sites, "wong_push": FP64_FLOP_PER_PARTICLE * n_active}
+            for name, (b, t) in kern.items():
+                roof[name] = {"bound": "alu", "achieved": flops[name] / t / 1e12, "peak": FP64_PEAK_TFLOPS,
+                              "unit": "TFLOP/s", "frac": flops[name] / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                              "flops_per_launch": flops[name], "us_per_launch": t * 1e6,
+                              "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 x 2.07 GHz"}
         dom = max(kern, key=lambda k: kern[k][1])
         single = args.workload != BATCHED
         line = {
