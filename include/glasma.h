@@ -30,7 +30,9 @@
  *   GL_BUF_E          [2][N*N][8]   e_x, e_y at n - 1/2
  *   GL_BUF_PI         [N*N][8]      pi at n - 1/2
  *   GL_BUF_SITE       [6][N*N][8]   E_x, E_y, E_eta, B_x, B_y, B_eta at the
- *                                   last pushed time t_{n-1} (download only)
+ *                                   last pushed time t_{n-1} (download only;
+ *                                   GL_ERR_STATE before the first push, or
+ *                                   when field steps since it overwrote them)
  *   GL_BUF_PARTICLES  [np][16]      x, y, eta, p^x, p^y, P_eta, Q^1..Q^8,
  *                                   p_T^2 at formation, species index;
  *                                   x, y in [0, N); P_eta = tau^2 p^eta
@@ -40,7 +42,8 @@
  *                                   W (3x3 complex, row-major re/im), X_x, X_y,
  *                                   X_z (8 components each), see gl_config
  *   GL_BUF_ENERGY     [N*N]         energy density of the Glasma fields at the
- *                                   last pushed time t_{n-1} (Figs. 6 and 9
+ *                                   last pushed time t_{n-1}, under the same
+ *                                   condition as GL_BUF_SITE (Figs. 6 and 9
  *                                   background): tr(E_x^2 + E_y^2 + E_eta^2 +
  *                                   B_x^2 + B_y^2 + B_eta^2) of the site fields,
  *                                   lattice units; the physical value is this
@@ -159,7 +162,8 @@ typedef struct {
     double unitarity_max;               /* max over links of ||U U^+ - 1||_F */
     double mean_trE_T2;                 /* lattice means of tr(E_x^2 + E_y^2), tr E_eta^2, */
     double mean_trE_L2;                 /* tr(B_x^2 + B_y^2), tr B_eta^2 at the last pushed */
-    double mean_trB_T2;                 /* time, lattice units (E^ = g a^2 E) */
+    double mean_trB_T2;                 /* time, lattice units (E^ = g a^2 E); NaN when */
+                                        /* GL_BUF_SITE could not be downloaded */
     double mean_trB_L2;
 } gl_obs;
 
@@ -306,7 +310,9 @@ gl_status gl_batch_init(gl_batch* batch);
  *     blocks per SM launched ahead of the field tiles (chunks of 1024), or
  *   - one persistent fused launch that interleaves field tiles and push
  *     chunks of 512, 1024 or 2048 particles.
- * Outputs may be NULL. */
+ * The push and whole-step trials run on copies of the particles in the spare
+ * particle buffers that sorting provides; if an event with particles has
+ * sort_every = 0, only the field tile shape is tuned.  Outputs may be NULL. */
 gl_status gl_batch_autotune(gl_batch* batch, int32_t* tile_shape, int32_t* push_block);
 
 /* Set the launch shapes and schedule directly (values as above: push_chunk

@@ -100,7 +100,7 @@ __device__ __forceinline__ void field_item(const BatchArgs& b, int blk) {
     const EvDesc& d = b.ev[s_e];
     const int64_t n = s_n;
     const int64_t Vn = (int64_t)d.N * d.N;
-    fused_tile<R, TX, TY, true>(carve_fields<R>(d.field[n & 1], Vn), carve_fields<R>(d.field[(n + 1) & 1], Vn),
+    fused_tile<R, TX, TY>(carve_fields<R>(d.field[n & 1], Vn), carve_fields<R>(d.field[(n + 1) & 1], Vn),
                                 (typename Prec<R>::V*)d.site[n & 1], s_a, blk - d.tile_begin);
 }
 
@@ -709,6 +709,7 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
     for (int e = 0; e < b->ne && have_copy; e++) {
         CtxView v;
         ctx_view(b->ev[e], &v);
+        if (v.np == 0) continue;  // nothing to push or copy
         if (!v.parts_alt) { have_copy = false; break; }
         cudaMemcpyAsync(v.parts_alt, v.parts, particle_bytes(b->prec, v.np), cudaMemcpyDeviceToDevice, b->stream);
         b->h_desc[e].parts = v.parts_alt;

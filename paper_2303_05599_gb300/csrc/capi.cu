@@ -56,7 +56,7 @@ struct gl_ctx {
     int* d_bad;
     int cur;
     int64_t step, pstep;
-    int64_t site_step;  // particle step whose site fields are in `site` (-1: none)
+    int64_t site_time[2];  // time index n whose site fields site_buf[n & 1] holds (-1: none)
     int tile;           // fused-kernel tile shape (gl_autotune)
     int push_block;     // push block size (gl_autotune)
     float tune_field_ms[4], tune_push_ms[3];
@@ -68,6 +68,10 @@ static char g_create_err[256] = "";
 
 // site-field buffer of time t_n
 static inline void* site_at(const gl_ctx* c, int64_t n) { return c->site_buf[n & 1]; }
+// the site fields of time n are held (written by a field step or site_once
+// and not overwritten since)
+static inline bool site_holds(const gl_ctx* c, int64_t n) { return n >= 0 && c->site_time[n & 1] == n; }
+static inline void site_forget(gl_ctx* c) { c->site_time[0] = c->site_time[1] = -1; }
 
 extern "C" {
 static uint32_t active_mask(const gl_ctx* c, int64_t n);
@@ -195,7 +199,10 @@ void ctx_advance(gl_ctx* c, int64_t steps) {
     c->step += steps;
     c->pstep += steps;
     c->cur = (int)(c->step & 1);
-    c->site_step = c->pstep - 1;
+    // the last push of the batch read the site fields of pstep - 1, written
+    // by the field step of that time; the other buffer is not tracked
+    c->site_time[(c->pstep - 1) & 1] = c->pstep - 1;
+    c->site_time[c->pstep & 1] = -1;
     if (c->prec == GL_FP32_2ROW && c->cfg.reunit_every > 0)
         c->reunit_count = (int)(c->step % c->cfg.reunit_every);
 }
@@ -306,7 +313,7 @@ gl_status gl_create(const gl_config* cfg, const gl_species* sp, int32_t ns, void
     }
     c->cur = 0;
     c->step = c->pstep = 0;
-    c->site_step = -1;
+    site_forget(c);
     c->tile = 0;
     c->push_block = 128;
     *out = c;
@@ -362,7 +369,7 @@ gl_status glasma_init(gl_ctx* c) {
     cudaMemcpyAsync(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, "glasma_init sync");
     c->step = c->pstep = 0;
-    c->site_step = -1;
+    site_forget(c);
     c->reunit_count = 0;
     if (bad) {
         char m[128];
@@ -405,6 +412,9 @@ static gl_status transfer_enqueue(gl_ctx* c, gl_buffer which, double* host, size
     if (count != expected_count(c, which)) return fail(c, GL_ERR_SIZE, "host buffer size does not match");
     if (to_device && (which == GL_BUF_SITE || which == GL_BUF_ENERGY))
         return fail(c, GL_ERR_ARG, "site fields and energy density are download-only");
+    if ((which == GL_BUF_SITE || which == GL_BUF_ENERGY) && !site_holds(c, c->pstep - 1))
+        return fail(c, GL_ERR_STATE, "the site fields of the last pushed time are not held (no push yet, or later "
+                                     "field steps overwrote them)");
     if (count == 0) return GL_OK;
     double* stg = (double*)c->scratch;
     if (to_device) cudaMemcpyAsync(stg, host, count * sizeof(double), cudaMemcpyHostToDevice, c->stream);
@@ -448,31 +458,30 @@ gl_status gl_set_step(gl_ctx* c, int64_t step) {
         c->cur = (int)(step & 1);
     }
     c->step = c->pstep = step;
-    c->site_step = -1;
+    site_forget(c);
     // the re-unitarisation period counts from step 0, so a resumed run
     // re-unitarises at the same steps as an uninterrupted one
     if (c->prec == GL_FP32_2ROW && c->cfg.reunit_every > 0) c->reunit_count = (int)(step % c->cfg.reunit_every);
     return GL_OK;
 }
 
-// One leapfrog step on stream st.  When the particles are at the fields'
-// time the same kernel also interpolates E, B at that time for the push.
-static void one_field_step(gl_ctx* c, bool site, cudaStream_t st) {
+// One leapfrog step on stream st; the same kernel interpolates E, B at the
+// fields' time t_step into the site buffer of that time's parity.
+static void one_field_step(gl_ctx* c, cudaStream_t st) {
     int reunit = 0;
     if (c->prec == GL_FP32_2ROW && c->cfg.reunit_every > 0) {
         if (++c->reunit_count >= c->cfg.reunit_every) { reunit = 1; c->reunit_count = 0; }
     }
-    site = site && c->pstep == c->step;
-    launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], site ? site_at(c, c->step) : nullptr, c->N,
-                      c->step, c->dt, reunit, c->tile, st);
-    if (site) c->site_step = c->pstep;
+    launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], site_at(c, c->step), c->N, c->step, c->dt,
+                      reunit, c->tile, st);
+    c->site_time[c->step & 1] = c->step;
     c->cur = 1 - c->cur;
     c->step++;
 }
 
 gl_status glasma_step(gl_ctx* c, int32_t n) {
     if (!c || n < 0) return GL_ERR_ARG;
-    for (int k = 0; k < n; k++) one_field_step(c, k == n - 1 && c->np > 0, c->stream);
+    for (int k = 0; k < n; k++) one_field_step(c, c->stream);
     return check_cuda(c, "glasma_step");
 }
 
@@ -480,13 +489,13 @@ static gl_status site_once(gl_ctx* c) {
     if (c->pstep != c->step - 1) return fail(c, GL_ERR_STATE, "needs exactly one field step since the particles' time");
     launch_site_fields(c->prec, c->field[1 - c->cur], c->field[c->cur], site_at(c, c->pstep), c->N, c->pstep * c->dt,
                        c->stream);
-    c->site_step = c->pstep;
+    c->site_time[c->pstep & 1] = c->pstep;
     return GL_OK;
 }
 
 gl_status wong_site_fields(gl_ctx* c) {
     if (!c) return GL_ERR_ARG;
-    if (c->site_step == c->pstep && c->pstep == c->step - 1) return GL_OK;  // written by the field step
+    if (site_holds(c, c->pstep) && c->pstep == c->step - 1) return GL_OK;  // written by the field step
     if (gl_status s = site_once(c)) return s;
     return check_cuda(c, "wong_site_fields");
 }
@@ -511,7 +520,7 @@ static gl_status push_once(gl_ctx* c, cudaStream_t st, void* bn1) {
 gl_status wong_push(gl_ctx* c) {
     if (!c) return GL_ERR_ARG;
     if (c->pstep != c->step - 1) return fail(c, GL_ERR_STATE, "wong_push needs exactly one field step since the particles' time");
-    if (c->site_step != c->pstep)
+    if (!site_holds(c, c->pstep))
         if (gl_status s = site_once(c)) return s;
     if (gl_status s = push_once(c, c->stream, c->field[c->cur])) return s;
     return check_cuda(c, "wong_push");
@@ -537,12 +546,12 @@ gl_status gl_step_coupled(gl_ctx* c, int32_t n) {
     if (n == 0) return GL_OK;
     if (c->pstep != c->step) return fail(c, GL_ERR_STATE, "particles are not at the fields' time");
     if (c->np == 0) {
-        for (int k = 0; k < n; k++) one_field_step(c, false, c->stream);
+        for (int k = 0; k < n; k++) one_field_step(c, c->stream);
         c->pstep = c->step;
         return check_cuda(c, "gl_step_coupled");
     }
     if (gl_status s = ensure_aux(c)) return s;
-    one_field_step(c, true, c->stream);
+    one_field_step(c, c->stream);
     for (int k = 1; k <= n; k++) {
         cudaEventRecord(c->ev_f, c->stream);          // field step of pstep + 1 done
         cudaStreamWaitEvent(c->aux, c->ev_f, 0);
@@ -550,7 +559,7 @@ gl_status gl_step_coupled(gl_ctx* c, int32_t n) {
         if (gl_status s = push_once(c, c->aux, bn1)) return s;
         if (k == n) break;
         if (k >= 2) cudaStreamWaitEvent(c->stream, c->ev_p, 0);  // push of the step before
-        one_field_step(c, true, c->stream);
+        one_field_step(c, c->stream);
         cudaEventRecord(c->ev_p, c->aux);
     }
     cudaEventRecord(c->ev_p, c->aux);
@@ -584,7 +593,7 @@ gl_status gl_autotune(gl_ctx* c, int32_t* tile_out, int32_t* push_block_out) {
     for (int k = 0; k < 4; k++) {
         if (c->prec == GL_FP64 && (k == 0 || k == 3)) { c->tune_field_ms[k] = 0; continue; }
         const float ms = timed([&] {
-            launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], c->np ? site_at(c, c->step) : nullptr, c->N, c->step,
+            launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], site_at(c, c->step), c->N, c->step,
                               c->dt, 0, tiles[k], c->stream);
         });
         c->tune_field_ms[k] = ms;
@@ -611,7 +620,7 @@ gl_status gl_autotune(gl_ctx* c, int32_t* tile_out, int32_t* push_block_out) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->site_step = -1;
+    c->site_time[c->step & 1] = -1;  // trial field launches wrote that buffer
     if (tile_out) *tile_out = c->tile;
     if (push_block_out) *push_block_out = c->push_block;
     return check_cuda(c, "gl_autotune");
@@ -673,10 +682,12 @@ static void observables_fill(const gl_ctx* c, uint32_t what, const double* host,
     o->gauss_max = F ? f[FO_GMAX] : NAN;
     o->gauss_rms = F ? sqrt(f[FO_GSUM] / (double)c->Vn) : NAN;
     o->unitarity_max = F ? f[FO_UMAX] : NAN;
-    o->mean_trE_T2 = F ? f[FO_ET2] / (double)c->Vn : NAN;
-    o->mean_trE_L2 = F ? f[FO_EL2] / (double)c->Vn : NAN;
-    o->mean_trB_T2 = F ? f[FO_BT2] / (double)c->Vn : NAN;
-    o->mean_trB_L2 = F ? f[FO_BL2] / (double)c->Vn : NAN;
+    // the means of the squared site fields refer to the last pushed time
+    const bool S = F && site_holds(c, c->pstep - 1);
+    o->mean_trE_T2 = S ? f[FO_ET2] / (double)c->Vn : NAN;
+    o->mean_trE_L2 = S ? f[FO_EL2] / (double)c->Vn : NAN;
+    o->mean_trB_T2 = S ? f[FO_BT2] / (double)c->Vn : NAN;
+    o->mean_trB_L2 = S ? f[FO_BL2] / (double)c->Vn : NAN;
 }
 
 gl_status observables(gl_ctx* c, gl_obs* o) { return gl_observables_ex(c, GL_OBS_ALL, o); }

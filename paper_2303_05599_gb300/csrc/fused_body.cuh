@@ -4,7 +4,7 @@
 // One CTA owns a TX x TY tile of sites (TX = 32: one warp per tile row).  Per
 // step it computes, from U(n), phi(n), e(n-1/2), pi(n-1/2):
 //   the momenta e(n+1/2), pi(n+1/2), the links U(n+1) and the scalar phi(n+1),
-//   and (SITE) the site fields E, B at t_n that the particle push gathers.
+//   and the site fields E, B at t_n that the particle push gathers.
 // Every cell plaquette is formed once per tile and shared.  With
 //   A(c)  = components of i[P(c)]_ah,  P(c) = Ux(c) Uy(c+x) Ux(c+y)^+ Uy(c)^+,
 //   Dn(s) = Uy(s-y)^+ A(s-y) Uy(s-y),   Lf(s) = Ux(s-x)^+ A(s-x) Ux(s-x),
@@ -217,7 +217,7 @@ __host__ __device__ inline StepR<R> step_r(const StepArgs& a) {
 
 // one tile (index `tile` of a lattice with tiles_x tiles per row); the caller
 // provides the dynamic shared memory of Tile<R, TX, TY>::bytes
-template <typename R, int TX, int TY, bool SITE>
+template <typename R, int TX, int TY>
 __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>& out, typename Prec<R>::V* site,
                                            const StepR<R>& a, int tile) {
     using T = Tile<R, TX, TY>;
@@ -377,30 +377,31 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
             p_new.v[c] = p_old.v[c] + dt * inv_t * lap;
             ph_new.v[c] = ph.v[c] + a.dt_th * p_new.v[c];
         }
-        if (SITE) {
-            // E_i = (1/4t){e_i(s) + U_i(s-i)^+ e_i(s-i) U_i(s-i)}, e summed over n -+ 1/2
-            const A8<R> sx = conj_dn(Ux_m, s_alg(sEs, es - 1, EN));
-            const A8<R> sy = conj_dn(Uy_m, s_alg(sEs + AP * EN, es - EW, EN));
-            const A8<R> hx = s_alg(sEs, es, EN), hy = s_alg(sEs + AP * EN, es, EN);
-            const A8<R> cr = conj_dn(Uy_m, s_alg(sLf, es - EW, EN));
-            A8<R> Ex, Ey, Ee, Bx, By, Be;
-            const R q = R(0.25) * inv_t, hf = R(0.5) * inv_t;
+        // the site fields of t_n, written by every field step (one code path for
+        // every caller, so the fields evolve bitwise alike whether or not the
+        // site fields are used)
+        // E_i = (1/4t){e_i(s) + U_i(s-i)^+ e_i(s-i) U_i(s-i)}, e summed over n -+ 1/2
+        const A8<R> sx = conj_dn(Ux_m, s_alg(sEs, es - 1, EN));
+        const A8<R> sy = conj_dn(Uy_m, s_alg(sEs + AP * EN, es - EW, EN));
+        const A8<R> hx = s_alg(sEs, es, EN), hy = s_alg(sEs + AP * EN, es, EN);
+        const A8<R> cr = conj_dn(Uy_m, s_alg(sLf, es - EW, EN));
+        A8<R> Ex, Ey, Ee, Bx, By, Be;
+        const R q = R(0.25) * inv_t, hf = R(0.5) * inv_t;
 #pragma unroll
-            for (int c = 0; c < 8; c++) {
-                Ex.v[c] = q * (hx.v[c] + sx.v[c]);
-                Ey.v[c] = q * (hy.v[c] + sy.v[c]);
-                Ee.v[c] = R(0.5) * (p_old.v[c] + p_new.v[c]);
-                Bx.v[c] = -hf * (my_ty.v[c] - by.v[c]);
-                By.v[c] = hf * (my_tx.v[c] - bx.v[c]);
-                Be.v[c] = R(0.25) * (my_b.v[c] + cr.v[c]);
-            }
-            store_alg(site, g, Vn, Ex);
-            store_alg(site + (size_t)1 * AP * Vn, g, Vn, Ey);
-            store_alg(site + (size_t)2 * AP * Vn, g, Vn, Ee);
-            store_alg(site + (size_t)3 * AP * Vn, g, Vn, Bx);
-            store_alg(site + (size_t)4 * AP * Vn, g, Vn, By);
-            store_alg(site + (size_t)5 * AP * Vn, g, Vn, Be);
+        for (int c = 0; c < 8; c++) {
+            Ex.v[c] = q * (hx.v[c] + sx.v[c]);
+            Ey.v[c] = q * (hy.v[c] + sy.v[c]);
+            Ee.v[c] = R(0.5) * (p_old.v[c] + p_new.v[c]);
+            Bx.v[c] = -hf * (my_ty.v[c] - by.v[c]);
+            By.v[c] = hf * (my_tx.v[c] - bx.v[c]);
+            Be.v[c] = R(0.25) * (my_b.v[c] + cr.v[c]);
         }
+        store_alg(site, g, Vn, Ex);
+        store_alg(site + (size_t)1 * AP * Vn, g, Vn, Ey);
+        store_alg(site + (size_t)2 * AP * Vn, g, Vn, Ee);
+        store_alg(site + (size_t)3 * AP * Vn, g, Vn, Bx);
+        store_alg(site + (size_t)4 * AP * Vn, g, Vn, By);
+        store_alg(site + (size_t)5 * AP * Vn, g, Vn, Be);
         store_alg(out.e, g, Vn, my_ex);
         store_alg(out.e + (size_t)AP * Vn, g, Vn, my_ey);
         store_alg(out.pi, g, Vn, p_new);

@@ -19,8 +19,8 @@ struct SpeciesParams {
     int ptau_diag;                 // GL_CFG_PTAU_DIAGNOSTIC
 };
 
-// field step n -> n+1 on buffers in/out (FP64 or FP32 two-row layout); when
-// site is not null the same kernel also writes the site E, B at t_n
+// field step n -> n+1 on buffers in/out (FP64 or FP32 two-row layout); the
+// same kernel also writes the site E, B at t_n into site (not null)
 // tile: 0 = 32x8, 1 = 32x4, 2 = 32x2, 3 = 32x16 (FP64: 32x4 for 0, 1 and 3)
 void launch_fused_step(int prec, void* in, void* out, void* site, int N, int64_t n, double dt, int reunit, int tile,
                        cudaStream_t st);

@@ -106,6 +106,34 @@ def test_observables_parts():
             assert math.isnan(getattr(part[e], f))
 
 
+def test_batch_with_an_event_without_particles():
+    """An event whose species are all empty sits in a batch beside normal
+    events: it gets no push chunks and no sort, zero sums, and every event
+    still evolves bitwise as it does alone."""
+    ws = events(W.FP32_2ROW, sort_every=3)[:3]
+    empty = ws[1]
+    empty.species = [W.Species(s.mass_GeV, s.tau_form_fm, 0, s.rep, s.mom_mode, s.p0_GeV, s.p1_GeV)
+                     for s in empty.species]
+    batch = B.Batch(ws)
+    with torch.cuda.stream(batch.stream):
+        batch.init()
+        batch.autotune()
+        batch.step(8)
+        obs = batch.observables()
+        singles = []
+        for w in ws:
+            ev = B.Event(w, stream=batch.stream)
+            ev.glasma_init()
+            ev.wong_init()
+            ev.step(8)
+            singles.append(ev)
+    assert list(obs[1].n_active)[:2] == [0, 0]
+    assert list(obs[1].sum_px2)[:2] == [0.0, 0.0]
+    for eb, es in zip(batch.events, singles):
+        for which in (B.GL_BUF_LINKS, B.GL_BUF_E, B.GL_BUF_PHI, B.GL_BUF_PARTICLES):
+            assert np.array_equal(eb.download(which), es.download(which))
+
+
 RESTORE_BUFS = (B.GL_BUF_LINKS, B.GL_BUF_PHI, B.GL_BUF_E, B.GL_BUF_PI, B.GL_BUF_PARTICLES)
 
 

@@ -315,6 +315,29 @@ def test_cell_edge_ties_and_degenerate_momenta():
     assert np.all(np.isfinite(got))
 
 
+@pytest.mark.parametrize("prec", [W.FP64, W.FP32_2ROW])
+def test_fields_independent_of_the_particles(prec):
+    """The fields do not feel the particles: coupled steps, fields-only steps
+    and an event without particles evolve them bitwise alike (one field
+    kernel writes the site fields on every path).  Site fields overwritten by
+    later field steps are not handed out."""
+    def make(count):
+        return wl(40, prec=prec, species=[W.Species(W.M_CHARM, 0.06, count, W.REP_F, W.MOM_UNIFORM_PT, 0.0, 5.0)])
+    a = B.Event(make(300)); a.glasma_init(); a.wong_init(); a.step(8)
+    b = B.Event(make(300)); b.glasma_init(); b.wong_init(); b.glasma_step(8)
+    c = B.Event(make(0)); c.glasma_init(); c.step(8)
+    for which in (B.GL_BUF_LINKS, B.GL_BUF_E, B.GL_BUF_PHI, B.GL_BUF_PI):
+        ref = a.download(which)
+        assert np.array_equal(ref, b.download(which)) and np.array_equal(ref, c.download(which))
+    a.download(B.GL_BUF_SITE)                 # the last push's site fields are held
+    for ev in (a, c):
+        ev.glasma_step(2)                     # overwrites the buffer of that time's parity
+        with pytest.raises(B.GlasmaError) as e:
+            ev.download(B.GL_BUF_SITE)
+        assert e.value.status == B.GL_ERR_STATE
+        assert math.isnan(ev.observables().mean_trE_T2)
+
+
 def test_call_order_errors():
     w = wl(8, species=[W.Species(W.M_CHARM, 0.0, 4)])
     ev = B.Event(w)
