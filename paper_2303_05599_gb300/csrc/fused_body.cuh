@@ -319,8 +319,8 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
         const A8<R> A0 = s_alg(sA, e, EN);
         const A8<R> ph = s_alg(sPhi, l, LN);
         if (wx) {
-            const A8<R> Dn = conj_dn(lk(1, l - LW), s_alg(sA, e - EW, EN));
-            const A8<R> tx = conj_up(lk(0, l), s_alg(sPhi, l + 1, LN));
+            const A8<R> Dn = conj_dn_t(lk(1, l - LW), s_alg(sA, e - EW, EN));
+            const A8<R> tx = conj_up_t(lk(0, l), s_alg(sPhi, l + 1, LN));
             const A8<R> cx = icomm(tx, ph);
             const A8<R> eox = s_alg(sEs, e, EN);
             A8<R> ex_n, sx;
@@ -338,8 +338,8 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
             }
         }
         if (wy) {
-            const A8<R> Lf = conj_dn(lk(0, l - 1), s_alg(sA, e - 1, EN));
-            const A8<R> ty = conj_up(lk(1, l), s_alg(sPhi, l + LW, LN));
+            const A8<R> Lf = conj_dn_t(lk(0, l - 1), s_alg(sA, e - 1, EN));
+            const A8<R> ty = conj_up_t(lk(1, l), s_alg(sPhi, l + LW, LN));
             const A8<R> cy = icomm(ty, ph);
             const A8<R> eoy = s_alg(sEs + AP * EN, e, EN);
             A8<R> ey_n, sy;
@@ -368,8 +368,8 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
         const A8<R> ph = s_alg(sPhi, ls, LN);
         const M3<R> Ux_m = lk(0, ls - 1);
         const M3<R> Uy_m = lk(1, ls - LW);
-        const A8<R> bx = conj_dn(Ux_m, s_alg(sPhi, ls - 1, LN));
-        const A8<R> by = conj_dn(Uy_m, s_alg(sPhi, ls - LW, LN));
+        const A8<R> bx = conj_dn_t(Ux_m, s_alg(sPhi, ls - 1, LN));
+        const A8<R> by = conj_dn_t(Uy_m, s_alg(sPhi, ls - LW, LN));
         A8<R> p_new, ph_new;
 #pragma unroll
         for (int c = 0; c < 8; c++) {
@@ -381,10 +381,10 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
         // every caller, so the fields evolve bitwise alike whether or not the
         // site fields are used)
         // E_i = (1/4t){e_i(s) + U_i(s-i)^+ e_i(s-i) U_i(s-i)}, e summed over n -+ 1/2
-        const A8<R> sx = conj_dn(Ux_m, s_alg(sEs, es - 1, EN));
-        const A8<R> sy = conj_dn(Uy_m, s_alg(sEs + AP * EN, es - EW, EN));
+        const A8<R> sx = conj_dn_t(Ux_m, s_alg(sEs, es - 1, EN));
+        const A8<R> sy = conj_dn_t(Uy_m, s_alg(sEs + AP * EN, es - EW, EN));
         const A8<R> hx = s_alg(sEs, es, EN), hy = s_alg(sEs + AP * EN, es, EN);
-        const A8<R> cr = conj_dn(Uy_m, s_alg(sLf, es - EW, EN));
+        const A8<R> cr = conj_dn_t(Uy_m, s_alg(sLf, es - EW, EN));
         A8<R> Ex, Ey, Ee, Bx, By, Be;
         const R q = R(0.25) * inv_t, hf = R(0.5) * inv_t;
 #pragma unroll

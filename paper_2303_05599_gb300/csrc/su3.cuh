@@ -294,10 +294,69 @@ __device__ __forceinline__ A8<R> conj_dn(const M3<R>& V, const A8<R>& x) {
     return o;
 }
 
+// conj_dn without the (2, 2) entry of the product: V^+ X V is traceless like
+// X, so its eighth component follows from the first two diagonal entries
+// (the same value up to rounding, six fused multiply-adds fewer).  Used by
+// the field step, where the transports are the bulk of the arithmetic.
+template <typename R>
+__device__ __forceinline__ A8<R> conj_dn_t(const M3<R>& V, const A8<R>& x) {
+    const M3<R> X = alg_to_mat2(x);
+    M3<R> Y;  // X V, with X's diagonal real
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            R sr = X.re[i][i] * V.re[i][j], si = X.re[i][i] * V.im[i][j];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (k == i) continue;
+                sr = fma(X.re[i][k], V.re[k][j], sr);
+                sr = fma(-X.im[i][k], V.im[k][j], sr);
+                si = fma(X.re[i][k], V.im[k][j], si);
+                si = fma(X.im[i][k], V.re[k][j], si);
+            }
+            Y.re[i][j] = sr;
+            Y.im[i][j] = si;
+        }
+    R zr[3][3], zi[3][3];  // V^+ Y, upper triangle but (2, 2)
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = i; j < 3; j++) {
+            R sr = R(0), si = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                sr = fma(V.re[k][i], Y.re[k][j], sr);
+                sr = fma(V.im[k][i], Y.im[k][j], sr);
+                if (i != j) {
+                    si = fma(V.re[k][i], Y.im[k][j], si);
+                    si = fma(-V.im[k][i], Y.re[k][j], si);
+                }
+            }
+            zr[i][j] = sr;
+            zi[i][j] = si;
+        }
+    A8<R> o;
+    o.v[0] = zr[0][1];
+    o.v[1] = -zi[0][1];
+    o.v[2] = R(0.5) * (zr[0][0] - zr[1][1]);
+    o.v[3] = zr[0][2];
+    o.v[4] = -zi[0][2];
+    o.v[5] = zr[1][2];
+    o.v[6] = -zi[1][2];
+    // (Z00 + Z11 - 2 Z22) / sqrt 3 with Z22 = -(Z00 + Z11), halved for 2X
+    o.v[7] = (zr[0][0] + zr[1][1]) * R(0.86602540378443864676);
+    return o;
+}
+
 // components of V X V^+ for Hermitian X
 template <typename R>
 __device__ __forceinline__ A8<R> conj_up(const M3<R>& V, const A8<R>& x) {
     return conj_dn(dag(V), x);
+}
+template <typename R>
+__device__ __forceinline__ A8<R> conj_up_t(const M3<R>& V, const A8<R>& x) {
+    return conj_dn_t(dag(V), x);
 }
 
 // X^2 for Hermitian X: the upper triangle is formed, the lower one mirrored
