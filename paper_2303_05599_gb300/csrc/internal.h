@@ -76,7 +76,7 @@ void launch_jets_obs(int prec, const void* jets, int64_t n, double* partials, do
 // canonical FP64 <-> device probes
 void launch_jets_convert(int prec, void* jets, int64_t n, double* stg, int to_device, cudaStream_t st);
 
-// counting sort of the particles by row, motion class and cell from src into dst (same layout)
+// radix sort of the particles by row, motion class and cell from src into dst (same layout)
 void launch_sort(int prec, void* src, void* dst, int64_t np, int N, int ns, const int* motion, void* scratch,
                  cudaStream_t st);
 // one event of a batched sort; pblk_begin / cblk_begin: its first block in the
