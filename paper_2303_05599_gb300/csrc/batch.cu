@@ -753,7 +753,9 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
             for (int tile = 0; tile < N_TILES; tile++) {
                 if (b->prec == GL_FP64 && tile != TILE_32x4) continue;
                 if (g == 0 && tile != tile0) continue;
-                if (tile == TILE_32x16) continue;
+                // resident push blocks (g > 0) leave no room beside the
+                // 512-thread tiles; the plain two-stream step takes any tile
+                if (g > 0 && tile == TILE_32x16) continue;
                 b->tile = tile;
                 float best_g = 1e30f;
                 for (int kc = 0; kc < (g == 0 ? N_SEP_CHUNKS : 1); kc++) {
