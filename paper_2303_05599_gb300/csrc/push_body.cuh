@@ -108,13 +108,22 @@ __device__ __forceinline__ void push_one(const typename Prec<R>::V* __restrict__
     if (yn < R(0)) yn += (R)N;
     p.x = xn;
     p.y = yn;
-    // CPIC: rotate with the crossed links at t_{n+1}, x first, then y
+    // CPIC: rotate with the crossed links at t_{n+1}, x first, then y.  A step
+    // up takes U^+ Q U with the link of the old cell, a step down U Q U^+ =
+    // (U^+)^+ Q U^+ with the link of the new cell: one transport per axis,
+    // with U or U^+ chosen per lane, so that a warp runs it once whichever
+    // way its lanes cross (crossings are rare, but some lane of a warp crosses
+    // almost every step)
     const int dxc = jxu - ixu, dyc = jyu - iyu;
     const int jx = wrapi(jxu, N), jy = wrapi(jyu, N);
-    if (dxc == 1) p.q = conj_dn(load_link(bn1.U, 0, cell, Vn), p.q);
-    else if (dxc == -1) p.q = conj_up(load_link(bn1.U, 0, (int64_t)iy * N + jx, Vn), p.q);
-    if (dyc == 1) p.q = conj_dn(load_link(bn1.U, 1, (int64_t)iy * N + jx, Vn), p.q);
-    else if (dyc == -1) p.q = conj_up(load_link(bn1.U, 1, (int64_t)jy * N + jx, Vn), p.q);
+    if (dxc == 1 || dxc == -1) {
+        const M3<R> U = load_link(bn1.U, 0, dxc == 1 ? cell : (int64_t)iy * N + jx, Vn);
+        p.q = conj_dn(dxc == 1 ? U : dag(U), p.q);
+    }
+    if (dyc == 1 || dyc == -1) {
+        const M3<R> U = load_link(bn1.U, 1, dyc == 1 ? (int64_t)iy * N + jx : (int64_t)jy * N + jx, Vn);
+        p.q = conj_dn(dyc == 1 ? U : dag(U), p.q);
+    }
     // rapidity Wilson line at the new cell: Q <- e^{-i deta phi} Q e^{+i deta phi}
     if (deta != R(0)) {
         const A8<R> ph = load_alg(bn1.phi, (int64_t)jy * N + jx, Vn);
