@@ -59,8 +59,8 @@ BATCHED = "batched64"
 # workload for the current kernels (profiles/launches_default_30x256.md).
 # Absent: not captured for the current kernels.
 TRAFFIC = {
-    ("n256_charm_static", 30, "field_step", 1): 440526848 + 759340544,
-    ("n256_charm_static", 30, "wong_push", 1): 874971136 + 217174016,
+    ("n256_charm_static", 30, "field_step", 1): 440528640 + 759451392,
+    ("n256_charm_static", 30, "wong_push", 1): 873888768 + 217574144,
 }
 
 
