@@ -106,6 +106,64 @@ def test_observables_parts():
             assert math.isnan(getattr(part[e], f))
 
 
+def _rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(1e-300, np.abs(b).max()))
+
+
+@pytest.mark.parametrize("workload", ["n256_charm_static", "batched64"])
+def test_full_size_batch_step_against_the_oracle(workload):
+    """The benchmark's configuration at full size: its events (30 x 256^2,
+    or the 64 events of 64/128/256), autotuned launch shapes, CUDA-graph
+    steps until every species is formed; then one more batched step of
+    sampled events (one per lattice size) against one oracle step from their
+    downloaded states.  FP32 two-row: 2e-5 relative on every field, the site
+    fields and the particles away from cell edges."""
+    import oracle as O
+    if workload == "batched64":
+        ws = W.config_batched_events()
+        sample = [min(i for i, v in enumerate(ws) if v.N == N) for N in (64, 128, 256)]
+    else:
+        ws = []
+        for e in range(30):
+            w = W.config_n256()
+            w.seed = e
+            ws.append(w)
+        sample = [0, 29]
+    batch = B.Batch(ws)
+    n_form = max(int(math.ceil(sp.tau_form_fm / (w.dtau_over_a * w.a_fm) - 1e-9)) for w in ws for sp in w.species)
+    with torch.cuda.stream(batch.stream):
+        batch.init()
+        batch.autotune()
+        batch.step(n_form + 1)
+        saved = {}
+        for e in sample:
+            ev = batch.events[e]
+            st = O.FieldState(ev.N, ev.download(B.GL_BUF_LINKS), ev.download(B.GL_BUF_PHI),
+                              ev.download(B.GL_BUF_E), ev.download(B.GL_BUF_PI))
+            saved[e] = (st, ev.download(B.GL_BUF_PARTICLES))
+        batch.step(1)
+    for e in sample:
+        w, ev = ws[e], batch.events[e]
+        st, part = saved[e]
+        ls = w.lattice_species()
+        kind = O.kinds_of([s[0] for s in ls], [s.mom_mode for s in w.species])
+        run = O.Run(st, part.copy(), [s[0] for s in ls], [s[1] for s in ls], [s.rep for s in w.species], w.dt,
+                    step=n_form + 1, kind=kind)
+        run.step()
+        errs = [_rel(ev.download(B.GL_BUF_LINKS), run.st.U), _rel(ev.download(B.GL_BUF_E), run.st.e),
+                _rel(ev.download(B.GL_BUF_PHI), run.st.phi), _rel(ev.download(B.GL_BUF_PI), run.st.pi),
+                _rel(ev.download(B.GL_BUF_SITE), run.site)]
+        got = ev.download(B.GL_BUF_PARTICLES)
+
+        def near_edge(x):
+            f = (x + 0.5) % 1.0
+            return (np.minimum(f, 1 - f) < 1e-3).any(axis=1)
+        keep = ~(near_edge(part[:, :2]) | near_edge(run.part[:, :2]))
+        perr = [_rel(got[keep, sl], run.part[keep, sl]) for sl in (slice(0, 2), slice(3, 5), slice(5, 6), slice(6, 14))]
+        print(workload, "event", e, "N", w.N, "errors", errs, perr, "compared", int(keep.sum()), "of", len(keep))
+        assert max(errs) < 2e-5 and max(perr) < 2e-5
+
+
 def test_batch_with_an_event_without_particles():
     """An event whose species are all empty sits in a batch beside normal
     events: it gets no push chunks and no sort, zero sums, and every event
