@@ -402,16 +402,16 @@ __device__ __forceinline__ void fused_tile(const Fields<R>& in, const Fields<R>&
         store_alg(site + (size_t)3 * AP * Vn, g, Vn, Bx);
         store_alg(site + (size_t)4 * AP * Vn, g, Vn, By);
         store_alg(site + (size_t)5 * AP * Vn, g, Vn, Be);
-        store_alg(out.e, g, Vn, my_ex);
-        store_alg(out.e + (size_t)AP * Vn, g, Vn, my_ey);
-        store_alg(out.pi, g, Vn, p_new);
-        store_alg(out.phi, g, Vn, ph_new);
+        store_alg_cs(out.e, g, Vn, my_ex);
+        store_alg_cs(out.e + (size_t)AP * Vn, g, Vn, my_ey);
+        store_alg_cs(out.pi, g, Vn, p_new);
+        store_alg_cs(out.phi, g, Vn, ph_new);
         M3<R> nx = mul(exp_i_alg<R, ExpN<R>::n>(my_ex, a.dt_over_th), lk(0, ls));
         if (a.reunit) reunit(nx);
-        store_link(out.U, 0, g, Vn, nx);
+        store_link_cs(out.U, 0, g, Vn, nx);
         M3<R> ny = mul(exp_i_alg<R, ExpN<R>::n>(my_ey, a.dt_over_th), lk(1, ls));
         if (a.reunit) reunit(ny);
-        store_link(out.U, 1, g, Vn, ny);
+        store_link_cs(out.U, 1, g, Vn, ny);
     }
 }
 

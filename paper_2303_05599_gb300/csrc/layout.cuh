@@ -122,6 +122,29 @@ __device__ __forceinline__ void store_alg(float4* A, int64_t s, int64_t Vn, cons
     A[Vn + s] = make_float4(x.v[4], x.v[5], x.v[6], x.v[7]);
 }
 
+// the same stores with the streaming (evict-first) cache hint: for values the
+// next launch reads long after they have left L2, so that they do not push
+// out lines that are still to be read
+__device__ __forceinline__ void store_link_cs(double2* U, int d, int64_t s, int64_t Vn, const M3<double>& m) {
+    double2* b = U + (size_t)d * 9 * Vn + s;
+#pragma unroll
+    for (int k = 0; k < 9; k++) __stcs(b + (size_t)k * Vn, make_double2(m.re[k / 3][k % 3], m.im[k / 3][k % 3]));
+}
+__device__ __forceinline__ void store_link_cs(float4* U, int d, int64_t s, int64_t Vn, const M3<float>& m) {
+    float4* b = U + (size_t)d * 3 * Vn + s;
+    __stcs(b, make_float4(m.re[0][0], m.im[0][0], m.re[0][1], m.im[0][1]));
+    __stcs(b + Vn, make_float4(m.re[0][2], m.im[0][2], m.re[1][0], m.im[1][0]));
+    __stcs(b + 2 * Vn, make_float4(m.re[1][1], m.im[1][1], m.re[1][2], m.im[1][2]));
+}
+__device__ __forceinline__ void store_alg_cs(double2* A, int64_t s, int64_t Vn, const A8<double>& x) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) __stcs(A + (size_t)k * Vn + s, make_double2(x.v[2 * k], x.v[2 * k + 1]));
+}
+__device__ __forceinline__ void store_alg_cs(float4* A, int64_t s, int64_t Vn, const A8<float>& x) {
+    __stcs(A + s, make_float4(x.v[0], x.v[1], x.v[2], x.v[3]));
+    __stcs(A + Vn + s, make_float4(x.v[4], x.v[5], x.v[6], x.v[7]));
+}
+
 // components of i[A, B] for Hermitian A, B: -f_abc A^a B^b T^c, with the nine
 // independent structure constants of SU(3)
 template <typename R>
