@@ -301,7 +301,8 @@ gl_status gl_batch_init(gl_batch* batch);
 
 /* Choose the launch shapes and the step schedule from timed trial launches
  * that do not change the state (waits).  Chosen: the field tile shape (0:
- * 32x8, 1: 32x4, 2: 32x16; FP64 batches use 32x4); the block size (128,
+ * 32x8, 1: 32x4, 2: 32x16; FP64 batches use 32x4), by the whole step as for
+ * the push; the block size (128,
  * 256, 512) and chunk (particles per block: 128, 256, 512, 1024) of the
  * separate push kernel, by the time of the whole overlapped step, not of the
  * push alone; and the steady-state step, either
@@ -328,7 +329,7 @@ gl_status gl_batch_get_launch(const gl_batch* batch, int32_t* tile_shape, int32_
 
 /* Trial timings of the last autotune, ms (0 where not tried): field_ms[3] by
  * tile shape; push_ms[3] by push block size; step_ms[8] for a whole step:
- * [0] two streams (the fastest push block and chunk sizes), [1..3] fused with push chunks of 512, 1024, 2048, [4..7]
+ * [0] two streams (the fastest tile shape, push block and chunk sizes), [1..3] fused with push chunks of 512, 1024, 2048, [4..7]
  * two streams with push_grid 1 beside the 32x8 and 32x4 tiles, then push_grid
  * 2 beside the same. */
 gl_status gl_batch_tuning(const gl_batch* batch, float* field_ms, float* push_ms, float* step_ms);

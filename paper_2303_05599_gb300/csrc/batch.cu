@@ -752,9 +752,10 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
         for (int g = 0; g <= 2; g++)
             for (int tile = 0; tile < N_TILES; tile++) {
                 if (b->prec == GL_FP64 && tile != TILE_32x4) continue;
-                if (g == 0 && tile != tile0) continue;
                 // resident push blocks (g > 0) leave no room beside the
-                // 512-thread tiles; the plain two-stream step takes any tile
+                // 512-thread tiles; the plain two-stream step tries every
+                // tile shape, since the fastest field kernel alone is not
+                // always the fastest beside the push
                 if (g > 0 && tile == TILE_32x16) continue;
                 b->tile = tile;
                 float best_g = 1e30f;
@@ -784,7 +785,8 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
                         }
                     }
                 }
-                b->tune_step_ms[g == 0 ? 0 : 1 + N_CHUNKS + 2 * (g - 1) + (tile == TILE_32x4)] = best_g;
+                float& slot = b->tune_step_ms[g == 0 ? 0 : 1 + N_CHUNKS + 2 * (g - 1) + (tile == TILE_32x4)];
+                if (slot == 0 || best_g < slot) slot = best_g;
             }
         b->tile = tile0;
         for (int k = 0; k < N_CHUNKS; k++) {

@@ -47,6 +47,31 @@ struct Parts<double> {
         pxy[i] = make_double2(s.px, s.py);
         eP[i] = make_double2(s.eta, s.Pe);
     }
+    // streaming (evict-first) forms for the push, which reads and writes each
+    // particle once a step: the particles leave L2 to the gathered site fields
+    __device__ PState<double> load_cs(int64_t i) const {
+        PState<double> s;
+        double2 a = __ldcs(xy + i), b = __ldcs(pxy + i), c = __ldcs(eP + i);
+        s.x = a.x; s.y = a.y; s.px = b.x; s.py = b.y; s.eta = c.x; s.Pe = c.y;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            double2 v = __ldcs(q + (size_t)k * np + i);
+            s.q.v[2 * k] = v.x;
+            s.q.v[2 * k + 1] = v.y;
+        }
+        return s;
+    }
+    __device__ void store_cs(int64_t i, const PState<double>& s) const {
+        __stcs(xy + i, make_double2(s.x, s.y));
+        __stcs(pxy + i, make_double2(s.px, s.py));
+        __stcs(eP + i, make_double2(s.eta, s.Pe));
+#pragma unroll
+        for (int k = 0; k < 4; k++) __stcs(q + (size_t)k * np + i, make_double2(s.q.v[2 * k], s.q.v[2 * k + 1]));
+    }
+    __device__ void store_momenta_cs(int64_t i, const PState<double>& s) const {
+        __stcs(pxy + i, make_double2(s.px, s.py));
+        __stcs(eP + i, make_double2(s.eta, s.Pe));
+    }
 };
 
 template <>
@@ -78,6 +103,27 @@ struct Parts<float> {
     __device__ void store_momenta(int64_t i, const PState<float>& s) const {
         xyp[i] = make_float4(s.x, s.y, s.px, s.py);
         eP[i] = make_float2(s.eta, s.Pe);
+    }
+    // streaming (evict-first) forms for the push, as for FP64
+    __device__ PState<float> load_cs(int64_t i) const {
+        PState<float> s;
+        float4 a = __ldcs(xyp + i);
+        float2 c = __ldcs(eP + i);
+        float4 q0 = __ldcs(q + i), q1 = __ldcs(q + np + i);
+        s.x = a.x; s.y = a.y; s.px = a.z; s.py = a.w; s.eta = c.x; s.Pe = c.y;
+        s.q.v[0] = q0.x; s.q.v[1] = q0.y; s.q.v[2] = q0.z; s.q.v[3] = q0.w;
+        s.q.v[4] = q1.x; s.q.v[5] = q1.y; s.q.v[6] = q1.z; s.q.v[7] = q1.w;
+        return s;
+    }
+    __device__ void store_cs(int64_t i, const PState<float>& s) const {
+        __stcs(xyp + i, make_float4(s.x, s.y, s.px, s.py));
+        __stcs(eP + i, make_float2(s.eta, s.Pe));
+        __stcs(q + i, make_float4(s.q.v[0], s.q.v[1], s.q.v[2], s.q.v[3]));
+        __stcs(q + np + i, make_float4(s.q.v[4], s.q.v[5], s.q.v[6], s.q.v[7]));
+    }
+    __device__ void store_momenta_cs(int64_t i, const PState<float>& s) const {
+        __stcs(xyp + i, make_float4(s.x, s.y, s.px, s.py));
+        __stcs(eP + i, make_float2(s.eta, s.Pe));
     }
 };
 

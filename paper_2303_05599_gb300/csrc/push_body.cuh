@@ -46,7 +46,7 @@ __device__ __forceinline__ void push_one(const typename Prec<R>::V* __restrict__
     const int64_t Vn = (int64_t)N * N;
     const int s = P.sp[i];
     if (!((active >> s) & 1u)) return;
-    PState<R> p = P.load(i);
+    PState<R> p = P.load_cs(i);
     const int ixu = (int)floor_r<R>(p.x + R(0.5)), iyu = (int)floor_r<R>(p.y + R(0.5));
     // wrap keeps every index inside the lattice even for a non-finite position
     // (float-to-int conversion maps NaN to 0 and saturates out-of-range values)
@@ -60,7 +60,7 @@ __device__ __forceinline__ void push_one(const typename Prec<R>::V* __restrict__
         p.px += dt * qEx;
         p.py += dt * qEy;
         p.Pe += dt * qEe;
-        P.store_momenta(i, p);
+        P.store_momenta_cs(i, p);
         return;
     }
     if (sa.motion[s] == MOTION_EIKONAL) {
@@ -79,7 +79,7 @@ __device__ __forceinline__ void push_one(const typename Prec<R>::V* __restrict__
         if (xn < R(0)) xn += (R)N;
         p.x = xn;
         if (jxu != ixu) p.q = conj_dn(load_link(bn1.U, 0, cell, Vn), p.q);
-        P.store(i, p);
+        P.store_cs(i, p);
         return;
     }
     const R qBx = a_dot(p.q, load_alg(site + (size_t)3 * AP * Vn, cell, Vn));
@@ -129,7 +129,7 @@ __device__ __forceinline__ void push_one(const typename Prec<R>::V* __restrict__
         const A8<R> ph = load_alg(bn1.phi, (int64_t)jy * N + jx, Vn);
         p.q = conj_up(exp_i_alg<R, (sizeof(R) == 8 ? 20 : 6)>(ph, -deta), p.q);
     }
-    P.store(i, p);
+    P.store_cs(i, p);
 }
 
 }  // namespace gl
