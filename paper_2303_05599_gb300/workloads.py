@@ -52,7 +52,7 @@ class Workload:
     tau_max_fm: float = 1.0
     precision: int = FP64
     reunit_every: int = 64
-    sort_every: int = 16
+    sort_every: int = 32
     n_jets: int = 0              # light-like jet-correlator probes (single events)
     ptau_diagnostic: bool = False  # integrate p^tau beside the mass shell (GL_BUF_PTAU)
     seed: int = 0

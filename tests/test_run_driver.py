@@ -67,6 +67,7 @@ def test_checkpoint_resume_is_bitwise():
     from paper_2303_05599_gb300 import _binding as B
     assert torch.cuda.is_available()
     w = W.Workload("ckpt", N=24, L_fm=2.25, Ns=4, precision=W.FP32_2ROW, seed=4, n_jets=16, ptau_diagnostic=True,
+                   sort_every=8,  # sorts before and after the checkpoint
                    species=[W.Species(W.M_CHARM, 0.0, 300, W.REP_F, W.MOM_UNIFORM_PT, 0.0, 3.0),
                             W.Species(0.0, 0.0, 50, W.REP_A, W.MOM_EIKONAL_X, 0.0)])
     bufs = (B.GL_BUF_LINKS, B.GL_BUF_PHI, B.GL_BUF_E, B.GL_BUF_PI, B.GL_BUF_PARTICLES, B.GL_BUF_PTAU, B.GL_BUF_JETS)
