@@ -544,6 +544,7 @@ gl_ctx* gl_batch_event(gl_batch* b, int32_t e) { return b && e >= 0 && e < b->ne
 const char* gl_batch_error_string(const gl_batch* b) { return b ? b->err : ""; }
 
 gl_status gl_batch_init(gl_batch* b) {
+    gl::ApiRange range_("gl_batch_init");
     if (!b) return GL_ERR_ARG;
     b->desc_valid = 0;
     for (int e = 0; e < b->ne; e++) {
@@ -674,6 +675,7 @@ static void enqueue_overlap_step(gl_batch* b) {
 static gl_status ensure_aux(gl_batch* b);
 
 gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_out) {
+    gl::ApiRange range_("gl_batch_autotune");
     if (!b) return GL_ERR_ARG;
     b->desc_valid = 0;  // the trials rewrite the device descriptors and clock
     if (gl_status s = ensure_aux(b)) return s;
@@ -875,6 +877,7 @@ static int64_t common_step(const gl_batch* b) {
 // events) alone, then m - 1 replays of the captured overlapped step, then the
 // last push alone.
 gl_status gl_batch_step(gl_batch* b, int32_t n_steps) {
+    gl::ApiRange range_("gl_batch_step");
     if (!b || n_steps < 0) return GL_ERR_ARG;
     if (n_steps == 0) return GL_OK;
     if (gl_status s = sync_desc(b)) return s;
@@ -923,6 +926,7 @@ gl_status gl_batch_step(gl_batch* b, int32_t n_steps) {
 // returns the summed durations of the field and push kernels (waits).  The
 // state evolves exactly as under gl_batch_step.
 gl_status gl_batch_step_timed(gl_batch* b, int32_t n_steps, double* field_ms, double* push_ms) {
+    gl::ApiRange range_("gl_batch_step_timed");
     if (!b || n_steps < 1) return GL_ERR_ARG;
     if (gl_status s = sync_desc(b)) return s;
     const int ne = 4 * n_steps;
@@ -973,6 +977,7 @@ static gl_status ensure_aux(gl_batch* b);
 // its own staging and sort buffers), so that one event's host copy overlaps
 // another's conversion and sort
 gl_status gl_batch_upload(gl_batch* b, gl_buffer which, const double* const* host, const size_t* count) {
+    gl::ApiRange range_("gl_batch_upload");
     if (!b || !host || !count) return GL_ERR_ARG;
     if (gl_status s = ensure_aux(b)) return s;
     cudaEventRecord(b->ev_a, b->stream);
@@ -997,6 +1002,7 @@ gl_status gl_batch_upload(gl_batch* b, gl_buffer which, const double* const* hos
 gl_status gl_batch_observables(gl_batch* b, gl_obs* out) { return gl_batch_observables_ex(b, GL_OBS_ALL, out); }
 
 gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
+    gl::ApiRange range_("gl_batch_observables_ex");
     if (!b || !out || (what & ~GL_OBS_ALL)) return GL_ERR_ARG;
     // obs rows of all events: out pointers (also for the gather when only the
     // field checks are asked for)

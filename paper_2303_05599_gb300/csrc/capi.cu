@@ -360,6 +360,7 @@ static uint32_t active_mask(const gl_ctx* c, int64_t n) {
 }
 
 gl_status glasma_init(gl_ctx* c) {
+    gl::ApiRange range_("glasma_init");
     if (!c) return GL_ERR_ARG;
     launch_mv_init(c->prec, c->field[c->cur], c->scratch, c->N, c->cfg.Ns, c->g2mu_a, c->m_a, c->Lambda_a,
                    c->cfg.seed, c->d_bad, c->stream);
@@ -380,6 +381,7 @@ gl_status glasma_init(gl_ctx* c) {
 }
 
 gl_status wong_init(gl_ctx* c) {
+    gl::ApiRange range_("wong_init");
     if (!c) return GL_ERR_ARG;
     launch_sample(c->prec, c->parts, c->np, c->N, c->cfg.seed, c->off, c->ns, c->rep, c->mode, c->p0, c->p1, c->q0,
                   c->stream);
@@ -440,10 +442,12 @@ static gl_status transfer(gl_ctx* c, gl_buffer which, double* host, size_t count
 }
 
 gl_status gl_upload(gl_ctx* c, gl_buffer which, const double* host, size_t count) {
+    gl::ApiRange range_("gl_upload");
     return transfer(c, which, (double*)host, count, 1);
 }
 
 gl_status gl_download(gl_ctx* c, gl_buffer which, double* host, size_t count) {
+    gl::ApiRange range_("gl_download");
     return transfer(c, which, host, count, 0);
 }
 
@@ -480,6 +484,7 @@ static void one_field_step(gl_ctx* c, cudaStream_t st) {
 }
 
 gl_status glasma_step(gl_ctx* c, int32_t n) {
+    gl::ApiRange range_("glasma_step");
     if (!c || n < 0) return GL_ERR_ARG;
     for (int k = 0; k < n; k++) one_field_step(c, c->stream);
     return check_cuda(c, "glasma_step");
@@ -494,6 +499,7 @@ static gl_status site_once(gl_ctx* c) {
 }
 
 gl_status wong_site_fields(gl_ctx* c) {
+    gl::ApiRange range_("wong_site_fields");
     if (!c) return GL_ERR_ARG;
     if (site_holds(c, c->pstep) && c->pstep == c->step - 1) return GL_OK;  // written by the field step
     if (gl_status s = site_once(c)) return s;
@@ -518,6 +524,7 @@ static gl_status push_once(gl_ctx* c, cudaStream_t st, void* bn1) {
 }
 
 gl_status wong_push(gl_ctx* c) {
+    gl::ApiRange range_("wong_push");
     if (!c) return GL_ERR_ARG;
     if (c->pstep != c->step - 1) return fail(c, GL_ERR_STATE, "wong_push needs exactly one field step since the particles' time");
     if (!site_holds(c, c->pstep))
@@ -542,6 +549,7 @@ static gl_status ensure_aux(gl_ctx* c) {
 // time s; the field step s+1, which rewrites the buffers of time s-1, waits
 // for that push.  The caller's stream waits for the last push.
 gl_status gl_step_coupled(gl_ctx* c, int32_t n) {
+    gl::ApiRange range_("gl_step_coupled");
     if (!c || n < 0) return GL_ERR_ARG;
     if (n == 0) return GL_OK;
     if (c->pstep != c->step) return fail(c, GL_ERR_STATE, "particles are not at the fields' time");
@@ -568,6 +576,7 @@ gl_status gl_step_coupled(gl_ctx* c, int32_t n) {
 }
 
 gl_status gl_autotune(gl_ctx* c, int32_t* tile_out, int32_t* push_block_out) {
+    gl::ApiRange range_("gl_autotune");
     if (!c) return GL_ERR_ARG;
     if (c->pstep != c->step) return fail(c, GL_ERR_STATE, "autotune needs the particles at the fields' time");
     cudaEvent_t e0, e1;
@@ -693,6 +702,7 @@ static void observables_fill(const gl_ctx* c, uint32_t what, const double* host,
 gl_status observables(gl_ctx* c, gl_obs* o) { return gl_observables_ex(c, GL_OBS_ALL, o); }
 
 gl_status gl_jets_observables(gl_ctx* c, double* out3) {
+    gl::ApiRange range_("gl_jets_observables");
     if (!c || !out3) return GL_ERR_ARG;
     if (!c->n_jets) return fail(c, GL_ERR_STATE, "the context has no jet-correlator probes");
     double* dout = c->jet_partials + 1024 * 3;
@@ -707,6 +717,7 @@ gl_status gl_jets_observables(gl_ctx* c, double* out3) {
 }
 
 gl_status gl_observables_ex(gl_ctx* c, uint32_t what, gl_obs* o) {
+    gl::ApiRange range_("gl_observables_ex");
     if (!c || !o || (what & ~GL_OBS_ALL)) return GL_ERR_ARG;
     observables_launch(c, what);
     return observables_read(c, what, o);

@@ -5,8 +5,19 @@
 #include <stdint.h>
 
 #include "../../include/glasma.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace gl {
+
+// a named range on the profiler timeline (NVTX) for the life of a C-ABI call;
+// without a profiler attached it costs a pointer test
+struct ApiRange {
+    explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+    ApiRange(const ApiRange&) = delete;
+    ApiRange& operator=(const ApiRange&) = delete;
+};
+
 
 // how a species moves: Wong particles of finite mass, infinitely massive
 // static quarks (Sec. 5.1), eikonal light-like partons along +x (Sec. 5.2)
