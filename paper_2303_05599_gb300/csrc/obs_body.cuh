@@ -73,21 +73,22 @@ __device__ __forceinline__ float nanmax_f(float a, float b) { return (a > b || a
 
 template <typename R>
 struct CasimirSlot;
+// (smallest, largest) packed into the 8 bytes of a double slot (low, high word)
+__device__ __forceinline__ double pack_minmax(float mn, float mx) {
+    return __hiloint2double(__float_as_int(mx), __float_as_int(mn));
+}
+__device__ __forceinline__ float unpack_min(double d) { return __int_as_float(__double2loint(d)); }
+__device__ __forceinline__ float unpack_max(double d) { return __int_as_float(__double2hiint(d)); }
+
 template <>
 struct CasimirSlot<float> {
-    static __device__ __forceinline__ void init(double* slot) {
-        *(float2*)slot = make_float2(INFINITY, -INFINITY);
-    }
+    static __device__ __forceinline__ void init(double* slot) { *slot = pack_minmax(INFINITY, -INFINITY); }
     static __device__ __forceinline__ void add(double* slot, float q, double) {
-        float2 e = *(float2*)slot;
-        e.x = nanmin_f(e.x, q);
-        e.y = nanmax_f(e.y, q);
-        *(float2*)slot = e;
+        *slot = pack_minmax(nanmin_f(unpack_min(*slot), q), nanmax_f(unpack_max(*slot), q));
     }
     static __device__ __forceinline__ double finish(const double* slot, double ref, long long n) {
         if (n == 0) return 0.0;
-        const float2 e = *(const float2*)slot;
-        return nanmax(fabs((double)e.x - ref), fabs((double)e.y - ref));
+        return nanmax(fabs((double)unpack_min(*slot) - ref), fabs((double)unpack_max(*slot) - ref));
     }
 };
 template <>
@@ -113,7 +114,7 @@ __device__ __forceinline__ void particle_obs_block(const Parts<R>& P, double t, 
     const int ns = oa.sp.n_species, rows = ns * PO_N, tid = threadIdx.x;
     for (int s = 0; s < ns; s++) {
         double* a = obs_acc + (size_t)s * PO_N * OBS_THREADS + tid;
-        *(long long*)(a + PO_COUNT * OBS_THREADS) = 0;
+        a[PO_COUNT * OBS_THREADS] = __longlong_as_double(0);
         a[PO_PX2 * OBS_THREADS] = 0.0;
         a[PO_PY2 * OBS_THREADS] = 0.0;
         a[PO_PL2 * OBS_THREADS] = 0.0;
@@ -127,7 +128,7 @@ __device__ __forceinline__ void particle_obs_block(const Parts<R>& P, double t, 
         const R pl = particle_pl<R>(p, (R)t, (R)oa.sp.mass[s], oa.sp.motion[s] != MOTION_WONG);
         const double px = p.px, py = p.py, dpl = pl;
         double* a = obs_acc + (size_t)s * PO_N * OBS_THREADS + tid;
-        *(long long*)(a + PO_COUNT * OBS_THREADS) += 1;
+        a[PO_COUNT * OBS_THREADS] = __longlong_as_double(__double_as_longlong(a[PO_COUNT * OBS_THREADS]) + 1);
         a[PO_PX2 * OBS_THREADS] = fma(px, px, a[PO_PX2 * OBS_THREADS]);
         a[PO_PY2 * OBS_THREADS] = fma(py, py, a[PO_PY2 * OBS_THREADS]);
         a[PO_PL2 * OBS_THREADS] = fma(dpl, dpl, a[PO_PL2 * OBS_THREADS]);
@@ -151,7 +152,7 @@ __device__ __forceinline__ void particle_obs_block(const Parts<R>& P, double t, 
     // the thread's partial values in place, in its own column
     for (int s = 0; s < ns; s++) {
         double* a = obs_acc + (size_t)s * PO_N * OBS_THREADS + tid;
-        const long long n = *(long long*)(a + PO_COUNT * OBS_THREADS);
+        const long long n = __double_as_longlong(a[PO_COUNT * OBS_THREADS]);
         a[PO_COUNT * OBS_THREADS] = (double)n;
         a[PO_DPT2 * OBS_THREADS] = a[PO_PX2 * OBS_THREADS] + a[PO_PY2 * OBS_THREADS] - a[PO_DPT2 * OBS_THREADS];
         a[PO_Q2 * OBS_THREADS] = CasimirSlot<R>::finish(a + PO_Q2 * OBS_THREADS, oa.q2ref[s], n);

@@ -244,8 +244,11 @@ __device__ __forceinline__ M3<R> alg_to_mat2(const A8<R>& x) {
 // Hermitian result is formed).  The product is taken of 2 X, so that the
 // off-diagonal components need no factor 2 and the diagonal ones a factor
 // 1/2; scaling by powers of 2 is exact, so the result is bitwise that of X.
-template <typename R>
-__device__ __forceinline__ A8<R> conj_dn(const M3<R>& V, const A8<R>& x) {
+// TRACELESS: the (2, 2) entry is not formed; V^+ X V is traceless like X, so
+// its eighth component follows from the first two diagonal entries (the same
+// value up to rounding, six fused multiply-adds fewer).
+template <typename R, bool TRACELESS>
+__device__ __forceinline__ A8<R> conj_dn_impl(const M3<R>& V, const A8<R>& x) {
     const M3<R> X = alg_to_mat2(x);
     M3<R> Y;  // X V, with X's diagonal real
 #pragma unroll
@@ -264,9 +267,9 @@ __device__ __forceinline__ A8<R> conj_dn(const M3<R>& V, const A8<R>& x) {
             Y.re[i][j] = sr;
             Y.im[i][j] = si;
         }
-    R zr[3][3], zi[3][3];  // V^+ Y, upper triangle
+    R zr[3][3], zi[3][3];  // V^+ Y, upper triangle (but (2, 2) when TRACELESS)
 #pragma unroll
-    for (int i = 0; i < 3; i++)
+    for (int i = 0; i < (TRACELESS ? 2 : 3); i++)
 #pragma unroll
         for (int j = i; j < 3; j++) {
             R sr = R(0), si = R(0);
@@ -290,63 +293,25 @@ __device__ __forceinline__ A8<R> conj_dn(const M3<R>& V, const A8<R>& x) {
     o.v[4] = -zi[0][2];
     o.v[5] = zr[1][2];
     o.v[6] = -zi[1][2];
-    o.v[7] = (zr[0][0] + zr[1][1] - R(2) * zr[2][2]) * (R(0.5) * inv_sqrt3<R>());
+    if constexpr (TRACELESS) {
+        // (Z00 + Z11 - 2 Z22) / sqrt 3 with Z22 = -(Z00 + Z11), halved for 2X
+        o.v[7] = (zr[0][0] + zr[1][1]) * R(0.86602540378443864676);
+    } else {
+        o.v[7] = (zr[0][0] + zr[1][1] - R(2) * zr[2][2]) * (R(0.5) * inv_sqrt3<R>());
+    }
     return o;
 }
 
-// conj_dn without the (2, 2) entry of the product: V^+ X V is traceless like
-// X, so its eighth component follows from the first two diagonal entries
-// (the same value up to rounding, six fused multiply-adds fewer).  Used by
-// the field step, where the transports are the bulk of the arithmetic.
+template <typename R>
+__device__ __forceinline__ A8<R> conj_dn(const M3<R>& V, const A8<R>& x) {
+    return conj_dn_impl<R, false>(V, x);
+}
+
+// conj_dn for the field step, where the transports are the bulk of the
+// arithmetic: the traceless form
 template <typename R>
 __device__ __forceinline__ A8<R> conj_dn_t(const M3<R>& V, const A8<R>& x) {
-    const M3<R> X = alg_to_mat2(x);
-    M3<R> Y;  // X V, with X's diagonal real
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            R sr = X.re[i][i] * V.re[i][j], si = X.re[i][i] * V.im[i][j];
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                if (k == i) continue;
-                sr = fma(X.re[i][k], V.re[k][j], sr);
-                sr = fma(-X.im[i][k], V.im[k][j], sr);
-                si = fma(X.re[i][k], V.im[k][j], si);
-                si = fma(X.im[i][k], V.re[k][j], si);
-            }
-            Y.re[i][j] = sr;
-            Y.im[i][j] = si;
-        }
-    R zr[3][3], zi[3][3];  // V^+ Y, upper triangle but (2, 2)
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = i; j < 3; j++) {
-            R sr = R(0), si = R(0);
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                sr = fma(V.re[k][i], Y.re[k][j], sr);
-                sr = fma(V.im[k][i], Y.im[k][j], sr);
-                if (i != j) {
-                    si = fma(V.re[k][i], Y.im[k][j], si);
-                    si = fma(-V.im[k][i], Y.re[k][j], si);
-                }
-            }
-            zr[i][j] = sr;
-            zi[i][j] = si;
-        }
-    A8<R> o;
-    o.v[0] = zr[0][1];
-    o.v[1] = -zi[0][1];
-    o.v[2] = R(0.5) * (zr[0][0] - zr[1][1]);
-    o.v[3] = zr[0][2];
-    o.v[4] = -zi[0][2];
-    o.v[5] = zr[1][2];
-    o.v[6] = -zi[1][2];
-    // (Z00 + Z11 - 2 Z22) / sqrt 3 with Z22 = -(Z00 + Z11), halved for 2X
-    o.v[7] = (zr[0][0] + zr[1][1]) * R(0.86602540378443864676);
-    return o;
+    return conj_dn_impl<R, true>(V, x);
 }
 
 // components of V X V^+ for Hermitian X
