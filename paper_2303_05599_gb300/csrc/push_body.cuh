@@ -110,19 +110,23 @@ __device__ __forceinline__ void push_one(const typename Prec<R>::V* __restrict__
     p.y = yn;
     // CPIC: rotate with the crossed links at t_{n+1}, x first, then y.  A step
     // up takes U^+ Q U with the link of the old cell, a step down U Q U^+ =
-    // (U^+)^+ Q U^+ with the link of the new cell: one transport per axis,
-    // with U or U^+ chosen per lane, so that a warp runs it once whichever
-    // way its lanes cross (crossings are rare, but some lane of a warp crosses
-    // almost every step)
+    // (U^+)^+ Q U^+ with the link of the new cell.  Each lane has up to two
+    // transports to make (bit 0: x, bit 1: y); one loop body serves both axes,
+    // with the link and U or U^+ chosen per lane, so that a warp runs as many
+    // transports as its busiest lane needs (crossings are rare, but some lane
+    // of a warp crosses almost every step)
     const int dxc = jxu - ixu, dyc = jyu - iyu;
     const int jx = wrapi(jxu, N), jy = wrapi(jyu, N);
-    if (dxc == 1 || dxc == -1) {
-        const M3<R> U = load_link(bn1.U, 0, dxc == 1 ? cell : (int64_t)iy * N + jx, Vn);
-        p.q = conj_dn(dxc == 1 ? U : dag(U), p.q);
-    }
-    if (dyc == 1 || dyc == -1) {
-        const M3<R> U = load_link(bn1.U, 1, dyc == 1 ? (int64_t)iy * N + jx : (int64_t)jy * N + jx, Vn);
-        p.q = conj_dn(dyc == 1 ? U : dag(U), p.q);
+    // cell indices of an event fit in 32 bits (N <= 32768)
+    const int ix_link = dxc == 1 ? (int)cell : iy * N + jx;
+    const int iy_link = dyc == 1 ? iy * N + jx : jy * N + jx;
+    int todo = ((dxc == 1 || dxc == -1) ? 1 : 0) | ((dyc == 1 || dyc == -1) ? 2 : 0);
+#pragma unroll 1
+    while (todo) {
+        const bool on_x = todo & 1;
+        const M3<R> U = load_link(bn1.U, on_x ? 0 : 1, on_x ? ix_link : iy_link, Vn);
+        p.q = conj_dn((on_x ? dxc : dyc) == 1 ? U : dag(U), p.q);
+        todo &= todo - 1;
     }
     // rapidity Wilson line at the new cell: Q <- e^{-i deta phi} Q e^{+i deta phi}
     if (deta != R(0)) {
