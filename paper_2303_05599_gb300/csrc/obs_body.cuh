@@ -9,13 +9,15 @@
 // particle count, so an event gives bitwise the same observables whether it is
 // reduced on its own or inside a batch.
 //
-// Per-particle quantities are evaluated in the state's precision; every
-// accumulation is FP64.  Within a block each thread accumulates its own
-// particles (c0 + tid, c0 + tid + OBS_THREADS, ...) into its own column of
-// shared memory, then one fixed-order tree combines the columns.  FP64 issue
-// is the scarce resource of this reduction, so a particle costs four FP64
-// fused adds (p_x^2, p_y^2, p_L^2, p_T^2(tau_form)) and its conversions: the
-// count is an integer and the Casimir deviations are taken at the extremes.
+// Per-particle quantities are evaluated in the state's precision.  Within a
+// block each thread accumulates its own particles (c0 + tid, c0 + tid +
+// OBS_THREADS, ...) into its own column of shared memory, then one
+// fixed-order FP64 tree combines the columns.  FP64 issue is the scarce
+// resource of this reduction (GB300 runs FP64 at 1/64 of the FP32 rate), so a
+// particle of an FP32 state costs one FP64 add (p_T^2(tau_form), stored in
+// FP64): its squares p_x^2, p_y^2, p_L^2 are summed as exact float pairs (see
+// SquareSum), the count is an integer and the Casimir deviations are taken at
+// the extremes.  An FP64 state sums its squares with FP64 fused adds.
 #pragma once
 #include "internal.h"
 #include "layout.cuh"
@@ -62,79 +64,149 @@ __host__ __device__ inline size_t obs_smem_bytes(int ns) {
     return (size_t)ns * PO_N * OBS_THREADS * sizeof(double);
 }
 
-// Casimir deviations |q - ref| of one thread's particles.  FP32 state: the
-// thread keeps the smallest and largest q (exact in any precision: no
-// rounding) in the 8-byte slot of its column and takes |q - ref| in FP64 at
-// the two extremes only, where the largest deviation lies; bitwise the
-// maximum of the per-particle FP64 deviations.  FP64 state: the deviation per
-// particle.  A NaN q propagates.
+// Casimir drifts max |q - ref|.  FP32 state: the smallest and largest q
+// (exact in any precision: no rounding) are kept in the 8-byte slot, through
+// the block's tree as well, and |q - ref| is taken in FP64 once per block at
+// the two extremes, where the largest deviation lies.  The rounded |q - ref|
+// is monotonic on either side of ref, so this is bitwise the maximum of the
+// per-particle FP64 deviations.  FP64 state: the deviation per particle.  A
+// NaN q propagates.
 __device__ __forceinline__ float nanmin_f(float a, float b) { return (a < b || a != a) ? a : b; }
 __device__ __forceinline__ float nanmax_f(float a, float b) { return (a > b || a != a) ? a : b; }
 
+// two floats in the 8 bytes of a double slot (low word, high word)
+__device__ __forceinline__ double pack_f2(float lo_word, float hi_word) {
+    return __hiloint2double(__float_as_int(hi_word), __float_as_int(lo_word));
+}
+__device__ __forceinline__ float f2_lo(double d) { return __int_as_float(__double2loint(d)); }
+__device__ __forceinline__ float f2_hi(double d) { return __int_as_float(__double2hiint(d)); }
+
 template <typename R>
 struct CasimirSlot;
-// (smallest, largest) packed into the 8 bytes of a double slot (low, high word)
-__device__ __forceinline__ double pack_minmax(float mn, float mx) {
-    return __hiloint2double(__float_as_int(mx), __float_as_int(mn));
-}
-__device__ __forceinline__ float unpack_min(double d) { return __int_as_float(__double2loint(d)); }
-__device__ __forceinline__ float unpack_max(double d) { return __int_as_float(__double2hiint(d)); }
-
 template <>
 struct CasimirSlot<float> {
-    static __device__ __forceinline__ void init(double* slot) { *slot = pack_minmax(INFINITY, -INFINITY); }
-    static __device__ __forceinline__ void add(double* slot, float q, double) {
-        *slot = pack_minmax(nanmin_f(unpack_min(*slot), q), nanmax_f(unpack_max(*slot), q));
+    // (smallest, largest) in the (low, high) word
+    static __device__ __forceinline__ double init() { return pack_f2(INFINITY, -INFINITY); }
+    static __device__ __forceinline__ double add(double v, float q, double) {
+        return pack_f2(nanmin_f(f2_lo(v), q), nanmax_f(f2_hi(v), q));
     }
-    static __device__ __forceinline__ double finish(const double* slot, double ref, long long n) {
+    static __device__ __forceinline__ double combine(double a, double b) {
+        return pack_f2(nanmin_f(f2_lo(a), f2_lo(b)), nanmax_f(f2_hi(a), f2_hi(b)));
+    }
+    static __device__ __forceinline__ double finish(double v, double ref, long long n) {
         if (n == 0) return 0.0;
-        return nanmax(fabs((double)unpack_min(*slot) - ref), fabs((double)unpack_max(*slot) - ref));
+        return nanmax(fabs((double)f2_lo(v) - ref), fabs((double)f2_hi(v) - ref));
     }
 };
 template <>
 struct CasimirSlot<double> {
-    static __device__ __forceinline__ void init(double* slot) { *slot = 0.0; }
-    static __device__ __forceinline__ void add(double* slot, double q, double ref) {
-        *slot = nanmax(*slot, fabs(q - ref));
-    }
-    static __device__ __forceinline__ double finish(const double* slot, double, long long) { return *slot; }
+    static __device__ __forceinline__ double init() { return 0.0; }
+    static __device__ __forceinline__ double add(double v, double q, double ref) { return nanmax(v, fabs(q - ref)); }
+    static __device__ __forceinline__ double combine(double a, double b) { return nanmax(a, b); }
+    static __device__ __forceinline__ double finish(double v, double, long long) { return v; }
 };
+
+// Sums of squares x^2.  FP32 state: the square of a float is exact as a pair
+// of floats, hi = x*x rounded and lo = fma(x, x, -hi) its rounding error
+// (Dekker's product with a fused multiply-add).  A sum is kept as an
+// unevaluated pair (S, s) in the 8-byte slot, through the block's tree as
+// well: hi parts (and, in the tree, the other S) enter S through Knuth's
+// error-free two-sum, and the two-sum errors and lo parts are added up in s.
+// Every step but the additions into s is exact, so a sum of k squares carries
+// a relative error of about k 2^-48 (an FP64 sum: k 2^-53), on FP32 issue
+// only; the pair becomes one FP64 value once per block.  The operations are
+// the round-to-nearest intrinsics, which the compiler neither contracts into
+// fused multiply-adds nor reorders.  A square beyond the FP32 range (|x| >
+// 1.8e19) makes the sum NaN.  FP64 state: FP64 fused adds.
+__device__ __forceinline__ void two_sum_f(float a, float b, float& t, float& err) {
+    t = __fadd_rn(a, b);
+    const float bv = __fsub_rn(t, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(t, bv)), __fsub_rn(b, bv));
+}
+template <typename R>
+struct SquareSum;
+template <>
+struct SquareSum<float> {
+    // (S, s) in the (low, high) word
+    static __device__ __forceinline__ double init() { return pack_f2(0.0f, 0.0f); }
+    static __device__ __forceinline__ double add(double v, float x) {
+        const float hi = __fmul_rn(x, x), lo = __fmaf_rn(x, x, -hi);
+        float t, err;
+        two_sum_f(f2_lo(v), hi, t, err);
+        return pack_f2(t, __fadd_rn(f2_hi(v), __fadd_rn(err, lo)));
+    }
+    static __device__ __forceinline__ double combine(double a, double b) {
+        float t, err;
+        two_sum_f(f2_lo(a), f2_lo(b), t, err);
+        return pack_f2(t, __fadd_rn(__fadd_rn(f2_hi(a), f2_hi(b)), err));
+    }
+    static __device__ __forceinline__ double finish(double v) { return (double)f2_lo(v) + (double)f2_hi(v); }
+};
+template <>
+struct SquareSum<double> {
+    static __device__ __forceinline__ double init() { return 0.0; }
+    static __device__ __forceinline__ double add(double v, double x) { return fma(x, x, v); }
+    static __device__ __forceinline__ double combine(double a, double b) { return a + b; }
+    static __device__ __forceinline__ double finish(double v) { return v; }
+};
+
+// the particle count, a 64-bit integer in the slot's bits
+__device__ __forceinline__ double count_add(double v, long long k) {
+    return __longlong_as_double(__double_as_longlong(v) + k);
+}
+
+// the tree's combination of two slots of kind k (PO_*)
+template <typename R>
+__device__ __forceinline__ double obs_combine(int k, double a, double b) {
+    switch (k) {
+    case PO_COUNT: return count_add(a, __double_as_longlong(b));
+    case PO_PX2:
+    case PO_PY2:
+    case PO_PL2: return SquareSum<R>::combine(a, b);
+    case PO_DPT2: return a + b;
+    default: return CasimirSlot<R>::combine(a, b);
+    }
+}
 
 // partial observables of particles [c0, c1) into out[GL_MAX_SPECIES * PO_N];
 // blockDim.x == OBS_THREADS, obs_smem_bytes(oa.sp.n_species) of dynamic
-// shared memory at least.  Per thread and species, in its column: the count
-// (an integer in the PO_COUNT slot until the end), sums of p_x^2, p_y^2, p_L^2
-// (the products of the state's values, exact in FP64) and of p_T^2(tau_form)
-// in the PO_DPT2 slot (<dp_T^2> = sum p_x^2 + sum p_y^2 - sum p_T^2(tau_form)),
-// and the Casimir slots; then one fixed-order tree over the columns.
+// shared memory at least.  Per thread and species, in its column: the count,
+// the sums of p_x^2, p_y^2, p_L^2 (SquareSum) and of p_T^2(tau_form) (FP64,
+// in the PO_DPT2 slot) and the Casimir slots; then one fixed-order tree over
+// the columns, and one thread per species turns the block's slots into FP64
+// values (<dp_T^2> = sum p_x^2 + sum p_y^2 - sum p_T^2(tau_form)).
 template <typename R>
 __device__ __forceinline__ void particle_obs_block(const Parts<R>& P, double t, uint32_t active, const ObsArgs& oa,
                                                    int64_t c0, int64_t c1, double* out) {
     extern __shared__ double obs_acc[];
+    __shared__ R obs_mass[GL_MAX_SPECIES];
     const int ns = oa.sp.n_species, rows = ns * PO_N, tid = threadIdx.x;
     for (int s = 0; s < ns; s++) {
         double* a = obs_acc + (size_t)s * PO_N * OBS_THREADS + tid;
         a[PO_COUNT * OBS_THREADS] = __longlong_as_double(0);
-        a[PO_PX2 * OBS_THREADS] = 0.0;
-        a[PO_PY2 * OBS_THREADS] = 0.0;
-        a[PO_PL2 * OBS_THREADS] = 0.0;
+        a[PO_PX2 * OBS_THREADS] = SquareSum<R>::init();
+        a[PO_PY2 * OBS_THREADS] = SquareSum<R>::init();
+        a[PO_PL2 * OBS_THREADS] = SquareSum<R>::init();
         a[PO_DPT2 * OBS_THREADS] = 0.0;
-        CasimirSlot<R>::init(a + PO_Q2 * OBS_THREADS);
-        CasimirSlot<R>::init(a + PO_Q3 * OBS_THREADS);
+        a[PO_Q2 * OBS_THREADS] = CasimirSlot<R>::init();
+        a[PO_Q3 * OBS_THREADS] = CasimirSlot<R>::init();
     }
+    // the masses in the state's precision, converted once per block
+    if (tid < ns) obs_mass[tid] = (R)oa.sp.mass[tid];
+    __syncthreads();
+    const R tr = (R)t;
     // two particles per iteration, both loaded before either is accumulated
     // (in order: the first, then the second), so their loads overlap
-    auto accumulate = [&](int64_t i, int s, const PState<R>& p, double pt0) {
-        const R pl = particle_pl<R>(p, (R)t, (R)oa.sp.mass[s], oa.sp.motion[s] != MOTION_WONG);
-        const double px = p.px, py = p.py, dpl = pl;
+    auto accumulate = [&](int s, const PState<R>& p, double pt0) {
+        const R pl = particle_pl<R>(p, tr, obs_mass[s], oa.sp.motion[s] != MOTION_WONG);
         double* a = obs_acc + (size_t)s * PO_N * OBS_THREADS + tid;
-        a[PO_COUNT * OBS_THREADS] = __longlong_as_double(__double_as_longlong(a[PO_COUNT * OBS_THREADS]) + 1);
-        a[PO_PX2 * OBS_THREADS] = fma(px, px, a[PO_PX2 * OBS_THREADS]);
-        a[PO_PY2 * OBS_THREADS] = fma(py, py, a[PO_PY2 * OBS_THREADS]);
-        a[PO_PL2 * OBS_THREADS] = fma(dpl, dpl, a[PO_PL2 * OBS_THREADS]);
+        a[PO_COUNT * OBS_THREADS] = count_add(a[PO_COUNT * OBS_THREADS], 1);
+        a[PO_PX2 * OBS_THREADS] = SquareSum<R>::add(a[PO_PX2 * OBS_THREADS], p.px);
+        a[PO_PY2 * OBS_THREADS] = SquareSum<R>::add(a[PO_PY2 * OBS_THREADS], p.py);
+        a[PO_PL2 * OBS_THREADS] = SquareSum<R>::add(a[PO_PL2 * OBS_THREADS], pl);
         a[PO_DPT2 * OBS_THREADS] += pt0;
-        CasimirSlot<R>::add(a + PO_Q2 * OBS_THREADS, a_dot(p.q, p.q), oa.q2ref[s]);
-        CasimirSlot<R>::add(a + PO_Q3 * OBS_THREADS, casimir3(p.q), oa.q3ref[s]);
+        a[PO_Q2 * OBS_THREADS] = CasimirSlot<R>::add(a[PO_Q2 * OBS_THREADS], a_dot(p.q, p.q), oa.q2ref[s]);
+        a[PO_Q3 * OBS_THREADS] = CasimirSlot<R>::add(a[PO_Q3 * OBS_THREADS], casimir3(p.q), oa.q3ref[s]);
     };
     for (int64_t i = c0 + tid; i < c1; i += 2 * OBS_THREADS) {
         const int64_t j = i + OBS_THREADS;
@@ -146,17 +218,8 @@ __device__ __forceinline__ void particle_obs_block(const Parts<R>& P, double t, 
         double ti = 0.0, tj = 0.0;
         if (oki) { pi_ = P.load(i); ti = P.pt0[i]; }
         if (okj) { pj = P.load(j); tj = P.pt0[j]; }
-        if (oki) accumulate(i, si, pi_, ti);
-        if (okj) accumulate(j, sj, pj, tj);
-    }
-    // the thread's partial values in place, in its own column
-    for (int s = 0; s < ns; s++) {
-        double* a = obs_acc + (size_t)s * PO_N * OBS_THREADS + tid;
-        const long long n = __double_as_longlong(a[PO_COUNT * OBS_THREADS]);
-        a[PO_COUNT * OBS_THREADS] = (double)n;
-        a[PO_DPT2 * OBS_THREADS] = a[PO_PX2 * OBS_THREADS] + a[PO_PY2 * OBS_THREADS] - a[PO_DPT2 * OBS_THREADS];
-        a[PO_Q2 * OBS_THREADS] = CasimirSlot<R>::finish(a + PO_Q2 * OBS_THREADS, oa.q2ref[s], n);
-        a[PO_Q3 * OBS_THREADS] = CasimirSlot<R>::finish(a + PO_Q3 * OBS_THREADS, oa.q3ref[s], n);
+        if (oki) accumulate(si, pi_, ti);
+        if (okj) accumulate(sj, pj, tj);
     }
     // level o folds column c + o into column c (c < o) of every row
     for (int o = OBS_THREADS / 2; o > 0; o >>= 1) {
@@ -164,11 +227,25 @@ __device__ __forceinline__ void particle_obs_block(const Parts<R>& P, double t, 
         for (int w = tid; w < rows * o; w += OBS_THREADS) {
             const int r = w / o, c = w - r * o;
             double* a = obs_acc + r * OBS_THREADS;
-            a[c] = po_is_max(r % PO_N) ? nanmax(a[c], a[c + o]) : a[c] + a[c + o];
+            a[c] = obs_combine<R>(r % PO_N, a[c], a[c + o]);
         }
     }
     __syncthreads();
-    for (int k = tid; k < GL_MAX_SPECIES * PO_N; k += OBS_THREADS) out[k] = k < rows ? obs_acc[k * OBS_THREADS] : 0.0;
+    if (tid < ns) {
+        const double* a = obs_acc + (size_t)tid * PO_N * OBS_THREADS;  // column 0
+        double* o = out + tid * PO_N;
+        const long long n = __double_as_longlong(a[PO_COUNT * OBS_THREADS]);
+        const double px2 = SquareSum<R>::finish(a[PO_PX2 * OBS_THREADS]);
+        const double py2 = SquareSum<R>::finish(a[PO_PY2 * OBS_THREADS]);
+        o[PO_COUNT] = (double)n;
+        o[PO_PX2] = px2;
+        o[PO_PY2] = py2;
+        o[PO_PL2] = SquareSum<R>::finish(a[PO_PL2 * OBS_THREADS]);
+        o[PO_DPT2] = px2 + py2 - a[PO_DPT2 * OBS_THREADS];
+        o[PO_Q2] = CasimirSlot<R>::finish(a[PO_Q2 * OBS_THREADS], oa.q2ref[tid], n);
+        o[PO_Q3] = CasimirSlot<R>::finish(a[PO_Q3 * OBS_THREADS], oa.q3ref[tid], n);
+    }
+    for (int k = rows + tid; k < GL_MAX_SPECIES * PO_N; k += OBS_THREADS) out[k] = 0.0;
 }
 
 // allow the largest dynamic shared memory of particle_obs_block on kernel f
