@@ -324,22 +324,23 @@ def run_ours(args):
         f_ms, p_ms = batch.step_timed(K)
         obs = batch.observables()
         # end to end through the public API: every event's state (the fields of
-        # one time slice and the particles) uploaded from pinned host memory,
-        # then K steps with the observables of every event read back each step
+        # one time slice and the particles, as native snapshots) uploaded from
+        # pinned host memory, then K steps with the observables of every event
+        # read back each step
+        parts = (B.GL_NATIVE_FIELDS, B.GL_NATIVE_PARTICLES)
         host = []
         for ev in batch.events:
             bufs = {}
-            for which in (B.GL_BUF_LINKS, B.GL_BUF_PHI, B.GL_BUF_E, B.GL_BUF_PI, B.GL_BUF_PARTICLES):
-                a = ev.download(which)
-                t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
-                t.numpy()[...] = a
-                bufs[which] = t
+            for part in parts:
+                t = torch.empty(ev.native_bytes(part), dtype=torch.uint8, pin_memory=True)
+                ev.download_native(part, out=t.numpy())
+                bufs[part] = t
             host.append(bufs)
-        h2d = sum(t.numel() * 8 for bufs in host for t in bufs.values())
+        h2d = sum(t.numel() for bufs in host for t in bufs.values())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for which in (B.GL_BUF_LINKS, B.GL_BUF_PHI, B.GL_BUF_E, B.GL_BUF_PI, B.GL_BUF_PARTICLES):
-            batch.upload(which, [bufs[which].numpy() for bufs in host])
+        for part in parts:
+            batch.upload_native(part, [bufs[part].numpy() for bufs in host])
         t1 = time.perf_counter()
         for _ in range(K):
             batch.step(1)
@@ -413,10 +414,10 @@ def run_ours(args):
             "roofline_kernels": roof,
             "e2e": dict({"value": world * sites * K / e2e_t, "unit": "site-updates/s",
                          "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": len(ws) * ctypes.sizeof(B.gl_obs),
-                         "includes": "gl_batch_upload of every event's fields and particles from pinned host memory "
-                                     "(FP64 canonical layout); K x (gl_batch_step(1) + the per-species particle "
-                                     "sums of every event read back to the host); one full report with the FP64 "
-                                     "field checks at the end",
+                         "includes": "gl_batch_upload_native of every event's fields and particles from pinned "
+                                     "host memory (native snapshots: the device layout, from gl_download_native); "
+                                     "K x (gl_batch_step(1) + the per-species particle sums of every event read "
+                                     "back to the host); one full report with the FP64 field checks at the end",
                          "gauss_max_final": max(o.gauss_max for o in final)}, **e2e_parts),
             "gpu_launches": 3 * K + sort_launches(ws) * sum(1 for s_ in range(pre + 1, pre + K + 1)
                                                           if ws[0].sort_every > 0 and s_ % ws[0].sort_every == 0),

@@ -204,6 +204,35 @@ gl_status gl_upload(gl_ctx* ctx, gl_buffer which, const double* host, size_t cou
 /* Copy a context buffer out in the canonical layout (waits). */
 gl_status gl_download(gl_ctx* ctx, gl_buffer which, double* host, size_t count);
 
+/* Native snapshots: one part of a context's state as the bytes of its device
+ * layout in the context's precision, for checkpoints that are restored into a
+ * context created with the same gl_config and species (the bytes are opaque
+ * and valid only there).  A native round trip restores the state bitwise,
+ * particle order and p^tau diagnostic included, and moves fewer bytes than
+ * the canonical layout (FP32: 224 B per site and 76 B per particle, against
+ * 544 B and 128 B).
+ *   GL_NATIVE_FIELDS     U, phi, e, pi of the current time slice
+ *   GL_NATIVE_PARTICLES  every particle array, in device order (sorted), with
+ *                        the species and original indices */
+typedef enum { GL_NATIVE_FIELDS = 0, GL_NATIVE_PARTICLES = 1 } gl_native_part;
+
+/* Size in bytes of a native part (0 for a NULL context or an unknown part). */
+size_t gl_native_bytes(const gl_ctx* ctx, gl_native_part part);
+
+/* Copy a native part to host memory of exactly gl_native_bytes() bytes
+ * (waits).  GL_ERR_SIZE if bytes does not match, GL_ERR_ARG for an unknown
+ * part. */
+gl_status gl_download_native(gl_ctx* ctx, gl_native_part part, void* host, size_t bytes);
+
+/* Copy a native part from host memory into the context (waits).  Like
+ * gl_upload, it sets neither the step (gl_set_step) nor the site fields.
+ * Particles: every species index must lie in [0, n_species) and every
+ * original index in [0, np); the device checks both after the copy, and if
+ * any is out of range it sets that entry to species 0 / its own position and
+ * returns GL_ERR_ARG (the particle state is then unspecified, but every
+ * later call stays within its arrays). */
+gl_status gl_upload_native(gl_ctx* ctx, gl_native_part part, const void* host, size_t bytes);
+
 /* Set the field step index n (t_n = n dt) of the uploaded state; the
  * particles are taken to be at the same time.  The uploaded fields stay the
  * current ones, so uploads may come before or after this call. */
@@ -349,6 +378,12 @@ gl_status gl_batch_step_timed(gl_batch* batch, int32_t n_steps, double* field_ms
  * (waits).  Errors as gl_upload, reported for the first failing event; the
  * events before it are uploaded. */
 gl_status gl_batch_upload(gl_batch* batch, gl_buffer which, const double* const* host, const size_t* count);
+
+/* gl_upload_native of part `part` of every event: host[e] holds bytes[e]
+ * bytes for event e.  Events alternate between two streams, as in
+ * gl_batch_upload, with one wait at the end (waits).  Errors as
+ * gl_upload_native, reported for the first failing event. */
+gl_status gl_batch_upload_native(gl_batch* batch, gl_native_part part, const void* const* host, const size_t* bytes);
 
 /* observables() of every event into out[n_events] (waits). */
 gl_status gl_batch_observables(gl_batch* batch, gl_obs* out);

@@ -19,6 +19,7 @@ GL_FP64, GL_FP32_2ROW = 0, 1
 (GL_BUF_LINKS, GL_BUF_PHI, GL_BUF_E, GL_BUF_PI, GL_BUF_SITE, GL_BUF_PARTICLES, GL_BUF_JETS, GL_BUF_ENERGY,
  GL_BUF_PTAU) = range(9)
 JET_LEN = 44
+GL_NATIVE_FIELDS, GL_NATIVE_PARTICLES = 0, 1
 GL_CFG_PTAU_DIAGNOSTIC = 1
 
 STATUS_NAMES = {0: "GL_OK", 1: "GL_ERR_ARG", 2: "GL_ERR_CUDA", 3: "GL_ERR_STATE", 4: "GL_ERR_TIMEOUT",
@@ -65,6 +66,9 @@ SIGNATURES = {
     "gl_upload": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
     "gl_download": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
     "gl_set_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "gl_native_bytes": (ctypes.c_size_t, [_P, ctypes.c_int]),
+    "gl_download_native": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
+    "gl_upload_native": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
     "glasma_step": (ctypes.c_int, [_P, ctypes.c_int32]),
     "wong_site_fields": (ctypes.c_int, [_P]),
     "wong_push": (ctypes.c_int, [_P]),
@@ -89,6 +93,7 @@ SIGNATURES = {
     "gl_batch_step_timed": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "gl_batch_observables": (ctypes.c_int, [_P, _P]),
     "gl_batch_upload": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "gl_batch_upload_native": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "gl_batch_set_launch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_int32]),
     "gl_batch_get_launch": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -268,6 +273,28 @@ class Event:
                "gl_download")
         return a
 
+    def native_bytes(self, part):
+        """Size of native snapshot part GL_NATIVE_FIELDS or GL_NATIVE_PARTICLES."""
+        return int(lib().gl_native_bytes(self.ctx, part))
+
+    def download_native(self, part, out=None):
+        """Native snapshot part (device layout bytes, gl_download_native) into a
+        new uint8 array, or into `out` (a C-contiguous array of exactly
+        native_bytes(part) bytes, e.g. the numpy view of a pinned tensor)."""
+        n = self.native_bytes(part)
+        a = np.empty(n, dtype=np.uint8) if out is None else out
+        if a.nbytes != n or not a.flags.c_contiguous:
+            raise ValueError("native part %d needs a contiguous buffer of %d bytes" % (part, n))
+        _check(lib().gl_download_native(self.ctx, part, a.ctypes.data_as(ctypes.c_void_p), n), self.ctx,
+               "gl_download_native")
+        return a
+
+    def upload_native(self, part, arr):
+        """Native snapshot part from a C-contiguous buffer (gl_upload_native)."""
+        a = np.ascontiguousarray(arr)
+        _check(lib().gl_upload_native(self.ctx, part, a.ctypes.data_as(ctypes.c_void_p), a.nbytes), self.ctx,
+               "gl_upload_native")
+
 
 class Batch:
     """Many MV events (same precision and time step, any N) advanced together
@@ -362,6 +389,17 @@ class Batch:
         ptrs = (ctypes.c_void_p * self.ne)(*[a.ctypes.data for a in keep])
         counts = (ctypes.c_size_t * self.ne)(*[a.size for a in keep])
         self._chk(lib().gl_batch_upload(self.b, which, ptrs, counts), "gl_batch_upload")
+
+    def upload_native(self, part, arrays):
+        """Native snapshot part of every event from arrays[e] (C-contiguous,
+        e.g. from Event.download_native), with one wait for all events
+        (gl_batch_upload_native)."""
+        keep = [np.ascontiguousarray(a) for a in arrays]
+        if len(keep) != self.ne:
+            raise ValueError("one array per event")
+        ptrs = (ctypes.c_void_p * self.ne)(*[a.ctypes.data for a in keep])
+        sizes = (ctypes.c_size_t * self.ne)(*[a.nbytes for a in keep])
+        self._chk(lib().gl_batch_upload_native(self.b, part, ptrs, sizes), "gl_batch_upload_native")
 
     def observables(self, what=None):
         out = (gl_obs * self.ne)()

@@ -378,6 +378,7 @@ struct gl_batch {
     // trial steps: two streams; fused by push chunk; two streams with 1 and 2
     // resident push blocks per SM beside the 32x8 and the 32x4 tiles
     float tune_step_ms[1 + N_CHUNKS + 4];
+    int* h_bad;  // pinned [ne]: the index-check flags of a native particle upload (allocated on first use)
     char err[256];
 };
 
@@ -528,6 +529,7 @@ gl_status gl_batch_destroy(gl_batch* b) {
     }
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->h_bad) cudaFreeHost(b->h_bad);
     for (int e = 0; e < b->ne; e++) gl_destroy(b->ev[e]);
     delete[] b->ev;
     delete[] b->h_desc;
@@ -997,6 +999,48 @@ gl_status gl_batch_upload(gl_batch* b, gl_buffer which, const double* const* hos
         return bfail(b, st, m);
     }
     return ok ? GL_OK : bfail(b, GL_ERR_CUDA, "batch upload failed");
+}
+
+// as gl_batch_upload: events alternate between the two streams; the index
+// checks of native particles land in pinned host flags read after the wait
+gl_status gl_batch_upload_native(gl_batch* b, gl_native_part part, const void* const* host, const size_t* bytes) {
+    gl::ApiRange range_("gl_batch_upload_native");
+    if (!b || !host || !bytes) return GL_ERR_ARG;
+    if (gl_status s = ensure_aux(b)) return s;
+    const bool parts = part == GL_NATIVE_PARTICLES;
+    if (parts && !b->h_bad && cudaHostAlloc((void**)&b->h_bad, sizeof(int) * b->ne, cudaHostAllocDefault) != cudaSuccess) {
+        b->h_bad = nullptr;
+        return bfail(b, GL_ERR_CUDA, "pinned host allocation failed");
+    }
+    if (parts) memset(b->h_bad, 0, sizeof(int) * b->ne);
+    cudaEventRecord(b->ev_a, b->stream);
+    cudaStreamWaitEvent(b->aux, b->ev_a, 0);
+    gl_status st = GL_OK;
+    int bad = -1;
+    for (int e = 0; e < b->ne && st == GL_OK; e++) {
+        const cudaStream_t s = (e & 1) ? b->aux : b->stream;
+        st = ctx_upload_native_enqueue(b->ev[e], (int)part, host[e], bytes[e], s);
+        if (st != GL_OK) bad = e;
+        else if (parts && bytes[e] > 0)
+            cudaMemcpyAsync(b->h_bad + e, ctx_bad_flag(b->ev[e]), sizeof(int), cudaMemcpyDeviceToHost, s);
+    }
+    cudaEventRecord(b->ev_b, b->aux);
+    cudaStreamWaitEvent(b->stream, b->ev_b, 0);
+    const bool ok = cudaStreamSynchronize(b->stream) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+    if (bad >= 0) {
+        char m[300];
+        snprintf(m, sizeof m, "event %d: %s", bad, gl_error_string(b->ev[bad]));
+        return bfail(b, st, m);
+    }
+    if (!ok) return bfail(b, GL_ERR_CUDA, "batch native upload failed");
+    if (parts)
+        for (int e = 0; e < b->ne; e++)
+            if (b->h_bad[e]) {
+                char m[300];
+                snprintf(m, sizeof m, "event %d: native particles: species or original index out of range (repaired)", e);
+                return bfail(b, GL_ERR_ARG, m);
+            }
+    return GL_OK;
 }
 
 gl_status gl_batch_observables(gl_batch* b, gl_obs* out) { return gl_batch_observables_ex(b, GL_OBS_ALL, out); }

@@ -79,6 +79,7 @@ static void observables_launch(gl_ctx* c, uint32_t what);
 static gl_status observables_read(gl_ctx* c, uint32_t what, gl_obs* o);
 static gl_status transfer_enqueue(gl_ctx* c, gl_buffer which, double* host, size_t count, int to_device);
 static void observables_fill(const gl_ctx* c, uint32_t what, const double* host, gl_obs* o);
+static gl_status native_upload_enqueue(gl_ctx* c, int part, const void* host, size_t bytes, cudaStream_t st);
 }
 
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -229,6 +230,10 @@ gl_status ctx_upload_enqueue(gl_ctx* c, gl_buffer which, const double* host, siz
     c->stream = own;
     return s;
 }
+gl_status ctx_upload_native_enqueue(gl_ctx* c, int part, const void* host, size_t bytes, cudaStream_t st) {
+    return ::native_upload_enqueue(c, part, host, bytes, st);
+}
+const int* ctx_bad_flag(const gl_ctx* c) { return c->d_bad; }
 void ctx_obs_fill(const gl_ctx* c, uint32_t what, const double* host, gl_obs* o) {
     ::observables_fill(c, what, host, o);
 }
@@ -449,6 +454,57 @@ gl_status gl_upload(gl_ctx* c, gl_buffer which, const double* host, size_t count
 gl_status gl_download(gl_ctx* c, gl_buffer which, double* host, size_t count) {
     gl::ApiRange range_("gl_download");
     return transfer(c, which, host, count, 0);
+}
+
+// ------------------------------------------------------------ native snapshots
+static size_t native_bytes(const gl_ctx* c, int part) {
+    if (part == GL_NATIVE_FIELDS) return field_bytes(c->prec, c->Vn);
+    if (part == GL_NATIVE_PARTICLES) return particle_bytes(c->prec, c->np);
+    return 0;
+}
+
+static gl_status native_check(gl_ctx* c, int part, const void* host, size_t bytes) {
+    if (!c || (!host && bytes)) return GL_ERR_ARG;
+    if (part != GL_NATIVE_FIELDS && part != GL_NATIVE_PARTICLES) return fail(c, GL_ERR_ARG, "unknown native part");
+    if (bytes != native_bytes(c, part)) return fail(c, GL_ERR_SIZE, "host buffer size does not match gl_native_bytes()");
+    return GL_OK;
+}
+
+// the copy into the current field slice or the particle arrays, then (for
+// particles) the index check into c->d_bad, all on st
+static gl_status native_upload_enqueue(gl_ctx* c, int part, const void* host, size_t bytes, cudaStream_t st) {
+    if (gl_status s = native_check(c, part, host, bytes)) return s;
+    if (bytes == 0) return GL_OK;
+    void* dst = part == GL_NATIVE_FIELDS ? c->field[c->cur] : c->parts;
+    cudaMemcpyAsync(dst, host, bytes, cudaMemcpyHostToDevice, st);
+    if (part == GL_NATIVE_PARTICLES) {
+        cudaMemsetAsync(c->d_bad, 0, sizeof(int), st);
+        launch_parts_validate(c->prec, c->parts, c->np, c->ns, c->d_bad, st);
+    }
+    return check_cuda(c, "gl_upload_native");
+}
+
+size_t gl_native_bytes(const gl_ctx* c, gl_native_part part) { return c ? native_bytes(c, (int)part) : 0; }
+
+gl_status gl_download_native(gl_ctx* c, gl_native_part part, void* host, size_t bytes) {
+    gl::ApiRange range_("gl_download_native");
+    if (gl_status s = native_check(c, (int)part, host, bytes)) return s;
+    if (bytes == 0) return GL_OK;
+    const void* src = part == GL_NATIVE_FIELDS ? c->field[c->cur] : c->parts;
+    cudaMemcpyAsync(host, src, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, "gl_download_native sync");
+    return check_cuda(c, "gl_download_native");
+}
+
+gl_status gl_upload_native(gl_ctx* c, gl_native_part part, const void* host, size_t bytes) {
+    gl::ApiRange range_("gl_upload_native");
+    if (gl_status s = native_upload_enqueue(c, (int)part, host, bytes, c->stream)) return s;
+    int bad = 0;
+    if (part == GL_NATIVE_PARTICLES && bytes > 0)
+        cudaMemcpyAsync(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, "gl_upload_native sync");
+    if (bad) return fail(c, GL_ERR_ARG, "native particles: species or original index out of range (repaired)");
+    return GL_OK;
 }
 
 gl_status gl_set_step(gl_ctx* c, int64_t step) {

@@ -49,6 +49,9 @@ int launch_mv_init(int prec, void* b, void* scratch, int N, int Ns, double g2mu_
                    uint64_t seed, int* d_bad, cudaStream_t st);
 // canonical FP64 <-> device layout conversions (staging buffer is FP64 canonical)
 void launch_parts_convert(int prec, void* parts, int64_t np, double* stg, int to_device, cudaStream_t st);
+// species and original indices of a native particle upload checked and
+// repaired on the device (*d_bad |= 1 if any was out of range)
+void launch_parts_validate(int prec, void* parts, int64_t np, int ns, int* d_bad, cudaStream_t st);
 // integrated p^tau of the particles <-> canonical [np] in the caller's order
 void launch_ptau_convert(int prec, void* parts, int64_t np, double* stg, int to_device, cudaStream_t st);
 size_t init_scratch_bytes(int64_t Vn);
@@ -156,6 +159,10 @@ void ctx_obs_launch(gl_ctx* c, uint32_t what);
 void ctx_obs_fill(const gl_ctx* c, uint32_t what, const double* row, gl_obs* o);
 // gl_upload without its wait: copies, conversions and a particle sort enqueued on st
 gl_status ctx_upload_enqueue(gl_ctx* c, gl_buffer which, const double* host, size_t count, cudaStream_t st);
+// gl_upload_native enqueued on st: the copy and, for particles, the index
+// check, which sets the context's device flag (read back by the caller)
+gl_status ctx_upload_native_enqueue(gl_ctx* c, int part, const void* host, size_t bytes, cudaStream_t st);
+const int* ctx_bad_flag(const gl_ctx* c);
 
 // observable slots
 enum { PO_COUNT = 0, PO_PX2, PO_PY2, PO_PL2, PO_DPT2, PO_Q2, PO_Q3, PO_N };

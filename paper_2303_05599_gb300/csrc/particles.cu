@@ -291,6 +291,34 @@ __global__ void parts_convert_kernel(Parts<R> P, double* stg, int to_device) {
     }
 }
 
+// indices of a particle array copied in from a native snapshot: a species
+// index outside [0, ns) becomes 0 and an original index outside [0, np) the
+// particle's own position, and *bad is set, so that no later kernel indexes
+// outside its arrays with them
+template <typename R>
+__global__ void parts_validate_kernel(Parts<R> P, int ns, int* bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.np; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = P.sp[i], id = P.id[i];
+        if (s < 0 || s >= ns) {
+            P.sp[i] = 0;
+            atomicOr(bad, 1);
+        }
+        if (id < 0 || (int64_t)id >= P.np) {
+            P.id[i] = (int32_t)i;
+            atomicOr(bad, 1);
+        }
+    }
+}
+
+void launch_parts_validate(int prec, void* parts, int64_t np, int ns, int* d_bad, cudaStream_t st) {
+    const int threads = 256;
+    int64_t blocks = (np + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) return;
+    if (prec == 0) parts_validate_kernel<double><<<(unsigned)blocks, threads, 0, st>>>(carve_parts<double>(parts, np), ns, d_bad);
+    else parts_validate_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(carve_parts<float>(parts, np), ns, d_bad);
+}
+
 void launch_parts_convert(int prec, void* parts, int64_t np, double* stg, int to_device, cudaStream_t st) {
     const int threads = 128;
     int64_t blocks = (np + threads - 1) / threads;

@@ -90,3 +90,32 @@ def test_lattice_units_match_workload_module():
     m, tf, p0, p1 = w.lattice_species()[0]
     assert abs(m - 1.27 * w.a_GeVinv) < 1e-15 and abs(tf - 0.06 / w.a_fm) < 1e-12
     assert math.isinf(w.lattice_species()[1][0])
+
+
+def test_native_snapshot_sizes_and_checks_without_touching_the_gpu():
+    """gl_native_bytes from the configuration alone; a wrong size or an
+    unknown part is refused before any copy."""
+    L = B.lib()
+    w = W.config_small()
+    cfg = B.make_config(w)
+    sp = B.make_species(w)
+    ctx = ctypes.c_void_p()
+    need = L.gl_workspace_bytes(ctypes.byref(cfg), sp, 1)
+    assert L.gl_create(ctypes.byref(cfg), sp, 1, ctypes.c_void_p(0x100000), need, None, ctypes.byref(ctx)) == B.GL_OK
+    n = w.n_particles
+    a256 = lambda b: (b + 255) // 256 * 256
+    if w.precision == W.FP64:
+        per_site = 34 * 16
+        parts = 3 * a256(16 * n) + a256(64 * n) + 2 * a256(4 * n) + 2 * a256(8 * n)
+    else:
+        per_site = 14 * 16
+        parts = a256(16 * n) + a256(8 * n) + a256(32 * n) + 3 * a256(4 * n) + a256(8 * n)
+    assert L.gl_native_bytes(ctx, B.GL_NATIVE_FIELDS) == w.N * w.N * per_site
+    assert L.gl_native_bytes(ctx, B.GL_NATIVE_PARTICLES) == parts
+    assert L.gl_native_bytes(ctx, 5) == 0 and L.gl_native_bytes(None, B.GL_NATIVE_FIELDS) == 0
+    buf = (ctypes.c_uint8 * 64)()
+    assert L.gl_upload_native(ctx, B.GL_NATIVE_FIELDS, buf, 64) == B.GL_ERR_SIZE
+    assert L.gl_download_native(ctx, B.GL_NATIVE_PARTICLES, buf, 64) == B.GL_ERR_SIZE
+    assert L.gl_upload_native(ctx, 9, buf, 64) == B.GL_ERR_ARG
+    assert L.gl_download_native(None, B.GL_NATIVE_FIELDS, buf, 64) == B.GL_ERR_ARG
+    assert L.gl_destroy(ctx) == B.GL_OK
