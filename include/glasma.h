@@ -11,8 +11,9 @@
  * by the library (gl_create / gl_destroy).
  *
  * Every call is enqueued on the CUDA stream given to gl_create and returns
- * without waiting, except gl_upload, gl_download and observables, which wait
- * for the stream.  Calls on one context must not overlap from several host
+ * without waiting, except the uploads and downloads (gl_upload, gl_download,
+ * gl_upload_native, gl_download_native, gl_batch_upload*) and the
+ * observables, which wait for the stream.  Calls on one context must not overlap from several host
  * threads.  Errors are returned as gl_status; gl_error_string gives the last
  * message of a context.  No call aborts the process.
  *
