@@ -379,6 +379,8 @@ struct gl_batch {
     // resident push blocks per SM beside the 32x8 and the 32x4 tiles
     float tune_step_ms[1 + N_CHUNKS + 4];
     int* h_bad;  // pinned [ne]: the index-check flags of a native particle upload (allocated on first use)
+    BObs* p_obs;    // pinned copy of h_obs for its upload, and
+    double* p_rows; // pinned [ne][OBS_W] for the gathered obs rows (both allocated on first use)
     char err[256];
 };
 
@@ -530,6 +532,8 @@ gl_status gl_batch_destroy(gl_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->h_bad) cudaFreeHost(b->h_bad);
+    if (b->p_obs) cudaFreeHost(b->p_obs);
+    if (b->p_rows) cudaFreeHost(b->p_rows);
     for (int e = 0; e < b->ne; e++) gl_destroy(b->ev[e]);
     delete[] b->ev;
     delete[] b->h_desc;
@@ -1077,7 +1081,18 @@ gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
                 cudaMemsetAsync(o.out, 0, GL_MAX_SPECIES * PO_N * sizeof(double), b->stream);
         }
     }
-    cudaMemcpyAsync(b->d_obs, b->h_obs, sizeof(BObs) * b->ne, cudaMemcpyHostToDevice, b->stream);
+    // pinned staging: both copies are plain DMA, without the driver's bounce
+    // buffer (the previous call's copies finished before its wait returned)
+    if (!b->p_obs && (cudaHostAlloc((void**)&b->p_obs, sizeof(BObs) * b->ne, cudaHostAllocDefault) != cudaSuccess ||
+                      cudaHostAlloc((void**)&b->p_rows, sizeof(double) * OBS_W * b->ne, cudaHostAllocDefault) !=
+                          cudaSuccess)) {
+        if (b->p_obs) cudaFreeHost(b->p_obs);
+        b->p_obs = nullptr;
+        b->p_rows = nullptr;
+        return bfail(b, GL_ERR_CUDA, "pinned host allocation failed");
+    }
+    memcpy(b->p_obs, b->h_obs, sizeof(BObs) * b->ne);
+    cudaMemcpyAsync(b->d_obs, b->p_obs, sizeof(BObs) * b->ne, cudaMemcpyHostToDevice, b->stream);
     if (blocks > 0) {
         int ns = 0;
         for (int e = 0; e < b->ne; e++) ns = b->h_obs[e].oa.sp.n_species > ns ? b->h_obs[e].oa.sp.n_species : ns;
@@ -1095,13 +1110,10 @@ gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
     if (what & GL_OBS_FIELDS)
         for (int e = 0; e < b->ne; e++) ctx_obs_launch(b->ev[e], GL_OBS_FIELDS);
     gather_obs_kernel<<<b->ne, 64, 0, b->stream>>>(b->d_obs, b->d_obs_all);
-    double* host = new (std::nothrow) double[(size_t)OBS_W * b->ne];
-    if (!host) return bfail(b, GL_ERR_ARG, "host allocation failed");
-    cudaMemcpyAsync(host, b->d_obs_all, sizeof(double) * OBS_W * b->ne, cudaMemcpyDeviceToHost, b->stream);
+    cudaMemcpyAsync(b->p_rows, b->d_obs_all, sizeof(double) * OBS_W * b->ne, cudaMemcpyDeviceToHost, b->stream);
     const bool ok = cudaStreamSynchronize(b->stream) == cudaSuccess && cudaGetLastError() == cudaSuccess;
     if (ok)
-        for (int e = 0; e < b->ne; e++) ctx_obs_fill(b->ev[e], what, host + (size_t)OBS_W * e, &out[e]);
-    delete[] host;
+        for (int e = 0; e < b->ne; e++) ctx_obs_fill(b->ev[e], what, b->p_rows + (size_t)OBS_W * e, &out[e]);
     return ok ? GL_OK : bfail(b, GL_ERR_CUDA, "batch observables failed");
 }
 
