@@ -26,8 +26,10 @@ def gpu_ready():
 
 
 def events(prec, sort_every=0):
+    # the 5x5 event: one tile wraps around its lattice, and every particle
+    # stays within a few cells of the periodic boundary
     out = []
-    for e, N in enumerate([16, 40, 24, 64]):
+    for e, N in enumerate([16, 40, 24, 64, 5]):
         out.append(W.Workload("b%d" % e, N=N, L_fm=0.04 * N * 2, Ns=4, precision=prec, seed=11 + e,
                               sort_every=sort_every,
                               species=[W.Species(W.M_CHARM, 0.06, 300 + 50 * e, W.REP_F, W.MOM_UNIFORM_PT, 0.0, 5.0),

@@ -155,7 +155,9 @@ def _coupled(N, prec, steps, species=MIXED, seed=3):
     return w, ev, run
 
 
-@pytest.mark.parametrize("N", [16, 37])
+# 4 and 5: a single tile wraps around the whole lattice several times, and
+# every particle crosses the periodic boundary within a few cells
+@pytest.mark.parametrize("N", [4, 5, 16, 37])
 def test_coupled_fp64_parity(N):
     w, ev, run = _coupled(N, W.FP64, 30)
     got = ev.download(B.GL_BUF_PARTICLES)
@@ -186,10 +188,11 @@ def per_particle_rel(got, want):
     return (np.abs(got - want) / scale).max(axis=1)
 
 
-def test_coupled_fp32_error_bounds():
+@pytest.mark.parametrize("N", [5, 32])
+def test_coupled_fp32_error_bounds(N):
     # FP32 positions can round to the other side of a cell edge and take a
     # different colour rotation; the bulk of the ensemble must agree closely
-    w, ev, run = _coupled(32, W.FP32_2ROW, 40)
+    w, ev, run = _coupled(N, W.FP32_2ROW, 40)
     got = ev.download(B.GL_BUF_PARTICLES)
     e = {k: per_particle_rel(got[:, sl], run.part[:, sl])
          for k, sl in [("x", slice(0, 2)), ("p", slice(3, 5)), ("P_eta", slice(5, 6)), ("Q", slice(6, 14))]}
