@@ -112,10 +112,11 @@ def _rel(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(1e-300, np.abs(b).max()))
 
 
-@pytest.mark.parametrize("workload", ["n256_charm_static", "batched64"])
+@pytest.mark.parametrize("workload", ["n256_charm_static", "batched64", "n1024_mixed"])
 def test_full_size_batch_step_against_the_oracle(workload):
-    """The benchmark's configuration at full size: its events (30 x 256^2,
-    or the 64 events of 64/128/256), autotuned launch shapes, CUDA-graph
+    """The benchmark's configurations at full size: their events (30 x 256^2,
+    the 64 events of 64/128/256, or one 1024^2 event with 4e6 charm, beauty
+    and light-like particles), autotuned launch shapes, CUDA-graph
     steps until every species is formed; then one more batched step of
     sampled events (one per lattice size) against one oracle step from their
     downloaded states.  FP32 two-row: 2e-5 relative on every field, the site
@@ -124,6 +125,9 @@ def test_full_size_batch_step_against_the_oracle(workload):
     if workload == "batched64":
         ws = W.config_batched_events()
         sample = [min(i for i, v in enumerate(ws) if v.N == N) for N in (64, 128, 256)]
+    elif workload == "n1024_mixed":
+        ws = [W.config_n1024()]
+        sample = [0]
     else:
         ws = []
         for e in range(30):
