@@ -60,8 +60,8 @@ BATCHED = "batched64"
 # workload for the current kernels (profiles/launches_default_30x256.md).
 # Absent: not captured for the current kernels.
 TRAFFIC = {
-    ("n256_charm_static", 30, "field_step", 1): 440516096 + 759025408,
-    ("n256_charm_static", 30, "wong_push", 1): 861562624 + 212743680,
+    ("n256_charm_static", 30, "field_step", 1): 440508928 + 758149888,
+    ("n256_charm_static", 30, "wong_push", 1): 861613312 + 212559616,
 }
 
 

@@ -37,7 +37,7 @@ struct ExpN;
 template <>
 struct ExpN<double> { static constexpr int n = 20; };
 template <>
-struct ExpN<float> { static constexpr int n = 8; };
+struct ExpN<float> { static constexpr int n = 6; };
 
 template <typename R, int TX, int TY>
 struct Tile {

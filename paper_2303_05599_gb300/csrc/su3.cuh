@@ -445,33 +445,31 @@ __device__ __forceinline__ M3<R> exp_i_alg(const A8<R>& x, R s) {
             }
         c1 *= scl * scl;
     }
-    // det X (real for Hermitian X): cofactor expansion along the first row
-    R m1r, m1i, m2r, m2i, m3r, m3i, pr, pi_, qr, qi;
-    cmul(X.re[1][1], X.im[1][1], X.re[2][2], X.im[2][2], pr, pi_);
-    cmul(X.re[1][2], X.im[1][2], X.re[2][1], X.im[2][1], qr, qi);
-    m1r = pr - qr; m1i = pi_ - qi;
-    cmul(X.re[1][0], X.im[1][0], X.re[2][2], X.im[2][2], pr, pi_);
-    cmul(X.re[1][2], X.im[1][2], X.re[2][0], X.im[2][0], qr, qi);
-    m2r = pr - qr; m2i = pi_ - qi;
-    cmul(X.re[1][0], X.im[1][0], X.re[2][1], X.im[2][1], pr, pi_);
-    cmul(X.re[1][1], X.im[1][1], X.re[2][0], X.im[2][0], qr, qi);
-    m3r = pr - qr; m3i = pi_ - qi;
-    R c0 = (X.re[0][0] * m1r - X.im[0][0] * m1i)
-         - (X.re[0][1] * m2r - X.im[0][1] * m2i)
-         + (X.re[0][2] * m3r - X.im[0][2] * m3i);
-    // coefficients of 1, X, X^2 in (iX)^k / k!, summed
-    R ar = R(1), ai = R(0), br = R(0), bi = R(0), cr = R(0), ci = R(0);
+    // det X of Hermitian X (real diagonal, X_ji = conj X_ij): x00 x11 x22
+    // + 2 Re(x01 x12 conj x02) - x00 |x12|^2 - x11 |x02|^2 - x22 |x01|^2
+    const R pr = X.re[0][1] * X.re[1][2] - X.im[0][1] * X.im[1][2];
+    const R pi_ = X.re[0][1] * X.im[1][2] + X.im[0][1] * X.re[1][2];
+    const R n01 = X.re[0][1] * X.re[0][1] + X.im[0][1] * X.im[0][1];
+    const R n02 = X.re[0][2] * X.re[0][2] + X.im[0][2] * X.im[0][2];
+    const R n12 = X.re[1][2] * X.re[1][2] + X.im[1][2] * X.im[1][2];
+    const R c0 = X.re[0][0] * (X.re[1][1] * X.re[2][2] - n12) - X.re[1][1] * n02 - X.re[2][2] * n01 +
+                 R(2) * (pr * X.re[0][2] + pi_ * X.im[0][2]);
+    // (iX)^k / k! = i^k (a_k + b_k X + g_k X^2) with real a, b, g: from
+    // X^3 = c1 X + c0, a_{k+1} = c0 g_k / (k+1), b_{k+1} = (a_k + c1 g_k) /
+    // (k+1), g_{k+1} = b_k / (k+1).  The factor i^k only decides, at compile
+    // time, which part of the complex sums f0, f1, f2 a term enters, and with
+    // which sign.
+    R a = R(1), b = R(0), g = R(0);
     R f0r = R(1), f0i = R(0), f1r = R(0), f1i = R(0), f2r = R(0), f2i = R(0);
 #pragma unroll
     for (int k = 1; k <= TERMS; k++) {
         const R inv = R(1) / R(k);
-        // a' = i c0 c / k ; b' = i (a + c1 c) / k ; c' = i b / k
-        R nar = -c0 * ci * inv, nai = c0 * cr * inv;
-        R tr_ = ar + c1 * cr, ti = ai + c1 * ci;
-        R nbr = -ti * inv, nbi = tr_ * inv;
-        R ncr = -bi * inv, nci = br * inv;
-        ar = nar; ai = nai; br = nbr; bi = nbi; cr = ncr; ci = nci;
-        f0r += ar; f0i += ai; f1r += br; f1i += bi; f2r += cr; f2i += ci;
+        const R na = c0 * g * inv, nb = (a + c1 * g) * inv, ng = b * inv;
+        a = na; b = nb; g = ng;
+        if ((k & 3) == 1) { f0i += a; f1i += b; f2i += g; }
+        else if ((k & 3) == 2) { f0r -= a; f1r -= b; f2r -= g; }
+        else if ((k & 3) == 3) { f0i -= a; f1i -= b; f2i -= g; }
+        else { f0r += a; f1r += b; f2r += g; }
     }
     M3<R> U;
 #pragma unroll
