@@ -72,8 +72,8 @@ TRAFFIC = {
 # 8 events of the default workload: per site of the field step, and per
 # active particle of its half Wong, half static mix.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-FP64_FLOP_PER_SITE = 5938
-FP64_FLOP_PER_PARTICLE = 616
+FP64_FLOP_PER_SITE = 5332
+FP64_FLOP_PER_PARTICLE = 498
 
 
 def sort_launches(ws):
