@@ -144,9 +144,17 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
+        with open(self.path) as f:
+            return self.summarise(f)
+
+    @staticmethod
+    def summarise(lines):
+        """Median SM clock, the highest maximum clock and the throttle reasons
+        seen active, from lines of the query in Q (CSV, no header, no units)."""
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             p = [x.strip() for x in line.split(",")]
             if len(p) < 9:
                 continue

@@ -1,0 +1,50 @@
+"""Host-side logic of bench.py, without a GPU: the algorithmic bytes behind
+the roofline, the count of sort launches the JSON line claims, and the
+summary of the nvidia-smi clock samples."""
+import math
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_2303_05599_gb300 import workloads as W  # noqa: E402
+
+
+def test_algorithmic_bytes():
+    # FP32 two-row: (24 link + 8 phi + 16 e + 8 pi) floats read and written,
+    # plus 48 site-field floats written
+    assert bench.field_bytes_per_site(1) == 640
+    assert bench.field_bytes_per_site(0) == (36 + 8 + 16 + 8) * 2 * 8 + 48 * 8 == 1472
+    # a particle: 14 reals read and written plus its species index; a site:
+    # 48 site-field reals and 8 scalar reals read
+    assert bench.push_bytes(1, 1000, 64) == 116 * 1000 + 224 * 64
+    assert bench.push_bytes(0, 1000, 64) == 228 * 1000 + 448 * 64
+
+
+def test_sort_launches():
+    # the default batch: two motion classes on 256^2 -> keys below 2^17, three
+    # 8-bit passes: keys, 3 x (histogram, three scans, scatter), gather
+    ws = [W.config_n256() for _ in range(30)]
+    assert bench.sort_launches(ws) == 17
+    # one motion class on 16^2: keys below 2^8, one pass
+    w = W.Workload("one", N=16, L_fm=1.0, species=[W.Species(W.M_CHARM, 0.0, 10, W.REP_F, W.MOM_FIXED_PT, 0.5)])
+    assert bench.sort_launches([w]) == 7
+    # static quarks and eikonal partons are classes of their own
+    w.species.append(W.Species(math.inf, 0.0, 10, W.REP_A, W.MOM_FIXED_PT, 0.0))
+    w.species.append(W.Species(0.0, 0.0, 10, W.REP_F, 3, 10.0))
+    assert bench.sort_launches([w]) == 12  # 3 x 256 - 1 needs 10 bits: two passes
+
+
+def test_clock_summary():
+    lines = ["0, 2070, 2070, 905.1, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+             "0, 2055, 2070, 910.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+             "0, 2070, 2070, 912.3, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+             "malformed line\n",
+             "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active\n"]
+    s = bench.ClockSampler.summarise(lines)
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    slow = ["0, 1200, 2070, 700, 0x8, Active, Not Active, Active, Not Active\n"]
+    assert bench.ClockSampler.summarise(slow)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.ClockSampler.summarise([])["samples"] == 0
