@@ -151,25 +151,85 @@ class ClockSampler:
     def summarise(lines):
         """Median SM clock, the highest maximum clock and the throttle reasons
         seen active, from lines of the query in Q (CSV, no header, no units)."""
-        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        samples = []
         for line in lines:
             p = [x.strip() for x in line.split(",")]
             if len(p) < 9:
                 continue
             try:
-                sm.append(float(p[1]))
-                mx.append(float(p[2]))
+                sm, mx = float(p[1]), float(p[2])
             except ValueError:
                 continue
-            for k, n in enumerate(names):
-                if p[5 + k].lower().startswith("active"):
-                    reasons.add(n)
-        if sm:
-            sm.sort()
-            out = {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
-        return out
+            samples.append((sm, mx, {n for k, n in enumerate(names) if p[5 + k].lower().startswith("active")}))
+        return summarise_clock_samples(samples)
+
+
+def summarise_clock_samples(samples):
+    """(SM MHz, max SM MHz, set of active reasons) samples -> the JSON record."""
+    if not samples:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    sm = sorted(x[0] for x in samples)
+    reasons = set()
+    for x in samples:
+        reasons |= x[2]
+    return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(x[1] for x in samples), "reasons": sorted(reasons),
+            "samples": len(samples)}
+
+
+# NVML throttle-reason bits (nvmlClocksThrottleReason*) reported in the JSON line
+NVML_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+
+class NvmlClockSampler:
+    """The same record from NVML read queries (SM clock, its maximum and the
+    active throttle reasons) polled every 2 ms by a thread, so that a timed
+    region of a few tens of milliseconds still holds many samples.  Needs
+    libnvidia-ml from the driver; start() returns False without it."""
+
+    def __init__(self, device):
+        self.device = device
+        self.samples = []
+        self.thread = None
+
+    def start(self):
+        import threading
+        try:
+            import torch
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return False
+            p = torch.cuda.get_device_properties(self.device)
+            bus = b"%08x:%02x:%02x.0" % (getattr(p, "pci_domain_id", 0), p.pci_bus_id, p.pci_device_id)
+            h = ctypes.c_void_p()
+            if nv.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(h)) != 0:
+                return False
+        except Exception:
+            return False
+        self.nv, self.h = nv, h
+        self.stop_flag = False
+
+        def poll():
+            clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+            while not self.stop_flag:
+                if (nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and  # NVML_CLOCK_SM
+                        nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+                        nv.nvmlDeviceGetCurrentClocksThrottleReasons(h, ctypes.byref(rs)) == 0):
+                    self.samples.append((float(clk.value), float(mx.value),
+                                         {n for bit, n in NVML_REASONS.items() if rs.value & bit}))
+                time.sleep(0.002)
+
+        self.thread = threading.Thread(target=poll, daemon=True)
+        self.thread.start()
+        return True
+
+    def stop(self):
+        if self.thread is None:
+            return summarise_clock_samples([])
+        self.stop_flag = True
+        self.thread.join(timeout=5)
+        self.nv.nvmlShutdown()
+        return dict(summarise_clock_samples(self.samples), source="nvml")
 
 
 def _rel(a, b):
@@ -328,8 +388,10 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        clocks = ClockSampler(local)
-        clocks.start()
+        clocks = NvmlClockSampler(local)
+        if not clocks.start():
+            clocks = ClockSampler(local)
+            clocks.start()
         e0.record(stream)
         batch.step(K)                      # K coupled steps: CUDA-graph replays
         e1.record(stream)

@@ -48,3 +48,52 @@ def test_clock_summary():
     slow = ["0, 1200, 2070, 700, 0x8, Active, Not Active, Active, Not Active\n"]
     assert bench.ClockSampler.summarise(slow)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     assert bench.ClockSampler.summarise([])["samples"] == 0
+
+
+class _FakeNvml:
+    """NVML read queries answered from fixed values (no GPU, no driver)."""
+
+    def __init__(self, reasons):
+        self.reasons = reasons
+        self.bus = None
+
+    def nvmlInit_v2(self):
+        return 0
+
+    def nvmlShutdown(self):
+        return 0
+
+    def nvmlDeviceGetHandleByPciBusId_v2(self, bus, handle):
+        self.bus = bus.value
+        handle._obj.value = 1234
+        return 0
+
+    def nvmlDeviceGetClockInfo(self, h, kind, out):
+        assert kind == 1  # NVML_CLOCK_SM
+        out._obj.value = 1980
+        return 0
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind, out):
+        out._obj.value = 2070
+        return 0
+
+    def nvmlDeviceGetCurrentClocksThrottleReasons(self, h, out):
+        out._obj.value = self.reasons
+        return 0
+
+
+def test_nvml_clock_sampler(monkeypatch):
+    import time
+    import types
+    import torch
+    fake = _FakeNvml(0x4 | 0x1)  # sw_power_cap, and GPU idle (not reported)
+    monkeypatch.setattr(bench.ctypes, "CDLL", lambda name: fake)
+    props = types.SimpleNamespace(pci_domain_id=0, pci_bus_id=0x1b, pci_device_id=0)
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda d: props)
+    s = bench.NvmlClockSampler(0)
+    assert s.start()
+    time.sleep(0.05)
+    rec = s.stop()
+    assert fake.bus == b"00000000:1b:00.0"
+    assert rec["samples"] >= 2 and rec["sm_mhz"] == 1980.0 and rec["sm_max_mhz"] == 2070.0
+    assert rec["reasons"] == ["sw_power_cap"] and rec["source"] == "nvml"
