@@ -25,8 +25,10 @@
  *                            (x, y in lattice units in [0, N); static species keep
  *                            the accumulated longitudinal momentum in the P_eta slot)
  *
- * Parity unpinned: none of the functions below; every one is pinned by a test
- * listed in the oracle section of the design notes.
+ * Parity unpinned: none of the functions below.  Each is pinned by a CPU test
+ * (tests/test_oracle_algebra.py, test_oracle_field.py, test_oracle_particles.py)
+ * against what the paper or the mathematics fixes: closed forms, limiting
+ * cases, conservation laws, brute force and printed values.
  */
 #ifndef ORACLE_GLASMA_H
 #define ORACLE_GLASMA_H

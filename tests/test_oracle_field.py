@@ -194,6 +194,34 @@ def test_uniform_abelian_E_eta_is_static():
     assert np.abs(st.e).max() == 0.0
 
 
+def test_site_E_is_P_over_t_in_a_uniform_abelian_field():
+    # Sec. 3.2 defines the site field as E_i = P^i / tau.  In lattice units
+    # that is e_i / t; for a field uniform in space and time it must hold
+    # exactly, whatever the interpolation.  Cartan-diagonal links (random,
+    # non-uniform) commute with a Cartan e, so the transport of the backward
+    # link momentum is exact too.  Different e at n -+ 1/2 give their mean.
+    N, t = 6, 2.3
+    V = N * N
+    rng = np.random.default_rng(3)
+    u = np.zeros((2, V, 3, 3), dtype=np.complex128)
+    for d in range(2):
+        for s in range(V):
+            u[d, s] = np.diag(np.exp(1j * _diag(*rng.normal(size=2))))
+    e_old = np.zeros((2, V, 8))
+    e_new = np.zeros((2, V, 8))
+    e_old[0, :, 2], e_old[0, :, 7] = 0.37, -0.21
+    e_new[0, :, 2], e_new[0, :, 7] = 0.41, -0.19
+    e_old[1, :, 2] = e_new[1, :, 2] = -0.53
+    old = O.FieldState(N, H.links_to_canon(u), None, e_old, None)
+    new = O.FieldState(N, H.links_to_canon(u), None, e_new, None)
+    site = O.site_fields(old, new, t)
+    assert np.abs(site[0, :, 2] - 0.39 / t).max() < 1e-15
+    assert np.abs(site[0, :, 7] - (-0.20) / t).max() < 1e-15
+    assert np.abs(site[1, :, 2] - (-0.53) / t).max() < 1e-15
+    for a in (0, 1, 3, 4, 5, 6):
+        assert np.abs(site[0:2, :, a]).max() < 1e-16
+
+
 def _rho_python(N, Ns, sigma, seed, nucleus, sheet):
     key = [seed & 0xFFFFFFFF, seed >> 32]
     rho = np.zeros((8, N * N))
@@ -246,9 +274,59 @@ def test_link_matching_abelian_and_residual():
         assert abs(np.linalg.det(U) - 1) < 1e-13
 
 
-def test_mv_init_abelian_has_no_E_eta_and_gauss_zero():
+def test_mv_init_gauss_zero_and_links_unitary():
+    # at tau = 0 the Gauss residual is exactly 0 (e = phi = 0); the links are
+    # SU(3) and the initial E_eta is not trivially zero
     st = mv_state(8)
     assert np.abs(O.gauss(st)).max() == 0.0
     assert np.abs(st.pi).max() > 1e-3
     u, d = O.unitarity(st)
     assert u < 1e-13 and d < 1e-13
+
+
+def _poisson(rho, N, m_a, Lam):
+    k = 2 * np.sin(np.pi * np.arange(N) / N)
+    k2 = k[None, :] ** 2 + k[:, None] ** 2
+    G = 1.0 / (k2 + m_a ** 2)
+    G[0, 0] = 0.0
+    G[k2 > Lam ** 2] = 0.0
+    return np.stack([np.fft.ifft2(np.fft.fft2(rho[a].reshape(N, N)) * G).real.reshape(-1) for a in range(8)], 1)
+
+
+def _E_eta_weak_field(N, alpha_A, alpha_B):
+    """-i sum_i [d_i alpha_A, d_i alpha_B] on the lattice, the commutators of
+    the forward and the backward differences averaged at each site."""
+    s = np.arange(N * N)
+    A = H.alg2mat(alpha_A)
+    B = H.alg2mat(alpha_B)
+    out = np.zeros((N * N, 3, 3), dtype=np.complex128)
+    for dx, dy in ((1, 0), (0, 1)):
+        fw = H.shift(N, s, dx, dy)
+        dA = A[fw] - A
+        dB = B[fw] - B
+        c = dA @ dB - dB @ dA                 # forward difference commutator at x
+        out += 0.5 * (c + c[H.shift(N, s, -dx, -dy)])  # and the backward one (at x - i)
+    return H.mat2alg(-1j * out)
+
+
+def test_mv_init_E_eta_weak_field_limit():
+    # Initial condition of Sec. 2: A^eta(0) = (ig/2)[alpha_A^i, alpha_B^i] with
+    # P^eta = (1/tau) d_tau A_eta and A_eta = -tau^2 A^eta gives
+    # E_eta(0) = -ig [alpha_A^i, alpha_B^i].  For one colour sheet per nucleus
+    # scaled by eps, the pure-gauge fields are alpha^i = -d_i Lambda + O(eps^2)
+    # with Lambda the Poisson solution of each nucleus, so the lattice E_eta(0)
+    # must equal -i sum_i [d_i Lambda_A, d_i Lambda_B] up to a relative O(eps).
+    # A wrong factor, sign or a dropped average fails at O(1).
+    N, m_a, Lam, seed = 8, 0.1, 2.5, 5
+    res = []
+    for eps in (2e-3, 1e-3):
+        st, bad = O.mv_init(N, 1, eps, m_a, Lam, seed)
+        assert bad == 0
+        la = _poisson(_rho_python(N, 1, eps, seed, 0, 0), N, m_a, Lam)
+        lb = _poisson(_rho_python(N, 1, eps, seed, 1, 0), N, m_a, Lam)
+        want = _E_eta_weak_field(N, la, lb)
+        assert np.abs(want).max() > 1e-3 * eps ** 2   # the commutator is not degenerate
+        res.append(np.abs(st.pi - want).max() / np.abs(want).max())
+    # relative residual O(eps): small, and halves with eps
+    assert res[1] < 2e-2
+    assert 1.6 < res[0] / res[1] < 2.4

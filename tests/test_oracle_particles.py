@@ -107,6 +107,30 @@ def test_static_limit_equals_integrated_E_correlator():
     assert np.abs(part[:, 3]).max() > 0.05
 
 
+def test_static_quark_in_a_uniform_E_x_gets_Q_E_integral():
+    # Trivial links, phi = pi = 0 and a uniform Abelian e_x = c T^3: every
+    # force term vanishes, so e_x stays c T^3 and the site field is
+    # E_x = c / t_n (Sec. 3.2: E_i = P^i / tau).  A static quark then gets
+    # p_x = Q^3 c sum_n dt / t_n over its active steps, which approaches
+    # Q^3 c ln(t / t_form) at O(dt); p_y and p_L stay 0.
+    N, dt, tf, c, steps = 4, 0.0625, 0.5, 0.8, 120
+    st = O.FieldState(N)
+    st.e[0, :, 2] = c
+    part = O.sample_species(N, 9, 0, 0, 0, 0.0, 0.0, 40)
+    Q3 = part[:, 8].copy()
+    r = O.Run(st, part, [math.inf], [tf], [0], dt)
+    acc = 0.0
+    for _ in range(steps):
+        if r.t() >= tf:
+            acc += dt / r.t()
+        r.step()
+    assert np.abs(r.st.e[0, :, 2] - c).max() < 1e-14
+    assert np.abs(part[:, 3] - Q3 * c * acc).max() < 1e-13
+    assert np.abs(part[:, 4:6]).max() < 1e-15
+    assert abs(acc - math.log(r.t() / tf)) < dt / tf
+    assert np.abs(part[:, 3]).max() > 0.3
+
+
 def test_static_ensemble_average_and_casimir_scaling():
     # <(Q.X)^2> over the Haar ensemble = T_R X^a X^a (Fierz with <Q^a Q^b> =
     # T_R delta^ab); adjoint over fundamental = q2(A)/q2(F) = 6, i.e. 9/4 after
