@@ -3,12 +3,14 @@
 A step is one pass of the whole hot path over every event of the batch: the
 fused field kernel (leapfrog step of Sec. 2 with the E/B interpolation of
 Sec. 3.2 to the sites) and the particle push (Wong equations with the CPIC
-colour rotation, Sec. 3).  The default workload is 30 events (the paper
-averages 30 MV events, Sec. 7.1) of the 256x256 configuration (L = 10 fm,
-g^2 mu = 2 GeV, m = 0.2 GeV, Ns = 50, dtau = a/8), each with 1e5 charm quarks
-(p_T = 0.5 GeV) and 1e5 static quarks, FP32 two-row links.  All events advance
-together: one field launch and one push launch per step, replayed from a CUDA
-graph, with the field step of t_s overlapping the push of t_{s-1}.
+colour rotation, Sec. 3).  The default workload is the batched one: 64
+independent MV events with N drawn from {64, 128, 256} (event e has
+N = [64, 128, 256][e % 3]), a = 0.04 fm, g^2 mu = 2 GeV, m = 0.2 GeV, Ns = 50,
+dtau = a/8, each with 1e4 charm quarks of p_T ~ U[0, 5] GeV, FP32 two-row
+links re-unitarised in FP64 every 64 steps.  All events advance together:
+one field launch and one push launch per step, replayed from a CUDA graph,
+with the field step of t_s overlapping the push of t_{s-1}.  The timed window
+ends on a re-unitarising step, so its cost is inside the number.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload NAME] [--precision fp32|fp64] [--events E]
@@ -40,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n256_charm_static")
+    ap.add_argument("--workload", default="batched64")
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=6,
@@ -58,14 +60,10 @@ def parse():
 
 BATCHED = "batched64"
 
-# DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
-# keyed by (workload, events per GPU, kernel, precision), captured on the full
-# workload for the current kernels (profiles/launches_default_30x256.md).
-# Absent: not captured for the current kernels.
-TRAFFIC = {
-    ("n256_charm_static", 30, "field_step", 1): 440508928 + 758149888,
-    ("n256_charm_static", 30, "wong_push", 1): 861613312 + 212559616,
-}
+# DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum
+# of one single-kernel capture), keyed by (workload, events per GPU, kernel,
+# precision).  Absent: not captured for the current kernels.
+TRAFFIC = {}
 
 
 # FP64 path: bound by the FP64 pipe (ncu: 90 % of its cycles active), so its
@@ -92,13 +90,43 @@ def sort_launches(ws):
     return 2 + 5 * passes
 
 
-def field_bytes_per_site(prec):
-    """Fused leapfrog + site-field kernel: every field of step n read once, the
-    fields of step n+1 written once (U: 2 links, phi, e: 2, pi) and the six site
-    fields E, B written once."""
+def leapfrog_bytes_per_site(prec):
+    """The leapfrog's own algorithmic bytes: every field of step n read once and
+    the fields of step n+1 written once (U: 2 links, phi, e: 2, pi); FP32 links
+    are stored as two rows."""
     r = 8 if prec == 0 else 4
     links = 36 if prec == 0 else 24
-    return (links + 8 + 16 + 8) * 2 * r + 48 * r
+    return (links + 8 + 16 + 8) * 2 * r
+
+
+def site_field_bytes_per_site(prec):
+    """The six site fields E, B at t_n (48 reals) written once by the same launch."""
+    return 48 * (8 if prec == 0 else 4)
+
+
+def field_bytes_per_site(prec):
+    """Fused leapfrog + site-field kernel: the leapfrog's bytes and the site-field write."""
+    return leapfrog_bytes_per_site(prec) + site_field_bytes_per_site(prec)
+
+
+def timed_window_start(pre, K, every):
+    """First timed step: `pre`, or later so that the K timed steps end on a
+    re-unitarising step (step n re-unitarises when (n + 1) % every == 0)."""
+    if every <= 0:
+        return pre
+    r = every * ((pre + 1 + every - 1) // every) - 1   # first re-unitarising step >= pre
+    return pre if r < pre + K else r - K + 1
+
+
+def representatives(ws):
+    """One event of each lattice size, with the number of events of that size:
+    the CPU samples time these and weight them by the counts."""
+    reps = {}
+    for i, w in enumerate(ws):
+        if w.N not in reps:
+            reps[w.N] = [i, 0]
+        reps[w.N][1] += 1
+    return [(i, c) for i, c in sorted(reps.values())]
 
 
 def push_bytes(prec, n_active, V):
@@ -256,11 +284,11 @@ def _ensemble(part, mass, t, static):
     return out
 
 
-def cpu_baseline(w, ev, args):
-    """The oracle as it stands on the host cores: a few coupled steps of the
-    full lattice and all particles, from the GPU state after the run.  The
-    same steps are then taken by the GPU on that event alone, and the GPU's
-    error against the FP64 oracle is reported for every observable."""
+def _oracle_sample(w, ev, args, budget_s):
+    """The oracle on one event from the GPU state: `cpu_sample_steps` coupled
+    steps, the same steps taken by the GPU on that event, the GPU's errors, and
+    more oracle steps until the sample reaches `budget_s` of CPU time.
+    Returns (seconds per step, steps, errors, step0)."""
     import math
     import numpy as np
     import oracle as O
@@ -298,24 +326,50 @@ def cpu_baseline(w, ev, args):
         "momenta_per_particle_p50_p99": [float(v) for v in np.percentile(
             np.abs(gp[:, 3:6] - run.part[:, 3:6]).max(axis=1) / max(1e-300, np.abs(run.part[:, 3:6]).max()), [50, 99])],
         "charges": _rel(gp[:, 6:14], run.part[:, 6:14]),
-        "cell_flips": "the max values come from the few particles whose FP32 position rounds to the other side "
-                      "of a cell edge (different NGP cell); the percentiles show the rest",
         "ensemble_pT2": {str(s): abs(ens_g[s][0] / ens_o[s][0] - 1) for s in ens_o if ens_o[s][0] > 0},
         "ensemble_pL2": {str(s): abs(ens_g[s][1] / ens_o[s][1] - 1) for s in ens_o if ens_o[s][1] > 0},
     }
     # the timed sample goes on past the compared steps, to a bounded amount of CPU work
     n_steps = k
     t1 = time.perf_counter()
-    while dt + (time.perf_counter() - t1) < args.cpu_sample_seconds:
+    while dt + (time.perf_counter() - t1) < budget_s:
         run.step()
         n_steps += 1
     dt += time.perf_counter() - t1
-    return {"value": w.N * w.N * n_steps / dt, "unit": "site-updates/s", "cores": O.threads(), "kind": "oracle",
-            "sample": "%d coupled steps of the full %dx%d lattice with all %d particles of one event, FP64, from "
-                      "the GPU state at step %d (%.1f s; the first %d also taken by the GPU for error_vs_oracle)"
-                      % (n_steps, w.N, w.N, w.n_particles, step0, dt, k),
-            "particle_steps_per_s": w.n_particles * n_steps / dt,
-            "error_vs_oracle": err}
+    return dt / n_steps, n_steps, err, step0
+
+
+def cpu_baseline(ws, events, args):
+    """The oracle as it stands on the host cores, on a bounded sample of the
+    workload: one event of each lattice size, from the GPU state after the
+    run, for an equal share of `cpu_sample_seconds` each.  The per-step times
+    are weighted by the number of events of each size, so the rate is the
+    oracle's on the whole workload.  The same steps are taken by the GPU on
+    each sampled event, and its errors against the FP64 oracle are reported
+    for every observable."""
+    import oracle as O
+    reps = representatives(ws)
+    budget = args.cpu_sample_seconds / len(reps)
+    t_all = sites = parts = 0.0
+    errors, desc = {}, []
+    for i, count in reps:
+        w = ws[i]
+        t_step, n, err, step0 = _oracle_sample(w, events[i], args, budget)
+        t_all += count * t_step
+        sites += count * w.N * w.N
+        parts += count * w.n_particles
+        errors["N%d" % w.N] = err
+        desc.append("%d steps of a %dx%d event with %d particles from step %d (x%d events)"
+                    % (n, w.N, w.N, w.n_particles, step0, count))
+    return {"value": sites / t_all, "unit": "site-updates/s", "cores": O.threads(), "kind": "oracle",
+            "sample": "FP64 coupled steps of the full lattice with all particles, from the GPU state: " +
+                      "; ".join(desc) + " (%.1f s of CPU time; the per-step times weighted by the event counts; "
+                      "the first %d steps of each also taken by the GPU for error_vs_oracle)"
+                      % (args.cpu_sample_seconds, args.cpu_sample_steps),
+            "particle_steps_per_s": parts / t_all,
+            "error_vs_oracle": errors,
+            "cell_flips": "the max values come from the few particles whose FP32 position rounds to the other "
+                          "side of a cell edge (different NGP cell); the percentiles show the rest"}
 
 
 def events_for(args, rank):
@@ -380,7 +434,7 @@ def run_ours(args):
         # untimed: W warm-up steps, at least up to the first step at which every
         # species is formed (the steady state of the run)
         n_form = max(int(math.ceil(sp.tau_form_fm / (w.dtau_over_a * w.a_fm) - 1e-9)) for w in ws for sp in w.species)
-        pre = max(args.warmup, n_form + 1)
+        pre = timed_window_start(max(args.warmup, n_form + 1), K, ws[0].reunit_every if ws[0].precision else 0)
         batch.step(pre)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -456,6 +510,16 @@ def run_ours(args):
             roof[name] = {"bound": "hbm", "achieved": b / t / 1e9, "peak": hbm, "unit": "GB/s",
                           "frac": b / t / 1e9 / hbm, "traffic": TRAFFIC.get((args.workload, len(ws), name, prec)),
                           "bytes_per_launch": b, "us_per_launch": t * 1e6, "peak_source": peak_src}
+        # the field launch's bytes itemised: the leapfrog's own (each field of
+        # step n read once, step n+1 written once) and the site-field write;
+        # the fraction on the leapfrog's bytes alone stands beside the total
+        t_f = kern["field_step"][1]
+        lf = leapfrog_bytes_per_site(prec) * sites
+        roof["field_step"].update({
+            "bytes_per_site": {"leapfrog": leapfrog_bytes_per_site(prec),
+                               "site_fields": site_field_bytes_per_site(prec)},
+            "frac_leapfrog_bytes_only": lf / t_f / 1e9 / hbm,
+            "achieved_leapfrog_bytes_only": lf / t_f / 1e9})
         if prec == 0:
             flops = {"field_step": FP64_FLOP_PER_SITE * sites, "wong_push": FP64_FLOP_PER_PARTICLE * n_active}
             for name, (b, t) in kern.items():
@@ -505,7 +569,7 @@ def run_ours(args):
             "clocks": ck,
         }
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(ws[0], batch.events[0], args)
+            line["cpu_baseline"] = cpu_baseline(ws, batch.events, args)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -515,8 +579,10 @@ def run_ours(args):
 
 def run_reference(args):
     """The oracle (plain FP64 CPU implementation) on the host cores, same
-    workload, metric and unit; each step is one oracle coupled step of the
-    full lattice with all particles."""
+    workload, metric and unit.  Each step is one oracle coupled step (full
+    lattice, all particles) of one event of each lattice size of the
+    workload; the per-step times are weighted by the number of events of
+    each size, so the rate is the oracle's on the whole workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -525,31 +591,40 @@ def run_reference(args):
     from oracle import build as ob
     ob.build()
     evs = events_for(args, 0)
-    w = evs[0]
-    st, bad = O.mv_init(w.N, w.Ns, w.g2mu_a, w.m_a, w.Lambda_a, w.seed)
-    ls = w.lattice_species()
-    part = np.concatenate([O.sample_species(w.N, w.seed, k, s.rep, s.mom_mode, ls[k][2], ls[k][3], s.count)
-                           for k, s in enumerate(w.species)])
-    run = O.Run(st, part, [s[0] for s in ls], [s[1] for s in ls], [s.rep for s in w.species], w.dt)
-    for _ in range(args.warmup):
-        run.step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        run.step()
-    dt = time.perf_counter() - t0
-    V = w.N * w.N
-    value = V * args.steps / dt
+    runs = []
+    for i, count in representatives(evs):
+        w = evs[i]
+        st, bad = O.mv_init(w.N, w.Ns, w.g2mu_a, w.m_a, w.Lambda_a, w.seed)
+        ls = w.lattice_species()
+        part = np.concatenate([O.sample_species(w.N, w.seed, k, s.rep, s.mom_mode, ls[k][2], ls[k][3], s.count)
+                               for k, s in enumerate(w.species)])
+        runs.append((w, count, O.Run(st, part, [s[0] for s in ls], [s[1] for s in ls], [s.rep for s in w.species],
+                                     w.dt)))
+    t_all = sites = parts = 0.0
+    for w, count, run in runs:
+        for _ in range(args.warmup):
+            run.step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            run.step()
+        t = (time.perf_counter() - t0) / args.steps
+        t_all += count * t
+        sites += count * w.N * w.N
+        parts += count * w.n_particles
+    value = sites / t_all
+    sample = "; ".join("%dx%d with %d particles (x%d events)" % (w.N, w.N, w.n_particles, c) for w, c, _ in runs)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic: oracle MV event and particles",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_all * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic: oracle MV events and particles",
         "config": {"workload": args.workload + (" x %d events" % len(evs) if args.workload != BATCHED else ""),
-                   "N": w.N, "particles": w.n_particles, "precision": "fp64 oracle (CPU)"},
-        "particle_steps_per_s": w.n_particles * args.steps / dt,
+                   "sites": int(sites), "particles": int(parts), "precision": "fp64 oracle (CPU)"},
+        "particle_steps_per_s": parts / t_all,
         "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": O.threads(), "kind": "oracle",
-                         "sample": "event 0 of the workload (%dx%d, %d particles): %d coupled steps of the full "
-                                   "lattice with all particles after %d warm-up steps" % (
-                                       w.N, w.N, w.n_particles, args.steps, args.warmup)},
+                         "sample": "one event of each lattice size: %s; %d coupled steps of the full lattice with "
+                                   "all particles after %d warm-up steps, per-step times weighted by the event "
+                                   "counts (ms_per_step: the whole workload's step, extrapolated so)"
+                                   % (sample, args.steps, args.warmup)},
         "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

@@ -407,10 +407,15 @@ gl_status gl_batch_observables_ex(gl_batch* batch, uint32_t what, gl_obs* out);
  * d_particles: device array of np canonical FP64 records [np][16] (the
  *   GL_BUF_PARTICLES layout, lattice units); np <= GL_NOALLOC_MAX_PARTICLES,
  *   GL_ERR_SIZE otherwise.
- * mass, rep: host arrays of n_species entries (1..GL_MAX_SPECIES): lattice
- *   mass m a (INFINITY = static) and charge representation (0 F, 1 A).
+ * mass, rep, kind: host arrays of n_species entries (1..GL_MAX_SPECIES):
+ *   lattice mass m a, charge representation (0 F, 1 A) and motion class
+ *   (0 Wong particle, 1 static quark of infinite mass, 2 eikonal light-like
+ *   parton of mom_mode 3).  p_L is the lab p_z built from P_eta = tau^2 p^eta
+ *   for class 0 and the accumulated longitudinal momentum in the P_eta slot
+ *   for classes 1 and 2, as in observables().  Other values: GL_ERR_ARG.
  * active_mask: bit s set if species s is included; t: lattice time t_n used
  *   for p_L.
+ * A NaN in a record propagates: into the sums, and into the Casimir maxima.
  * d_out: device array of n_species x 7 doubles per species: count, sum p_x^2,
  *   sum p_y^2, sum p_L^2, sum (p_T^2 - p_T^2 at formation), max |q2 - q2(R)|,
  *   max |q3 - q3(R)|  (lattice units).
@@ -423,7 +428,8 @@ gl_status gl_batch_observables_ex(gl_batch* batch, uint32_t what, gl_obs* out);
  * calls that overlap on the GPU (different streams, or different host threads
  * on one device) race and must be serialised by the caller. */
 gl_status gl_ensemble_sums_noalloc(const double* d_particles, int64_t np, int32_t n_species, const double* mass,
-                                   const int32_t* rep, uint32_t active_mask, double t, double* d_out, void* stream);
+                                   const int32_t* rep, const int32_t* kind, uint32_t active_mask, double t,
+                                   double* d_out, void* stream);
 
 #ifdef __cplusplus
 }

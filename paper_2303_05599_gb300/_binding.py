@@ -78,7 +78,7 @@ SIGNATURES = {
     "gl_autotune": (ctypes.c_int, [_P, _P, _P]),
     "gl_tuning": (ctypes.c_int, [_P, _P, _P]),
     "gl_jets_observables": (ctypes.c_int, [_P, _P]),
-    "gl_ensemble_sums_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P, ctypes.c_uint32,
+    "gl_ensemble_sums_noalloc": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, ctypes.c_uint32,
                                                 ctypes.c_double, _P, _P]),
     "gl_batch_workspace_bytes": (ctypes.c_size_t, [_P, _P, ctypes.c_int32, ctypes.c_int32]),
     "gl_batch_create": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _P,

@@ -34,7 +34,7 @@ static __device__ __align__(256) double na_scratch[NA_MAX_BLOCKS * NA_WIDTH];
 
 struct NaArgs {
     double mass[GL_MAX_SPECIES];
-    int is_static[GL_MAX_SPECIES];
+    int accumulated[GL_MAX_SPECIES];  // static or eikonal: p_L is the accumulated P_eta slot
     double q2ref[GL_MAX_SPECIES], q3ref[GL_MAX_SPECIES];
     int n_species;
 };
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(NA_THREADS) na_sums_kernel(const double* __res
             if (s >= 0) {
                 const double px = p[3], py = p[4], Pe = p[5], eta = p[2];
                 double pl;
-                if (a.is_static[s]) {
+                if (a.accumulated[s]) {
                     pl = Pe;
                 } else {
                     const double w = t > 0 ? Pe / t : 0.0;
@@ -93,19 +93,20 @@ __global__ void __launch_bounds__(NA_THREADS) na_sums_kernel(const double* __res
 #pragma unroll
                 for (int k = 0; k < PO_N; k++) {
                     const double y = __shfl_down_sync(0xffffffffu, x[k], o);
-                    x[k] = na_is_max(k) ? fmax(x[k], y) : x[k] + y;
+                    x[k] = na_is_max(k) ? nanmax(x[k], y) : x[k] + y;
                 }
             if (lane == 0)
                 for (int k = 0; k < PO_N; k++) {
                     double* d = &wacc[warp][sp * PO_N + k];
-                    *d = na_is_max(k) ? fmax(*d, x[k]) : *d + x[k];
+                    *d = na_is_max(k) ? nanmax(*d, x[k]) : *d + x[k];
                 }
         }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < NA_WIDTH; k += NA_THREADS) {
         double acc = 0.0;
-        for (int w = 0; w < NA_THREADS / 32; w++) acc = na_is_max(k % PO_N) ? fmax(acc, wacc[w][k]) : acc + wacc[w][k];
+        for (int w = 0; w < NA_THREADS / 32; w++)
+            acc = na_is_max(k % PO_N) ? nanmax(acc, wacc[w][k]) : acc + wacc[w][k];
         partials[(size_t)blockIdx.x * NA_WIDTH + k] = acc;
     }
 }
@@ -115,7 +116,7 @@ __global__ void na_finish_kernel(const double* partials, int nblocks, int n_spec
         double acc = 0.0;
         for (int b = 0; b < nblocks; b++) {
             const double x = partials[(size_t)b * NA_WIDTH + k];
-            acc = na_is_max(k % PO_N) ? fmax(acc, x) : acc + x;
+            acc = na_is_max(k % PO_N) ? nanmax(acc, x) : acc + x;
         }
         out[k] = acc;
     }
@@ -129,10 +130,13 @@ static void* na_ptr[256];  // device address of na_scratch, per device ordinal
 using namespace gl;
 
 extern "C" gl_status gl_ensemble_sums_noalloc(const double* d_particles, int64_t np, int32_t n_species,
-                                              const double* mass, const int32_t* rep, uint32_t active_mask,
-                                              double t, double* d_out, void* stream) {
-    if (np < 0 || n_species < 1 || n_species > GL_MAX_SPECIES || !mass || !rep || !d_out || (np > 0 && !d_particles))
+                                              const double* mass, const int32_t* rep, const int32_t* kind,
+                                              uint32_t active_mask, double t, double* d_out, void* stream) {
+    if (np < 0 || n_species < 1 || n_species > GL_MAX_SPECIES || !mass || !rep || !kind || !d_out ||
+        (np > 0 && !d_particles))
         return GL_ERR_ARG;
+    for (int k = 0; k < n_species; k++)
+        if (kind[k] < MOTION_WONG || kind[k] > MOTION_EIKONAL || (rep[k] != 0 && rep[k] != 1)) return GL_ERR_ARG;
     if (np > GL_NOALLOC_MAX_PARTICLES) return GL_ERR_SIZE;  // more particles than the static scratch covers
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return GL_ERR_CUDA;
@@ -155,8 +159,8 @@ extern "C" gl_status gl_ensemble_sums_noalloc(const double* d_particles, int64_t
     a.n_species = n_species;
     for (int k = 0; k < GL_MAX_SPECIES; k++) {
         const bool on = k < n_species;
-        a.is_static[k] = on && isinf(mass[k]);
-        a.mass[k] = on && !a.is_static[k] ? mass[k] : 0.0;
+        a.accumulated[k] = on && kind[k] != MOTION_WONG;
+        a.mass[k] = on && !a.accumulated[k] ? mass[k] : 0.0;
         a.q2ref[k] = on && rep[k] == 1 ? 24.0 : 4.0;
         a.q3ref[k] = on && rep[k] == 1 ? 0.0 : 10.0 / 3.0;
     }

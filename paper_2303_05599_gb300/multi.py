@@ -24,7 +24,8 @@ def shard_events(n_events, rank, world):
 
 def local_sums(obs_list, n_species):
     """Per-species sums and maxima over this rank's events, as two arrays
-    [n_species, 5] and [n_species, 2] (from gl_obs records or dicts)."""
+    [n_species, 5] and [n_species, 2] (from gl_obs records or dicts).  A NaN
+    in any event's maximum makes that maximum NaN (np.maximum propagates it)."""
     s = np.zeros((n_species, len(SUM_FIELDS)))
     m = np.zeros((n_species, len(MAX_FIELDS)))
     for o in obs_list:
@@ -32,7 +33,7 @@ def local_sums(obs_list, n_species):
             for j, f in enumerate(SUM_FIELDS):
                 s[k, j] += _get(o, f, k)
             for j, f in enumerate(MAX_FIELDS):
-                m[k, j] = max(m[k, j], _get(o, f, k))
+                m[k, j] = np.maximum(m[k, j], _get(o, f, k))
     return s, m
 
 
@@ -51,11 +52,17 @@ def ensemble_reduce(obs_list, n_species, group=None):
     s, m = local_sums(obs_list, n_species)
     if dist.is_available() and dist.is_initialized():
         dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+        # a collective's MAX need not propagate NaN: the maxima travel with
+        # NaN replaced by -inf, and a count of NaN entries travels beside them
+        nan = np.isnan(m)
         ts = torch.tensor(s, dtype=torch.float64, device=dev)
-        tm = torch.tensor(m, dtype=torch.float64, device=dev)
+        tm = torch.tensor(np.where(nan, -np.inf, m), dtype=torch.float64, device=dev)
+        tn = torch.tensor(nan.astype(np.float64), dtype=torch.float64, device=dev)
         dist.all_reduce(ts, op=dist.ReduceOp.SUM, group=group)
         dist.all_reduce(tm, op=dist.ReduceOp.MAX, group=group)
+        dist.all_reduce(tn, op=dist.ReduceOp.SUM, group=group)
         s, m = ts.cpu().numpy(), tm.cpu().numpy()
+        m = np.where(tn.cpu().numpy() > 0, np.nan, m)
     out = []
     for k in range(n_species):
         n = s[k, 0]

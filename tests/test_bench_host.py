@@ -23,6 +23,39 @@ def test_algorithmic_bytes():
     assert bench.push_bytes(0, 1000, 64) == 228 * 1000 + 448 * 64
 
 
+def test_leapfrog_and_site_field_bytes_are_itemised():
+    # the leapfrog's own bytes (the survey's 448 B per FP32 two-row site) and
+    # the 192 B site-field write add up to the fused launch's bytes
+    assert bench.leapfrog_bytes_per_site(1) == 448
+    assert bench.site_field_bytes_per_site(1) == 192
+    assert bench.leapfrog_bytes_per_site(0) == 1088
+    for prec in (0, 1):
+        assert bench.field_bytes_per_site(prec) == (bench.leapfrog_bytes_per_site(prec)
+                                                    + bench.site_field_bytes_per_site(prec))
+
+
+def test_timed_window_ends_on_a_reunitarising_step():
+    # step n re-unitarises when (n + 1) % every == 0
+    for pre in (3, 13, 40, 63, 64, 100):
+        for K in (1, 5, 20, 60, 64, 200):
+            start = bench.timed_window_start(pre, K, 64)
+            assert start >= pre
+            assert any((n + 1) % 64 == 0 for n in range(start, start + K)), (pre, K, start)
+            # not moved when the window already holds one
+            if any((n + 1) % 64 == 0 for n in range(pre, pre + K)):
+                assert start == pre
+    assert bench.timed_window_start(13, 20, 64) == 44
+    assert bench.timed_window_start(13, 20, 0) == 13
+
+
+def test_representatives_weight_each_lattice_size():
+    ws = W.config_batched_events()
+    reps = bench.representatives(ws)
+    assert [ws[i].N for i, _ in reps] == [64, 128, 256]
+    assert [c for _, c in reps] == [22, 21, 21]
+    assert sum(c for _, c in reps) == len(ws)
+
+
 def test_sort_launches():
     # the default batch: two motion classes on 256^2 -> keys below 2^17, three
     # 8-bit passes: keys, 3 x (histogram, three scans, scatter), gather

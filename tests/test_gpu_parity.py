@@ -17,6 +17,9 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 FP64_TOL = 1e-10
+# FP32 particles without a cell flip, per-particle relative error after 40
+# coupled steps (Euler amplifies field rounding linearly in the step count)
+FP32_PARTICLE_TOL = 2e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -188,17 +191,47 @@ def per_particle_rel(got, want):
     return (np.abs(got - want) / scale).max(axis=1)
 
 
+def ngp_cells(part, N, fp32):
+    """NGP cell of every particle, floor(x + 1/2) in the state's precision
+    (the rule both sides use), wrapped onto the lattice."""
+    if fp32:
+        x = part[:, :2].astype(np.float32)
+        c = np.floor(x + np.float32(0.5)).astype(np.int64)
+    else:
+        c = np.floor(part[:, :2] + 0.5).astype(np.int64)
+    return c % N
+
+
 @pytest.mark.parametrize("N", [5, 32])
 def test_coupled_fp32_error_bounds(N):
-    # FP32 positions can round to the other side of a cell edge and take a
-    # different colour rotation; the bulk of the ensemble must agree closely
-    w, ev, run = _coupled(N, W.FP32_2ROW, 40)
+    # An FP32 position can round to the other side of a cell edge; the particle
+    # then gathers another cell's fields and takes another colour rotation.
+    # Those particles are found exactly, by comparing every step's NGP cells
+    # with the oracle's, and left out; the maximum error of all the others is
+    # bounded.
+    w = wl(N, prec=W.FP32_2ROW, species=MIXED, seed=3)
+    st = oracle_init(w)
+    part = oracle_particles(w)
+    ev = B.Event(w)
+    upload_state(ev, st)
+    ev.upload(B.GL_BUF_PARTICLES, part)
+    run = oracle_run(w, st, part)
     got = ev.download(B.GL_BUF_PARTICLES)
+    flipped = (ngp_cells(got, N, True) != ngp_cells(run.part, N, False)).any(axis=1)
+    steps = 40
+    for _ in range(steps):
+        run.step()
+        ev.step(1)
+        got = ev.download(B.GL_BUF_PARTICLES)
+        flipped |= (ngp_cells(got, N, True) != ngp_cells(run.part, N, False)).any(axis=1)
+    keep = ~flipped
     e = {k: per_particle_rel(got[:, sl], run.part[:, sl])
          for k, sl in [("x", slice(0, 2)), ("p", slice(3, 5)), ("P_eta", slice(5, 6)), ("Q", slice(6, 14))]}
-    summary = {k: (float(np.median(v)), float(np.percentile(v, 95)), float(v.max())) for k, v in e.items()}
-    print("FP32 particle error vs FP64 oracle after 40 steps (median, p95, max):", summary)
-    assert all(s[1] < 1e-3 for s in summary.values())
+    summary = {k: (float(np.median(v[keep])), float(v[keep].max())) for k, v in e.items()}
+    print("FP32 particle error vs FP64 oracle after %d steps, %d of %d particles without a cell flip "
+          "(median, max):" % (steps, keep.sum(), len(keep)), summary)
+    assert keep.sum() >= 0.9 * len(keep)
+    assert all(s[1] < FP32_PARTICLE_TOL for s in summary.values())
     o = ev.observables()
     print("FP32 Casimir drift q2 %s q3 %s" % (list(o.casimir2_dev)[:4], list(o.casimir3_dev)[:4]))
     # relative to the species' q2 (4 fundamental, 24 adjoint): FP32 rounding of
