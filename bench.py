@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--events", type=int, default=0, help="events per GPU (default 30; 1 for n1024_mixed)")
     ap.add_argument("--launch", default=None, help="fixed launch shapes and schedule "
                                                    "TILE:PUSH_BLOCK:PUSH_CHUNK:fused|streams[:PUSH_GRID] "
-                                                   "(e.g. 32x8:128:1024:streams:1) "
+                                                   "(e.g. strip16:128:1024:streams:1) "
                                                    "instead of the autotuner")
     return ap.parse_args()
 

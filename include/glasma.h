@@ -259,13 +259,16 @@ gl_status wong_push(gl_ctx* ctx);
 /* n_steps coupled steps: glasma_step(1) + wong_push each. */
 gl_status gl_step_coupled(gl_ctx* ctx, int32_t n_steps);
 
-/* Choose the tile shape of the field kernel (0: 32x8, 1: 32x4, 2: 32x2, 3: 32x16) and
- * the push block size (64, 128, 256) for this context from timed trial
- * launches (waits).  Needs the particles at the fields' time; the trials write
- * only buffers that the next coupled step rewrites.  Outputs may be NULL. */
+/* Choose the launch shape of the field kernel and the push block size (64,
+ * 128, 256) for this context from timed trial launches.  FP32 field shapes
+ * (the strip kernel: a warp walks up a strip of 32 columns): 0 = 16 warps per
+ * SM, 1 = 12, 2 = 8 (more registers per thread each).  FP64 tiles: 1 = 32x4,
+ * 2 = 32x2.  Results do not depend on the shape.  Waits.  Needs the
+ * particles at the fields' time; the trials write only buffers that the next
+ * coupled step rewrites.  Outputs may be NULL. */
 gl_status gl_autotune(gl_ctx* ctx, int32_t* tile_shape, int32_t* push_block);
 
-/* Trial timings of the last gl_autotune, ms: field_ms[4] by tile shape,
+/* Trial timings of the last gl_autotune, ms: field_ms[4] by field shape,
  * push_ms[3] by block size (0 where not tried). */
 gl_status gl_tuning(const gl_ctx* ctx, float* field_ms, float* push_ms);
 
@@ -299,7 +302,7 @@ gl_status gl_observables_ex(gl_ctx* ctx, uint32_t what, gl_obs* out);
 /* ---- Batches of events ------------------------------------------------
  * Many independent MV events (the paper averages its observables over many
  * events, Sec. 7.1), possibly of different N, advanced together: one coupled
- * step of the whole batch is one field launch over the tiles of every event
+ * step of the whole batch is one field launch over the sites of every event
  * and one push launch over the particles of every event, captured once in a
  * CUDA graph and replayed; the field launch of step s runs concurrently with
  * the push of step s - 1 (the schedule is chosen by gl_batch_autotune).  All
@@ -330,26 +333,28 @@ gl_ctx* gl_batch_event(gl_batch* batch, int32_t e);
 gl_status gl_batch_init(gl_batch* batch);
 
 /* Choose the launch shapes and the step schedule from timed trial launches
- * that do not change the state (waits).  Chosen: the field tile shape (0:
- * 32x8, 1: 32x4, 2: 32x16; FP64 batches use 32x4), by the whole step as for
- * the push; the block size (128,
+ * that do not change the state (waits).  Chosen: the field launch shape (FP32
+ * strips: 0 = 16 warps per SM, 1 = 12, 2 = 8, the rows of all events' strips
+ * split evenly among the resident warps; FP64 batches use the 32x4 tile, 1),
+ * by the whole step as for the push; the block size (128,
  * 256, 512) and chunk (particles per block: 128, 256, 512, 1024) of the
  * separate push kernel, by the time of the whole overlapped step, not of the
  * push alone; and the steady-state step, either
  *   - the field and push kernels on two streams, the push with one block per
  *     chunk of particles or (push_grid 1, 2) that many resident 128-thread
- *     blocks per SM launched ahead of the field tiles (chunks of 1024), or
- *   - one persistent fused launch that interleaves field tiles and push
- *     chunks of 512, 1024 or 2048 particles.
+ *     blocks per SM launched ahead of the field kernel (chunks of 1024), or
+ *   - one persistent fused launch that interleaves field items (FP32: 24
+ *     rows of a strip for each of a block's 8 warps; FP64: 32x4 tiles) and
+ *     push chunks of 512, 1024 or 2048 particles.
  * The push and whole-step trials run on copies of the particles in the spare
  * particle buffers that sorting provides; if an event with particles has
- * sort_every = 0, only the field tile shape is tuned.  Outputs may be NULL. */
+ * sort_every = 0, only the field launch shape is tuned.  Outputs may be NULL. */
 gl_status gl_batch_autotune(gl_batch* batch, int32_t* tile_shape, int32_t* push_block);
 
 /* Set the launch shapes and schedule directly (values as above: push_chunk
  * 128, 256, 512, 1024 or 2048; fused 0 or 1; push_grid 0, 1 or 2, ignored
  * when fused).  Results do not depend on them.
- * GL_ERR_ARG for other values or a tile other than 32x4 in an FP64 batch. */
+ * GL_ERR_ARG for other values or a tile other than 32x4 (1) in an FP64 batch. */
 gl_status gl_batch_set_launch(gl_batch* batch, int32_t tile_shape, int32_t push_block, int32_t push_chunk,
                               int32_t fused, int32_t push_grid);
 
@@ -358,10 +363,11 @@ gl_status gl_batch_get_launch(const gl_batch* batch, int32_t* tile_shape, int32_
                               int32_t* push_chunk, int32_t* fused, int32_t* push_grid);
 
 /* Trial timings of the last autotune, ms (0 where not tried): field_ms[3] by
- * tile shape; push_ms[3] by push block size; step_ms[8] for a whole step:
- * [0] two streams (the fastest tile shape, push block and chunk sizes), [1..3] fused with push chunks of 512, 1024, 2048, [4..7]
- * two streams with push_grid 1 beside the 32x8 and 32x4 tiles, then push_grid
- * 2 beside the same. */
+ * field launch shape; push_ms[3] by push block size; step_ms[8] for a whole
+ * step: [0] two streams (the fastest field shape, push block and chunk sizes),
+ * [1..3] fused with push chunks of 512, 1024, 2048, [4..7] two streams with
+ * push_grid 1 beside field shape 0 (FP64: the 32x8 slot) and 1, then push_grid
+ * 2 beside the same (the best of the other FP32 shapes in the first slot). */
 gl_status gl_batch_tuning(const gl_batch* batch, float* field_ms, float* push_ms, float* step_ms);
 
 /* n_steps coupled steps of every event (all events at one common step). */

@@ -102,7 +102,13 @@ SIGNATURES = {
 
 GL_NOALLOC_MAX_PARTICLES = 2097152
 GL_OBS_PARTICLES, GL_OBS_FIELDS, GL_OBS_ALL = 1, 2, 3
-BATCH_TILES = ("32x8", "32x4", "32x16")
+BATCH_TILES = ("32x8", "32x4", "32x16")   # FP64 field tiles of a batch (32x4 is the one used)
+# FP32 field launch shapes of the strip kernel: resident warps per SM
+STRIP_SHAPES = ("strip16", "strip12", "strip8")
+
+
+def _shape_names(precision):
+    return BATCH_TILES if precision == 0 else STRIP_SHAPES
 
 _lib = None
 
@@ -246,7 +252,8 @@ class Event:
         f = (ctypes.c_float * 4)()
         q = (ctypes.c_float * 3)()
         lib().gl_tuning(self.ctx, f, q)
-        return {"tile": ("32x8", "32x4", "32x2", "32x16")[t.value], "push_block": p.value,
+        names = ("32x8", "32x4", "32x2", "32x16") if self.w.precision == 0 else STRIP_SHAPES + ("strip16",)
+        return {"tile": names[t.value], "push_block": p.value,
                 "field_ms": list(f), "push_ms": list(q)}
 
     def _shape(self, which):
@@ -356,12 +363,17 @@ class Batch:
         """The launch shapes and schedule in use."""
         v = [ctypes.c_int32() for _ in range(5)]
         self._chk(lib().gl_batch_get_launch(self.b, *[ctypes.byref(x) for x in v]), "gl_batch_get_launch")
-        return {"tile": BATCH_TILES[v[0].value], "push_block": v[1].value, "push_chunk": v[2].value,
+        return {"tile": _shape_names(self.ws_list[0].precision)[v[0].value], "push_block": v[1].value,
+                "push_chunk": v[2].value,
                 "fused": bool(v[3].value), "push_grid": v[4].value}
 
     def set_launch(self, tile, push_block=128, push_chunk=1024, fused=False, push_grid=0):
-        """Fix the launch shapes and schedule (tile name from BATCH_TILES)."""
-        self._chk(lib().gl_batch_set_launch(self.b, BATCH_TILES.index(tile), push_block, push_chunk, int(fused),
+        """Fix the launch shapes and schedule (field shape: a name from
+        STRIP_SHAPES for FP32 batches, from BATCH_TILES for FP64 ones)."""
+        names = _shape_names(self.ws_list[0].precision)
+        if tile not in names:
+            raise GlasmaError(GL_ERR_ARG, "set_launch", "field shape %r is not one of %s" % (tile, names))
+        self._chk(lib().gl_batch_set_launch(self.b, names.index(tile), push_block, push_chunk, int(fused),
                                             push_grid), "gl_batch_set_launch")
 
     def step(self, n=1):

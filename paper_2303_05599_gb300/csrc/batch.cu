@@ -25,10 +25,10 @@
 
 #include <new>
 
-#include "fused_body.cuh"
 #include "internal.h"
 #include "obs_body.cuh"
 #include "push_body.cuh"
+#include "strip_body.cuh"
 
 namespace gl {
 
@@ -40,9 +40,10 @@ struct EvDesc {
     void* site[2];   // site fields of t_n in site[n & 1]
     void* parts;
     int N;
-    int tiles_x;     // for the chosen tile shape
-    int tile_begin;  // first block of this event in the field launch
+    int tiles_x;     // FP64: for the chosen tile shape
+    int tile_begin;  // FP64: first block of this event in the field launch
     int chunk_begin; // first block of this event in the push launch
+    int64_t seg_begin;  // FP32: first segment of this event's strips in the flat segment list
     int64_t np;
     double mass[GL_MAX_SPECIES];
     int motion[GL_MAX_SPECIES];
@@ -77,6 +78,33 @@ __device__ __forceinline__ int find_event_warp(const EvDesc* ev, int ne, int blo
         if (m != 0xffffffffu) break;
     }
     return cnt > 0 ? cnt - 1 : 0;
+}
+
+// the last event whose first segment is <= j, found by a whole warp as in
+// find_event_warp
+__device__ __forceinline__ int find_event_seg(const EvDesc* ev, int ne, int64_t j) {
+    const int lane = threadIdx.x & 31;
+    int cnt = 0;
+    for (int g = 0; g < ne; g += 32) {
+        const int k = g + lane;
+        const bool le = k < ne && ev[k].seg_begin <= j;
+        const unsigned m = __ballot_sync(0xffffffffu, le);
+        cnt += __popc(m);
+        if (m != 0xffffffffu) break;
+    }
+    return cnt > 0 ? cnt - 1 : 0;
+}
+
+// FP32 field step of segment j of the batch's flat segment list, by one warp
+// in step with its block (j beyond the list: the last segment, no stores)
+__device__ __forceinline__ void strip_seg_item(const BatchArgs& b, StripWarpSmem& S, int64_t n, const StripStep& a,
+                                               int64_t j, int64_t nseg) {
+    const bool real = j < nseg;
+    if (!real) j = nseg - 1;
+    const EvDesc& d = b.ev[find_event_seg(b.ev, b.ne, j)];
+    const int64_t Vn = (int64_t)d.N * d.N;
+    strip_run_segment(S, carve_fields<float>(d.field[n & 1], Vn), carve_fields<float>(d.field[(n + 1) & 1], Vn),
+                      (float4*)d.site[n & 1], d.N, j - d.seg_begin, real, a);
 }
 
 // one field tile (block `blk` of the tile prefix table) of step n = clock
@@ -156,6 +184,20 @@ __global__ void __launch_bounds__(TX * TY, (Tile<R, TX, TY>::min_blocks)) batch_
     field_item<R, TX, TY>(b, blockIdx.x);
 }
 
+// FP32 field step of the whole batch: blocks of WPB warps take WPB
+// consecutive segments of the flat list per item (nseg segments, `items`
+// items strided over the grid)
+template <int WPB, int MINB>
+__global__ void __launch_bounds__(WPB * 32, MINB) batch_strip_kernel(BatchArgs b, int64_t nseg, int items) {
+    extern __shared__ __align__(16) unsigned char strip_smem[];
+    StripWarpSmem* S = (StripWarpSmem*)strip_smem;
+    const int wib = threadIdx.x >> 5;
+    const int64_t n = *b.clock;
+    const StripStep a = strip_step(n, b.dt, b.reunit_every);
+    for (int it = blockIdx.x; it < items; it += gridDim.x)
+        strip_seg_item(b, S[wib], n, a, (int64_t)it * WPB + wib, nseg);
+}
+
 // at most 64 FP32 registers (B threads, 1024 / B blocks per SM): enough
 // warps per SM to keep the particle and site-field loads in flight
 template <typename R, int B>
@@ -188,6 +230,27 @@ __global__ void __launch_bounds__(128) batch_push_persist_kernel(BatchArgs b, in
 // this launch writes, so the two kinds of work are independent.  Field tiles
 // are bound by issue (SU(3) arithmetic), push chunks by memory latency;
 // sharing every SM between them keeps both busy.
+// The same persistent step with FP32 strips: a field item is 8 consecutive
+// segments, one for each of the block's 8 warps.
+__global__ void __launch_bounds__(256, 1) batch_fused_strip_kernel(BatchArgs b, int lag, int64_t nseg, int n_field,
+                                                                   int n_push) {
+    extern __shared__ __align__(16) unsigned char strip_smem[];
+    StripWarpSmem* S = (StripWarpSmem*)strip_smem;
+    const int wib = threadIdx.x >> 5;
+    const int64_t total = (int64_t)n_field + n_push;
+    for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+        const int64_t f0 = w * n_field / total, f1 = (w + 1) * n_field / total;
+        if (f1 > f0) {
+            const int64_t n = *b.clock;
+            const StripStep a = strip_step(n, b.dt, b.reunit_every);
+            strip_seg_item(b, S[wib], n, a, f0 * 8 + wib, nseg);
+        } else {
+            push_item<float>(b, lag, (int)(w - f0));
+        }
+        __syncthreads();  // shared memory is reused by the next item
+    }
+}
+
 template <typename R, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY, (Tile<R, TX, TY>::min_blocks))
     batch_fused_kernel(BatchArgs b, int lag, int n_field, int n_push) {
@@ -278,22 +341,53 @@ static void set_smem_attr() {
     }
 }
 
+// FP32 strip launch shapes the autotuner chooses from (the tile index of an
+// FP32 batch): warps per block and blocks per SM, i.e. 16 warps per SM at 128
+// registers, 12 at 168, 8 at 255
+static const int STRIP_SHAPES[N_TILES][2] = {{8, 2}, {12, 1}, {8, 1}};
+
+// resident blocks of a strip launch shape on this device (the kernel's own
+// occupancy on an idle GPU)
+template <int WPB, int MINB>
+static int batch_strip_blocks() {
+    static int blocks[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!blocks[dev]) {
+        const int smem = WPB * (int)sizeof(StripWarpSmem);
+        cudaFuncSetAttribute(batch_strip_kernel<WPB, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int per_sm = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_strip_kernel<WPB, MINB>, WPB * 32, smem);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        blocks[dev] = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    }
+    return blocks[dev];
+}
+
+template <int WPB, int MINB>
+static void launch_strip_shape(int64_t nseg, const BatchArgs& b, cudaStream_t st) {
+    if (nseg < 1) return;
+    const int items = (int)((nseg + WPB - 1) / WPB);
+    int grid = batch_strip_blocks<WPB, MINB>();
+    if (grid > items) grid = items;
+    batch_strip_kernel<WPB, MINB><<<grid, WPB * 32, WPB * sizeof(StripWarpSmem), st>>>(b, nseg, items);
+}
+
 template <typename R>
-static void launch_batch_field(int tile, int blocks, const BatchArgs& b, cudaStream_t st) {
+static void launch_batch_field(int tile, int blocks, int64_t nseg, const BatchArgs& b, cudaStream_t st) {
     if constexpr (sizeof(R) == 8) {
         // FP64: the 32x4 tile only (shared memory)
         (void)tile;
+        (void)nseg;
         set_smem_attr<R, 32, 4>();
         batch_field_kernel<R, 32, 4><<<blocks, 128, Tile<R, 32, 4>::bytes, st>>>(b);
-    } else if (tile == TILE_32x8) {
-        set_smem_attr<R, 32, 8>();
-        batch_field_kernel<R, 32, 8><<<blocks, 256, Tile<R, 32, 8>::bytes, st>>>(b);
-    } else if (tile == TILE_32x16) {
-        set_smem_attr<R, 32, 16>();
-        batch_field_kernel<R, 32, 16><<<blocks, 512, Tile<R, 32, 16>::bytes, st>>>(b);
+    } else if (tile == 1) {
+        launch_strip_shape<12, 1>(nseg, b, st);
+    } else if (tile == 2) {
+        launch_strip_shape<8, 1>(nseg, b, st);
     } else {
-        set_smem_attr<R, 32, 4>();
-        batch_field_kernel<R, 32, 4><<<blocks, 128, Tile<R, 32, 4>::bytes, st>>>(b);
+        launch_strip_shape<8, 2>(nseg, b, st);
     }
 }
 
@@ -324,17 +418,38 @@ static void launch_fused_t(const BatchArgs& b, int lag, int n_field, int n_push,
     batch_fused_kernel<R, TX, TY><<<g, TX * TY, Tile<R, TX, TY>::bytes, st>>>(b, lag, n_field, n_push);
 }
 
+// FP32: the persistent fused launch over strip items and push chunks
+static void launch_fused_strip(const BatchArgs& b, int lag, int64_t nseg, int n_push, cudaStream_t st) {
+    static int grid[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    const int smem = 8 * (int)sizeof(StripWarpSmem);
+    if (!grid[dev]) {
+        cudaFuncSetAttribute(batch_fused_strip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int per_sm = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_fused_strip_kernel, 256, smem);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid[dev] = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    }
+    const int n_field = (int)((nseg + 7) / 8);
+    int g = grid[dev];
+    if (g > n_field + n_push) g = n_field + n_push;
+    if (g < 1) return;
+    batch_fused_strip_kernel<<<g, 256, smem, st>>>(b, lag, nseg, n_field, n_push);
+}
+
 template <typename R>
-static void launch_batch_fused(int tile, const BatchArgs& b, int lag, int n_field, int n_push, cudaStream_t st) {
+static void launch_batch_fused(int tile, const BatchArgs& b, int lag, int n_field, int64_t nseg, int n_push,
+                               cudaStream_t st) {
     if constexpr (sizeof(R) == 8) {
         (void)tile;
+        (void)nseg;
         launch_fused_t<R, 32, 4>(b, lag, n_field, n_push, st);
-    } else if (tile == TILE_32x8) {
-        launch_fused_t<R, 32, 8>(b, lag, n_field, n_push, st);
-    } else if (tile == TILE_32x16) {
-        launch_fused_t<R, 32, 16>(b, lag, n_field, n_push, st);
     } else {
-        launch_fused_t<R, 32, 4>(b, lag, n_field, n_push, st);
+        (void)tile;
+        (void)n_field;
+        launch_fused_strip(b, lag, nseg, n_push, st);
     }
 }
 
@@ -368,7 +483,8 @@ struct gl_batch {
     int push_chunk;   // particles per push block
     int fused;        // 1: one persistent fused launch per step; 0: field and push on two streams
     int push_grid;    // two streams: 0 = one push block per chunk, k > 0 = k resident 128-thread blocks per SM
-    int field_blocks;
+    int field_blocks;      // FP64: tiles of all events
+    int64_t field_segs;    // FP32: segments of all events' strips
     int push_blocks;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -511,7 +627,7 @@ gl_status gl_batch_create(const gl_config* cfgs, const gl_species* species, int3
         }
         o += a256b(w);
     }
-    b->tile = b->prec == GL_FP64 ? TILE_32x4 : TILE_32x8;
+    b->tile = b->prec == GL_FP64 ? TILE_32x4 : 0;
     b->push_block = 128;
     b->push_chunk = PUSH_CHUNK;
     b->fused = 0;
@@ -569,6 +685,7 @@ gl_status gl_batch_init(gl_batch* b) {
 // same step with their particles at that step
 static gl_status sync_desc(gl_batch* b) {
     int tb = 0, cb = 0;
+    int64_t rb = 0;
     const int TX = TILE_DIMS[b->tile][0], TY = TILE_DIMS[b->tile][1];
     int64_t step0 = -1;
     for (int e = 0; e < b->ne; e++) {
@@ -588,6 +705,8 @@ static gl_status sync_desc(gl_batch* b) {
         d.tiles_x = (v.N + TX - 1) / TX;
         d.tile_begin = tb;
         tb += d.tiles_x * ((v.N + TY - 1) / TY);
+        d.seg_begin = rb;
+        rb += strip_segments(v.N);
         d.chunk_begin = cb;
         cb += (int)((v.np + b->push_chunk - 1) / b->push_chunk);
         d.np = v.np;
@@ -601,6 +720,7 @@ static gl_status sync_desc(gl_batch* b) {
         }
     }
     b->field_blocks = tb;
+    b->field_segs = rb;
     b->push_blocks = cb;
     // nothing changed since the last upload (the usual case between steps):
     // no copy and no wait
@@ -622,8 +742,8 @@ static BatchArgs batch_args(const gl_batch* b, int reunit_every) {
 
 static void launch_field(gl_batch* b, cudaStream_t st) {
     const BatchArgs a = batch_args(b, b->reunit_every);
-    if (b->prec == GL_FP64) launch_batch_field<double>(b->tile, b->field_blocks, a, st);
-    else launch_batch_field<float>(b->tile, b->field_blocks, a, st);
+    if (b->prec == GL_FP64) launch_batch_field<double>(b->tile, b->field_blocks, b->field_segs, a, st);
+    else launch_batch_field<float>(b->tile, b->field_blocks, b->field_segs, a, st);
 }
 
 static int sm_count() {
@@ -656,8 +776,8 @@ static void launch_push(gl_batch* b, int lag, cudaStream_t st) {
 
 static void launch_fused(gl_batch* b, int lag, cudaStream_t st) {
     const BatchArgs a = batch_args(b, b->reunit_every);
-    if (b->prec == GL_FP64) launch_batch_fused<double>(b->tile, a, lag, b->field_blocks, b->push_blocks, st);
-    else launch_batch_fused<float>(b->tile, a, lag, b->field_blocks, b->push_blocks, st);
+    if (b->prec == GL_FP64) launch_batch_fused<double>(b->tile, a, lag, b->field_blocks, b->field_segs, b->push_blocks, st);
+    else launch_batch_fused<float>(b->tile, a, lag, b->field_blocks, b->field_segs, b->push_blocks, st);
 }
 
 // one steady-state step at clock s, the field step of t_s and the push of the
@@ -701,8 +821,8 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
         if (gl_status s = sync_desc(b)) return s;
         const BatchArgs a = batch_args(b, 0);
         const float ms = time_trial(b, e0, e1, 4, [&] {
-            if (b->prec == GL_FP64) launch_batch_field<double>(tile, b->field_blocks, a, b->stream);
-            else launch_batch_field<float>(tile, b->field_blocks, a, b->stream);
+            if (b->prec == GL_FP64) launch_batch_field<double>(tile, b->field_blocks, b->field_segs, a, b->stream);
+            else launch_batch_field<float>(tile, b->field_blocks, b->field_segs, a, b->stream);
         });
         b->tune_field_ms[tile] = ms;
         if (ms < best_f) { best_f = ms; bt = tile; }
@@ -764,7 +884,7 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
                 // 512-thread tiles; the plain two-stream step tries every
                 // tile shape, since the fastest field kernel alone is not
                 // always the fastest beside the push
-                if (g > 0 && tile == TILE_32x16) continue;
+                if (g > 0 && b->prec == GL_FP64 && tile == TILE_32x16) continue;
                 b->tile = tile;
                 float best_g = 1e30f;
                 for (int kc = 0; kc < (g == 0 ? N_SEP_CHUNKS : 1); kc++) {
@@ -779,8 +899,9 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
                             cudaStreamWaitEvent(b->aux, b->ev_a, 0);
                             launch_push_shape(b, ag, lag, blk, g, b->aux);
                             cudaEventRecord(b->ev_b, b->aux);
-                            if (b->prec == GL_FP64) launch_batch_field<double>(tile, b->field_blocks, ag, b->stream);
-                            else launch_batch_field<float>(tile, b->field_blocks, ag, b->stream);
+                            if (b->prec == GL_FP64)
+                                launch_batch_field<double>(tile, b->field_blocks, b->field_segs, ag, b->stream);
+                            else launch_batch_field<float>(tile, b->field_blocks, b->field_segs, ag, b->stream);
                             cudaStreamWaitEvent(b->stream, b->ev_b, 0);
                         });
                         if (ms < best_g) best_g = ms;
@@ -802,8 +923,11 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
             if (gl_status s = trial_desc(b)) return s;
             const BatchArgs ak = batch_args(b, 0);
             const float ms = time_trial(b, e0, e1, 4, [&] {
-                if (b->prec == GL_FP64) launch_batch_fused<double>(b->tile, ak, lag, b->field_blocks, b->push_blocks, b->stream);
-                else launch_batch_fused<float>(b->tile, ak, lag, b->field_blocks, b->push_blocks, b->stream);
+                if (b->prec == GL_FP64)
+                    launch_batch_fused<double>(b->tile, ak, lag, b->field_blocks, b->field_segs, b->push_blocks,
+                                               b->stream);
+                else launch_batch_fused<float>(b->tile, ak, lag, b->field_blocks, b->field_segs, b->push_blocks,
+                                               b->stream);
             });
             b->tune_step_ms[1 + k] = ms;
             if (ms < best_s) { best_s = ms; bf = 1; bc = PUSH_CHUNKS[k]; bg = 0; bt2 = tile0; }
@@ -889,7 +1013,6 @@ gl_status gl_batch_step(gl_batch* b, int32_t n_steps) {
     if (gl_status s = sync_desc(b)) return s;
     if (gl_status s = ensure_aux(b)) return s;
     if (b->prec == GL_FP64) set_smem_attr<double, 32, 4>();
-    else { set_smem_attr<float, 32, 8>(); set_smem_attr<float, 32, 4>(); set_smem_attr<float, 32, 16>(); }
     // (re)capture the overlapped step when the launch shapes changed
     if (!b->exec || b->graph_tile != b->tile || b->graph_push_block != b->push_block ||
         b->graph_push_chunk != b->push_chunk || b->graph_fused != b->fused || b->graph_push_grid != b->push_grid) {

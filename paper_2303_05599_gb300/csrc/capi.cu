@@ -60,7 +60,6 @@ struct gl_ctx {
     int tile;           // fused-kernel tile shape (gl_autotune)
     int push_block;     // push block size (gl_autotune)
     float tune_field_ms[4], tune_push_ms[3];
-    int reunit_count;
     char err[256];
 };
 
@@ -189,7 +188,6 @@ void ctx_view(const gl_ctx* c, CtxView* v) {
         v->t_form[k] = c->t_form[k];
     }
     v->ns = c->ns;
-    v->reunit_count = c->reunit_count;
     v->parts_alt = c->parts_alt;
     v->sort_every = c->sort_ok ? c->cfg.sort_every : 0;
     v->ptau_diag = c->spp.ptau_diag;
@@ -204,8 +202,6 @@ void ctx_advance(gl_ctx* c, int64_t steps) {
     // by the field step of that time; the other buffer is not tracked
     c->site_time[(c->pstep - 1) & 1] = c->pstep - 1;
     c->site_time[c->pstep & 1] = -1;
-    if (c->prec == GL_FP32_2ROW && c->cfg.reunit_every > 0)
-        c->reunit_count = (int)(c->step % c->cfg.reunit_every);
 }
 size_t ctx_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t ns) {
     return gl_workspace_bytes(cfg, sp, ns);
@@ -376,7 +372,6 @@ gl_status glasma_init(gl_ctx* c) {
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, "glasma_init sync");
     c->step = c->pstep = 0;
     site_forget(c);
-    c->reunit_count = 0;
     if (bad) {
         char m[128];
         snprintf(m, sizeof m, "link matching did not converge on %d links", bad);
@@ -519,21 +514,18 @@ gl_status gl_set_step(gl_ctx* c, int64_t step) {
     }
     c->step = c->pstep = step;
     site_forget(c);
-    // the re-unitarisation period counts from step 0, so a resumed run
-    // re-unitarises at the same steps as an uninterrupted one
-    if (c->prec == GL_FP32_2ROW && c->cfg.reunit_every > 0) c->reunit_count = (int)(step % c->cfg.reunit_every);
     return GL_OK;
 }
 
 // One leapfrog step on stream st; the same kernel interpolates E, B at the
-// fields' time t_step into the site buffer of that time's parity.
+// fields' time t_step into the site buffer of that time's parity.  FP32 links
+// of row y are re-unitarised in the steps n with (n + 1 + y) % reunit_every
+// == 0, a rule of the step index alone, so a resumed run re-unitarises where
+// an uninterrupted one does.
 static void one_field_step(gl_ctx* c, cudaStream_t st) {
-    int reunit = 0;
-    if (c->prec == GL_FP32_2ROW && c->cfg.reunit_every > 0) {
-        if (++c->reunit_count >= c->cfg.reunit_every) { reunit = 1; c->reunit_count = 0; }
-    }
+    const int every = c->prec == GL_FP32_2ROW ? c->cfg.reunit_every : 0;
     launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], site_at(c, c->step), c->N, c->step, c->dt,
-                      reunit, c->tile, st);
+                      every, c->tile, st);
     c->site_time[c->step & 1] = c->step;
     c->cur = 1 - c->cur;
     c->step++;
@@ -653,10 +645,14 @@ gl_status gl_autotune(gl_ctx* c, int32_t* tile_out, int32_t* push_block_out) {
     };
     // field kernel: writes only the spare time slice and the site fields at
     // the current time, both of which the next coupled step rewrites
+    // FP64: tiles 32x4 (1) and 32x2 (2); FP32: strip shapes 0, 1, 2
     const int tiles[4] = {0, 1, 2, 3};
     float best = 1e30f;
     for (int k = 0; k < 4; k++) {
-        if (c->prec == GL_FP64 && (k == 0 || k == 3)) { c->tune_field_ms[k] = 0; continue; }
+        if ((c->prec == GL_FP64 && (k == 0 || k == 3)) || (c->prec != GL_FP64 && k == 3)) {
+            c->tune_field_ms[k] = 0;
+            continue;
+        }
         const float ms = timed([&] {
             launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], site_at(c, c->step), c->N, c->step,
                               c->dt, 0, tiles[k], c->stream);

@@ -31,10 +31,12 @@ struct SpeciesParams {
 };
 
 // field step n -> n+1 on buffers in/out (FP64 or FP32 two-row layout); the
-// same kernel also writes the site E, B at t_n into site (not null)
-// tile: 0 = 32x8, 1 = 32x4, 2 = 32x2, 3 = 32x16 (FP64: 32x4 for 0, 1 and 3)
-void launch_fused_step(int prec, void* in, void* out, void* site, int N, int64_t n, double dt, int reunit, int tile,
-                       cudaStream_t st);
+// same kernel also writes the site E, B at t_n into site (not null).
+// FP32: the strip kernel, tile = launch shape 0 (16 warps per SM), 1 (12) or
+// 2 (8); its links of row y are re-unitarised in FP64 in the steps n with
+// (n + 1 + y) % reunit_every == 0 (0: never).  FP64: tile 2 = 32x2, else 32x4.
+void launch_fused_step(int prec, void* in, void* out, void* site, int N, int64_t n, double dt, int reunit_every,
+                       int tile, cudaStream_t st);
 // site E, B at t_n from buffer n (U, phi, e(n-1/2), pi(n-1/2)) and buffer n+1 (e, pi at n+1/2)
 void launch_site_fields(int prec, const void* bn, const void* bn1, void* site, int N, double t, cudaStream_t st);
 // Euler + CPIC push of all particles active at t_n (bit s of active_mask)
@@ -138,7 +140,6 @@ struct CtxView {
     double t_form[GL_MAX_SPECIES];
     int ptau_diag;
     int ns;
-    int reunit_count;
     void* parts_alt;
     int sort_every;
     void* sort_scratch;

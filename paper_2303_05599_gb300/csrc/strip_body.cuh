@@ -1,0 +1,440 @@
+// FP32 Glasma leapfrog step and site E/B interpolation (Sec. 2.1 and 3.2 of
+// arXiv:2303.05599) on column strips, one warp per strip segment.
+//
+// A warp owns a strip of 32 columns (lane l has x = x0 + l, x0 a multiple of
+// 32) and walks up a range of its rows.  For row y it computes, from U(n),
+// phi(n), e(n-1/2), pi(n-1/2):
+//   the momenta e(n+1/2), pi(n+1/2), the links U(n+1), the scalar phi(n+1),
+//   and the site fields E, B at t_n,
+// with the plaquette A(s) = i[Ux(s) Uy(s+x) Ux(s+y)^+ Uy(s)^+]_ah formed once
+// per site.  The neighbours a site needs come from three places:
+//   x + 1 (Uy, phi):       the next lane, by shuffle (the last valid lane of
+//                          the strip loads its right neighbour itself);
+//   x - 1 (transports by the left link of A, phi and the summed e_x):
+//                          the previous lane computes them as transports by
+//                          its own Ux and hands them over by shuffle; lane 0
+//                          takes them from the halo pass (below);
+//   y - 1 (transports by the lower Uy of A, phi, the summed e_y and Lf):
+//                          carried in registers from the previous row;
+//   y + 1 (Ux, phi):       the next row, already staged in shared memory.
+// So every site does its nine adjoint transports, one plaquette, two
+// exponential link updates, and no work is repeated for halo sites, except
+// the left column once per 23 rows (the halo pass) and one row per segment
+// start (the carries of the row below, a "dry" row whose stores are off).
+//
+// Inputs of a row (the two links as two float4 rows each, phi) are copied by
+// each lane into its own slots of a two-row ring in shared memory with
+// cp.async one row ahead; e and pi go to a one-row slot that is refilled for
+// the next row as soon as this row has read them.  Each lane copies and reads
+// only its own slots, so nothing in a warp waits for another warp: there are
+// no block barriers, only per-thread cp.async waits and one __syncwarp per
+// halo block.
+//
+// Results do not depend on how rows are split among warps: the carries of a
+// segment's first row come from the same loop body (dry), and the values of
+// the column left of a strip always come from the halo pass, whose code does
+// not depend on where its block starts.
+#pragma once
+#include "fused_body.cuh"
+#include "internal.h"
+#include "layout.cuh"
+
+namespace gl {
+
+constexpr int STRIP_W = 32;  // columns per strip = lanes per warp
+constexpr int HALO_B = 23;   // rows per halo block (at most 31: one lane computes the row below)
+constexpr int RING_V = 8;    // float4 per lane per row: Ux (3), Uy (3), phi (2)
+constexpr int RING_X = 5;    // the last lane's right neighbour: Uy (3), phi (2)
+constexpr int MOM_V = 6;     // float4 per lane per row: e_x (2), e_y (2), pi (2)
+
+// 13,600 bytes per warp: 16 warps fit an SM
+struct StripWarpSmem {
+    float4 ring[2][RING_V][STRIP_W];
+    float4 mom[MOM_V][STRIP_W];
+    float4 extra[2][RING_X];
+    float4 halo[HALO_B][6];  // Lf source, bx source, sx source at (x0 - 1, y): 2 float4 each
+};
+
+// step scalars of t_n in single precision, the step index and the
+// re-unitarisation period: the links of row y are re-unitarised in the step
+// n with (n + 1 + y) % every == 0, so each link once every `every` steps and
+// the FP64 work spread evenly over the steps (every = 0: never)
+struct StripStep {
+    float t, dt, inv_t, dt_over_th, dt_th;
+    int every;
+    int64_t n;
+};
+
+__host__ __device__ inline StripStep strip_step(int64_t n, double dt, int every) {
+    const StepArgs a = step_args(0, 0, n, dt, 0);
+    StripStep s;
+    s.t = (float)a.t;
+    s.dt = (float)a.dt;
+    s.inv_t = (float)a.inv_t;
+    s.dt_over_th = (float)a.dt_over_th;
+    s.dt_th = (float)a.dt_th;
+    s.every = every;
+    s.n = n;
+    return s;
+}
+
+// FP64 Gram-Schmidt of rows 0 and 1 of a two-row link, with the reciprocal
+// square roots from the double-precision rsqrt
+__device__ __forceinline__ void reunit_rows(M3<float>& u) {
+    double r0r[3], r0i[3], r1r[3], r1i[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        r0r[j] = u.re[0][j]; r0i[j] = u.im[0][j];
+        r1r[j] = u.re[1][j]; r1i[j] = u.im[1][j];
+    }
+    double n0 = 0;
+#pragma unroll
+    for (int j = 0; j < 3; j++) n0 = fma(r0r[j], r0r[j], fma(r0i[j], r0i[j], n0));
+    n0 = rsqrt(n0);
+#pragma unroll
+    for (int j = 0; j < 3; j++) { r0r[j] *= n0; r0i[j] *= n0; }
+    double cr = 0, ci = 0;  // <r0, r1>
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        cr = fma(r0r[j], r1r[j], fma(r0i[j], r1i[j], cr));
+        ci = fma(r0r[j], r1i[j], fma(-r0i[j], r1r[j], ci));
+    }
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        r1r[j] -= fma(cr, r0r[j], -ci * r0i[j]);
+        r1i[j] -= fma(cr, r0i[j], ci * r0r[j]);
+    }
+    double n1 = 0;
+#pragma unroll
+    for (int j = 0; j < 3; j++) n1 = fma(r1r[j], r1r[j], fma(r1i[j], r1i[j], n1));
+    n1 = rsqrt(n1);
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        u.re[0][j] = (float)r0r[j]; u.im[0][j] = (float)r0i[j];
+        u.re[1][j] = (float)(r1r[j] * n1); u.im[1][j] = (float)(r1i[j] * n1);
+    }
+}
+
+__device__ __forceinline__ M3<float> link_of(const float4 a, const float4 c, const float4 e) {
+    M3<float> m;
+    m.re[0][0] = a.x; m.im[0][0] = a.y; m.re[0][1] = a.z; m.im[0][1] = a.w;
+    m.re[0][2] = c.x; m.im[0][2] = c.y; m.re[1][0] = c.z; m.im[1][0] = c.w;
+    m.re[1][1] = e.x; m.im[1][1] = e.y; m.re[1][2] = e.z; m.im[1][2] = e.w;
+    rebuild_row2(m);
+    return m;
+}
+__device__ __forceinline__ A8<float> alg_of(const float4 a, const float4 b) {
+    A8<float> x;
+    x.v[0] = a.x; x.v[1] = a.y; x.v[2] = a.z; x.v[3] = a.w;
+    x.v[4] = b.x; x.v[5] = b.y; x.v[6] = b.z; x.v[7] = b.w;
+    return x;
+}
+
+__device__ __forceinline__ A8<float> shfl_up_a8(const A8<float>& x) {
+    A8<float> o;
+#pragma unroll
+    for (int c = 0; c < 8; c++) o.v[c] = __shfl_up_sync(0xffffffffu, x.v[c], 1);
+    return o;
+}
+__device__ __forceinline__ A8<float> shfl_down_a8(const A8<float>& x) {
+    A8<float> o;
+#pragma unroll
+    for (int c = 0; c < 8; c++) o.v[c] = __shfl_down_sync(0xffffffffu, x.v[c], 1);
+    return o;
+}
+__device__ __forceinline__ M3<float> shfl_down_m3(const M3<float>& m) {
+    M3<float> o;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            o.re[i][j] = __shfl_down_sync(0xffffffffu, m.re[i][j], 1);
+            o.im[i][j] = __shfl_down_sync(0xffffffffu, m.im[i][j], 1);
+        }
+    return o;
+}
+
+
+// the lane's column geometry within its strip
+struct StripLane {
+    int lane;
+    int x;      // own column (wrapped onto the lattice for lanes beyond it)
+    int xr;     // right neighbour of the last valid lane
+    int xl;     // column left of the strip
+    bool valid; // x0 + lane < N
+    bool last;  // the last valid lane of the strip
+};
+
+__device__ __forceinline__ StripLane strip_lane(int N, int x0) {
+    StripLane L;
+    L.lane = threadIdx.x & 31;
+    const int w = N - x0 < STRIP_W ? N - x0 : STRIP_W;  // valid lanes
+    L.valid = L.lane < w;
+    L.last = L.lane == w - 1;
+    L.x = L.valid ? x0 + L.lane : x0;  // lanes beyond the lattice read a valid column, store nothing
+    L.xr = wrapi(x0 + w, N);
+    L.xl = wrapi(x0 - 1, N);
+    return L;
+}
+
+// row y's links and scalar of this lane (and the last lane's right
+// neighbour) into ring slot k: one cp.async group
+__device__ __forceinline__ void strip_issue_row(StripWarpSmem& S, int k, const Fields<float>& in, int64_t Vn, int N,
+                                                const StripLane& L, int y) {
+    const int64_t g = (int64_t)wrapi(y, N) * N;
+#pragma unroll
+    for (int p = 0; p < 6; p++) cp_async16(&S.ring[k][p][L.lane], in.U + (size_t)p * Vn + g + L.x);
+#pragma unroll
+    for (int p = 0; p < 2; p++) cp_async16(&S.ring[k][6 + p][L.lane], in.phi + (size_t)p * Vn + g + L.x);
+    if (L.last) {
+#pragma unroll
+        for (int p = 0; p < 3; p++) cp_async16(&S.extra[k][p], in.U + (size_t)(3 + p) * Vn + g + L.xr);
+#pragma unroll
+        for (int p = 0; p < 2; p++) cp_async16(&S.extra[k][3 + p], in.phi + (size_t)p * Vn + g + L.xr);
+    }
+    cp_async_commit();
+}
+
+// row y's momenta e_x, e_y, pi of this lane into the momentum slot: one
+// cp.async group
+__device__ __forceinline__ void strip_issue_mom(StripWarpSmem& S, const Fields<float>& in, int64_t Vn, int N,
+                                                const StripLane& L, int y) {
+    const int64_t g = (int64_t)wrapi(y, N) * N + L.x;
+#pragma unroll
+    for (int p = 0; p < 4; p++) cp_async16(&S.mom[p][L.lane], in.e + (size_t)p * Vn + g);
+#pragma unroll
+    for (int p = 0; p < 2; p++) cp_async16(&S.mom[4 + p][L.lane], in.pi + (size_t)p * Vn + g);
+    cp_async_commit();
+}
+
+// Halo pass: the transports by Ux(x0 - 1, y) of A, phi and the summed e_x at
+// the column left of the strip, for rows y0 .. y0 + nb - 1 (nb <= HALO_B), into
+// S.halo[y - y0].  Lane j works on row y0 - 1 + j; it needs the transported
+// plaquette of the row below, which lane j - 1 supplies.
+__device__ __forceinline__ void strip_halo(StripWarpSmem& S, const Fields<float>& in, int64_t Vn, int N, int x0,
+                                           const StripLane& L, int y0, int nb, const StripStep& a) {
+    const int yh = wrapi(y0 - 1 + L.lane, N);
+    const int yu = wrapi(y0 + L.lane, N);
+    const int64_t gl = (int64_t)yh * N + L.xl, g0 = (int64_t)yh * N + x0;
+    const M3<float> Ux = load_link(in.U, 0, gl, Vn);
+    const M3<float> Uy = load_link(in.U, 1, gl, Vn);
+    const M3<float> UyR = load_link(in.U, 1, g0, Vn);
+    // Ux of the row above: the next lane's link, the last lane loads it
+    M3<float> UxU = shfl_down_m3(Ux);
+    if (L.lane == 31) UxU = load_link(in.U, 0, (int64_t)yu * N + L.xl, Vn);
+    const A8<float> ph = load_alg(in.phi, gl, Vn);
+    const A8<float> phR = load_alg(in.phi, g0, Vn);
+    const A8<float> ex = load_alg(in.e, gl, Vn);
+    const A8<float> A = iah_of_mul_nd(mul_nd(mul(Ux, UyR), UxU), Uy);
+    const A8<float> Dn = shfl_up_a8(conj_dn_t(Uy, A));
+    const A8<float> tx = conj_up_t(Ux, phR);
+    const A8<float> cx = icomm(tx, ph);
+    const float t = a.t, dt = a.dt, inv_t = a.inv_t;
+    A8<float> es;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        const float en = ex.v[c] + dt * (t * (A.v[c] - Dn.v[c]) + inv_t * cx.v[c]);
+        es.v[c] = ex.v[c] + en;
+    }
+    const A8<float> lf = conj_dn_t(Ux, A);
+    const A8<float> bx = conj_dn_t(Ux, ph);
+    const A8<float> sx = conj_dn_t(Ux, es);
+    if (L.lane >= 1 && L.lane <= nb) {
+        float4* h = S.halo[L.lane - 1];
+        h[0] = make_float4(lf.v[0], lf.v[1], lf.v[2], lf.v[3]);
+        h[1] = make_float4(lf.v[4], lf.v[5], lf.v[6], lf.v[7]);
+        h[2] = make_float4(bx.v[0], bx.v[1], bx.v[2], bx.v[3]);
+        h[3] = make_float4(bx.v[4], bx.v[5], bx.v[6], bx.v[7]);
+        h[4] = make_float4(sx.v[0], sx.v[1], sx.v[2], sx.v[3]);
+        h[5] = make_float4(sx.v[4], sx.v[5], sx.v[6], sx.v[7]);
+    }
+    __syncwarp();
+}
+
+// the transports carried from row y - 1 to row y (all by Uy(x, y - 1))
+struct StripCarry {
+    A8<float> dn;  // plaquette below: Uy^+ A Uy
+    A8<float> by;  // scalar below: Uy^+ phi Uy
+    A8<float> sy;  // summed e_y below: Uy^+ (e_y(n-1/2) + e_y(n+1/2)) Uy
+    A8<float> cr;  // Lf below: Uy^+ Lf Uy (the fourth clover leaf)
+};
+
+// Rows y_begin .. y_end - 1 of the strip at x0 (y_end - y_begin <= N) for
+// the fields of step n in `in`: step n + 1 into `out`, the site fields of t_n
+// into `site`.  Rows at or beyond y_stop store nothing (dummy rows, which keep
+// the warps of a block in step; y_stop <= y_end).  With `sync`, every row
+// starts at a block barrier, so all warps of the block must call this with
+// the same y_end - y_begin.
+__device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<float>& in, const Fields<float>& out,
+                                              float4* site, int N, int x0, int y_begin, int y_end, int y_stop,
+                                              const StripStep& a, bool sync) {
+    const int64_t Vn = (int64_t)N * N;
+    const StripLane L = strip_lane(N, x0);
+    const float t = a.t, dt = a.dt, inv_t = a.inv_t, c_link = a.dt_over_th, dt_th = a.dt_th;
+    const float q = 0.25f * inv_t, hf = 0.5f * inv_t;
+
+    StripCarry C;
+    C.dn = C.by = C.sy = C.cr = a_zero<float>();
+    // rows r = y_begin - 1 (dry: only its carries are formed) .. y_end - 1
+    const int r_first = y_begin - 1;
+    strip_issue_row(S, 0, in, Vn, N, L, r_first);
+    strip_issue_row(S, 1, in, Vn, N, L, r_first + 1);
+    strip_issue_mom(S, in, Vn, N, L, r_first);
+    int halo_end = r_first;  // rows below halo_end have halo values in S.halo
+    int halo_base = r_first;
+#pragma unroll 1
+    for (int r = r_first; r < y_end; r++) {
+        if (sync) __syncthreads();
+        if (r == halo_end) {
+            const int nb = y_end - r < HALO_B ? y_end - r : HALO_B;
+            strip_halo(S, in, Vn, N, x0, L, r, nb, a);
+            halo_base = r;
+            halo_end = r + nb;
+        }
+        const bool dry = r < y_begin;
+        const bool st = !dry && L.valid && r < y_stop;
+        const int k = (r - r_first) & 1, k1 = k ^ 1;
+        const int y = wrapi(r, N);
+        const int64_t g = (int64_t)y * N + L.x;
+        // rows r and r + 1 are in the ring (r + 1 was issued a row ago), and
+        // row r's momenta in their slot
+        cp_async_wait_group<0>();
+        const M3<float> Ux = link_of(S.ring[k][0][L.lane], S.ring[k][1][L.lane], S.ring[k][2][L.lane]);
+        const M3<float> Uy = link_of(S.ring[k][3][L.lane], S.ring[k][4][L.lane], S.ring[k][5][L.lane]);
+        const A8<float> ph = alg_of(S.ring[k][6][L.lane], S.ring[k][7][L.lane]);
+        M3<float> UyR = shfl_down_m3(Uy);
+        if (L.last) UyR = link_of(S.extra[k][0], S.extra[k][1], S.extra[k][2]);
+        const M3<float> UxN = link_of(S.ring[k1][0][L.lane], S.ring[k1][1][L.lane], S.ring[k1][2][L.lane]);
+        const A8<float> phN = alg_of(S.ring[k1][6][L.lane], S.ring[k1][7][L.lane]);
+
+        // Each value is used as soon as it is known and the outputs stored as
+        // they are formed, so that few values live at once.  The dry row forms
+        // only what the carries need (A, Lf, the e_y update).
+        const A8<float> A = iah_of_mul_nd(mul_nd(mul(Ux, UyR), UxN), Uy);   // plaquette at (x, y)
+        const float4* h = S.halo[r - halo_base];
+        // clover: A, its transports from x - 1 (Lf, by the left lane's Ux) and
+        // from y - 1, and the fourth leaf carried from the row below
+        A8<float> Lf = shfl_up_a8(conj_dn_t(Ux, A));
+        if (L.lane == 0) Lf = alg_of(h[0], h[1]);
+        A8<float> lap = a_zero<float>();  // the covariant Laplacian of phi, x part first
+        if (!dry) {
+            A8<float> Be;
+#pragma unroll
+            for (int c = 0; c < 8; c++) Be.v[c] = 0.25f * (((A.v[c] + Lf.v[c]) + C.dn.v[c]) + C.cr.v[c]);
+            if (st) store_alg(site + (size_t)10 * Vn, g, Vn, Be);
+            // x direction: D_x phi, the e_x update, E_x, the x link
+            A8<float> phR = shfl_down_a8(ph);
+            if (L.last) phR = alg_of(S.extra[k][3], S.extra[k][4]);
+            A8<float> bx = shfl_up_a8(conj_dn_t(Ux, ph));
+            if (L.lane == 0) bx = alg_of(h[2], h[3]);
+            const A8<float> tx = conj_up_t(Ux, phR);
+            const A8<float> cx = icomm(tx, ph);
+            A8<float> By;
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                By.v[c] = hf * (tx.v[c] - bx.v[c]);
+                lap.v[c] = tx.v[c] + bx.v[c];
+            }
+            if (st) store_alg(site + (size_t)8 * Vn, g, Vn, By);
+            const A8<float> ex = alg_of(S.mom[0][L.lane], S.mom[1][L.lane]);
+            A8<float> exn, exs;
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                exn.v[c] = ex.v[c] + dt * (t * (A.v[c] - C.dn.v[c]) + inv_t * cx.v[c]);
+                exs.v[c] = ex.v[c] + exn.v[c];
+            }
+            A8<float> sx = shfl_up_a8(conj_dn_t(Ux, exs));
+            if (L.lane == 0) sx = alg_of(h[4], h[5]);
+            A8<float> Ex;
+#pragma unroll
+            for (int c = 0; c < 8; c++) Ex.v[c] = q * (exs.v[c] + sx.v[c]);
+            if (st) {
+                store_alg(site, g, Vn, Ex);
+                store_alg_cs(out.e, g, Vn, exn);
+                M3<float> nx = mul(exp_i_alg<float, ExpN<float>::n>(exn, c_link), Ux);
+                if (a.every > 0 && (a.n + 1 + y) % a.every == 0) reunit_rows(nx);
+                store_link_cs(out.U, 0, g, Vn, nx);
+            }
+        }
+        const A8<float> ty = conj_up_t(Uy, phN);
+        const A8<float> cy = icomm(ty, ph);
+        // every value read from ring slot k has been used by now: row r + 2 goes there
+        if (r + 2 <= y_end) strip_issue_row(S, k, in, Vn, N, L, r + 2);
+        // y direction: D_y phi, the e_y update, E_y, the scalar and pi
+        const A8<float> ey = alg_of(S.mom[2][L.lane], S.mom[3][L.lane]);
+        A8<float> eyn, eys;
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            eyn.v[c] = ey.v[c] + dt * (t * (Lf.v[c] - A.v[c]) + inv_t * cy.v[c]);
+            eys.v[c] = ey.v[c] + eyn.v[c];
+        }
+        if (!dry) {
+            const A8<float> po = alg_of(S.mom[4][L.lane], S.mom[5][L.lane]);
+            A8<float> Ey, Ee, Bx, pn, phn;
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                Ey.v[c] = q * (eys.v[c] + C.sy.v[c]);
+                Bx.v[c] = -hf * (ty.v[c] - C.by.v[c]);
+                pn.v[c] = po.v[c] + dt * inv_t * ((lap.v[c] + (ty.v[c] + C.by.v[c])) - 4.0f * ph.v[c]);
+                phn.v[c] = ph.v[c] + dt_th * pn.v[c];
+                Ee.v[c] = 0.5f * (po.v[c] + pn.v[c]);
+            }
+            if (st) {
+                store_alg(site + (size_t)2 * Vn, g, Vn, Ey);
+                store_alg(site + (size_t)4 * Vn, g, Vn, Ee);
+                store_alg(site + (size_t)6 * Vn, g, Vn, Bx);
+                store_alg_cs(out.e + (size_t)2 * Vn, g, Vn, eyn);
+                store_alg_cs(out.pi, g, Vn, pn);
+                store_alg_cs(out.phi, g, Vn, phn);
+            }
+        }
+        // the momentum slot's values are all used: the next row's go there
+        if (r + 1 < y_end) strip_issue_mom(S, in, Vn, N, L, r + 1);
+        if (st) {
+            M3<float> ny = mul(exp_i_alg<float, ExpN<float>::n>(eyn, c_link), Uy);
+            if (a.every > 0 && (a.n + 1 + y) % a.every == 0) reunit_rows(ny);
+            store_link_cs(out.U, 1, g, Vn, ny);
+        }
+        // the carries for row r + 1, by this row's Uy
+        C.dn = conj_dn_t(Uy, A);
+        C.by = conj_dn_t(Uy, ph);
+        C.sy = conj_dn_t(Uy, eys);
+        C.cr = conj_dn_t(Uy, Lf);
+    }
+    cp_async_wait_group<0>();
+}
+
+// Work split: the strips of an event are cut into segments of STRIP_SEG rows
+// (the last one shorter when STRIP_SEG does not divide N); segment j of the
+// event is strip j / nblk, rows from (j % nblk) STRIP_SEG, nblk = the
+// segments per strip.  A block of W warps takes W consecutive segments of the
+// flat list and runs them in step, a barrier per row; warps beyond the list
+// repeat its last segment without storing.
+constexpr int STRIP_SEG = 16;
+
+__host__ __device__ inline int64_t strip_segments(int N) {
+    return (int64_t)((N + STRIP_W - 1) / STRIP_W) * ((N + STRIP_SEG - 1) / STRIP_SEG);
+}
+
+struct StripSeg {
+    int x0, y0, len;
+};
+
+__device__ __forceinline__ StripSeg strip_seg_of(int N, int64_t j) {
+    const int nblk = (N + STRIP_SEG - 1) / STRIP_SEG;
+    const int strip = (int)(j / nblk), blk = (int)(j - (int64_t)strip * nblk);
+    StripSeg g;
+    g.x0 = strip * STRIP_W;
+    g.y0 = blk * STRIP_SEG;
+    g.len = N - g.y0 < STRIP_SEG ? N - g.y0 : STRIP_SEG;
+    return g;
+}
+
+// one segment of an event in step with the block (real: store its rows)
+__device__ __forceinline__ void strip_run_segment(StripWarpSmem& S, const Fields<float>& in, const Fields<float>& out,
+                                                  float4* site, int N, int64_t j, bool real, const StripStep& a) {
+    const StripSeg g = strip_seg_of(N, j);
+    strip_segment(S, in, out, site, N, g.x0, g.y0, g.y0 + STRIP_SEG, real ? g.y0 + g.len : g.y0, a, true);
+}
+
+}  // namespace gl

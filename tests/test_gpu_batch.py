@@ -316,7 +316,7 @@ def test_schedules_agree(prec):
     schedules (push one block per chunk, or resident push blocks) evolve the
     batch bitwise alike, across sort segments."""
     ws = events(prec, sort_every=5)
-    tile = "32x4" if prec == W.FP64 else "32x8"
+    tile = "32x4" if prec == W.FP64 else "strip16"
     shapes = [dict(tile=tile, push_block=128, push_chunk=1024, fused=False, push_grid=0),
               dict(tile=tile, push_block=256, push_chunk=512, fused=True, push_grid=0),
               dict(tile=tile, push_block=128, push_chunk=2048, fused=True, push_grid=0),
@@ -325,7 +325,9 @@ def test_schedules_agree(prec):
               dict(tile=tile, push_block=128, push_chunk=128, fused=False, push_grid=0),
               dict(tile=tile, push_block=256, push_chunk=256, fused=False, push_grid=0)]
     if prec != W.FP64:
-        shapes.append(dict(tile="32x16", push_block=512, push_chunk=1024, fused=True, push_grid=0))
+        # the other strip launch shapes: rows split among 12 or 8 warps per SM
+        shapes.append(dict(tile="strip12", push_block=512, push_chunk=1024, fused=False, push_grid=0))
+        shapes.append(dict(tile="strip8", push_block=128, push_chunk=512, fused=False, push_grid=1))
     results = []
     for sh in shapes:
         batch = B.Batch(ws)
@@ -351,6 +353,8 @@ def test_set_launch_rejects_bad_shapes():
     batch = B.Batch(ws)
     with pytest.raises(B.GlasmaError):
         batch.set_launch("32x8")          # FP64 batches use 32x4
+    with pytest.raises(B.GlasmaError):
+        batch.set_launch("strip16")       # FP32 launch shapes only
     with pytest.raises(B.GlasmaError):
         batch.set_launch("32x4", push_block=100)
     with pytest.raises(B.GlasmaError):
