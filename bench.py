@@ -377,22 +377,27 @@ def events_for(args, rank):
     workload (the paper averages 30 events, Sec. 7.1), or the 64 uneven events
     of the batched workload."""
     from paper_2303_05599_gb300 import workloads as W
-    if args.workload == BATCHED:
-        evs = W.config_batched_events()
-        for w in evs:
-            w.seed = w.seed + 64 * rank
-        return evs
-    n = args.events if args.events else (1 if W.WORKLOADS[args.workload]().N >= 1024 else 30)
-    evs = []
-    for e in range(n):
-        w = W.WORKLOADS[args.workload]()
-        w.n_jets = 0  # jet-correlator probes run on the single-event API only
+
+    def options(w):
         if args.reunit_every is not None:
             w.reunit_every = args.reunit_every
         if args.precision == "fp64":
             w.precision = W.FP64
         elif args.precision == "fp32":
             w.precision = W.FP32_2ROW
+        return w
+
+    if args.workload == BATCHED:
+        evs = W.config_batched_events()
+        for w in evs:
+            w.seed = w.seed + 64 * rank
+            options(w)
+        return evs
+    n = args.events if args.events else (1 if W.WORKLOADS[args.workload]().N >= 1024 else 30)
+    evs = []
+    for e in range(n):
+        w = options(W.WORKLOADS[args.workload]())
+        w.n_jets = 0  # jet-correlator probes run on the single-event API only
         w.seed = rank * n + e
         evs.append(w)
     return evs

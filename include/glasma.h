@@ -362,12 +362,20 @@ gl_status gl_batch_set_launch(gl_batch* batch, int32_t tile_shape, int32_t push_
 gl_status gl_batch_get_launch(const gl_batch* batch, int32_t* tile_shape, int32_t* push_block,
                               int32_t* push_chunk, int32_t* fused, int32_t* push_grid);
 
+/* FP32 batches: the rows per strip segment of the field kernel in use (the
+ * unit of work of one warp: the strips of all events are cut into segments of
+ * this length and spread over the resident warps; chosen by a cost model of
+ * the launch shape's resident warps, or by gl_batch_autotune from trial
+ * launches).  Results do not depend on it.  0 for FP64 batches or NULL. */
+int32_t gl_batch_segment_rows(const gl_batch* batch);
+
 /* Trial timings of the last autotune, ms (0 where not tried): field_ms[3] by
- * field launch shape; push_ms[3] by push block size; step_ms[8] for a whole
- * step: [0] two streams (the fastest field shape, push block and chunk sizes),
- * [1..3] fused with push chunks of 512, 1024, 2048, [4..7] two streams with
- * push_grid 1 beside field shape 0 (FP64: the 32x8 slot) and 1, then push_grid
- * 2 beside the same (the best of the other FP32 shapes in the first slot). */
+ * field launch shape (the fastest of its segment lengths); push_ms[3] by push
+ * block size; step_ms[8] for a whole step: [0] two streams (the fastest field
+ * shape, push block and chunk sizes), [1..3] fused with push chunks of 512,
+ * 1024, 2048, [4..7] two streams with push_grid 1 beside field shape 0 (FP64:
+ * the 32x8 slot) and 1, then push_grid 2 beside the same (the best of the
+ * other FP32 shapes in the first slot). */
 gl_status gl_batch_tuning(const gl_batch* batch, float* field_ms, float* push_ms, float* step_ms);
 
 /* n_steps coupled steps of every event (all events at one common step). */

@@ -98,6 +98,7 @@ SIGNATURES = {
                                            ctypes.c_int32]),
     "gl_batch_get_launch": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "gl_batch_observables_ex": (ctypes.c_int, [_P, ctypes.c_uint32, _P]),
+    "gl_batch_segment_rows": (ctypes.c_int32, [_P]),
 }
 
 GL_NOALLOC_MAX_PARTICLES = 2097152
@@ -364,7 +365,7 @@ class Batch:
         v = [ctypes.c_int32() for _ in range(5)]
         self._chk(lib().gl_batch_get_launch(self.b, *[ctypes.byref(x) for x in v]), "gl_batch_get_launch")
         return {"tile": _shape_names(self.ws_list[0].precision)[v[0].value], "push_block": v[1].value,
-                "push_chunk": v[2].value,
+                "push_chunk": v[2].value, "segment_rows": int(lib().gl_batch_segment_rows(self.b)),
                 "fused": bool(v[3].value), "push_grid": v[4].value}
 
     def set_launch(self, tile, push_block=128, push_chunk=1024, fused=False, push_grid=0):

@@ -60,6 +60,7 @@ struct BatchArgs {
     int reunit_every;
     const int64_t* clock;
     int push_chunk;  // particles per push block
+    int seg_rows;    // FP32: rows per strip segment
 };
 
 // the last event whose first block is <= block (the prefix tables are
@@ -104,7 +105,7 @@ __device__ __forceinline__ void strip_seg_item(const BatchArgs& b, StripWarpSmem
     const EvDesc& d = b.ev[find_event_seg(b.ev, b.ne, j)];
     const int64_t Vn = (int64_t)d.N * d.N;
     strip_run_segment(S, carve_fields<float>(d.field[n & 1], Vn), carve_fields<float>(d.field[(n + 1) & 1], Vn),
-                      (float4*)d.site[n & 1], d.N, j - d.seg_begin, real, a);
+                      (float4*)d.site[n & 1], d.N, j - d.seg_begin, real, a, b.seg_rows);
 }
 
 // one field tile (block `blk` of the tile prefix table) of step n = clock
@@ -342,9 +343,8 @@ static void set_smem_attr() {
 }
 
 // FP32 strip launch shapes the autotuner chooses from (the tile index of an
-// FP32 batch): warps per block and blocks per SM, i.e. 16 warps per SM at 128
-// registers, 12 at 168, 8 at 255
-static const int STRIP_SHAPES[N_TILES][2] = {{8, 2}, {12, 1}, {8, 1}};
+// FP32 batch), warps per block x blocks per SM: 0 = 8 x 2 (16 warps per SM at
+// 128 registers), 1 = 12 x 1 (168 registers), 2 = 8 x 1 (255 registers)
 
 // resident blocks of a strip launch shape on this device (the kernel's own
 // occupancy on an idle GPU)
@@ -372,6 +372,13 @@ static void launch_strip_shape(int64_t nseg, const BatchArgs& b, cudaStream_t st
     int grid = batch_strip_blocks<WPB, MINB>();
     if (grid > items) grid = items;
     batch_strip_kernel<WPB, MINB><<<grid, WPB * 32, WPB * sizeof(StripWarpSmem), st>>>(b, nseg, items);
+}
+
+// warps per block and resident blocks of FP32 strip launch shape `tile`
+static void strip_shape_geometry(int tile, int* wpb, int* blocks) {
+    if (tile == 1) { *wpb = 12; *blocks = batch_strip_blocks<12, 1>(); }
+    else if (tile == 2) { *wpb = 8; *blocks = batch_strip_blocks<8, 1>(); }
+    else { *wpb = 8; *blocks = batch_strip_blocks<8, 2>(); }
 }
 
 template <typename R>
@@ -485,6 +492,8 @@ struct gl_batch {
     int push_grid;    // two streams: 0 = one push block per chunk, k > 0 = k resident 128-thread blocks per SM
     int field_blocks;      // FP64: tiles of all events
     int64_t field_segs;    // FP32: segments of all events' strips
+    int seg_rows;          // FP32: rows per segment, for the current launch shape
+    int seg_tuned[N_TILES];  // FP32: the autotuner's segment length per launch shape (0: the cost model's)
     int push_blocks;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -492,7 +501,7 @@ struct gl_batch {
     float tune_field_ms[N_TILES];
     float tune_push_ms[3];
     // trial steps: two streams; fused by push chunk; two streams with 1 and 2
-    // resident push blocks per SM beside the 32x8 and the 32x4 tiles
+    // resident push blocks per SM beside field shapes 0 and 1
     float tune_step_ms[1 + N_CHUNKS + 4];
     int* h_bad;  // pinned [ne]: the index-check flags of a native particle upload (allocated on first use)
     BObs* p_obs;    // pinned copy of h_obs for its upload, and
@@ -628,6 +637,7 @@ gl_status gl_batch_create(const gl_config* cfgs, const gl_species* species, int3
         o += a256b(w);
     }
     b->tile = b->prec == GL_FP64 ? TILE_32x4 : 0;
+    b->seg_rows = 16;  // replaced by the first descriptor sync
     b->push_block = 128;
     b->push_chunk = PUSH_CHUNK;
     b->fused = 0;
@@ -688,6 +698,21 @@ static gl_status sync_desc(gl_batch* b) {
     int64_t rb = 0;
     const int TX = TILE_DIMS[b->tile][0], TY = TILE_DIMS[b->tile][1];
     int64_t step0 = -1;
+    if (b->prec != GL_FP64) {
+        // the segment length that spreads all events' strips evenly over the
+        // resident warps of the current launch shape
+        int wpb = 8, blocks = 1;
+        strip_shape_geometry(b->tile, &wpb, &blocks);
+        int* Ns = new (std::nothrow) int[b->ne];
+        if (!Ns) return bfail(b, GL_ERR_ARG, "out of host memory");
+        for (int e = 0; e < b->ne; e++) {
+            CtxView v;
+            ctx_view(b->ev[e], &v);
+            Ns[e] = v.N;
+        }
+        b->seg_rows = b->seg_tuned[b->tile] > 0 ? b->seg_tuned[b->tile] : strip_seg_rows(Ns, b->ne, wpb, blocks);
+        delete[] Ns;
+    }
     for (int e = 0; e < b->ne; e++) {
         CtxView v;
         ctx_view(b->ev[e], &v);
@@ -706,7 +731,7 @@ static gl_status sync_desc(gl_batch* b) {
         d.tile_begin = tb;
         tb += d.tiles_x * ((v.N + TY - 1) / TY);
         d.seg_begin = rb;
-        rb += strip_segments(v.N);
+        rb += b->prec != GL_FP64 ? strip_segments(v.N, b->seg_rows) : 0;
         d.chunk_begin = cb;
         cb += (int)((v.np + b->push_chunk - 1) / b->push_chunk);
         d.np = v.np;
@@ -737,7 +762,7 @@ static gl_status sync_desc(gl_batch* b) {
 }
 
 static BatchArgs batch_args(const gl_batch* b, int reunit_every) {
-    return BatchArgs{b->d_desc, b->ne, b->dt, reunit_every, b->d_clock, b->push_chunk};
+    return BatchArgs{b->d_desc, b->ne, b->dt, reunit_every, b->d_clock, b->push_chunk, b->seg_rows};
 }
 
 static void launch_field(gl_batch* b, cudaStream_t st) {
@@ -818,14 +843,36 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
     for (int tile = 0; tile < N_TILES; tile++) {
         if (b->prec == GL_FP64 && tile != TILE_32x4) continue;  // FP64 tile must fit shared memory
         b->tile = tile;
-        if (gl_status s = sync_desc(b)) return s;
-        const BatchArgs a = batch_args(b, 0);
-        const float ms = time_trial(b, e0, e1, 4, [&] {
-            if (b->prec == GL_FP64) launch_batch_field<double>(tile, b->field_blocks, b->field_segs, a, b->stream);
-            else launch_batch_field<float>(tile, b->field_blocks, b->field_segs, a, b->stream);
-        });
-        b->tune_field_ms[tile] = ms;
-        if (ms < best_f) { best_f = ms; bt = tile; }
+        // FP32: the segment lengths tried beside the cost model's choice (its
+        // half and double, and 16 rows); the fastest is kept for the shape
+        int cand[4] = {0, 0, 0, 0}, nc = 1;
+        if (b->prec != GL_FP64) {
+            b->seg_tuned[tile] = 0;
+            if (gl_status s = sync_desc(b)) return s;
+            const int m = b->seg_rows;
+            const int more[3] = {16, 2 * m, m / 2};
+            cand[0] = m;
+            for (int k = 0; k < 3; k++) {
+                bool dup = more[k] < 4;
+                for (int c = 0; c < nc; c++) dup = dup || cand[c] == more[k];
+                if (!dup) cand[nc++] = more[k];
+            }
+        }
+        float best_t = 1e30f;
+        int best_seg = 0;
+        for (int c = 0; c < nc; c++) {
+            if (b->prec != GL_FP64) b->seg_tuned[tile] = cand[c];
+            if (gl_status s = sync_desc(b)) return s;
+            const BatchArgs a = batch_args(b, 0);
+            const float ms = time_trial(b, e0, e1, 4, [&] {
+                if (b->prec == GL_FP64) launch_batch_field<double>(tile, b->field_blocks, b->field_segs, a, b->stream);
+                else launch_batch_field<float>(tile, b->field_blocks, b->field_segs, a, b->stream);
+            });
+            if (ms < best_t) { best_t = ms; best_seg = cand[c]; }
+        }
+        if (b->prec != GL_FP64) b->seg_tuned[tile] = best_seg;
+        b->tune_field_ms[tile] = best_t;
+        if (best_t < best_f) { best_f = best_t; bt = tile; }
     }
     b->tile = bt;
     if (gl_status s = sync_desc(b)) return s;
@@ -887,12 +934,13 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
                 if (g > 0 && b->prec == GL_FP64 && tile == TILE_32x16) continue;
                 b->tile = tile;
                 float best_g = 1e30f;
-                for (int kc = 0; kc < (g == 0 ? N_SEP_CHUNKS : 1); kc++) {
-                    b->push_chunk = g == 0 ? SEP_CHUNKS[kc] : PUSH_CHUNK;
+                const bool per_chunk = g == 0;  // separate push blocks, one per chunk
+                for (int kc = 0; kc < (per_chunk ? N_SEP_CHUNKS : 1); kc++) {
+                    b->push_chunk = per_chunk ? SEP_CHUNKS[kc] : PUSH_CHUNK;
                     if (gl_status s = trial_desc(b)) return s;
                     const BatchArgs ag = batch_args(b, 0);
-                    for (int kb = 0; kb < (g == 0 ? 3 : 1); kb++) {
-                        const int blk = g == 0 ? PUSH_BLOCKS[kb] : 128;
+                    for (int kb = 0; kb < (per_chunk ? 3 : 1); kb++) {
+                        const int blk = per_chunk ? PUSH_BLOCKS[kb] : 128;
                         if (blk > b->push_chunk) continue;  // threads without particles
                         const float ms = time_trial(b, e0, e1, 4, [&] {
                             cudaEventRecord(b->ev_a, b->stream);
@@ -910,7 +958,7 @@ gl_status gl_batch_autotune(gl_batch* b, int32_t* tile_out, int32_t* push_block_
                             bt2 = tile;
                             bg = g;
                             bc = b->push_chunk;
-                            if (g == 0) bp = blk;
+                            if (per_chunk) bp = blk;
                         }
                     }
                 }
@@ -1257,6 +1305,8 @@ gl_status gl_batch_set_launch(gl_batch* b, int32_t tile, int32_t push_block, int
     b->push_grid = fused ? 0 : push_grid;
     return GL_OK;
 }
+
+int32_t gl_batch_segment_rows(const gl_batch* b) { return b && b->prec != GL_FP64 ? b->seg_rows : 0; }
 
 gl_status gl_batch_get_launch(const gl_batch* b, int32_t* tile, int32_t* push_block, int32_t* push_chunk,
                               int32_t* fused, int32_t* push_grid) {

@@ -57,7 +57,8 @@ struct gl_ctx {
     int cur;
     int64_t step, pstep;
     int64_t site_time[2];  // time index n whose site fields site_buf[n & 1] holds (-1: none)
-    int tile;           // fused-kernel tile shape (gl_autotune)
+    int tile;           // field-kernel launch shape (gl_autotune)
+    int seg;            // FP32: rows per strip segment (gl_autotune; 0: the cost model's)
     int push_block;     // push block size (gl_autotune)
     float tune_field_ms[4], tune_push_ms[3];
     char err[256];
@@ -316,6 +317,7 @@ gl_status gl_create(const gl_config* cfg, const gl_species* sp, int32_t ns, void
     c->step = c->pstep = 0;
     site_forget(c);
     c->tile = 0;
+    c->seg = 0;
     c->push_block = 128;
     *out = c;
     return GL_OK;
@@ -525,7 +527,7 @@ gl_status gl_set_step(gl_ctx* c, int64_t step) {
 static void one_field_step(gl_ctx* c, cudaStream_t st) {
     const int every = c->prec == GL_FP32_2ROW ? c->cfg.reunit_every : 0;
     launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], site_at(c, c->step), c->N, c->step, c->dt,
-                      every, c->tile, st);
+                      every, c->tile, c->seg, st);
     c->site_time[c->step & 1] = c->step;
     c->cur = 1 - c->cur;
     c->step++;
@@ -645,7 +647,8 @@ gl_status gl_autotune(gl_ctx* c, int32_t* tile_out, int32_t* push_block_out) {
     };
     // field kernel: writes only the spare time slice and the site fields at
     // the current time, both of which the next coupled step rewrites
-    // FP64: tiles 32x4 (1) and 32x2 (2); FP32: strip shapes 0, 1, 2
+    // FP64: tiles 32x4 (1) and 32x2 (2); FP32: strip shapes 0, 1, 2, each with
+    // the cost model's segment length, its half and double, and 16 rows
     const int tiles[4] = {0, 1, 2, 3};
     float best = 1e30f;
     for (int k = 0; k < 4; k++) {
@@ -653,12 +656,27 @@ gl_status gl_autotune(gl_ctx* c, int32_t* tile_out, int32_t* push_block_out) {
             c->tune_field_ms[k] = 0;
             continue;
         }
-        const float ms = timed([&] {
-            launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], site_at(c, c->step), c->N, c->step,
-                              c->dt, 0, tiles[k], c->stream);
-        });
-        c->tune_field_ms[k] = ms;
-        if (ms < best) { best = ms; c->tile = tiles[k]; }
+        int cand[4] = {0, 0, 0, 0}, nc = 1;
+        if (c->prec != GL_FP64) {
+            const int m = strip_model_seg(c->N, tiles[k]);
+            const int more[3] = {16, 2 * m, m / 2};
+            cand[0] = m;
+            for (int j = 0; j < 3; j++) {
+                bool dup = more[j] < 4;
+                for (int q = 0; q < nc; q++) dup = dup || cand[q] == more[j];
+                if (!dup) cand[nc++] = more[j];
+            }
+        }
+        float best_k = 1e30f;
+        for (int q = 0; q < nc; q++) {
+            const float ms = timed([&] {
+                launch_fused_step(c->prec, c->field[c->cur], c->field[1 - c->cur], site_at(c, c->step), c->N,
+                                  c->step, c->dt, 0, tiles[k], cand[q], c->stream);
+            });
+            if (ms < best_k) best_k = ms;
+            if (ms < best) { best = ms; c->tile = tiles[k]; c->seg = cand[q]; }
+        }
+        c->tune_field_ms[k] = best_k;
     }
     // push: on a copy of the particles, at a step where every species is formed
     if (c->np && c->parts_alt) {

@@ -35,8 +35,11 @@ struct SpeciesParams {
 // FP32: the strip kernel, tile = launch shape 0 (16 warps per SM), 1 (12) or
 // 2 (8); its links of row y are re-unitarised in FP64 in the steps n with
 // (n + 1 + y) % reunit_every == 0 (0: never).  FP64: tile 2 = 32x2, else 32x4.
+// seg: FP32 rows per strip segment (0: the cost model's choice for the shape)
 void launch_fused_step(int prec, void* in, void* out, void* site, int N, int64_t n, double dt, int reunit_every,
-                       int tile, cudaStream_t st);
+                       int tile, int seg, cudaStream_t st);
+// the cost model's segment length for an N x N lattice and FP32 launch shape `tile`
+int strip_model_seg(int N, int tile);
 // site E, B at t_n from buffer n (U, phi, e(n-1/2), pi(n-1/2)) and buffer n+1 (e, pi at n+1/2)
 void launch_site_fields(int prec, const void* bn, const void* bn1, void* site, int N, double t, cudaStream_t st);
 // Euler + CPIC push of all particles active at t_n (bit s of active_mask)

@@ -34,14 +34,14 @@ static void launch_t(void* in, void* out, void* site, int N, int64_t n, double d
 // strips per item and run them in step; `items` items strided over the grid
 template <int WPB, int MINB>
 __global__ void __launch_bounds__(WPB * 32, MINB) strip_step_kernel(Fields<float> in, Fields<float> out, float4* site,
-                                                                     int N, StripStep a, int items) {
+                                                                     int N, StripStep a, int items, int seg) {
     extern __shared__ __align__(16) unsigned char strip_smem[];
     StripWarpSmem* S = (StripWarpSmem*)strip_smem;
     const int wib = threadIdx.x >> 5;
-    const int64_t nseg = strip_segments(N);
+    const int64_t nseg = strip_segments(N, seg);
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
         const int64_t j = (int64_t)it * WPB + wib;
-        strip_run_segment(S[wib], in, out, site, N, j < nseg ? j : nseg - 1, j < nseg, a);
+        strip_run_segment(S[wib], in, out, site, N, j < nseg ? j : nseg - 1, j < nseg, a, seg);
     }
 }
 
@@ -64,28 +64,37 @@ static int strip_blocks() {
 }
 
 template <int WPB, int MINB>
-static void launch_strip(void* in, void* out, void* site, int N, int64_t n, double dt, int every, cudaStream_t st) {
+static void launch_strip(void* in, void* out, void* site, int N, int64_t n, double dt, int every, int seg,
+                         cudaStream_t st) {
     const int64_t Vn = (int64_t)N * N;
-    const int items = (int)((strip_segments(N) + WPB - 1) / WPB);
     int grid = strip_blocks<WPB, MINB>();
+    if (seg <= 0) seg = strip_seg_rows(&N, 1, WPB, grid);
+    const int items = (int)((strip_segments(N, seg) + WPB - 1) / WPB);
     if (grid > items) grid = items;
     strip_step_kernel<WPB, MINB><<<grid, WPB * 32, WPB * sizeof(StripWarpSmem), st>>>(
-        carve_fields<float>(in, Vn), carve_fields<float>(out, Vn), (float4*)site, N, strip_step(n, dt, every), items);
+        carve_fields<float>(in, Vn), carve_fields<float>(out, Vn), (float4*)site, N, strip_step(n, dt, every), items,
+        seg);
 }
 
 void launch_fused_step(int prec, void* in, void* out, void* site, int N, int64_t n, double dt, int reunit_every,
-                       int tile, cudaStream_t st) {
+                       int tile, int seg, cudaStream_t st) {
     if (prec == 0) {
         // FP64 tiles: 32x4 (139 KB of shared memory) or 32x2
         if (tile == 2) launch_t<double, 32, 2>(in, out, site, N, n, dt, st);
         else launch_t<double, 32, 4>(in, out, site, N, n, dt, st);
     } else if (tile == 1) {
-        launch_strip<12, 1>(in, out, site, N, n, dt, reunit_every, st);
+        launch_strip<12, 1>(in, out, site, N, n, dt, reunit_every, seg, st);
     } else if (tile == 2) {
-        launch_strip<8, 1>(in, out, site, N, n, dt, reunit_every, st);
+        launch_strip<8, 1>(in, out, site, N, n, dt, reunit_every, seg, st);
     } else {
-        launch_strip<8, 2>(in, out, site, N, n, dt, reunit_every, st);
+        launch_strip<8, 2>(in, out, site, N, n, dt, reunit_every, seg, st);
     }
+}
+
+int strip_model_seg(int N, int tile) {
+    if (tile == 1) return strip_seg_rows(&N, 1, 12, strip_blocks<12, 1>());
+    if (tile == 2) return strip_seg_rows(&N, 1, 8, strip_blocks<8, 1>());
+    return strip_seg_rows(&N, 1, 8, strip_blocks<8, 2>());
 }
 
 }  // namespace gl

@@ -404,37 +404,59 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
     cp_async_wait_group<0>();
 }
 
-// Work split: the strips of an event are cut into segments of STRIP_SEG rows
-// (the last one shorter when STRIP_SEG does not divide N); segment j of the
-// event is strip j / nblk, rows from (j % nblk) STRIP_SEG, nblk = the
-// segments per strip.  A block of W warps takes W consecutive segments of the
-// flat list and runs them in step, a barrier per row; warps beyond the list
-// repeat its last segment without storing.
-constexpr int STRIP_SEG = 16;
-
-__host__ __device__ inline int64_t strip_segments(int N) {
-    return (int64_t)((N + STRIP_W - 1) / STRIP_W) * ((N + STRIP_SEG - 1) / STRIP_SEG);
+// Work split: the strips of an event are cut into segments of `seg` rows (the
+// last one shorter when seg does not divide N); segment j of the event is
+// strip j / nblk, rows from (j % nblk) seg, nblk = the segments per strip.  A
+// block of W warps takes W consecutive segments of the flat list and runs
+// them in step, a barrier per row; warps beyond the list repeat its last
+// segment without storing.  The segment length is chosen per launch (below)
+// so that the segments fill the resident warps evenly.
+__host__ __device__ inline int64_t strip_segments(int N, int seg) {
+    return (int64_t)((N + STRIP_W - 1) / STRIP_W) * ((N + seg - 1) / seg);
 }
 
 struct StripSeg {
     int x0, y0, len;
 };
 
-__device__ __forceinline__ StripSeg strip_seg_of(int N, int64_t j) {
-    const int nblk = (N + STRIP_SEG - 1) / STRIP_SEG;
+__device__ __forceinline__ StripSeg strip_seg_of(int N, int64_t j, int seg) {
+    const int nblk = (N + seg - 1) / seg;
     const int strip = (int)(j / nblk), blk = (int)(j - (int64_t)strip * nblk);
     StripSeg g;
     g.x0 = strip * STRIP_W;
-    g.y0 = blk * STRIP_SEG;
-    g.len = N - g.y0 < STRIP_SEG ? N - g.y0 : STRIP_SEG;
+    g.y0 = blk * seg;
+    g.len = N - g.y0 < seg ? N - g.y0 : seg;
     return g;
 }
 
 // one segment of an event in step with the block (real: store its rows)
 __device__ __forceinline__ void strip_run_segment(StripWarpSmem& S, const Fields<float>& in, const Fields<float>& out,
-                                                  float4* site, int N, int64_t j, bool real, const StripStep& a) {
-    const StripSeg g = strip_seg_of(N, j);
-    strip_segment(S, in, out, site, N, g.x0, g.y0, g.y0 + STRIP_SEG, real ? g.y0 + g.len : g.y0, a, true);
+                                                  float4* site, int N, int64_t j, bool real, const StripStep& a,
+                                                  int seg) {
+    const StripSeg g = strip_seg_of(N, j, seg);
+    strip_segment(S, in, out, site, N, g.x0, g.y0, g.y0 + seg, real ? g.y0 + g.len : g.y0, a, true);
+}
+
+// Segment length for lattices Ns[0..n) on `blocks` resident blocks of `wpb`
+// warps: the length S >= 4 that minimises the modelled time, rounds x (S rows
+// + the dry row + the halo passes), where rounds = the items of wpb segments
+// per resident block, rounded up.  The dry row costs about 0.6 of a row and a
+// halo pass (up to HALO_B rows of the left column) about 0.45.  Long segments
+// cost fewer dry rows and halo passes; short ones fill the last round.
+inline int strip_seg_rows(const int* Ns, int n, int wpb, int blocks) {
+    int nmax = 1;
+    for (int e = 0; e < n; e++) nmax = Ns[e] > nmax ? Ns[e] : nmax;
+    int best = nmax < 4 ? nmax : 4;
+    double best_cost = 1e300;
+    for (int S = 4; S <= (nmax > 4 ? nmax : 4); S++) {
+        int64_t nseg = 0;
+        for (int e = 0; e < n; e++) nseg += strip_segments(Ns[e], S);
+        const int64_t items = (nseg + wpb - 1) / wpb;
+        const int64_t rounds = (items + blocks - 1) / (blocks > 0 ? blocks : 1);
+        const double cost = (double)rounds * (S + 0.6 + 0.45 * ((S + 1 + HALO_B - 1) / HALO_B));
+        if (cost < best_cost - 1e-9) { best_cost = cost; best = S; }
+    }
+    return best;
 }
 
 }  // namespace gl

@@ -35,6 +35,8 @@ def parse(argv=None):
     ap.add_argument("--field-checks", action="store_true", help="FP64 Gauss/unitarity checks at every report")
     ap.add_argument("--gauss-tol", type=float, default=1e-3)
     ap.add_argument("--unitarity-tol", type=float, default=1e-4)
+    ap.add_argument("--summary", action="store_true",
+                    help="end with one JSON line: wall time of the run (steps and reports) and its rates")
     return ap.parse_args(argv)
 
 
@@ -113,10 +115,13 @@ def main(argv=None):
         stream = batch.stream
     else:
         batch, stream = None, torch.cuda.current_stream()
+    import time
     with torch.cuda.stream(stream):
         if batch:
             batch.init()
             batch.autotune()
+        torch.cuda.synchronize()
+        t_start = time.perf_counter()
         done = 0
         while done < n_total:
             k = min(every, n_total - done)
@@ -136,6 +141,8 @@ def main(argv=None):
                 row["unitarity_max"] = max(o.unitarity_max for o in obs)
                 row["energy_density_lattice"] = sum(A.mean_energy_lattice(o) for o in obs) / len(obs)
             rows.append(row)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_start
     # instantaneous transport coefficients over the report series
     if len(rows) >= 2:
         tau = [r["tau_fm"] for r in rows]
@@ -148,6 +155,14 @@ def main(argv=None):
     if rank == 0:
         for r in rows:
             sys.stdout.write(json.dumps(r) + "\n")
+        if args.summary:
+            sites = sum(w.N * w.N for w in ws) * world
+            parts = sum(w.n_particles for w in ws) * world
+            sys.stdout.write(json.dumps({"summary": {
+                "workload": args.workload, "events": args.events, "steps": n_total, "reports": len(rows),
+                "tau_max_fm": n_total * dtau, "wall_s": wall, "field_checks": bool(args.field_checks),
+                "site_updates_per_s": sites * n_total / wall, "particle_steps_per_s": parts * n_total / wall,
+                "health": "ok", "launch": batch.launch() if batch else None}}) + "\n")
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
