@@ -78,41 +78,40 @@ __host__ __device__ inline StripStep strip_step(int64_t n, double dt, int every)
     return s;
 }
 
-// FP64 Gram-Schmidt of rows 0 and 1 of a two-row link, with the reciprocal
-// square roots from the double-precision rsqrt
+// Gram-Schmidt of rows 0 and 1 of a two-row link with the sums in FP64: the
+// squared norms and the inner product are accumulated in FP64 from the FP32
+// entries (each product exact) and the reciprocal square roots taken by the
+// FP64 rsqrt; the rows are scaled and corrected in FP32, the precision they
+// are stored in.  Right after it a link is unitary to FP32 rounding.
 __device__ __forceinline__ void reunit_rows(M3<float>& u) {
-    double r0r[3], r0i[3], r1r[3], r1i[3];
-#pragma unroll
-    for (int j = 0; j < 3; j++) {
-        r0r[j] = u.re[0][j]; r0i[j] = u.im[0][j];
-        r1r[j] = u.re[1][j]; r1i[j] = u.im[1][j];
-    }
     double n0 = 0;
 #pragma unroll
-    for (int j = 0; j < 3; j++) n0 = fma(r0r[j], r0r[j], fma(r0i[j], r0i[j], n0));
-    n0 = rsqrt(n0);
+    for (int j = 0; j < 3; j++)
+        n0 = fma((double)u.re[0][j], (double)u.re[0][j], fma((double)u.im[0][j], (double)u.im[0][j], n0));
+    const float s0 = (float)rsqrt(n0);
 #pragma unroll
-    for (int j = 0; j < 3; j++) { r0r[j] *= n0; r0i[j] *= n0; }
+    for (int j = 0; j < 3; j++) { u.re[0][j] *= s0; u.im[0][j] *= s0; }
     double cr = 0, ci = 0;  // <r0, r1>
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-        cr = fma(r0r[j], r1r[j], fma(r0i[j], r1i[j], cr));
-        ci = fma(r0r[j], r1i[j], fma(-r0i[j], r1r[j], ci));
+        const double ar = u.re[0][j], ai = u.im[0][j], br = u.re[1][j], bi = u.im[1][j];
+        cr = fma(ar, br, fma(ai, bi, cr));
+        ci = fma(ar, bi, fma(-ai, br, ci));
     }
+    const float fr = (float)cr, fi = (float)ci;
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-        r1r[j] -= fma(cr, r0r[j], -ci * r0i[j]);
-        r1i[j] -= fma(cr, r0i[j], ci * r0r[j]);
+        const float ar = u.re[0][j], ai = u.im[0][j];
+        u.re[1][j] -= fr * ar - fi * ai;
+        u.im[1][j] -= fr * ai + fi * ar;
     }
     double n1 = 0;
 #pragma unroll
-    for (int j = 0; j < 3; j++) n1 = fma(r1r[j], r1r[j], fma(r1i[j], r1i[j], n1));
-    n1 = rsqrt(n1);
+    for (int j = 0; j < 3; j++)
+        n1 = fma((double)u.re[1][j], (double)u.re[1][j], fma((double)u.im[1][j], (double)u.im[1][j], n1));
+    const float s1 = (float)rsqrt(n1);
 #pragma unroll
-    for (int j = 0; j < 3; j++) {
-        u.re[0][j] = (float)r0r[j]; u.im[0][j] = (float)r0i[j];
-        u.re[1][j] = (float)(r1r[j] * n1); u.im[1][j] = (float)(r1i[j] * n1);
-    }
+    for (int j = 0; j < 3; j++) { u.re[1][j] *= s1; u.im[1][j] *= s1; }
 }
 
 __device__ __forceinline__ M3<float> link_of(const float4 a, const float4 c, const float4 e) {
@@ -262,9 +261,10 @@ struct StripCarry {
 // Rows y_begin .. y_end - 1 of the strip at x0 (y_end - y_begin <= N) for
 // the fields of step n in `in`: step n + 1 into `out`, the site fields of t_n
 // into `site`.  Rows at or beyond y_stop store nothing (dummy rows, which keep
-// the warps of a block in step; y_stop <= y_end).  With `sync`, every row
-// starts at a block barrier, so all warps of the block must call this with
-// the same y_end - y_begin.
+// the warps of a block in step; y_stop <= y_end).  With `sync`, every second
+// row starts at a block barrier (often enough to keep the warps on the same
+// instructions), so all warps of the block must call this with the same
+// y_end - y_begin.
 __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<float>& in, const Fields<float>& out,
                                               float4* site, int N, int x0, int y_begin, int y_end, int y_stop,
                                               const StripStep& a, bool sync) {
@@ -284,7 +284,7 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
     int halo_base = r_first;
 #pragma unroll 1
     for (int r = r_first; r < y_end; r++) {
-        if (sync) __syncthreads();
+        if (sync && ((r - r_first) & 1) == 0) __syncthreads();
         if (r == halo_end) {
             const int nb = y_end - r < HALO_B ? y_end - r : HALO_B;
             strip_halo(S, in, Vn, N, x0, L, r, nb, a);
