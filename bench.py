@@ -52,8 +52,8 @@ def parse():
     ap.add_argument("--reunit-every", type=int, default=None)
     ap.add_argument("--events", type=int, default=0, help="events per GPU (default 30; 1 for n1024_mixed)")
     ap.add_argument("--launch", default=None, help="fixed launch shapes and schedule "
-                                                   "TILE:PUSH_BLOCK:PUSH_CHUNK:fused|streams[:PUSH_GRID] "
-                                                   "(e.g. strip16:128:1024:streams:1) "
+                                                   "TILE:PUSH_BLOCK:PUSH_CHUNK:fused|streams[:PUSH_GRID[:SEGMENT_ROWS]] "
+                                                   "(e.g. strip12:128:256:streams:0:16) "
                                                    "instead of the autotuner")
     return ap.parse_args()
 
@@ -61,9 +61,13 @@ def parse():
 BATCHED = "batched64"
 
 # DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum
-# of one single-kernel capture), keyed by (workload, events per GPU, kernel,
-# precision).  Absent: not captured for the current kernels.
-TRAFFIC = {}
+# of one single-kernel capture of a full launch at the autotuner's launch
+# shapes), keyed by (workload, events per GPU, kernel, precision).  Absent:
+# not captured for the current kernels.
+TRAFFIC = {
+    ("batched64", 64, "field_step", 1): 523057408 + 694286080,
+    ("batched64", 64, "wong_push", 1): 482682368 + 32894976,
+}
 
 
 # FP64 path: bound by the FP64 pipe (ncu: 90 % of its cycles active), so its
@@ -433,6 +437,8 @@ def run_ours(args):
             parts = args.launch.split(":")
             tile, pb, pc, mode = parts[:4]
             batch.set_launch(tile, int(pb), int(pc), mode == "fused", int(parts[4]) if len(parts) > 4 else 0)
+            if len(parts) > 5:
+                batch.set_segment_rows(int(parts[5]))
             tune = dict(batch.launch(), fixed=True)
         else:
             tune = batch.autotune()

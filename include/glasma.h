@@ -369,6 +369,12 @@ gl_status gl_batch_get_launch(const gl_batch* batch, int32_t* tile_shape, int32_
  * launches).  Results do not depend on it.  0 for FP64 batches or NULL. */
 int32_t gl_batch_segment_rows(const gl_batch* batch);
 
+/* FP32 batches: fix the rows per strip segment for the current field launch
+ * shape (set the shape first, with gl_batch_set_launch); 0 returns to the cost
+ * model's choice.  Results do not depend on it.  GL_ERR_ARG for rows < 0 or
+ * > 65536, or a non-zero value in an FP64 batch. */
+gl_status gl_batch_set_segment_rows(gl_batch* batch, int32_t rows);
+
 /* Trial timings of the last autotune, ms (0 where not tried): field_ms[3] by
  * field launch shape (the fastest of its segment lengths); push_ms[3] by push
  * block size; step_ms[8] for a whole step: [0] two streams (the fastest field

@@ -99,6 +99,7 @@ SIGNATURES = {
     "gl_batch_get_launch": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "gl_batch_observables_ex": (ctypes.c_int, [_P, ctypes.c_uint32, _P]),
     "gl_batch_segment_rows": (ctypes.c_int32, [_P]),
+    "gl_batch_set_segment_rows": (ctypes.c_int, [_P, ctypes.c_int32]),
 }
 
 GL_NOALLOC_MAX_PARTICLES = 2097152
@@ -376,6 +377,11 @@ class Batch:
             raise GlasmaError(GL_ERR_ARG, "set_launch", "field shape %r is not one of %s" % (tile, names))
         self._chk(lib().gl_batch_set_launch(self.b, names.index(tile), push_block, push_chunk, int(fused),
                                             push_grid), "gl_batch_set_launch")
+
+    def set_segment_rows(self, rows):
+        """FP32: rows per strip segment of the field kernel for the current
+        launch shape (0: the cost model's choice)."""
+        self._chk(lib().gl_batch_set_segment_rows(self.b, rows), "gl_batch_set_segment_rows")
 
     def step(self, n=1):
         self._chk(lib().gl_batch_step(self.b, n), "gl_batch_step")

@@ -1308,6 +1308,14 @@ gl_status gl_batch_set_launch(gl_batch* b, int32_t tile, int32_t push_block, int
 
 int32_t gl_batch_segment_rows(const gl_batch* b) { return b && b->prec != GL_FP64 ? b->seg_rows : 0; }
 
+gl_status gl_batch_set_segment_rows(gl_batch* b, int32_t rows) {
+    if (!b || rows < 0 || rows > 65536) return GL_ERR_ARG;
+    if (b->prec == GL_FP64) return rows == 0 ? GL_OK : GL_ERR_ARG;
+    b->seg_tuned[b->tile] = rows;  // applied by the next descriptor sync
+    b->desc_valid = 0;
+    return GL_OK;
+}
+
 gl_status gl_batch_get_launch(const gl_batch* b, int32_t* tile, int32_t* push_block, int32_t* push_chunk,
                               int32_t* fused, int32_t* push_grid) {
     if (!b) return GL_ERR_ARG;

@@ -361,3 +361,36 @@ def test_set_launch_rejects_bad_shapes():
     with pytest.raises(B.GlasmaError):
         batch.set_launch("32x4", push_chunk=1000)
     batch.close()
+
+
+def test_segment_length_changes_nothing():
+    """The FP32 field kernel cuts the strips of all events into segments of a
+    per-launch length (the unit of work of one warp; a segment's first row gets
+    its carries from a dry row, the column left of a strip from the halo
+    pass): any length, shorter or longer than a lattice, evolves the batch
+    bitwise alike, re-unitarisations and sorts included."""
+    ws = events(W.FP32_2ROW, sort_every=5)
+    for w in ws:
+        w.reunit_every = 4
+    results = []
+    for rows in (0, 5, 23, 64):
+        batch = B.Batch(ws)
+        with torch.cuda.stream(batch.stream):
+            batch.init()
+            batch.set_launch("strip12", 128, 256, False, 0)
+            batch.set_segment_rows(rows)
+            batch.step(13)
+            torch.cuda.synchronize()
+            assert rows == 0 or batch.launch()["segment_rows"] == rows
+            results.append([[ev.download(buf) for buf in (B.GL_BUF_LINKS, B.GL_BUF_E, B.GL_BUF_PI, B.GL_BUF_PHI,
+                                                          B.GL_BUF_PARTICLES, B.GL_BUF_SITE)]
+                            for ev in batch.events])
+        batch.close()
+    for r in results[1:]:
+        for e in range(len(ws)):
+            for a, b in zip(results[0][e], r[e]):
+                assert np.array_equal(a, b)
+    fp64 = B.Batch(events(W.FP64)[:1])
+    with pytest.raises(B.GlasmaError):
+        fp64.set_segment_rows(16)
+    fp64.close()
