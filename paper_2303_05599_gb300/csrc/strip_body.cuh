@@ -24,11 +24,12 @@
 //
 // Inputs of a row (the two links as two float4 rows each, phi) are copied by
 // each lane into its own slots of a two-row ring in shared memory with
-// cp.async one row ahead; e and pi go to a one-row slot that is refilled for
-// the next row as soon as this row has read them.  Each lane copies and reads
-// only its own slots, so nothing in a warp waits for another warp: there are
-// no block barriers, only per-thread cp.async waits and one __syncwarp per
-// halo block.
+// cp.async: row r + 2 goes into the slot of row r as soon as row r has read
+// it into registers, near the start of row r, so each copy has about a row to
+// land.  e and pi go to a one-row slot that is refilled for the next row as
+// soon as this row has read them.  Each lane copies and reads only its own
+// slots, so the only waits are per-thread cp.async waits, one __syncwarp per
+// halo block and the block barriers that keep the warps in step.
 //
 // Results do not depend on how rows are split among warps: the carries of a
 // segment's first row come from the same loop body (dry), and the values of
@@ -46,8 +47,12 @@ constexpr int HALO_B = 23;   // rows per halo block (at most 31: one lane comput
 constexpr int RING_V = 8;    // float4 per lane per row: Ux (3), Uy (3), phi (2)
 constexpr int RING_X = 5;    // the last lane's right neighbour: Uy (3), phi (2)
 constexpr int MOM_V = 6;     // float4 per lane per row: e_x (2), e_y (2), pi (2)
+constexpr int STRIP_SYNC = 2;  // rows between the block barriers that keep a block's warps in step
 
-// 13,600 bytes per warp: 16 warps fit an SM
+// One warp's staging area, 13,632 bytes: 16 warps fit an SM.  (A second
+// momentum slot, so that the next row's momenta could be issued a whole row
+// ahead, takes the shared memory of 12 warps to 200 KB; the L1 left beside it
+// is too small and both the field step and the push beside it run slower.)
 struct StripWarpSmem {
     float4 ring[2][RING_V][STRIP_W];
     float4 mom[MOM_V][STRIP_W];
@@ -127,6 +132,32 @@ __device__ __forceinline__ A8<float> alg_of(const float4 a, const float4 b) {
     x.v[0] = a.x; x.v[1] = a.y; x.v[2] = a.z; x.v[3] = a.w;
     x.v[4] = b.x; x.v[5] = b.y; x.v[6] = b.z; x.v[7] = b.w;
     return x;
+}
+
+// Component-wise updates of algebra elements on packed pairs of FP32
+// components (2i, 2i + 1), one f32x2 instruction per pair.
+__device__ __forceinline__ float2 pr(const A8<float>& x, int i) { return make_float2(x.v[2 * i], x.v[2 * i + 1]); }
+__device__ __forceinline__ void put(A8<float>& x, int i, float2 p) {
+    x.v[2 * i] = p.x;
+    x.v[2 * i + 1] = p.y;
+}
+__device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
+
+// The momentum update of one link direction, e(n+1/2) = e(n-1/2) + dt (t (P - Q)
+// + c / t), with P - Q the plaquette difference and c the scalar current; es
+// = e(n-1/2) + e(n+1/2), the sum the site field E averages.
+__device__ __forceinline__ void e_update(const A8<float>& e, const A8<float>& P, const A8<float>& Q,
+                                         const A8<float>& c, float t, float dt, float inv_t, A8<float>& en,
+                                         A8<float>& es) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        float2 u = __fmul2_rn(bc(-t), pr(Q, i));
+        u = __ffma2_rn(bc(t), pr(P, i), u);
+        u = __ffma2_rn(bc(inv_t), pr(c, i), u);
+        const float2 n = __ffma2_rn(bc(dt), u, pr(e, i));
+        put(en, i, n);
+        put(es, i, __fadd2_rn(pr(e, i), n));
+    }
 }
 
 __device__ __forceinline__ A8<float> shfl_up_a8(const A8<float>& x) {
@@ -228,13 +259,8 @@ __device__ __forceinline__ void strip_halo(StripWarpSmem& S, const Fields<float>
     const A8<float> Dn = shfl_up_a8(conj_dn_t(Uy, A));
     const A8<float> tx = conj_up_t(Ux, phR);
     const A8<float> cx = icomm(tx, ph);
-    const float t = a.t, dt = a.dt, inv_t = a.inv_t;
-    A8<float> es;
-#pragma unroll
-    for (int c = 0; c < 8; c++) {
-        const float en = ex.v[c] + dt * (t * (A.v[c] - Dn.v[c]) + inv_t * cx.v[c]);
-        es.v[c] = ex.v[c] + en;
-    }
+    A8<float> en, es;
+    e_update(ex, A, Dn, cx, a.t, a.dt, a.inv_t, en, es);
     const A8<float> lf = conj_dn_t(Ux, A);
     const A8<float> bx = conj_dn_t(Ux, ph);
     const A8<float> sx = conj_dn_t(Ux, es);
@@ -284,7 +310,7 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
     int halo_base = r_first;
 #pragma unroll 1
     for (int r = r_first; r < y_end; r++) {
-        if (sync && ((r - r_first) & 1) == 0) __syncthreads();
+        if (sync && (r - r_first) % STRIP_SYNC == 0) __syncthreads();
         if (r == halo_end) {
             const int nb = y_end - r < HALO_B ? y_end - r : HALO_B;
             strip_halo(S, in, Vn, N, x0, L, r, nb, a);
@@ -304,6 +330,8 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
         const A8<float> ph = alg_of(S.ring[k][6][L.lane], S.ring[k][7][L.lane]);
         M3<float> UyR = shfl_down_m3(Uy);
         if (L.last) UyR = link_of(S.extra[k][0], S.extra[k][1], S.extra[k][2]);
+        A8<float> phR = shfl_down_a8(ph);
+        if (L.last) phR = alg_of(S.extra[k][3], S.extra[k][4]);
         const M3<float> UxN = link_of(S.ring[k1][0][L.lane], S.ring[k1][1][L.lane], S.ring[k1][2][L.lane]);
         const A8<float> phN = alg_of(S.ring[k1][6][L.lane], S.ring[k1][7][L.lane]);
 
@@ -311,6 +339,9 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
         // they are formed, so that few values live at once.  The dry row forms
         // only what the carries need (A, Lf, the e_y update).
         const A8<float> A = iah_of_mul_nd(mul_nd(mul(Ux, UyR), UxN), Uy);   // plaquette at (x, y)
+        // ring slot k (Ux, Uy, phi and the right neighbour's Uy, phi of row r)
+        // has been read into registers above: row r + 2 goes there
+        if (r + 2 <= y_end) strip_issue_row(S, k, in, Vn, N, L, r + 2);
         const float4* h = S.halo[r - halo_base];
         // clover: A, its transports from x - 1 (Lf, by the left lane's Ux) and
         // from y - 1, and the fourth leaf carried from the row below
@@ -323,8 +354,6 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
             for (int c = 0; c < 8; c++) Be.v[c] = 0.25f * (((A.v[c] + Lf.v[c]) + C.dn.v[c]) + C.cr.v[c]);
             if (st) store_alg(site + (size_t)10 * Vn, g, Vn, Be);
             // x direction: D_x phi, the e_x update, E_x, the x link
-            A8<float> phR = shfl_down_a8(ph);
-            if (L.last) phR = alg_of(S.extra[k][3], S.extra[k][4]);
             A8<float> bx = shfl_up_a8(conj_dn_t(Ux, ph));
             if (L.lane == 0) bx = alg_of(h[2], h[3]);
             const A8<float> tx = conj_up_t(Ux, phR);
@@ -338,11 +367,7 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
             if (st) store_alg(site + (size_t)8 * Vn, g, Vn, By);
             const A8<float> ex = alg_of(S.mom[0][L.lane], S.mom[1][L.lane]);
             A8<float> exn, exs;
-#pragma unroll
-            for (int c = 0; c < 8; c++) {
-                exn.v[c] = ex.v[c] + dt * (t * (A.v[c] - C.dn.v[c]) + inv_t * cx.v[c]);
-                exs.v[c] = ex.v[c] + exn.v[c];
-            }
+            e_update(ex, A, C.dn, cx, t, dt, inv_t, exn, exs);
             A8<float> sx = shfl_up_a8(conj_dn_t(Ux, exs));
             if (L.lane == 0) sx = alg_of(h[4], h[5]);
             A8<float> Ex;
@@ -358,16 +383,10 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
         }
         const A8<float> ty = conj_up_t(Uy, phN);
         const A8<float> cy = icomm(ty, ph);
-        // every value read from ring slot k has been used by now: row r + 2 goes there
-        if (r + 2 <= y_end) strip_issue_row(S, k, in, Vn, N, L, r + 2);
         // y direction: D_y phi, the e_y update, E_y, the scalar and pi
         const A8<float> ey = alg_of(S.mom[2][L.lane], S.mom[3][L.lane]);
         A8<float> eyn, eys;
-#pragma unroll
-        for (int c = 0; c < 8; c++) {
-            eyn.v[c] = ey.v[c] + dt * (t * (Lf.v[c] - A.v[c]) + inv_t * cy.v[c]);
-            eys.v[c] = ey.v[c] + eyn.v[c];
-        }
+        e_update(ey, Lf, A, cy, t, dt, inv_t, eyn, eys);
         if (!dry) {
             const A8<float> po = alg_of(S.mom[4][L.lane], S.mom[5][L.lane]);
             A8<float> Ey, Ee, Bx, pn, phn;
@@ -388,7 +407,7 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
                 store_alg_cs(out.phi, g, Vn, phn);
             }
         }
-        // the momentum slot's values are all used: the next row's go there
+        // the momentum slot's values are all read now: the next row's go there
         if (r + 1 < y_end) strip_issue_mom(S, in, Vn, N, L, r + 1);
         if (st) {
             M3<float> ny = mul(exp_i_alg<float, ExpN<float>::n>(eyn, c_link), Uy);
