@@ -244,11 +244,8 @@ __device__ __forceinline__ M3<R> alg_to_mat2(const A8<R>& x) {
 // Hermitian result is formed).  The product is taken of 2 X, so that the
 // off-diagonal components need no factor 2 and the diagonal ones a factor
 // 1/2; scaling by powers of 2 is exact, so the result is bitwise that of X.
-// TRACELESS: the (2, 2) entry is not formed; V^+ X V is traceless like X, so
-// its eighth component follows from the first two diagonal entries (the same
-// value up to rounding, six fused multiply-adds fewer).
-template <typename R, bool TRACELESS>
-__device__ __forceinline__ A8<R> conj_dn_impl(const M3<R>& V, const A8<R>& x) {
+template <typename R>
+__device__ __forceinline__ A8<R> conj_dn(const M3<R>& V, const A8<R>& x) {
     const M3<R> X = alg_to_mat2(x);
     M3<R> Y;  // X V, with X's diagonal real
 #pragma unroll
@@ -267,9 +264,9 @@ __device__ __forceinline__ A8<R> conj_dn_impl(const M3<R>& V, const A8<R>& x) {
             Y.re[i][j] = sr;
             Y.im[i][j] = si;
         }
-    R zr[3][3], zi[3][3];  // V^+ Y, upper triangle (but (2, 2) when TRACELESS)
+    R zr[3][3], zi[3][3];  // V^+ Y, upper triangle
 #pragma unroll
-    for (int i = 0; i < (TRACELESS ? 2 : 3); i++)
+    for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = i; j < 3; j++) {
             R sr = R(0), si = R(0);
@@ -293,25 +290,67 @@ __device__ __forceinline__ A8<R> conj_dn_impl(const M3<R>& V, const A8<R>& x) {
     o.v[4] = -zi[0][2];
     o.v[5] = zr[1][2];
     o.v[6] = -zi[1][2];
-    if constexpr (TRACELESS) {
-        // (Z00 + Z11 - 2 Z22) / sqrt 3 with Z22 = -(Z00 + Z11), halved for 2X
-        o.v[7] = (zr[0][0] + zr[1][1]) * R(0.86602540378443864676);
-    } else {
-        o.v[7] = (zr[0][0] + zr[1][1] - R(2) * zr[2][2]) * (R(0.5) * inv_sqrt3<R>());
-    }
+    o.v[7] = (zr[0][0] + zr[1][1] - R(2) * zr[2][2]) * (R(0.5) * inv_sqrt3<R>());
     return o;
 }
 
-template <typename R>
-__device__ __forceinline__ A8<R> conj_dn(const M3<R>& V, const A8<R>& x) {
-    return conj_dn_impl<R, false>(V, x);
-}
-
 // conj_dn for the field step, where the transports are the bulk of the
-// arithmetic: the traceless form
+// arithmetic.  V^+ X V is traceless like X, so the (2, 2) entry is not formed:
+// the eighth component follows from the first two diagonal entries (the same
+// value up to rounding).  Rows 0 and 1 of the result, all that is left to
+// form, are rows 0 and 1 of W = V^+ (2X) times V, so the product is
+// associated that way and only two rows of W are formed: six entries instead
+// of the nine of (2X) V, about 108 multiply-adds instead of 138.
 template <typename R>
 __device__ __forceinline__ A8<R> conj_dn_t(const M3<R>& V, const A8<R>& x) {
-    return conj_dn_impl<R, true>(V, x);
+    const M3<R> X = alg_to_mat2(x);
+    R wr[2][3], wi[2][3];  // W = V^+ X, rows 0 and 1, with X's diagonal real
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            // conj(V_ji) X_jj, then conj(V_ki) X_kj for k != j
+            R sr = V.re[j][i] * X.re[j][j], si = -(V.im[j][i] * X.re[j][j]);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                if (k == j) continue;
+                sr = fma(V.re[k][i], X.re[k][j], sr);
+                sr = fma(V.im[k][i], X.im[k][j], sr);
+                si = fma(V.re[k][i], X.im[k][j], si);
+                si = fma(-V.im[k][i], X.re[k][j], si);
+            }
+            wr[i][j] = sr;
+            wi[i][j] = si;
+        }
+    R zr[2][3], zi[2][3];  // Z = W V, upper triangle of rows 0 and 1
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = i; j < 3; j++) {
+            R sr = R(0), si = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                sr = fma(wr[i][k], V.re[k][j], sr);
+                sr = fma(-wi[i][k], V.im[k][j], sr);
+                if (i != j) {
+                    si = fma(wr[i][k], V.im[k][j], si);
+                    si = fma(wi[i][k], V.re[k][j], si);
+                }
+            }
+            zr[i][j] = sr;
+            zi[i][j] = si;
+        }
+    A8<R> o;
+    o.v[0] = zr[0][1];
+    o.v[1] = -zi[0][1];
+    o.v[2] = R(0.5) * (zr[0][0] - zr[1][1]);
+    o.v[3] = zr[0][2];
+    o.v[4] = -zi[0][2];
+    o.v[5] = zr[1][2];
+    o.v[6] = -zi[1][2];
+    // (Z00 + Z11 - 2 Z22) / sqrt 3 with Z22 = -(Z00 + Z11), halved for 2X
+    o.v[7] = (zr[0][0] + zr[1][1]) * R(0.86602540378443864676);
+    return o;
 }
 
 // components of V X V^+ for Hermitian X
