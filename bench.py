@@ -73,12 +73,13 @@ TRAFFIC = {
 # FP64 path: bound by the FP64 pipe (ncu: 90 % of its cycles active), so its
 # roofline is arithmetic.  Peak: 152 SMs x 2 FP64 FMA per clock x 2 flops x
 # 2.07 GHz = 1.26 TFLOP/s (NVIDIA's nominal 1.25).  Flops counted with ncu
-# (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on; 2 per DFMA) on
-# 8 events of the default workload: per site of the field step, and per
-# active particle of its half Wong, half static mix.
+# (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on; 2 per DFMA):
+# per site of the field step (the 64 uneven events), and per active particle
+# of the push, which depends on the species mix (all Wong charm quarks in the
+# 64-event batch; half Wong, half static in 30 x 256^2).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-FP64_FLOP_PER_SITE = 5332
-FP64_FLOP_PER_PARTICLE = 498
+FP64_FLOP_PER_SITE = 4815
+FP64_FLOP_PER_PARTICLE = {"batched64": 958, "n256_charm_static": 498}
 
 
 def sort_launches(ws):
@@ -532,8 +533,15 @@ def run_ours(args):
             "frac_leapfrog_bytes_only": lf / t_f / 1e9 / hbm,
             "achieved_leapfrog_bytes_only": lf / t_f / 1e9})
         if prec == 0:
-            flops = {"field_step": FP64_FLOP_PER_SITE * sites, "wong_push": FP64_FLOP_PER_PARTICLE * n_active}
+            flops = {"field_step": FP64_FLOP_PER_SITE * sites}
+            if args.workload in FP64_FLOP_PER_PARTICLE:
+                flops["wong_push"] = FP64_FLOP_PER_PARTICLE[args.workload] * n_active
             for name, (b, t) in kern.items():
+                if name not in flops:
+                    roof[name] = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                  "frac": None, "traffic": None, "us_per_launch": t * 1e6,
+                                  "note": "FP64 flops per particle not counted for this species mix"}
+                    continue
                 roof[name] = {"bound": "alu", "achieved": flops[name] / t / 1e12, "peak": FP64_PEAK_TFLOPS,
                               "unit": "TFLOP/s", "frac": flops[name] / t / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
                               "flops_per_launch": flops[name], "us_per_launch": t * 1e6,

@@ -134,6 +134,50 @@ __device__ __forceinline__ A8<float> alg_of(const float4 a, const float4 b) {
     return x;
 }
 
+// Products of SU(3) matrices with rows 0 and 1 multiplied out and row 2 the
+// conjugate cross product of the two, as for a stored link: c = a b and
+// c = a b^+.
+__device__ __forceinline__ M3<float> mul_su3(const M3<float>& a, const M3<float>& b) {
+    M3<float> c;
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                sr = fmaf(a.re[i][k], b.re[k][j], sr);
+                sr = fmaf(-a.im[i][k], b.im[k][j], sr);
+                si = fmaf(a.re[i][k], b.im[k][j], si);
+                si = fmaf(a.im[i][k], b.re[k][j], si);
+            }
+            c.re[i][j] = sr;
+            c.im[i][j] = si;
+        }
+    rebuild_row2(c);
+    return c;
+}
+__device__ __forceinline__ M3<float> mul_nd_su3(const M3<float>& a, const M3<float>& b) {
+    M3<float> c;
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                sr = fmaf(a.re[i][k], b.re[j][k], sr);
+                sr = fmaf(a.im[i][k], b.im[j][k], sr);
+                si = fmaf(a.im[i][k], b.re[j][k], si);
+                si = fmaf(-a.re[i][k], b.im[j][k], si);
+            }
+            c.re[i][j] = sr;
+            c.im[i][j] = si;
+        }
+    rebuild_row2(c);
+    return c;
+}
+
 // Component-wise updates of algebra elements on packed pairs of FP32
 // components (2i, 2i + 1), one f32x2 instruction per pair.
 __device__ __forceinline__ float2 pr(const A8<float>& x, int i) { return make_float2(x.v[2 * i], x.v[2 * i + 1]); }
@@ -255,7 +299,7 @@ __device__ __forceinline__ void strip_halo(StripWarpSmem& S, const Fields<float>
     const A8<float> ph = load_alg(in.phi, gl, Vn);
     const A8<float> phR = load_alg(in.phi, g0, Vn);
     const A8<float> ex = load_alg(in.e, gl, Vn);
-    const A8<float> A = iah_of_mul_nd(mul_nd(mul(Ux, UyR), UxU), Uy);
+    const A8<float> A = iah_of_mul_nd(mul_nd_su3(mul_su3(Ux, UyR), UxU), Uy);
     const A8<float> Dn = shfl_up_a8(conj_dn_t(Uy, A));
     const A8<float> tx = conj_up_t(Ux, phR);
     const A8<float> cx = icomm(tx, ph);
@@ -308,6 +352,10 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
     strip_issue_mom(S, in, Vn, N, L, r_first);
     int halo_end = r_first;  // rows below halo_end have halo values in S.halo
     int halo_base = r_first;
+    // (n + 1 + r) mod every, the re-unitarisation phase of row r (the rows
+    // that store have y = r): one 64-bit remainder per segment, then a step
+    // of one per row
+    int ru = a.every > 0 ? (int)((a.n + 1 + r_first) % a.every) : 1;
 #pragma unroll 1
     for (int r = r_first; r < y_end; r++) {
         if (sync && (r - r_first) % STRIP_SYNC == 0) __syncthreads();
@@ -338,7 +386,7 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
         // Each value is used as soon as it is known and the outputs stored as
         // they are formed, so that few values live at once.  The dry row forms
         // only what the carries need (A, Lf, the e_y update).
-        const A8<float> A = iah_of_mul_nd(mul_nd(mul(Ux, UyR), UxN), Uy);   // plaquette at (x, y)
+        const A8<float> A = iah_of_mul_nd(mul_nd_su3(mul_su3(Ux, UyR), UxN), Uy);   // plaquette at (x, y)
         // ring slot k (Ux, Uy, phi and the right neighbour's Uy, phi of row r)
         // has been read into registers above: row r + 2 goes there
         if (r + 2 <= y_end) strip_issue_row(S, k, in, Vn, N, L, r + 2);
@@ -377,7 +425,7 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
                 store_alg(site, g, Vn, Ex);
                 store_alg_cs(out.e, g, Vn, exn);
                 M3<float> nx = mul(exp_i_alg<float, ExpN<float>::n>(exn, c_link), Ux);
-                if (a.every > 0 && (a.n + 1 + y) % a.every == 0) reunit_rows(nx);
+                if (ru == 0) reunit_rows(nx);
                 store_link_cs(out.U, 0, g, Vn, nx);
             }
         }
@@ -411,9 +459,10 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
         if (r + 1 < y_end) strip_issue_mom(S, in, Vn, N, L, r + 1);
         if (st) {
             M3<float> ny = mul(exp_i_alg<float, ExpN<float>::n>(eyn, c_link), Uy);
-            if (a.every > 0 && (a.n + 1 + y) % a.every == 0) reunit_rows(ny);
+            if (ru == 0) reunit_rows(ny);
             store_link_cs(out.U, 1, g, Vn, ny);
         }
+        if (a.every > 0 && ++ru == a.every) ru = 0;
         // the carries for row r + 1, by this row's Uy
         C.dn = conj_dn_t(Uy, A);
         C.by = conj_dn_t(Uy, ph);
