@@ -65,8 +65,8 @@ BATCHED = "batched64"
 # shapes), keyed by (workload, events per GPU, kernel, precision).  Absent:
 # not captured for the current kernels.
 TRAFFIC = {
-    ("batched64", 64, "field_step", 1): 521496832 + 693666560,
-    ("batched64", 64, "wong_push", 1): 482682368 + 32894976,
+    ("batched64", 64, "field_step", 1): 521397248 + 694363648,
+    ("batched64", 64, "wong_push", 1): 484288256 + 32479232,
 }
 
 
