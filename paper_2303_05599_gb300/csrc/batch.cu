@@ -278,6 +278,7 @@ struct BObs {
     double* partials;
     double* out;
     ObsArgs oa;
+    FieldObsEv fo;  // the field checks: the event's blocks of the one launch over all events
 };
 
 __device__ __forceinline__ int find_obs_event(const BObs* ev, int ne, int block) {
@@ -1225,11 +1226,14 @@ gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
     if (!b || !out || (what & ~GL_OBS_ALL)) return GL_ERR_ARG;
     // obs rows of all events: out pointers (also for the gather when only the
     // field checks are asked for)
-    int blocks = 0;
+    int blocks = 0, fblocks = 0;
     for (int e = 0; e < b->ne; e++) {
         ObsEvent o;
         ctx_obs_event(b->ev[e], &o);
         b->h_obs[e].out = o.out;
+        b->h_obs[e].fo = o.fo;
+        b->h_obs[e].fo.block_begin = fblocks;
+        fblocks += o.fo.nblocks;
     }
     if (what & GL_OBS_PARTICLES) {
         for (int e = 0; e < b->ne; e++) {
@@ -1277,9 +1281,10 @@ gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
         }
         batch_obs_finalize<<<b->ne * GL_MAX_SPECIES * PO_N, 256, 0, b->stream>>>(b->d_obs);
     }
-    // the field checks per event (the contexts share the batch stream)
+    // the field checks of all events, one launch
     if (what & GL_OBS_FIELDS)
-        for (int e = 0; e < b->ne; e++) ctx_obs_launch(b->ev[e], GL_OBS_FIELDS);
+        launch_field_obs_events(b->prec, b->h_obs[0].fo, (const char*)b->d_obs + offsetof(BObs, fo), sizeof(BObs),
+                                b->ne, fblocks, b->stream);
     gather_obs_kernel<<<b->ne, 64, 0, b->stream>>>(b->d_obs, b->d_obs_all);
     cudaMemcpyAsync(b->p_rows, b->d_obs_all, sizeof(double) * OBS_W * b->ne, cudaMemcpyDeviceToHost, b->stream);
     const bool ok = cudaStreamSynchronize(b->stream) == cudaSuccess && cudaGetLastError() == cudaSuccess;

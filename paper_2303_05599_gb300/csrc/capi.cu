@@ -18,7 +18,7 @@ void launch_parts_convert(int prec, void* parts, int64_t np, double* stg, int to
 using namespace gl;
 
 static const double HBARC = 0.1973269804;  // GeV fm
-static const int MAX_BLOCKS = 1024;
+static const int MAX_BLOCKS = FIELD_OBS_MAX_BLOCKS;  // rows of per-block partial results
 
 struct gl_ctx {
     gl_config cfg;
@@ -218,8 +218,14 @@ void ctx_obs_event(const gl_ctx* c, ObsEvent* o) {
     for (int k = 0; k < GL_MAX_SPECIES; k++) { o->q2ref[k] = c->q2ref[k]; o->q3ref[k] = c->q3ref[k]; }
     o->partials = c->partials;
     o->out = c->obs_dev;
+    o->fo.fields = c->field[c->cur];
+    o->fo.site = site_at(c, c->pstep - 1);
+    o->fo.N = c->N;
+    o->fo.block_begin = 0;
+    o->fo.nblocks = field_obs_blocks(c->N);
+    o->fo.partials = c->partials + (size_t)MAX_BLOCKS * GL_MAX_SPECIES * PO_N;
+    o->fo.out = c->obs_dev + GL_MAX_SPECIES * PO_N;
 }
-void ctx_obs_launch(gl_ctx* c, uint32_t what) { ::observables_launch(c, what); }
 gl_status ctx_upload_enqueue(gl_ctx* c, gl_buffer which, const double* host, size_t count, cudaStream_t st) {
     const cudaStream_t own = c->stream;
     c->stream = st;  // the copy, the conversion and a particle sort go to st
@@ -721,10 +727,11 @@ static void observables_launch(gl_ctx* c, uint32_t what) {
         ctx_obs_event(c, &o);
         launch_particle_obs(c->prec, o.parts, o.np, o.t, o.mask, o.sp, o.q2ref, o.q3ref, o.partials, o.out, c->stream);
     }
-    if (what & GL_OBS_FIELDS)
-        launch_field_obs(c->prec, c->field[c->cur], site_at(c, c->pstep - 1), c->N,
-                         c->partials + (size_t)MAX_BLOCKS * GL_MAX_SPECIES * PO_N, MAX_BLOCKS,
-                         c->obs_dev + GL_MAX_SPECIES * PO_N, c->stream);
+    if (what & GL_OBS_FIELDS) {
+        ObsEvent o;
+        ctx_obs_event(c, &o);
+        launch_field_obs_events(c->prec, o.fo, nullptr, 0, 0, o.fo.nblocks, c->stream);
+    }
 }
 
 // read back the reductions enqueued by observables_launch (waits); the values

@@ -67,6 +67,33 @@ void launch_convert(int prec, int which, int to_device, void* dev, double* stagi
 void launch_particle_obs(int prec, const void* parts, int64_t np, double t, uint32_t active_mask,
                          const SpeciesParams& sp, const double q2ref[GL_MAX_SPECIES],
                          const double q3ref[GL_MAX_SPECIES], double* partials, double* out, cudaStream_t st);
+// The FP64 field checks of one event: the fields of the current time, the
+// site fields of the last step, N, the event's first block in a launch over
+// several events and its number of blocks, the per-block rows
+// [blocks][FO_N] and the FO_N results.
+struct FieldObsEv {
+    const void* fields;
+    const void* site;
+    int N;
+    int block_begin;
+    int nblocks;
+    double* partials;
+    double* out;
+};
+static constexpr int FIELD_OBS_MAX_BLOCKS = 1024;
+// blocks of an N x N event's field checks: one site a thread in blocks of
+// 256, at most FIELD_OBS_MAX_BLOCKS (then grid-strided)
+inline int field_obs_blocks(int N) {
+    const int64_t b = ((int64_t)N * N + 255) / 256;
+    return (int)(b < FIELD_OBS_MAX_BLOCKS ? b : FIELD_OBS_MAX_BLOCKS);
+}
+// The field checks of ne events in one launch of `blocks` blocks (the sum of
+// their nblocks), their descriptors `stride` bytes apart from the device
+// address evs; or, with ne == 0, of the one event `one` (block_begin 0).  One
+// kernel serves both, so an event's results are bitwise the same whether it
+// is checked alone or with others.
+void launch_field_obs_events(int prec, const FieldObsEv& one, const void* evs, size_t stride, int ne, int blocks,
+                             cudaStream_t st);
 // one context's particle-observables launch, for the batched reduction
 struct ObsEvent {
     void* parts;
@@ -77,9 +104,8 @@ struct ObsEvent {
     double q2ref[GL_MAX_SPECIES], q3ref[GL_MAX_SPECIES];
     double* partials;
     double* out;
+    FieldObsEv fo;  // its field checks
 };
-void launch_field_obs(int prec, const void* b, const void* site, int N, double* partials, int max_blocks,
-                      double* out, cudaStream_t st);
 // energy density per site, tr of the squared site fields (FP64 out[N*N])
 void launch_energy(int prec, const void* site, int N, double* out, cudaStream_t st);
 
@@ -156,9 +182,6 @@ void ctx_sort(gl_ctx* c);
 void ctx_swap_parts(gl_ctx* c);
 void ctx_obs_event(const gl_ctx* c, ObsEvent* o);
 size_t ctx_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t ns);
-// enqueue a context's observable reductions into its obs row (ObsEvent::out,
-// GL_MAX_SPECIES * PO_N particle values then FO_N field values), no wait
-void ctx_obs_launch(gl_ctx* c, uint32_t what);
 // a gl_obs record from a host copy of that row
 void ctx_obs_fill(const gl_ctx* c, uint32_t what, const double* row, gl_obs* o);
 // gl_upload without its wait: copies, conversions and a particle sort enqueued on st
