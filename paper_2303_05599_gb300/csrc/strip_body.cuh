@@ -474,11 +474,13 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
 
 // Work split: the strips of an event are cut into segments of `seg` rows (the
 // last one shorter when seg does not divide N); segment j of the event is
-// strip j / nblk, rows from (j % nblk) seg, nblk = the segments per strip.  A
-// block of W warps takes W consecutive segments of the flat list and runs
-// them in step, a barrier per row; warps beyond the list repeat its last
-// segment without storing.  The segment length is chosen per launch (below)
-// so that the segments fill the resident warps evenly.
+// strip j % nstrips, rows from (j / nstrips) seg: neighbouring strips over the
+// same rows are consecutive, so the W warps of a block, which take W
+// consecutive segments of the flat list and run them in step (a barrier every
+// second row), read and write the same rows of each plane at the same time.
+// Warps beyond the list repeat its last segment without storing.  The segment
+// length is chosen per launch (below) so that the segments fill the resident
+// warps evenly.
 __host__ __device__ inline int64_t strip_segments(int N, int seg) {
     return (int64_t)((N + STRIP_W - 1) / STRIP_W) * ((N + seg - 1) / seg);
 }
@@ -488,8 +490,8 @@ struct StripSeg {
 };
 
 __device__ __forceinline__ StripSeg strip_seg_of(int N, int64_t j, int seg) {
-    const int nblk = (N + seg - 1) / seg;
-    const int strip = (int)(j / nblk), blk = (int)(j - (int64_t)strip * nblk);
+    const int nstrips = (N + STRIP_W - 1) / STRIP_W;
+    const int blk = (int)(j / nstrips), strip = (int)(j - (int64_t)blk * nstrips);
     StripSeg g;
     g.x0 = strip * STRIP_W;
     g.y0 = blk * seg;
