@@ -362,11 +362,12 @@ gl_status gl_batch_set_launch(gl_batch* batch, int32_t tile_shape, int32_t push_
 gl_status gl_batch_get_launch(const gl_batch* batch, int32_t* tile_shape, int32_t* push_block,
                               int32_t* push_chunk, int32_t* fused, int32_t* push_grid);
 
-/* FP32 batches: the rows per strip segment of the field kernel in use (the
- * unit of work of one warp: the strips of all events are cut into segments of
- * this length and spread over the resident warps; chosen by a cost model of
- * the launch shape's resident warps, or by gl_batch_autotune from trial
- * launches).  Results do not depend on it.  0 for FP64 batches or NULL. */
+/* FP32 batches: the rows per strip segment of the field kernel that the next
+ * step launches (the unit of work of one warp: the strips of all events are
+ * cut into segments of this length and spread over the resident warps; set by
+ * gl_batch_set_segment_rows, chosen by gl_batch_autotune from trial launches,
+ * or else by a cost model of the launch shape's resident warps).  Results do
+ * not depend on it.  0 for FP64 batches or NULL. */
 int32_t gl_batch_segment_rows(const gl_batch* batch);
 
 /* FP32 batches: fix the rows per strip segment for the current field launch

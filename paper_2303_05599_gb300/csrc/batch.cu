@@ -505,6 +505,9 @@ struct gl_batch {
     // resident push blocks per SM beside field shapes 0 and 1
     float tune_step_ms[1 + N_CHUNKS + 4];
     int* h_bad;  // pinned [ne]: the index-check flags of a native particle upload (allocated on first use)
+    PartsCheckEv* p_pchk;  // pinned [ne]: the index-check descriptors (allocated with h_bad)
+    PartsCheckEv* d_pchk;  // [ne] the same on the device, and
+    int* d_bad;            // [ne] the index-check flags
     BObs* p_obs;    // pinned copy of h_obs for its upload, and
     double* p_rows; // pinned [ne][OBS_W] for the gathered obs rows (both allocated on first use)
     char err[256];
@@ -521,6 +524,25 @@ static gl_status bfail(gl_batch* b, gl_status s, const char* m) {
 }
 
 extern "C" {
+// the strip segment length of the current launch shape: the one set or
+// tuned for it, else the one that spreads all events' strips evenly over its
+// resident warps (0: out of host memory)
+static int batch_seg_rows(const gl_batch* b) {
+    if (b->seg_tuned[b->tile] > 0) return b->seg_tuned[b->tile];
+    int wpb = 8, blocks = 1;
+    strip_shape_geometry(b->tile, &wpb, &blocks);
+    int* Ns = new (std::nothrow) int[b->ne];
+    if (!Ns) return 0;
+    for (int e = 0; e < b->ne; e++) {
+        CtxView v;
+        ctx_view(b->ev[e], &v);
+        Ns[e] = v.N;
+    }
+    const int rows = strip_seg_rows(Ns, b->ne, wpb, blocks);
+    delete[] Ns;
+    return rows;
+}
+
 static gl_status sync_desc(gl_batch* b);
 }
 
@@ -561,7 +583,8 @@ size_t gl_batch_workspace_bytes(const gl_config* cfgs, const gl_species* species
                                 int32_t n_events) {
     if (!cfgs || n_events < 1 || n_events > MAX_EVENTS) return 0;
     size_t o = a256b(sizeof(EvDesc) * n_events) + 256 + a256b(sizeof(BObs) * n_events) +
-               a256b(sizeof(double) * OBS_W * n_events) + a256b(sizeof(SortEv) * n_events);
+               a256b(sizeof(double) * OBS_W * n_events) + a256b(sizeof(SortEv) * n_events) +
+               a256b(sizeof(PartsCheckEv) * n_events) + a256b(sizeof(int) * n_events);
     for (int e = 0; e < n_events; e++) {
         const size_t w = ctx_workspace_bytes(&cfgs[e], species ? species + (size_t)e * n_species : nullptr, n_species);
         if (!w) return 0;
@@ -620,6 +643,10 @@ gl_status gl_batch_create(const gl_config* cfgs, const gl_species* species, int3
     o += a256b(sizeof(double) * OBS_W * n_events);
     b->d_sort = (SortEv*)(ws + o);
     o += a256b(sizeof(SortEv) * n_events);
+    b->d_pchk = (PartsCheckEv*)(ws + o);
+    o += a256b(sizeof(PartsCheckEv) * n_events);
+    b->d_bad = (int*)(ws + o);
+    o += a256b(sizeof(int) * n_events);
     for (int e = 0; e < n_events; e++) {
         const gl_species* sp = species ? species + (size_t)e * n_species : nullptr;
         const size_t w = ctx_workspace_bytes(&cfgs[e], sp, n_species);
@@ -659,6 +686,7 @@ gl_status gl_batch_destroy(gl_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->h_bad) cudaFreeHost(b->h_bad);
+    if (b->p_pchk) cudaFreeHost(b->p_pchk);
     if (b->p_obs) cudaFreeHost(b->p_obs);
     if (b->p_rows) cudaFreeHost(b->p_rows);
     for (int e = 0; e < b->ne; e++) gl_destroy(b->ev[e]);
@@ -700,19 +728,8 @@ static gl_status sync_desc(gl_batch* b) {
     const int TX = TILE_DIMS[b->tile][0], TY = TILE_DIMS[b->tile][1];
     int64_t step0 = -1;
     if (b->prec != GL_FP64) {
-        // the segment length that spreads all events' strips evenly over the
-        // resident warps of the current launch shape
-        int wpb = 8, blocks = 1;
-        strip_shape_geometry(b->tile, &wpb, &blocks);
-        int* Ns = new (std::nothrow) int[b->ne];
-        if (!Ns) return bfail(b, GL_ERR_ARG, "out of host memory");
-        for (int e = 0; e < b->ne; e++) {
-            CtxView v;
-            ctx_view(b->ev[e], &v);
-            Ns[e] = v.N;
-        }
-        b->seg_rows = b->seg_tuned[b->tile] > 0 ? b->seg_tuned[b->tile] : strip_seg_rows(Ns, b->ne, wpb, blocks);
-        delete[] Ns;
+        b->seg_rows = batch_seg_rows(b);
+        if (b->seg_rows < 1) return bfail(b, GL_ERR_ARG, "out of host memory");
     }
     for (int e = 0; e < b->ne; e++) {
         CtxView v;
@@ -1184,30 +1201,49 @@ gl_status gl_batch_upload_native(gl_batch* b, gl_native_part part, const void* c
     if (!b || !host || !bytes) return GL_ERR_ARG;
     if (gl_status s = ensure_aux(b)) return s;
     const bool parts = part == GL_NATIVE_PARTICLES;
-    if (parts && !b->h_bad && cudaHostAlloc((void**)&b->h_bad, sizeof(int) * b->ne, cudaHostAllocDefault) != cudaSuccess) {
-        b->h_bad = nullptr;
-        return bfail(b, GL_ERR_CUDA, "pinned host allocation failed");
+    if (parts && !b->h_bad) {
+        if (cudaHostAlloc((void**)&b->h_bad, sizeof(int) * b->ne, cudaHostAllocDefault) != cudaSuccess ||
+            cudaHostAlloc((void**)&b->p_pchk, sizeof(PartsCheckEv) * b->ne, cudaHostAllocDefault) != cudaSuccess) {
+            if (b->h_bad) cudaFreeHost(b->h_bad);
+            b->h_bad = nullptr;
+            b->p_pchk = nullptr;
+            return bfail(b, GL_ERR_CUDA, "pinned host allocation failed");
+        }
     }
-    if (parts) memset(b->h_bad, 0, sizeof(int) * b->ne);
+    // the copies, events alternating between the batch's two streams
     cudaEventRecord(b->ev_a, b->stream);
     cudaStreamWaitEvent(b->aux, b->ev_a, 0);
     gl_status st = GL_OK;
     int bad = -1;
     for (int e = 0; e < b->ne && st == GL_OK; e++) {
-        const cudaStream_t s = (e & 1) ? b->aux : b->stream;
-        st = ctx_upload_native_enqueue(b->ev[e], (int)part, host[e], bytes[e], s);
+        st = ctx_upload_native_copy(b->ev[e], (int)part, host[e], bytes[e], (e & 1) ? b->aux : b->stream);
         if (st != GL_OK) bad = e;
-        else if (parts && bytes[e] > 0)
-            cudaMemcpyAsync(b->h_bad + e, ctx_bad_flag(b->ev[e]), sizeof(int), cudaMemcpyDeviceToHost, s);
     }
     cudaEventRecord(b->ev_b, b->aux);
     cudaStreamWaitEvent(b->stream, b->ev_b, 0);
-    const bool ok = cudaStreamSynchronize(b->stream) == cudaSuccess && cudaGetLastError() == cudaSuccess;
     if (bad >= 0) {
+        cudaStreamSynchronize(b->stream);
         char m[300];
         snprintf(m, sizeof m, "event %d: %s", bad, gl_error_string(b->ev[bad]));
         return bfail(b, st, m);
     }
+    // particles: the index check of every event in one launch, its flags in
+    // one copy (events uploaded with no bytes are checked as well: their
+    // arrays are unchanged and valid)
+    if (parts) {
+        int blocks = 0;
+        for (int e = 0; e < b->ne; e++) {
+            PartsCheckEv d = ctx_parts_check_event(b->ev[e]);
+            d.block_begin = blocks;
+            blocks += d.nblocks;
+            b->p_pchk[e] = d;
+        }
+        cudaMemcpyAsync(b->d_pchk, b->p_pchk, sizeof(PartsCheckEv) * b->ne, cudaMemcpyHostToDevice, b->stream);
+        cudaMemsetAsync(b->d_bad, 0, sizeof(int) * b->ne, b->stream);
+        launch_parts_validate_events(b->prec, b->d_pchk, b->ne, blocks, b->d_bad, b->stream);
+        cudaMemcpyAsync(b->h_bad, b->d_bad, sizeof(int) * b->ne, cudaMemcpyDeviceToHost, b->stream);
+    }
+    const bool ok = cudaStreamSynchronize(b->stream) == cudaSuccess && cudaGetLastError() == cudaSuccess;
     if (!ok) return bfail(b, GL_ERR_CUDA, "batch native upload failed");
     if (parts)
         for (int e = 0; e < b->ne; e++)
@@ -1311,7 +1347,10 @@ gl_status gl_batch_set_launch(gl_batch* b, int32_t tile, int32_t push_block, int
     return GL_OK;
 }
 
-int32_t gl_batch_segment_rows(const gl_batch* b) { return b && b->prec != GL_FP64 ? b->seg_rows : 0; }
+int32_t gl_batch_segment_rows(const gl_batch* b) {
+    if (!b || b->prec == GL_FP64) return 0;
+    return b->desc_valid ? b->seg_rows : batch_seg_rows(b);  // the next launch's, also before it
+}
 
 gl_status gl_batch_set_segment_rows(gl_batch* b, int32_t rows) {
     if (!b || rows < 0 || rows > 65536) return GL_ERR_ARG;

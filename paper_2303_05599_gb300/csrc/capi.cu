@@ -80,6 +80,7 @@ static gl_status observables_read(gl_ctx* c, uint32_t what, gl_obs* o);
 static gl_status transfer_enqueue(gl_ctx* c, gl_buffer which, double* host, size_t count, int to_device);
 static void observables_fill(const gl_ctx* c, uint32_t what, const double* host, gl_obs* o);
 static gl_status native_upload_enqueue(gl_ctx* c, int part, const void* host, size_t bytes, cudaStream_t st);
+static gl_status native_check(gl_ctx* c, int part, const void* host, size_t bytes);
 }
 
 static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -233,10 +234,21 @@ gl_status ctx_upload_enqueue(gl_ctx* c, gl_buffer which, const double* host, siz
     c->stream = own;
     return s;
 }
-gl_status ctx_upload_native_enqueue(gl_ctx* c, int part, const void* host, size_t bytes, cudaStream_t st) {
-    return ::native_upload_enqueue(c, part, host, bytes, st);
+gl_status ctx_upload_native_copy(gl_ctx* c, int part, const void* host, size_t bytes, cudaStream_t st) {
+    if (gl_status s = ::native_check(c, part, host, bytes)) return s;
+    if (bytes == 0) return GL_OK;
+    cudaMemcpyAsync(part == GL_NATIVE_FIELDS ? c->field[c->cur] : c->parts, host, bytes, cudaMemcpyHostToDevice, st);
+    return check_cuda(c, "gl_batch_upload_native");
 }
-const int* ctx_bad_flag(const gl_ctx* c) { return c->d_bad; }
+PartsCheckEv ctx_parts_check_event(const gl_ctx* c) {
+    PartsCheckEv e;
+    e.parts = c->parts;
+    e.np = c->np;
+    e.ns = c->ns;
+    e.block_begin = 0;
+    e.nblocks = parts_check_blocks(c->np);
+    return e;
+}
 void ctx_obs_fill(const gl_ctx* c, uint32_t what, const double* host, gl_obs* o) {
     ::observables_fill(c, what, host, o);
 }

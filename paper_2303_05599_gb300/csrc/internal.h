@@ -186,10 +186,24 @@ size_t ctx_workspace_bytes(const gl_config* cfg, const gl_species* sp, int32_t n
 void ctx_obs_fill(const gl_ctx* c, uint32_t what, const double* row, gl_obs* o);
 // gl_upload without its wait: copies, conversions and a particle sort enqueued on st
 gl_status ctx_upload_enqueue(gl_ctx* c, gl_buffer which, const double* host, size_t count, cudaStream_t st);
-// gl_upload_native enqueued on st: the copy and, for particles, the index
-// check, which sets the context's device flag (read back by the caller)
-gl_status ctx_upload_native_enqueue(gl_ctx* c, int part, const void* host, size_t bytes, cudaStream_t st);
-const int* ctx_bad_flag(const gl_ctx* c);
+// gl_upload_native's copy alone, enqueued on st (a batch checks the particle
+// indices of all its events afterwards, in one launch)
+gl_status ctx_upload_native_copy(gl_ctx* c, int part, const void* host, size_t bytes, cudaStream_t st);
+// the particle-index check of one event in a launch over several events: its
+// particle arrays, count and species, its first block in the launch and its
+// number of blocks
+struct PartsCheckEv {
+    void* parts;
+    int64_t np;
+    int ns;
+    int block_begin;
+    int nblocks;
+};
+PartsCheckEv ctx_parts_check_event(const gl_ctx* c);
+int parts_check_blocks(int64_t np);
+// the check of ne events (descriptors in device memory) in `blocks` blocks:
+// out-of-range species or original indices are repaired and set bad[e]
+void launch_parts_validate_events(int prec, const PartsCheckEv* evs, int ne, int blocks, int* bad, cudaStream_t st);
 
 // observable slots
 enum { PO_COUNT = 0, PO_PX2, PO_PY2, PO_PL2, PO_DPT2, PO_Q2, PO_Q3, PO_N };

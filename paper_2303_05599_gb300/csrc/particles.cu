@@ -319,6 +319,40 @@ void launch_parts_validate(int prec, void* parts, int64_t np, int ns, int* d_bad
     else parts_validate_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(carve_parts<float>(parts, np), ns, d_bad);
 }
 
+int parts_check_blocks(int64_t np) { return (int)((np + 255) / 256 < 1024 ? (np + 255) / 256 : 1024); }
+
+// block b is block b - block_begin of its event, grid-strided over that
+// event's particles
+template <typename R>
+__global__ void __launch_bounds__(256) parts_validate_events_kernel(const PartsCheckEv* ev, int ne, int* bad) {
+    int lo = 0, hi = ne - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ev[mid].block_begin <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const PartsCheckEv& d = ev[lo];
+    const Parts<R> P = carve_parts<R>(d.parts, d.np);
+    const int blk = blockIdx.x - d.block_begin;
+    for (int64_t i = (int64_t)blk * blockDim.x + threadIdx.x; i < P.np; i += (int64_t)d.nblocks * blockDim.x) {
+        const int32_t s = P.sp[i], id = P.id[i];
+        if (s < 0 || s >= d.ns) {
+            P.sp[i] = 0;
+            atomicOr(bad + lo, 1);
+        }
+        if (id < 0 || (int64_t)id >= P.np) {
+            P.id[i] = (int32_t)i;
+            atomicOr(bad + lo, 1);
+        }
+    }
+}
+
+void launch_parts_validate_events(int prec, const PartsCheckEv* evs, int ne, int blocks, int* bad, cudaStream_t st) {
+    if (blocks < 1 || ne < 1) return;
+    if (prec == 0) parts_validate_events_kernel<double><<<blocks, 256, 0, st>>>(evs, ne, bad);
+    else parts_validate_events_kernel<float><<<blocks, 256, 0, st>>>(evs, ne, bad);
+}
+
 void launch_parts_convert(int prec, void* parts, int64_t np, double* stg, int to_device, cudaStream_t st) {
     const int threads = 128;
     int64_t blocks = (np + threads - 1) / threads;

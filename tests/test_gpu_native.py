@@ -138,3 +138,34 @@ def test_out_of_range_indices_are_reported_and_repaired():
     ev.download(B.GL_BUF_PARTICLES)  # every record lands inside the host buffer
     ev.upload_native(B.GL_NATIVE_PARTICLES, p)
     assert np.array_equal(ev.download_native(B.GL_NATIVE_PARTICLES), p)
+
+
+def test_batch_upload_reports_and_repairs_the_event_with_bad_indices():
+    """The batched upload checks every event's particle indices in one launch:
+    the event with a bad species and a bad original index is named in the
+    error, its records are repaired, and the other events are unchanged."""
+    ws = events(W.FP32_2ROW)
+    b = B.Batch(ws)
+    with torch.cuda.stream(b.stream):
+        b.init()
+        b.step(3)
+        ps = [ev.download_native(B.GL_NATIVE_PARTICLES) for ev in b.events]
+        n = ws[1].n_particles
+        o_sp = _a256(16 * n) + _a256(8 * n) + _a256(32 * n)
+        o_id = o_sp + _a256(4 * n) + _a256(8 * n)
+        bad = [p.copy() for p in ps]
+        bad[1][o_sp:o_sp + 4 * n].view(np.int32)[7] = -1
+        bad[1][o_id:o_id + 4 * n].view(np.int32)[2] = n
+        with pytest.raises(B.GlasmaError) as e:
+            b.upload_native(B.GL_NATIVE_PARTICLES, bad)
+        assert e.value.status == B.GL_ERR_ARG
+        assert "event 1" in str(e.value)
+        fixed = b.events[1].download_native(B.GL_NATIVE_PARTICLES)
+        assert fixed[o_sp:o_sp + 4 * n].view(np.int32)[7] == 0
+        assert fixed[o_id:o_id + 4 * n].view(np.int32)[2] == 2
+        for k in (0, 2):
+            assert np.array_equal(b.events[k].download_native(B.GL_NATIVE_PARTICLES), ps[k])
+        b.upload_native(B.GL_NATIVE_PARTICLES, ps)
+        for k in range(3):
+            assert np.array_equal(b.events[k].download_native(B.GL_NATIVE_PARTICLES), ps[k])
+    b.close()
