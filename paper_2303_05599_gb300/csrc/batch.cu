@@ -176,8 +176,11 @@ __device__ __forceinline__ void push_item(const BatchArgs& b, int lag, int blk) 
     const Fields<R> bn1 = carve_fields<R>(d.field[(n + 1) & 1], Vn);
     const int64_t base = (int64_t)(blk - d.chunk_begin) * b.push_chunk;
     const int64_t end = base + b.push_chunk < d.np ? base + b.push_chunk : d.np;
-    for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x)
+    for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x) {
+        // the next particle's state into L2 while this one is pushed
+        if (i + blockDim.x < end) P.prefetch_l2(i + blockDim.x);
         push_one<R>((const typename Prec<R>::V*)d.site[n & 1], bn1, P, i, d.N, s_t, s_dt, s_dto, s_active, s_sa);
+    }
 }
 
 template <typename R, int TX, int TY>

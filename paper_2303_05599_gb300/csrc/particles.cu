@@ -127,8 +127,12 @@ template <typename R, int B>
 __global__ void __launch_bounds__(B, (sizeof(R) == 4 ? 1024 : 512) / B) push_kernel(const typename Prec<R>::V* __restrict__ site,
                                                            Fields<R> bn1, Parts<R> P, int N, R t, R dt, R dt_over_t,
                                                            uint32_t active, SpeciesArgs<R> sa) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.np; i += (int64_t)gridDim.x * blockDim.x)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.np; i += stride) {
+        // the next particle's state into L2 while this one is pushed
+        if (i + stride < P.np) P.prefetch_l2(i + stride);
         push_one<R>(site, bn1, P, i, N, t, dt, dt_over_t, active, sa);
+    }
 }
 
 template <typename R>

@@ -47,6 +47,7 @@ struct Parts<double> {
         pxy[i] = make_double2(s.px, s.py);
         eP[i] = make_double2(s.eta, s.Pe);
     }
+    __device__ void prefetch_l2(int64_t) const {}
     // streaming (evict-first) forms for the push, which reads and writes each
     // particle once a step: the particles leave L2 to the gathered site fields
     __device__ PState<double> load_cs(int64_t i) const {
@@ -124,6 +125,14 @@ struct Parts<float> {
     __device__ void store_momenta_cs(int64_t i, const PState<float>& s) const {
         __stcs(xyp + i, make_float4(s.x, s.y, s.px, s.py));
         __stcs(eP + i, make_float2(s.eta, s.Pe));
+    }
+    // particle i's state and species requested into L2 ahead of its load
+    __device__ void prefetch_l2(int64_t i) const {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(xyp + i));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(eP + i));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(q + i));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(q + np + i));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(sp + i));
     }
 };
 

@@ -131,7 +131,7 @@ __device__ __forceinline__ void push_one(const typename Prec<R>::V* __restrict__
     // rapidity Wilson line at the new cell: Q <- e^{-i deta phi} Q e^{+i deta phi}
     if (deta != R(0)) {
         const A8<R> ph = load_alg(bn1.phi, (int64_t)jy * N + jx, Vn);
-        p.q = conj_up(exp_i_alg<R, (sizeof(R) == 8 ? 20 : 6)>(ph, -deta), p.q);
+        p.q = conj_up_t(exp_i_alg<R, (sizeof(R) == 8 ? 20 : 6)>(ph, -deta), p.q);
     }
     P.store_cs(i, p);
 }
