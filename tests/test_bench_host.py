@@ -24,7 +24,7 @@ def test_algorithmic_bytes():
 
 
 def test_leapfrog_and_site_field_bytes_are_itemised():
-    # the leapfrog's own bytes (the survey's 448 B per FP32 two-row site) and
+    # the leapfrog's own bytes (448 B per FP32 two-row site: every field read and written once) and
     # the 192 B site-field write add up to the fused launch's bytes
     assert bench.leapfrog_bytes_per_site(1) == 448
     assert bench.site_field_bytes_per_site(1) == 192
