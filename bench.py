@@ -216,8 +216,8 @@ NVML_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowd
 
 class NvmlClockSampler:
     """The same record from NVML read queries (SM clock, its maximum and the
-    active throttle reasons) polled every 2 ms by a thread, so that a timed
-    region of a few tens of milliseconds still holds many samples.  Needs
+    active throttle reasons) polled every 0.25 ms by a thread, so that a timed
+    region of a few milliseconds still holds many samples.  Needs
     libnvidia-ml from the driver; start() returns False without it."""
 
     def __init__(self, device):
@@ -250,7 +250,7 @@ class NvmlClockSampler:
                         nv.nvmlDeviceGetCurrentClocksThrottleReasons(h, ctypes.byref(rs)) == 0):
                     self.samples.append((float(clk.value), float(mx.value),
                                          {n for bit, n in NVML_REASONS.items() if rs.value & bit}))
-                time.sleep(0.002)
+                time.sleep(0.00025)
 
         self.thread = threading.Thread(target=poll, daemon=True)
         self.thread.start()
