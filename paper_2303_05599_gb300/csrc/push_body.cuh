@@ -114,7 +114,8 @@ __device__ __forceinline__ void push_one(const typename Prec<R>::V* __restrict__
     // transports to make (bit 0: x, bit 1: y); one loop body serves both axes,
     // with the link and U or U^+ chosen per lane, so that a warp runs as many
     // transports as its busiest lane needs (crossings are rare, but some lane
-    // of a warp crosses almost every step)
+    // of a warp crosses almost every step).  The traceless transport: a link is
+    // unitary to rounding
     const int dxc = jxu - ixu, dyc = jyu - iyu;
     const int jx = wrapi(jxu, N), jy = wrapi(jyu, N);
     // cell indices of an event fit in 32 bits (N <= 32768)
@@ -125,7 +126,7 @@ __device__ __forceinline__ void push_one(const typename Prec<R>::V* __restrict__
     while (todo) {
         const bool on_x = todo & 1;
         const M3<R> U = load_link(bn1.U, on_x ? 0 : 1, on_x ? ix_link : iy_link, Vn);
-        p.q = conj_dn((on_x ? dxc : dyc) == 1 ? U : dag(U), p.q);
+        p.q = conj_dn_t((on_x ? dxc : dyc) == 1 ? U : dag(U), p.q);
         todo &= todo - 1;
     }
     // rapidity Wilson line at the new cell: Q <- e^{-i deta phi} Q e^{+i deta phi}
