@@ -416,6 +416,19 @@ gl_status gl_batch_observables(gl_batch* batch, gl_obs* out);
  * bitwise those of gl_observables_ex on that event alone. */
 gl_status gl_batch_observables_ex(gl_batch* batch, uint32_t what, gl_obs* out);
 
+/* gl_batch_observables_ex in two halves, so that the results of one step can
+ * be read back while the next runs.  _begin enqueues the reductions of the
+ * events' current state (`what`: GL_OBS_* bits) and their copy into one of
+ * two pinned host slots, and returns without waiting; _end waits for the
+ * oldest outstanding request and fills out[n_events] with its results,
+ * bitwise those gl_batch_observables_ex would have given at the time of the
+ * _begin.  At most two requests are outstanding (a third _begin, an _end
+ * with none, or gl_batch_observables_ex with one outstanding: GL_ERR_STATE).
+ * Steps enqueued between _begin and _end run after the request on the
+ * batch's stream.  gl_batch_destroy waits for outstanding requests. */
+gl_status gl_batch_observables_begin(gl_batch* batch, uint32_t what);
+gl_status gl_batch_observables_end(gl_batch* batch, gl_obs* out);
+
 /* Largest particle count gl_ensemble_sums_noalloc accepts. */
 #define GL_NOALLOC_MAX_PARTICLES 2097152
 

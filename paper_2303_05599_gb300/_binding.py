@@ -98,6 +98,8 @@ SIGNATURES = {
                                            ctypes.c_int32]),
     "gl_batch_get_launch": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "gl_batch_observables_ex": (ctypes.c_int, [_P, ctypes.c_uint32, _P]),
+    "gl_batch_observables_begin": (ctypes.c_int, [_P, ctypes.c_uint32]),
+    "gl_batch_observables_end": (ctypes.c_int, [_P, _P]),
     "gl_batch_segment_rows": (ctypes.c_int32, [_P]),
     "gl_batch_set_segment_rows": (ctypes.c_int, [_P, ctypes.c_int32]),
 }
@@ -426,6 +428,17 @@ class Batch:
             self._chk(lib().gl_batch_observables(self.b, out), "gl_batch_observables")
         else:
             self._chk(lib().gl_batch_observables_ex(self.b, what, out), "gl_batch_observables_ex")
+        return list(out)
+
+    def observables_begin(self, what=None):
+        """Enqueue the observables of the current state (no wait)."""
+        self._chk(lib().gl_batch_observables_begin(self.b, GL_OBS_ALL if what is None else what),
+                  "gl_batch_observables_begin")
+
+    def observables_end(self):
+        """The results of the oldest outstanding observables_begin (waits)."""
+        out = (gl_obs * self.ne)()
+        self._chk(lib().gl_batch_observables_end(self.b, out), "gl_batch_observables_end")
         return list(out)
 
     def close(self):

@@ -511,8 +511,15 @@ struct gl_batch {
     PartsCheckEv* p_pchk;  // pinned [ne]: the index-check descriptors (allocated with h_bad)
     PartsCheckEv* d_pchk;  // [ne] the same on the device, and
     int* d_bad;            // [ne] the index-check flags
-    BObs* p_obs;    // pinned copy of h_obs for its upload, and
-    double* p_rows; // pinned [ne][OBS_W] for the gathered obs rows (both allocated on first use)
+    // observables requests: two slots, each with a pinned copy of h_obs for
+    // its upload, pinned [ne][OBS_W] for the gathered rows, and an event
+    // after its copy back (allocated on first use); obs_count requests are
+    // outstanding, the oldest in slot obs_head
+    BObs* p_obs[2];
+    double* p_rows[2];
+    cudaEvent_t obs_done[2];
+    uint32_t obs_what[2];
+    int obs_head, obs_count;
     char err[256];
 };
 
@@ -690,8 +697,14 @@ gl_status gl_batch_destroy(gl_batch* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->h_bad) cudaFreeHost(b->h_bad);
     if (b->p_pchk) cudaFreeHost(b->p_pchk);
-    if (b->p_obs) cudaFreeHost(b->p_obs);
-    if (b->p_rows) cudaFreeHost(b->p_rows);
+    for (int k = 0; k < 2; k++) {
+        if (b->obs_done[k]) {
+            cudaEventSynchronize(b->obs_done[k]);  // no copy lands in freed memory
+            cudaEventDestroy(b->obs_done[k]);
+        }
+        if (b->p_obs[k]) cudaFreeHost(b->p_obs[k]);
+        if (b->p_rows[k]) cudaFreeHost(b->p_rows[k]);
+    }
     for (int e = 0; e < b->ne; e++) gl_destroy(b->ev[e]);
     delete[] b->ev;
     delete[] b->h_desc;
@@ -1260,9 +1273,10 @@ gl_status gl_batch_upload_native(gl_batch* b, gl_native_part part, const void* c
 
 gl_status gl_batch_observables(gl_batch* b, gl_obs* out) { return gl_batch_observables_ex(b, GL_OBS_ALL, out); }
 
-gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
-    gl::ApiRange range_("gl_batch_observables_ex");
-    if (!b || !out || (what & ~GL_OBS_ALL)) return GL_ERR_ARG;
+// enqueue the observables of every event into slot k: descriptors up, the
+// reductions, the gather and the copy back into the slot's pinned rows, then
+// the slot's event (no wait)
+static gl_status obs_enqueue(gl_batch* b, uint32_t what, int k) {
     // obs rows of all events: out pointers (also for the gather when only the
     // field checks are asked for)
     int blocks = 0, fblocks = 0;
@@ -1288,7 +1302,7 @@ gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
             d.partials = o.partials;
             d.out = o.out;
             d.oa.sp = o.sp;
-            for (int k = 0; k < GL_MAX_SPECIES; k++) { d.oa.q2ref[k] = o.q2ref[k]; d.oa.q3ref[k] = o.q3ref[k]; }
+            for (int q = 0; q < GL_MAX_SPECIES; q++) { d.oa.q2ref[q] = o.q2ref[q]; d.oa.q3ref[q] = o.q3ref[q]; }
             blocks += d.nblocks;
             // an event without particles: zero sums, as the single-event path
             if (d.nblocks == 0)
@@ -1296,17 +1310,21 @@ gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
         }
     }
     // pinned staging: both copies are plain DMA, without the driver's bounce
-    // buffer (the previous call's copies finished before its wait returned)
-    if (!b->p_obs && (cudaHostAlloc((void**)&b->p_obs, sizeof(BObs) * b->ne, cudaHostAllocDefault) != cudaSuccess ||
-                      cudaHostAlloc((void**)&b->p_rows, sizeof(double) * OBS_W * b->ne, cudaHostAllocDefault) !=
-                          cudaSuccess)) {
-        if (b->p_obs) cudaFreeHost(b->p_obs);
-        b->p_obs = nullptr;
-        b->p_rows = nullptr;
-        return bfail(b, GL_ERR_CUDA, "pinned host allocation failed");
+    // buffer (the slot's previous copies finished before its wait returned)
+    if (!b->p_obs[k]) {
+        if (cudaHostAlloc((void**)&b->p_obs[k], sizeof(BObs) * b->ne, cudaHostAllocDefault) != cudaSuccess ||
+            cudaHostAlloc((void**)&b->p_rows[k], sizeof(double) * OBS_W * b->ne, cudaHostAllocDefault) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->obs_done[k], cudaEventDisableTiming) != cudaSuccess) {
+            if (b->p_obs[k]) cudaFreeHost(b->p_obs[k]);
+            if (b->p_rows[k]) cudaFreeHost(b->p_rows[k]);
+            b->p_obs[k] = nullptr;
+            b->p_rows[k] = nullptr;
+            b->obs_done[k] = nullptr;
+            return bfail(b, GL_ERR_CUDA, "pinned host allocation failed");
+        }
     }
-    memcpy(b->p_obs, b->h_obs, sizeof(BObs) * b->ne);
-    cudaMemcpyAsync(b->d_obs, b->p_obs, sizeof(BObs) * b->ne, cudaMemcpyHostToDevice, b->stream);
+    memcpy(b->p_obs[k], b->h_obs, sizeof(BObs) * b->ne);
+    cudaMemcpyAsync(b->d_obs, b->p_obs[k], sizeof(BObs) * b->ne, cudaMemcpyHostToDevice, b->stream);
     if (blocks > 0) {
         int ns = 0;
         for (int e = 0; e < b->ne; e++) ns = b->h_obs[e].oa.sp.n_species > ns ? b->h_obs[e].oa.sp.n_species : ns;
@@ -1325,11 +1343,47 @@ gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
         launch_field_obs_events(b->prec, b->h_obs[0].fo, (const char*)b->d_obs + offsetof(BObs, fo), sizeof(BObs),
                                 b->ne, fblocks, b->stream);
     gather_obs_kernel<<<b->ne, 64, 0, b->stream>>>(b->d_obs, b->d_obs_all);
-    cudaMemcpyAsync(b->p_rows, b->d_obs_all, sizeof(double) * OBS_W * b->ne, cudaMemcpyDeviceToHost, b->stream);
-    const bool ok = cudaStreamSynchronize(b->stream) == cudaSuccess && cudaGetLastError() == cudaSuccess;
-    if (ok)
-        for (int e = 0; e < b->ne; e++) ctx_obs_fill(b->ev[e], what, b->p_rows + (size_t)OBS_W * e, &out[e]);
-    return ok ? GL_OK : bfail(b, GL_ERR_CUDA, "batch observables failed");
+    cudaMemcpyAsync(b->p_rows[k], b->d_obs_all, sizeof(double) * OBS_W * b->ne, cudaMemcpyDeviceToHost, b->stream);
+    cudaEventRecord(b->obs_done[k], b->stream);
+    b->obs_what[k] = what;
+    if (cudaGetLastError() != cudaSuccess) return bfail(b, GL_ERR_CUDA, "batch observables launch failed");
+    return GL_OK;
+}
+
+// wait for slot k's request and fill out[n_events] from its rows
+static gl_status obs_finish(gl_batch* b, int k, gl_obs* out) {
+    const bool ok = cudaEventSynchronize(b->obs_done[k]) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+    if (!ok) return bfail(b, GL_ERR_CUDA, "batch observables failed");
+    for (int e = 0; e < b->ne; e++) ctx_obs_fill(b->ev[e], b->obs_what[k], b->p_rows[k] + (size_t)OBS_W * e, &out[e]);
+    return GL_OK;
+}
+
+gl_status gl_batch_observables_ex(gl_batch* b, uint32_t what, gl_obs* out) {
+    gl::ApiRange range_("gl_batch_observables_ex");
+    if (!b || !out || (what & ~GL_OBS_ALL)) return GL_ERR_ARG;
+    if (b->obs_count > 0) return bfail(b, GL_ERR_STATE, "observables requests outstanding (gl_batch_observables_end)");
+    if (gl_status st = obs_enqueue(b, what, b->obs_head)) return st;
+    return obs_finish(b, b->obs_head, out);
+}
+
+gl_status gl_batch_observables_begin(gl_batch* b, uint32_t what) {
+    gl::ApiRange range_("gl_batch_observables_begin");
+    if (!b || (what & ~GL_OBS_ALL)) return GL_ERR_ARG;
+    if (b->obs_count >= 2) return bfail(b, GL_ERR_STATE, "two observables requests outstanding");
+    const int k = (b->obs_head + b->obs_count) & 1;
+    if (gl_status st = obs_enqueue(b, what, k)) return st;
+    b->obs_count++;
+    return GL_OK;
+}
+
+gl_status gl_batch_observables_end(gl_batch* b, gl_obs* out) {
+    gl::ApiRange range_("gl_batch_observables_end");
+    if (!b || !out) return GL_ERR_ARG;
+    if (b->obs_count == 0) return bfail(b, GL_ERR_STATE, "no observables request outstanding");
+    const int k = b->obs_head;
+    b->obs_head ^= 1;
+    b->obs_count--;
+    return obs_finish(b, k, out);
 }
 
 gl_status gl_batch_set_launch(gl_batch* b, int32_t tile, int32_t push_block, int32_t push_chunk, int32_t fused,

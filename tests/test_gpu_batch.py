@@ -396,3 +396,44 @@ def test_segment_length_changes_nothing():
     with pytest.raises(B.GlasmaError):
         fp64.set_segment_rows(16)
     fp64.close()
+
+
+def test_observables_begin_end_equal_the_synchronous_call():
+    """gl_batch_observables_begin/_end with up to two requests outstanding (a
+    step enqueued between a request and its read) give bitwise the values the
+    synchronous call gives at the same steps; misuse is GL_ERR_STATE."""
+    ws = events(W.FP32_2ROW, sort_every=3)
+    a, b = B.Batch(ws), B.Batch(ws)
+    got_a, got_b = [], []
+    with torch.cuda.stream(a.stream):
+        a.init()
+        for _ in range(7):
+            a.step(1)
+            got_a.append(a.observables(B.GL_OBS_PARTICLES))
+        got_a.append(a.observables())
+    with torch.cuda.stream(b.stream):
+        b.init()
+        with pytest.raises(B.GlasmaError) as e:
+            b.observables_end()
+        assert e.value.status == B.GL_ERR_STATE
+        for k in range(7):
+            b.step(1)
+            b.observables_begin(B.GL_OBS_PARTICLES)
+            if k > 0:
+                got_b.append(b.observables_end())
+        b.observables_begin()
+        with pytest.raises(B.GlasmaError) as e:
+            b.observables_begin()
+        assert e.value.status == B.GL_ERR_STATE
+        with pytest.raises(B.GlasmaError) as e:
+            b.observables()
+        assert e.value.status == B.GL_ERR_STATE
+        got_b.append(b.observables_end())
+        got_b.append(b.observables_end())
+    n_species = len(ws[0].species)
+    assert len(got_a) == len(got_b) == 8
+    for ra, rb in zip(got_a, got_b):
+        for oa, ob in zip(ra, rb):
+            same_obs(oa, ob, n_species)
+    a.close()
+    b.close()
