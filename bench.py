@@ -243,19 +243,26 @@ class NvmlClockSampler:
             return False
         self.nv, self.h = nv, h
         self.stop_flag = False
+        mx = ctypes.c_uint()
+        if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) != 0:  # NVML_CLOCK_SM
+            return False
+        first = threading.Event()
 
         def poll():
-            clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+            # two queries a sample (each takes a fraction of a millisecond);
+            # the maximum clock does not change
+            clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
             while not self.stop_flag:
-                if (nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and  # NVML_CLOCK_SM
-                        nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+                if (nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and
                         nv.nvmlDeviceGetCurrentClocksThrottleReasons(h, ctypes.byref(rs)) == 0):
                     self.samples.append((float(clk.value), float(mx.value),
                                          {n for bit, n in NVML_REASONS.items() if rs.value & bit}))
+                first.set()
                 time.sleep(0.00025)
 
         self.thread = threading.Thread(target=poll, daemon=True)
         self.thread.start()
+        first.wait(timeout=0.5)  # the timed region starts after the first sample
         return True
 
     def stop(self):
