@@ -290,15 +290,22 @@ __device__ __forceinline__ void strip_halo(StripWarpSmem& S, const Fields<float>
     const int yh = wrapi(y0 - 1 + L.lane, N);
     const int yu = wrapi(y0 + L.lane, N);
     const int64_t gl = (int64_t)yh * N + L.xl, g0 = (int64_t)yh * N + x0;
-    const M3<float> Ux = load_link(in.U, 0, gl, Vn);
-    const M3<float> Uy = load_link(in.U, 1, gl, Vn);
-    const M3<float> UyR = load_link(in.U, 1, g0, Vn);
+    // lanes 0 .. nb work on the rows handed on; lane nb + 1 only supplies its
+    // Ux (the link of the row above lane nb's); the lanes beyond load nothing
+    // and work on zeros
+    M3<float> Ux = m_zero<float>(), Uy = m_zero<float>(), UyR = m_zero<float>();
+    A8<float> ph = a_zero<float>(), phR = a_zero<float>(), ex = a_zero<float>();
+    if (L.lane <= nb + 1) Ux = load_link(in.U, 0, gl, Vn);
+    if (L.lane <= nb) {
+        Uy = load_link(in.U, 1, gl, Vn);
+        UyR = load_link(in.U, 1, g0, Vn);
+        ph = load_alg(in.phi, gl, Vn);
+        phR = load_alg(in.phi, g0, Vn);
+        ex = load_alg(in.e, gl, Vn);
+    }
     // Ux of the row above: the next lane's link, the last lane loads it
     M3<float> UxU = shfl_down_m3(Ux);
-    if (L.lane == 31) UxU = load_link(in.U, 0, (int64_t)yu * N + L.xl, Vn);
-    const A8<float> ph = load_alg(in.phi, gl, Vn);
-    const A8<float> phR = load_alg(in.phi, g0, Vn);
-    const A8<float> ex = load_alg(in.e, gl, Vn);
+    if (L.lane == 31 && L.lane <= nb) UxU = load_link(in.U, 0, (int64_t)yu * N + L.xl, Vn);
     const A8<float> A = iah_of_mul_nd(mul_nd_su3(mul_su3(Ux, UyR), UxU), Uy);
     const A8<float> Dn = shfl_up_a8(conj_dn_t(Uy, A));
     const A8<float> tx = conj_up_t(Ux, phR);
@@ -352,6 +359,11 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
     strip_issue_mom(S, in, Vn, N, L, r_first);
     int halo_end = r_first;  // rows below halo_end have halo values in S.halo
     int halo_base = r_first;
+    // the bounds the row body tests, as values the compiler cannot relate to
+    // the loop's first and last rows: one copy of the row body serves the dry
+    // row and the rows near the end (no peeled iterations to fetch)
+    int yb = y_begin, ye = y_end;
+    asm volatile("" : "+r"(yb), "+r"(ye), "+r"(halo_end));
     // (n + 1 + r) mod every, the re-unitarisation phase of row r (the rows
     // that store have y = r): one 64-bit remainder per segment, then a step
     // of one per row
@@ -365,7 +377,7 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
             halo_base = r;
             halo_end = r + nb;
         }
-        const bool dry = r < y_begin;
+        const bool dry = r < yb;
         const bool st = !dry && L.valid && r < y_stop;
         const int k = (r - r_first) & 1, k1 = k ^ 1;
         const int y = wrapi(r, N);
@@ -389,7 +401,7 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
         const A8<float> A = iah_of_mul_nd(mul_nd_su3(mul_su3(Ux, UyR), UxN), Uy);   // plaquette at (x, y)
         // ring slot k (Ux, Uy, phi and the right neighbour's Uy, phi of row r)
         // has been read into registers above: row r + 2 goes there
-        if (r + 2 <= y_end) strip_issue_row(S, k, in, Vn, N, L, r + 2);
+        if (r + 2 <= ye) strip_issue_row(S, k, in, Vn, N, L, r + 2);
         const float4* h = S.halo[r - halo_base];
         // clover: A, its transports from x - 1 (Lf, by the left lane's Ux) and
         // from y - 1, and the fourth leaf carried from the row below
@@ -456,7 +468,7 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
             }
         }
         // the momentum slot's values are all read now: the next row's go there
-        if (r + 1 < y_end) strip_issue_mom(S, in, Vn, N, L, r + 1);
+        if (r + 1 < ye) strip_issue_mom(S, in, Vn, N, L, r + 1);
         if (st) {
             M3<float> ny = mul(exp_i_alg<float, ExpN<float>::n>(eyn, c_link), Uy);
             if (ru == 0) reunit_rows(ny);
