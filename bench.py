@@ -65,10 +65,10 @@ BATCHED = "batched64"
 # shapes), keyed by (workload, events per GPU, kernel, precision).  Absent:
 # not captured for the current kernels.
 TRAFFIC = {
-    ("batched64", 64, "field_step", 1): 521365760 + 694928384,
-    ("batched64", 64, "wong_push", 1): 376825856 + 29904128,
-    ("n1024_mixed", 1, "field_step", 1): 301949952 + 377344256,
-    ("n1024_mixed", 1, "wong_push", 1): 597517056 + 199652608,
+    ("batched64", 64, "field_step", 1): 514721792 + 694291712,
+    ("batched64", 64, "wong_push", 1): 376806400 + 28170496,
+    ("n1024_mixed", 1, "field_step", 1): 302000896 + 377403904,
+    ("n1024_mixed", 1, "wong_push", 1): 589935360 + 197241088,
 }
 
 
