@@ -308,19 +308,19 @@ __global__ void __launch_bounds__(OBS_THREADS) batch_obs_kernel(const BObs* ev, 
                           d.partials + (size_t)b * GL_MAX_SPECIES * PO_N);
 }
 
-// one block per (event, value)
-__global__ void __launch_bounds__(256) batch_obs_finalize(const BObs* ev) {
-    constexpr int W = GL_MAX_SPECIES * PO_N;
-    const BObs& d = ev[blockIdx.x / W];
-    particle_obs_reduce(d.partials, d.nblocks, blockIdx.x % W, d.out);
-}
-
-// every event's obs row into one array [n_events][OBS_W], so the host reads
-// all of them with one copy; one block per event
+// One block per event: the final reductions of the requested parts (the
+// particle values, unless the event has no particles and its row was zeroed;
+// the field checks) into the event's obs row, by the functions the
+// single-event launches use, then the row into all[n_events][OBS_W], so that
+// the host reads every event's row with one copy.
 static constexpr int OBS_W = GL_MAX_SPECIES * PO_N + FO_N;
-__global__ void __launch_bounds__(64) gather_obs_kernel(const BObs* ev, double* all) {
-    const double* src = ev[blockIdx.x].out;
-    for (int k = threadIdx.x; k < OBS_W; k += blockDim.x) all[(size_t)blockIdx.x * OBS_W + k] = src[k];
+__global__ void __launch_bounds__(256) batch_obs_finish(const BObs* ev, uint32_t what, double* all) {
+    const BObs& d = ev[blockIdx.x];
+    if ((what & GL_OBS_PARTICLES) && d.nblocks > 0)
+        obs_finalize_block(d.partials, d.nblocks, GL_MAX_SPECIES * PO_N, ParticleObsKind(), d.out);
+    if (what & GL_OBS_FIELDS) obs_finalize_block(d.fo.partials, d.fo.nblocks, FO_N, FieldObsKind(), d.fo.out);
+    __syncthreads();  // the row's values, written by this block
+    for (int k = threadIdx.x; k < OBS_W; k += blockDim.x) all[(size_t)blockIdx.x * OBS_W + k] = d.out[k];
 }
 
 // tile shapes the autotuner chooses from
@@ -1336,13 +1336,12 @@ static gl_status obs_enqueue(gl_batch* b, uint32_t what, int k) {
             obs_smem_attr(batch_obs_kernel<float>);
             batch_obs_kernel<float><<<blocks, OBS_THREADS, smem, b->stream>>>(b->d_obs, b->ne);
         }
-        batch_obs_finalize<<<b->ne * GL_MAX_SPECIES * PO_N, 256, 0, b->stream>>>(b->d_obs);
     }
     // the field checks of all events, one launch
     if (what & GL_OBS_FIELDS)
         launch_field_obs_events(b->prec, b->h_obs[0].fo, (const char*)b->d_obs + offsetof(BObs, fo), sizeof(BObs),
-                                b->ne, fblocks, b->stream);
-    gather_obs_kernel<<<b->ne, 64, 0, b->stream>>>(b->d_obs, b->d_obs_all);
+                                b->ne, fblocks, false, b->stream);
+    batch_obs_finish<<<b->ne, 256, 0, b->stream>>>(b->d_obs, what, b->d_obs_all);
     cudaMemcpyAsync(b->p_rows[k], b->d_obs_all, sizeof(double) * OBS_W * b->ne, cudaMemcpyDeviceToHost, b->stream);
     cudaEventRecord(b->obs_done[k], b->stream);
     b->obs_what[k] = what;

@@ -742,7 +742,7 @@ static void observables_launch(gl_ctx* c, uint32_t what) {
     if (what & GL_OBS_FIELDS) {
         ObsEvent o;
         ctx_obs_event(c, &o);
-        launch_field_obs_events(c->prec, o.fo, nullptr, 0, 0, o.fo.nblocks, c->stream);
+        launch_field_obs_events(c->prec, o.fo, nullptr, 0, 0, o.fo.nblocks, true, c->stream);
     }
 }
 
@@ -777,9 +777,10 @@ static void observables_fill(const gl_ctx* c, uint32_t what, const double* host,
         o->casimir3_dev[k] = P ? h[PO_Q3] : NAN;
     }
     const double* f = host + GL_MAX_SPECIES * PO_N;
-    o->gauss_max = F ? f[FO_GMAX] : NAN;
+    // the kernels keep the maxima as squared norms
+    o->gauss_max = F ? sqrt(f[FO_GMAX]) : NAN;
     o->gauss_rms = F ? sqrt(f[FO_GSUM] / (double)c->Vn) : NAN;
-    o->unitarity_max = F ? f[FO_UMAX] : NAN;
+    o->unitarity_max = F ? sqrt(f[FO_UMAX]) : NAN;
     // the means of the squared site fields refer to the last pushed time
     const bool S = F && site_holds(c, c->pstep - 1);
     o->mean_trE_T2 = S ? f[FO_ET2] / (double)c->Vn : NAN;

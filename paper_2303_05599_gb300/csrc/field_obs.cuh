@@ -2,9 +2,11 @@
 // the links, the squared site fields whose lattice means give the energy
 // density) and the block reduction of their accumulators, shared by the
 // single-event launch (obs.cu) and the one launch over all events of a batch.
+// The maxima leave the kernels as squared norms; the host takes their roots.
 #pragma once
 #include "internal.h"
 #include "layout.cuh"
+#include "obs_body.cuh"
 
 namespace gl {
 
@@ -28,8 +30,12 @@ __device__ __forceinline__ M3<double> to_d(const M3<R>& a) {
 // Site s = (x, y) into the accumulators v[FO_N]:
 //   G(x) = sum_i [e_i(x) - U_i(x-i)^+ e_i(x-i) U_i(x-i)] + i[phi(x), pi(x)]
 // (with the full transport: for a link that is not unitary, which is what the
-// check is for, U^+ e U has a trace), ||U U^+ - 1||_F of both links at s, and
-// tr X^2 = X^a X^a / 2 of the six site fields.
+// check is for, U^+ e U has a trace) and ||U U^+ - 1||_F of both links at s,
+// in FP64; the maxima are kept as squared norms (the root, monotonic, is taken
+// once of the maximum).  The sums of squares of the six site fields, whose
+// halves are tr X^2 = X^a X^a / 2, go into SquareSum<R> slots: an FP32
+// state's squares are exact as float pairs, so its sums cost no FP64 issue
+// (field_obs_finish turns the slots into FP64 values).
 template <typename R>
 __device__ __forceinline__ void field_obs_site(const Fields<R>& f, const typename Prec<R>::V* __restrict__ site,
                                                int N, int64_t Vn, int64_t s, double* v) {
@@ -37,39 +43,58 @@ __device__ __forceinline__ void field_obs_site(const Fields<R>& f, const typenam
     const int x = (int)(s % N), y = (int)(s / N);
     const int64_t sb[2] = {(int64_t)y * N + (x == 0 ? N - 1 : x - 1), (int64_t)(y == 0 ? N - 1 : y - 1) * N + x};
     A8<double> G = icomm(to_d(load_alg(f.phi, s, Vn)), to_d(load_alg(f.pi, s, Vn)));
+#pragma unroll
     for (int d = 0; d < 2; d++) {
         const typename Prec<R>::V* e = f.e + (size_t)d * AP * Vn;
         const A8<double> eh = to_d(load_alg(e, s, Vn));
         const A8<double> eb = conj_dn(to_d(load_link(f.U, d, sb[d], Vn)), to_d(load_alg(e, sb[d], Vn)));
         for (int a = 0; a < 8; a++) G.v[a] += eh.v[a] - eb.v[a];
-        // unitarity of the link at (d, s): ||U U^+ - 1||_F from the Gram
-        // matrix of the rows (Hermitian: upper triangle, off-diagonal twice)
+        // unitarity of the link at (d, s): ||U U^+ - 1||_F^2 from the Gram
+        // matrix of the rows (Hermitian: upper triangle, off-diagonal twice;
+        // the diagonal is real)
         const M3<double> u = to_d(load_link(f.U, d, s, Vn));
         double n2 = 0;
         for (int i = 0; i < 3; i++)
             for (int j = i; j < 3; j++) {
                 double gr = 0, gi = 0;
                 for (int k = 0; k < 3; k++) {
-                    gr += u.re[i][k] * u.re[j][k] + u.im[i][k] * u.im[j][k];
-                    gi += u.im[i][k] * u.re[j][k] - u.re[i][k] * u.im[j][k];
+                    gr = fma(u.re[i][k], u.re[j][k], gr);
+                    gr = fma(u.im[i][k], u.im[j][k], gr);
+                    if (i != j) {
+                        gi = fma(u.im[i][k], u.re[j][k], gi);
+                        gi = fma(-u.re[i][k], u.im[j][k], gi);
+                    }
                 }
                 const double r = gr - (i == j ? 1.0 : 0.0);
                 n2 += (i == j ? 1.0 : 2.0) * (r * r + gi * gi);
             }
-        v[FO_UMAX] = nanmax(v[FO_UMAX], sqrt(n2));
+        v[FO_UMAX] = nanmax(v[FO_UMAX], n2);
     }
     const double g2 = a_dot(G, G);
-    v[FO_GMAX] = nanmax(v[FO_GMAX], sqrt(g2));
+    v[FO_GMAX] = nanmax(v[FO_GMAX], g2);
     v[FO_GSUM] += g2;
-    double tr[6];
+#pragma unroll
     for (int k = 0; k < 6; k++) {
-        const A8<double> X = to_d(load_alg(site + (size_t)k * AP * Vn, s, Vn));
-        tr[k] = 0.5 * a_dot(X, X);
+        const A8<R> X = load_alg(site + (size_t)k * AP * Vn, s, Vn);
+        const int slot = k < 2 ? FO_ET2 : k == 2 ? FO_EL2 : k < 5 ? FO_BT2 : FO_BL2;
+#pragma unroll
+        for (int a = 0; a < 8; a++) v[slot] = SquareSum<R>::add(v[slot], X.v[a]);
     }
-    v[FO_ET2] += tr[0] + tr[1];
-    v[FO_EL2] += tr[2];
-    v[FO_BT2] += tr[3] + tr[4];
-    v[FO_BL2] += tr[5];
+}
+
+// the thread's accumulators before its first site
+template <typename R>
+__device__ __forceinline__ void field_obs_init(double* v) {
+    v[FO_GMAX] = v[FO_GSUM] = v[FO_UMAX] = 0.0;
+#pragma unroll
+    for (int k = FO_ET2; k <= FO_BL2; k++) v[k] = SquareSum<R>::init();
+}
+
+// after its last site: the sums of squares as FP64 halves (tr X^2)
+template <typename R>
+__device__ __forceinline__ void field_obs_finish(double* v) {
+#pragma unroll
+    for (int k = FO_ET2; k <= FO_BL2; k++) v[k] = 0.5 * SquareSum<R>::finish(v[k]);
 }
 
 // the block's accumulators (maxima and sums, fixed order) into row[FO_N];
@@ -92,25 +117,6 @@ __device__ __forceinline__ void field_obs_block_reduce(double* v, double* row) {
             a = (k == FO_GMAX || k == FO_UMAX) ? nanmax(a, wacc[w][k]) : a + wacc[w][k];
         row[k] = a;
     }
-}
-
-// value k of the per-block rows partials[nblocks][FO_N] into *out, by one
-// block of 256 threads: strided partial results, then a fixed-order tree
-__device__ __forceinline__ void field_obs_final(const double* partials, int nblocks, int k, double* out) {
-    __shared__ double red[256];
-    const bool mx = k == FO_GMAX || k == FO_UMAX;
-    double a = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        const double v = partials[(size_t)b * FO_N + k];
-        a = mx ? nanmax(a, v) : a + v;
-    }
-    red[threadIdx.x] = a;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] = mx ? nanmax(red[threadIdx.x], red[threadIdx.x + o]) : red[threadIdx.x] + red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = red[0];
 }
 
 }  // namespace gl

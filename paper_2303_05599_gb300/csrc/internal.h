@@ -91,9 +91,11 @@ inline int field_obs_blocks(int N) {
 // their nblocks), their descriptors `stride` bytes apart from the device
 // address evs; or, with ne == 0, of the one event `one` (block_begin 0).  One
 // kernel serves both, so an event's results are bitwise the same whether it
-// is checked alone or with others.
+// is checked alone or with others.  finalize: also reduce each event's rows
+// into its out (one block per event, obs_finalize_block); a caller that
+// passes false runs that reduction itself, with the same function.
 void launch_field_obs_events(int prec, const FieldObsEv& one, const void* evs, size_t stride, int ne, int blocks,
-                             cudaStream_t st);
+                             bool finalize, cudaStream_t st);
 // one context's particle-observables launch, for the batched reduction
 struct ObsEvent {
     void* parts;

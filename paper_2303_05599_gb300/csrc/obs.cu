@@ -31,26 +31,27 @@ __global__ void __launch_bounds__(256) field_obs_kernel(FieldObsEv one, const ch
     const int64_t Vn = (int64_t)d.N * d.N;
     const Fields<R> f = carve_fields<R>((void*)d.fields, Vn);
     const typename Prec<R>::V* site = (const typename Prec<R>::V*)d.site;
-    double v[FO_N] = {0, 0, 0, 0, 0, 0, 0};
+    double v[FO_N];
+    field_obs_init<R>(v);
     for (int64_t s = (int64_t)blk * blockDim.x + threadIdx.x; s < Vn; s += (int64_t)d.nblocks * blockDim.x)
         field_obs_site<R>(f, site, d.N, Vn, s, v);
+    field_obs_finish<R>(v);
     field_obs_block_reduce(v, d.partials + (size_t)blk * FO_N);
 }
 
-// value k of event e in block e * FO_N + k
+// the FO_N values of event e in block e
 __global__ void __launch_bounds__(256) field_obs_finalize(FieldObsEv one, const char* evs, size_t stride, int ne) {
-    const FieldObsEv d = field_obs_event(one, ne > 0 ? evs : nullptr, stride, blockIdx.x / FO_N);
-    const int k = blockIdx.x % FO_N;
-    field_obs_final(d.partials, d.nblocks, k, d.out + k);
+    const FieldObsEv d = field_obs_event(one, ne > 0 ? evs : nullptr, stride, blockIdx.x);
+    obs_finalize_block(d.partials, d.nblocks, FO_N, FieldObsKind(), d.out);
 }
 
 void launch_field_obs_events(int prec, const FieldObsEv& one, const void* evs, size_t stride, int ne, int blocks,
-                             cudaStream_t st) {
+                             bool finalize, cudaStream_t st) {
     if (blocks < 1) return;
     const char* p = (const char*)evs;
     if (prec == 0) field_obs_kernel<double><<<blocks, 256, 0, st>>>(one, p, stride, ne);
     else field_obs_kernel<float><<<blocks, 256, 0, st>>>(one, p, stride, ne);
-    field_obs_finalize<<<(ne > 0 ? ne : 1) * FO_N, 256, 0, st>>>(one, p, stride, ne);
+    if (finalize) field_obs_finalize<<<ne > 0 ? ne : 1, 256, 0, st>>>(one, p, stride, ne);
 }
 
 // ------------------------------------------------------------ canonical <-> device

@@ -29,13 +29,13 @@ namespace gl {
 static constexpr int OBS_THREADS = 256;
 static constexpr int OBS_MAX_BLOCKS = 1024;
 
-// particles per observables block: at least 4096 (16 a thread, so that the
-// block's final tree is a small share of its FP64 work), at most
-// OBS_MAX_BLOCKS blocks
+// particles per observables block: at least 1024 (4 a thread; the block's
+// final tree, ns x 7 rows of 255 combinations, stays a small share of its
+// work), at most OBS_MAX_BLOCKS blocks
 __host__ __device__ inline int64_t obs_chunk(int64_t np) {
     int64_t c = (np + OBS_MAX_BLOCKS - 1) / OBS_MAX_BLOCKS;
     c = (c + OBS_THREADS - 1) / OBS_THREADS * OBS_THREADS;
-    return c < 4096 ? 4096 : c;
+    return c < 1024 ? 1024 : c;
 }
 __host__ __device__ inline int obs_blocks(int64_t np) {
     return np > 0 ? (int)((np + obs_chunk(np) - 1) / obs_chunk(np)) : 0;
@@ -254,24 +254,39 @@ inline void obs_smem_attr(K f) {
     cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)obs_smem_bytes(GL_MAX_SPECIES));
 }
 
-// value k of GL_MAX_SPECIES * PO_N from nblocks partial rows: strided partial
-// results, then a fixed-order tree; blockDim.x == 256
-__device__ __forceinline__ void particle_obs_reduce(const double* partials, int nblocks, int k, double* out) {
-    __shared__ double red[256];
-    const int width = GL_MAX_SPECIES * PO_N;
-    const bool mx = po_is_max(k % PO_N);
-    double a = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        const double v = partials[(size_t)b * width + k];
-        a = mx ? nanmax(a, v) : a + v;
+// The final reduction of per-block partial rows [nblocks][width] (sums, or
+// NaN-propagating maxima where is_max(k)) into out[0, width), by one block:
+// warp w takes values w, w + warps, ...; for each, lane l combines rows l,
+// l + 32, ... in order, then the warp's fixed shuffle tree.  The order
+// depends only on nblocks, so every launch that reduces the same rows (one
+// event, or one block per event of a batch) gives bitwise the same values.
+template <typename IsMax>
+__device__ __forceinline__ void obs_finalize_block(const double* partials, int nblocks, int width, IsMax is_max,
+                                                   double* out) {
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    for (int k = threadIdx.x >> 5; k < width; k += warps) {
+        const bool mx = is_max(k);
+        double a = 0.0;
+        for (int b = lane; b < nblocks; b += 32) {
+            const double v = partials[(size_t)b * width + k];
+            a = mx ? nanmax(a, v) : a + v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double oth = __shfl_down_sync(0xffffffffu, a, o);
+            a = mx ? nanmax(a, oth) : a + oth;
+        }
+        if (lane == 0) out[k] = a;
     }
-    red[threadIdx.x] = a;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] = mx ? nanmax(red[threadIdx.x], red[threadIdx.x + o]) : red[threadIdx.x] + red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[k] = red[0];
 }
+
+// the kinds of the particle values (GL_MAX_SPECIES x PO_N) and of the field
+// checks (FO_N)
+struct ParticleObsKind {
+    __device__ bool operator()(int k) const { return po_is_max(k % PO_N); }
+};
+struct FieldObsKind {
+    __device__ bool operator()(int k) const { return k == FO_GMAX || k == FO_UMAX; }
+};
 
 }  // namespace gl

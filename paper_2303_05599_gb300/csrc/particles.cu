@@ -367,7 +367,7 @@ void launch_parts_convert(int prec, void* parts, int64_t np, double* stg, int to
 }
 
 // ------------------------------------------------------------ particle observables
-// one block per chunk of obs_chunk(np) particles, then one block per value
+// one block per chunk of obs_chunk(np) particles, then one block for the final reduction
 template <typename R>
 __global__ void __launch_bounds__(OBS_THREADS) particle_obs_kernel(Parts<R> P, double t, uint32_t active, ObsArgs oa,
                                                                    double* partials) {
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(OBS_THREADS) particle_obs_kernel(Parts<R> P, d
 }
 
 __global__ void __launch_bounds__(256) particle_obs_finalize(const double* partials, int nblocks, double* out) {
-    particle_obs_reduce(partials, nblocks, blockIdx.x, out);
+    obs_finalize_block(partials, nblocks, GL_MAX_SPECIES * PO_N, ParticleObsKind(), out);
 }
 
 void launch_particle_obs(int prec, const void* parts, int64_t np, double t, uint32_t active_mask,
@@ -402,7 +402,7 @@ void launch_particle_obs(int prec, const void* parts, int64_t np, double t, uint
         particle_obs_kernel<float><<<blocks, OBS_THREADS, smem, st>>>(carve_parts<float>((void*)parts, np), t,
                                                                       active_mask, oa, partials);
     }
-    particle_obs_finalize<<<GL_MAX_SPECIES * PO_N, 256, 0, st>>>(partials, blocks, out);
+    particle_obs_finalize<<<1, 256, 0, st>>>(partials, blocks, out);
 }
 
 }  // namespace gl
