@@ -309,18 +309,25 @@ __global__ void __launch_bounds__(OBS_THREADS) batch_obs_kernel(const BObs* ev, 
 }
 
 // One block per event: the final reductions of the requested parts (the
-// particle values, unless the event has no particles and its row was zeroed;
-// the field checks) into the event's obs row, by the functions the
-// single-event launches use, then the row into all[n_events][OBS_W], so that
-// the host reads every event's row with one copy.
+// particle values, or zeros for an event without particles; the field checks)
+// into the event's obs row, by the function the single-event launches use,
+// and into all[n_events][OBS_W], so that the host reads every event's row
+// with one copy (the parts not requested are not copied: the host does not
+// read them).
 static constexpr int OBS_W = GL_MAX_SPECIES * PO_N + FO_N;
-__global__ void __launch_bounds__(256) batch_obs_finish(const BObs* ev, uint32_t what, double* all) {
+static_assert(GL_MAX_SPECIES * PO_N <= OBS_FINAL_WARPS * OBS_FINAL_V && FO_N <= OBS_FINAL_WARPS * OBS_FINAL_V,
+              "obs_finalize_block takes at most OBS_FINAL_WARPS x OBS_FINAL_V values");
+__global__ void __launch_bounds__(OBS_FINAL_WARPS * 32) batch_obs_finish(const BObs* ev, uint32_t what, double* all) {
     const BObs& d = ev[blockIdx.x];
-    if ((what & GL_OBS_PARTICLES) && d.nblocks > 0)
-        obs_finalize_block(d.partials, d.nblocks, GL_MAX_SPECIES * PO_N, ParticleObsKind(), d.out);
-    if (what & GL_OBS_FIELDS) obs_finalize_block(d.fo.partials, d.fo.nblocks, FO_N, FieldObsKind(), d.fo.out);
-    __syncthreads();  // the row's values, written by this block
-    for (int k = threadIdx.x; k < OBS_W; k += blockDim.x) all[(size_t)blockIdx.x * OBS_W + k] = d.out[k];
+    double* row = all + (size_t)blockIdx.x * OBS_W;
+    if (what & GL_OBS_PARTICLES) {
+        if (d.nblocks > 0)
+            obs_finalize_block(d.partials, d.nblocks, GL_MAX_SPECIES * PO_N, ParticleObsKind(), d.out, row);
+        else
+            for (int k = threadIdx.x; k < GL_MAX_SPECIES * PO_N; k += blockDim.x) row[k] = 0.0;
+    }
+    if (what & GL_OBS_FIELDS)
+        obs_finalize_block(d.fo.partials, d.fo.nblocks, FO_N, FieldObsKind(), d.fo.out, row + GL_MAX_SPECIES * PO_N);
 }
 
 // tile shapes the autotuner chooses from
@@ -1341,7 +1348,7 @@ static gl_status obs_enqueue(gl_batch* b, uint32_t what, int k) {
     if (what & GL_OBS_FIELDS)
         launch_field_obs_events(b->prec, b->h_obs[0].fo, (const char*)b->d_obs + offsetof(BObs, fo), sizeof(BObs),
                                 b->ne, fblocks, false, b->stream);
-    batch_obs_finish<<<b->ne, 256, 0, b->stream>>>(b->d_obs, what, b->d_obs_all);
+    batch_obs_finish<<<b->ne, OBS_FINAL_WARPS * 32, 0, b->stream>>>(b->d_obs, what, b->d_obs_all);
     cudaMemcpyAsync(b->p_rows[k], b->d_obs_all, sizeof(double) * OBS_W * b->ne, cudaMemcpyDeviceToHost, b->stream);
     cudaEventRecord(b->obs_done[k], b->stream);
     b->obs_what[k] = what;

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) field_obs_kernel(FieldObsEv one, const ch
 }
 
 // the FO_N values of event e in block e
-__global__ void __launch_bounds__(256) field_obs_finalize(FieldObsEv one, const char* evs, size_t stride, int ne) {
+__global__ void __launch_bounds__(OBS_FINAL_WARPS * 32) field_obs_finalize(FieldObsEv one, const char* evs, size_t stride, int ne) {
     const FieldObsEv d = field_obs_event(one, ne > 0 ? evs : nullptr, stride, blockIdx.x);
     obs_finalize_block(d.partials, d.nblocks, FO_N, FieldObsKind(), d.out);
 }
@@ -51,7 +51,7 @@ void launch_field_obs_events(int prec, const FieldObsEv& one, const void* evs, s
     const char* p = (const char*)evs;
     if (prec == 0) field_obs_kernel<double><<<blocks, 256, 0, st>>>(one, p, stride, ne);
     else field_obs_kernel<float><<<blocks, 256, 0, st>>>(one, p, stride, ne);
-    if (finalize) field_obs_finalize<<<ne > 0 ? ne : 1, 256, 0, st>>>(one, p, stride, ne);
+    if (finalize) field_obs_finalize<<<ne > 0 ? ne : 1, OBS_FINAL_WARPS * 32, 0, st>>>(one, p, stride, ne);
 }
 
 // ------------------------------------------------------------ canonical <-> device

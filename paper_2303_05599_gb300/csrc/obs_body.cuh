@@ -11,8 +11,9 @@
 //
 // Per-particle quantities are evaluated in the state's precision.  Within a
 // block each thread accumulates its own particles (c0 + tid, c0 + tid +
-// OBS_THREADS, ...) into its own column of shared memory, then one
-// fixed-order FP64 tree combines the columns.  FP64 issue is the scarce
+// OBS_THREADS, ...) into its own column of shared memory, then a fixed-order
+// reduction combines the columns (per row: each lane over four columns, then a
+// shuffle tree).  FP64 issue is the scarce
 // resource of this reduction (GB300 runs FP64 at 1/64 of the FP32 rate), so a
 // particle of an FP32 state costs one FP64 add (p_T^2(tau_form), stored in
 // FP64): its squares p_x^2, p_y^2, p_L^2 are summed as exact float pairs (see
@@ -172,9 +173,9 @@ __device__ __forceinline__ double obs_combine(int k, double a, double b) {
 // blockDim.x == OBS_THREADS, obs_smem_bytes(oa.sp.n_species) of dynamic
 // shared memory at least.  Per thread and species, in its column: the count,
 // the sums of p_x^2, p_y^2, p_L^2 (SquareSum) and of p_T^2(tau_form) (FP64,
-// in the PO_DPT2 slot) and the Casimir slots; then one fixed-order tree over
-// the columns, and one thread per species turns the block's slots into FP64
-// values (<dp_T^2> = sum p_x^2 + sum p_y^2 - sum p_T^2(tau_form)).
+// in the PO_DPT2 slot) and the Casimir slots; then one fixed-order reduction
+// of each row's columns, and one thread per species turns the block's slots
+// into FP64 values (<dp_T^2> = sum p_x^2 + sum p_y^2 - sum p_T^2(tau_form)).
 template <typename R>
 __device__ __forceinline__ void particle_obs_block(const Parts<R>& P, double t, uint32_t active, const ObsArgs& oa,
                                                    int64_t c0, int64_t c1, double* out) {
@@ -221,14 +222,19 @@ __device__ __forceinline__ void particle_obs_block(const Parts<R>& P, double t, 
         if (oki) accumulate(si, pi_, ti);
         if (okj) accumulate(sj, pj, tj);
     }
-    // level o folds column c + o into column c (c < o) of every row
-    for (int o = OBS_THREADS / 2; o > 0; o >>= 1) {
-        __syncthreads();
-        for (int w = tid; w < rows * o; w += OBS_THREADS) {
-            const int r = w / o, c = w - r * o;
-            double* a = obs_acc + r * OBS_THREADS;
-            a[c] = obs_combine<R>(r % PO_N, a[c], a[c + o]);
-        }
+    // each row's columns: warp w takes rows w, w + 8, ...; lane l combines
+    // columns l, l + 32, ... in order, then the warp's fixed shuffle tree, and
+    // lane 0 leaves the row's total in column 0
+    __syncthreads();
+    const int lane = tid & 31;
+    for (int r = tid >> 5; r < rows; r += OBS_THREADS / 32) {
+        double* a = obs_acc + r * OBS_THREADS;
+        const int kind = r % PO_N;
+        double x = a[lane];
+        for (int c = lane + 32; c < OBS_THREADS; c += 32) x = obs_combine<R>(kind, x, a[c]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = obs_combine<R>(kind, x, __shfl_down_sync(0xffffffffu, x, o));
+        if (lane == 0) a[0] = x;
     }
     __syncthreads();
     if (tid < ns) {
@@ -255,28 +261,49 @@ inline void obs_smem_attr(K f) {
 }
 
 // The final reduction of per-block partial rows [nblocks][width] (sums, or
-// NaN-propagating maxima where is_max(k)) into out[0, width), by one block:
-// warp w takes values w, w + warps, ...; for each, lane l combines rows l,
-// l + 32, ... in order, then the warp's fixed shuffle tree.  The order
-// depends only on nblocks, so every launch that reduces the same rows (one
-// event, or one block per event of a batch) gives bitwise the same values.
+// NaN-propagating maxima where is_max(k)) into out[0, width) and, when copy
+// is not null, into copy[0, width) as well, by one block of 8 warps: warp w
+// takes values w, w + 8, ... (at most OBS_FINAL_V of them); for each, lane l
+// combines rows l, l + 32, ... in order, then the warp's fixed shuffle tree.
+// A lane loads its row's values of all the warp's values at once, so a
+// reduction over at most 32 rows waits on one load.  The order depends only
+// on nblocks, so every launch that reduces the same rows (one event, or one
+// block per event of a batch) gives bitwise the same values.
+static constexpr int OBS_FINAL_WARPS = 8, OBS_FINAL_V = 8;
 template <typename IsMax>
 __device__ __forceinline__ void obs_finalize_block(const double* partials, int nblocks, int width, IsMax is_max,
-                                                   double* out) {
-    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
-    for (int k = threadIdx.x >> 5; k < width; k += warps) {
-        const bool mx = is_max(k);
-        double a = 0.0;
-        for (int b = lane; b < nblocks; b += 32) {
-            const double v = partials[(size_t)b * width + k];
-            a = mx ? nanmax(a, v) : a + v;
+                                                   double* out, double* copy = nullptr) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double acc[OBS_FINAL_V];
+#pragma unroll
+    for (int j = 0; j < OBS_FINAL_V; j++) acc[j] = 0.0;
+    for (int b = lane; b < nblocks; b += 32) {
+        const double* row = partials + (size_t)b * width;
+        double v[OBS_FINAL_V];
+#pragma unroll
+        for (int j = 0; j < OBS_FINAL_V; j++) {
+            const int k = w + j * OBS_FINAL_WARPS;
+            v[j] = k < width ? row[k] : 0.0;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double oth = __shfl_down_sync(0xffffffffu, a, o);
-            a = mx ? nanmax(a, oth) : a + oth;
+        for (int j = 0; j < OBS_FINAL_V; j++) {
+            const int k = w + j * OBS_FINAL_WARPS;
+            acc[j] = (k < width && is_max(k)) ? nanmax(acc[j], v[j]) : acc[j] + v[j];
         }
-        if (lane == 0) out[k] = a;
+    }
+#pragma unroll
+    for (int j = 0; j < OBS_FINAL_V; j++) {
+        const int k = w + j * OBS_FINAL_WARPS;
+        const bool mx = k < width && is_max(k);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double oth = __shfl_down_sync(0xffffffffu, acc[j], o);
+            acc[j] = mx ? nanmax(acc[j], oth) : acc[j] + oth;
+        }
+        if (lane == 0 && k < width) {
+            out[k] = acc[j];
+            if (copy) copy[k] = acc[j];
+        }
     }
 }
 

@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(OBS_THREADS) particle_obs_kernel(Parts<R> P, d
     particle_obs_block<R>(P, t, active, oa, c0, c1, partials + (size_t)blockIdx.x * GL_MAX_SPECIES * PO_N);
 }
 
-__global__ void __launch_bounds__(256) particle_obs_finalize(const double* partials, int nblocks, double* out) {
+__global__ void __launch_bounds__(OBS_FINAL_WARPS * 32) particle_obs_finalize(const double* partials, int nblocks, double* out) {
     obs_finalize_block(partials, nblocks, GL_MAX_SPECIES * PO_N, ParticleObsKind(), out);
 }
 
@@ -402,7 +402,7 @@ void launch_particle_obs(int prec, const void* parts, int64_t np, double t, uint
         particle_obs_kernel<float><<<blocks, OBS_THREADS, smem, st>>>(carve_parts<float>((void*)parts, np), t,
                                                                       active_mask, oa, partials);
     }
-    particle_obs_finalize<<<1, 256, 0, st>>>(partials, blocks, out);
+    particle_obs_finalize<<<1, OBS_FINAL_WARPS * 32, 0, st>>>(partials, blocks, out);
 }
 
 }  // namespace gl
