@@ -30,13 +30,17 @@ namespace gl {
 static constexpr int OBS_THREADS = 256;
 static constexpr int OBS_MAX_BLOCKS = 1024;
 
-// particles per observables block: at least 1024 (4 a thread; the block's
-// final tree, ns x 7 rows of 255 combinations, stays a small share of its
-// work), at most OBS_MAX_BLOCKS blocks
+// particles per observables block: an eighth of the event's particles, kept
+// within [1024, 4096] (at least 4 a thread, so that the block's reductions of
+// its columns stay a small share of its work; small events still spread over
+// 8 blocks, large ones take 16 a thread), and at most OBS_MAX_BLOCKS blocks;
+// a multiple of OBS_THREADS.  A function of the event's particle count only.
 __host__ __device__ inline int64_t obs_chunk(int64_t np) {
+    int64_t t = (np + 7) / 8;
+    t = t < 1024 ? 1024 : t > 4096 ? 4096 : t;
     int64_t c = (np + OBS_MAX_BLOCKS - 1) / OBS_MAX_BLOCKS;
-    c = (c + OBS_THREADS - 1) / OBS_THREADS * OBS_THREADS;
-    return c < 1024 ? 1024 : c;
+    if (c < t) c = t;
+    return (c + OBS_THREADS - 1) / OBS_THREADS * OBS_THREADS;
 }
 __host__ __device__ inline int obs_blocks(int64_t np) {
     return np > 0 ? (int)((np + obs_chunk(np) - 1) / obs_chunk(np)) : 0;
