@@ -382,9 +382,13 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
         const int k = (r - r_first) & 1, k1 = k ^ 1;
         const int y = wrapi(r, N);
         const int64_t g = (int64_t)y * N + L.x;
-        // rows r and r + 1 are in the ring (r + 1 was issued a row ago), and
-        // row r's momenta in their slot
-        cp_async_wait_group<0>();
+        // rows r and r + 1 are in the ring (r + 1 was issued a row ago).  Each
+        // row commits two cp.async groups, ring row r + 2 after the plaquette
+        // and the momenta of row r + 1 at its end (empty groups where there is
+        // nothing to copy), so all but the newest group (row r's momenta)
+        // are complete here, and all but the newest (ring row r + 2) before
+        // the momenta are read: their copy has the plaquette's time as well
+        cp_async_wait_group<1>();
         const M3<float> Ux = link_of(S.ring[k][0][L.lane], S.ring[k][1][L.lane], S.ring[k][2][L.lane]);
         const M3<float> Uy = link_of(S.ring[k][3][L.lane], S.ring[k][4][L.lane], S.ring[k][5][L.lane]);
         const A8<float> ph = alg_of(S.ring[k][6][L.lane], S.ring[k][7][L.lane]);
@@ -402,6 +406,7 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
         // ring slot k (Ux, Uy, phi and the right neighbour's Uy, phi of row r)
         // has been read into registers above: row r + 2 goes there
         if (r + 2 <= ye) strip_issue_row(S, k, in, Vn, N, L, r + 2);
+        else cp_async_commit();
         const float4* h = S.halo[r - halo_base];
         // clover: A, its transports from x - 1 (Lf, by the left lane's Ux) and
         // from y - 1, and the fourth leaf carried from the row below
@@ -425,6 +430,7 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
                 lap.v[c] = tx.v[c] + bx.v[c];
             }
             if (st) store_alg(site + (size_t)8 * Vn, g, Vn, By);
+            cp_async_wait_group<1>();
             const A8<float> ex = alg_of(S.mom[0][L.lane], S.mom[1][L.lane]);
             A8<float> exn, exs;
             e_update(ex, A, C.dn, cx, t, dt, inv_t, exn, exs);
@@ -444,6 +450,7 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
         const A8<float> ty = conj_up_t(Uy, phN);
         const A8<float> cy = icomm(ty, ph);
         // y direction: D_y phi, the e_y update, E_y, the scalar and pi
+        cp_async_wait_group<1>();
         const A8<float> ey = alg_of(S.mom[2][L.lane], S.mom[3][L.lane]);
         A8<float> eyn, eys;
         e_update(ey, Lf, A, cy, t, dt, inv_t, eyn, eys);
@@ -469,6 +476,7 @@ __device__ __forceinline__ void strip_segment(StripWarpSmem& S, const Fields<flo
         }
         // the momentum slot's values are all read now: the next row's go there
         if (r + 1 < ye) strip_issue_mom(S, in, Vn, N, L, r + 1);
+        else cp_async_commit();
         if (st) {
             M3<float> ny = mul(exp_i_alg<float, ExpN<float>::n>(eyn, c_link), Uy);
             if (ru == 0) reunit_rows(ny);
