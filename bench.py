@@ -65,9 +65,9 @@ BATCHED = "batched64"
 # shapes), keyed by (workload, events per GPU, kernel, precision).  Absent:
 # not captured for the current kernels.
 TRAFFIC = {
-    ("batched64", 64, "field_step", 1): 514721792 + 694291712,
+    ("batched64", 64, "field_step", 1): 514717696 + 694459904,
     ("batched64", 64, "wong_push", 1): 376806400 + 28170496,
-    ("n1024_mixed", 1, "field_step", 1): 302000896 + 377403904,
+    ("n1024_mixed", 1, "field_step", 1): 301978624 + 377472000,
     ("n1024_mixed", 1, "wong_push", 1): 589935360 + 197241088,
 }
 
