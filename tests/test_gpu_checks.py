@@ -13,7 +13,8 @@ a snapshot taken in the middle of a period is bitwise the uninterrupted one
 Check values: on a state with a Gauss-law violation, a non-unitary link and
 charges off their Casimir shells, gauss_max, gauss_rms, unitarity_max and the
 Casimir deviations equal the oracle's (Gauss constraint of Sec. 2; Casimirs
-of App. A) at 1e-10."""
+of App. A) at 1e-10; on an FP32 state, the check values and the squared site
+fields equal the oracle's of the same stored values."""
 import math
 
 import numpy as np
@@ -260,6 +261,40 @@ def test_field_check_values_equal_the_oracle():
     assert abs(o.gauss_max - want_max) <= 1e-10 * want_max
     assert abs(o.gauss_rms - want_rms) <= 1e-10 * want_rms
     assert abs(o.unitarity_max - want_u) <= 1e-10 * want_u
+
+
+def test_fp32_check_values_equal_the_oracle_on_the_same_state():
+    """The FP64 checks of an FP32 state (links with their third row rebuilt
+    from the two stored ones, momenta and site fields as stored) against the
+    oracle's Gauss residual, unitarity and squared site fields of the same
+    values, downloaded exactly.  The residuals are small differences of O(1)
+    terms summed in another order on each side (relative 1e-8); the squared
+    site fields are summed as exact float pairs on the GPU (relative 1e-12)."""
+    sp = [W.Species(W.M_CHARM, 0.0, 200, W.REP_F, W.MOM_FIXED_PT, 0.5)]
+    w = wl(24, W.FP32_2ROW, species=sp, seed=7)
+    ev = B.Event(w)
+    ev.glasma_init()
+    ev.wong_init()
+    ev.step(12)
+    o = ev.observables()
+    st = download_state(ev)
+    G = O.gauss(st)
+    g2 = (G * G).sum(1)
+    want_max, want_rms = math.sqrt(g2.max()), math.sqrt(g2.mean())
+    want_u, _ = O.unitarity(st)
+    site = ev.download(B.GL_BUF_SITE)
+    tr = 0.5 * (site ** 2).sum(axis=2)
+    V = w.N * w.N
+    want = {"mean_trE_T2": (tr[0] + tr[1]).sum() / V, "mean_trE_L2": tr[2].sum() / V,
+            "mean_trB_T2": (tr[3] + tr[4]).sum() / V, "mean_trB_L2": tr[5].sum() / V}
+    print("gauss_max %.6e/%.6e gauss_rms %.6e/%.6e unitarity_max %.6e/%.6e"
+          % (o.gauss_max, want_max, o.gauss_rms, want_rms, o.unitarity_max, want_u))
+    assert 0 < want_max < 1e-4 and 0 < want_u < 1e-4
+    assert abs(o.gauss_max - want_max) <= 1e-8 * want_max
+    assert abs(o.gauss_rms - want_rms) <= 1e-8 * want_rms
+    assert abs(o.unitarity_max - want_u) <= 1e-8 * want_u
+    for f, v in want.items():
+        assert v > 0 and abs(getattr(o, f) - v) <= 1e-12 * v, (f, getattr(o, f), v)
 
 
 def test_casimir_deviations_equal_the_oracle():
