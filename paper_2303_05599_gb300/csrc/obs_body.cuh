@@ -12,7 +12,7 @@
 // Per-particle quantities are evaluated in the state's precision.  Within a
 // block each thread accumulates its own particles (c0 + tid, c0 + tid +
 // OBS_THREADS, ...) into its own column of shared memory, then a fixed-order
-// reduction combines the columns (per row: each lane over four columns, then a
+// reduction combines the columns (per row: each lane over eight columns, then a
 // shuffle tree).  FP64 issue is the scarce
 // resource of this reduction (GB300 runs FP64 at 1/64 of the FP32 rate), so a
 // particle of an FP32 state costs one FP64 add (p_T^2(tau_form), stored in
