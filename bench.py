@@ -595,7 +595,9 @@ def run_ours(args):
             "roofline": dict(roof[dom], kernel=dom),
             "roofline_kernels": roof,
             "e2e": dict({"value": world * sites * K / e2e_t, "unit": "site-updates/s",
-                         "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": len(ws) * ctypes.sizeof(B.gl_obs),
+                         "h2d_bytes_per_step": h2d / K,
+                         # one request of every event's rows a step, and the final report
+                         "d2h_bytes_per_step": len(ws) * B.lib().gl_batch_obs_row_bytes() * (K + 1) / K,
                          "includes": "gl_batch_upload_native of every event's fields and particles from pinned "
                                      "host memory (native snapshots: the device layout, from gl_download_native); "
                                      "K x (gl_batch_step(1) + the per-species particle sums of every event read "

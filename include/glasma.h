@@ -429,6 +429,12 @@ gl_status gl_batch_observables_ex(gl_batch* batch, uint32_t what, gl_obs* out);
 gl_status gl_batch_observables_begin(gl_batch* batch, uint32_t what);
 gl_status gl_batch_observables_end(gl_batch* batch, gl_obs* out);
 
+/* Bytes of one event's results in the one device-to-host copy of a batch
+ * observables request: GL_MAX_SPECIES x 7 per-species values and the 7 field
+ * check values, FP64, which the host unpacks into the event's gl_obs record.
+ * Host only: no GPU work, no error. */
+size_t gl_batch_obs_row_bytes(void);
+
 /* Largest particle count gl_ensemble_sums_noalloc accepts. */
 #define GL_NOALLOC_MAX_PARTICLES 2097152
 

@@ -100,6 +100,7 @@ SIGNATURES = {
     "gl_batch_observables_ex": (ctypes.c_int, [_P, ctypes.c_uint32, _P]),
     "gl_batch_observables_begin": (ctypes.c_int, [_P, ctypes.c_uint32]),
     "gl_batch_observables_end": (ctypes.c_int, [_P, _P]),
+    "gl_batch_obs_row_bytes": (ctypes.c_size_t, []),
     "gl_batch_segment_rows": (ctypes.c_int32, [_P]),
     "gl_batch_set_segment_rows": (ctypes.c_int, [_P, ctypes.c_int32]),
 }

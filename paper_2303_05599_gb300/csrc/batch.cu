@@ -596,6 +596,8 @@ static float time_trial(gl_batch* b, cudaEvent_t e0, cudaEvent_t e1, int reps, F
 
 extern "C" {
 
+size_t gl_batch_obs_row_bytes(void) { return sizeof(double) * OBS_W; }
+
 size_t gl_batch_workspace_bytes(const gl_config* cfgs, const gl_species* species, int32_t n_species,
                                 int32_t n_events) {
     if (!cfgs || n_events < 1 || n_events > MAX_EVENTS) return 0;

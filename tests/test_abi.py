@@ -35,6 +35,14 @@ def test_every_declared_symbol_is_exported():
     assert set(names) <= set(B.SIGNATURES)
 
 
+def test_batch_obs_row_bytes():
+    # GL_MAX_SPECIES x 7 per-species values and 7 field check values, FP64;
+    # host only, so it is called here without a GPU
+    n = B.lib().gl_batch_obs_row_bytes()
+    assert n == 8 * (B.GL_MAX_SPECIES * 7 + 7)
+    assert n <= ctypes.sizeof(B.gl_obs)
+
+
 def test_struct_sizes_match_header():
     # gl_config: 4 int32 + 5 double + uint64 + 2 int32; gl_species: 2 double + int64 + 2 int32 + 2 double
     assert ctypes.sizeof(B.gl_config) == 16 + 40 + 8 + 8 + 8
