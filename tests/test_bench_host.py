@@ -1,6 +1,7 @@
 """Host-side logic of bench.py, without a GPU: the algorithmic bytes behind
-the roofline, the count of sort launches the JSON line claims, and the
-summary of the nvidia-smi clock samples."""
+the roofline, the count of sort launches the JSON line claims, the summary
+of the nvidia-smi clock samples, and the reference arm (the oracle on the
+host cores) end to end."""
 import math
 import os
 import sys
@@ -130,3 +131,23 @@ def test_nvml_clock_sampler(monkeypatch):
     assert fake.bus == b"00000000:1b:00.0"
     assert rec["samples"] >= 2 and rec["sm_mhz"] == 1980.0 and rec["sm_max_mhz"] == 2070.0
     assert rec["reasons"] == ["sw_power_cap"] and rec["source"] == "nvml"
+
+
+def test_reference_arm_prints_one_line_without_a_gpu():
+    # the reference arm times the oracle on the host cores: one JSON line with
+    # the arm's metric and unit, no host-device bytes, and the oracle as its
+    # CPU baseline (a few seconds of CPU work at one step)
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "site-updates/s" and d["value"] > 0
+    assert d["higher_is_better"] is True and d["steps"] == 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["config"]["workload"] == "batched64"
